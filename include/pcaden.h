@@ -1,0 +1,185 @@
+/*
+ * pcaden -- lazy Probabilistic Cellular Automaton (PCA) sampler for Bayesian
+ * image denoising on one NVIDIA GB300 (sm_103a).  C ABI.
+ *
+ * Method: Costarelli, Piconi, Troiani, "Bayesian Inversion via Probabilistic
+ * Cellular Automata: an application to image denoising" (arXiv 2507.14869).
+ *
+ * A chain holds a label image x (H x W, labels 0..L-1) and samples, sweep by
+ * sweep, an approximation of the denoising posterior of Section 2 (Bayes'
+ * rule with a Gibbs prior, Eq. gibbs-prior, and a noise likelihood,
+ * Eq. likelihood_general_expression).  Two samplers:
+ *
+ *   PCAD_SAMPLER_PCA       the lazy PCA of Section 5.2 (Eq.
+ *                          posterior_pca_transition_matrix): every pixel is
+ *                          resampled simultaneously from its conditional on
+ *                          the previous configuration, with an inertial price
+ *                          lambda * 1{s != x_i} for changing label;
+ *   PCAD_SAMPLER_GIBBS_CB  the single-site Gibbs sampler of Section 5.1
+ *                          (Eq. gibbs_sampler_elementary_step) in checkerboard
+ *                          colour order (2 colours for the 4-neighbourhood, 4
+ *                          for the 8-neighbourhood), in place.
+ *
+ * Energy of label s at site i (lower = likelier), in natural-log units:
+ *   E_i(s) = sum_{j in N(i)} V(s, x_j) + U(g_i, s) + lambda * 1{s != x_i}
+ *   V(s,t) = -pair_coef * 1{s = t}              (Potts, Eq. prior_pair_potential;
+ *                                                pair_coef = c_P = 2 beta J)
+ *          =  pair_coef * min(|s - t|, pair_T)  (truncated linear)
+ *   U(g,s) = (g - s)^2 / (2 sigma^2)            (Gaussian, sigma in label units)
+ *          = -ln(1-p) if s = g else -ln p       (flip channel, L = 2 only)
+ * N(i) is the 4- or 8-neighbourhood (Eq. neighborhood); neighbours outside
+ * the image are dropped (free boundary).  The initial state is the
+ * observation g.  Draws are inverse-CDF in label order with a 24-bit uniform
+ * from Philox4x32-10 keyed by (seed, chain, sweep, row, col) (see DRAWS).
+ *
+ * DRAWS.  Counter (col >> 2, row, sweep, (tag << 24) | chain), key (seed low,
+ * seed high), word col & 3, u = (word >> 8) * 2^-24; tag 0 = PCA, 1 = Gibbs.
+ * New label = smallest k with u * Z < C_k, C_k = sum_{s <= k} exp(-E_i(s)),
+ * Z = C_{L-1}.  The kernels evaluate this in FP32 with a rigorous error
+ * bound and re-evaluate in FP64 every draw whose uniform lies within that
+ * bound of a CDF boundary; such draws are counted (pcad_chain_stats).
+ *
+ * CONVENTIONS.
+ *   - Every function returns a pcad_status; nothing throws across the ABI.
+ *     On failure, output handles are set to NULL and pcad_last_error()
+ *     returns a message for the calling thread.
+ *   - Images are row-major uint8 label planes; "pitch" is the distance in
+ *     bytes between rows (>= W).  Host buffers are owned by the caller.
+ *   - A chain owns its device memory (allocated on its stream) and is not
+ *     thread-safe: one host thread at a time.  cuda_stream is a cudaStream_t
+ *     (NULL = the legacy default stream); run calls are asynchronous on it,
+ *     read calls synchronise it.
+ *   - Limits: 2 <= L <= 256; nbhd 4 or 8; 1 <= H, W <= 65535 (H*W <= 2^31);
+ *     prior range (pair_coef * nbhd * pair_T, or |pair_coef| * nbhd for
+ *     Potts) <= 40; 0 <= lambda <= 40; flip only with L = 2 and
+ *     |ln((1-p)/p)| <= 40; chain id < 2^24.  The posterior-mean accumulator
+ *     is FP32 and exact while (L-1) * (accumulated sweeps) < 2^24; run calls
+ *     that would pass that bound fail with PCAD_EINVAL.
+ */
+#ifndef PCADEN_H
+#define PCADEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PCAD_OK = 0,
+    PCAD_EINVAL = 1,   /* invalid argument or parameter outside the limits */
+    PCAD_ENOMEM = 2,   /* device or host allocation failed / budget exceeded */
+    PCAD_ECUDA = 3,    /* a CUDA runtime call failed */
+    PCAD_ETIMEOUT = 4, /* a bounded device-side wait gave up */
+    PCAD_ESTATE = 5    /* call not valid in the object's current state */
+} pcad_status;
+
+typedef enum { PCAD_PAIR_POTTS = 0, PCAD_PAIR_TRUNC_LINEAR = 1 } pcad_pair;
+typedef enum { PCAD_NOISE_GAUSS = 0, PCAD_NOISE_FLIP = 1 } pcad_noise;
+typedef enum { PCAD_SAMPLER_PCA = 0, PCAD_SAMPLER_GIBBS_CB = 1 } pcad_sampler;
+
+/* Model parameters (Sections 4-5).  pair_coef: Potts reward c_P = 2 beta J or
+ * truncated-linear slope c_T; pair_T: truncation (ignored for Potts); sigma:
+ * Gaussian std in label units; flip_p: flip probability; inertia: lambda =
+ * beta q (0 gives the naive synchronous update; ignored by Gibbs). */
+typedef struct {
+    int L;
+    int nbhd;
+    int pair;        /* pcad_pair */
+    float pair_coef;
+    int pair_T;
+    int noise;       /* pcad_noise */
+    float sigma;
+    float flip_p;
+    float inertia;
+    int sampler;     /* pcad_sampler */
+} pcad_model;
+
+typedef struct pcad_chain pcad_chain;
+
+/* Create a chain from a host observation g (H x W labels, row pitch g_pitch
+ * bytes).  The state starts at g, the sweep counter at 0.  burn_in: number
+ * of initial sweeps not accumulated into the posterior mean.  Problem
+ * statement: Section 2 (noisy g, noise model, prior, inertia). */
+pcad_status pcad_chain_create(const uint8_t *g_host, int H, int W, int g_pitch,
+                              const pcad_model *m, uint64_t seed, uint32_t chain_id,
+                              int burn_in, void *cuda_stream, pcad_chain **out);
+
+/* Same, from a device observation (borrowed for the duration of the call and
+ * copied on cuda_stream). */
+pcad_status pcad_chain_create_dev(const uint8_t *g_dev, int H, int W, int g_pitch,
+                                  const pcad_model *m, uint64_t seed, uint32_t chain_id,
+                                  int burn_in, void *cuda_stream, pcad_chain **out);
+
+/* Run nsweeps sweeps (asynchronous; continues the sweep counter).  After the
+ * k-th sweep overall (k = 1, 2, ...), the state is added to the accumulator
+ * when k > burn_in (conditional-mean estimator, Section 2). */
+pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps);
+
+/* Block until the chain's queued work is done. */
+pcad_status pcad_chain_sync(pcad_chain *ch);
+
+/* Copy the current sample (the paper's retrieved image is the last sample,
+ * Section 6) to host memory (H rows of W bytes, row pitch out_pitch). */
+pcad_status pcad_chain_read_sample(pcad_chain *ch, uint8_t *host_out, int out_pitch);
+
+/* Copy the current sample to device memory (asynchronous on the chain's stream). */
+pcad_status pcad_chain_read_sample_dev(pcad_chain *ch, uint8_t *dev_out, int out_pitch);
+
+/* Posterior-mean estimate in label units (mean of the accumulated samples;
+ * for L = 2 the mean spin is 2 * value - 1), H x W floats, host memory.
+ * PCAD_ESTATE when nothing has been accumulated yet. */
+pcad_status pcad_chain_read_mean(pcad_chain *ch, float *host_out);
+
+/* Overwrite the current state with host labels (every label < L). */
+pcad_status pcad_chain_write_sample(pcad_chain *ch, const uint8_t *host_in, int in_pitch);
+
+/* Sweeps done so far and sweeps accumulated into the mean. */
+pcad_status pcad_chain_sweeps(const pcad_chain *ch, uint64_t *t, uint64_t *n_accumulated);
+
+/* Draws re-evaluated in FP64 because their uniform fell within the FP32
+ * error bound of a CDF boundary (synchronises the chain). */
+pcad_status pcad_chain_stats(pcad_chain *ch, uint64_t *fp64_draws);
+
+/* PSNR (dB) and SSIM of the chain's posterior mean against a clean host
+ * label image, luminance label/(L-1) (Section 6: PSNR with max x of the
+ * original; SSIM of Wang et al. 2004, 11x11 Gaussian window sigma 1.5,
+ * K1 = 0.01, K2 = 0.03, range 1, over window positions inside the image;
+ * images smaller than 11 use the single-window form).  Computed on the GPU
+ * in FP64.  which = 0: posterior mean, 1: current sample. */
+pcad_status pcad_chain_metrics(pcad_chain *ch, const uint8_t *clean_host, int clean_pitch,
+                               int which, double *psnr_db, double *ssim);
+
+/* PSNR / SSIM of an arbitrary estimate (label units, H x W floats, host)
+ * against clean labels (host), as above. */
+pcad_status pcad_metrics(const float *est_host, const uint8_t *clean_host, int H, int W,
+                         int L, double *psnr_db, double *ssim);
+
+/* Checkpoint: serialise the whole chain state (labels, accumulator,
+ * counters, model, RNG key) to a host blob.  With host_blob = NULL only the
+ * required size is written to *bytes.  Synchronises the chain. */
+pcad_status pcad_chain_export(pcad_chain *ch, void *host_blob, size_t *bytes);
+
+/* Re-create a chain from an exported blob on cuda_stream; continuing it is
+ * bit-identical to continuing the original. */
+pcad_status pcad_chain_import(const void *host_blob, size_t bytes, void *cuda_stream,
+                              pcad_chain **out);
+
+/* Release the chain's device memory (synchronises its stream).  NULL is a no-op. */
+void pcad_chain_destroy(pcad_chain *ch);
+
+/* Static description of a status code. */
+const char *pcad_status_str(pcad_status s);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *pcad_last_error(void);
+
+/* Library version string. */
+const char *pcad_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCADEN_H */

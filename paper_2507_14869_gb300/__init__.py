@@ -1,0 +1,16 @@
+"""GB300-native lazy Probabilistic Cellular Automaton sampler for Bayesian
+image denoising (arXiv 2507.14869).
+
+The computation lives in ``libpcaden.so`` (hand-written CUDA for sm_103a,
+C ABI declared in ``include/pcaden.h``).  This package is the thin ctypes
+binding with the same entry-point names, plus the build step.
+"""
+from ._capi import (  # noqa: F401
+    NOISE_FLIP, NOISE_GAUSS, PAIR_POTTS, PAIR_TRUNC_LINEAR, SAMPLER_GIBBS_CB, SAMPLER_PCA,
+    Chain, PcadError, PcadModel, as_model, lib, library_path,
+    pcad_chain_create, pcad_chain_create_dev, pcad_chain_destroy, pcad_chain_export,
+    pcad_chain_import, pcad_chain_metrics, pcad_chain_read_mean, pcad_chain_read_sample,
+    pcad_chain_read_sample_dev, pcad_chain_run, pcad_chain_stats, pcad_chain_sweeps,
+    pcad_chain_sync, pcad_chain_write_sample, pcad_last_error, pcad_metrics, pcad_status_str,
+    pcad_version,
+)

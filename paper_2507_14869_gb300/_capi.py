@@ -1,0 +1,328 @@
+"""ctypes binding of libpcaden (include/pcaden.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and raises
+PcadError on a non-zero status.  All computation happens in the library's
+CUDA kernels; there is no fallback path.  Device pointers and CUDA streams
+may come from PyTorch (``tensor.data_ptr()``, ``stream.cuda_stream``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+PAIR_POTTS, PAIR_TRUNC_LINEAR = 0, 1
+NOISE_GAUSS, NOISE_FLIP = 0, 1
+SAMPLER_PCA, SAMPLER_GIBBS_CB = 0, 1
+
+
+class PcadError(RuntimeError):
+    def __init__(self, fn: str, status: int, msg: str):
+        super().__init__(f"{fn} failed: status {status} ({_status_name(status)}): {msg}")
+        self.status = status
+
+
+def _status_name(s: int) -> str:
+    return {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ETIMEOUT", 5: "ESTATE"}.get(s, "?")
+
+
+class PcadModel(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("nbhd", ctypes.c_int), ("pair", ctypes.c_int),
+                ("pair_coef", ctypes.c_float), ("pair_T", ctypes.c_int),
+                ("noise", ctypes.c_int), ("sigma", ctypes.c_float),
+                ("flip_p", ctypes.c_float), ("inertia", ctypes.c_float),
+                ("sampler", ctypes.c_int)]
+
+
+def as_model(m, sampler=None) -> PcadModel:
+    """PcadModel from a PcadModel, a dict or any object with the same fields."""
+    if isinstance(m, PcadModel):
+        out = PcadModel.from_buffer_copy(m)
+    else:
+        d = m if isinstance(m, dict) else {f: getattr(m, f) for f, _ in PcadModel._fields_
+                                           if hasattr(m, f)}
+        out = PcadModel(L=int(d["L"]), nbhd=int(d.get("nbhd", 4)), pair=int(d.get("pair", 1)),
+                        pair_coef=float(d.get("pair_coef", 0.0)), pair_T=int(d.get("pair_T", 1)),
+                        noise=int(d.get("noise", 0)), sigma=float(d.get("sigma", 1.0)),
+                        flip_p=float(d.get("flip_p", 0.1)), inertia=float(d.get("inertia", 0.0)),
+                        sampler=int(d.get("sampler", 0)))
+    if sampler is not None:
+        out.sampler = int(sampler)
+    return out
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libpcaden.so, building it first if it is missing or stale."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError("libpcaden.so is missing and could not be built")
+            L = ctypes.CDLL(path)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _declare(L):
+    vp, u8p, fp, dp = (ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint8),
+                       ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_double))
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    mp = ctypes.POINTER(PcadModel)
+    sig = {
+        "pcad_chain_create": [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, mp, ctypes.c_uint64,
+                              ctypes.c_uint32, ctypes.c_int, vp, ctypes.POINTER(vp)],
+        "pcad_chain_create_dev": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, mp,
+                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, vp,
+                                  ctypes.POINTER(vp)],
+        "pcad_chain_run": [vp, ctypes.c_int],
+        "pcad_chain_sync": [vp],
+        "pcad_chain_read_sample": [vp, u8p, ctypes.c_int],
+        "pcad_chain_read_sample_dev": [vp, vp, ctypes.c_int],
+        "pcad_chain_read_mean": [vp, fp],
+        "pcad_chain_write_sample": [vp, u8p, ctypes.c_int],
+        "pcad_chain_sweeps": [vp, u64p, u64p],
+        "pcad_chain_stats": [vp, u64p],
+        "pcad_chain_metrics": [vp, u8p, ctypes.c_int, ctypes.c_int, dp, dp],
+        "pcad_metrics": [fp, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp],
+        "pcad_chain_export": [vp, vp, ctypes.POINTER(ctypes.c_size_t)],
+        "pcad_chain_import": [vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.pcad_chain_destroy.argtypes = [vp]
+    L.pcad_chain_destroy.restype = None
+    L.pcad_status_str.argtypes = [ctypes.c_int]
+    L.pcad_status_str.restype = ctypes.c_char_p
+    L.pcad_last_error.argtypes = []
+    L.pcad_last_error.restype = ctypes.c_char_p
+    L.pcad_version.argtypes = []
+    L.pcad_version.restype = ctypes.c_char_p
+
+
+def _check(name: str, status: int):
+    if status != 0:
+        raise PcadError(name, status, lib().pcad_last_error().decode(errors="replace"))
+
+
+def _u8(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.uint8)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return ctypes.c_void_p(int(s.cuda_stream))
+    return ctypes.c_void_p(int(s))
+
+
+# ------------------------------------------------------------- entry points
+
+def pcad_chain_create(g, model, seed: int, chain_id: int = 0, burn_in: int = 0, stream=None):
+    g = _u8(g)
+    H, W = g.shape
+    h = ctypes.c_void_p()
+    m = as_model(model)
+    _check("pcad_chain_create",
+           lib().pcad_chain_create(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), H, W, W,
+                                   ctypes.byref(m), int(seed), int(chain_id), int(burn_in),
+                                   _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def pcad_chain_create_dev(g_dev_ptr: int, H: int, W: int, pitch: int, model, seed: int,
+                          chain_id: int = 0, burn_in: int = 0, stream=None):
+    h = ctypes.c_void_p()
+    m = as_model(model)
+    _check("pcad_chain_create_dev",
+           lib().pcad_chain_create_dev(ctypes.c_void_p(int(g_dev_ptr)), H, W, pitch,
+                                       ctypes.byref(m), int(seed), int(chain_id), int(burn_in),
+                                       _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def pcad_chain_run(h, nsweeps: int):
+    _check("pcad_chain_run", lib().pcad_chain_run(h, int(nsweeps)))
+
+
+def pcad_chain_sync(h):
+    _check("pcad_chain_sync", lib().pcad_chain_sync(h))
+
+
+def pcad_chain_read_sample(h, H: int, W: int) -> np.ndarray:
+    out = np.empty((H, W), dtype=np.uint8)
+    _check("pcad_chain_read_sample",
+           lib().pcad_chain_read_sample(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), W))
+    return out
+
+
+def pcad_chain_read_sample_dev(h, dev_ptr: int, pitch: int):
+    _check("pcad_chain_read_sample_dev",
+           lib().pcad_chain_read_sample_dev(h, ctypes.c_void_p(int(dev_ptr)), int(pitch)))
+
+
+def pcad_chain_read_mean(h, H: int, W: int) -> np.ndarray:
+    out = np.empty((H, W), dtype=np.float32)
+    _check("pcad_chain_read_mean",
+           lib().pcad_chain_read_mean(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def pcad_chain_write_sample(h, x):
+    x = _u8(x)
+    _check("pcad_chain_write_sample",
+           lib().pcad_chain_write_sample(h, x.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                         x.shape[1]))
+
+
+def pcad_chain_sweeps(h):
+    t = ctypes.c_uint64()
+    n = ctypes.c_uint64()
+    _check("pcad_chain_sweeps", lib().pcad_chain_sweeps(h, ctypes.byref(t), ctypes.byref(n)))
+    return int(t.value), int(n.value)
+
+
+def pcad_chain_stats(h) -> int:
+    v = ctypes.c_uint64()
+    _check("pcad_chain_stats", lib().pcad_chain_stats(h, ctypes.byref(v)))
+    return int(v.value)
+
+
+def pcad_chain_metrics(h, clean, which: int = 0):
+    clean = _u8(clean)
+    p = ctypes.c_double()
+    s = ctypes.c_double()
+    _check("pcad_chain_metrics",
+           lib().pcad_chain_metrics(h, clean.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+                                    clean.shape[1], int(which), ctypes.byref(p), ctypes.byref(s)))
+    return float(p.value), float(s.value)
+
+
+def pcad_metrics(est, clean, L: int):
+    est = np.ascontiguousarray(est, dtype=np.float32)
+    clean = _u8(clean)
+    H, W = clean.shape
+    p = ctypes.c_double()
+    s = ctypes.c_double()
+    _check("pcad_metrics",
+           lib().pcad_metrics(est.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                              clean.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), H, W, int(L),
+                              ctypes.byref(p), ctypes.byref(s)))
+    return float(p.value), float(s.value)
+
+
+def pcad_chain_export(h) -> bytes:
+    n = ctypes.c_size_t(0)
+    _check("pcad_chain_export", lib().pcad_chain_export(h, None, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check("pcad_chain_export", lib().pcad_chain_export(h, buf, ctypes.byref(n)))
+    return buf.raw[: n.value]
+
+
+def pcad_chain_import(blob: bytes, stream=None):
+    h = ctypes.c_void_p()
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check("pcad_chain_import",
+           lib().pcad_chain_import(buf, len(blob), _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def pcad_chain_destroy(h):
+    if h is not None and h.value:
+        lib().pcad_chain_destroy(h)
+
+
+def pcad_status_str(s: int) -> str:
+    return lib().pcad_status_str(int(s)).decode()
+
+
+def pcad_last_error() -> str:
+    return lib().pcad_last_error().decode(errors="replace")
+
+
+def pcad_version() -> str:
+    return lib().pcad_version().decode()
+
+
+class Chain:
+    """Owning wrapper of a pcad_chain handle."""
+
+    def __init__(self, g, model, seed: int, chain_id: int = 0, burn_in: int = 0, stream=None,
+                 sampler=None, _handle=None, _shape=None):
+        if _handle is not None:
+            self.h = _handle
+            self.H, self.W = _shape
+            self.L = None
+            return
+        g = _u8(g)
+        self.H, self.W = g.shape
+        m = as_model(model, sampler)
+        self.L = m.L
+        self.h = pcad_chain_create(g, m, seed, chain_id, burn_in, stream)
+
+    @classmethod
+    def from_blob(cls, blob: bytes, stream=None):
+        h = pcad_chain_import(blob, stream)
+        import struct
+        H, W = struct.unpack_from("<ii", blob, 12)
+        return cls(None, None, 0, _handle=h, _shape=(H, W))
+
+    def run(self, n: int):
+        pcad_chain_run(self.h, n)
+        return self
+
+    def sync(self):
+        pcad_chain_sync(self.h)
+
+    def sample(self) -> np.ndarray:
+        return pcad_chain_read_sample(self.h, self.H, self.W)
+
+    def mean(self) -> np.ndarray:
+        return pcad_chain_read_mean(self.h, self.H, self.W)
+
+    def set_sample(self, x):
+        pcad_chain_write_sample(self.h, x)
+
+    def sweeps(self):
+        return pcad_chain_sweeps(self.h)
+
+    def fp64_draws(self) -> int:
+        return pcad_chain_stats(self.h)
+
+    def metrics(self, clean, which: int = 0):
+        return pcad_chain_metrics(self.h, clean, which)
+
+    def export(self) -> bytes:
+        return pcad_chain_export(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            pcad_chain_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

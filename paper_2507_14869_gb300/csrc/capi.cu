@@ -1,0 +1,700 @@
+// C ABI and chain runtime (see include/pcaden.h for the contract).
+//
+// A chain owns, in one stream-ordered device allocation: two label planes
+// (ping-pong for the synchronous PCA update; Gibbs updates one in place),
+// the observation, the FP32 accumulator, the model tables, the device sweep
+// counter and the FP64-redraw counter.  Sweeps are issued in blocks of
+// kGraphSweeps captured once per chain into a CUDA graph: every kernel reads
+// its sweep index as *counter + offset and the block ends with a one-thread
+// kernel that advances the counter, so one instantiated graph replays any
+// block (the ping-pong parity returns to 0 after an even number of sweeps).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/pcaden.h"
+#include "pcad_internal.h"
+
+using namespace pcad;
+
+namespace {
+
+thread_local std::string g_err;
+constexpr int kGraphSweeps = 32;    // sweeps per captured block (even)
+constexpr int kTable = 511;
+
+pcad_status fail(pcad_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(call)                                                                  \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(PCAD_ECUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+pcad_status validate_model(const pcad_model *m)
+{
+    if (!m)
+        return fail(PCAD_EINVAL, "model is NULL");
+    if (m->L < 2 || m->L > 256)
+        return fail(PCAD_EINVAL, "L=%d outside [2, 256]", m->L);
+    if (m->nbhd != 4 && m->nbhd != 8)
+        return fail(PCAD_EINVAL, "nbhd=%d must be 4 or 8", m->nbhd);
+    if (m->pair != PCAD_PAIR_POTTS && m->pair != PCAD_PAIR_TRUNC_LINEAR)
+        return fail(PCAD_EINVAL, "unknown pair potential %d", m->pair);
+    if (m->noise != PCAD_NOISE_GAUSS && m->noise != PCAD_NOISE_FLIP)
+        return fail(PCAD_EINVAL, "unknown noise model %d", m->noise);
+    if (m->sampler != PCAD_SAMPLER_PCA && m->sampler != PCAD_SAMPLER_GIBBS_CB)
+        return fail(PCAD_EINVAL, "unknown sampler %d", m->sampler);
+    if (!std::isfinite(m->pair_coef))
+        return fail(PCAD_EINVAL, "pair_coef not finite");
+    const int T = m->pair == PCAD_PAIR_POTTS ? 1 : m->pair_T;
+    if (m->pair == PCAD_PAIR_TRUNC_LINEAR && (m->pair_T < 0 || m->pair_T > 255))
+        return fail(PCAD_EINVAL, "pair_T=%d outside [0, 255]", m->pair_T);
+    if (std::fabs((double)m->pair_coef) * m->nbhd * T > 40.0)
+        return fail(PCAD_EINVAL, "prior range |pair_coef|*nbhd*T = %g exceeds 40",
+                    std::fabs((double)m->pair_coef) * m->nbhd * T);
+    if (m->noise == PCAD_NOISE_GAUSS) {
+        if (!(m->sigma > 0.0f) || !std::isfinite(m->sigma))
+            return fail(PCAD_EINVAL, "sigma must be positive and finite");
+    } else {
+        if (m->L != 2)
+            return fail(PCAD_EINVAL, "flip noise needs L=2");
+        if (!(m->flip_p > 0.0f && m->flip_p < 1.0f))
+            return fail(PCAD_EINVAL, "flip_p must be in (0, 1)");
+        const double p = m->flip_p;
+        if (std::fabs(std::log((1.0 - p) / p)) > 40.0)
+            return fail(PCAD_EINVAL, "|ln((1-p)/p)| exceeds 40");
+    }
+    if (!(m->inertia >= 0.0f && m->inertia <= 40.0f))
+        return fail(PCAD_EINVAL, "inertia must be in [0, 40]");
+    return PCAD_OK;
+}
+
+// Host copy of the model tables and the FP32 error bound.
+struct ModelTables {
+    float ta32[kTable];
+    double ta64[kTable];
+    std::vector<double> pr64;
+    DevModel dm;  // table pointers filled once uploaded
+};
+
+void build_tables(const pcad_model &m, ModelTables &t)
+{
+    const int T = m.pair == PCAD_PAIR_POTTS ? 1 : m.pair_T;
+    const int pmax = m.nbhd * T;
+    const double c = (double)m.pair_coef;
+    for (int d = -255; d <= 255; ++d) {
+        double v;
+        if (m.noise == PCAD_NOISE_GAUSS) {
+            const double s = (double)m.sigma;
+            const double a = 1.0 / (2.0 * s * s);
+            v = std::exp(-(a * (double)(d * d)));
+        } else {
+            const double p = (double)m.flip_p;
+            v = d == 0 ? 1.0 : (std::abs(d) == 1 ? p / (1.0 - p) : 0.0);
+        }
+        t.ta64[d + 255] = v;
+        t.ta32[d + 255] = (float)v;
+    }
+    t.pr64.assign(pmax + 1, 0.0);
+    for (int P = 0; P <= pmax; ++P)
+        t.pr64[P] = std::exp(-(c * (double)P));
+    const double lam = m.sampler == PCAD_SAMPLER_PCA ? (double)m.inertia : 0.0;
+    DevModel &d = t.dm;
+    d.L = m.L;
+    d.nbhd = m.nbhd;
+    d.T = T;
+    d.pmax = pmax;
+    d.gam = (float)(-c * 1.4426950408889634074);
+    d.Tf = (float)T;
+    d.em1 = (float)std::expm1(lam);
+    d.el64 = std::exp(lam);
+    // Rigorous bound on |C_k/Z (FP32) - F_k (exact)|: per-weight relative
+    // error e_w (table rounding, FMA rounding, exponent argument rounding
+    // 2u|gam|P ln 2, exp2f within 2 ulp) and summation error
+    // (8 in-chunk + NC chunk-level + 4 combining additions) u, doubled for
+    // the ratio, plus the uniform's product rounding; 1.5x slack.
+    const double u = 5.9604644775390625e-08;
+    const double e_w = 2.0 * u + 2.384185791015625e-07 +
+                       2.0 * u * 0.6931471805599453 * std::fabs((double)d.gam) * pmax;
+    const double gsum = (double)(kChunk + chunk_class(m.L) + 4) * u;
+    d.eta = (float)(1.5 * (3.0 * e_w + 2.0 * gsum) + 8.0 * u);
+    d.ta32 = nullptr;
+    d.ta64 = nullptr;
+    d.pr64 = nullptr;
+}
+
+}  // namespace
+
+struct pcad_chain {
+    int H = 0, W = 0, pitch = 0;
+    pcad_model model{};
+    uint64_t seed = 0;
+    uint32_t chain_id = 0;
+    int burn_in = 0;
+    uint64_t t = 0;      // host mirror of the device sweep counter
+    uint64_t n_acc = 0;
+    int cur = 0;         // PCA: plane holding the current state
+    cudaStream_t stream = nullptr;
+    void *block = nullptr;   // single device allocation
+    uint8_t *x[2] = {nullptr, nullptr};
+    uint8_t *g = nullptr;
+    float *acc = nullptr;
+    float *fplane = nullptr;      // H*W floats for read-back / metrics
+    uint8_t *clean = nullptr;     // H*W bytes for metrics input
+    uint32_t *tdev = nullptr;
+    unsigned long long *fp64 = nullptr;
+    double *mscratch = nullptr;   // 8 scratch + 2 results
+    float *ta32 = nullptr;
+    double *ta64 = nullptr, *pr64 = nullptr;
+    DevModel dm{};
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+SweepArgs make_args(const pcad_chain *ch)
+{
+    SweepArgs a{};
+    a.g = ch->g;
+    a.acc = ch->acc;
+    a.fp64_draws = ch->fp64;
+    a.sweep_base = ch->tdev;
+    a.seed = ch->seed;
+    a.H = ch->H;
+    a.W = ch->W;
+    a.pitch = ch->pitch;
+    a.chain = ch->chain_id;
+    a.burn_in = ch->burn_in;
+    a.m = ch->dm;
+    return a;
+}
+
+// Issue sweeps [*counter + off0, *counter + off0 + n) without advancing the counter.
+pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t st)
+{
+    SweepArgs a = make_args(ch);
+    const int ncol = ch->model.nbhd == 4 ? 2 : 4;
+    for (int k = 0; k < n; ++k) {
+        a.sweep_off = (uint32_t)(off0 + k);
+        if (ch->model.sampler == PCAD_SAMPLER_PCA) {
+            a.xin = ch->x[cur];
+            a.xout = ch->x[cur ^ 1];
+            CUDA_TRY(launch_pca_sweep(a, st));
+            cur ^= 1;
+        } else {
+            a.xin = ch->x[cur];
+            a.xout = nullptr;
+            for (int q = 0; q < ncol; ++q) {
+                a.last_phase = q == ncol - 1;
+                CUDA_TRY(launch_gibbs_phase(a, q, st));
+            }
+        }
+    }
+    return PCAD_OK;
+}
+
+pcad_status build_graph(pcad_chain *ch)
+{
+    cudaStream_t cap;
+    CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    pcad_status st = PCAD_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int cur = 0;
+        st = issue_sweeps(ch, 0, kGraphSweeps, cur, cap);
+        cudaError_t e2 = launch_advance(ch->tdev, kGraphSweeps, cap);
+        e = cudaStreamEndCapture(cap, &graph);
+        if (st == PCAD_OK && e2 != cudaSuccess)
+            st = fail(PCAD_ECUDA, "advance launch: %s", cudaGetErrorString(e2));
+    }
+    if (st == PCAD_OK && e != cudaSuccess)
+        st = fail(PCAD_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+    if (st == PCAD_OK) {
+        e = cudaGraphInstantiate(&ch->graph, graph, 0);
+        if (e != cudaSuccess)
+            st = fail(PCAD_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    }
+    if (graph)
+        cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    return st;
+}
+
+pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, int g_pitch,
+                          const pcad_model *m, uint64_t seed, uint32_t chain_id, int burn_in,
+                          void *cuda_stream, pcad_chain **out)
+{
+    if (!out)
+        return fail(PCAD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g_src)
+        return fail(PCAD_EINVAL, "g is NULL");
+    if (H < 1 || W < 1 || H > 65535 || W > 65535 || (long long)H * W > (1LL << 31))
+        return fail(PCAD_EINVAL, "image size %dx%d outside the limits", H, W);
+    if (g_pitch < W)
+        return fail(PCAD_EINVAL, "g_pitch %d < W %d", g_pitch, W);
+    if (burn_in < 0)
+        return fail(PCAD_EINVAL, "burn_in < 0");
+    if (chain_id >= (1u << 24))
+        return fail(PCAD_EINVAL, "chain id must be < 2^24");
+    pcad_status st = validate_model(m);
+    if (st != PCAD_OK)
+        return st;
+
+    ModelTables tabs;
+    build_tables(*m, tabs);
+
+    pcad_chain *ch = new pcad_chain();
+    ch->H = H;
+    ch->W = W;
+    ch->pitch = (int)align_up((size_t)W, 16);
+    ch->model = *m;
+    ch->seed = seed;
+    ch->chain_id = chain_id;
+    ch->burn_in = burn_in;
+    ch->stream = (cudaStream_t)cuda_stream;
+
+    const size_t plane = align_up((size_t)ch->pitch * H, 256);
+    const size_t fbytes = align_up((size_t)H * W * sizeof(float), 256);
+    const size_t cbytes = align_up((size_t)H * W, 256);
+    const size_t tbytes = align_up(kTable * sizeof(float), 256) +
+                          align_up(kTable * sizeof(double), 256) +
+                          align_up(tabs.pr64.size() * sizeof(double), 256);
+    const size_t misc = 256;
+    const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + misc;
+    cudaError_t e = cudaMallocAsync(&ch->block, total, ch->stream);
+    if (e != cudaSuccess) {
+        delete ch;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PCAD_ENOMEM : PCAD_ECUDA,
+                    "device allocation of %zu bytes: %s", total, cudaGetErrorString(e));
+    }
+    char *p = (char *)ch->block;
+    ch->x[0] = (uint8_t *)p; p += plane;
+    ch->x[1] = (uint8_t *)p; p += plane;
+    ch->g = (uint8_t *)p; p += plane;
+    ch->acc = (float *)p; p += fbytes;
+    ch->fplane = (float *)p; p += fbytes;
+    ch->clean = (uint8_t *)p; p += cbytes;
+    ch->ta32 = (float *)p; p += align_up(kTable * sizeof(float), 256);
+    ch->ta64 = (double *)p; p += align_up(kTable * sizeof(double), 256);
+    ch->pr64 = (double *)p; p += align_up(tabs.pr64.size() * sizeof(double), 256);
+    ch->tdev = (uint32_t *)p;
+    ch->fp64 = (unsigned long long *)(p + 8);
+    ch->mscratch = (double *)(p + 16);
+
+    auto cleanup = [&](pcad_status s) {
+        cudaFreeAsync(ch->block, ch->stream);
+        cudaStreamSynchronize(ch->stream);
+        delete ch;
+        return s;
+    };
+    const cudaMemcpyKind gk = g_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    e = cudaMemcpy2DAsync(ch->g, ch->pitch, g_src, g_pitch, W, H, gk, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpy2DAsync(ch->x[0], ch->pitch, ch->g, ch->pitch, W, H,
+                              cudaMemcpyDeviceToDevice, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ch->acc, 0, fbytes, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ch->ta32, tabs.ta32, sizeof(tabs.ta32), cudaMemcpyHostToDevice,
+                            ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ch->ta64, tabs.ta64, sizeof(tabs.ta64), cudaMemcpyHostToDevice,
+                            ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ch->pr64, tabs.pr64.data(), tabs.pr64.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(ch->tdev, 0, misc, ch->stream);
+    if (e == cudaSuccess) {
+        int *bad = (int *)(ch->mscratch);
+        e = launch_check_labels(ch->g, ch->pitch, H, W, m->L, bad, ch->stream);
+        int hbad = 0;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ch->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(ch->stream);
+        if (e == cudaSuccess && hbad != 0)
+            return cleanup(fail(PCAD_EINVAL, "%d observed labels are >= L=%d", hbad, m->L));
+    }
+    if (e != cudaSuccess)
+        return cleanup(fail(PCAD_ECUDA, "chain set-up: %s", cudaGetErrorString(e)));
+    ch->dm = tabs.dm;
+    ch->dm.ta32 = ch->ta32;
+    ch->dm.ta64 = ch->ta64;
+    ch->dm.pr64 = ch->pr64;
+    *out = ch;
+    return PCAD_OK;
+}
+
+bool acc_would_overflow(const pcad_chain *ch, uint64_t n)
+{
+    const uint64_t t1 = ch->t + n;
+    const uint64_t start = ch->t > (uint64_t)ch->burn_in ? ch->t : (uint64_t)ch->burn_in;
+    const uint64_t add = t1 > start ? t1 - start : 0;
+    return (uint64_t)(ch->model.L - 1) * (ch->n_acc + add) >= (1ull << 24);
+}
+
+}  // namespace
+
+extern "C" {
+
+pcad_status pcad_chain_create(const uint8_t *g_host, int H, int W, int g_pitch,
+                              const pcad_model *m, uint64_t seed, uint32_t chain_id,
+                              int burn_in, void *cuda_stream, pcad_chain **out)
+{
+    return create_common(g_host, false, H, W, g_pitch, m, seed, chain_id, burn_in, cuda_stream,
+                         out);
+}
+
+pcad_status pcad_chain_create_dev(const uint8_t *g_dev, int H, int W, int g_pitch,
+                                  const pcad_model *m, uint64_t seed, uint32_t chain_id,
+                                  int burn_in, void *cuda_stream, pcad_chain **out)
+{
+    return create_common(g_dev, true, H, W, g_pitch, m, seed, chain_id, burn_in, cuda_stream,
+                         out);
+}
+
+pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (nsweeps < 0)
+        return fail(PCAD_EINVAL, "nsweeps < 0");
+    if (nsweeps == 0)
+        return PCAD_OK;
+    if (ch->t + (uint64_t)nsweeps > 0xFFFFFFFFull)
+        return fail(PCAD_EINVAL, "sweep counter would exceed 2^32");
+    if (acc_would_overflow(ch, (uint64_t)nsweeps))
+        return fail(PCAD_EINVAL, "accumulator would leave the exact FP32 range");
+    int left = nsweeps;
+    // Whole captured blocks need the ping-pong parity at 0 (always true for Gibbs).
+    const bool parity_ok = ch->model.sampler != PCAD_SAMPLER_PCA || ch->cur == 0;
+    if (left >= kGraphSweeps && parity_ok) {
+        if (!ch->graph) {
+            pcad_status st = build_graph(ch);
+            if (st != PCAD_OK)
+                return st;
+        }
+        while (left >= kGraphSweeps) {
+            CUDA_TRY(cudaGraphLaunch(ch->graph, ch->stream));
+            left -= kGraphSweeps;
+        }
+    }
+    if (left > 0) {
+        int cur = ch->cur;
+        pcad_status st = issue_sweeps(ch, 0, left, cur, ch->stream);
+        if (st != PCAD_OK)
+            return st;
+        CUDA_TRY(launch_advance(ch->tdev, (uint32_t)left, ch->stream));
+        ch->cur = cur;
+    }
+    const uint64_t start = ch->t > (uint64_t)ch->burn_in ? ch->t : (uint64_t)ch->burn_in;
+    const uint64_t t1 = ch->t + (uint64_t)nsweeps;
+    ch->n_acc += t1 > start ? t1 - start : 0;
+    ch->t = t1;
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_sync(pcad_chain *ch)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_read_sample(pcad_chain *ch, uint8_t *host_out, int out_pitch)
+{
+    if (!ch || !host_out)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (out_pitch < ch->W)
+        return fail(PCAD_EINVAL, "out_pitch < W");
+    CUDA_TRY(cudaMemcpy2DAsync(host_out, out_pitch, ch->x[ch->cur], ch->pitch, ch->W, ch->H,
+                               cudaMemcpyDeviceToHost, ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_read_sample_dev(pcad_chain *ch, uint8_t *dev_out, int out_pitch)
+{
+    if (!ch || !dev_out)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (out_pitch < ch->W)
+        return fail(PCAD_EINVAL, "out_pitch < W");
+    CUDA_TRY(cudaMemcpy2DAsync(dev_out, out_pitch, ch->x[ch->cur], ch->pitch, ch->W, ch->H,
+                               cudaMemcpyDeviceToDevice, ch->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_read_mean(pcad_chain *ch, float *host_out)
+{
+    if (!ch || !host_out)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (ch->n_acc == 0)
+        return fail(PCAD_ESTATE, "no sweep accumulated yet");
+    const long n = (long)ch->H * ch->W;
+    CUDA_TRY(launch_mean(ch->acc, (float)ch->n_acc, ch->fplane, n, ch->stream));
+    CUDA_TRY(cudaMemcpyAsync(host_out, ch->fplane, n * sizeof(float), cudaMemcpyDeviceToHost,
+                             ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_write_sample(pcad_chain *ch, const uint8_t *host_in, int in_pitch)
+{
+    if (!ch || !host_in)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (in_pitch < ch->W)
+        return fail(PCAD_EINVAL, "in_pitch < W");
+    uint8_t *dst = ch->x[ch->cur];
+    CUDA_TRY(cudaMemcpy2DAsync(dst, ch->pitch, host_in, in_pitch, ch->W, ch->H,
+                               cudaMemcpyHostToDevice, ch->stream));
+    int *bad = (int *)ch->mscratch;
+    CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), ch->stream));
+    CUDA_TRY(launch_check_labels(dst, ch->pitch, ch->H, ch->W, ch->model.L, bad, ch->stream));
+    int hbad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    if (hbad)
+        return fail(PCAD_EINVAL, "%d labels are >= L", hbad);
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_sweeps(const pcad_chain *ch, uint64_t *t, uint64_t *n_accumulated)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (t)
+        *t = ch->t;
+    if (n_accumulated)
+        *n_accumulated = ch->n_acc;
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_stats(pcad_chain *ch, uint64_t *fp64_draws)
+{
+    if (!ch || !fp64_draws)
+        return fail(PCAD_EINVAL, "NULL argument");
+    unsigned long long v = 0;
+    CUDA_TRY(cudaMemcpyAsync(&v, ch->fp64, sizeof(v), cudaMemcpyDeviceToHost, ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    *fp64_draws = v;
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_metrics(pcad_chain *ch, const uint8_t *clean_host, int clean_pitch,
+                               int which, double *psnr_db, double *ssim)
+{
+    if (!ch || !clean_host)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (clean_pitch < ch->W)
+        return fail(PCAD_EINVAL, "clean_pitch < W");
+    const long n = (long)ch->H * ch->W;
+    if (which == 0) {
+        if (ch->n_acc == 0)
+            return fail(PCAD_ESTATE, "no sweep accumulated yet");
+        CUDA_TRY(launch_mean(ch->acc, (float)ch->n_acc, ch->fplane, n, ch->stream));
+    } else {
+        CUDA_TRY(launch_labels_to_float(ch->x[ch->cur], ch->pitch, ch->H, ch->W, ch->fplane,
+                                        ch->stream));
+    }
+    CUDA_TRY(cudaMemcpy2DAsync(ch->clean, ch->W, clean_host, clean_pitch, ch->W, ch->H,
+                               cudaMemcpyHostToDevice, ch->stream));
+    CUDA_TRY(launch_metrics(ch->fplane, ch->clean, ch->H, ch->W, ch->model.L, ch->mscratch,
+                            ch->mscratch + 8, ch->stream));
+    double res[2];
+    CUDA_TRY(cudaMemcpyAsync(res, ch->mscratch + 8, sizeof(res), cudaMemcpyDeviceToHost,
+                             ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    if (psnr_db)
+        *psnr_db = res[0];
+    if (ssim)
+        *ssim = res[1];
+    return PCAD_OK;
+}
+
+pcad_status pcad_metrics(const float *est_host, const uint8_t *clean_host, int H, int W, int L,
+                         double *psnr_db, double *ssim)
+{
+    if (!est_host || !clean_host)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (H < 1 || W < 1 || L < 2 || L > 256 || (long long)H * W < 2)
+        return fail(PCAD_EINVAL, "bad sizes");
+    const size_t n = (size_t)H * W;
+    void *blk = nullptr;
+    const size_t fb = align_up(n * sizeof(float), 256), cb = align_up(n, 256);
+    CUDA_TRY(cudaMalloc(&blk, fb + cb + 16 * sizeof(double)));
+    float *est = (float *)blk;
+    uint8_t *clean = (uint8_t *)((char *)blk + fb);
+    double *scr = (double *)((char *)blk + fb + cb);
+    double res[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(est, est_host, n * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(clean, clean_host, n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_metrics(est, clean, H, W, L, scr, scr + 8, 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(res, scr + 8, sizeof(res), cudaMemcpyDeviceToHost);
+    cudaFree(blk);
+    if (e != cudaSuccess)
+        return fail(PCAD_ECUDA, "metrics: %s", cudaGetErrorString(e));
+    if (psnr_db)
+        *psnr_db = res[0];
+    if (ssim)
+        *ssim = res[1];
+    return PCAD_OK;
+}
+
+namespace {
+struct BlobHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t H, W, burn_in;
+    pcad_model model;
+    uint64_t seed;
+    uint32_t chain_id;
+    uint32_t pad;
+    uint64_t t, n_acc, fp64;
+};
+const char kMagic[8] = {'P', 'C', 'A', 'D', 'C', 'H', 'N', '1'};
+}  // namespace
+
+pcad_status pcad_chain_export(pcad_chain *ch, void *host_blob, size_t *bytes)
+{
+    if (!ch || !bytes)
+        return fail(PCAD_EINVAL, "NULL argument");
+    const size_t n = (size_t)ch->H * ch->W;
+    const size_t need = sizeof(BlobHeader) + 2 * n + n * sizeof(float);
+    if (!host_blob) {
+        *bytes = need;
+        return PCAD_OK;
+    }
+    if (*bytes < need)
+        return fail(PCAD_EINVAL, "blob too small: %zu < %zu", *bytes, need);
+    BlobHeader h{};
+    memcpy(h.magic, kMagic, 8);
+    h.version = 1;
+    h.H = ch->H;
+    h.W = ch->W;
+    h.burn_in = ch->burn_in;
+    h.model = ch->model;
+    h.seed = ch->seed;
+    h.chain_id = ch->chain_id;
+    h.t = ch->t;
+    h.n_acc = ch->n_acc;
+    pcad_status st = pcad_chain_stats(ch, &h.fp64);
+    if (st != PCAD_OK)
+        return st;
+    char *b = (char *)host_blob;
+    memcpy(b, &h, sizeof(h));
+    // layout: header | current labels | observation | accumulator
+    CUDA_TRY(cudaMemcpy2DAsync(b + sizeof(h), ch->W, ch->x[ch->cur], ch->pitch, ch->W, ch->H,
+                               cudaMemcpyDeviceToHost, ch->stream));
+    CUDA_TRY(cudaMemcpy2DAsync(b + sizeof(h) + n, ch->W, ch->g, ch->pitch, ch->W, ch->H,
+                               cudaMemcpyDeviceToHost, ch->stream));
+    CUDA_TRY(cudaMemcpyAsync(b + sizeof(h) + 2 * n, ch->acc, n * sizeof(float),
+                             cudaMemcpyDeviceToHost, ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    *bytes = need;
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_import(const void *host_blob, size_t bytes, void *cuda_stream,
+                              pcad_chain **out)
+{
+    if (!out)
+        return fail(PCAD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!host_blob || bytes < sizeof(BlobHeader))
+        return fail(PCAD_EINVAL, "blob too small");
+    BlobHeader h;
+    memcpy(&h, host_blob, sizeof(h));
+    if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
+        return fail(PCAD_EINVAL, "not a pcaden chain blob");
+    if (h.H < 1 || h.W < 1 || h.H > 65535 || h.W > 65535 || h.t > 0xFFFFFFFFull)
+        return fail(PCAD_EINVAL, "corrupt blob header");
+    const size_t n = (size_t)h.H * h.W;
+    if (bytes < sizeof(h) + 2 * n + n * sizeof(float))
+        return fail(PCAD_EINVAL, "blob truncated");
+    const char *b = (const char *)host_blob;
+    pcad_chain *ch = nullptr;
+    pcad_status st = pcad_chain_create((const uint8_t *)(b + sizeof(h) + n), h.H, h.W, h.W,
+                                       &h.model, h.seed, h.chain_id, h.burn_in, cuda_stream, &ch);
+    if (st != PCAD_OK)
+        return st;
+    st = pcad_chain_write_sample(ch, (const uint8_t *)(b + sizeof(h)), h.W);
+    if (st != PCAD_OK) {
+        pcad_chain_destroy(ch);
+        return st;
+    }
+    const uint32_t t32 = (uint32_t)h.t;
+    const unsigned long long f = h.fp64;
+    cudaError_t e = cudaMemcpyAsync(ch->acc, b + sizeof(h) + 2 * n, n * sizeof(float),
+                                    cudaMemcpyHostToDevice, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ch->tdev, &t32, sizeof(t32), cudaMemcpyHostToDevice, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ch->fp64, &f, sizeof(f), cudaMemcpyHostToDevice, ch->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(ch->stream);
+    if (e != cudaSuccess) {
+        pcad_chain_destroy(ch);
+        return fail(PCAD_ECUDA, "import: %s", cudaGetErrorString(e));
+    }
+    ch->t = h.t;
+    ch->n_acc = h.n_acc;
+    *out = ch;
+    return PCAD_OK;
+}
+
+void pcad_chain_destroy(pcad_chain *ch)
+{
+    if (!ch)
+        return;
+    cudaStreamSynchronize(ch->stream);
+    if (ch->graph)
+        cudaGraphExecDestroy(ch->graph);
+    cudaFreeAsync(ch->block, ch->stream);
+    cudaStreamSynchronize(ch->stream);
+    delete ch;
+}
+
+const char *pcad_status_str(pcad_status s)
+{
+    switch (s) {
+    case PCAD_OK: return "ok";
+    case PCAD_EINVAL: return "invalid argument";
+    case PCAD_ENOMEM: return "out of memory";
+    case PCAD_ECUDA: return "CUDA error";
+    case PCAD_ETIMEOUT: return "device wait timed out";
+    case PCAD_ESTATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char *pcad_last_error(void) { return g_err.c_str(); }
+
+const char *pcad_version(void) { return "pcaden 0.1.0 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Internal declarations shared by the runtime (capi.cu) and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pcad_device.cuh"
+
+namespace pcad {
+
+// One sweep (PCA) or one colour phase (Gibbs) over one image.
+struct SweepArgs {
+    const uint8_t *xin;       // previous labels (PCA) / labels updated in place (Gibbs)
+    uint8_t *xout;            // next labels (PCA); unused by Gibbs
+    const uint8_t *g;         // observation
+    float *acc;               // posterior-mean accumulator (H x W, row stride W)
+    unsigned long long *fp64_draws;  // counter of FP64 re-evaluations
+    const uint32_t *sweep_base;  // device sweep counter of the chain
+    uint64_t seed;
+    int H, W, pitch;          // pitch: bytes between label rows (x and g)
+    uint32_t sweep_off;       // this update's sweep index = *sweep_base + sweep_off
+    uint32_t chain;
+    int burn_in;              // sweeps not accumulated
+    int last_phase;           // Gibbs: this phase completes the sweep
+    DevModel m;
+};
+
+__device__ __forceinline__ uint32_t sweep_index(const SweepArgs &a)
+{
+    return *a.sweep_base + a.sweep_off;
+}
+
+// Accumulate after the k-th completed sweep (k = index + 1) when k > burn_in.
+__device__ __forceinline__ bool accumulate_after(const SweepArgs &a, uint32_t t)
+{
+    return (long long)t + 1 > (long long)a.burn_in;
+}
+
+// *counter += n (one thread).
+cudaError_t launch_advance(uint32_t *counter, uint32_t n, cudaStream_t s);
+
+// Number of 8-label chunks rounded up to an instantiated size.
+int chunk_class(int L);
+
+// Launch one PCA sweep (xin -> xout) on `stream`.
+cudaError_t launch_pca_sweep(const SweepArgs &a, cudaStream_t stream);
+
+// Launch Gibbs colour phase q (0..ncolours-1) in place on a.xin.  When
+// a.accumulate is set, the phase must be the last of the sweep.
+cudaError_t launch_gibbs_phase(const SweepArgs &a, int q, cudaStream_t stream);
+
+// acc / n -> mean (H x W floats)
+cudaError_t launch_mean(const float *acc, float n, float *mean, long count, cudaStream_t s);
+
+// labels (pitched) -> float plane (label units)
+cudaError_t launch_labels_to_float(const uint8_t *x, int pitch, int H, int W, float *out,
+                                   cudaStream_t s);
+
+// Metrics: est (H x W floats, label units), clean (H x W bytes, contiguous).
+// out[0] = PSNR dB, out[1] = SSIM (device doubles).  scratch: >= 8 doubles.
+cudaError_t launch_metrics(const float *est, const uint8_t *clean, int H, int W, int L,
+                           double *scratch, double *out, cudaStream_t s);
+
+// Validate every label < L (returns count of bad labels into *bad, device int).
+cudaError_t launch_check_labels(const uint8_t *x, int pitch, int H, int W, int L, int *bad,
+                                cudaStream_t s);
+
+}  // namespace pcad
