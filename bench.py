@@ -1,0 +1,312 @@
+"""Benchmark: lazy-PCA denoising chain on one GB300 (plus Gibbs on the same GPU).
+
+Workload (one "step"): the greyscale 512x512 chain with L = 256 labels --
+smooth gradients plus 20 rectangles/disks, additive Gaussian noise sigma = 20
+(clipped, rounded), truncated-linear prior c_T = 0.05, T = 30 on the
+4-neighbourhood, inertia lambda = 2.0; 2000 lazy-PCA sweeps from the
+observation with burn-in 500 and the FP32 posterior-mean accumulator.
+Synthetic, seeded inputs (the paper's images are not public).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line.  `value` is site-updates/s with the inputs resident in
+HBM (CUDA events on the chain's stream, L2 flushed between steps); `e2e` is
+the same metric through the public C ABI with host buffers (create from
+pinned host memory, run, read the mean back).  `--impl reference` times the
+FP64 CPU oracle on the host cores on bounded samples of the same workload.
+Under torchrun each rank runs its own independent chain (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SWEEPS = 2000
+BURN_IN = 500
+WORKLOAD = ("greyscale 512x512, L=256 (uint8), Gaussian sigma=20, truncated-linear "
+            "c_T=0.05 T=30 4-nbhd, lambda=2.0, 2000 sweeps, burn-in 500, FP32 posterior mean")
+# SFU ex2 issue: 32 per SM per clock (4 SM sub-partitions x 8) x 152 SMs x 2070 MHz
+SFU_PEAK_T = 152 * 32 * 2.070e9 / 1e12
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-gibbs", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not getattr(self, "out", ""):
+            return None
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for row in csv.reader(io.StringIO(self.out)):
+            if len(row) < 9:
+                continue
+            try:
+                sm.append(float(row[1]))
+                smax.append(float(row[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, row[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _inputs():
+    from pcad_inputs import greyscale_512
+    return greyscale_512(seed=2)
+
+
+def cpu_baseline(seconds: float = 12.0):
+    """FP64 oracle PCA sweeps of the 512x512 L=256 image on all host cores."""
+    import oracle
+    clean, noisy, m = _inputs()
+    x = noisy.copy()
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        x, _ = oracle.pca_sweep(m, noisy, x, 2, 0, n)
+        n += 1
+        if time.perf_counter() - t0 > seconds or n >= 64:
+            break
+    dt = time.perf_counter() - t0
+    H, W = noisy.shape
+    return {"value": H * W * n / dt, "unit": "site-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{n} lazy-PCA sweeps of the 512x512 L=256 image "
+                                        f"({dt:.1f} s, OpenMP over rows)"}
+
+
+def run_reference(a):
+    world, rank, _ = _dist()
+    if rank != 0:
+        return
+    import oracle
+    clean, noisy, m = _inputs()
+    H, W = noisy.shape
+    x = noisy.copy()
+    for t in range(a.warmup):
+        x, _ = oracle.pca_sweep(m, noisy, x, 2, 0, t)
+    times = []
+    for k in range(a.steps):
+        t0 = time.perf_counter()
+        x, _ = oracle.pca_sweep(m, noisy, x, 2, 0, a.warmup + k)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    v = H * W * a.steps / T
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": "site-updates/s", "value": v,
+            "unit": "site-updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * T / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "step": "one lazy-PCA sweep of the full image "
+                                                    "(bounded sample of the 2000-sweep chain)"},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v,
+                             "sample": f"{a.steps} sweeps of the 512x512 L=256 image"},
+            "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+
+    import paper_2507_14869_gb300 as pc
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    clean, noisy, m = _inputs()
+    H, W = noisy.shape
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def timed(chain, steps, warm):
+        for _ in range(warm):
+            chain.reset().run(SWEEPS)
+        chain.sync()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                flush.fill_(k & 0xFF)              # L2 flush between timed steps
+                evs[k][0].record(stream)
+                chain.reset().run(SWEEPS)
+                evs[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        wall = time.perf_counter() - wall0
+        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
+        return ms, wall
+
+    pca = pc.Chain(noisy, m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream)
+    with ClockSampler(local) as clk:
+        ms, wall = timed(pca, a.steps, a.warmup)
+    T = sum(ms) / 1e3
+    T_max = T
+    if world > 1:
+        t = torch.tensor([T], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        T_max = float(t.item())
+    sites = H * W * SWEEPS
+    value = world * sites * a.steps / T_max
+    launch_ms = 1e3 * T / (a.steps * SWEEPS)
+    fp64 = pca.fp64_draws()
+    psnr, ssim = pca.metrics(clean, 0)
+    pca_sample_psnr, _ = pca.metrics(clean, 1)
+
+    gibbs = None
+    if not a.no_gibbs:
+        gch = pc.Chain(noisy, m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream,
+                       sampler=pc.SAMPLER_GIBBS_CB)
+        gsteps = max(2, a.steps // 2)
+        gms, _ = timed(gch, gsteps, 1)
+        gT = sum(gms) / 1e3
+        gp, gs = gch.metrics(clean, 0)
+        gibbs = {"value": sites * gsteps / gT, "unit": "site-updates/s",
+                 "ms_per_step": 1e3 * gT / gsteps, "steps": gsteps, "psnr_db": gp, "ssim": gs,
+                 "launches_per_step": 2 * SWEEPS + (SWEEPS + 31) // 32,
+                 "kernel": "gibbs_cb_kernel<32,4> (2 colour phases per sweep)"}
+        gch.close()
+
+    # end to end through the public API with host buffers (pinned)
+    g_host = torch.empty((H, W), dtype=torch.uint8, pin_memory=True)
+    g_host.numpy()[:] = noisy
+    mean_host = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(2, min(a.steps, 5))
+    torch.cuda.synchronize(dev)
+    e2e_t = []
+    for k in range(e2e_steps + 1):
+        t0 = time.perf_counter()
+        ch = pc.Chain(g_host.numpy(), m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream)
+        ch.run(SWEEPS)
+        pc.pcad_chain_read_mean(ch.h, H, W, out=mean_host.numpy())
+        ch.close()
+        if k > 0:                                     # first one warms the allocator
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_v = world * sites / statistics.mean(e2e_t)
+
+    if rank != 0:
+        return
+    per_launch_labels = H * W * m.L
+    achieved = per_launch_labels / (launch_ms * 1e-3) / 1e12
+    traffic = os.environ.get("PCAD_NCU_TRAFFIC_BYTES")
+    line = {
+        "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
+        "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * T_max / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sites": H * W, "sweeps_per_step": SWEEPS,
+                   "burn_in": BURN_IN, "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "independent chain per GPU" if world > 1 else "1 GPU"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
+                     "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
+                     "traffic": int(traffic) if traffic else None,
+                     "kernel": "pca_direct_kernel<32,4>",
+                     "work_per_unit": "one exponential (SFU) per label evaluation, L=256 per "
+                                      "site-update",
+                     "peak_source": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count x max "
+                                    "clock; 29.9/clk/SM measured)",
+                     "ms_per_launch": launch_ms},
+        "gpu_launches": a.steps * (SWEEPS + (SWEEPS + 31) // 32),
+        "e2e": {"value": e2e_v, "unit": "site-updates/s", "h2d_bytes_per_step": H * W,
+                "d2h_bytes_per_step": H * W * 4, "steps": e2e_steps,
+                "ms_per_step": 1e3 * statistics.mean(e2e_t),
+                "path": "pcad_chain_create(host) + pcad_chain_run + pcad_chain_read_mean(host)"},
+        "label_evals_per_s": value * m.L,
+        "fp64_redraw_fraction": fp64 / float(H * W * SWEEPS),   # counter restarts each step
+        "psnr_db": psnr, "ssim": ssim, "last_sample_psnr_db": pca_sample_psnr,
+        "wall_s_timed": wall,
+    }
+    if gibbs:
+        line["gibbs"] = gibbs
+    clocks = clk.summary()
+    line["clocks"] = clocks
+    if world == 1 and not a.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,10 @@ pcad_status pcad_chain_create_dev(const uint8_t *g_dev, int H, int W, int g_pitc
  * when k > burn_in (conditional-mean estimator, Section 2). */
 pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps);
 
+/* Restart the chain from its observation (state = g, accumulator and
+ * counters zero, sweep counter 0) without reallocating (asynchronous). */
+pcad_status pcad_chain_reset(pcad_chain *ch);
+
 /* Block until the chain's queued work is done. */
 pcad_status pcad_chain_sync(pcad_chain *ch);
 

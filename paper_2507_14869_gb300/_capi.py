@@ -89,6 +89,7 @@ def _declare(L):
                                   ctypes.POINTER(vp)],
         "pcad_chain_run": [vp, ctypes.c_int],
         "pcad_chain_sync": [vp],
+        "pcad_chain_reset": [vp],
         "pcad_chain_read_sample": [vp, u8p, ctypes.c_int],
         "pcad_chain_read_sample_dev": [vp, vp, ctypes.c_int],
         "pcad_chain_read_mean": [vp, fp],
@@ -164,6 +165,10 @@ def pcad_chain_sync(h):
     _check("pcad_chain_sync", lib().pcad_chain_sync(h))
 
 
+def pcad_chain_reset(h):
+    _check("pcad_chain_reset", lib().pcad_chain_reset(h))
+
+
 def pcad_chain_read_sample(h, H: int, W: int) -> np.ndarray:
     out = np.empty((H, W), dtype=np.uint8)
     _check("pcad_chain_read_sample",
@@ -176,8 +181,11 @@ def pcad_chain_read_sample_dev(h, dev_ptr: int, pitch: int):
            lib().pcad_chain_read_sample_dev(h, ctypes.c_void_p(int(dev_ptr)), int(pitch)))
 
 
-def pcad_chain_read_mean(h, H: int, W: int) -> np.ndarray:
-    out = np.empty((H, W), dtype=np.float32)
+def pcad_chain_read_mean(h, H: int, W: int, out=None) -> np.ndarray:
+    if out is None:
+        out = np.empty((H, W), dtype=np.float32)
+    if out.dtype != np.float32 or out.size != H * W or not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be a contiguous float32 array of H*W elements")
     _check("pcad_chain_read_mean",
            lib().pcad_chain_read_mean(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
     return out
@@ -288,6 +296,10 @@ class Chain:
 
     def sync(self):
         pcad_chain_sync(self.h)
+
+    def reset(self):
+        pcad_chain_reset(self.h)
+        return self
 
     def sample(self) -> np.ndarray:
         return pcad_chain_read_sample(self.h, self.H, self.W)

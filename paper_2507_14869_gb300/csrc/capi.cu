@@ -89,7 +89,6 @@ pcad_status validate_model(const pcad_model *m)
 
 // Host copy of the model tables and the FP32 error bound.
 struct ModelTables {
-    float ta32[kTable];
     double ta64[kTable];
     std::vector<double> pr64;
     DevModel dm;  // table pointers filled once uploaded
@@ -111,32 +110,45 @@ void build_tables(const pcad_model &m, ModelTables &t)
             v = d == 0 ? 1.0 : (std::abs(d) == 1 ? p / (1.0 - p) : 0.0);
         }
         t.ta64[d + 255] = v;
-        t.ta32[d + 255] = (float)v;
     }
     t.pr64.assign(pmax + 1, 0.0);
     for (int P = 0; P <= pmax; ++P)
         t.pr64[P] = std::exp(-(c * (double)P));
     const double lam = m.sampler == PCAD_SAMPLER_PCA ? (double)m.inertia : 0.0;
+    const double log2e = 1.4426950408889634074;
     DevModel &d = t.dm;
     d.L = m.L;
     d.nbhd = m.nbhd;
     d.T = T;
     d.pmax = pmax;
-    d.gam = (float)(-c * 1.4426950408889634074);
+    d.gam = (float)(-c * log2e);
+    if (m.noise == PCAD_NOISE_GAUSS) {
+        const double s = (double)m.sigma;
+        d.alpha = (float)(-log2e / (2.0 * s * s));
+    } else {
+        const double p = (double)m.flip_p;
+        d.alpha = (float)(-log2e * std::log((1.0 - p) / p));
+    }
     d.Tf = (float)T;
     d.em1 = (float)std::expm1(lam);
     d.el64 = std::exp(lam);
-    // Rigorous bound on |C_k/Z (FP32) - F_k (exact)|: per-weight relative
-    // error e_w (table rounding, FMA rounding, exponent argument rounding
-    // 2u|gam|P ln 2, exp2f within 2 ulp) and summation error
-    // (8 in-chunk + NC chunk-level + 4 combining additions) u, doubled for
-    // the ratio, plus the uniform's product rounding; 1.5x slack.
+    d.pad_ = 0;
+    // Rigorous bound on |C_k/Z (FP32) - F_k (exact)|.  Exponent v = alpha Q +
+    // gam P: |dv| <= u (2|gam P| + |alpha Q| + |v|) from the two rounded
+    // coefficients and the two roundings.  The CDF error from the weights is
+    // sum_s p_s theta_s, theta_s <= ln2 |dv_s| + e_ex2; with |gam P| <=
+    // |gam| pmax, |alpha Q| <= |v| + |gam| pmax and E_p|v| <= |v_max| + log2 L
+    // <= |gam| pmax + log2 L (entropy bound), the weight part is at most
+    // u ln2 (5 |gam| pmax + 2 log2 L) + e_ex2, doubled for the inertia
+    // correction.  Summation: 8 in-chunk additions, Kahan across chunks
+    // (2u), the pass-2 prefix (8), 3 combining roundings: 21u.  The ratio
+    // doubles both; 1.5x slack.  e_ex2: ex2.approx.ftz within 2 ulp.
     const double u = 5.9604644775390625e-08;
-    const double e_w = 2.0 * u + 2.384185791015625e-07 +
-                       2.0 * u * 0.6931471805599453 * std::fabs((double)d.gam) * pmax;
-    const double gsum = (double)(kChunk + chunk_class(m.L) + 4) * u;
-    d.eta = (float)(1.5 * (3.0 * e_w + 2.0 * gsum) + 8.0 * u);
-    d.ta32 = nullptr;
+    const double A = std::fabs((double)d.gam) * pmax;
+    const double e_w = u * 0.6931471805599453 * (5.0 * A + 2.0 * std::log2((double)m.L)) +
+                       4.0 * u;
+    const double gsum = 21.0 * u;
+    d.eta = (float)(1.5 * 2.0 * (2.0 * e_w + gsum) + 8.0 * u);
     d.ta64 = nullptr;
     d.pr64 = nullptr;
 }
@@ -162,7 +174,6 @@ struct pcad_chain {
     uint32_t *tdev = nullptr;
     unsigned long long *fp64 = nullptr;
     double *mscratch = nullptr;   // 8 scratch + 2 results
-    float *ta32 = nullptr;
     double *ta64 = nullptr, *pr64 = nullptr;
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
@@ -276,8 +287,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     const size_t plane = align_up((size_t)ch->pitch * H, 256);
     const size_t fbytes = align_up((size_t)H * W * sizeof(float), 256);
     const size_t cbytes = align_up((size_t)H * W, 256);
-    const size_t tbytes = align_up(kTable * sizeof(float), 256) +
-                          align_up(kTable * sizeof(double), 256) +
+    const size_t tbytes = align_up(kTable * sizeof(double), 256) +
                           align_up(tabs.pr64.size() * sizeof(double), 256);
     const size_t misc = 256;
     const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + misc;
@@ -295,7 +305,6 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->acc = (float *)p; p += fbytes;
     ch->fplane = (float *)p; p += fbytes;
     ch->clean = (uint8_t *)p; p += cbytes;
-    ch->ta32 = (float *)p; p += align_up(kTable * sizeof(float), 256);
     ch->ta64 = (double *)p; p += align_up(kTable * sizeof(double), 256);
     ch->pr64 = (double *)p; p += align_up(tabs.pr64.size() * sizeof(double), 256);
     ch->tdev = (uint32_t *)p;
@@ -315,9 +324,6 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
                               cudaMemcpyDeviceToDevice, ch->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ch->acc, 0, fbytes, ch->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ch->ta32, tabs.ta32, sizeof(tabs.ta32), cudaMemcpyHostToDevice,
-                            ch->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ch->ta64, tabs.ta64, sizeof(tabs.ta64), cudaMemcpyHostToDevice,
                             ch->stream);
@@ -340,7 +346,6 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     if (e != cudaSuccess)
         return cleanup(fail(PCAD_ECUDA, "chain set-up: %s", cudaGetErrorString(e)));
     ch->dm = tabs.dm;
-    ch->dm.ta32 = ch->ta32;
     ch->dm.ta64 = ch->ta64;
     ch->dm.pr64 = ch->pr64;
     *out = ch;
@@ -413,6 +418,21 @@ pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps)
     const uint64_t t1 = ch->t + (uint64_t)nsweeps;
     ch->n_acc += t1 > start ? t1 - start : 0;
     ch->t = t1;
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_reset(pcad_chain *ch)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    const size_t n = (size_t)ch->H * ch->W;
+    CUDA_TRY(cudaMemcpy2DAsync(ch->x[0], ch->pitch, ch->g, ch->pitch, ch->W, ch->H,
+                               cudaMemcpyDeviceToDevice, ch->stream));
+    CUDA_TRY(cudaMemsetAsync(ch->acc, 0, n * sizeof(float), ch->stream));
+    CUDA_TRY(cudaMemsetAsync(ch->tdev, 0, 16, ch->stream));
+    ch->cur = 0;
+    ch->t = 0;
+    ch->n_acc = 0;
     return PCAD_OK;
 }
 

@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace pcad {
@@ -44,12 +45,14 @@ struct DevModel {
     int nbhd;          // 4 or 8
     int T;             // truncation (1 for Potts)
     int pmax;          // nbhd * T: largest P(s)
-    float gam;         // -c * log2(e)
+    float gam;         // prior exponent coefficient, -c log2(e)
+    float alpha;       // data exponent coefficient: -log2(e)/(2 sigma^2) (Gaussian) or
+                       // -log2(e) ln((1-p)/p) (flip, with Q = (g-s)^2 in {0,1})
     float Tf;          // (float)T
     float em1;         // e^lambda - 1 (0: no inertia)
     float eta;         // FP32 error bound of the normalised CDF
-    const float *ta32;   // [511] data factor, FP32
-    const double *ta64;  // [511] data factor, FP64
+    int pad_;
+    const double *ta64;  // [511] data factor exp(-(U(g, g-d) - U(g,g))) at d + 255, FP64
     const double *pr64;  // [pmax + 1] exp(-c P), FP64
     double el64;         // e^lambda, FP64
 };
@@ -99,136 +102,170 @@ __device__ __forceinline__ uint32_t site_u24(uint64_t seed, uint32_t chain, uint
 
 // ------------------------------------------------------- FP32 chunk weights
 
-// Sum of the weights of labels [8c, 8c+8) (labels >= L masked when MASK).
-template <int NB, bool MASK>
-__device__ __forceinline__ float chunk_sum(const DevModel &m, const float *__restrict__ ta_s,
-                                           int g, const float (&xn)[NB], int c)
+__device__ __forceinline__ float ex2_ftz(float x)
 {
-    const float sb = (float)(c * kChunk);
-    float xr[NB];
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Weight 2^v of one label: v = alpha (g - s)^2 + gam P(s).  dg = g - s and
+// P are exact small integers; (g - s)^2 <= 65025 is exact in FP32.
+__device__ __forceinline__ float label_w(const DevModel &m, float P, float dg)
+{
+    const float q = __fmul_rn(dg, dg);
+    const float v = __fmaf_rn(m.alpha, q, __fmul_rn(m.gam, P));
+    return ex2_ftz(v);
+}
+
+// Prior sums P(s), s = sb + kk and sb + kk + 1, for two labels at once in
+// half precision (all operands are integers <= 2048, so exact): each
+// neighbour contributes min(|x_j - s|, T).
+template <int NB>
+__device__ __forceinline__ float2 prior_pair(const __half2 (&xr)[NB], __half2 k2, __half2 T2)
+{
+    __half2 P2 = __hmin2(__habs2(__hsub2(xr[0], k2)), T2);
+#pragma unroll
+    for (int j = 1; j < NB; ++j)
+        P2 = __hadd2(P2, __hmin2(__habs2(__hsub2(xr[j], k2)), T2));
+    return __half22float2(P2);
+}
+
+// Weights of labels [8c, 8c + 8); returns their sequential sum and, when
+// PREFIX, the inclusive running sums p[k].  Labels >= L weigh 0 when MASK.
+template <int NB, bool MASK, bool PREFIX>
+__device__ __forceinline__ float chunk_weights(const DevModel &m, const __half2 (&xh)[NB],
+                                               __half2 T2, float gf, int c,
+                                               float (&p)[kChunk])
+{
+    const float sbf = (float)(c * kChunk);
+    const __half2 sb2 = __float2half2_rn(sbf);
+    __half2 xr[NB];
 #pragma unroll
     for (int j = 0; j < NB; ++j)
-        xr[j] = xn[j] - sb;
-    const float *tap = ta_s + (g - c * kChunk + kTableOffset);
+        xr[j] = __hsub2(xh[j], sb2);
+    const float dgb = gf - sbf;
     float S = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-        float P = fminf(fabsf(xr[0] - (float)k), m.Tf);
-#pragma unroll
-        for (int j = 1; j < NB; ++j)
-            P += fminf(fabsf(xr[j] - (float)k), m.Tf);
-        const float e = exp2f(m.gam * P);
-        float a = tap[-k];
-        if (MASK && (c * kChunk + k >= m.L))
-            a = 0.0f;
-        S = __fmaf_rn(a, e, S);
+    for (int kk = 0; kk < kChunk; kk += 2) {
+        const float2 P = prior_pair<NB>(xr, __floats2half2_rn((float)kk, (float)(kk + 1)), T2);
+        float e0 = label_w(m, P.x, dgb - (float)kk);
+        float e1 = label_w(m, P.y, dgb - (float)(kk + 1));
+        if (MASK) {
+            if (c * kChunk + kk >= m.L) e0 = 0.0f;
+            if (c * kChunk + kk + 1 >= m.L) e1 = 0.0f;
+        }
+        S = __fadd_rn(S, e0);
+        if (PREFIX) p[kk] = S;
+        S = __fadd_rn(S, e1);
+        if (PREFIX) p[kk + 1] = S;
     }
     return S;
 }
 
-// Inclusive running sums p_k of the weights of chunk c.
+// Weight of a single label s (used for the inertia correction).
 template <int NB>
-__device__ __forceinline__ void chunk_prefix(const DevModel &m, const float *__restrict__ ta_s,
-                                             int g, const float (&xn)[NB], int c,
-                                             float (&p)[kChunk])
-{
-    const float sb = (float)(c * kChunk);
-    float xr[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-        xr[j] = xn[j] - sb;
-    const float *tap = ta_s + (g - c * kChunk + kTableOffset);
-    float S = 0.0f;
-#pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-        float P = fminf(fabsf(xr[0] - (float)k), m.Tf);
-#pragma unroll
-        for (int j = 1; j < NB; ++j)
-            P += fminf(fabsf(xr[j] - (float)k), m.Tf);
-        const float e = exp2f(m.gam * P);
-        float a = tap[-k];
-        if (c * kChunk + k >= m.L)
-            a = 0.0f;
-        S = __fmaf_rn(a, e, S);
-        p[k] = S;
-    }
-}
-
-template <int NB>
-__device__ __forceinline__ float label_weight(const DevModel &m, const float *__restrict__ ta_s,
-                                              int g, const float (&xn)[NB], int s)
+__device__ __forceinline__ float single_w(const DevModel &m, const float (&xn)[NB], float gf, int s)
 {
     const float sf = (float)s;
     float P = fminf(fabsf(xn[0] - sf), m.Tf);
 #pragma unroll
     for (int j = 1; j < NB; ++j)
-        P += fminf(fabsf(xn[j] - sf), m.Tf);
-    return ta_s[g - s + kTableOffset] * exp2f(m.gam * P);
+        P = __fadd_rn(P, fminf(fabsf(xn[j] - sf), m.Tf));
+    return label_w(m, P, gf - sf);
 }
+
+// Per-site inputs of a draw.
+template <int NB>
+struct SiteIn {
+    int g, xi;
+    int xni[NB];     // neighbour labels (missing: 1024)
+    uint32_t ub;     // 24-bit uniform numerator
+};
 
 // FP32 inverse-CDF draw.  Gcol points at this thread's column of a shared
 // scratch array (stride gstride floats) holding the chunk prefix sums.
 // Returns the label; `certain` is false when the uniform lies within the
 // error bound of a boundary of the chosen label's CDF interval.
 template <int NC, int NB>
-__device__ __forceinline__ int draw_fp32(const DevModel &m, const float *__restrict__ ta_s,
-                                         float *Gcol, int gstride, int g, int xi,
-                                         const float (&xn)[NB], float u, bool &certain)
+__device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gstride,
+                                         const SiteIn<NB> &in, bool &certain)
 {
-    // pass 1: chunk prefix sums of the inertia-free weights
-    float G = 0.0f;
+    float xn[NB];
+    __half2 xh[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        xn[j] = (float)in.xni[j];
+        xh[j] = __float2half2_rn(xn[j]);
+    }
+    const __half2 T2 = __float2half2_rn(m.Tf);
+    const float gf = (float)in.g;
+    const int xi = in.xi;
+    float pdummy[kChunk];
+    // pass 1: chunk prefix sums of the inertia-free weights (Kahan-compensated)
+    float G = 0.0f, comp = 0.0f;
     const int nfull = m.L / kChunk;  // chunks with no label >= L
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
-        const float S = (c < nfull) ? chunk_sum<NB, false>(m, ta_s, g, xn, c)
-                                    : chunk_sum<NB, true>(m, ta_s, g, xn, c);
-        G += S;
+        const float S = (c < nfull) ? chunk_weights<NB, false, false>(m, xh, T2, gf, c, pdummy)
+                                    : chunk_weights<NB, true, false>(m, xh, T2, gf, c, pdummy);
+        const float y = __fsub_rn(S, comp);
+        const float tt = __fadd_rn(G, y);
+        comp = __fsub_rn(__fsub_rn(tt, G), y);
+        G = tt;
         Gcol[c * gstride] = G;
     }
     float delta = 0.0f;
     if (m.em1 != 0.0f)
-        delta = label_weight<NB>(m, ta_s, g, xn, xi) * m.em1;
-    const float Z = G + delta;
-    const float t = u * Z;
+        delta = __fmul_rn(single_w<NB>(m, xn, gf, xi), m.em1);
+    const float Z = __fadd_rn(G, delta);
+    const float t = __fmul_rn((float)in.ub * (1.0f / 16777216.0f), Z);
     // smallest chunk whose (inertia-corrected) prefix exceeds t
     int lo = 0, hi = NC - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        const float gm = Gcol[mid * gstride] + ((xi <= mid * kChunk + kChunk - 1) ? delta : 0.0f);
+        const float gm = __fadd_rn(Gcol[mid * gstride],
+                                   (xi <= mid * kChunk + kChunk - 1) ? delta : 0.0f);
         if (t < gm)
             hi = mid;
         else
             lo = mid + 1;
     }
     const int cs = lo;
-    const float Gprev = cs > 0 ? Gcol[(cs - 1) * gstride] : 0.0f;
-    float p[kChunk];
-    chunk_prefix<NB>(m, ta_s, g, xn, cs, p);
     const int base = cs * kChunk;
     const int kmax = min(kChunk - 1, m.L - 1 - base);
+    if (kmax < 0) {  // only reachable through rounding: leave it to FP64
+        certain = false;
+        return m.L - 1;
+    }
+    const float Gprev = cs > 0 ? Gcol[(cs - 1) * gstride] : 0.0f;
+    float p[kChunk];
+    chunk_weights<NB, true, true>(m, xh, T2, gf, cs, p);
     int k = kmax;
     float hiC = 0.0f;
+    bool found = false;
 #pragma unroll
     for (int kk = kChunk - 1; kk >= 0; --kk) {
-        const float Ck = (Gprev + p[kk]) + ((base + kk >= xi) ? delta : 0.0f);
+        const float Ck = __fadd_rn(__fadd_rn(Gprev, p[kk]), (base + kk >= xi) ? delta : 0.0f);
         if (kk <= kmax && t < Ck) {
             k = kk;
             hiC = Ck;
+            found = true;
         }
     }
-    if (k == kmax && !(t < hiC))
-        hiC = (Gprev + p[kmax]) + ((base + kmax >= xi) ? delta : 0.0f);
+    if (!found)
+        hiC = __fadd_rn(__fadd_rn(Gprev, p[kmax]), (base + kmax >= xi) ? delta : 0.0f);
     float loC;
     if (k > 0)
-        loC = (Gprev + p[k - 1]) + ((base + k - 1 >= xi) ? delta : 0.0f);
+        loC = __fadd_rn(__fadd_rn(Gprev, p[k - 1]), (base + k - 1 >= xi) ? delta : 0.0f);
     else
-        loC = Gprev + ((base - 1 >= xi) ? delta : 0.0f);
-    const int s = base + k;
-    const float margin = m.eta * Z;
-    const bool ok_hi = (s == m.L - 1) || (hiC - t > margin);
-    const bool ok_lo = (s == 0) || (t - loC > margin);
-    certain = ok_hi && ok_lo;
-    return s;
+        loC = __fadd_rn(Gprev, (base - 1 >= xi) ? delta : 0.0f);
+    const int s = max(0, base + k);
+    const float margin = __fmul_rn(m.eta, Z);
+    const bool ok_hi = (s == m.L - 1) || (__fsub_rn(hiC, t) > margin);
+    const bool ok_lo = (s == 0) || (__fsub_rn(t, loC) > margin);
+    certain = found && ok_hi && ok_lo;
+    return min(s, m.L - 1);
 }
 
 // ------------------------------------------------------------ FP64 re-draw
@@ -249,22 +286,71 @@ __device__ __forceinline__ double weight64(const DevModel &m, int g, int xi, con
     return w;
 }
 
-// FP64 evaluation of the same draw: weights in FP64, sums in label order.
+// Warp-cooperative FP64 evaluation of the draws of the lanes with `need`
+// set: for each such lane in turn, the 32 lanes compute 8 labels' FP64
+// weights each, an FP64 warp scan gives the CDF, and the lane holding u*Z
+// finds the label.  All 32 lanes of the warp must call this together.
 template <int NB>
-__device__ __noinline__ int draw_fp64(const DevModel &m, int g, int xi, const int (&xni)[NB],
-                                      double u)
+__device__ __forceinline__ int warp_redraw_fp64(const DevModel &m, bool need, const SiteIn<NB> &in,
+                                                int s, unsigned long long *counter)
 {
-    double Z = 0.0;
-    for (int s = 0; s < m.L; ++s)
-        Z = __dadd_rn(Z, weight64<NB>(m, g, xi, xni, s));
-    const double t = __dmul_rn(u, Z);
-    double C = 0.0;
-    for (int s = 0; s < m.L; ++s) {
-        C = __dadd_rn(C, weight64<NB>(m, g, xi, xni, s));
-        if (t < C)
-            return s;
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    unsigned todo = __ballot_sync(kFull, need);
+    if (todo == 0u)
+        return s;
+    const int lane = (int)(threadIdx.x & 31u);
+    if (lane == 0)
+        atomicAdd(counter, (unsigned long long)__popc(todo));
+    while (todo) {
+        const int leader = __ffs((int)todo) - 1;
+        todo &= todo - 1u;
+        const int lg = __shfl_sync(kFull, in.g, leader);
+        const int lxi = __shfl_sync(kFull, in.xi, leader);
+        int lx[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            lx[j] = __shfl_sync(kFull, in.xni[j], leader);
+        const uint32_t lub = __shfl_sync(kFull, in.ub, leader);
+        double w[kChunk];
+        double part = 0.0;
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k) {
+            const int sl = lane * kChunk + k;
+            w[k] = sl < m.L ? weight64<NB>(m, lg, lxi, lx, sl) : 0.0;
+            part = __dadd_rn(part, w[k]);
+        }
+        double incl = part;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double v = __shfl_up_sync(kFull, incl, o);
+            if (lane >= o)
+                incl = __dadd_rn(incl, v);
+        }
+        const double Z = __shfl_sync(kFull, incl, 31);
+        const double t = __dmul_rn((double)lub * (1.0 / 16777216.0), Z);
+        double excl = __shfl_up_sync(kFull, incl, 1);
+        if (lane == 0)
+            excl = 0.0;
+        const unsigned hit = __ballot_sync(kFull, t < incl);
+        const int hl = hit ? __ffs((int)hit) - 1 : 31;
+        int res = 0;
+        if (lane == hl) {
+            double C = excl;
+            res = min(lane * kChunk + kChunk - 1, m.L - 1);
+#pragma unroll
+            for (int k = 0; k < kChunk; ++k) {
+                C = __dadd_rn(C, w[k]);
+                if (t < C && lane * kChunk + k < m.L) {
+                    res = lane * kChunk + k;
+                    break;
+                }
+            }
+        }
+        res = __shfl_sync(kFull, res, hl);
+        if (lane == leader)
+            s = res;
     }
-    return m.L - 1;
+    return s;
 }
 
 }  // namespace pcad

@@ -1,10 +1,10 @@
 // Sweep kernels: lazy PCA (Section 5.2) and checkerboard Gibbs (Section 5.1).
 //
-// One thread per site.  The site's labels, its neighbours' labels and its
+// One thread per site.  The site's label, its neighbours' labels and its
 // observation are read straight from global memory (each byte is reused by
 // up to 9 threads through L1); the per-label work (energy, exponential, CDF)
-// dominates for L >= 16.  The data-factor table lives in shared memory, as
-// do the per-thread chunk prefix sums of the two-pass CDF.
+// dominates for L >= 16.  The per-thread chunk prefix sums of the two-pass
+// CDF live in shared memory.
 #include "pcad_internal.h"
 
 namespace pcad {
@@ -14,13 +14,11 @@ namespace {
 constexpr int kBX = 32;
 constexpr int kBY = 4;
 constexpr int kThreads = kBX * kBY;
-constexpr int kTable = 511;
 
 // Neighbour order: up, down, left, right, then the four diagonals.
 template <int NB>
-__device__ __forceinline__ void load_neighbours(const uint8_t *__restrict__ x, int pitch, int H,
-                                                int W, int r, int c, float (&xn)[NB],
-                                                int (&xni)[NB])
+__device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__restrict__ x, int r,
+                                          int c, uint32_t tag, uint32_t t, SiteIn<NB> &in)
 {
     constexpr int dr[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
     constexpr int dc[8] = {0, 0, -1, 1, -1, 1, -1, 1};
@@ -28,57 +26,46 @@ __device__ __forceinline__ void load_neighbours(const uint8_t *__restrict__ x, i
     for (int j = 0; j < NB; ++j) {
         const int rr = r + dr[j];
         const int cc = c + dc[j];
-        const bool in = rr >= 0 && rr < H && cc >= 0 && cc < W;
-        const int v = in ? (int)x[(size_t)rr * pitch + cc] : kMissingLabelI;
-        xni[j] = v;
-        xn[j] = (float)v;
+        const bool inside = rr >= 0 && rr < a.H && cc >= 0 && cc < a.W;
+        in.xni[j] = inside ? (int)x[(size_t)rr * a.pitch + cc] : kMissingLabelI;
     }
-}
-
-__device__ __forceinline__ void load_table(float *ta_s, const float *ta32, int tid)
-{
-    for (int i = tid; i < kTable; i += kThreads)
-        ta_s[i] = ta32[i];
-}
-
-template <int NC, int NB>
-__device__ __forceinline__ int update_site(const SweepArgs &a, const uint8_t *x, const float *ta_s,
-                                           float *Gcol, int r, int c, uint32_t tag, uint32_t t)
-{
-    float xn[NB];
-    int xni[NB];
-    load_neighbours<NB>(x, a.pitch, a.H, a.W, r, c, xn, xni);
     const size_t idx = (size_t)r * a.pitch + c;
-    const int xi = x[idx];
-    const int g = a.g[idx];
-    const uint32_t ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
-    const float u = (float)ub * (1.0f / 16777216.0f);
-    bool certain;
-    int s = draw_fp32<NC, NB>(a.m, ta_s, Gcol, kThreads, g, xi, xn, u, certain);
-    if (!certain) {
-        s = draw_fp64<NB>(a.m, g, xi, xni, (double)ub * (1.0 / 16777216.0));
-        atomicAdd(a.fp64_draws, 1ull);
-    }
-    return s;
+    in.xi = x[idx];
+    in.g = a.g[idx];
+    in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
+}
+
+// Draw the new label of every valid site of the warp; uncertain FP32 draws
+// are re-evaluated in FP64 by the whole warp.  Every lane must call this.
+template <int NC, int NB>
+__device__ __forceinline__ int draw_site(const SweepArgs &a, bool valid, const SiteIn<NB> &in,
+                                         float *Gcol)
+{
+    int s = 0;
+    bool certain = true;
+    if (valid)
+        s = draw_fp32<NC, NB>(a.m, Gcol, kThreads, in, certain);
+    return warp_redraw_fp64<NB>(a.m, valid && !certain, in, s, a.fp64_draws);
 }
 
 template <int NC, int NB>
 __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 {
-    __shared__ float ta_s[kTable];
     __shared__ float G_s[NC * kThreads];
     const int tid = threadIdx.y * kBX + threadIdx.x;
-    load_table(ta_s, a.m.ta32, tid);
-    __syncthreads();
     const int c = blockIdx.x * kBX + threadIdx.x;
     const int r = blockIdx.y * kBY + threadIdx.y;
-    if (r >= a.H || c >= a.W)
-        return;
+    const bool valid = r < a.H && c < a.W;
     const uint32_t t = sweep_index(a);
-    const int s = update_site<NC, NB>(a, a.xin, ta_s, G_s + tid, r, c, kTagPCA, t);
-    a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-    if (accumulate_after(a, t))
-        a.acc[(size_t)r * a.W + c] += (float)s;
+    SiteIn<NB> in{};
+    if (valid)
+        load_site<NB>(a, a.xin, r, c, kTagPCA, t, in);
+    const int s = draw_site<NC, NB>(a, valid, in, G_s + tid);
+    if (valid) {
+        a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+        if (accumulate_after(a, t))
+            a.acc[(size_t)r * a.W + c] += (float)s;
+    }
 }
 
 // Gibbs colour phase q.  A thread owns one "cell": a pair of columns
@@ -90,11 +77,8 @@ __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 template <int NC, int NB>
 __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, int q)
 {
-    __shared__ float ta_s[kTable];
     __shared__ float G_s[NC * kThreads];
     const int tid = threadIdx.y * kBX + threadIdx.x;
-    load_table(ta_s, a.m.ta32, tid);
-    __syncthreads();
     const int cx = blockIdx.x * kBX + threadIdx.x;
     const int cy = blockIdx.y * kBY + threadIdx.y;
     uint8_t *x = const_cast<uint8_t *>(a.xin);
@@ -110,14 +94,16 @@ __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, i
         r = r0 + (q >> 1);
         c = c0 + (q & 1);
     }
-    if (r0 >= a.H || c0 >= a.W)
-        return;
+    const bool cell = r0 < a.H && c0 < a.W;
+    const bool valid = cell && r < a.H && c < a.W;
     const uint32_t t = sweep_index(a);
-    if (r < a.H && c < a.W) {
-        const int s = update_site<NC, NB>(a, x, ta_s, G_s + tid, r, c, kTagGibbs, t);
+    SiteIn<NB> in{};
+    if (valid)
+        load_site<NB>(a, x, r, c, kTagGibbs, t, in);
+    const int s = draw_site<NC, NB>(a, valid, in, G_s + tid);
+    if (valid)
         x[(size_t)r * a.pitch + c] = (uint8_t)s;
-    }
-    if (a.last_phase && accumulate_after(a, t)) {
+    if (cell && a.last_phase && accumulate_after(a, t)) {
         const int nr = NB == 4 ? 1 : 2;
 #pragma unroll
         for (int dr = 0; dr < nr; ++dr)
