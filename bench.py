@@ -48,6 +48,10 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-gibbs", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--profile-case", nargs=3, type=int, metavar=("SIDE", "L", "SWEEPS"),
+                   help="run one SIDE x SIDE chain with L labels for SWEEPS sweeps and exit "
+                        "(the small case ncu captures; prints no JSON line)")
+    p.add_argument("--sampler", type=int, default=0, help="profile case: 0 PCA, 1 Gibbs")
     return p.parse_args()
 
 
@@ -300,8 +304,28 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+def profile_case(side: int, L: int, sweeps: int, sampler: int):
+    """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
+    L > 16, else 1), truncated-linear prior (c_T 0.05, T 30 for L > 16; 0.85,
+    2 otherwise), lambda 2.0."""
+    import paper_2507_14869_gb300 as pc
+    from pcad_inputs import Model, gaussian_noise, greyscale_scene
+    sig = 20.0 if L > 16 else 1.0
+    clean = greyscale_scene(3, side, side, L)
+    noisy = gaussian_noise(4, clean, sig, L)
+    m = Model(L=L, pair=1, pair_coef=0.05 if L > 16 else 0.85, pair_T=30 if L > 16 else 2,
+              sigma=sig, inertia=2.0, sampler=sampler)
+    with pc.Chain(noisy, m, seed=1, chain_id=0, burn_in=0) as ch:
+        ch.run(sweeps)
+        ch.sync()
+        print(f"profile case {side}x{side} L={L} sweeps={sweeps} fp64 re-draws={ch.fp64_draws()}")
+
+
 def main():
     a = _args()
+    if a.profile_case:
+        profile_case(*a.profile_case, a.sampler)
+        return
     if a.impl == "reference":
         run_reference(a)
     else:
