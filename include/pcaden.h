@@ -173,6 +173,28 @@ pcad_status pcad_chain_import(const void *host_blob, size_t bytes, void *cuda_st
 /* Release the chain's device memory (synchronises its stream).  NULL is a no-op. */
 void pcad_chain_destroy(pcad_chain *ch);
 
+/* Allocation-free lazy-PCA run (no counterpart in the paper: a library
+ * convenience).  For callers that must not allocate device memory: the GPU
+ * memory is already owned by another pool, or the calling loop cannot afford
+ * cudaMalloc / cudaFree, which may synchronise the whole device.
+ * Runs nsweeps PCA sweeps from the device observation g_dev (H x W labels,
+ * row pitch `pitch` bytes) with the chain semantics of pcad_chain_create +
+ * pcad_chain_run, and writes the final sample to sample_dev (same pitch) and
+ * the posterior mean (label units, zeros when nsweeps <= burn_in) to mean_dev
+ * (H x W contiguous floats; also used as the accumulator).  Asynchronous on
+ * cuda_stream.  The second label plane, the model tables and the counters
+ * live in one 8 MiB array in the library's own device memory, held by every
+ * GPU that loads the library until the process exits: pitch * H may not
+ * exceed 8,355,840 bytes (PCAD_EINVAL otherwise), and m->sampler must be
+ * PCAD_SAMPLER_PCA.  All calls share that array, so calls whose GPU work
+ * overlaps (unordered streams) race.  The first call on a device looks up
+ * the array's address (make it before any stream capture).  No allocation
+ * of any kind is made. */
+pcad_status pcad_pca_run_noalloc(const uint8_t *g_dev, int H, int W, int pitch,
+                                 const pcad_model *m, uint64_t seed, uint32_t chain_id,
+                                 int nsweeps, int burn_in, uint8_t *sample_dev,
+                                 float *mean_dev, void *cuda_stream);
+
 /* Static description of a status code. */
 const char *pcad_status_str(pcad_status s);
 

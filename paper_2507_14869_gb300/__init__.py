@@ -12,5 +12,5 @@ from ._capi import (  # noqa: F401
     pcad_chain_import, pcad_chain_metrics, pcad_chain_read_mean, pcad_chain_read_sample,
     pcad_chain_read_sample_dev, pcad_chain_reset, pcad_chain_run, pcad_chain_stats, pcad_chain_sweeps,
     pcad_chain_sync, pcad_chain_write_sample, pcad_last_error, pcad_metrics, pcad_status_str,
-    pcad_version,
+    pcad_pca_run_noalloc, pcad_version,
 )

@@ -100,6 +100,9 @@ def _declare(L):
         "pcad_metrics": [fp, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp],
         "pcad_chain_export": [vp, vp, ctypes.POINTER(ctypes.c_size_t)],
         "pcad_chain_import": [vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "pcad_pca_run_noalloc": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, mp,
+                                 ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
+                                 vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -248,6 +251,20 @@ def pcad_chain_import(blob: bytes, stream=None):
     _check("pcad_chain_import",
            lib().pcad_chain_import(buf, len(blob), _stream(stream), ctypes.byref(h)))
     return h
+
+
+def pcad_pca_run_noalloc(g_dev_ptr: int, H: int, W: int, pitch: int, model, seed: int,
+                         chain_id: int, nsweeps: int, burn_in: int, sample_dev_ptr: int,
+                         mean_dev_ptr: int, stream=None):
+    """Lazy-PCA run that allocates no device memory (device pointers in and
+    out, e.g. from torch tensors); see include/pcaden.h."""
+    m = as_model(model)
+    _check("pcad_pca_run_noalloc",
+           lib().pcad_pca_run_noalloc(ctypes.c_void_p(int(g_dev_ptr)), int(H), int(W),
+                                      int(pitch), ctypes.byref(m), int(seed), int(chain_id),
+                                      int(nsweeps), int(burn_in),
+                                      ctypes.c_void_p(int(sample_dev_ptr)),
+                                      ctypes.c_void_p(int(mean_dev_ptr)), _stream(stream)))
 
 
 def pcad_chain_destroy(h):

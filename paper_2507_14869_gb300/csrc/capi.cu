@@ -718,3 +718,21 @@ const char *pcad_last_error(void) { return g_err.c_str(); }
 const char *pcad_version(void) { return "pcaden 0.1.0 (sm_103a)"; }
 
 }  // extern "C"
+
+// Helpers shared with other translation units of the library.
+namespace pcad {
+
+pcad_status check_model(const pcad_model *m) { return validate_model(m); }
+
+void model_tables(const pcad_model &m, double *ta64, std::vector<double> &pr64, DevModel &dm)
+{
+    ModelTables t;
+    build_tables(m, t);
+    memcpy(ta64, t.ta64, sizeof(t.ta64));
+    pr64 = t.pr64;
+    dm = t.dm;
+}
+
+pcad_status set_error(pcad_status st, const char *msg) { return fail(st, "%s", msg); }
+
+}  // namespace pcad

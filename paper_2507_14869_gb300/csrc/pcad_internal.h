@@ -3,8 +3,11 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <vector>
+
 #include <cuda_runtime.h>
 
+#include "../../include/pcaden.h"
 #include "pcad_device.cuh"
 
 namespace pcad {
@@ -65,5 +68,10 @@ cudaError_t launch_metrics(const float *est, const uint8_t *clean, int H, int W,
 // Validate every label < L (returns count of bad labels into *bad, device int).
 cudaError_t launch_check_labels(const uint8_t *x, int pitch, int H, int W, int L, int *bad,
                                 cudaStream_t s);
+
+// Model validation, host tables and error reporting shared by the entry points.
+pcad_status check_model(const pcad_model *m);
+void model_tables(const pcad_model &m, double *ta64, std::vector<double> &pr64, DevModel &dm);
+pcad_status set_error(pcad_status st, const char *msg);
 
 }  // namespace pcad
