@@ -163,6 +163,57 @@ __device__ __forceinline__ float chunk_weights(const DevModel &m, const __half2 
     return S;
 }
 
+// Chunks whose labels see a linear prior.  P(s+1) - P(s) changes only at
+// s = x_j - T, x_j, x_j + T (the kinks of min(|s - x_j|, T)); a chunk
+// [8c, 8c+7] is linear unless such a kink lies in [8c+1, 8c+6].  Returns a
+// bit per chunk that holds a kink ("dirty").  Neighbours outside the image
+// (label 1024) contribute a constant and no kink.
+template <int NB>
+__device__ __forceinline__ uint32_t dirty_chunks(const int (&xni)[NB], int T)
+{
+    uint32_t mask = 0u;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        if (xni[j] >= kMissingLabelI)
+            continue;
+#pragma unroll
+        for (int o = -1; o <= 1; ++o) {
+            const int e = xni[j] + o * T;
+            const int r = e & 7;
+            if (e > 0 && e < 256 && r != 0 && r != 7)
+                mask |= 1u << (e >> 3);
+        }
+    }
+    return mask;
+}
+
+// Chunk sum when P is linear on the chunk: P(8c + k) = P0 + k (P1 - P0),
+// exact; every weight is then bit-identical to chunk_weights's.
+template <int NB, bool MASK>
+__device__ __forceinline__ float chunk_weights_linear(const DevModel &m, const __half2 (&xh)[NB],
+                                                      __half2 T2, float gf, int c)
+{
+    const float sbf = (float)(c * kChunk);
+    const __half2 sb2 = __float2half2_rn(sbf);
+    __half2 xr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        xr[j] = __hsub2(xh[j], sb2);
+    const float2 P01 = prior_pair<NB>(xr, __floats2half2_rn(0.0f, 1.0f), T2);
+    const float slope = __fsub_rn(P01.y, P01.x);
+    const float dgb = gf - sbf;
+    float S = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+        const float P = k == 0 ? P01.x : (k == 1 ? P01.y : __fmaf_rn(slope, (float)k, P01.x));
+        float e = label_w(m, P, dgb - (float)k);
+        if (MASK && c * kChunk + k >= m.L)
+            e = 0.0f;
+        S = __fadd_rn(S, e);
+    }
+    return S;
+}
+
 // Weight of a single label s (used for the inertia correction).
 template <int NB>
 __device__ __forceinline__ float single_w(const DevModel &m, const float (&xn)[NB], float gf, int s)
@@ -189,7 +240,7 @@ struct SiteIn {
 // error bound of a boundary of the chosen label's CDF interval.
 template <int NC, int NB>
 __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gstride,
-                                         const SiteIn<NB> &in, bool &certain)
+                                         const SiteIn<NB> &in, uint32_t dirty, bool &certain)
 {
     float xn[NB];
     __half2 xh[NB];
@@ -207,8 +258,13 @@ __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gst
     const int nfull = m.L / kChunk;  // chunks with no label >= L
 #pragma unroll 1
     for (int c = 0; c < NC; ++c) {
-        const float S = (c < nfull) ? chunk_weights<NB, false, false>(m, xh, T2, gf, c, pdummy)
-                                    : chunk_weights<NB, true, false>(m, xh, T2, gf, c, pdummy);
+        float S;
+        if ((dirty >> c) & 1u)   // warp-uniform branch
+            S = (c < nfull) ? chunk_weights<NB, false, false>(m, xh, T2, gf, c, pdummy)
+                            : chunk_weights<NB, true, false>(m, xh, T2, gf, c, pdummy);
+        else
+            S = (c < nfull) ? chunk_weights_linear<NB, false>(m, xh, T2, gf, c)
+                            : chunk_weights_linear<NB, true>(m, xh, T2, gf, c);
         const float y = __fsub_rn(S, comp);
         const float tt = __fadd_rn(G, y);
         comp = __fsub_rn(__fsub_rn(tt, G), y);

@@ -43,8 +43,13 @@ __device__ __forceinline__ int draw_site(const SweepArgs &a, bool valid, const S
 {
     int s = 0;
     bool certain = true;
+    // chunks where any lane's prior has a kink take the general path; with
+    // few chunks (L <= 32) the mask costs more than the linear path saves
+    uint32_t dirty = 0xFFFFFFFFu;
+    if (NC >= 8)
+        dirty = __reduce_or_sync(0xFFFFFFFFu, valid ? dirty_chunks<NB>(in.xni, a.m.T) : 0u);
     if (valid)
-        s = draw_fp32<NC, NB>(a.m, Gcol, kThreads, in, certain);
+        s = draw_fp32<NC, NB>(a.m, Gcol, kThreads, in, dirty, certain);
     return warp_redraw_fp64<NB>(a.m, valid && !certain, in, s, a.fp64_draws);
 }
 
