@@ -173,6 +173,72 @@ pcad_status pcad_chain_import(const void *host_blob, size_t bytes, void *cuda_st
 /* Release the chain's device memory (synchronises its stream).  NULL is a no-op. */
 void pcad_chain_destroy(pcad_chain *ch);
 
+/* ------------------------------------------------------------- batches
+ * Many independent lazy-PCA chains (the paper's repeated runs, e.g. 10 runs
+ * x 14 inertia values in Section 6, are such a batch) advanced together: one
+ * persistent launch per sweep covers every chain, whatever its size, label
+ * count or model.  A chain's draws depend only on its own (seed, chain id,
+ * sweep, row, col), so each chain's results are bit-identical to running it
+ * alone with pcad_chain_create + pcad_chain_run. */
+typedef struct {
+    const uint8_t *g_host;   /* observation (H rows of g_pitch bytes); copied at creation */
+    int H, W, g_pitch;
+    pcad_model model;        /* sampler must be PCAD_SAMPLER_PCA */
+    uint64_t seed;
+    uint32_t chain_id;
+    int burn_in;
+} pcad_job;
+
+typedef struct pcad_batch pcad_batch;
+
+/* Create a batch of n chains (one per job) on cuda_stream.  autotune != 0
+ * times the tile height (4/8/16 rows of 32 sites per work item) and the
+ * work order (costliest first or image order) on this batch and keeps the
+ * fastest, cached per batch signature for the process. */
+pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *cuda_stream,
+                              pcad_batch **out);
+/* Advance every chain by nsweeps sweeps (asynchronous). */
+pcad_status pcad_batch_run(pcad_batch *b, int nsweeps);
+/* Restart every chain from its observation (asynchronous). */
+pcad_status pcad_batch_reset(pcad_batch *b);
+pcad_status pcad_batch_sync(pcad_batch *b);
+/* Current sample / posterior mean of chain i (host memory, as for a chain). */
+pcad_status pcad_batch_read_sample(pcad_batch *b, int i, uint8_t *host_out, int out_pitch);
+pcad_status pcad_batch_read_mean(pcad_batch *b, int i, float *host_out);
+/* Sweeps done, chosen tiling, grid size, autotuner's best slice time (ms per
+ * 16 sweeps) and the FP64 re-draw count summed over chains. */
+pcad_status pcad_batch_info(pcad_batch *b, uint64_t *t, int *tile_rows, int *lpt_order,
+                            int *grid, float *tune_ms, uint64_t *fp64_draws);
+void pcad_batch_destroy(pcad_batch *b);
+
+/* -------------------------------------------------------------- server
+ * Continuous batching of denoising requests.  Submitted requests wait in a
+ * first-come first-served queue and are admitted when a slot is free and
+ * their device memory fits the HBM budget; every pcad_server_step admits what
+ * it can, advances every admitted request by one slice of sweeps in shared
+ * launches, and retires the requests whose sweep budget is spent (their
+ * sample and posterior mean are copied to host memory held by the server
+ * until polled).  State and sweep counters stay on the device between
+ * slices; a request's results do not depend on what else was running. */
+typedef struct pcad_server pcad_server;
+
+pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cuda_stream,
+                               pcad_server **out);
+/* Queue a request for nsweeps sweeps (job->g_host is copied).  *id is its handle. */
+pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id);
+/* Admit, run one slice of slice_sweeps (1..16) sweeps, retire finished
+ * requests; blocks until the slice is done. */
+pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, int *n_pending,
+                             int *n_finished);
+/* *state: 0 queued, 1 running, 2 done.  When done and an output pointer is
+ * given, copies the sample (H x W bytes) and mean (H x W floats) and
+ * forgets the request. */
+pcad_status pcad_server_poll(pcad_server *sv, uint64_t id, int *state, uint8_t *sample_out,
+                             float *mean_out);
+pcad_status pcad_server_info(pcad_server *sv, size_t *hbm_used, uint64_t *slices,
+                             uint64_t *fp64_draws);
+void pcad_server_destroy(pcad_server *sv);
+
 /* Allocation-free lazy-PCA run (no counterpart in the paper: a library
  * convenience).  For callers that must not allocate device memory: the GPU
  * memory is already owned by another pool, or the calling loop cannot afford

@@ -41,6 +41,13 @@ class PcadModel(ctypes.Structure):
                 ("sampler", ctypes.c_int)]
 
 
+class PcadJob(ctypes.Structure):
+    _fields_ = [("g_host", ctypes.POINTER(ctypes.c_uint8)), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("g_pitch", ctypes.c_int), ("model", PcadModel),
+                ("seed", ctypes.c_uint64), ("chain_id", ctypes.c_uint32),
+                ("burn_in", ctypes.c_int)]
+
+
 def as_model(m, sampler=None) -> PcadModel:
     """PcadModel from a PcadModel, a dict or any object with the same fields."""
     if isinstance(m, PcadModel):
@@ -100,6 +107,21 @@ def _declare(L):
         "pcad_metrics": [fp, u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp],
         "pcad_chain_export": [vp, vp, ctypes.POINTER(ctypes.c_size_t)],
         "pcad_chain_import": [vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "pcad_batch_create": [ctypes.POINTER(PcadJob), ctypes.c_int, ctypes.c_int, vp,
+                              ctypes.POINTER(vp)],
+        "pcad_batch_run": [vp, ctypes.c_int],
+        "pcad_batch_reset": [vp],
+        "pcad_batch_sync": [vp],
+        "pcad_batch_read_sample": [vp, ctypes.c_int, u8p, ctypes.c_int],
+        "pcad_batch_read_mean": [vp, ctypes.c_int, fp],
+        "pcad_batch_info": [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), u64p],
+        "pcad_server_create": [ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
+        "pcad_server_submit": [vp, ctypes.POINTER(PcadJob), ctypes.c_int, u64p],
+        "pcad_server_step": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
+        "pcad_server_poll": [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), u8p, fp],
+        "pcad_server_info": [vp, ctypes.POINTER(ctypes.c_size_t), u64p, u64p],
         "pcad_pca_run_noalloc": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, mp,
                                  ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_int,
                                  vp, vp, vp],
@@ -110,6 +132,10 @@ def _declare(L):
         f.restype = ctypes.c_int
     L.pcad_chain_destroy.argtypes = [vp]
     L.pcad_chain_destroy.restype = None
+    L.pcad_batch_destroy.argtypes = [vp]
+    L.pcad_batch_destroy.restype = None
+    L.pcad_server_destroy.argtypes = [vp]
+    L.pcad_server_destroy.restype = None
     L.pcad_status_str.argtypes = [ctypes.c_int]
     L.pcad_status_str.restype = ctypes.c_char_p
     L.pcad_last_error.argtypes = []
@@ -355,3 +381,125 @@ class Chain:
 
     def __exit__(self, *exc):
         self.close()
+
+
+# ------------------------------------------------------------ batch / server
+
+def _job(g, model, seed, chain_id, burn_in):
+    g = _u8(g)
+    H, W = g.shape
+    j = PcadJob(g_host=g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), H=H, W=W, g_pitch=W,
+                model=as_model(model), seed=int(seed), chain_id=int(chain_id),
+                burn_in=int(burn_in))
+    return j, g
+
+
+def pcad_batch_create(jobs, autotune: bool = True, stream=None):
+    """jobs: sequence of (g, model, seed, chain_id, burn_in)."""
+    keep, arr = [], (PcadJob * len(jobs))()
+    for k, (g, m, seed, chain, burn) in enumerate(jobs):
+        arr[k], gg = _job(g, m, seed, chain, burn)
+        keep.append(gg)
+    h = ctypes.c_void_p()
+    _check("pcad_batch_create",
+           lib().pcad_batch_create(arr, len(jobs), int(bool(autotune)), _stream(stream),
+                                   ctypes.byref(h)))
+    return h
+
+
+def pcad_batch_run(h, nsweeps: int):
+    _check("pcad_batch_run", lib().pcad_batch_run(h, int(nsweeps)))
+
+
+def pcad_batch_reset(h):
+    _check("pcad_batch_reset", lib().pcad_batch_reset(h))
+
+
+def pcad_batch_sync(h):
+    _check("pcad_batch_sync", lib().pcad_batch_sync(h))
+
+
+def pcad_batch_read_sample(h, i: int, H: int, W: int) -> np.ndarray:
+    out = np.empty((H, W), dtype=np.uint8)
+    _check("pcad_batch_read_sample",
+           lib().pcad_batch_read_sample(h, int(i),
+                                        out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), W))
+    return out
+
+
+def pcad_batch_read_mean(h, i: int, H: int, W: int) -> np.ndarray:
+    out = np.empty((H, W), dtype=np.float32)
+    _check("pcad_batch_read_mean",
+           lib().pcad_batch_read_mean(h, int(i),
+                                      out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def pcad_batch_info(h) -> dict:
+    t = ctypes.c_uint64()
+    rows, lpt, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = ctypes.c_float()
+    f = ctypes.c_uint64()
+    _check("pcad_batch_info", lib().pcad_batch_info(h, ctypes.byref(t), ctypes.byref(rows),
+                                                    ctypes.byref(lpt), ctypes.byref(grid),
+                                                    ctypes.byref(ms), ctypes.byref(f)))
+    return dict(t=t.value, tile_rows=rows.value, lpt_order=lpt.value, grid=grid.value,
+                tune_ms=ms.value, fp64_draws=f.value)
+
+
+def pcad_batch_destroy(h):
+    if h is not None and h.value:
+        lib().pcad_batch_destroy(h)
+
+
+def pcad_server_create(max_slots: int, hbm_budget_bytes: int, stream=None):
+    h = ctypes.c_void_p()
+    _check("pcad_server_create", lib().pcad_server_create(int(max_slots), int(hbm_budget_bytes),
+                                                          _stream(stream), ctypes.byref(h)))
+    return h
+
+
+def pcad_server_submit(h, g, model, seed, chain_id, burn_in, nsweeps) -> int:
+    j, gg = _job(g, model, seed, chain_id, burn_in)
+    rid = ctypes.c_uint64()
+    _check("pcad_server_submit",
+           lib().pcad_server_submit(h, ctypes.byref(j), int(nsweeps), ctypes.byref(rid)))
+    return int(rid.value)
+
+
+def pcad_server_step(h, slice_sweeps: int = 16):
+    a, p, f = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("pcad_server_step", lib().pcad_server_step(h, int(slice_sweeps), ctypes.byref(a),
+                                                      ctypes.byref(p), ctypes.byref(f)))
+    return a.value, p.value, f.value
+
+
+def pcad_server_poll(h, rid: int, H: int = 0, W: int = 0):
+    """Returns (state, sample, mean); sample/mean are None unless state == 2
+    and H, W are given (the request is then forgotten by the server)."""
+    st = ctypes.c_int()
+    if H and W:
+        smp = np.empty((H, W), dtype=np.uint8)
+        mean = np.empty((H, W), dtype=np.float32)
+        _check("pcad_server_poll", lib().pcad_server_poll(
+            h, int(rid), ctypes.byref(st), smp.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)),
+            mean.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        if st.value == 2:
+            return st.value, smp, mean
+        return st.value, None, None
+    _check("pcad_server_poll", lib().pcad_server_poll(h, int(rid), ctypes.byref(st), None, None))
+    return st.value, None, None
+
+
+def pcad_server_info(h) -> dict:
+    used = ctypes.c_size_t()
+    sl = ctypes.c_uint64()
+    f = ctypes.c_uint64()
+    _check("pcad_server_info", lib().pcad_server_info(h, ctypes.byref(used), ctypes.byref(sl),
+                                                      ctypes.byref(f)))
+    return dict(hbm_used=used.value, slices=sl.value, fp64_draws=f.value)
+
+
+def pcad_server_destroy(h):
+    if h is not None and h.value:
+        lib().pcad_server_destroy(h)

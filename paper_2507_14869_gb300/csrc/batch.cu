@@ -1,0 +1,868 @@
+// Batched chains and the continuous-batching server.
+//
+// Both keep one SlotDesc per chain in device memory (pointers, size, model,
+// the chain's own sweep counter and sweep budget) and a work list of tiles
+// (rows x 32 sites of one chain), and advance every active chain by one sweep
+// per launch of the persistent batch kernel.  A chain's state after t sweeps
+// lives in x[t & 1] and its draws are keyed by its own (seed, chain id,
+// sweep, row, col), so a chain gives the same labels whatever else shares
+// the launch.
+//
+// pcad_batch: a fixed set of chains run in lockstep; sweeps are issued in
+// slices of kSlice captured once into a CUDA graph.  At creation an optional
+// autotuner times the tile height and the work-list order on the batch itself
+// and caches the choice per batch signature.
+//
+// pcad_server: requests of different sizes, models and sweep budgets are
+// admitted into free slots while the HBM budget allows, run slice by slice
+// next to whatever else is active, and leave when their budget is spent; the
+// caller collects results with pcad_server_poll.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <vector>
+
+#include "pcad_internal.h"
+
+using namespace pcad;
+
+namespace {
+
+constexpr int kSlice = 16;        // sweeps per batch slice (one graph)
+constexpr size_t kAlign = 256;
+constexpr int kTableBytes = 4096;  // 511 doubles
+
+size_t al(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+#define B_TRY(call)                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return set_error(PCAD_ECUDA, cudaGetErrorString(e_));                     \
+    } while (0)
+
+pcad_status check_job(const pcad_job &j)
+{
+    if (!j.g_host)
+        return set_error(PCAD_EINVAL, "job observation is NULL");
+    if (j.H < 1 || j.W < 1 || j.H > 65535 || j.W > 65535 || j.g_pitch < j.W)
+        return set_error(PCAD_EINVAL, "job size or pitch outside the limits");
+    if (j.burn_in < 0 || j.chain_id >= (1u << 24))
+        return set_error(PCAD_EINVAL, "job burn_in < 0 or chain id >= 2^24");
+    pcad_status st = check_model(&j.model);
+    if (st != PCAD_OK)
+        return st;
+    if (j.model.sampler != PCAD_SAMPLER_PCA)
+        return set_error(PCAD_EINVAL, "batches and the server run the PCA sampler");
+    return PCAD_OK;
+}
+
+// Per-chain device layout inside one allocation.
+struct SlotMem {
+    size_t x0, x1, g, acc, ta, pr, end;
+};
+
+SlotMem slot_layout(int H, int W, int pitch, size_t pr_bytes, size_t base)
+{
+    SlotMem s;
+    const size_t plane = al((size_t)pitch * H);
+    s.x0 = base;
+    s.x1 = s.x0 + plane;
+    s.g = s.x1 + plane;
+    s.acc = s.g + plane;
+    s.ta = s.acc + al((size_t)H * W * sizeof(float));
+    s.pr = s.ta + kTableBytes;
+    s.end = s.pr + al(pr_bytes);
+    return s;
+}
+
+size_t slot_bytes(const pcad_job &j)
+{
+    const int pitch = (int)((j.W + 15) / 16 * 16);
+    const int T = j.model.pair == PCAD_PAIR_POTTS ? 1 : j.model.pair_T;
+    return slot_layout(j.H, j.W, pitch, (size_t)(j.model.nbhd * T + 1) * sizeof(double), 0).end;
+}
+
+// Build a slot: copy g, x0 <- g, acc <- 0, tables; fill the descriptor.
+pcad_status init_slot(const pcad_job &j, char *base, const SlotMem &sm, int pitch,
+                      uint32_t *tdev, const uint32_t *budget, unsigned long long *fp64,
+                      cudaStream_t s, SlotDesc &d)
+{
+    double ta64[511];
+    std::vector<double> pr64;
+    DevModel dm{};
+    model_tables(j.model, ta64, pr64, dm);
+    B_TRY(cudaMemcpy2DAsync(base + sm.g, pitch, j.g_host, j.g_pitch, j.W, j.H,
+                            cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpy2DAsync(base + sm.x0, pitch, base + sm.g, pitch, j.W, j.H,
+                            cudaMemcpyDeviceToDevice, s));
+    B_TRY(cudaMemsetAsync(base + sm.acc, 0, (size_t)j.H * j.W * sizeof(float), s));
+    B_TRY(cudaMemcpyAsync(base + sm.ta, ta64, sizeof(ta64), cudaMemcpyHostToDevice, s));
+    B_TRY(cudaMemcpyAsync(base + sm.pr, pr64.data(), pr64.size() * sizeof(double),
+                          cudaMemcpyHostToDevice, s));
+    dm.ta64 = (const double *)(base + sm.ta);
+    dm.pr64 = (const double *)(base + sm.pr);
+    d = SlotDesc{};
+    d.g = (const uint8_t *)(base + sm.g);
+    d.x[0] = (uint8_t *)(base + sm.x0);
+    d.x[1] = (uint8_t *)(base + sm.x1);
+    d.acc = (float *)(base + sm.acc);
+    d.tdev = tdev;
+    d.budget = budget;
+    d.fp64_draws = fp64;
+    d.seed = j.seed;
+    d.H = j.H;
+    d.W = j.W;
+    d.pitch = pitch;
+    d.chain = j.chain_id;
+    d.burn_in = j.burn_in;
+    d.ncls = chunk_class(j.model.L);
+    d.nbhd = j.model.nbhd;
+    d.active = 1;
+    d.m = dm;
+    return PCAD_OK;
+}
+
+// Work list: tiles of `rows` x 32; LPT order puts the costliest tiles first.
+std::vector<WorkItem> make_items(const std::vector<SlotDesc> &d, const std::vector<int> &active,
+                                 int rows, bool lpt)
+{
+    std::vector<WorkItem> items;
+    std::vector<long> cost;
+    for (int i : active) {
+        for (int r0 = 0; r0 < d[i].H; r0 += rows)
+            for (int c0 = 0; c0 < d[i].W; c0 += 32) {
+                items.push_back(WorkItem{i, r0, c0, std::min(rows, ((d[i].H - r0 + 3) / 4) * 4)});
+                cost.push_back((long)d[i].ncls * 8 + 4);
+            }
+    }
+    if (lpt) {
+        std::vector<size_t> idx(items.size());
+        for (size_t k = 0; k < idx.size(); ++k)
+            idx[k] = k;
+        std::stable_sort(idx.begin(), idx.end(), [&](size_t a, size_t b) {
+            return cost[a] * items[a].rows > cost[b] * items[b].rows;
+        });
+        std::vector<WorkItem> out(items.size());
+        for (size_t k = 0; k < idx.size(); ++k)
+            out[k] = items[idx[k]];
+        items.swap(out);
+    }
+    return items;
+}
+
+int grid_size()
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * batch_blocks_per_sm();
+}
+
+struct TuneKey {
+    int n;
+    long sites[33];
+    bool operator<(const TuneKey &o) const
+    {
+        if (n != o.n)
+            return n < o.n;
+        return memcmp(sites, o.sites, sizeof(sites)) < 0;
+    }
+};
+struct TuneVal {
+    int rows;
+    int lpt;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+}  // namespace
+
+// ------------------------------------------------------------------- batch
+
+struct pcad_batch {
+    int n = 0;
+    cudaStream_t stream = nullptr;
+    void *block = nullptr;
+    std::vector<pcad_job> jobs;      // g_host pointers are not kept valid (set to NULL)
+    std::vector<SlotMem> mem;
+    std::vector<SlotDesc> desc;
+    SlotDesc *d_slots = nullptr;
+    WorkItem *d_items = nullptr;
+    int n_items = 0;
+    int *d_grab = nullptr;
+    uint32_t *d_t = nullptr, *d_budget = nullptr;
+    unsigned long long *d_fp64 = nullptr;
+    float *d_plane = nullptr;
+    size_t plane_floats = 0;
+    uint64_t t = 0;
+    int grid = 0;
+    int rows = 4;
+    int lpt = 1;
+    float tune_ms = 0.0f;
+    cudaGraphExec_t graph = nullptr;
+};
+
+namespace {
+
+pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
+{
+    std::vector<int> active(b->n);
+    for (int i = 0; i < b->n; ++i)
+        active[i] = i;
+    std::vector<WorkItem> items = make_items(b->desc, active, rows, lpt != 0);
+    if ((int)items.size() > b->n_items && b->d_items) {
+        B_TRY(cudaFreeAsync(b->d_items, b->stream));
+        b->d_items = nullptr;
+    }
+    if (!b->d_items)
+        B_TRY(cudaMallocAsync((void **)&b->d_items, items.size() * sizeof(WorkItem), b->stream));
+    B_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
+                          cudaMemcpyHostToDevice, b->stream));
+    b->n_items = (int)items.size();
+    b->rows = rows;
+    b->lpt = lpt;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    return PCAD_OK;
+}
+
+pcad_status batch_issue_slice(pcad_batch *b, cudaStream_t s)
+{
+    B_TRY(cudaMemsetAsync(b->d_grab, 0, kSlice * sizeof(int), s));
+    for (int k = 0; k < kSlice; ++k)
+        B_TRY(launch_batch_sweep(b->d_slots, b->d_items, b->n_items, b->d_grab + k, (uint32_t)k,
+                                 b->grid, s));
+    B_TRY(launch_batch_advance(b->d_slots, b->n, kSlice, s));
+    return PCAD_OK;
+}
+
+pcad_status batch_graph(pcad_batch *b)
+{
+    cudaStream_t cap;
+    B_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    pcad_status st = PCAD_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        st = batch_issue_slice(b, cap);
+        e = cudaStreamEndCapture(cap, &g);
+    }
+    if (st == PCAD_OK && e != cudaSuccess)
+        st = set_error(PCAD_ECUDA, cudaGetErrorString(e));
+    if (st == PCAD_OK) {
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        if (e != cudaSuccess)
+            st = set_error(PCAD_ECUDA, cudaGetErrorString(e));
+    }
+    if (g)
+        cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    return st;
+}
+
+pcad_status batch_run_sweeps(pcad_batch *b, int nsweeps)
+{
+    std::vector<uint32_t> bud(b->n, (uint32_t)(b->t + nsweeps));
+    B_TRY(cudaMemcpyAsync(b->d_budget, bud.data(), bud.size() * sizeof(uint32_t),
+                          cudaMemcpyHostToDevice, b->stream));
+    if (!b->graph) {
+        pcad_status st = batch_graph(b);
+        if (st != PCAD_OK)
+            return st;
+    }
+    for (int left = nsweeps; left > 0; left -= kSlice)
+        B_TRY(cudaGraphLaunch(b->graph, b->stream));
+    b->t += (uint64_t)nsweeps;
+    return PCAD_OK;
+}
+
+pcad_status batch_reset_state(pcad_batch *b)
+{
+    // x0 <- g and acc <- 0 for every slot, counters to zero
+    for (int i = 0; i < b->n; ++i) {
+        const SlotDesc &d = b->desc[i];
+        B_TRY(cudaMemcpy2DAsync(d.x[0], d.pitch, d.g, d.pitch, d.W, d.H, cudaMemcpyDeviceToDevice,
+                                b->stream));
+        B_TRY(cudaMemsetAsync(d.acc, 0, (size_t)d.H * d.W * sizeof(float), b->stream));
+    }
+    B_TRY(cudaMemsetAsync(b->d_t, 0, b->n * sizeof(uint32_t), b->stream));
+    B_TRY(cudaMemsetAsync(b->d_fp64, 0, b->n * sizeof(unsigned long long), b->stream));
+    b->t = 0;
+    return PCAD_OK;
+}
+
+pcad_status batch_autotune(pcad_batch *b)
+{
+    TuneKey key{};
+    key.n = b->n;
+    for (const SlotDesc &d : b->desc)
+        key.sites[std::min(d.ncls, 32)] += (long)d.H * d.W;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            b->tune_ms = it->second.ms;
+            return batch_set_items(b, it->second.rows, it->second.lpt);
+        }
+    }
+    cudaEvent_t e0, e1;
+    B_TRY(cudaEventCreate(&e0));
+    B_TRY(cudaEventCreate(&e1));
+    const int cand_rows[3] = {4, 8, 16};
+    TuneVal best{4, 1, 1e30f};
+    pcad_status st = PCAD_OK;
+    for (int lpt = 1; lpt >= 0 && st == PCAD_OK; --lpt)
+        for (int r : cand_rows) {
+            st = batch_set_items(b, r, lpt);
+            if (st != PCAD_OK)
+                break;
+            st = batch_run_sweeps(b, kSlice);   // warm + graph
+            if (st == PCAD_OK && cudaEventRecord(e0, b->stream) != cudaSuccess)
+                st = set_error(PCAD_ECUDA, "event record");
+            if (st == PCAD_OK)
+                st = batch_run_sweeps(b, kSlice);
+            if (st == PCAD_OK && cudaEventRecord(e1, b->stream) != cudaSuccess)
+                st = set_error(PCAD_ECUDA, "event record");
+            float ms = 0.0f;
+            if (st == PCAD_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                st = set_error(PCAD_ECUDA, "event timing");
+            if (st == PCAD_OK && ms < best.ms)
+                best = TuneVal{r, lpt, ms};
+            if (st == PCAD_OK)
+                st = batch_reset_state(b);
+            if (st != PCAD_OK)
+                break;
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PCAD_OK)
+        return st;
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    b->tune_ms = best.ms;
+    return batch_set_items(b, best.rows, best.lpt);
+}
+
+}  // namespace
+
+extern "C" {
+
+pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *cuda_stream,
+                              pcad_batch **out)
+{
+    if (!out)
+        return set_error(PCAD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!jobs || n < 1)
+        return set_error(PCAD_EINVAL, "need at least one job");
+    size_t total = 0;
+    std::vector<SlotMem> mem(n);
+    size_t max_plane = 1;
+    for (int i = 0; i < n; ++i) {
+        pcad_status st = check_job(jobs[i]);
+        if (st != PCAD_OK)
+            return st;
+        const int pitch = (jobs[i].W + 15) / 16 * 16;
+        const int T = jobs[i].model.pair == PCAD_PAIR_POTTS ? 1 : jobs[i].model.pair_T;
+        mem[i] = slot_layout(jobs[i].H, jobs[i].W, pitch,
+                             (size_t)(jobs[i].model.nbhd * T + 1) * sizeof(double), total);
+        total = mem[i].end;
+        max_plane = std::max(max_plane, (size_t)jobs[i].H * jobs[i].W);
+    }
+    const size_t off_desc = total;
+    total += al(n * sizeof(SlotDesc));
+    const size_t off_ctr = total;
+    total += al(n * (2 * sizeof(uint32_t) + sizeof(unsigned long long)));
+    const size_t off_grab = total;
+    total += al(kSlice * sizeof(int));
+    const size_t off_plane = total;
+    total += al(max_plane * sizeof(float));
+
+    pcad_batch *b = new pcad_batch();
+    b->n = n;
+    b->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaMallocAsync(&b->block, total, b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        cudaGetLastError();
+        return set_error(e == cudaErrorMemoryAllocation ? PCAD_ENOMEM : PCAD_ECUDA,
+                         cudaGetErrorString(e));
+    }
+    char *base = (char *)b->block;
+    b->mem = mem;
+    b->d_slots = (SlotDesc *)(base + off_desc);
+    unsigned long long *fp64 = (unsigned long long *)(base + off_ctr);
+    b->d_fp64 = fp64;
+    b->d_t = (uint32_t *)(fp64 + n);
+    b->d_budget = b->d_t + n;
+    b->d_grab = (int *)(base + off_grab);
+    b->d_plane = (float *)(base + off_plane);
+    b->plane_floats = max_plane;
+    b->grid = grid_size();
+    b->desc.resize(n);
+    auto bail = [&](pcad_status st) {
+        if (b->d_items)
+            cudaFreeAsync(b->d_items, b->stream);
+        cudaFreeAsync(b->block, b->stream);
+        cudaStreamSynchronize(b->stream);
+        delete b;
+        return st;
+    };
+    e = cudaMemsetAsync(base + off_ctr, 0, al(n * 16), b->stream);
+    if (e != cudaSuccess)
+        return bail(set_error(PCAD_ECUDA, cudaGetErrorString(e)));
+    for (int i = 0; i < n; ++i) {
+        const int pitch = (jobs[i].W + 15) / 16 * 16;
+        pcad_status st = init_slot(jobs[i], base, mem[i], pitch, b->d_t + i, b->d_budget + i,
+                                   fp64 + i, b->stream, b->desc[i]);
+        if (st != PCAD_OK)
+            return bail(st);
+        b->jobs.push_back(jobs[i]);
+        b->jobs.back().g_host = nullptr;
+    }
+    e = cudaMemcpyAsync(b->d_slots, b->desc.data(), n * sizeof(SlotDesc), cudaMemcpyHostToDevice,
+                        b->stream);
+    if (e != cudaSuccess)
+        return bail(set_error(PCAD_ECUDA, cudaGetErrorString(e)));
+    pcad_status st = autotune ? batch_autotune(b) : batch_set_items(b, 4, 1);
+    if (st == PCAD_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
+        st = set_error(PCAD_ECUDA, "batch set-up failed");
+    if (st != PCAD_OK)
+        return bail(st);
+    *out = b;
+    return PCAD_OK;
+}
+
+pcad_status pcad_batch_run(pcad_batch *b, int nsweeps)
+{
+    if (!b || nsweeps < 0)
+        return set_error(PCAD_EINVAL, "bad batch or sweep count");
+    if (nsweeps == 0)
+        return PCAD_OK;
+    if (b->t + (uint64_t)nsweeps > 0xFFFFFFFFull)
+        return set_error(PCAD_EINVAL, "sweep counter would exceed 2^32");
+    for (const pcad_job &j : b->jobs) {
+        const uint64_t t1 = b->t + nsweeps;
+        const uint64_t acc = t1 > (uint64_t)j.burn_in ? t1 - j.burn_in : 0;
+        if ((uint64_t)(j.model.L - 1) * acc >= (1ull << 24))
+            return set_error(PCAD_EINVAL, "accumulator would leave the exact FP32 range");
+    }
+    return batch_run_sweeps(b, nsweeps);
+}
+
+pcad_status pcad_batch_reset(pcad_batch *b)
+{
+    if (!b)
+        return set_error(PCAD_EINVAL, "batch is NULL");
+    return batch_reset_state(b);
+}
+
+pcad_status pcad_batch_sync(pcad_batch *b)
+{
+    if (!b)
+        return set_error(PCAD_EINVAL, "batch is NULL");
+    B_TRY(cudaStreamSynchronize(b->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_batch_read_sample(pcad_batch *b, int i, uint8_t *host_out, int out_pitch)
+{
+    if (!b || !host_out || i < 0 || i >= b->n)
+        return set_error(PCAD_EINVAL, "bad batch read");
+    const SlotDesc &d = b->desc[i];
+    if (out_pitch < d.W)
+        return set_error(PCAD_EINVAL, "out_pitch < W");
+    B_TRY(cudaMemcpy2DAsync(host_out, out_pitch, d.x[b->t & 1], d.pitch, d.W, d.H,
+                            cudaMemcpyDeviceToHost, b->stream));
+    B_TRY(cudaStreamSynchronize(b->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_batch_read_mean(pcad_batch *b, int i, float *host_out)
+{
+    if (!b || !host_out || i < 0 || i >= b->n)
+        return set_error(PCAD_EINVAL, "bad batch read");
+    const SlotDesc &d = b->desc[i];
+    const uint64_t n_acc = b->t > (uint64_t)d.burn_in ? b->t - d.burn_in : 0;
+    if (n_acc == 0)
+        return set_error(PCAD_ESTATE, "no sweep accumulated yet");
+    const long cnt = (long)d.H * d.W;
+    B_TRY(launch_mean(d.acc, (float)n_acc, b->d_plane, cnt, b->stream));
+    B_TRY(cudaMemcpyAsync(host_out, b->d_plane, cnt * sizeof(float), cudaMemcpyDeviceToHost,
+                          b->stream));
+    B_TRY(cudaStreamSynchronize(b->stream));
+    return PCAD_OK;
+}
+
+pcad_status pcad_batch_info(pcad_batch *b, uint64_t *t, int *tile_rows, int *lpt_order,
+                            int *grid, float *tune_ms, uint64_t *fp64_draws)
+{
+    if (!b)
+        return set_error(PCAD_EINVAL, "batch is NULL");
+    if (t)
+        *t = b->t;
+    if (tile_rows)
+        *tile_rows = b->rows;
+    if (lpt_order)
+        *lpt_order = b->lpt;
+    if (grid)
+        *grid = b->grid;
+    if (tune_ms)
+        *tune_ms = b->tune_ms;
+    if (fp64_draws) {
+        std::vector<unsigned long long> v(b->n);
+        B_TRY(cudaMemcpyAsync(v.data(), b->d_fp64, b->n * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, b->stream));
+        B_TRY(cudaStreamSynchronize(b->stream));
+        uint64_t s = 0;
+        for (auto x : v)
+            s += x;
+        *fp64_draws = s;
+    }
+    return PCAD_OK;
+}
+
+void pcad_batch_destroy(pcad_batch *b)
+{
+    if (!b)
+        return;
+    cudaStreamSynchronize(b->stream);
+    if (b->graph)
+        cudaGraphExecDestroy(b->graph);
+    if (b->d_items)
+        cudaFreeAsync(b->d_items, b->stream);
+    cudaFreeAsync(b->block, b->stream);
+    cudaStreamSynchronize(b->stream);
+    delete b;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ server
+
+namespace {
+
+struct Request {
+    uint64_t id = 0;
+    pcad_job job{};
+    std::vector<uint8_t> g;      // host copy of the observation (pitch W)
+    int nsweeps = 0;
+    int state = 0;               // 0 pending, 1 running, 2 done
+    int slot = -1;
+    uint64_t t = 0;              // sweeps done (host mirror)
+    size_t bytes = 0;
+    void *mem = nullptr;
+    std::vector<uint8_t> sample;
+    std::vector<float> mean;
+};
+
+}  // namespace
+
+struct pcad_server {
+    int max_slots = 0;
+    size_t budget = 0, used = 0;
+    cudaStream_t stream = nullptr;
+    void *ctl = nullptr;          // descriptors, counters, grab
+    SlotDesc *d_slots = nullptr;
+    uint32_t *d_t = nullptr, *d_budget = nullptr;
+    unsigned long long *d_fp64 = nullptr;
+    int *d_grab = nullptr;
+    WorkItem *d_items = nullptr;
+    int cap_items = 0, n_items = 0;
+    bool items_dirty = true;
+    int grid = 0;
+    std::vector<SlotDesc> desc;
+    std::vector<uint64_t> slot_req;   // 0 = free
+    std::deque<uint64_t> pending;
+    std::unordered_map<uint64_t, Request> reqs;
+    uint64_t next_id = 1;
+    uint64_t slices = 0;
+};
+
+namespace {
+
+pcad_status server_admit(pcad_server *sv)
+{
+    while (!sv->pending.empty()) {
+        Request &rq = sv->reqs[sv->pending.front()];
+        int slot = -1;
+        for (int i = 0; i < sv->max_slots; ++i)
+            if (sv->slot_req[i] == 0) {
+                slot = i;
+                break;
+            }
+        if (slot < 0 || sv->used + rq.bytes > sv->budget)
+            break;   // first-come first-served: wait for slots or memory
+        sv->pending.pop_front();
+        cudaError_t e = cudaMallocAsync(&rq.mem, rq.bytes, sv->stream);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            sv->pending.push_front(rq.id);
+            return set_error(PCAD_ENOMEM, cudaGetErrorString(e));
+        }
+        const int pitch = (rq.job.W + 15) / 16 * 16;
+        const int T = rq.job.model.pair == PCAD_PAIR_POTTS ? 1 : rq.job.model.pair_T;
+        SlotMem sm = slot_layout(rq.job.H, rq.job.W, pitch,
+                                 (size_t)(rq.job.model.nbhd * T + 1) * sizeof(double), 0);
+        pcad_job j = rq.job;
+        j.g_host = rq.g.data();
+        j.g_pitch = rq.job.W;
+        SlotDesc d{};
+        pcad_status st = init_slot(j, (char *)rq.mem, sm, pitch, sv->d_t + slot,
+                                   sv->d_budget + slot, sv->d_fp64 + slot, sv->stream, d);
+        if (st != PCAD_OK)
+            return st;
+        const uint32_t zero = 0, bud = (uint32_t)rq.nsweeps;
+        const unsigned long long z64 = 0;
+        B_TRY(cudaMemcpyAsync(sv->d_t + slot, &zero, 4, cudaMemcpyHostToDevice, sv->stream));
+        B_TRY(cudaMemcpyAsync(sv->d_budget + slot, &bud, 4, cudaMemcpyHostToDevice, sv->stream));
+        B_TRY(cudaMemcpyAsync(sv->d_fp64 + slot, &z64, 8, cudaMemcpyHostToDevice, sv->stream));
+        B_TRY(cudaMemcpyAsync(sv->d_slots + slot, &d, sizeof(d), cudaMemcpyHostToDevice,
+                              sv->stream));
+        sv->desc[slot] = d;
+        sv->slot_req[slot] = rq.id;
+        sv->used += rq.bytes;
+        rq.slot = slot;
+        rq.state = 1;
+        rq.t = 0;
+        sv->items_dirty = true;
+    }
+    return PCAD_OK;
+}
+
+pcad_status server_items(pcad_server *sv)
+{
+    std::vector<int> active;
+    for (int i = 0; i < sv->max_slots; ++i)
+        if (sv->slot_req[i] != 0)
+            active.push_back(i);
+    std::vector<WorkItem> items = make_items(sv->desc, active, 8, true);
+    if ((int)items.size() > sv->cap_items) {
+        if (sv->d_items)
+            B_TRY(cudaFreeAsync(sv->d_items, sv->stream));
+        sv->cap_items = std::max((int)items.size(), 2 * sv->cap_items);
+        B_TRY(cudaMallocAsync((void **)&sv->d_items, sv->cap_items * sizeof(WorkItem),
+                              sv->stream));
+    }
+    if (!items.empty())
+        B_TRY(cudaMemcpyAsync(sv->d_items, items.data(), items.size() * sizeof(WorkItem),
+                              cudaMemcpyHostToDevice, sv->stream));
+    sv->n_items = (int)items.size();
+    sv->items_dirty = false;
+    return PCAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cuda_stream,
+                               pcad_server **out)
+{
+    if (!out)
+        return set_error(PCAD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_slots < 1 || max_slots > 65536 || hbm_budget_bytes == 0)
+        return set_error(PCAD_EINVAL, "max_slots in [1, 65536] and a non-zero budget");
+    pcad_server *sv = new pcad_server();
+    sv->max_slots = max_slots;
+    sv->budget = hbm_budget_bytes;
+    sv->stream = (cudaStream_t)cuda_stream;
+    const size_t bytes = al(max_slots * sizeof(SlotDesc)) +
+                         al(max_slots * (2 * sizeof(uint32_t) + sizeof(unsigned long long))) +
+                         al(kSlice * sizeof(int));
+    cudaError_t e = cudaMallocAsync(&sv->ctl, bytes, sv->stream);
+    if (e != cudaSuccess) {
+        delete sv;
+        cudaGetLastError();
+        return set_error(PCAD_ENOMEM, cudaGetErrorString(e));
+    }
+    char *p = (char *)sv->ctl;
+    sv->d_slots = (SlotDesc *)p;
+    p += al(max_slots * sizeof(SlotDesc));
+    sv->d_fp64 = (unsigned long long *)p;
+    sv->d_t = (uint32_t *)(sv->d_fp64 + max_slots);
+    sv->d_budget = sv->d_t + max_slots;
+    p += al(max_slots * (2 * sizeof(uint32_t) + sizeof(unsigned long long)));
+    sv->d_grab = (int *)p;
+    e = cudaMemsetAsync(sv->ctl, 0, bytes, sv->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(sv->stream);
+    if (e != cudaSuccess) {
+        cudaFreeAsync(sv->ctl, sv->stream);
+        delete sv;
+        return set_error(PCAD_ECUDA, cudaGetErrorString(e));
+    }
+    sv->desc.assign(max_slots, SlotDesc{});
+    sv->slot_req.assign(max_slots, 0);
+    sv->grid = grid_size();
+    *out = sv;
+    return PCAD_OK;
+}
+
+pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id)
+{
+    if (!sv || !job || !id)
+        return set_error(PCAD_EINVAL, "NULL argument");
+    if (nsweeps < 1)
+        return set_error(PCAD_EINVAL, "nsweeps must be >= 1");
+    pcad_status st = check_job(*job);
+    if (st != PCAD_OK)
+        return st;
+    const uint64_t acc = nsweeps > job->burn_in ? (uint64_t)(nsweeps - job->burn_in) : 0;
+    if ((uint64_t)(job->model.L - 1) * acc >= (1ull << 24))
+        return set_error(PCAD_EINVAL, "accumulator would leave the exact FP32 range");
+    Request rq;
+    rq.id = sv->next_id++;
+    rq.job = *job;
+    rq.job.g_host = nullptr;
+    rq.nsweeps = nsweeps;
+    rq.bytes = slot_bytes(*job);
+    if (rq.bytes > sv->budget)
+        return set_error(PCAD_ENOMEM, "request larger than the whole HBM budget");
+    rq.g.resize((size_t)job->H * job->W);
+    for (int r = 0; r < job->H; ++r)
+        memcpy(rq.g.data() + (size_t)r * job->W, job->g_host + (size_t)r * job->g_pitch, job->W);
+    *id = rq.id;
+    sv->pending.push_back(rq.id);
+    sv->reqs.emplace(rq.id, std::move(rq));
+    return PCAD_OK;
+}
+
+pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, int *n_pending,
+                             int *n_finished)
+{
+    if (!sv || slice_sweeps < 1 || slice_sweeps > kSlice)
+        return set_error(PCAD_EINVAL, "slice_sweeps must be in [1, 16]");
+    pcad_status st = server_admit(sv);
+    if (st != PCAD_OK)
+        return st;
+    if (sv->items_dirty) {
+        st = server_items(sv);
+        if (st != PCAD_OK)
+            return st;
+    }
+    int finished = 0, active = 0;
+    if (sv->n_items > 0) {
+        B_TRY(cudaMemsetAsync(sv->d_grab, 0, kSlice * sizeof(int), sv->stream));
+        for (int k = 0; k < slice_sweeps; ++k)
+            B_TRY(launch_batch_sweep(sv->d_slots, sv->d_items, sv->n_items, sv->d_grab + k,
+                                     (uint32_t)k, sv->grid, sv->stream));
+        B_TRY(launch_batch_advance(sv->d_slots, sv->max_slots, (uint32_t)slice_sweeps,
+                                   sv->stream));
+        ++sv->slices;
+        // harvest: chains whose budget is spent
+        for (int i = 0; i < sv->max_slots; ++i) {
+            if (sv->slot_req[i] == 0)
+                continue;
+            Request &rq = sv->reqs[sv->slot_req[i]];
+            rq.t = std::min<uint64_t>(rq.t + slice_sweeps, (uint64_t)rq.nsweeps);
+            if (rq.t < (uint64_t)rq.nsweeps) {
+                ++active;
+                continue;
+            }
+            const SlotDesc &d = sv->desc[i];
+            rq.sample.resize((size_t)d.H * d.W);
+            rq.mean.assign((size_t)d.H * d.W, 0.0f);
+            B_TRY(cudaMemcpy2DAsync(rq.sample.data(), d.W, d.x[rq.t & 1], d.pitch, d.W, d.H,
+                                    cudaMemcpyDeviceToHost, sv->stream));
+            const uint64_t n_acc = rq.t > (uint64_t)d.burn_in ? rq.t - d.burn_in : 0;
+            if (n_acc > 0) {
+                B_TRY(launch_mean(d.acc, (float)n_acc, d.acc, (long)d.H * d.W, sv->stream));
+                B_TRY(cudaMemcpyAsync(rq.mean.data(), d.acc, (size_t)d.H * d.W * sizeof(float),
+                                      cudaMemcpyDeviceToHost, sv->stream));
+            }
+            SlotDesc off = d;
+            off.active = 0;
+            sv->desc[i] = off;
+            B_TRY(cudaMemcpyAsync(sv->d_slots + i, &sv->desc[i], sizeof(SlotDesc),
+                                  cudaMemcpyHostToDevice, sv->stream));
+            B_TRY(cudaFreeAsync(rq.mem, sv->stream));
+            rq.mem = nullptr;
+            sv->used -= rq.bytes;
+            sv->slot_req[i] = 0;
+            rq.state = 2;
+            rq.slot = -1;
+            sv->items_dirty = true;
+            ++finished;
+        }
+        B_TRY(cudaStreamSynchronize(sv->stream));
+    }
+    if (n_active)
+        *n_active = active;
+    if (n_pending)
+        *n_pending = (int)sv->pending.size();
+    if (n_finished)
+        *n_finished = finished;
+    return PCAD_OK;
+}
+
+pcad_status pcad_server_poll(pcad_server *sv, uint64_t id, int *state, uint8_t *sample_out,
+                             float *mean_out)
+{
+    if (!sv || !state)
+        return set_error(PCAD_EINVAL, "NULL argument");
+    auto it = sv->reqs.find(id);
+    if (it == sv->reqs.end())
+        return set_error(PCAD_EINVAL, "unknown or already collected request");
+    *state = it->second.state;
+    if (it->second.state == 2) {
+        if (sample_out)
+            memcpy(sample_out, it->second.sample.data(), it->second.sample.size());
+        if (mean_out)
+            memcpy(mean_out, it->second.mean.data(), it->second.mean.size() * sizeof(float));
+        if (sample_out || mean_out)
+            sv->reqs.erase(it);
+    }
+    return PCAD_OK;
+}
+
+pcad_status pcad_server_info(pcad_server *sv, size_t *hbm_used, uint64_t *slices,
+                             uint64_t *fp64_draws)
+{
+    if (!sv)
+        return set_error(PCAD_EINVAL, "server is NULL");
+    if (hbm_used)
+        *hbm_used = sv->used;
+    if (slices)
+        *slices = sv->slices;
+    if (fp64_draws) {
+        std::vector<unsigned long long> v(sv->max_slots);
+        B_TRY(cudaMemcpyAsync(v.data(), sv->d_fp64, v.size() * sizeof(unsigned long long),
+                              cudaMemcpyDeviceToHost, sv->stream));
+        B_TRY(cudaStreamSynchronize(sv->stream));
+        uint64_t s = 0;
+        for (auto x : v)
+            s += x;
+        *fp64_draws = s;
+    }
+    return PCAD_OK;
+}
+
+void pcad_server_destroy(pcad_server *sv)
+{
+    if (!sv)
+        return;
+    cudaStreamSynchronize(sv->stream);
+    for (auto &kv : sv->reqs)
+        if (kv.second.mem)
+            cudaFreeAsync(kv.second.mem, sv->stream);
+    if (sv->d_items)
+        cudaFreeAsync(sv->d_items, sv->stream);
+    cudaFreeAsync(sv->ctl, sv->stream);
+    cudaStreamSynchronize(sv->stream);
+    delete sv;
+}
+
+}  // extern "C"

@@ -69,6 +69,44 @@ cudaError_t launch_metrics(const float *est, const uint8_t *clean, int H, int W,
 cudaError_t launch_check_labels(const uint8_t *x, int pitch, int H, int W, int L, int *bad,
                                 cudaStream_t s);
 
+// One chain of a batched or served launch (device memory, filled by the host).
+// The state after t sweeps lives in x[t & 1]; *tdev is the chain's sweep
+// counter and *budget the sweep count it stops at.
+struct SlotDesc {
+    const uint8_t *g;
+    uint8_t *x[2];
+    float *acc;
+    uint32_t *tdev;
+    const uint32_t *budget;
+    unsigned long long *fp64_draws;
+    uint64_t seed;
+    int H, W, pitch;
+    uint32_t chain;
+    int burn_in;
+    int ncls;          // chunk_class(L)
+    int nbhd;
+    int active;        // 0: skip (free serving slot)
+    DevModel m;
+};
+
+// A tile of `rows` x 32 sites of one slot.
+struct WorkItem {
+    int slot;
+    int row0, col0;
+    int rows;
+};
+
+// One sweep (index *tdev + sweep_off for every slot) over all work items:
+// persistent blocks grab items through *grab (zeroed before the launch).
+cudaError_t launch_batch_sweep(const SlotDesc *slots, const WorkItem *items, int n_items,
+                               int *grab, uint32_t sweep_off, int grid, cudaStream_t s);
+
+// For every active slot: *tdev += min(n, *budget - *tdev).
+cudaError_t launch_batch_advance(const SlotDesc *slots, int n_slots, uint32_t n, cudaStream_t s);
+
+// Resident 128-thread blocks per SM of the batch kernel.
+int batch_blocks_per_sm();
+
 // Model validation, host tables and error reporting shared by the entry points.
 pcad_status check_model(const pcad_model *m);
 void model_tables(const pcad_model &m, double *ta64, std::vector<double> &pr64, DevModel &dm);

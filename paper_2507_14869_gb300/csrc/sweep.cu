@@ -53,6 +53,24 @@ __device__ __forceinline__ int draw_site(const SweepArgs &a, bool valid, const S
     return warp_redraw_fp64<NB>(a.m, valid && !certain, in, s, a.fp64_draws);
 }
 
+// One lazy-PCA site update (r, c) at sweep t: draw from x_in, write x_out,
+// accumulate after burn-in.  Every lane of the warp must call it (lanes
+// outside the image pass through the warp-level steps).
+template <int NC, int NB>
+__device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint32_t t, float *Gcol)
+{
+    const bool valid = r < a.H && c < a.W;
+    SiteIn<NB> in{};
+    if (valid)
+        load_site<NB>(a, a.xin, r, c, kTagPCA, t, in);
+    const int s = draw_site<NC, NB>(a, valid, in, Gcol);
+    if (valid) {
+        a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+        if (accumulate_after(a, t))
+            a.acc[(size_t)r * a.W + c] += (float)s;
+    }
+}
+
 template <int NC, int NB>
 __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 {
@@ -60,17 +78,7 @@ __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const int c = blockIdx.x * kBX + threadIdx.x;
     const int r = blockIdx.y * kBY + threadIdx.y;
-    const bool valid = r < a.H && c < a.W;
-    const uint32_t t = sweep_index(a);
-    SiteIn<NB> in{};
-    if (valid)
-        load_site<NB>(a, a.xin, r, c, kTagPCA, t, in);
-    const int s = draw_site<NC, NB>(a, valid, in, G_s + tid);
-    if (valid) {
-        a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-        if (accumulate_after(a, t))
-            a.acc[(size_t)r * a.W + c] += (float)s;
-    }
+    pca_site<NC, NB>(a, r, c, sweep_index(a), G_s + tid);
 }
 
 // Gibbs colour phase q.  A thread owns one "cell": a pair of columns
@@ -118,6 +126,107 @@ __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, i
                 if (rr < a.H && cc < a.W)
                     a.acc[(size_t)rr * a.W + cc] += (float)x[(size_t)rr * a.pitch + cc];
             }
+    }
+}
+
+// Batched lazy-PCA sweep over many chains of uneven size and model.  The
+// grid is persistent (a multiple of the SM count); each block takes work
+// items (tiles of one chain) in the host's order (costliest first) from an
+// atomic counter, runs the same per-site code as pca_direct_kernel, and
+// dispatches on the chain's chunk class and neighbourhood.  A chain's draws
+// depend only on its own (seed, chain id, sweep, row, col), so results are
+// bit-identical to running the chain alone.
+// One tile of a chain for one (chunk class, neighbourhood) variant; not
+// inlined so each variant keeps the single-chain kernel's register budget.
+template <int NC, int NB>
+__device__ __noinline__ void batch_tile(const SweepArgs *sa, int row0, int col0, int rows,
+                                        uint32_t t, float *Gcol)
+{
+    const SweepArgs &a = *sa;
+    const int c = col0 + (int)threadIdx.x;
+    for (int rr = 0; rr < rows; rr += kBY)
+        pca_site<NC, NB>(a, row0 + rr + (int)threadIdx.y, c, t, Gcol);
+}
+
+template <int NB>
+__device__ __forceinline__ void batch_dispatch(const SweepArgs *sa, int ncls, int row0, int col0,
+                                               int rows, uint32_t t, float *Gcol)
+{
+    switch (ncls) {
+    case 1: batch_tile<1, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 2: batch_tile<2, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 3: batch_tile<3, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 4: batch_tile<4, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 5: batch_tile<5, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 8: batch_tile<8, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 16: batch_tile<16, NB>(sa, row0, col0, rows, t, Gcol); break;
+    default: batch_tile<32, NB>(sa, row0, col0, rows, t, Gcol); break;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *__restrict__ slots,
+                                                             const WorkItem *__restrict__ items,
+                                                             int n_items, int *grab,
+                                                             uint32_t sweep_off)
+{
+    __shared__ float G_s[32 * kThreads];
+    __shared__ int s_item;
+    __shared__ uint32_t s_t;
+    __shared__ int s_go;
+    __shared__ SweepArgs s_args;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            const int it = atomicAdd(grab, 1);
+            s_item = it;
+            s_go = 0;
+            if (it < n_items) {
+                const SlotDesc &d = slots[items[it].slot];
+                const uint32_t t = *d.tdev + sweep_off;
+                if (d.active && t < *d.budget) {
+                    SweepArgs a{};
+                    a.xin = d.x[t & 1u];
+                    a.xout = d.x[(t + 1u) & 1u];
+                    a.g = d.g;
+                    a.acc = d.acc;
+                    a.fp64_draws = d.fp64_draws;
+                    a.seed = d.seed;
+                    a.H = d.H;
+                    a.W = d.W;
+                    a.pitch = d.pitch;
+                    a.chain = d.chain;
+                    a.burn_in = d.burn_in;
+                    a.last_phase = d.ncls;      // carries the chunk class to the block
+                    a.sweep_off = (uint32_t)d.nbhd;
+                    a.m = d.m;
+                    s_args = a;
+                    s_t = t;
+                    s_go = 1;
+                }
+            }
+        }
+        __syncthreads();
+        if (s_item >= n_items)
+            return;
+        if (!s_go)
+            continue;
+        const WorkItem w = items[s_item];
+        const int ncls = s_args.last_phase;
+        if (s_args.sweep_off == 8u)
+            batch_dispatch<8>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid);
+        else
+            batch_dispatch<4>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid);
+    }
+}
+
+__global__ void batch_advance_kernel(const SlotDesc *slots, int n_slots, uint32_t n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_slots && slots[i].active) {
+        const uint32_t t = *slots[i].tdev, b = *slots[i].budget;
+        if (t < b)
+            *slots[i].tdev = t + (b - t < n ? b - t : n);
     }
 }
 
@@ -197,6 +306,29 @@ cudaError_t launch_advance(uint32_t *counter, uint32_t n, cudaStream_t s)
 {
     advance_kernel<<<1, 32, 0, s>>>(counter, n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_sweep(const SlotDesc *slots, const WorkItem *items, int n_items,
+                               int *grab, uint32_t sweep_off, int grid, cudaStream_t s)
+{
+    batch_pca_kernel<<<grid, dim3(kBX, kBY), 0, s>>>(slots, items, n_items, grab, sweep_off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_advance(const SlotDesc *slots, int n_slots, uint32_t n, cudaStream_t s)
+{
+    if (n_slots > 0)
+        batch_advance_kernel<<<(n_slots + 127) / 128, 128, 0, s>>>(slots, n_slots, n);
+    return cudaGetLastError();
+}
+
+int batch_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_pca_kernel, kThreads, 0) !=
+        cudaSuccess)
+        nb = 1;
+    return nb > 0 ? nb : 1;
 }
 
 cudaError_t launch_pca_sweep(const SweepArgs &a, cudaStream_t st)

@@ -1,0 +1,155 @@
+"""Batched chains and the continuous-batching server against chains run
+alone (which the parity tests tie to the oracle): every chain's sample and
+posterior mean must be bit-identical, whatever else shares the launches."""
+import numpy as np
+import pytest
+
+import oracle
+from pcad_inputs import Model, flip_noise, gaussian_noise, greyscale_scene, shapes_binary
+
+pytestmark = pytest.mark.gpu
+
+POTTS, TL, GAUSS, FLIP = 0, 1, 0, 1
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import paper_2507_14869_gb300 as pc
+    pc.lib()
+    return pc
+
+
+def _grey(seed, H, W, L, sigma):
+    return gaussian_noise(seed + 1, greyscale_scene(seed, H, W, L, n_shapes=6), sigma, L)
+
+
+def _jobs():
+    bin_g = flip_noise(9, shapes_binary(8, 50, 71), 0.1)
+    return [
+        (bin_g, Model(L=2, pair=POTTS, pair_coef=1.2, noise=FLIP, flip_p=0.1, inertia=1.0), 1, 0, 10),
+        (bin_g, Model(L=2, pair=POTTS, pair_coef=1.2, noise=FLIP, flip_p=0.1, inertia=1.0), 1, 1, 10),
+        (_grey(2, 67, 45, 16, 1.0), Model(L=16, pair=TL, pair_coef=0.85, pair_T=2, sigma=1.0, inertia=2.0), 5, 3, 7),
+        (_grey(3, 1, 1, 16, 1.0), Model(L=16, pair=TL, pair_coef=0.85, pair_T=2, sigma=1.0, inertia=2.0), 5, 4, 0),
+        (_grey(4, 3, 130, 256, 20.0), Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0), 6, 5, 12),
+        (_grey(5, 40, 33, 256, 20.0), Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0), 6, 6, 12),
+        (_grey(6, 45, 52, 5, 1.0), Model(L=5, nbhd=8, pair=POTTS, pair_coef=0.8, sigma=1.0, inertia=0.7), 7, 7, 3),
+        (_grey(7, 29, 64, 33, 3.0), Model(L=33, nbhd=8, pair=POTTS, pair_coef=0.8, sigma=3.0, inertia=0.4), 7, 8, 3),
+        (_grey(8, 100, 100, 16, 1.2), Model(L=16, pair=TL, pair_coef=0.6, pair_T=3, sigma=1.2, inertia=0.0), 9, 9, 20),
+    ]
+
+
+def _alone(pc, g, m, seed, chain, burn, n):
+    with pc.Chain(g, m, seed=seed, chain_id=chain, burn_in=burn) as ch:
+        ch.run(n)
+        return ch.sample(), ch.mean()
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batch_is_bit_identical_to_chains_alone(pc, autotune):
+    jobs = _jobs()
+    b = pc.pcad_batch_create(jobs, autotune=autotune)
+    try:
+        for n_total, step in ((37, 37), (57, 20)):
+            pc.pcad_batch_run(b, step)
+            for i, (g, m, seed, chain, burn) in enumerate(jobs):
+                H, W = g.shape
+                xs, ms = _alone(pc, g, m, seed, chain, burn, n_total)
+                assert np.array_equal(pc.pcad_batch_read_sample(b, i, H, W), xs), (i, n_total)
+                assert np.array_equal(pc.pcad_batch_read_mean(b, i, H, W), ms), (i, n_total)
+        info = pc.pcad_batch_info(b)
+        assert info["t"] == 57 and info["tile_rows"] in (4, 8, 16)
+        # reset restarts every chain from its observation
+        pc.pcad_batch_reset(b)
+        pc.pcad_batch_run(b, 37)
+        g, m, seed, chain, burn = jobs[5]
+        xs, _ = _alone(pc, g, m, seed, chain, burn, 37)
+        assert np.array_equal(pc.pcad_batch_read_sample(b, 5, *g.shape), xs)
+    finally:
+        pc.pcad_batch_destroy(b)
+
+
+def test_batch_chain_matches_oracle(pc):
+    """One batched chain checked directly against the FP64 oracle."""
+    jobs = _jobs()
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_run(b, 25)
+        g, m, seed, chain, burn = jobs[2]
+        x, acc, nacc, _ = oracle.run_chain(m, g, 25, burn, seed=seed, chain=chain)
+        assert np.array_equal(pc.pcad_batch_read_sample(b, 2, *g.shape), x)
+        np.testing.assert_allclose(pc.pcad_batch_read_mean(b, 2, *g.shape), acc / nacc,
+                                   rtol=1e-6, atol=0)
+    finally:
+        pc.pcad_batch_destroy(b)
+
+
+def _serve_until_done(pc, sv, ids, shapes, slice_sweeps=16, max_steps=10000):
+    out = {}
+    for _ in range(max_steps):
+        pc.pcad_server_step(sv, slice_sweeps)
+        for rid in list(ids):
+            st, smp, mean = pc.pcad_server_poll(sv, rid, *shapes[rid])
+            if st == 2:
+                out[rid] = (smp, mean)
+                ids.remove(rid)
+        if not ids:
+            return out
+    raise AssertionError("server did not finish")
+
+
+def test_server_result_is_the_same_alone_and_in_the_mix(pc):
+    jobs = _jobs()
+    budgets = [40, 73, 16, 5, 33, 29, 50, 21, 64]
+    target = 5
+    g, m, seed, chain, burn = jobs[target]
+    ref = _alone(pc, g, m, seed, chain, burn, budgets[target])
+    # alone in a server
+    sv = pc.pcad_server_create(8, 1 << 30)
+    try:
+        rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, budgets[target])
+        res = _serve_until_done(pc, sv, [rid], {rid: g.shape}, slice_sweeps=7)
+        assert np.array_equal(res[rid][0], ref[0]) and np.array_equal(res[rid][1], ref[1])
+    finally:
+        pc.pcad_server_destroy(sv)
+    # in a mix: others arrive before and after, with other slice lengths
+    sv = pc.pcad_server_create(4, 1 << 30)
+    try:
+        shapes, ids, order = {}, [], [0, 2, 6, target, 1, 3, 4, 7, 8]
+        for k, i in enumerate(order):
+            gi, mi, si, ci, bi = jobs[i]
+            rid = pc.pcad_server_submit(sv, gi, mi, si, ci, bi, budgets[i])
+            shapes[rid] = gi.shape
+            ids.append(rid)
+            if i == target:
+                tid = rid
+            if k % 2 == 1:
+                pc.pcad_server_step(sv, 3)
+        want = {rid: i for rid, i in zip(ids, order)}
+        res = _serve_until_done(pc, sv, list(ids), shapes, slice_sweeps=11)
+        assert np.array_equal(res[tid][0], ref[0]) and np.array_equal(res[tid][1], ref[1])
+        for rid, (smp, mean) in res.items():
+            gi, mi, si, ci, bi = jobs[want[rid]]
+            xs, ms = _alone(pc, gi, mi, si, ci, bi, budgets[want[rid]])
+            assert np.array_equal(smp, xs)
+            assert np.array_equal(mean, ms)
+    finally:
+        pc.pcad_server_destroy(sv)
+
+
+def test_server_admission_waits_for_budget_and_slots(pc):
+    jobs = _jobs()
+    g, m, seed, chain, burn = jobs[8]          # 100x100 L=16
+    sv = pc.pcad_server_create(16, 100_000)     # room for one 100x100 request at a time
+    try:
+        ids = [pc.pcad_server_submit(sv, g, m, seed, chain + k, burn, 32) for k in range(3)]
+        act, pend, fin = pc.pcad_server_step(sv, 16)
+        assert act == 1 and pend == 2 and fin == 0
+        assert pc.pcad_server_info(sv)["hbm_used"] <= 200_000
+        res = _serve_until_done(pc, sv, list(ids), {r: g.shape for r in ids})
+        for k, rid in enumerate(ids):
+            xs, ms = _alone(pc, g, m, seed, chain + k, burn, 32)
+            assert np.array_equal(res[rid][0], xs)
+        with pytest.raises(pc.PcadError):
+            pc.pcad_server_submit(sv, np.zeros((400, 400), np.uint8), m, 1, 0, 0, 10)
+    finally:
+        pc.pcad_server_destroy(sv)
