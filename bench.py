@@ -52,6 +52,13 @@ def _args():
                    help="run one SIDE x SIDE chain with L labels for SWEEPS sweeps and exit "
                         "(the small case ncu captures; prints no JSON line)")
     p.add_argument("--sampler", type=int, default=0, help="profile case: 0 PCA, 1 Gibbs")
+    p.add_argument("--workload", default="chain", choices=["chain", "batch", "serve"],
+                   help="chain: the 512x512 L=256 chain (default); batch: uneven images x 4 "
+                        "chains in one persistent launch vs one chain per launch; serve: "
+                        "Poisson request stream through the continuous-batching server")
+    p.add_argument("--images", type=int, default=128, help="batch: number of images")
+    p.add_argument("--requests", type=int, default=24, help="serve: requests per rate")
+    p.add_argument("--rates", default="2,50", help="serve: comma-separated arrival rates (req/s)")
     return p.parse_args()
 
 
@@ -304,6 +311,197 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+BATCH_SWEEPS, BATCH_BURN = 200, 50
+
+
+def run_batch(a):
+    """Uneven images (short side log-uniform 64..2048, aspect 1..3, L in
+    {2, 16, 256}, per-image prior/inertia), 4 chains each, 200 sweeps with
+    burn-in 50: one persistent launch per sweep for all chains, against the
+    same chains run one after another through the chain API on the same GPU.
+    Outputs are bit-identical, so PSNR is equal by construction (checked)."""
+    import numpy as np
+    import torch
+
+    import paper_2507_14869_gb300 as pc
+    from pcad_inputs import batched_jobs
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    imgs = batched_jobs(seed=4, n_images=a.images, chains=4, sweeps=BATCH_SWEEPS,
+                        burn_in=BATCH_BURN)
+    jobs = [(j.noisy, j.model, j.seed, c, j.burn_in) for j in imgs for c in range(j.chains)]
+    sites = sum(g.size for g, *_ in jobs)
+    by_L = {}
+    for g, m, *_ in jobs:
+        by_L[m.L] = by_L.get(m.L, 0) + g.size
+
+    b = pc.pcad_batch_create(jobs, autotune=True, stream=stream)
+    info = pc.pcad_batch_info(b)
+    pc.pcad_batch_run(b, 16)
+    pc.pcad_batch_reset(b)
+    pc.pcad_batch_sync(b)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    with ClockSampler(0) as clk:
+        ev[0].record(stream)
+        pc.pcad_batch_run(b, BATCH_SWEEPS)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+    t_batch = ev[0].elapsed_time(ev[1]) / 1e3
+    fp64 = pc.pcad_batch_info(b)["fp64_draws"]
+
+    chains = [pc.Chain(g, m, seed=s, chain_id=c, burn_in=bi, stream=stream)
+              for g, m, s, c, bi in jobs]
+    for ch in chains[:8]:
+        ch.run(16)
+    for ch in chains:
+        ch.reset()
+    torch.cuda.synchronize()
+    ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev2[0].record(stream)
+    for ch in chains:
+        ch.run(BATCH_SWEEPS)
+    ev2[1].record(stream)
+    torch.cuda.synchronize()
+    t_plain = ev2[0].elapsed_time(ev2[1]) / 1e3
+
+    # equal PSNR: identical posterior means (checked on a spread of chains)
+    same = True
+    psnr = []
+    for k in range(0, len(jobs), max(1, len(jobs) // 16)):
+        g = jobs[k][0]
+        mb = pc.pcad_batch_read_mean(b, k, *g.shape)
+        same &= bool(np.array_equal(mb, chains[k].mean()))
+    for i, j in enumerate(imgs):
+        k = 4 * i
+        psnr.append(chains[k].metrics(j.clean, 0)[0])
+    for ch in chains:
+        ch.close()
+    pc.pcad_batch_destroy(b)
+    n_img = len(imgs)
+    line = {"metric": "img/s (batched, 4 chains per image)", "value": n_img / t_batch,
+            "unit": "img/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{n_img} uneven images x 4 chains, {BATCH_SWEEPS} sweeps, "
+                                   f"burn-in {BATCH_BURN}", "chain_sites": sites,
+                       "sites_by_L": {str(k): v for k, v in sorted(by_L.items())}},
+            "site_updates_per_s": sites * BATCH_SWEEPS / t_batch,
+            "plain_one_chain_per_launch": {"value": n_img / t_plain, "unit": "img/s",
+                                           "ms": 1e3 * t_plain,
+                                           "site_updates_per_s": sites * BATCH_SWEEPS / t_plain},
+            "speedup_vs_plain": t_plain / t_batch,
+            "identical_outputs": same, "mean_psnr_db": float(np.mean(psnr)),
+            "autotune": info, "fp64_redraw_fraction": fp64 / float(sites * BATCH_SWEEPS),
+            "gpu_launches": -(-BATCH_SWEEPS // 16) * 17,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def _serve_stream(pc, sv, reqs, slice_sweeps=16):
+    """Drive the server with arrivals at their Poisson times; returns
+    (latencies s, makespan s, results {index: (sample, mean)})."""
+    t0 = time.perf_counter()
+    order = sorted(range(len(reqs)), key=lambda i: reqs[i]["arrival"])
+    nxt, live, lat, res = 0, {}, {}, {}
+    while len(lat) < len(reqs):
+        now = time.perf_counter() - t0
+        while nxt < len(order) and reqs[order[nxt]]["arrival"] <= now:
+            i = order[nxt]
+            j = reqs[i]["job"]
+            rid = pc.pcad_server_submit(sv, j.noisy, j.model, j.seed, 0, j.burn_in, j.sweeps)
+            live[rid] = i
+            nxt += 1
+        if not live:
+            time.sleep(max(0.0, reqs[order[nxt]]["arrival"] - now))
+            continue
+        pc.pcad_server_step(sv, slice_sweeps)
+        done_t = time.perf_counter() - t0
+        for rid in list(live):
+            i = live[rid]
+            st, smp, mean = pc.pcad_server_poll(sv, rid, *reqs[i]["job"].noisy.shape)
+            if st == 2:
+                lat[i] = done_t - reqs[i]["arrival"]
+                res[i] = (smp, mean)
+                del live[rid]
+    return [lat[i] for i in range(len(reqs))], time.perf_counter() - t0, res
+
+
+def _plain_fifo(pc, reqs, stream):
+    """The same requests one at a time through the chain API, first come first
+    served: each request's service time is measured alone; latency is the
+    queueing simulation over the real arrival times."""
+    import torch
+    service, out = [], {}
+    for i, r in enumerate(reqs):
+        j = r["job"]
+        t = time.perf_counter()
+        with pc.Chain(j.noisy, j.model, seed=j.seed, chain_id=0, burn_in=j.burn_in,
+                      stream=stream) as ch:
+            ch.run(j.sweeps)
+            out[i] = (ch.sample(), ch.mean())
+        torch.cuda.synchronize()
+        service.append(time.perf_counter() - t)
+    free, lat = 0.0, []
+    for i in sorted(range(len(reqs)), key=lambda k: reqs[k]["arrival"]):
+        start = max(free, reqs[i]["arrival"])
+        free = start + service[i]
+        lat.append((i, free - reqs[i]["arrival"]))
+    lat = [v for _, v in sorted(lat)]
+    return lat, free, out, sum(service)
+
+
+def run_serve(a):
+    """Poisson arrivals of denoising requests (square side log-uniform
+    128..2048, L in {16, 256}, sigma uniform [5, 40] on the 0..255 scale,
+    300..3000 sweeps, burn-in a quarter, one chain each) through the
+    continuous-batching server with a 150 GB HBM budget; the same stream one
+    request at a time through the chain API is the comparison.  Results are
+    bit-identical (checked), so PSNR is equal."""
+    import numpy as np
+    import torch
+
+    import paper_2507_14869_gb300 as pc
+    from pcad_inputs import serving_requests
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    rates = [float(x) for x in a.rates.split(",") if x]
+    per_rate = []
+    with ClockSampler(0) as clk:
+        for k, rate in enumerate(rates):
+            reqs = serving_requests(seed=50 + k, rate=rate, n=a.requests)
+            sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
+            lat, span, res = _serve_stream(pc, sv, reqs)
+            info = pc.pcad_server_info(sv)
+            pc.pcad_server_destroy(sv)
+            plat, pspan, pres, busy = _plain_fifo(pc, reqs, stream)
+            same = all(np.array_equal(res[i][0], pres[i][0]) and
+                       np.array_equal(res[i][1], pres[i][1]) for i in res)
+            work = sum(r["job"].noisy.size * r["job"].sweeps for r in reqs)
+            psnr = [pc.pcad_metrics(res[i][1], reqs[i]["job"].clean, reqs[i]["job"].model.L)[0]
+                    for i in range(min(4, len(reqs)))]
+            per_rate.append({
+                "rate_req_s": rate, "requests": len(reqs),
+                "img_s": len(reqs) / span, "p50_s": float(np.percentile(lat, 50)),
+                "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
+                "site_updates_per_s": work / span, "slices": info["slices"],
+                "plain": {"img_s": len(reqs) / pspan, "p50_s": float(np.percentile(plat, 50)),
+                          "p99_s": float(np.percentile(plat, 99)), "busy_s": busy},
+                "identical_outputs": same, "psnr_db_first": psnr})
+    head = per_rate[-1]
+    line = {"metric": "served img/s (continuous batching)", "value": head["img_s"],
+            "unit": "img/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
+            "ms_per_step": 1e3 * head["makespan_s"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Poisson requests, side 128..2048, L in {16,256}, "
+                                   "300..3000 sweeps, 150 GB HBM budget, 16-sweep slices",
+                       "rates": rates, "requests_per_rate": a.requests},
+            "p50_s": head["p50_s"], "p99_s": head["p99_s"], "per_rate": per_rate,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def profile_case(side: int, L: int, sweeps: int, sampler: int):
     """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
     L > 16, else 1), truncated-linear prior (c_T 0.05, T 30 for L > 16; 0.85,
@@ -328,6 +526,10 @@ def main():
         return
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch":
+        run_batch(a)
+    elif a.workload == "serve":
+        run_serve(a)
     else:
         run_ours(a)
 
