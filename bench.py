@@ -38,6 +38,14 @@ WORKLOAD = ("greyscale 512x512, L=256 (uint8), Gaussian sigma=20, truncated-line
             "c_T=0.05 T=30 4-nbhd, lambda=2.0, 2000 sweeps, burn-in 500, FP32 posterior mean")
 # SFU ex2 issue: 32 per SM per clock (4 SM sub-partitions x 8) x 152 SMs x 2070 MHz
 SFU_PEAK_T = 152 * 32 * 2.070e9 / 1e12
+# DRAM bytes (read + write) per site of one pca_direct_kernel<32,4> launch,
+# from the ncu capture in profiles/pca_direct_l256_1024sq.md (6.33 MB over
+# 1024^2 sites), scaled by the sites of a 512^2 launch.  Set to None when the
+# kernel changes until it is captured again.
+NCU_DRAM_BYTES_PER_SITE = 6.326016e6 / (1024 * 1024)
+NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scaled by sites; "
+                    "the working set is L2-resident, so DRAM traffic is below the 3-11 B/site "
+                    "the sweep touches")
 
 
 def _args():
@@ -272,7 +280,7 @@ def run_ours(a):
         return
     per_launch_labels = H * W * m.L
     achieved = per_launch_labels / (launch_ms * 1e-3) / 1e12
-    traffic = os.environ.get("PCAD_NCU_TRAFFIC_BYTES")
+    traffic = NCU_DRAM_BYTES_PER_SITE * H * W if NCU_DRAM_BYTES_PER_SITE else None
     line = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -283,7 +291,7 @@ def run_ours(a):
                    "parallelism": "independent chain per GPU" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
                      "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
-                     "traffic": int(traffic) if traffic else None,
+                     "traffic": traffic, "traffic_source": NCU_TRAFFIC_NOTE,
                      "kernel": "pca_direct_kernel<32,4>",
                      "work_per_unit": "one exponential (SFU) per label evaluation, L=256 per "
                                       "site-update",
