@@ -60,7 +60,7 @@ def _args():
                    help="run one SIDE x SIDE chain with L labels for SWEEPS sweeps and exit "
                         "(the small case ncu captures; prints no JSON line)")
     p.add_argument("--sampler", type=int, default=0, help="profile case: 0 PCA, 1 Gibbs")
-    p.add_argument("--workload", default="chain", choices=["chain", "batch", "serve"],
+    p.add_argument("--workload", default="chain", choices=["chain", "batch", "serve", "blocking"],
                    help="chain: the 512x512 L=256 chain (default); batch: uneven images x 4 "
                         "chains in one persistent launch vs one chain per launch; serve: "
                         "Poisson request stream through the continuous-batching server")
@@ -510,6 +510,64 @@ def run_serve(a):
     print(json.dumps(line), flush=True)
 
 
+def run_blocking(a):
+    """Large single image, 8192x8192: L = 16 (sigma 1.0) and L = 256 (sigma 25)
+    as in the roofline workload, plus the binary flip-noise image; 200 sweeps
+    (40 for L = 256) from the observation, burn-in a quarter, run unblocked
+    (one launch per sweep) and with k = 1, 2, 4, 8 sweeps per TMA-tiled
+    launch.  Outputs are bit-identical across k (checked)."""
+    import numpy as np
+    import torch
+
+    import paper_2507_14869_gb300 as pc
+    from pcad_inputs import Model, flip_noise, large_image, shapes_binary
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    side = 8192
+    cases = []
+    for L in (16, 256):
+        _, noisy, m = large_image(side=side, L=L)
+        cases.append((f"L={L}", noisy, m, 200 if L == 16 else 40))
+    b = flip_noise(6, shapes_binary(5, side, side, n_shapes=64), 0.1)
+    cases.append(("L=2 flip", b, Model(L=2, pair=0, pair_coef=1.2, noise=1, flip_p=0.1,
+                                       inertia=1.0), 200))
+    rows = {}
+    with ClockSampler(0) as clk:
+        for name, g, m, n in cases:
+            res, ref = {}, None
+            for k in (0, 1, 2, 4, 8):
+                ch = pc.Chain(g, m, seed=3, chain_id=0, burn_in=n // 4, stream=stream)
+                ch.set_blocking(k)
+                ch.run(8)
+                ch.reset()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ch.run(n)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ch.sync()
+                ms = e0.elapsed_time(e1)
+                x = ch.sample()
+                same = True if ref is None else bool(np.array_equal(x, ref))
+                ref = x if ref is None else ref
+                res[f"k={k}" if k else "unblocked"] = {
+                    "ms_per_sweep": ms / n, "site_updates_per_s": g.size * n / (ms * 1e-3),
+                    "identical": same}
+                ch.close()
+            rows[name] = {"sweeps": n, "L": m.L, **res}
+    best = max(v["site_updates_per_s"] for k, v in rows["L=16"].items() if k.startswith("k="))
+    line = {"metric": "site-updates/s (8192^2, best k)", "value": best, "unit": "site-updates/s",
+            "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "8192x8192, L=16 sigma 1 / L=256 sigma 25 (c_T 0.05, T 30, "
+                                   "lambda 2) and binary flip p=0.1; unblocked vs k sweeps per "
+                                   "TMA-tiled launch"},
+            "cases": rows, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def profile_case(side: int, L: int, sweeps: int, sampler: int):
     """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
     L > 16, else 1), truncated-linear prior (c_T 0.05, T 30 for L > 16; 0.85,
@@ -538,6 +596,8 @@ def main():
         run_batch(a)
     elif a.workload == "serve":
         run_serve(a)
+    elif a.workload == "blocking":
+        run_blocking(a)
     else:
         run_ours(a)
 

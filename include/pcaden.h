@@ -121,6 +121,16 @@ pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps);
  * counters zero, sweep counter 0) without reallocating (asynchronous). */
 pcad_status pcad_chain_reset(pcad_chain *ch);
 
+/* Temporal blocking of the PCA sweep: k = 1, 2, 4 or 8 sweeps per kernel
+ * launch on shared-memory tiles loaded by TMA with a k-site halo (the tile
+ * recomputes its halo, so the labels are bit-identical to unblocked runs);
+ * k = 0 (the default) issues one launch per sweep with no tiles.  Fewer
+ * than k remaining sweeps of a run use single-sweep launches.  PCAD_EINVAL
+ * for other k or the Gibbs sampler; PCAD_ECUDA if the driver cannot encode
+ * the tile descriptors.  pcad_chain_sync reports PCAD_ETIMEOUT if a tile
+ * load ever failed to complete within its bounded wait. */
+pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
+
 /* Block until the chain's queued work is done. */
 pcad_status pcad_chain_sync(pcad_chain *ch);
 

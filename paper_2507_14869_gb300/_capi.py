@@ -97,6 +97,7 @@ def _declare(L):
         "pcad_chain_run": [vp, ctypes.c_int],
         "pcad_chain_sync": [vp],
         "pcad_chain_reset": [vp],
+        "pcad_chain_set_blocking": [vp, ctypes.c_int],
         "pcad_chain_read_sample": [vp, u8p, ctypes.c_int],
         "pcad_chain_read_sample_dev": [vp, vp, ctypes.c_int],
         "pcad_chain_read_mean": [vp, fp],
@@ -344,6 +345,10 @@ class Chain:
         pcad_chain_reset(self.h)
         return self
 
+    def set_blocking(self, k: int):
+        pcad_chain_set_blocking(self.h, k)
+        return self
+
     def sample(self) -> np.ndarray:
         return pcad_chain_read_sample(self.h, self.H, self.W)
 
@@ -503,3 +508,8 @@ def pcad_server_info(h) -> dict:
 def pcad_server_destroy(h):
     if h is not None and h.value:
         lib().pcad_server_destroy(h)
+
+
+def pcad_chain_set_blocking(h, k: int):
+    """k sweeps per launch on TMA-loaded shared-memory tiles (0: unblocked)."""
+    _check("pcad_chain_set_blocking", lib().pcad_chain_set_blocking(h, int(k)))

@@ -177,6 +177,11 @@ struct pcad_chain {
     double *ta64 = nullptr, *pr64 = nullptr;
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
+    int tb_k = 0;                 // sweeps per temporally blocked launch (0: one per launch)
+    bool maps_ready = false;
+    CUtensorMap xmap[2];          // TMA descriptors of the two label planes
+    CUtensorMap gmap;             // and of the observation
+    int *err = nullptr;           // bounded-wait timeout flag (device)
 };
 
 namespace {
@@ -203,7 +208,18 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
 {
     SweepArgs a = make_args(ch);
     const int ncol = ch->model.nbhd == 4 ? 2 : 4;
-    for (int k = 0; k < n; ++k) {
+    int done = 0;
+    if (ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k > 0) {
+        // temporally blocked: tb_k sweeps per launch, always into the other plane
+        for (; done + ch->tb_k <= n; done += ch->tb_k) {
+            a.sweep_off = (uint32_t)(off0 + done);
+            a.xin = ch->x[cur];
+            a.xout = ch->x[cur ^ 1];
+            CUDA_TRY(launch_pca_tb(ch->xmap[cur], ch->gmap, a, ch->tb_k, ch->err, st));
+            cur ^= 1;
+        }
+    }
+    for (int k = done; k < n; ++k) {
         a.sweep_off = (uint32_t)(off0 + k);
         if (ch->model.sampler == PCAD_SAMPLER_PCA) {
             a.xin = ch->x[cur];
@@ -310,6 +326,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->tdev = (uint32_t *)p;
     ch->fp64 = (unsigned long long *)(p + 8);
     ch->mscratch = (double *)(p + 16);
+    ch->err = (int *)(p + 128);
 
     auto cleanup = [&](pcad_status s) {
         cudaFreeAsync(ch->block, ch->stream);
@@ -441,6 +458,36 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    if (ch->tb_k > 0) {
+        int e = 0;
+        CUDA_TRY(cudaMemcpy(&e, ch->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e)
+            return fail(PCAD_ETIMEOUT, "a tile load of the blocked sweep did not complete");
+    }
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (k != 0 && k != 1 && k != 2 && k != 4 && k != 8)
+        return fail(PCAD_EINVAL, "sweeps per launch must be 0 (unblocked), 1, 2, 4 or 8");
+    if (k > 0 && ch->model.sampler != PCAD_SAMPLER_PCA)
+        return fail(PCAD_EINVAL, "temporal blocking applies to the PCA sampler");
+    if (k > 0 && !ch->maps_ready) {
+        if (!encode_plane_map(&ch->xmap[0], ch->x[0], ch->H, ch->W, ch->pitch) ||
+            !encode_plane_map(&ch->xmap[1], ch->x[1], ch->H, ch->W, ch->pitch) ||
+            !encode_plane_map(&ch->gmap, ch->g, ch->H, ch->W, ch->pitch))
+            return fail(PCAD_ECUDA, "TMA descriptor encoding failed");
+        ch->maps_ready = true;
+    }
+    if (k != ch->tb_k && ch->graph) {
+        cudaStreamSynchronize(ch->stream);
+        cudaGraphExecDestroy(ch->graph);
+        ch->graph = nullptr;
+    }
+    ch->tb_k = k;
     return PCAD_OK;
 }
 

@@ -234,6 +234,33 @@ struct SiteIn {
     uint32_t ub;     // 24-bit uniform numerator
 };
 
+// Two-label draw (L = 2): the same weights and the same certified test as
+// the chunked path, without the chunk machinery.  Label 0 iff u Z < w0.
+template <int NB>
+__device__ __forceinline__ int draw_binary(const DevModel &m, const SiteIn<NB> &in, bool &certain)
+{
+    float P0 = 0.0f, P1 = 0.0f;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const float xj = (float)in.xni[j];
+        P0 = __fadd_rn(P0, fminf(fabsf(xj), m.Tf));
+        P1 = __fadd_rn(P1, fminf(fabsf(xj - 1.0f), m.Tf));
+    }
+    const float gf = (float)in.g;
+    float w0 = label_w(m, P0, gf);
+    float w1 = label_w(m, P1, gf - 1.0f);
+    float delta = 0.0f;
+    if (m.em1 != 0.0f)
+        delta = __fmul_rn(in.xi == 0 ? w0 : w1, m.em1);
+    const float C0 = in.xi == 0 ? __fadd_rn(w0, delta) : w0;
+    const float Z = __fadd_rn(__fadd_rn(w0, w1), delta);
+    const float t = __fmul_rn((float)in.ub * (1.0f / 16777216.0f), Z);
+    const float margin = __fmul_rn(m.eta, Z);
+    const int s = t < C0 ? 0 : 1;
+    certain = s == 0 ? (__fsub_rn(C0, t) > margin) : (__fsub_rn(t, C0) > margin);
+    return s;
+}
+
 // FP32 inverse-CDF draw.  Gcol points at this thread's column of a shared
 // scratch array (stride gstride floats) holding the chunk prefix sums.
 // Returns the label; `certain` is false when the uniform lies within the
@@ -242,6 +269,8 @@ template <int NC, int NB>
 __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gstride,
                                          const SiteIn<NB> &in, uint32_t dirty, bool &certain)
 {
+    if (NC == 1 && m.L == 2)
+        return draw_binary<NB>(m, in, certain);
     float xn[NB];
     __half2 xh[NB];
 #pragma unroll

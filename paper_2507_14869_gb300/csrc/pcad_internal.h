@@ -5,6 +5,7 @@
 #include <cstdint>
 #include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/pcaden.h"
@@ -106,6 +107,15 @@ cudaError_t launch_batch_advance(const SlotDesc *slots, int n_slots, uint32_t n,
 
 // Resident 128-thread blocks per SM of the batch kernel.
 int batch_blocks_per_sm();
+
+// Temporally blocked PCA: k (1..8) sweeps per launch from the plane behind
+// xmap into a.xout; sweep indices *a.sweep_base + a.sweep_off + 0..k-1.
+// *err is set when a bounded wait for the tile loads gives up.
+cudaError_t launch_pca_tb(const CUtensorMap &xmap, const CUtensorMap &gmap, const SweepArgs &a,
+                          int k, int *err, cudaStream_t s);
+
+// TMA descriptor of a uint8 plane (box 96 x 48); false if the driver refuses.
+bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);
 
 // Model validation, host tables and error reporting shared by the entry points.
 pcad_status check_model(const pcad_model *m);
