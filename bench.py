@@ -60,6 +60,8 @@ def _args():
                    help="run one SIDE x SIDE chain with L labels for SWEEPS sweeps and exit "
                         "(the small case ncu captures; prints no JSON line)")
     p.add_argument("--sampler", type=int, default=0, help="profile case: 0 PCA, 1 Gibbs")
+    p.add_argument("--blocking", type=int, default=0,
+                   help="profile case: sweeps per TMA-tiled launch (0: unblocked)")
     p.add_argument("--workload", default="chain", choices=["chain", "batch", "serve", "blocking"],
                    help="chain: the 512x512 L=256 chain (default); batch: uneven images x 4 "
                         "chains in one persistent launch vs one chain per launch; serve: "
@@ -568,27 +570,34 @@ def run_blocking(a):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(side: int, L: int, sweeps: int, sampler: int):
+def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0):
     """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
     L > 16, else 1), truncated-linear prior (c_T 0.05, T 30 for L > 16; 0.85,
-    2 otherwise), lambda 2.0."""
+    2 otherwise), lambda 2.0; L = 2 uses the binary flip-noise scene (Ising
+    c_P 1.2, p 0.1, lambda 1.0).  blocking: sweeps per TMA-tiled launch."""
     import paper_2507_14869_gb300 as pc
-    from pcad_inputs import Model, gaussian_noise, greyscale_scene
-    sig = 20.0 if L > 16 else 1.0
-    clean = greyscale_scene(3, side, side, L)
-    noisy = gaussian_noise(4, clean, sig, L)
-    m = Model(L=L, pair=1, pair_coef=0.05 if L > 16 else 0.85, pair_T=30 if L > 16 else 2,
-              sigma=sig, inertia=2.0, sampler=sampler)
+    from pcad_inputs import Model, flip_noise, gaussian_noise, greyscale_scene, shapes_binary
+    if L == 2:
+        noisy = flip_noise(6, shapes_binary(5, side, side, n_shapes=16), 0.1)
+        m = Model(L=2, pair=0, pair_coef=1.2, noise=1, flip_p=0.1, inertia=1.0, sampler=sampler)
+    else:
+        sig = 20.0 if L > 16 else 1.0
+        clean = greyscale_scene(3, side, side, L)
+        noisy = gaussian_noise(4, clean, sig, L)
+        m = Model(L=L, pair=1, pair_coef=0.05 if L > 16 else 0.85, pair_T=30 if L > 16 else 2,
+                  sigma=sig, inertia=2.0, sampler=sampler)
     with pc.Chain(noisy, m, seed=1, chain_id=0, burn_in=0) as ch:
+        ch.set_blocking(blocking)
         ch.run(sweeps)
         ch.sync()
-        print(f"profile case {side}x{side} L={L} sweeps={sweeps} fp64 re-draws={ch.fp64_draws()}")
+        print(f"profile case {side}x{side} L={L} sweeps={sweeps} k={blocking} "
+              f"fp64 re-draws={ch.fp64_draws()}")
 
 
 def main():
     a = _args()
     if a.profile_case:
-        profile_case(*a.profile_case, a.sampler)
+        profile_case(*a.profile_case, a.sampler, a.blocking)
         return
     if a.impl == "reference":
         run_reference(a)
