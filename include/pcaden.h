@@ -131,6 +131,24 @@ pcad_status pcad_chain_reset(pcad_chain *ch);
  * load ever failed to complete within its bounded wait. */
 pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
 
+/* Kernel of the unblocked PCA sweep (k = 0 above).  The prior sums of
+ * Eq. posterior_pca_transition_matrix are, per site, the product of the
+ * neighbour-label histogram with the banded matrix max(T - |t - s|, 0);
+ * PCAD_KERNEL_TENSOR computes that product on the tensor cores (tcgen05)
+ * and the rest of the draw on the CUDA cores; PCAD_KERNEL_CUDA_CORE
+ * evaluates every label's prior on the CUDA cores.  Both draw exactly the
+ * same labels.  PCAD_KERNEL_AUTO (the default) takes the tensor cores when
+ * the model allows it: PCA sampler, L >= 64, T <= 65.  PCAD_EINVAL for an
+ * unknown kind or PCAD_KERNEL_TENSOR on a model outside those limits.
+ * pcad_chain_sync reports PCAD_ETIMEOUT if a tensor-core completion wait
+ * ever gave up. */
+typedef enum {
+    PCAD_KERNEL_AUTO = 0,
+    PCAD_KERNEL_CUDA_CORE = 1,
+    PCAD_KERNEL_TENSOR = 2
+} pcad_kernel;
+pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
+
 /* Block until the chain's queued work is done. */
 pcad_status pcad_chain_sync(pcad_chain *ch);
 

@@ -98,6 +98,7 @@ def _declare(L):
         "pcad_chain_sync": [vp],
         "pcad_chain_reset": [vp],
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
+        "pcad_chain_set_kernel": [vp, ctypes.c_int],
         "pcad_chain_read_sample": [vp, u8p, ctypes.c_int],
         "pcad_chain_read_sample_dev": [vp, vp, ctypes.c_int],
         "pcad_chain_read_mean": [vp, fp],
@@ -349,6 +350,10 @@ class Chain:
         pcad_chain_set_blocking(self.h, k)
         return self
 
+    def set_kernel(self, kind: int):
+        pcad_chain_set_kernel(self.h, kind)
+        return self
+
     def sample(self) -> np.ndarray:
         return pcad_chain_read_sample(self.h, self.H, self.W)
 
@@ -513,3 +518,13 @@ def pcad_server_destroy(h):
 def pcad_chain_set_blocking(h, k: int):
     """k sweeps per launch on TMA-loaded shared-memory tiles (0: unblocked)."""
     _check("pcad_chain_set_blocking", lib().pcad_chain_set_blocking(h, int(k)))
+
+
+PCAD_KERNEL_AUTO = 0
+PCAD_KERNEL_CUDA_CORE = 1
+PCAD_KERNEL_TENSOR = 2
+
+
+def pcad_chain_set_kernel(h, kind: int):
+    """Kernel of unblocked PCA sweeps: auto, CUDA cores, or tensor-core prior sums."""
+    _check("pcad_chain_set_kernel", lib().pcad_chain_set_kernel(h, int(kind)))

@@ -132,7 +132,6 @@ void build_tables(const pcad_model &m, ModelTables &t)
     d.Tf = (float)T;
     d.em1 = (float)std::expm1(lam);
     d.el64 = std::exp(lam);
-    d.pad_ = 0;
     // Rigorous bound on |C_k/Z (FP32) - F_k (exact)|.  Exponent v = alpha Q +
     // gam P: |dv| <= u (2|gam P| + |alpha Q| + |v|) from the two rounded
     // coefficients and the two roundings.  The CDF error from the weights is
@@ -149,6 +148,13 @@ void build_tables(const pcad_model &m, ModelTables &t)
                        4.0 * u;
     const double gsum = 21.0 * u;
     d.eta = (float)(1.5 * 2.0 * (2.0 * e_w + gsum) + 8.0 * u);
+    // Tensor-core sweep: v' = alpha Q + mu Pb with mu = -gam and Pb = nT - P
+    // (n neighbours inside the image), i.e. v' = v + mu n T.  |dv'| <= u (2|v'|
+    // + 3 mu Pb) and E_p|v'| <= E_p|v| + A <= 2A + log2 L, so the weight part
+    // becomes u ln2 (7A + 2 log2 L) + e_ex2; the summation part is unchanged.
+    const double e_wb = u * 0.6931471805599453 * (7.0 * A + 2.0 * std::log2((double)m.L)) +
+                        4.0 * u;
+    d.eta_b = (float)(1.5 * 2.0 * (2.0 * e_wb + gsum) + 8.0 * u);
     d.ta64 = nullptr;
     d.pr64 = nullptr;
 }
@@ -178,6 +184,7 @@ struct pcad_chain {
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
     int tb_k = 0;                 // sweeps per temporally blocked launch (0: one per launch)
+    int kernel = PCAD_KERNEL_AUTO;  // kernel of unblocked PCA sweeps
     bool maps_ready = false;
     CUtensorMap xmap[2];          // TMA descriptors of the two label planes
     CUtensorMap gmap;             // and of the observation
@@ -203,10 +210,19 @@ SweepArgs make_args(const pcad_chain *ch)
     return a;
 }
 
+// Unblocked PCA sweeps run on the tensor-core kernel.
+bool uses_tc(const pcad_chain *ch)
+{
+    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->kernel == PCAD_KERNEL_CUDA_CORE)
+        return false;
+    return pca_tc_eligible(ch->dm);
+}
+
 // Issue sweeps [*counter + off0, *counter + off0 + n) without advancing the counter.
 pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t st)
 {
     SweepArgs a = make_args(ch);
+    const bool tc = uses_tc(ch);
     const int ncol = ch->model.nbhd == 4 ? 2 : 4;
     int done = 0;
     if (ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k > 0) {
@@ -224,7 +240,7 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
         if (ch->model.sampler == PCAD_SAMPLER_PCA) {
             a.xin = ch->x[cur];
             a.xout = ch->x[cur ^ 1];
-            CUDA_TRY(launch_pca_sweep(a, st));
+            CUDA_TRY(tc ? launch_pca_tc(a, ch->err, st) : launch_pca_sweep(a, st));
             cur ^= 1;
         } else {
             a.xin = ch->x[cur];
@@ -458,12 +474,34 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     CUDA_TRY(cudaStreamSynchronize(ch->stream));
-    if (ch->tb_k > 0) {
+    if (ch->tb_k > 0 || uses_tc(ch)) {
         int e = 0;
         CUDA_TRY(cudaMemcpy(&e, ch->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (e == 2)
+            return fail(PCAD_ECUDA, "tensor-core sweep: shared memory not 1024-byte aligned");
         if (e)
-            return fail(PCAD_ETIMEOUT, "a tile load of the blocked sweep did not complete");
+            return fail(PCAD_ETIMEOUT, "a bounded wait of the sweep kernel (tile load or MMA "
+                                       "completion) gave up");
     }
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE && kind != PCAD_KERNEL_TENSOR)
+        return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE or _TENSOR");
+    if (kind == PCAD_KERNEL_TENSOR &&
+        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_tc_eligible(ch->dm)))
+        return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, L >= 64 and "
+                                 "T <= 65");
+    if (kind != ch->kernel && ch->graph) {
+        cudaStreamSynchronize(ch->stream);
+        cudaGraphExecDestroy(ch->graph);
+        ch->graph = nullptr;
+    }
+    ch->kernel = kind;
     return PCAD_OK;
 }
 

@@ -51,7 +51,7 @@ struct DevModel {
     float Tf;          // (float)T
     float em1;         // e^lambda - 1 (0: no inertia)
     float eta;         // FP32 error bound of the normalised CDF
-    int pad_;
+    float eta_b;       // the same for the banded-prior weights of the tensor-core sweep
     const double *ta64;  // [511] data factor exp(-(U(g, g-d) - U(g,g))) at d + 255, FP64
     const double *pr64;  // [pmax + 1] exp(-c P), FP64
     double el64;         // e^lambda, FP64
@@ -261,6 +261,68 @@ __device__ __forceinline__ int draw_binary(const DevModel &m, const SiteIn<NB> &
     return s;
 }
 
+// Inverse-CDF selection shared by the FP32 draws.  Gcol (stride gstride)
+// holds the inclusive chunk prefix sums of the inertia-free weights of the
+// nc chunks, G their total; delta is the inertia correction added at and
+// above label xi.  chunk_prefix(c, p) must return the inclusive prefix sums
+// p[0..7] of chunk c's weights, bit-identical to the weights behind Gcol.
+// Returns the label; `certain` is false when u lies within eta Z of an end
+// of the chosen label's CDF interval.
+template <typename ChunkPrefix>
+__device__ __forceinline__ int cdf_select(const DevModel &m, float eta, const float *Gcol,
+                                          int gstride, int nc, float G, float delta, int xi,
+                                          uint32_t ub, bool &certain, ChunkPrefix chunk_prefix)
+{
+    const float Z = __fadd_rn(G, delta);
+    const float t = __fmul_rn((float)ub * (1.0f / 16777216.0f), Z);
+    // smallest chunk whose (inertia-corrected) prefix exceeds t
+    int lo = 0, hi = nc - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float gm = __fadd_rn(Gcol[mid * gstride],
+                                   (xi <= mid * kChunk + kChunk - 1) ? delta : 0.0f);
+        if (t < gm)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    const int cs = lo;
+    const int base = cs * kChunk;
+    const int kmax = min(kChunk - 1, m.L - 1 - base);
+    if (kmax < 0) {  // only reachable through rounding: leave it to FP64
+        certain = false;
+        return m.L - 1;
+    }
+    const float Gprev = cs > 0 ? Gcol[(cs - 1) * gstride] : 0.0f;
+    float p[kChunk];
+    chunk_prefix(cs, p);
+    int k = kmax;
+    float hiC = 0.0f;
+    bool found = false;
+#pragma unroll
+    for (int kk = kChunk - 1; kk >= 0; --kk) {
+        const float Ck = __fadd_rn(__fadd_rn(Gprev, p[kk]), (base + kk >= xi) ? delta : 0.0f);
+        if (kk <= kmax && t < Ck) {
+            k = kk;
+            hiC = Ck;
+            found = true;
+        }
+    }
+    if (!found)
+        hiC = __fadd_rn(__fadd_rn(Gprev, p[kmax]), (base + kmax >= xi) ? delta : 0.0f);
+    float loC;
+    if (k > 0)
+        loC = __fadd_rn(__fadd_rn(Gprev, p[k - 1]), (base + k - 1 >= xi) ? delta : 0.0f);
+    else
+        loC = __fadd_rn(Gprev, (base - 1 >= xi) ? delta : 0.0f);
+    const int s = max(0, base + k);
+    const float margin = __fmul_rn(eta, Z);
+    const bool ok_hi = (s == m.L - 1) || (__fsub_rn(hiC, t) > margin);
+    const bool ok_lo = (s == 0) || (__fsub_rn(t, loC) > margin);
+    certain = found && ok_hi && ok_lo;
+    return min(s, m.L - 1);
+}
+
 // FP32 inverse-CDF draw.  Gcol points at this thread's column of a shared
 // scratch array (stride gstride floats) holding the chunk prefix sums.
 // Returns the label; `certain` is false when the uniform lies within the
@@ -303,54 +365,10 @@ __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gst
     float delta = 0.0f;
     if (m.em1 != 0.0f)
         delta = __fmul_rn(single_w<NB>(m, xn, gf, xi), m.em1);
-    const float Z = __fadd_rn(G, delta);
-    const float t = __fmul_rn((float)in.ub * (1.0f / 16777216.0f), Z);
-    // smallest chunk whose (inertia-corrected) prefix exceeds t
-    int lo = 0, hi = NC - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const float gm = __fadd_rn(Gcol[mid * gstride],
-                                   (xi <= mid * kChunk + kChunk - 1) ? delta : 0.0f);
-        if (t < gm)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    const int cs = lo;
-    const int base = cs * kChunk;
-    const int kmax = min(kChunk - 1, m.L - 1 - base);
-    if (kmax < 0) {  // only reachable through rounding: leave it to FP64
-        certain = false;
-        return m.L - 1;
-    }
-    const float Gprev = cs > 0 ? Gcol[(cs - 1) * gstride] : 0.0f;
-    float p[kChunk];
-    chunk_weights<NB, true, true>(m, xh, T2, gf, cs, p);
-    int k = kmax;
-    float hiC = 0.0f;
-    bool found = false;
-#pragma unroll
-    for (int kk = kChunk - 1; kk >= 0; --kk) {
-        const float Ck = __fadd_rn(__fadd_rn(Gprev, p[kk]), (base + kk >= xi) ? delta : 0.0f);
-        if (kk <= kmax && t < Ck) {
-            k = kk;
-            hiC = Ck;
-            found = true;
-        }
-    }
-    if (!found)
-        hiC = __fadd_rn(__fadd_rn(Gprev, p[kmax]), (base + kmax >= xi) ? delta : 0.0f);
-    float loC;
-    if (k > 0)
-        loC = __fadd_rn(__fadd_rn(Gprev, p[k - 1]), (base + k - 1 >= xi) ? delta : 0.0f);
-    else
-        loC = __fadd_rn(Gprev, (base - 1 >= xi) ? delta : 0.0f);
-    const int s = max(0, base + k);
-    const float margin = __fmul_rn(m.eta, Z);
-    const bool ok_hi = (s == m.L - 1) || (__fsub_rn(hiC, t) > margin);
-    const bool ok_lo = (s == 0) || (__fsub_rn(t, loC) > margin);
-    certain = found && ok_hi && ok_lo;
-    return min(s, m.L - 1);
+    return cdf_select(m, m.eta, Gcol, gstride, NC, G, delta, xi, in.ub, certain,
+                      [&](int cs, float (&p)[kChunk]) {
+                          chunk_weights<NB, true, true>(m, xh, T2, gf, cs, p);
+                      });
 }
 
 // ------------------------------------------------------------ FP64 re-draw

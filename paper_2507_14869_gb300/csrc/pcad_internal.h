@@ -41,6 +41,28 @@ __device__ __forceinline__ bool accumulate_after(const SweepArgs &a, uint32_t t)
     return (long long)t + 1 > (long long)a.burn_in;
 }
 
+// Inputs of site (r, c) from the labels x at sweep t.  Neighbour order:
+// up, down, left, right, then the four diagonals; a neighbour outside the
+// image is "missing" (label 1024).
+template <int NB>
+__device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__restrict__ x, int r,
+                                          int c, uint32_t tag, uint32_t t, SiteIn<NB> &in)
+{
+    constexpr int dr[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
+    constexpr int dc[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const int rr = r + dr[j];
+        const int cc = c + dc[j];
+        const bool inside = rr >= 0 && rr < a.H && cc >= 0 && cc < a.W;
+        in.xni[j] = inside ? (int)x[(size_t)rr * a.pitch + cc] : kMissingLabelI;
+    }
+    const size_t idx = (size_t)r * a.pitch + c;
+    in.xi = x[idx];
+    in.g = a.g[idx];
+    in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
+}
+
 // *counter += n (one thread).
 cudaError_t launch_advance(uint32_t *counter, uint32_t n, cudaStream_t s);
 
@@ -113,6 +135,15 @@ int batch_blocks_per_sm();
 // *err is set when a bounded wait for the tile loads gives up.
 cudaError_t launch_pca_tb(const CUtensorMap &xmap, const CUtensorMap &gmap, const SweepArgs &a,
                           int k, int *err, cudaStream_t s);
+
+// Tensor-core lazy-PCA sweep (prior sums by tcgen05.mma).  Eligible models:
+// L >= kTcMinLabels and truncation T <= kTcMaxT (the banded window must fit
+// shared memory).  *err is set (1: timeout, 2: misaligned shared memory)
+// when the kernel gives up.
+constexpr int kTcMinLabels = 64;
+constexpr int kTcMaxT = 65;
+bool pca_tc_eligible(const DevModel &m);
+cudaError_t launch_pca_tc(const SweepArgs &a, int *err, cudaStream_t s);
 
 // TMA descriptor of a uint8 plane (box 96 x 48); false if the driver refuses.
 bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);

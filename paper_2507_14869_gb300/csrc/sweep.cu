@@ -15,26 +15,6 @@ constexpr int kBX = 32;
 constexpr int kBY = 4;
 constexpr int kThreads = kBX * kBY;
 
-// Neighbour order: up, down, left, right, then the four diagonals.
-template <int NB>
-__device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__restrict__ x, int r,
-                                          int c, uint32_t tag, uint32_t t, SiteIn<NB> &in)
-{
-    constexpr int dr[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
-    constexpr int dc[8] = {0, 0, -1, 1, -1, 1, -1, 1};
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        const int rr = r + dr[j];
-        const int cc = c + dc[j];
-        const bool inside = rr >= 0 && rr < a.H && cc >= 0 && cc < a.W;
-        in.xni[j] = inside ? (int)x[(size_t)rr * a.pitch + cc] : kMissingLabelI;
-    }
-    const size_t idx = (size_t)r * a.pitch + c;
-    in.xi = x[idx];
-    in.g = a.g[idx];
-    in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
-}
-
 // Draw the new label of every valid site of the warp; uncertain FP32 draws
 // are re-evaluated in FP64 by the whole warp.  Every lane must call this.
 template <int NC, int NB>
