@@ -48,6 +48,26 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
                     "the sweep touches")
 
 
+# The same for pca_tc_kernel<4>; None until an ncu capture of the current
+# kernel gives it.
+NCU_TC_DRAM_BYTES_PER_SITE = None
+NCU_TC_TRAFFIC_NOTE = "not captured for this kernel version"
+
+KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2}
+
+
+def _tensor_path(kernel, m):
+    """Whether an unblocked PCA sweep of model m runs on the tensor-core kernel
+    (only on request; the default is the CUDA-core kernel)."""
+    T = 1 if m.pair == 0 else m.pair_T
+    o = (T - 1 + 15) // 16 * 16                       # band padding of the histogram
+    a_slabs = (64 * ((m.L + 63) // 64) + 2 * o + 63) // 64
+    b_slabs = (64 + 2 * o + 63) // 64
+    smem = 2 * a_slabs * 16384 + b_slabs * 8192 + 2 * ((m.L + 7) // 8) * 512 + 4 * 2048 + 240
+    eligible = m.L >= 64 and T <= 65 and smem <= 232448
+    return kernel == "tensor" and eligible
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -66,6 +86,9 @@ def _args():
                    help="chain: the 512x512 L=256 chain (default); batch: uneven images x 4 "
                         "chains in one persistent launch vs one chain per launch; serve: "
                         "Poisson request stream through the continuous-batching server")
+    p.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor"],
+                   help="kernel of the unblocked PCA sweep (chain workload and profile case): "
+                        "auto = cuda_core; tensor = prior sums by tcgen05.mma")
     p.add_argument("--images", type=int, default=128, help="batch: number of images")
     p.add_argument("--requests", type=int, default=24, help="serve: requests per rate")
     p.add_argument("--rates", default="2,50", help="serve: comma-separated arrival rates (req/s)")
@@ -231,7 +254,10 @@ def run_ours(a):
         ms = [e0.elapsed_time(e1) for e0, e1 in evs]
         return ms, wall
 
+    kind = KERNEL_KINDS[a.kernel]
+    on_tc = _tensor_path(a.kernel, m)
     pca = pc.Chain(noisy, m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream)
+    pca.set_kernel(kind)
     with ClockSampler(local) as clk:
         ms, wall = timed(pca, a.steps, a.warmup)
     T = sum(ms) / 1e3
@@ -271,6 +297,7 @@ def run_ours(a):
     for k in range(e2e_steps + 1):
         t0 = time.perf_counter()
         ch = pc.Chain(g_host.numpy(), m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream)
+        ch.set_kernel(kind)
         ch.run(SWEEPS)
         pc.pcad_chain_read_mean(ch.h, H, W, out=mean_host.numpy())
         ch.close()
@@ -282,7 +309,8 @@ def run_ours(a):
         return
     per_launch_labels = H * W * m.L
     achieved = per_launch_labels / (launch_ms * 1e-3) / 1e12
-    traffic = NCU_DRAM_BYTES_PER_SITE * H * W if NCU_DRAM_BYTES_PER_SITE else None
+    per_site = NCU_TC_DRAM_BYTES_PER_SITE if on_tc else NCU_DRAM_BYTES_PER_SITE
+    traffic = per_site * H * W if per_site else None
     line = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -293,8 +321,10 @@ def run_ours(a):
                    "parallelism": "independent chain per GPU" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
                      "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
-                     "traffic": traffic, "traffic_source": NCU_TRAFFIC_NOTE,
-                     "kernel": "pca_direct_kernel<32,4>",
+                     "traffic": traffic,
+                     "traffic_source": NCU_TC_TRAFFIC_NOTE if on_tc else NCU_TRAFFIC_NOTE,
+                     "kernel": ("pca_tc_kernel<4> (tcgen05 banded prior sums, CUDA-core CDF)"
+                                if on_tc else "pca_direct_kernel<32,4>"),
                      "work_per_unit": "one exponential (SFU) per label evaluation, L=256 per "
                                       "site-update",
                      "peak_source": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count x max "
@@ -570,7 +600,8 @@ def run_blocking(a):
     print(json.dumps(line), flush=True)
 
 
-def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0):
+def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0,
+                 kernel: str = "auto"):
     """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
     L > 16, else 1), truncated-linear prior (c_T 0.05, T 30 for L > 16; 0.85,
     2 otherwise), lambda 2.0; L = 2 uses the binary flip-noise scene (Ising
@@ -588,16 +619,18 @@ def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0
                   sigma=sig, inertia=2.0, sampler=sampler)
     with pc.Chain(noisy, m, seed=1, chain_id=0, burn_in=0) as ch:
         ch.set_blocking(blocking)
+        if sampler == 0:
+            ch.set_kernel(KERNEL_KINDS[kernel])
         ch.run(sweeps)
         ch.sync()
-        print(f"profile case {side}x{side} L={L} sweeps={sweeps} k={blocking} "
+        print(f"profile case {side}x{side} L={L} sweeps={sweeps} k={blocking} kernel={kernel} "
               f"fp64 re-draws={ch.fp64_draws()}")
 
 
 def main():
     a = _args()
     if a.profile_case:
-        profile_case(*a.profile_case, a.sampler, a.blocking)
+        profile_case(*a.profile_case, a.sampler, a.blocking, a.kernel)
         return
     if a.impl == "reference":
         run_reference(a)

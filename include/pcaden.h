@@ -137,9 +137,15 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * PCAD_KERNEL_TENSOR computes that product on the tensor cores (tcgen05)
  * and the rest of the draw on the CUDA cores; PCAD_KERNEL_CUDA_CORE
  * evaluates every label's prior on the CUDA cores.  Both draw exactly the
- * same labels.  PCAD_KERNEL_AUTO (the default) takes the tensor cores when
- * the model allows it: PCA sampler, L >= 64, T <= 65.  PCAD_EINVAL for an
- * unknown kind or PCAD_KERNEL_TENSOR on a model outside those limits.
+ * same labels.  PCAD_KERNEL_AUTO (the default) is the CUDA-core kernel,
+ * which measured faster on GB300 for every model the tensor-core kernel
+ * accepts (L = 256, 2048 x 2048: 8.1e9 against 6.4e9 site-updates/s).  The
+ * tensor-core kernel accepts the PCA sampler with L >= 64, T <= 65 (Potts:
+ * T = 1), and two histogram operands of 128 x (64 ceil(L/64) + 2 o) FP16
+ * (o = T - 1 rounded up to 16), the 64 x (64 + 2 o) band block and two
+ * 128 x ceil(L/8) FP32 chunk-sum arrays within 227 KB of shared memory --
+ * for L = 256 that is T <= 33.  PCAD_EINVAL for an unknown kind or
+ * PCAD_KERNEL_TENSOR on a model outside those limits.
  * pcad_chain_sync reports PCAD_ETIMEOUT if a tensor-core completion wait
  * ever gave up. */
 typedef enum {

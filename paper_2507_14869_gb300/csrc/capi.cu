@@ -151,10 +151,12 @@ void build_tables(const pcad_model &m, ModelTables &t)
     // Tensor-core sweep: v' = alpha Q + mu Pb with mu = -gam and Pb = nT - P
     // (n neighbours inside the image), i.e. v' = v + mu n T.  |dv'| <= u (2|v'|
     // + 3 mu Pb) and E_p|v'| <= E_p|v| + A <= 2A + log2 L, so the weight part
-    // becomes u ln2 (7A + 2 log2 L) + e_ex2; the summation part is unchanged.
+    // becomes u ln2 (7A + 2 log2 L) + e_ex2.  Its chunk sums come in up to
+    // four label ranges, each Kahan-summed, joined by three more additions:
+    // 24u of summation.
     const double e_wb = u * 0.6931471805599453 * (7.0 * A + 2.0 * std::log2((double)m.L)) +
                         4.0 * u;
-    d.eta_b = (float)(1.5 * 2.0 * (2.0 * e_wb + gsum) + 8.0 * u);
+    d.eta_b = (float)(1.5 * 2.0 * (2.0 * e_wb + 24.0 * u) + 8.0 * u);
     d.ta64 = nullptr;
     d.pr64 = nullptr;
 }
@@ -210,12 +212,12 @@ SweepArgs make_args(const pcad_chain *ch)
     return a;
 }
 
-// Unblocked PCA sweeps run on the tensor-core kernel.
+// Unblocked PCA sweeps run on the tensor-core kernel only on request: the
+// CUDA-core kernel measured faster for every eligible model on GB300.
 bool uses_tc(const pcad_chain *ch)
 {
-    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->kernel == PCAD_KERNEL_CUDA_CORE)
-        return false;
-    return pca_tc_eligible(ch->dm);
+    return ch->model.sampler == PCAD_SAMPLER_PCA && ch->kernel == PCAD_KERNEL_TENSOR &&
+           pca_tc_eligible(ch->dm);
 }
 
 // Issue sweeps [*counter + off0, *counter + off0 + n) without advancing the counter.
@@ -494,8 +496,8 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE or _TENSOR");
     if (kind == PCAD_KERNEL_TENSOR &&
         (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_tc_eligible(ch->dm)))
-        return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, L >= 64 and "
-                                 "T <= 65");
+        return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, L >= 64, "
+                                 "T <= 65 and its banded operands within shared memory");
     if (kind != ch->kernel && ch->graph) {
         cudaStreamSynchronize(ch->stream);
         cudaGraphExecDestroy(ch->graph);

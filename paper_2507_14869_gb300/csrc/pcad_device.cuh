@@ -261,39 +261,40 @@ __device__ __forceinline__ int draw_binary(const DevModel &m, const SiteIn<NB> &
     return s;
 }
 
-// Inverse-CDF selection shared by the FP32 draws.  Gcol (stride gstride)
-// holds the inclusive chunk prefix sums of the inertia-free weights of the
-// nc chunks, G their total; delta is the inertia correction added at and
-// above label xi.  chunk_prefix(c, p) must return the inclusive prefix sums
-// p[0..7] of chunk c's weights, bit-identical to the weights behind Gcol.
-// Returns the label; `certain` is false when u lies within eta Z of an end
-// of the chosen label's CDF interval.
-template <typename ChunkPrefix>
-__device__ __forceinline__ int cdf_select(const DevModel &m, float eta, const float *Gcol,
-                                          int gstride, int nc, float G, float delta, int xi,
-                                          uint32_t ub, bool &certain, ChunkPrefix chunk_prefix)
+// Chunk step of the inverse CDF: the smallest chunk c (of nc) whose
+// inclusive, inertia-corrected prefix Gc(c) (+ delta when label xi lies at
+// or below the chunk's end) exceeds t.
+template <typename ChunkG>
+__device__ __forceinline__ int cdf_find_chunk(ChunkG Gc, int nc, float t, float delta, int xi)
 {
-    const float Z = __fadd_rn(G, delta);
-    const float t = __fmul_rn((float)ub * (1.0f / 16777216.0f), Z);
-    // smallest chunk whose (inertia-corrected) prefix exceeds t
     int lo = 0, hi = nc - 1;
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
-        const float gm = __fadd_rn(Gcol[mid * gstride],
-                                   (xi <= mid * kChunk + kChunk - 1) ? delta : 0.0f);
+        const float gm = __fadd_rn(Gc(mid), (xi <= mid * kChunk + kChunk - 1) ? delta : 0.0f);
         if (t < gm)
             hi = mid;
         else
             lo = mid + 1;
     }
-    const int cs = lo;
+    return lo;
+}
+
+// Label step of the inverse CDF inside chunk cs, whose predecessors sum to
+// Gprev, with the certification: chunk_prefix(c, p) must return the
+// inclusive prefix sums p[0..7] of chunk c's weights, bit-identical to the
+// weights behind the chunk sums.  Returns the label; `certain` is false when
+// t = u Z lies within eta Z of an end of the chosen label's CDF interval.
+template <typename ChunkPrefix>
+__device__ __forceinline__ int cdf_finish(const DevModel &m, float eta, int cs, float Gprev,
+                                          float Z, float t, float delta, int xi, bool &certain,
+                                          ChunkPrefix chunk_prefix)
+{
     const int base = cs * kChunk;
     const int kmax = min(kChunk - 1, m.L - 1 - base);
     if (kmax < 0) {  // only reachable through rounding: leave it to FP64
         certain = false;
         return m.L - 1;
     }
-    const float Gprev = cs > 0 ? Gcol[(cs - 1) * gstride] : 0.0f;
     float p[kChunk];
     chunk_prefix(cs, p);
     int k = kmax;
@@ -321,6 +322,22 @@ __device__ __forceinline__ int cdf_select(const DevModel &m, float eta, const fl
     const bool ok_lo = (s == 0) || (__fsub_rn(t, loC) > margin);
     certain = found && ok_hi && ok_lo;
     return min(s, m.L - 1);
+}
+
+// Inverse-CDF selection shared by the FP32 draws.  Gc(c) returns the
+// inclusive prefix sum of the inertia-free weights up to chunk c (of nc), G
+// their total; delta is the inertia correction added at and above label xi;
+// ub the 24-bit uniform numerator.
+template <typename ChunkG, typename ChunkPrefix>
+__device__ __forceinline__ int cdf_select(const DevModel &m, float eta, ChunkG Gc, int nc,
+                                          float G, float delta, int xi, uint32_t ub,
+                                          bool &certain, ChunkPrefix chunk_prefix)
+{
+    const float Z = __fadd_rn(G, delta);
+    const float t = __fmul_rn((float)ub * (1.0f / 16777216.0f), Z);
+    const int cs = cdf_find_chunk(Gc, nc, t, delta, xi);
+    const float Gprev = cs > 0 ? Gc(cs - 1) : 0.0f;
+    return cdf_finish(m, eta, cs, Gprev, Z, t, delta, xi, certain, chunk_prefix);
 }
 
 // FP32 inverse-CDF draw.  Gcol points at this thread's column of a shared
@@ -365,8 +382,8 @@ __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gst
     float delta = 0.0f;
     if (m.em1 != 0.0f)
         delta = __fmul_rn(single_w<NB>(m, xn, gf, xi), m.em1);
-    return cdf_select(m, m.eta, Gcol, gstride, NC, G, delta, xi, in.ub, certain,
-                      [&](int cs, float (&p)[kChunk]) {
+    return cdf_select(m, m.eta, [&](int c) { return Gcol[c * gstride]; }, NC, G, delta, xi,
+                      in.ub, certain, [&](int cs, float (&p)[kChunk]) {
                           chunk_weights<NB, true, true>(m, xh, T2, gf, cs, p);
                       });
 }

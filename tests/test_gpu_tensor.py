@@ -45,8 +45,8 @@ CASES = [
     ("L128_potts_30x40", lambda: (_grey(7, 30, 40, 128, 6.0),
                                   Model(L=128, pair=POTTS, pair_coef=1.1, sigma=6.0,
                                         inertia=1.0))),
-    ("L256_T65_21x53", lambda: (_grey(8, 21, 53, 256, 30.0),
-                                Model(L=256, pair=TL, pair_coef=0.02, pair_T=65, sigma=30.0,
+    ("L128_T65_21x53", lambda: (_grey(8, 21, 53, 128, 15.0),
+                                Model(L=128, pair=TL, pair_coef=0.02, pair_T=65, sigma=15.0,
                                       inertia=0.0))),
     ("L71_3x1", lambda: (_grey(9, 3, 1, 71, 5.0),
                          Model(L=71, pair=TL, pair_coef=0.3, pair_T=4, sigma=5.0, inertia=1.0))),
@@ -87,10 +87,10 @@ def test_tensor_matches_oracle(pc, nbhd):
     np.testing.assert_allclose(mg, acc / nacc, rtol=1e-6, atol=0)
 
 
-def test_auto_takes_tensor_path_and_redraws_in_fp64(pc):
+def test_auto_equals_tensor_and_redraws_in_fp64(pc):
     g, m = CASES[0][1]()
-    x_auto, m_auto, fp64 = _run(pc, g, m, pc.PCAD_KERNEL_AUTO)
-    x_tc, m_tc, _ = _run(pc, g, m, pc.PCAD_KERNEL_TENSOR)
+    x_auto, m_auto, _ = _run(pc, g, m, pc.PCAD_KERNEL_AUTO)
+    x_tc, m_tc, fp64 = _run(pc, g, m, pc.PCAD_KERNEL_TENSOR)
     assert np.array_equal(x_auto, x_tc) and np.array_equal(m_auto, m_tc)
     assert fp64 > 0   # some uniforms fall inside the certified margin
 
@@ -104,10 +104,12 @@ def test_set_kernel_rejects(pc):
         with pytest.raises(pc.PcadError):
             ch.set_kernel(7)
         ch.set_kernel(pc.PCAD_KERNEL_CUDA_CORE)
-    wide = Model(L=256, pair=TL, pair_coef=0.01, pair_T=100, sigma=20.0, inertia=1.0)
-    with pc.Chain(_grey(13, 20, 20, 256, 20.0), wide, seed=1) as ch:
-        with pytest.raises(pc.PcadError):
-            ch.set_kernel(pc.PCAD_KERNEL_TENSOR)      # T > 65
+    for T in (100, 40):   # T > 65; at L = 256 the band of T = 40 exceeds shared memory
+        wide = Model(L=256, pair=TL, pair_coef=0.01, pair_T=T, sigma=20.0, inertia=1.0)
+        with pc.Chain(_grey(13, 20, 20, 256, 20.0), wide, seed=1) as ch:
+            with pytest.raises(pc.PcadError):
+                ch.set_kernel(pc.PCAD_KERNEL_TENSOR)
+            ch.run(3)                                  # the CUDA-core kernel
     gibbs = Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
     with pc.Chain(_grey(14, 20, 20, 256, 20.0), gibbs, seed=1) as ch:
         with pytest.raises(pc.PcadError):
