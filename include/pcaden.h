@@ -155,6 +155,41 @@ typedef enum {
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 
+/* Posterior energy of the current sample x (Section 4, Eq.
+ * mrf_gauss_noise_posterior_distribution; pi_post ~ exp(-H)):
+ *   H(x) = sum over unordered neighbour pairs V(x_i, x_j) + sum_i U(g_i, x_i)
+ * with the per-edge pair weight of the single-site conditional (Potts
+ * V = -c_P 1{x_i = x_j}, truncated linear V = c_T min(|x_i - x_j|, T);
+ * Gaussian U = (g - x)^2 / (2 sigma^2), flip U = -ln(1 - p) or -ln p), free
+ * boundary.  Optional outputs: the integer sums it is made of -- pair_sum
+ * (Potts: pairs with equal labels; truncated linear: sum of
+ * min(|x_i - x_j|, T)) and data_sum (Gaussian: sum of (g - x)^2; flip:
+ * sites with x != g); H = (-c_P or c_T) pair_sum + data_sum / (2 sigma^2)
+ * (Gaussian) or -ln(1-p) (H W - data_sum) - ln(p) data_sum (flip), in FP64.
+ * Synchronises the chain's stream. */
+pcad_status pcad_chain_energy(pcad_chain *ch, double *energy, uint64_t *pair_sum,
+                              uint64_t *data_sum);
+
+/* Minimum-energy tracking (the maximum a posteriori state by lowest
+ * posterior energy, Section 2): with capacity > 0, every later sweep also
+ * computes H of its result, records it (the first `capacity` values) and
+ * keeps the lowest-energy state seen with the number of completed sweeps
+ * at which it occurred; pcad_chain_reset clears the record.  capacity = 0
+ * turns tracking off and frees its memory (pitch x H bytes + 8 capacity
+ * bytes).  PCAD_ESTATE with temporal blocking on (and set_blocking refuses
+ * k > 0 while tracking).  Not part of an exported checkpoint. */
+pcad_status pcad_chain_track_energy(pcad_chain *ch, int capacity);
+
+/* Energies recorded so far: *n = their number (may exceed max; the first
+ * min(*n, max) are copied to host).  PCAD_ESTATE when tracking is off. */
+pcad_status pcad_chain_read_energies(pcad_chain *ch, double *host, int max, int *n);
+
+/* The lowest-energy state recorded (H rows of W bytes, row pitch
+ * out_pitch), its energy and its sweep count.  PCAD_ESTATE when tracking is
+ * off or no sweep was tracked yet. */
+pcad_status pcad_chain_read_min_state(pcad_chain *ch, uint8_t *host_out, int out_pitch,
+                                      double *energy, uint64_t *sweep);
+
 /* Block until the chain's queued work is done. */
 pcad_status pcad_chain_sync(pcad_chain *ch);
 

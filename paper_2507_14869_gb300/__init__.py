@@ -12,6 +12,8 @@ from ._capi import (  # noqa: F401
     pcad_chain_import, pcad_chain_metrics, pcad_chain_read_mean, pcad_chain_read_sample,
     pcad_chain_read_sample_dev, pcad_chain_reset, pcad_chain_run, pcad_chain_set_blocking, pcad_chain_stats, pcad_chain_sweeps,
     pcad_chain_set_kernel, PCAD_KERNEL_AUTO, PCAD_KERNEL_CUDA_CORE, PCAD_KERNEL_TENSOR,
+    pcad_chain_energy, pcad_chain_track_energy, pcad_chain_read_energies,
+    pcad_chain_read_min_state,
     pcad_chain_sync, pcad_chain_write_sample, pcad_last_error, pcad_metrics, pcad_status_str,
     pcad_pca_run_noalloc, pcad_version,
     PcadJob, pcad_batch_create, pcad_batch_destroy, pcad_batch_info, pcad_batch_read_mean,

@@ -99,6 +99,10 @@ def _declare(L):
         "pcad_chain_reset": [vp],
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
         "pcad_chain_set_kernel": [vp, ctypes.c_int],
+        "pcad_chain_energy": [vp, dp, u64p, u64p],
+        "pcad_chain_track_energy": [vp, ctypes.c_int],
+        "pcad_chain_read_energies": [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+        "pcad_chain_read_min_state": [vp, u8p, ctypes.c_int, dp, u64p],
         "pcad_chain_read_sample": [vp, u8p, ctypes.c_int],
         "pcad_chain_read_sample_dev": [vp, vp, ctypes.c_int],
         "pcad_chain_read_mean": [vp, fp],
@@ -354,6 +358,21 @@ class Chain:
         pcad_chain_set_kernel(self.h, kind)
         return self
 
+    def energy(self):
+        """(H, pair_sum, data_sum) of the current sample."""
+        return pcad_chain_energy(self.h)
+
+    def track_energy(self, capacity: int):
+        pcad_chain_track_energy(self.h, capacity)
+        return self
+
+    def energies(self) -> np.ndarray:
+        return pcad_chain_read_energies(self.h)
+
+    def min_state(self):
+        """(state, energy, sweep) of the lowest-energy state tracked."""
+        return pcad_chain_read_min_state(self.h, self.H, self.W)
+
     def sample(self) -> np.ndarray:
         return pcad_chain_read_sample(self.h, self.H, self.W)
 
@@ -518,6 +537,40 @@ def pcad_server_destroy(h):
 def pcad_chain_set_blocking(h, k: int):
     """k sweeps per launch on TMA-loaded shared-memory tiles (0: unblocked)."""
     _check("pcad_chain_set_blocking", lib().pcad_chain_set_blocking(h, int(k)))
+
+
+def pcad_chain_energy(h):
+    """Posterior energy H of the chain's current sample and its integer sums."""
+    e = ctypes.c_double()
+    p, d = ctypes.c_uint64(), ctypes.c_uint64()
+    _check("pcad_chain_energy", lib().pcad_chain_energy(h, ctypes.byref(e), ctypes.byref(p),
+                                                        ctypes.byref(d)))
+    return e.value, p.value, d.value
+
+
+def pcad_chain_track_energy(h, capacity: int):
+    _check("pcad_chain_track_energy", lib().pcad_chain_track_energy(h, int(capacity)))
+
+
+def pcad_chain_read_energies(h) -> np.ndarray:
+    n = ctypes.c_int()
+    _check("pcad_chain_read_energies", lib().pcad_chain_read_energies(h, None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.float64)
+    if n.value:
+        _check("pcad_chain_read_energies",
+               lib().pcad_chain_read_energies(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              n.value, ctypes.byref(n)))
+    return out
+
+
+def pcad_chain_read_min_state(h, H: int, W: int):
+    out = np.zeros((H, W), dtype=np.uint8)
+    e = ctypes.c_double()
+    t = ctypes.c_uint64()
+    _check("pcad_chain_read_min_state",
+           lib().pcad_chain_read_min_state(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), W,
+                                           ctypes.byref(e), ctypes.byref(t)))
+    return out, e.value, t.value
 
 
 PCAD_KERNEL_AUTO = 0

@@ -191,6 +191,10 @@ struct pcad_chain {
     CUtensorMap xmap[2];          // TMA descriptors of the two label planes
     CUtensorMap gmap;             // and of the observation
     int *err = nullptr;           // bounded-wait timeout flag (device)
+    unsigned long long *esums = nullptr;   // energy reduction sums (device, 2 x u64)
+    EnergyCoef ecoef{};
+    EnergyTrack track{};          // minimum-energy tracking (trace == nullptr: off)
+    void *track_block = nullptr;
 };
 
 namespace {
@@ -244,6 +248,9 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
             a.xout = ch->x[cur ^ 1];
             CUDA_TRY(tc ? launch_pca_tc(a, ch->err, st) : launch_pca_sweep(a, st));
             cur ^= 1;
+            if (ch->track.trace)
+                CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
+                                       ch->esums, nullptr, ch->track, ch->tdev, a.sweep_off, st));
         } else {
             a.xin = ch->x[cur];
             a.xout = nullptr;
@@ -251,6 +258,9 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
                 a.last_phase = q == ncol - 1;
                 CUDA_TRY(launch_gibbs_phase(a, q, st));
             }
+            if (ch->track.trace)
+                CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
+                                       ch->esums, nullptr, ch->track, ch->tdev, a.sweep_off, st));
         }
     }
     return PCAD_OK;
@@ -344,7 +354,9 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->tdev = (uint32_t *)p;
     ch->fp64 = (unsigned long long *)(p + 8);
     ch->mscratch = (double *)(p + 16);
+    ch->esums = (unsigned long long *)(p + 96);
     ch->err = (int *)(p + 128);
+    ch->ecoef = energy_coef(*m, (long)H * W);
 
     auto cleanup = [&](pcad_status s) {
         cudaFreeAsync(ch->block, ch->stream);
@@ -456,6 +468,24 @@ pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps)
     return PCAD_OK;
 }
 
+namespace {
+
+// Empty the energy trace and forget the minimum (asynchronous).
+pcad_status reset_track(pcad_chain *ch)
+{
+    const double inf = HUGE_VAL;
+    CUDA_TRY(cudaMemsetAsync(ch->track.n, 0, sizeof(unsigned int), ch->stream));
+    CUDA_TRY(cudaMemsetAsync(ch->track.flag, 0, sizeof(int), ch->stream));
+    CUDA_TRY(cudaMemsetAsync(ch->track.best_sweep, 0, sizeof(unsigned long long), ch->stream));
+    CUDA_TRY(cudaMemcpyAsync(ch->track.best, &inf, sizeof(double), cudaMemcpyHostToDevice,
+                             ch->stream));
+    return cudaStreamSynchronize(ch->stream) == cudaSuccess
+               ? PCAD_OK
+               : fail(PCAD_ECUDA, "energy tracking reset failed");
+}
+
+}  // namespace
+
 pcad_status pcad_chain_reset(pcad_chain *ch)
 {
     if (!ch)
@@ -468,6 +498,8 @@ pcad_status pcad_chain_reset(pcad_chain *ch)
     ch->cur = 0;
     ch->t = 0;
     ch->n_acc = 0;
+    if (ch->track.trace)
+        return reset_track(ch);
     return PCAD_OK;
 }
 
@@ -485,6 +517,109 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
             return fail(PCAD_ETIMEOUT, "a bounded wait of the sweep kernel (tile load or MMA "
                                        "completion) gave up");
     }
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_energy(pcad_chain *ch, double *energy, uint64_t *pair_sum,
+                              uint64_t *data_sum)
+{
+    if (!ch || !energy)
+        return fail(PCAD_EINVAL, "chain or energy is NULL");
+    double res[3] = {0.0, 0.0, 0.0};
+    CUDA_TRY(launch_energy(ch->x[ch->cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef, ch->esums,
+                           ch->mscratch, EnergyTrack{}, ch->tdev, 0, ch->stream));
+    CUDA_TRY(cudaMemcpyAsync(res, ch->mscratch, sizeof(res), cudaMemcpyDeviceToHost,
+                             ch->stream));
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    *energy = res[0];
+    if (pair_sum)
+        *pair_sum = (uint64_t)res[1];
+    if (data_sum)
+        *data_sum = (uint64_t)res[2];
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_track_energy(pcad_chain *ch, int capacity)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (capacity < 0)
+        return fail(PCAD_EINVAL, "capacity must be >= 0");
+    if (capacity > 0 && ch->tb_k > 0)
+        return fail(PCAD_ESTATE, "energy tracking needs every sweep's state: no temporal blocking");
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    if (ch->graph) {
+        cudaGraphExecDestroy(ch->graph);
+        ch->graph = nullptr;
+    }
+    if (ch->track_block) {
+        CUDA_TRY(cudaFreeAsync(ch->track_block, ch->stream));
+        ch->track_block = nullptr;
+    }
+    ch->track = EnergyTrack{};
+    if (capacity == 0)
+        return PCAD_OK;
+    const size_t head = 64;   // best, best_sweep, n, flag
+    const size_t trace = align_up((size_t)capacity * sizeof(double), 256);
+    const size_t plane = (size_t)ch->pitch * ch->H;
+    void *blk = nullptr;
+    cudaError_t e = cudaMallocAsync(&blk, head + trace + plane, ch->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PCAD_ENOMEM : PCAD_ECUDA,
+                    "energy tracking allocation: %s", cudaGetErrorString(e));
+    }
+    char *p = (char *)blk;
+    ch->track_block = blk;
+    ch->track.best = (double *)p;
+    ch->track.best_sweep = (unsigned long long *)(p + 8);
+    ch->track.n = (unsigned int *)(p + 16);
+    ch->track.flag = (int *)(p + 20);
+    ch->track.trace = (double *)(p + head);
+    ch->track.cap = capacity;
+    ch->track.xb = (uint8_t *)(p + head + trace);
+    return reset_track(ch);
+}
+
+pcad_status pcad_chain_read_energies(pcad_chain *ch, double *host, int max, int *n)
+{
+    if (!ch || !n || (max > 0 && !host))
+        return fail(PCAD_EINVAL, "chain, host or n is NULL");
+    if (!ch->track.trace) {
+        *n = 0;
+        return fail(PCAD_ESTATE, "energy tracking is off");
+    }
+    unsigned int cnt = 0;
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    CUDA_TRY(cudaMemcpy(&cnt, ch->track.n, sizeof(cnt), cudaMemcpyDeviceToHost));
+    const int k = (int)cnt < max ? (int)cnt : max;
+    if (k > 0)
+        CUDA_TRY(cudaMemcpy(host, ch->track.trace, (size_t)k * sizeof(double),
+                            cudaMemcpyDeviceToHost));
+    *n = (int)cnt;
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_read_min_state(pcad_chain *ch, uint8_t *host_out, int out_pitch,
+                                      double *energy, uint64_t *sweep)
+{
+    if (!ch || !host_out || out_pitch < ch->W)
+        return fail(PCAD_EINVAL, "bad output buffer");
+    if (!ch->track.trace)
+        return fail(PCAD_ESTATE, "energy tracking is off");
+    double best = 0.0;
+    unsigned long long bs = 0;
+    CUDA_TRY(cudaStreamSynchronize(ch->stream));
+    CUDA_TRY(cudaMemcpy(&best, ch->track.best, sizeof(best), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(&bs, ch->track.best_sweep, sizeof(bs), cudaMemcpyDeviceToHost));
+    if (bs == 0)
+        return fail(PCAD_ESTATE, "no sweep has been tracked yet");
+    CUDA_TRY(cudaMemcpy2D(host_out, out_pitch, ch->track.xb, ch->pitch, ch->W, ch->H,
+                          cudaMemcpyDeviceToHost));
+    if (energy)
+        *energy = best;
+    if (sweep)
+        *sweep = bs;
     return PCAD_OK;
 }
 
@@ -515,6 +650,8 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k)
         return fail(PCAD_EINVAL, "sweeps per launch must be 0 (unblocked), 1, 2, 4 or 8");
     if (k > 0 && ch->model.sampler != PCAD_SAMPLER_PCA)
         return fail(PCAD_EINVAL, "temporal blocking applies to the PCA sampler");
+    if (k > 0 && ch->track.trace)
+        return fail(PCAD_ESTATE, "energy tracking needs every sweep's state: no temporal blocking");
     if (k > 0 && !ch->maps_ready) {
         if (!encode_plane_map(&ch->xmap[0], ch->x[0], ch->H, ch->W, ch->pitch) ||
             !encode_plane_map(&ch->xmap[1], ch->x[1], ch->H, ch->W, ch->pitch) ||
@@ -782,6 +919,8 @@ void pcad_chain_destroy(pcad_chain *ch)
     cudaStreamSynchronize(ch->stream);
     if (ch->graph)
         cudaGraphExecDestroy(ch->graph);
+    if (ch->track_block)
+        cudaFreeAsync(ch->track_block, ch->stream);
     cudaFreeAsync(ch->block, ch->stream);
     cudaStreamSynchronize(ch->stream);
     delete ch;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the runtime (capi.cu) and the kernels.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <vector>
@@ -135,6 +136,38 @@ int batch_blocks_per_sm();
 // *err is set when a bounded wait for the tile loads gives up.
 cudaError_t launch_pca_tb(const CUtensorMap &xmap, const CUtensorMap &gmap, const SweepArgs &a,
                           int k, int *err, cudaStream_t s);
+
+// Posterior energy H(x) = pair_c * pair_sum + data term, from the integer
+// sums of energy.cu: data term = data_sum / two_s2 (Gaussian) or
+// lf_same * (n_sites - data_sum) + lf_diff * data_sum (flip).
+struct EnergyCoef {
+    int potts, T, gauss, nbhd;
+    double pair_c;       // -c_P (Potts) or c_T (truncated linear)
+    double two_s2;       // 2 sigma^2
+    double lf_same;      // -ln(1 - p)
+    double lf_diff;      // -ln p
+    unsigned long long n_sites;
+};
+EnergyCoef energy_coef(const pcad_model &m, long n_sites);
+
+// Minimum-energy tracking state (device pointers; trace == nullptr: off).
+struct EnergyTrack {
+    double *trace;                  // H after each tracked sweep
+    int cap;
+    unsigned int *n;                // entries recorded
+    double *best;                   // lowest H so far (+inf initially)
+    unsigned long long *best_sweep; // completed sweeps when it was reached
+    int *flag;                      // this sweep set a new minimum
+    uint8_t *xb;                    // the lowest-energy state (same pitch as x)
+};
+
+// sums (2 x u64, zero on entry, zero again on return) <- integer sums of
+// labelling x; out[0..2] <- H, pair sum, data sum (when out != nullptr); with
+// tracking, record H as the energy after sweep *tdev + sweep_off.
+cudaError_t launch_energy(const uint8_t *x, const uint8_t *g, int H, int W, int pitch,
+                          const EnergyCoef &k, unsigned long long *sums, double *out,
+                          const EnergyTrack &tr, const uint32_t *tdev, uint32_t sweep_off,
+                          cudaStream_t s);
 
 // Tensor-core lazy-PCA sweep (prior sums by tcgen05.mma).  Eligible models:
 // L >= kTcMinLabels and truncation T <= kTcMaxT (the banded window must fit
