@@ -76,7 +76,9 @@ typedef enum {
 } pcad_status;
 
 typedef enum { PCAD_PAIR_POTTS = 0, PCAD_PAIR_TRUNC_LINEAR = 1 } pcad_pair;
-typedef enum { PCAD_NOISE_GAUSS = 0, PCAD_NOISE_FLIP = 1 } pcad_noise;
+/* PCAD_NOISE_NONE: no likelihood (U = 0): the chain samples the prior; used
+ * to synthesise MRF test images from random labels (Section 6). */
+typedef enum { PCAD_NOISE_GAUSS = 0, PCAD_NOISE_FLIP = 1, PCAD_NOISE_NONE = 2 } pcad_noise;
 typedef enum { PCAD_SAMPLER_PCA = 0, PCAD_SAMPLER_GIBBS_CB = 1 } pcad_sampler;
 
 /* Model parameters (Sections 4-5).  pair_coef: Potts reward c_P = 2 beta J or
@@ -154,6 +156,20 @@ typedef enum {
     PCAD_KERNEL_TENSOR = 2
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
+
+/* Change the model's coefficients (pair_coef, sigma, flip_p, inertia) for
+ * the sweeps queued after this call; L, nbhd, pair, pair_T, noise and
+ * sampler must stay (PCAD_EINVAL otherwise).  The state, the accumulator
+ * and the sweep counter carry on.  This is the annealing step of Section 6:
+ * with beta rising, c_P = 2 beta J and lambda = beta q are rescaled while
+ * the likelihood stays (its 1/(2 sigma^2) is not multiplied by beta). */
+pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m);
+
+/* Run a schedule: for each stage k, set models[k] and run sweeps[k] sweeps
+ * (the annealed protocol of Section 6: beta = 1.25 + 0.25 k for 4 stages of
+ * 250 sweeps, with the last sample as the estimate). */
+pcad_status pcad_chain_run_schedule(pcad_chain *ch, const pcad_model *models, const int *sweeps,
+                                    int nstages);
 
 /* Posterior energy of the current sample x (Section 4, Eq.
  * mrf_gauss_noise_posterior_distribution; pi_post ~ exp(-H)):
@@ -268,6 +284,11 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
                               pcad_batch **out);
 /* Advance every chain by nsweeps sweeps (asynchronous). */
 pcad_status pcad_batch_run(pcad_batch *b, int nsweeps);
+
+/* Change chain i's coefficients for the sweeps queued after this call (as
+ * pcad_chain_set_model: L, nbhd, pair, pair_T, noise and sampler stay).
+ * Synchronises the batch's stream. */
+pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m);
 /* Restart every chain from its observation (asynchronous). */
 pcad_status pcad_batch_reset(pcad_batch *b);
 pcad_status pcad_batch_sync(pcad_batch *b);

@@ -32,7 +32,7 @@ _lock = threading.Lock()
 _lib = None
 
 POTTS, TRUNC_LINEAR = 0, 1
-GAUSS, FLIP = 0, 1
+GAUSS, FLIP, NONE = 0, 1, 2
 PCA, GIBBS = 0, 1
 ORDER_ROW, ORDER_COL, ORDER_COLOUR = 0, 1, 2
 

@@ -7,8 +7,8 @@ Eq. mrf_gauss_noise_posterior_distribution) with the per-edge pair weight of
 the single-site conditional (Eq. gibbs_sampler_elementary_step): Potts
 V(s, t) = -c_P 1{s = t}, truncated linear V(s, t) = c_T min(|s - t|, T);
 Gaussian noise U(g, s) = (g - s)^2 / (2 sigma^2), flip noise U = -ln(1 - p)
-when s = g and -ln p otherwise.  A free boundary: pairs leaving the image do
-not exist.
+when s = g and -ln p otherwise, no likelihood (prior only) U = 0.  A free
+boundary: pairs leaving the image do not exist.
 
 Every term is a model coefficient times an integer count, so H is computed
 as (coefficient) x (integer sum): ``energy_terms`` returns the two integer
@@ -21,7 +21,7 @@ import math
 
 import numpy as np
 
-from . import GAUSS, POTTS, _f32
+from . import FLIP, GAUSS, POTTS, _f32
 
 
 def _pairs(x: np.ndarray, nbhd: int):
@@ -46,10 +46,13 @@ def energy_terms(m, g: np.ndarray, x: np.ndarray):
             pair += int(np.count_nonzero(a == b))
         else:
             pair += int(np.minimum(np.abs(a - b), int(d.get("pair_T", 1))).sum())
-    if int(d.get("noise", GAUSS)) == GAUSS:
+    noise = int(d.get("noise", GAUSS))
+    if noise == GAUSS:
         data = int(((G - X) ** 2).sum())
-    else:
+    elif noise == FLIP:
         data = int(np.count_nonzero(G != X))
+    else:   # no likelihood
+        data = 0
     return pair, data
 
 
@@ -58,9 +61,12 @@ def combine(m, n_sites: int, pair: int, data: int) -> float:
     d = m.as_dict() if hasattr(m, "as_dict") else dict(m)
     c = _f32(d.get("pair_coef", 0.0))
     pair_e = (-c if int(d.get("pair", 1)) == POTTS else c) * float(pair)
-    if int(d.get("noise", GAUSS)) == GAUSS:
+    noise = int(d.get("noise", GAUSS))
+    if noise == GAUSS:
         s = _f32(d.get("sigma", 1.0))
         data_e = float(data) / (2.0 * s * s)
+    elif noise != FLIP:
+        data_e = 0.0
     else:
         p = _f32(d.get("flip_p", 0.1))
         data_e = -math.log1p(-p) * float(n_sites - data) - math.log(p) * float(data)

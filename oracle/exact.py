@@ -23,7 +23,7 @@ import itertools
 
 import numpy as np
 
-from . import GAUSS, POTTS, _f32, site_probs
+from . import FLIP, GAUSS, POTTS, _f32, site_probs
 
 _D8 = [(-1, 0), (1, 0), (0, -1), (0, 1), (-1, -1), (-1, 1), (1, -1), (1, 1)]
 
@@ -72,6 +72,8 @@ def data_U(P, g, s):
     s = np.asarray(s, dtype=np.int64)
     if P["noise"] == GAUSS:
         return (np.asarray(g, dtype=np.int64) - s) ** 2 / (2.0 * P["sigma"] * P["sigma"])
+    if P["noise"] != FLIP:   # no likelihood
+        return np.zeros(np.shape(s))
     same = -np.log(1.0 - P["p"])
     diff = -np.log(P["p"])
     return np.where(s == g, same, diff)

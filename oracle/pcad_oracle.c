@@ -54,6 +54,7 @@
 #define ORC_TRUNC_LINEAR 1
 #define ORC_GAUSS 0
 #define ORC_FLIP 1
+#define ORC_NONE 2   /* no likelihood: the prior alone */
 #define ORC_TAG_PCA 0u
 #define ORC_TAG_GIBBS 1u
 #define ORC_NEAR 1e-6
@@ -63,7 +64,7 @@ typedef struct {
     int nbhd;         /* 4 or 8 */
     int pair;         /* ORC_POTTS or ORC_TRUNC_LINEAR */
     int pair_T;       /* truncation T (truncated linear) */
-    int noise;        /* ORC_GAUSS or ORC_FLIP */
+    int noise;        /* ORC_GAUSS, ORC_FLIP or ORC_NONE */
     int pad_;
     double pair_coef; /* c_P (Potts reward) or c_T (slope) */
     double sigma;     /* Gaussian std, label units */
@@ -137,8 +138,10 @@ static void site_energies(const orc_model *m, int g, int xi, const int *nb, int 
         if (m->noise == ORC_GAUSS) {
             int dg = g - s;
             data = a * (double)(dg * dg);
-        } else {
+        } else if (m->noise == ORC_FLIP) {
             data = (s == g) ? u_same : u_diff;
+        } else {
+            data = 0.0;
         }
         double inert = (s != xi) ? lam : 0.0;
         E[s] = (prior + data) + inert;

@@ -19,7 +19,7 @@ _lock = threading.Lock()
 _lib = None
 
 PAIR_POTTS, PAIR_TRUNC_LINEAR = 0, 1
-NOISE_GAUSS, NOISE_FLIP = 0, 1
+NOISE_GAUSS, NOISE_FLIP, NOISE_NONE = 0, 1, 2
 SAMPLER_PCA, SAMPLER_GIBBS_CB = 0, 1
 
 
@@ -100,6 +100,9 @@ def _declare(L):
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
         "pcad_chain_set_kernel": [vp, ctypes.c_int],
         "pcad_chain_energy": [vp, dp, u64p, u64p],
+        "pcad_chain_set_model": [vp, mp],
+        "pcad_chain_run_schedule": [vp, mp, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
+        "pcad_batch_set_model": [vp, ctypes.c_int, mp],
         "pcad_chain_track_energy": [vp, ctypes.c_int],
         "pcad_chain_read_energies": [vp, dp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "pcad_chain_read_min_state": [vp, u8p, ctypes.c_int, dp, u64p],
@@ -325,11 +328,13 @@ class Chain:
             self.h = _handle
             self.H, self.W = _shape
             self.L = None
+            self.sampler = None
             return
         g = _u8(g)
         self.H, self.W = g.shape
         m = as_model(model, sampler)
         self.L = m.L
+        self.sampler = m.sampler
         self.h = pcad_chain_create(g, m, seed, chain_id, burn_in, stream)
 
     @classmethod
@@ -356,6 +361,15 @@ class Chain:
 
     def set_kernel(self, kind: int):
         pcad_chain_set_kernel(self.h, kind)
+        return self
+
+    def set_model(self, model):
+        """New coefficients; the chain's sampler is kept."""
+        pcad_chain_set_model(self.h, as_model(model, self.sampler))
+        return self
+
+    def run_schedule(self, models, sweeps):
+        pcad_chain_run_schedule(self.h, [as_model(m, self.sampler) for m in models], sweeps)
         return self
 
     def energy(self):
@@ -537,6 +551,27 @@ def pcad_server_destroy(h):
 def pcad_chain_set_blocking(h, k: int):
     """k sweeps per launch on TMA-loaded shared-memory tiles (0: unblocked)."""
     _check("pcad_chain_set_blocking", lib().pcad_chain_set_blocking(h, int(k)))
+
+
+def pcad_chain_set_model(h, model):
+    """New coefficients (annealing); the model's structure must stay."""
+    m = as_model(model)
+    _check("pcad_chain_set_model", lib().pcad_chain_set_model(h, ctypes.byref(m)))
+
+
+def pcad_chain_run_schedule(h, models, sweeps):
+    """For each stage: set models[k], run sweeps[k] sweeps."""
+    n = len(models)
+    if len(sweeps) != n:
+        raise ValueError("one sweep count per model")
+    arr = (PcadModel * n)(*[as_model(m) for m in models])
+    sw = (ctypes.c_int * n)(*[int(k) for k in sweeps])
+    _check("pcad_chain_run_schedule", lib().pcad_chain_run_schedule(h, arr, sw, n))
+
+
+def pcad_batch_set_model(h, i: int, model):
+    m = as_model(model)
+    _check("pcad_batch_set_model", lib().pcad_batch_set_model(h, int(i), ctypes.byref(m)))
 
 
 def pcad_chain_energy(h):

@@ -461,6 +461,41 @@ pcad_status pcad_batch_run(pcad_batch *b, int nsweeps)
     return batch_run_sweeps(b, nsweeps);
 }
 
+pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
+{
+    if (!b || i < 0 || i >= b->n)
+        return set_error(PCAD_EINVAL, "bad batch or chain index");
+    pcad_status st = check_model(m);
+    if (st != PCAD_OK)
+        return st;
+    const pcad_model &o = b->jobs[i].model;
+    const int To = o.pair == PCAD_PAIR_POTTS ? 1 : o.pair_T;
+    const int Tn = m->pair == PCAD_PAIR_POTTS ? 1 : m->pair_T;
+    if (m->L != o.L || m->nbhd != o.nbhd || m->pair != o.pair || Tn != To ||
+        m->noise != o.noise || m->sampler != o.sampler)
+        return set_error(PCAD_EINVAL, "set_model changes coefficients only (L, nbhd, pair, "
+                                      "pair_T, noise and sampler stay)");
+    double ta64[511];
+    std::vector<double> pr64;
+    DevModel dm{};
+    model_tables(*m, ta64, pr64, dm);
+    char *base = (char *)b->block;
+    const SlotMem &sm = b->mem[i];
+    // stream-ordered: sweeps queued before use the old model; the launches
+    // read the descriptor from device memory, so captured graphs stay valid
+    B_TRY(cudaMemcpyAsync(base + sm.ta, ta64, sizeof(ta64), cudaMemcpyHostToDevice, b->stream));
+    B_TRY(cudaMemcpyAsync(base + sm.pr, pr64.data(), pr64.size() * sizeof(double),
+                          cudaMemcpyHostToDevice, b->stream));
+    dm.ta64 = (const double *)(base + sm.ta);
+    dm.pr64 = (const double *)(base + sm.pr);
+    b->desc[i].m = dm;
+    B_TRY(cudaMemcpyAsync(&b->d_slots[i], &b->desc[i], sizeof(SlotDesc), cudaMemcpyHostToDevice,
+                          b->stream));
+    B_TRY(cudaStreamSynchronize(b->stream));   // the host copies must outlive the transfers
+    b->jobs[i].model = *m;
+    return PCAD_OK;
+}
+
 pcad_status pcad_batch_reset(pcad_batch *b)
 {
     if (!b)

@@ -58,7 +58,8 @@ pcad_status validate_model(const pcad_model *m)
         return fail(PCAD_EINVAL, "nbhd=%d must be 4 or 8", m->nbhd);
     if (m->pair != PCAD_PAIR_POTTS && m->pair != PCAD_PAIR_TRUNC_LINEAR)
         return fail(PCAD_EINVAL, "unknown pair potential %d", m->pair);
-    if (m->noise != PCAD_NOISE_GAUSS && m->noise != PCAD_NOISE_FLIP)
+    if (m->noise != PCAD_NOISE_GAUSS && m->noise != PCAD_NOISE_FLIP &&
+        m->noise != PCAD_NOISE_NONE)
         return fail(PCAD_EINVAL, "unknown noise model %d", m->noise);
     if (m->sampler != PCAD_SAMPLER_PCA && m->sampler != PCAD_SAMPLER_GIBBS_CB)
         return fail(PCAD_EINVAL, "unknown sampler %d", m->sampler);
@@ -73,7 +74,7 @@ pcad_status validate_model(const pcad_model *m)
     if (m->noise == PCAD_NOISE_GAUSS) {
         if (!(m->sigma > 0.0f) || !std::isfinite(m->sigma))
             return fail(PCAD_EINVAL, "sigma must be positive and finite");
-    } else {
+    } else if (m->noise == PCAD_NOISE_FLIP) {
         if (m->L != 2)
             return fail(PCAD_EINVAL, "flip noise needs L=2");
         if (!(m->flip_p > 0.0f && m->flip_p < 1.0f))
@@ -105,9 +106,11 @@ void build_tables(const pcad_model &m, ModelTables &t)
             const double s = (double)m.sigma;
             const double a = 1.0 / (2.0 * s * s);
             v = std::exp(-(a * (double)(d * d)));
-        } else {
+        } else if (m.noise == PCAD_NOISE_FLIP) {
             const double p = (double)m.flip_p;
             v = d == 0 ? 1.0 : (std::abs(d) == 1 ? p / (1.0 - p) : 0.0);
+        } else {
+            v = 1.0;   // no likelihood
         }
         t.ta64[d + 255] = v;
     }
@@ -125,9 +128,11 @@ void build_tables(const pcad_model &m, ModelTables &t)
     if (m.noise == PCAD_NOISE_GAUSS) {
         const double s = (double)m.sigma;
         d.alpha = (float)(-log2e / (2.0 * s * s));
-    } else {
+    } else if (m.noise == PCAD_NOISE_FLIP) {
         const double p = (double)m.flip_p;
         d.alpha = (float)(-log2e * std::log((1.0 - p) / p));
+    } else {
+        d.alpha = 0.0f;
     }
     d.Tf = (float)T;
     d.em1 = (float)std::expm1(lam);
@@ -516,6 +521,68 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
         if (e)
             return fail(PCAD_ETIMEOUT, "a bounded wait of the sweep kernel (tile load or MMA "
                                        "completion) gave up");
+    }
+    return PCAD_OK;
+}
+
+namespace {
+
+// set_model may change coefficients only: the state layout, the tables' sizes
+// and the kernels chosen stay as they are.
+bool same_structure(const pcad_model &a, const pcad_model &b)
+{
+    const int Ta = a.pair == PCAD_PAIR_POTTS ? 1 : a.pair_T;
+    const int Tb = b.pair == PCAD_PAIR_POTTS ? 1 : b.pair_T;
+    return a.L == b.L && a.nbhd == b.nbhd && a.pair == b.pair && Ta == Tb &&
+           a.noise == b.noise && a.sampler == b.sampler;
+}
+
+}  // namespace
+
+pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    pcad_status st = validate_model(m);
+    if (st != PCAD_OK)
+        return st;
+    if (!same_structure(*m, ch->model))
+        return fail(PCAD_EINVAL, "set_model changes coefficients only (L, nbhd, pair, pair_T, "
+                                 "noise and sampler stay)");
+    ModelTables tabs;
+    build_tables(*m, tabs);
+    // stream-ordered: sweeps queued before use the old tables
+    CUDA_TRY(cudaMemcpyAsync(ch->ta64, tabs.ta64, sizeof(tabs.ta64), cudaMemcpyHostToDevice,
+                             ch->stream));
+    CUDA_TRY(cudaMemcpyAsync(ch->pr64, tabs.pr64.data(), tabs.pr64.size() * sizeof(double),
+                             cudaMemcpyHostToDevice, ch->stream));
+    if (ch->graph) {   // captured sweeps hold the old coefficients
+        CUDA_TRY(cudaStreamSynchronize(ch->stream));
+        cudaGraphExecDestroy(ch->graph);
+        ch->graph = nullptr;
+    }
+    ch->model = *m;
+    ch->dm = tabs.dm;
+    ch->dm.ta64 = ch->ta64;
+    ch->dm.pr64 = ch->pr64;
+    ch->ecoef = energy_coef(*m, (long)ch->H * ch->W);
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_run_schedule(pcad_chain *ch, const pcad_model *models, const int *sweeps,
+                                    int nstages)
+{
+    if (!ch || nstages < 0 || (nstages > 0 && (!models || !sweeps)))
+        return fail(PCAD_EINVAL, "bad schedule");
+    for (int k = 0; k < nstages; ++k)
+        if (sweeps[k] < 0)
+            return fail(PCAD_EINVAL, "stage %d has a negative sweep count", k);
+    for (int k = 0; k < nstages; ++k) {
+        pcad_status st = pcad_chain_set_model(ch, &models[k]);
+        if (st == PCAD_OK)
+            st = pcad_chain_run(ch, sweeps[k]);
+        if (st != PCAD_OK)
+            return st;
     }
     return PCAD_OK;
 }

@@ -9,7 +9,8 @@
 //   pair sum: Potts -> pairs with equal labels (V = -c_P each),
 //             truncated linear -> sum of min(|x_i - x_j|, T) (V = c_T each);
 //   data sum: Gaussian -> sum of (g_i - x_i)^2 (U = that / (2 sigma^2)),
-//             flip -> sites with x_i != g_i (U = -ln p there, -ln(1 - p) elsewhere).
+//             flip -> sites with x_i != g_i (U = -ln p there, -ln(1 - p) elsewhere);
+//             none (prior only) -> 0.
 // The sums are reduced exactly in 64-bit integers; H is combined from them
 // in FP64 by one thread.  Pairs are counted once: right and down neighbours
 // (and the two lower diagonals for the 8-neighbourhood), free boundary.
@@ -45,7 +46,8 @@ __global__ void __launch_bounds__(kEThreads) energy_sums_kernel(const uint8_t *_
                 pair += k.potts ? (xi == xj ? 1u : 0u) : (uint32_t)min(abs(xi - xj), k.T);
             }
         }
-        data += k.gauss ? (uint32_t)((gi - xi) * (gi - xi)) : (gi != xi ? 1u : 0u);
+        if (!k.none)
+            data += k.gauss ? (uint32_t)((gi - xi) * (gi - xi)) : (gi != xi ? 1u : 0u);
     }
     // block reduction in 64 bits, one atomic per block and sum
     unsigned long long p64 = pair, d64 = data;
@@ -83,7 +85,7 @@ __global__ void energy_finish_kernel(unsigned long long *sums, EnergyCoef k, dou
     double e = __dmul_rn(k.pair_c, pair);
     if (k.gauss)
         e = __dadd_rn(e, __ddiv_rn(data, k.two_s2));
-    else
+    else if (!k.none)
         e = __dadd_rn(e, __dadd_rn(__dmul_rn(k.lf_same, __dsub_rn((double)k.n_sites, data)),
                                    __dmul_rn(k.lf_diff, data)));
     if (out) {   // H and the two sums (exact in FP64: both are < 2^53)
@@ -136,10 +138,11 @@ EnergyCoef energy_coef(const pcad_model &m, long n_sites)
     k.potts = m.pair == PCAD_PAIR_POTTS;
     k.T = m.pair == PCAD_PAIR_POTTS ? 1 : m.pair_T;
     k.gauss = m.noise == PCAD_NOISE_GAUSS;
+    k.none = m.noise == PCAD_NOISE_NONE;
     k.nbhd = m.nbhd;
     k.pair_c = (k.potts ? -1.0 : 1.0) * (double)m.pair_coef;
     k.two_s2 = 2.0 * (double)m.sigma * (double)m.sigma;
-    if (!k.gauss) {
+    if (m.noise == PCAD_NOISE_FLIP) {
         const double p = (double)m.flip_p;
         k.lf_same = -std::log1p(-p);
         k.lf_diff = -std::log(p);

@@ -138,10 +138,11 @@ cudaError_t launch_pca_tb(const CUtensorMap &xmap, const CUtensorMap &gmap, cons
                           int k, int *err, cudaStream_t s);
 
 // Posterior energy H(x) = pair_c * pair_sum + data term, from the integer
-// sums of energy.cu: data term = data_sum / two_s2 (Gaussian) or
-// lf_same * (n_sites - data_sum) + lf_diff * data_sum (flip).
+// sums of energy.cu: data term = data_sum / two_s2 (Gaussian),
+// lf_same * (n_sites - data_sum) + lf_diff * data_sum (flip) or 0 (none).
 struct EnergyCoef {
     int potts, T, gauss, nbhd;
+    int none;            // no likelihood: data term 0
     double pair_c;       // -c_P (Potts) or c_T (truncated linear)
     double two_s2;       // 2 sigma^2
     double lf_same;      // -ln(1 - p)

@@ -40,6 +40,7 @@ PAIR_POTTS = 0
 PAIR_TRUNC_LINEAR = 1
 NOISE_GAUSS = 0
 NOISE_FLIP = 1
+NOISE_NONE = 2   # prior only (synthetic MRF images)
 SAMPLER_PCA = 0
 SAMPLER_GIBBS = 1
 
