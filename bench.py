@@ -82,10 +82,12 @@ def _args():
     p.add_argument("--sampler", type=int, default=0, help="profile case: 0 PCA, 1 Gibbs")
     p.add_argument("--blocking", type=int, default=0,
                    help="profile case: sweeps per TMA-tiled launch (0: unblocked)")
-    p.add_argument("--workload", default="chain", choices=["chain", "batch", "serve", "blocking"],
+    p.add_argument("--workload", default="chain",
+                   choices=["chain", "batch", "serve", "blocking", "protocol"],
                    help="chain: the 512x512 L=256 chain (default); batch: uneven images x 4 "
                         "chains in one persistent launch vs one chain per launch; serve: "
-                        "Poisson request stream through the continuous-batching server")
+                        "Poisson request stream through the continuous-batching server; "
+                        "protocol: the paper's annealed runs on MRF images and the q grid")
     p.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor"],
                    help="kernel of the unblocked PCA sweep (chain workload and profile case): "
                         "auto = cuda_core; tensor = prior sums by tcgen05.mma")
@@ -438,6 +440,85 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+PROTO_CASES = ((5, 0.25), (9, 0.2), (33, 0.1))   # (levels, sigma in intensity units)
+
+
+def run_protocol(a):
+    """The paper's restoration protocol on synthetic MRF images (its own test
+    images are not public): for each (levels, sigma), a 256 x 256 image drawn
+    from the Potts prior (J = 1/3, beta 1.5, 200 Gibbs sweeps from random
+    levels), Gaussian noise, then annealed 4-colour Gibbs and annealed lazy
+    PCA (beta 1.25 + 0.25 per 250 sweeps, 1000 sweeps, q = 0.46, last sample)
+    over 3 runs each: PSNR / SSIM and the time of one 1000-sweep run.  Then
+    the q grid (14 values x 10 runs, one batch) on the 9-level image, with
+    the mean PSNR per q and the count of positive second differences
+    (0 = concave)."""
+    import numpy as np
+    import torch
+
+    import paper_2507_14869_gb300 as pc
+    from paper_2507_14869_gb300 import protocol as pr
+    from pcad_inputs import gaussian_noise, random_lattice
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    side, J, q, runs = 256, 1.0 / 3.0, 0.46, 3
+    cases = []
+    grid_case = None
+    with ClockSampler(0) as clk:
+        for L, sigma in PROTO_CASES:
+            clean = pr.mrf_image(random_lattice(100 + L, side, side, L), L, J=J, beta=1.5,
+                                 sweeps=200, seed=L, stream=stream)
+            noisy = gaussian_noise(200 + L, clean, sigma * (L - 1), L)
+            row = {"levels": L, "sigma": sigma, "noisy_psnr_db": pr.metrics(noisy, clean, L)[0]}
+            for name, sampler in (("gibbs", pc.SAMPLER_GIBBS_CB), ("pca", pc.SAMPLER_PCA)):
+                ms, sw = pr.schedule(L, J, q, sigma, sampler=sampler)
+                res, times = [], []
+                for r in range(runs + 1):   # run 0 warms up
+                    with pc.Chain(noisy, ms[0], seed=7, chain_id=r, burn_in=sum(sw),
+                                  stream=stream) as ch:
+                        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                        ev[0].record(stream)
+                        ch.run_schedule(ms, sw)
+                        ev[1].record(stream)
+                        torch.cuda.synchronize()
+                        if r > 0:
+                            times.append(ev[0].elapsed_time(ev[1]))
+                            res.append(pr.metrics(ch.sample(), clean, L))
+                row[name] = {"psnr_db": float(np.mean([x[0] for x in res])),
+                             "ssim": float(np.mean([x[1] for x in res])),
+                             "ms_per_run": float(np.mean(times)),
+                             "site_updates_per_s": side * side * sum(sw) / (np.mean(times) / 1e3)}
+            cases.append(row)
+            if L == 9:
+                grid_case = (clean, noisy, L, sigma)
+        clean, noisy, L, sigma = grid_case
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        grid = pr.q_grid(noisy, clean, L, J, sigma, seed=11, runs=10, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        t_grid = ev[0].elapsed_time(ev[1]) / 1e3
+    curve = [float(np.mean([x[0] for x in grid[qq]])) for qq in pr.Q_GRID]
+    chains = len(pr.Q_GRID) * 10
+    line = {"metric": "site-updates/s (annealed lazy PCA, paper protocol)",
+            "value": float(np.mean([c["pca"]["site_updates_per_s"] for c in cases])),
+            "unit": "site-updates/s", "n_gpus": 1, "steps": runs, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic MRF images (Potts prior samples; the paper's images are not "
+                    "public)",
+            "config": {"workload": f"{side}x{side} MRF images, levels/sigma {PROTO_CASES}, "
+                                   "8-nbhd Potts J=1/3, annealed beta 1.25+0.25/250 sweeps, "
+                                   "1000 sweeps, q=0.46, last sample"},
+            "cases": cases,
+            "q_grid": {"levels": 9, "sigma": 0.2, "q": list(pr.Q_GRID), "runs": 10,
+                       "mean_psnr_db": curve, "concavity": pr.concavity(curve),
+                       "chains": chains, "s_total": t_grid,
+                       "site_updates_per_s": chains * side * side * 1000 / t_grid},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def _serve_stream(pc, sv, reqs, slice_sweeps=16):
     """Drive the server with arrivals at their Poisson times; returns
     (latencies s, makespan s, results {index: (sample, mean)})."""
@@ -640,6 +721,8 @@ def main():
         run_serve(a)
     elif a.workload == "blocking":
         run_blocking(a)
+    elif a.workload == "protocol":
+        run_protocol(a)
     else:
         run_ours(a)
 
