@@ -39,7 +39,7 @@ ORDER_ROW, ORDER_COL, ORDER_COLOUR = 0, 1, 2
 
 class OrcModel(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("nbhd", ctypes.c_int), ("pair", ctypes.c_int),
-                ("pair_T", ctypes.c_int), ("noise", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("pair_T", ctypes.c_int), ("noise", ctypes.c_int), ("inertia_norm", ctypes.c_int),
                 ("pair_coef", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("flip_p", ctypes.c_double), ("inertia", ctypes.c_double)]
 
@@ -123,7 +123,8 @@ def model_struct(m) -> OrcModel:
     d = m.as_dict() if hasattr(m, "as_dict") else dict(m)
     s = OrcModel()
     s.L = int(d["L"]); s.nbhd = int(d.get("nbhd", 4)); s.pair = int(d.get("pair", 1))
-    s.pair_T = int(d.get("pair_T", 1)); s.noise = int(d.get("noise", 0)); s.pad_ = 0
+    s.pair_T = int(d.get("pair_T", 1)); s.noise = int(d.get("noise", 0))
+    s.inertia_norm = int(d.get("inertia_norm", 0))
     s.pair_coef = _f32(d.get("pair_coef", 0.0)); s.sigma = _f32(d.get("sigma", 1.0))
     s.flip_p = _f32(d.get("flip_p", 0.1)); s.inertia = _f32(d.get("inertia", 0.0))
     return s

@@ -11,7 +11,9 @@ per-site conditional in ``pcad_oracle.c``:
   * the lazy-PCA pair Hamiltonian, symmetric lift of Section 5.2 with the
     L0 inertia of Section 3:
     H~(x,w) = sum_i sum_{j in N(i)} V(w_i, x_j) + sum_i [U_i(w_i) + U_i(x_i)]
-              + lambda sum_i 1{w_i != x_i},
+              + lambda sum_i rho(w_i, x_i),
+    with the inertia price rho = 1{w != x} (L0) or (|w - x| / (L - 1))^p for
+    the L1 / L2 norms on intensities (Section 3),
     its transition matrix P(x,w) = exp(-H~(x,w)) / Z_x
     (Eq. double_hamiltonian_pca_general_form) and stationary measure
     pi~(x) = Z_x / Z (Eq. symm_ham_pca_stationary_measure);
@@ -33,7 +35,18 @@ def _params(m):
     return dict(L=int(d["L"]), nbhd=int(d.get("nbhd", 4)), pair=int(d.get("pair", 1)),
                 T=int(d.get("pair_T", 1)), noise=int(d.get("noise", 0)),
                 c=_f32(d.get("pair_coef", 0.0)), sigma=_f32(d.get("sigma", 1.0)),
-                p=_f32(d.get("flip_p", 0.1)), lam=_f32(d.get("inertia", 0.0)))
+                p=_f32(d.get("flip_p", 0.1)), lam=_f32(d.get("inertia", 0.0)),
+                norm=int(d.get("inertia_norm", 0)))
+
+
+def inertia_price(P, a, b):
+    """rho(a, b): 1{a != b}, or (|a - b| / (L - 1))^p for p = inertia_norm."""
+    a = np.asarray(a, dtype=np.int64)
+    b = np.asarray(b, dtype=np.int64)
+    if P["norm"] == 0:
+        return (a != b).astype(np.float64)
+    d = np.abs(a - b) / float(P["L"] - 1)
+    return d if P["norm"] == 1 else d * d
 
 
 def states(n: int, L: int) -> np.ndarray:
@@ -95,7 +108,7 @@ def posterior_logweights(m, g: np.ndarray) -> np.ndarray:
 
 def _site_energy_all(P, X, nb, gf, i, s):
     """E_i(s | x) for every state x (rows of X): the lazy-PCA conditional energy."""
-    e = data_U(P, gf[i], s) + P["lam"] * (X[:, i] != s)
+    e = data_U(P, gf[i], s) + P["lam"] * inertia_price(P, X[:, i], s)
     for j in nb[i]:
         e = e + pair_V(P, s, X[:, j])
     return e
@@ -132,7 +145,7 @@ def pair_hamiltonian(m, g: np.ndarray) -> np.ndarray:
         for j in nb[i]:
             Ht += pair_V(P, Wc[..., i], Xr[..., j])
         Ht += data_U(P, gf[i], Wc[..., i]) + data_U(P, gf[i], Xr[..., i])
-        Ht += P["lam"] * (Wc[..., i] != Xr[..., i])
+        Ht += P["lam"] * inertia_price(P, Wc[..., i], Xr[..., i])
     return Ht
 
 
@@ -186,14 +199,21 @@ def j0_gibbs_marginal(m, g_i: int) -> np.ndarray:
 
 def j0_pca_marginal(m, g_i: int) -> np.ndarray:
     """J = 0 lazy PCA: independent single-site chains with transition
-    P(x, s) ~ exp(-U(s) - lambda 1{s != x}); stationary law
-    pi(x) ~ exp(-U(x)) [exp(-lambda) Z_U + (1 - exp(-lambda)) exp(-U(x))]."""
+    P(x, s) ~ exp(-U(s) - lambda rho(s, x)), rho symmetric; detailed balance
+    gives pi(x) ~ exp(-U(x)) sum_s exp(-U(s) - lambda rho(s, x)), which for the
+    L0 price is exp(-U(x)) [exp(-lambda) Z_U + (1 - exp(-lambda)) exp(-U(x))]."""
     P = _params(m)
-    u = data_U(P, g_i, np.arange(P["L"]))
+    L = P["L"]
+    u = data_U(P, g_i, np.arange(L))
     eu = np.exp(-(u - u.min()))
-    ZU = eu.sum()
-    el = np.exp(-P["lam"])
-    w = eu * (el * ZU + (1.0 - el) * eu)
+    if P["norm"] == 0:
+        ZU = eu.sum()
+        el = np.exp(-P["lam"])
+        w = eu * (el * ZU + (1.0 - el) * eu)
+    else:
+        s = np.arange(L)
+        R = inertia_price(P, s[:, None], s[None, :])
+        w = eu * (np.exp(-P["lam"] * R) @ eu)
     return w / w.sum()
 
 
@@ -205,7 +225,7 @@ def single_site_chain_stationary(m, g_i: int) -> np.ndarray:
     u = data_U(P, g_i, np.arange(L))
     K = np.zeros((L, L))
     for x in range(L):
-        e = u + P["lam"] * (np.arange(L) != x)
+        e = u + P["lam"] * inertia_price(P, np.arange(L), x)
         w = np.exp(-(e - e.min()))
         K[x] = w / w.sum()
     vals, vecs = np.linalg.eig(K.T)

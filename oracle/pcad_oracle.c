@@ -65,7 +65,7 @@ typedef struct {
     int pair;         /* ORC_POTTS or ORC_TRUNC_LINEAR */
     int pair_T;       /* truncation T (truncated linear) */
     int noise;        /* ORC_GAUSS, ORC_FLIP or ORC_NONE */
-    int pad_;
+    int inertia_norm; /* 0: lambda 1{s != x_i}; p = 1, 2: lambda (|s - x_i| / (L-1))^p */
     double pair_coef; /* c_P (Potts reward) or c_T (slope) */
     double sigma;     /* Gaussian std, label units */
     double flip_p;    /* flip probability */
@@ -112,7 +112,10 @@ double orc_uniform(uint64_t seed, uint32_t chain, uint32_t tag, uint32_t sweep,
 
 /* Energies E_i(s) for s = 0..L-1 (eq. gibbs_sampler_elementary_step with the
  * lazy-PCA inertial term of Section 5.2).  nb holds the labels of the nnb
- * neighbours that exist (free boundary).  lam is the inertia (0 for Gibbs). */
+ * neighbours that exist (free boundary).  lam is the inertia (0 for Gibbs):
+ * the L0 price lam 1{s != x_i} of Section 3, or with inertia_norm p = 1, 2
+ * the Lp price lam (|s - x_i| / (L - 1))^p on intensities (Section 3, the
+ * norms proportional to the size of the change). */
 static void site_energies(const orc_model *m, int g, int xi, const int *nb, int nnb,
                           double lam, double *E)
 {
@@ -143,7 +146,13 @@ static void site_energies(const orc_model *m, int g, int xi, const int *nb, int 
         } else {
             data = 0.0;
         }
-        double inert = (s != xi) ? lam : 0.0;
+        double inert;
+        if (m->inertia_norm == 0) {
+            inert = (s != xi) ? lam : 0.0;
+        } else {
+            const double d = (double)abs(s - xi) / (double)(m->L - 1);
+            inert = lam * (m->inertia_norm == 1 ? d : d * d);
+        }
         E[s] = (prior + data) + inert;
     }
 }

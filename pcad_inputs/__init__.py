@@ -64,12 +64,14 @@ class Model:
     flip_p: float = 0.1
     inertia: float = 2.0
     sampler: int = SAMPLER_PCA
+    inertia_norm: int = 0   # 0: lambda 1{s != x_i}; 1, 2: lambda (|s - x_i| / (L-1))^p
 
     def as_dict(self) -> dict:
         return dict(L=self.L, nbhd=self.nbhd, pair=self.pair,
                     pair_coef=self.pair_coef, pair_T=self.pair_T,
                     noise=self.noise, sigma=self.sigma, flip_p=self.flip_p,
-                    inertia=self.inertia, sampler=self.sampler)
+                    inertia=self.inertia, sampler=self.sampler,
+                    inertia_norm=self.inertia_norm)
 
 
 def _rng(seed: int) -> np.random.Generator:

@@ -31,6 +31,14 @@ def _models():
                                    sigma=0.8, inertia=0.9), (3, 3)),
         ("potts_gauss_L3_2x2_8", Model(L=3, nbhd=8, pair=POTTS, pair_coef=0.7,
                                        noise=GAUSS, sigma=1.0, inertia=0.4), (2, 2)),
+        # L1 / L2 inertia norms on intensities (Section 3)
+        ("tl_gauss_L4_T2_1x3_l1", Model(L=4, nbhd=4, pair=TL, pair_coef=0.6, pair_T=2,
+                                        noise=GAUSS, sigma=1.3, inertia=1.7, inertia_norm=1),
+         (1, 3)),
+        ("tl_gauss_L3_2x2_l2", Model(L=3, nbhd=4, pair=TL, pair_coef=0.8, pair_T=1,
+                                     noise=GAUSS, sigma=0.9, inertia=2.5, inertia_norm=2), (2, 2)),
+        ("potts_gauss_L5_1x3_l2_8", Model(L=5, nbhd=8, pair=POTTS, pair_coef=0.7, noise=GAUSS,
+                                          sigma=1.1, inertia=3.0, inertia_norm=2), (1, 3)),
     ]
 
 
@@ -114,6 +122,31 @@ def test_j0_closed_form_matches_single_site_chain(orc, L, sigma, lam):
         cf = exact.j0_pca_marginal(m, gi)
         ev = exact.single_site_chain_stationary(m, gi)
         np.testing.assert_allclose(cf, ev, rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("L,sigma,lam,norm", [(16, 2.0, 1.5, 1), (16, 2.0, 3.0, 2),
+                                               (256, 20.0, 2.0, 1), (5, 0.7, 4.0, 2)])
+def test_j0_closed_form_matches_single_site_chain_norms(orc, L, sigma, lam, norm):
+    m = Model(L=L, nbhd=4, pair=TL, pair_coef=0.0, pair_T=1, noise=GAUSS, sigma=sigma,
+              inertia=lam, inertia_norm=norm)
+    for gi in (0, L // 3, L - 1):
+        cf = exact.j0_pca_marginal(m, gi)
+        ev = exact.single_site_chain_stationary(m, gi)
+        np.testing.assert_allclose(cf, ev, rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("norm,E", [(1, (3.0, 1.5, 3.0)), (2, (3.0, 1.0, 3.0))])
+def test_hand_worked_norm_conditional(orc, norm, E):
+    """L = 3, truncated linear c = 0.5, T = 1, Gaussian sigma = 1, lambda = 2,
+    g = 2, x_i = 0, two neighbours at label 1:
+      s = 0: prior 0.5 (1 + 1) = 1, data (2-0)^2/2 = 2, inertia 0
+      s = 1: prior 0, data 1/2, inertia 2 (1/2)^p = 1 (p = 1) or 1/2 (p = 2)
+      s = 2: prior 1, data 0, inertia 2 (2/2)^p = 2."""
+    m = Model(L=3, nbhd=4, pair=TL, pair_coef=0.5, pair_T=1, noise=GAUSS, sigma=1.0,
+              inertia=2.0, inertia_norm=norm)
+    p = orc.site_probs(m, 2, 0, [1, 1], 2.0)
+    w = np.exp(-np.array(E))
+    np.testing.assert_allclose(p, w / w.sum(), rtol=1e-13)
 
 
 def test_j0_conditional_is_data_term_only(orc):
