@@ -84,7 +84,11 @@ typedef enum { PCAD_SAMPLER_PCA = 0, PCAD_SAMPLER_GIBBS_CB = 1 } pcad_sampler;
 /* Model parameters (Sections 4-5).  pair_coef: Potts reward c_P = 2 beta J or
  * truncated-linear slope c_T; pair_T: truncation (ignored for Potts); sigma:
  * Gaussian std in label units; flip_p: flip probability; inertia: lambda =
- * beta q (0 gives the naive synchronous update; ignored by Gibbs). */
+ * beta q (0 gives the naive synchronous update; ignored by Gibbs);
+ * inertia_norm: the inertia price of changing label x_i to s (Section 3) --
+ * 0: lambda 1{s != x_i} (L0), 1 or 2: lambda (|s - x_i| / (L - 1))^p on
+ * intensities (L1 / L2).  The norms run on the single-chain sweep kernel
+ * (not with temporal blocking, batches or the tensor-core kernel). */
 typedef struct {
     int L;
     int nbhd;
@@ -96,6 +100,7 @@ typedef struct {
     float flip_p;
     float inertia;
     int sampler;     /* pcad_sampler */
+    int inertia_norm; /* 0 (L0), 1 (L1) or 2 (L2) */
 } pcad_model;
 
 typedef struct pcad_chain pcad_chain;

@@ -38,7 +38,7 @@ class PcadModel(ctypes.Structure):
                 ("pair_coef", ctypes.c_float), ("pair_T", ctypes.c_int),
                 ("noise", ctypes.c_int), ("sigma", ctypes.c_float),
                 ("flip_p", ctypes.c_float), ("inertia", ctypes.c_float),
-                ("sampler", ctypes.c_int)]
+                ("sampler", ctypes.c_int), ("inertia_norm", ctypes.c_int)]
 
 
 class PcadJob(ctypes.Structure):
@@ -59,7 +59,8 @@ def as_model(m, sampler=None) -> PcadModel:
                         pair_coef=float(d.get("pair_coef", 0.0)), pair_T=int(d.get("pair_T", 1)),
                         noise=int(d.get("noise", 0)), sigma=float(d.get("sigma", 1.0)),
                         flip_p=float(d.get("flip_p", 0.1)), inertia=float(d.get("inertia", 0.0)),
-                        sampler=int(d.get("sampler", 0)))
+                        sampler=int(d.get("sampler", 0)),
+                        inertia_norm=int(d.get("inertia_norm", 0)))
     if sampler is not None:
         out.sampler = int(sampler)
     return out

@@ -58,6 +58,8 @@ pcad_status check_job(const pcad_job &j)
         return st;
     if (j.model.sampler != PCAD_SAMPLER_PCA)
         return set_error(PCAD_EINVAL, "batches and the server run the PCA sampler");
+    if (j.model.inertia_norm != 0 && j.model.L > 2 && j.model.inertia > 0.0f)
+        return set_error(PCAD_EINVAL, "batches and the server run the L0 inertia price only");
     return PCAD_OK;
 }
 
@@ -472,7 +474,7 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
     const int To = o.pair == PCAD_PAIR_POTTS ? 1 : o.pair_T;
     const int Tn = m->pair == PCAD_PAIR_POTTS ? 1 : m->pair_T;
     if (m->L != o.L || m->nbhd != o.nbhd || m->pair != o.pair || Tn != To ||
-        m->noise != o.noise || m->sampler != o.sampler)
+        m->noise != o.noise || m->sampler != o.sampler || m->inertia_norm != o.inertia_norm)
         return set_error(PCAD_EINVAL, "set_model changes coefficients only (L, nbhd, pair, "
                                       "pair_T, noise and sampler stay)");
     double ta64[511];

@@ -85,6 +85,8 @@ pcad_status validate_model(const pcad_model *m)
     }
     if (!(m->inertia >= 0.0f && m->inertia <= 40.0f))
         return fail(PCAD_EINVAL, "inertia must be in [0, 40]");
+    if (m->inertia_norm < 0 || m->inertia_norm > 2)
+        return fail(PCAD_EINVAL, "inertia_norm=%d must be 0, 1 or 2", m->inertia_norm);
     return PCAD_OK;
 }
 
@@ -92,6 +94,7 @@ pcad_status validate_model(const pcad_model *m)
 struct ModelTables {
     double ta64[kTable];
     std::vector<double> pr64;
+    double in64[256];   // Lp inertia price factors (norm 1, 2)
     DevModel dm;  // table pointers filled once uploaded
 };
 
@@ -135,8 +138,18 @@ void build_tables(const pcad_model &m, ModelTables &t)
         d.alpha = 0.0f;
     }
     d.Tf = (float)T;
-    d.em1 = (float)std::expm1(lam);
+    // Lp prices only for the PCA sampler (Gibbs has no inertia)
+    // (for L = 2, (|s - x_i| / 1)^p = 1{s != x_i}: the L0 price exactly)
+    const int norm = (lam > 0.0 && m.L > 2) ? m.inertia_norm : 0;
+    d.norm = norm;
+    d.em1 = norm == 0 ? (float)std::expm1(lam) : 0.0f;
     d.el64 = std::exp(lam);
+    d.kappa = norm == 0 ? 0.0f
+                        : (float)(-lam * log2e / std::pow((double)(m.L - 1), (double)norm));
+    for (int dd = 0; dd < 256; ++dd) {
+        const double q = (double)dd / (double)(m.L - 1);
+        t.in64[dd] = norm == 0 ? 1.0 : std::exp(-lam * (norm == 1 ? q : q * q));
+    }
     // Rigorous bound on |C_k/Z (FP32) - F_k (exact)|.  Exponent v = alpha Q +
     // gam P: |dv| <= u (2|gam P| + |alpha Q| + |v|) from the two rounded
     // coefficients and the two roundings.  The CDF error from the weights is
@@ -153,6 +166,19 @@ void build_tables(const pcad_model &m, ModelTables &t)
                        4.0 * u;
     const double gsum = 21.0 * u;
     d.eta = (float)(1.5 * 2.0 * (2.0 * e_w + gsum) + 8.0 * u);
+    if (norm != 0) {
+        // Lp price: v' = alpha Q + gam P + kappa R + c, R = |s - x_i|^p, the
+        // per-site shift c = |kappa| |g - x_i|^p in [0, I], I = lambda log2(e)
+        // (so v'(g) >= -A and v' <= I: no overflow, no flushed mass), FFMA
+        // chain kappa R + c -> + gam P -> + alpha Q.  |dv'| <= u (2|v'| + 3A +
+        // 4I) and E_p|v'| <= max(A, I) + log2 L, so the weight part is at most
+        // u ln2 (5A + 6I + 2 log2 L) + e_ex2 (7I taken for the rounding of c).
+        const double I = lam * 1.4426950408889634074;
+        const double e_wn = u * 0.6931471805599453 *
+                                (5.0 * A + 7.0 * I + 2.0 * std::log2((double)m.L)) +
+                            4.0 * u;
+        d.eta = (float)(1.5 * 2.0 * (2.0 * e_wn + gsum) + 8.0 * u);
+    }
     // Tensor-core sweep: v' = alpha Q + mu Pb with mu = -gam and Pb = nT - P
     // (n neighbours inside the image), i.e. v' = v + mu n T.  |dv'| <= u (2|v'|
     // + 3 mu Pb) and E_p|v'| <= E_p|v| + A <= 2A + log2 L, so the weight part
@@ -187,7 +213,7 @@ struct pcad_chain {
     uint32_t *tdev = nullptr;
     unsigned long long *fp64 = nullptr;
     double *mscratch = nullptr;   // 8 scratch + 2 results
-    double *ta64 = nullptr, *pr64 = nullptr;
+    double *ta64 = nullptr, *pr64 = nullptr, *in64 = nullptr;
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
     int tb_k = 0;                 // sweeps per temporally blocked launch (0: one per launch)
@@ -337,7 +363,8 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     const size_t fbytes = align_up((size_t)H * W * sizeof(float), 256);
     const size_t cbytes = align_up((size_t)H * W, 256);
     const size_t tbytes = align_up(kTable * sizeof(double), 256) +
-                          align_up(tabs.pr64.size() * sizeof(double), 256);
+                          align_up(tabs.pr64.size() * sizeof(double), 256) +
+                          sizeof(tabs.in64);
     const size_t misc = 256;
     const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + misc;
     cudaError_t e = cudaMallocAsync(&ch->block, total, ch->stream);
@@ -356,6 +383,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->clean = (uint8_t *)p; p += cbytes;
     ch->ta64 = (double *)p; p += align_up(kTable * sizeof(double), 256);
     ch->pr64 = (double *)p; p += align_up(tabs.pr64.size() * sizeof(double), 256);
+    ch->in64 = (double *)p; p += sizeof(tabs.in64);
     ch->tdev = (uint32_t *)p;
     ch->fp64 = (unsigned long long *)(p + 8);
     ch->mscratch = (double *)(p + 16);
@@ -380,6 +408,9 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
         e = cudaMemcpyAsync(ch->ta64, tabs.ta64, sizeof(tabs.ta64), cudaMemcpyHostToDevice,
                             ch->stream);
     if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ch->in64, tabs.in64, sizeof(tabs.in64), cudaMemcpyHostToDevice,
+                            ch->stream);
+    if (e == cudaSuccess)
         e = cudaMemcpyAsync(ch->pr64, tabs.pr64.data(), tabs.pr64.size() * sizeof(double),
                             cudaMemcpyHostToDevice, ch->stream);
     if (e == cudaSuccess)
@@ -400,6 +431,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->dm = tabs.dm;
     ch->dm.ta64 = ch->ta64;
     ch->dm.pr64 = ch->pr64;
+    ch->dm.in64 = ch->in64;
     *out = ch;
     return PCAD_OK;
 }
@@ -534,7 +566,7 @@ bool same_structure(const pcad_model &a, const pcad_model &b)
     const int Ta = a.pair == PCAD_PAIR_POTTS ? 1 : a.pair_T;
     const int Tb = b.pair == PCAD_PAIR_POTTS ? 1 : b.pair_T;
     return a.L == b.L && a.nbhd == b.nbhd && a.pair == b.pair && Ta == Tb &&
-           a.noise == b.noise && a.sampler == b.sampler;
+           a.noise == b.noise && a.sampler == b.sampler && a.inertia_norm == b.inertia_norm;
 }
 
 }  // namespace
@@ -548,7 +580,7 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
         return st;
     if (!same_structure(*m, ch->model))
         return fail(PCAD_EINVAL, "set_model changes coefficients only (L, nbhd, pair, pair_T, "
-                                 "noise and sampler stay)");
+                                 "noise, sampler and inertia_norm stay)");
     ModelTables tabs;
     build_tables(*m, tabs);
     // stream-ordered: sweeps queued before use the old tables
@@ -556,6 +588,8 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
                              ch->stream));
     CUDA_TRY(cudaMemcpyAsync(ch->pr64, tabs.pr64.data(), tabs.pr64.size() * sizeof(double),
                              cudaMemcpyHostToDevice, ch->stream));
+    CUDA_TRY(cudaMemcpyAsync(ch->in64, tabs.in64, sizeof(tabs.in64), cudaMemcpyHostToDevice,
+                             ch->stream));
     if (ch->graph) {   // captured sweeps hold the old coefficients
         CUDA_TRY(cudaStreamSynchronize(ch->stream));
         cudaGraphExecDestroy(ch->graph);
@@ -565,6 +599,7 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
     ch->dm = tabs.dm;
     ch->dm.ta64 = ch->ta64;
     ch->dm.pr64 = ch->pr64;
+    ch->dm.in64 = ch->in64;
     ch->ecoef = energy_coef(*m, (long)ch->H * ch->W);
     return PCAD_OK;
 }
@@ -717,6 +752,8 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k)
         return fail(PCAD_EINVAL, "sweeps per launch must be 0 (unblocked), 1, 2, 4 or 8");
     if (k > 0 && ch->model.sampler != PCAD_SAMPLER_PCA)
         return fail(PCAD_EINVAL, "temporal blocking applies to the PCA sampler");
+    if (k > 0 && ch->dm.norm != 0)
+        return fail(PCAD_EINVAL, "temporal blocking runs the L0 inertia price only");
     if (k > 0 && ch->track.trace)
         return fail(PCAD_ESTATE, "energy tracking needs every sweep's state: no temporal blocking");
     if (k > 0 && !ch->maps_ready) {

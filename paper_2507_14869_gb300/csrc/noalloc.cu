@@ -92,6 +92,8 @@ extern "C" pcad_status pcad_pca_run_noalloc(const uint8_t *g_dev, int H, int W, 
         return st;
     if (m->sampler != PCAD_SAMPLER_PCA)
         return set_error(PCAD_EINVAL, "the allocation-free entry point runs the PCA sampler");
+    if (m->inertia_norm != 0 && m->L > 2 && m->inertia > 0.0f)
+        return set_error(PCAD_EINVAL, "the allocation-free entry point runs the L0 inertia price");
     const uint64_t n_acc = nsweeps > burn_in ? (uint64_t)(nsweeps - burn_in) : 0;
     if ((uint64_t)(m->L - 1) * n_acc >= (1ull << 24))
         return set_error(PCAD_EINVAL, "accumulator would leave the exact FP32 range");

@@ -52,8 +52,11 @@ struct DevModel {
     float em1;         // e^lambda - 1 (0: no inertia)
     float eta;         // FP32 error bound of the normalised CDF
     float eta_b;       // the same for the banded-prior weights of the tensor-core sweep
+    int norm;          // inertia price: 0 L0 (via em1 / el64), 1 or 2 Lp (via kappa / in64)
+    float kappa;       // Lp price exponent coefficient, -lambda log2(e) / (L - 1)^p
     const double *ta64;  // [511] data factor exp(-(U(g, g-d) - U(g,g))) at d + 255, FP64
     const double *pr64;  // [pmax + 1] exp(-c P), FP64
+    const double *in64;  // [256] Lp price factor exp(-lambda (d / (L - 1))^p), FP64
     double el64;         // e^lambda, FP64
 };
 
@@ -388,9 +391,94 @@ __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gst
                       });
 }
 
+// ------------------------------------------------- Lp inertia price (p = 1, 2)
+// Exponent v' = alpha (g - s)^2 + gam P(s) + kappa R(s) + c with R = |s - x_i|^p
+// (exact integers) and the per-site shift c = |kappa| |g - x_i|^p, evaluated
+// as one FFMA chain: kappa R + c, + gam P, + alpha Q.
+
+__device__ __forceinline__ float label_wn(const DevModel &m, float P, float dg, float R, float c)
+{
+    const float q = __fmul_rn(dg, dg);
+    const float t1 = __fmaf_rn(m.kappa, R, c);
+    const float t2 = __fmaf_rn(m.gam, P, t1);
+    return ex2_ftz(__fmaf_rn(m.alpha, q, t2));
+}
+
+// Weights of labels [8c, 8c + 8) with the Lp price; as chunk_weights.
+template <int NB, bool MASK, bool PREFIX, int NORM>
+__device__ __forceinline__ float chunk_weights_n(const DevModel &m, const __half2 (&xh)[NB],
+                                                 __half2 T2, float gf, float xif, float csite,
+                                                 int c, float (&p)[kChunk])
+{
+    const float sbf = (float)(c * kChunk);
+    const __half2 sb2 = __float2half2_rn(sbf);
+    __half2 xr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        xr[j] = __hsub2(xh[j], sb2);
+    const float dgb = gf - sbf;
+    const float dxb = sbf - xif;
+    float S = 0.0f;
+#pragma unroll
+    for (int kk = 0; kk < kChunk; kk += 2) {
+        const float2 P = prior_pair<NB>(xr, __floats2half2_rn((float)kk, (float)(kk + 1)), T2);
+        const float d0 = dxb + (float)kk, d1 = dxb + (float)(kk + 1);
+        const float R0 = NORM == 1 ? fabsf(d0) : __fmul_rn(d0, d0);
+        const float R1 = NORM == 1 ? fabsf(d1) : __fmul_rn(d1, d1);
+        float e0 = label_wn(m, P.x, dgb - (float)kk, R0, csite);
+        float e1 = label_wn(m, P.y, dgb - (float)(kk + 1), R1, csite);
+        if (MASK) {
+            if (c * kChunk + kk >= m.L) e0 = 0.0f;
+            if (c * kChunk + kk + 1 >= m.L) e1 = 0.0f;
+        }
+        S = __fadd_rn(S, e0);
+        if (PREFIX) p[kk] = S;
+        S = __fadd_rn(S, e1);
+        if (PREFIX) p[kk + 1] = S;
+    }
+    return S;
+}
+
+// FP32 inverse-CDF draw with the Lp price (no single-label correction: the
+// price is part of every weight); as draw_fp32.
+template <int NC, int NB, int NORM>
+__device__ __forceinline__ int draw_fp32_norm(const DevModel &m, float *Gcol, int gstride,
+                                              const SiteIn<NB> &in, bool &certain)
+{
+    __half2 xh[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        xh[j] = __float2half2_rn((float)in.xni[j]);
+    const __half2 T2 = __float2half2_rn(m.Tf);
+    const float gf = (float)in.g;
+    const float xif = (float)in.xi;
+    const float D = fabsf(gf - xif);
+    const float csite = __fmul_rn(-m.kappa, NORM == 1 ? D : __fmul_rn(D, D));
+    float pdummy[kChunk];
+    float G = 0.0f, comp = 0.0f;
+    const int nfull = m.L / kChunk;
+#pragma unroll 1
+    for (int c = 0; c < NC; ++c) {
+        const float S = (c < nfull)
+                            ? chunk_weights_n<NB, false, false, NORM>(m, xh, T2, gf, xif, csite, c,
+                                                                      pdummy)
+                            : chunk_weights_n<NB, true, false, NORM>(m, xh, T2, gf, xif, csite, c,
+                                                                     pdummy);
+        const float y = __fsub_rn(S, comp);
+        const float tt = __fadd_rn(G, y);
+        comp = __fsub_rn(__fsub_rn(tt, G), y);
+        G = tt;
+        Gcol[c * gstride] = G;
+    }
+    return cdf_select(m, m.eta, [&](int cc) { return Gcol[cc * gstride]; }, NC, G, 0.0f, in.xi,
+                      in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
+                          chunk_weights_n<NB, true, true, NORM>(m, xh, T2, gf, xif, csite, cs, pp);
+                      });
+}
+
 // ------------------------------------------------------------ FP64 re-draw
 
-template <int NB>
+template <int NB, int NORM = 0>
 __device__ __forceinline__ double weight64(const DevModel &m, int g, int xi, const int (&xni)[NB],
                                            int s)
 {
@@ -401,7 +489,9 @@ __device__ __forceinline__ double weight64(const DevModel &m, int g, int xi, con
         P += d < m.T ? d : m.T;
     }
     double w = __dmul_rn(m.ta64[g - s + kTableOffset], m.pr64[P]);
-    if (m.em1 != 0.0f && s == xi)
+    if constexpr (NORM != 0)
+        w = __dmul_rn(w, m.in64[abs(s - xi)]);
+    else if (m.em1 != 0.0f && s == xi)
         w = __dmul_rn(w, m.el64);
     return w;
 }
@@ -410,7 +500,7 @@ __device__ __forceinline__ double weight64(const DevModel &m, int g, int xi, con
 // set: for each such lane in turn, the 32 lanes compute 8 labels' FP64
 // weights each, an FP64 warp scan gives the CDF, and the lane holding u*Z
 // finds the label.  All 32 lanes of the warp must call this together.
-template <int NB>
+template <int NB, int NORM = 0>
 __device__ __forceinline__ int warp_redraw_fp64(const DevModel &m, bool need, const SiteIn<NB> &in,
                                                 int s, unsigned long long *counter)
 {
@@ -436,7 +526,7 @@ __device__ __forceinline__ int warp_redraw_fp64(const DevModel &m, bool need, co
 #pragma unroll
         for (int k = 0; k < kChunk; ++k) {
             const int sl = lane * kChunk + k;
-            w[k] = sl < m.L ? weight64<NB>(m, lg, lxi, lx, sl) : 0.0;
+            w[k] = sl < m.L ? weight64<NB, NORM>(m, lg, lxi, lx, sl) : 0.0;
             part = __dadd_rn(part, w[k]);
         }
         double incl = part;

@@ -17,33 +17,39 @@ constexpr int kThreads = kBX * kBY;
 
 // Draw the new label of every valid site of the warp; uncertain FP32 draws
 // are re-evaluated in FP64 by the whole warp.  Every lane must call this.
-template <int NC, int NB>
+// NORM: the inertia price (0: L0 via the single-label correction; 1, 2: Lp).
+template <int NC, int NB, int NORM = 0>
 __device__ __forceinline__ int draw_site(const SweepArgs &a, bool valid, const SiteIn<NB> &in,
                                          float *Gcol)
 {
     int s = 0;
     bool certain = true;
-    // chunks where any lane's prior has a kink take the general path; with
-    // few chunks (L <= 32) the mask costs more than the linear path saves
-    uint32_t dirty = 0xFFFFFFFFu;
-    if (NC >= 8)
-        dirty = __reduce_or_sync(0xFFFFFFFFu, valid ? dirty_chunks<NB>(in.xni, a.m.T) : 0u);
-    if (valid)
-        s = draw_fp32<NC, NB>(a.m, Gcol, kThreads, in, dirty, certain);
-    return warp_redraw_fp64<NB>(a.m, valid && !certain, in, s, a.fp64_draws);
+    if constexpr (NORM == 0) {
+        // chunks where any lane's prior has a kink take the general path; with
+        // few chunks (L <= 32) the mask costs more than the linear path saves
+        uint32_t dirty = 0xFFFFFFFFu;
+        if (NC >= 8)
+            dirty = __reduce_or_sync(0xFFFFFFFFu, valid ? dirty_chunks<NB>(in.xni, a.m.T) : 0u);
+        if (valid)
+            s = draw_fp32<NC, NB>(a.m, Gcol, kThreads, in, dirty, certain);
+    } else {
+        if (valid)
+            s = draw_fp32_norm<NC, NB, NORM>(a.m, Gcol, kThreads, in, certain);
+    }
+    return warp_redraw_fp64<NB, NORM>(a.m, valid && !certain, in, s, a.fp64_draws);
 }
 
 // One lazy-PCA site update (r, c) at sweep t: draw from x_in, write x_out,
 // accumulate after burn-in.  Every lane of the warp must call it (lanes
 // outside the image pass through the warp-level steps).
-template <int NC, int NB>
+template <int NC, int NB, int NORM = 0>
 __device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint32_t t, float *Gcol)
 {
     const bool valid = r < a.H && c < a.W;
     SiteIn<NB> in{};
     if (valid)
         load_site<NB>(a, a.xin, r, c, kTagPCA, t, in);
-    const int s = draw_site<NC, NB>(a, valid, in, Gcol);
+    const int s = draw_site<NC, NB, NORM>(a, valid, in, Gcol);
     if (valid) {
         a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
         if (accumulate_after(a, t))
@@ -51,14 +57,14 @@ __device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint3
     }
 }
 
-template <int NC, int NB>
+template <int NC, int NB, int NORM>
 __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 {
     __shared__ float G_s[NC * kThreads];
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const int c = blockIdx.x * kBX + threadIdx.x;
     const int r = blockIdx.y * kBY + threadIdx.y;
-    pca_site<NC, NB>(a, r, c, sweep_index(a), G_s + tid);
+    pca_site<NC, NB, NORM>(a, r, c, sweep_index(a), G_s + tid);
 }
 
 // Gibbs colour phase q.  A thread owns one "cell": a pair of columns
@@ -215,7 +221,12 @@ cudaError_t launch_pca_t(const SweepArgs &a, cudaStream_t st)
 {
     dim3 block(kBX, kBY);
     dim3 grid((a.W + kBX - 1) / kBX, (a.H + kBY - 1) / kBY);
-    pca_direct_kernel<NC, NB><<<grid, block, 0, st>>>(a);
+    if (a.m.norm == 1)
+        pca_direct_kernel<NC, NB, 1><<<grid, block, 0, st>>>(a);
+    else if (a.m.norm == 2)
+        pca_direct_kernel<NC, NB, 2><<<grid, block, 0, st>>>(a);
+    else
+        pca_direct_kernel<NC, NB, 0><<<grid, block, 0, st>>>(a);
     return cudaGetLastError();
 }
 

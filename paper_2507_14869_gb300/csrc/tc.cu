@@ -765,7 +765,7 @@ cudaError_t configure(TcConfig &cfg)
 
 bool pca_tc_eligible(const DevModel &m)
 {
-    if (m.L < kTcMinLabels || m.L > 256 || m.T > kTcMaxT)
+    if (m.L < kTcMinLabels || m.L > 256 || m.T > kTcMaxT || m.norm != 0)
         return false;
     return tc_layout(m.L, m.T).smem <= kSmemMax;
 }
