@@ -217,12 +217,14 @@ def run_ours(a):
     import torch
 
     import paper_2507_14869_gb300 as pc
+    from paper_2507_14869_gb300 import replicas
 
     world, rank, local = _dist()
     if world > 1:
         import torch.distributed as dist
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
+    cid = replicas.chain_id(rank, 0, 1)   # one chain per rank, distinct uniforms
     dev = torch.device("cuda", local if world > 1 else 0)
     torch.cuda.set_device(dev)
     clean, noisy, m = _inputs()
@@ -258,16 +260,12 @@ def run_ours(a):
 
     kind = KERNEL_KINDS[a.kernel]
     on_tc = _tensor_path(a.kernel, m)
-    pca = pc.Chain(noisy, m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream)
+    pca = pc.Chain(noisy, m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream)
     pca.set_kernel(kind)
     with ClockSampler(local) as clk:
         ms, wall = timed(pca, a.steps, a.warmup)
     T = sum(ms) / 1e3
-    T_max = T
-    if world > 1:
-        t = torch.tensor([T], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        T_max = float(t.item())
+    T_max = replicas.max_time(T)   # the slowest rank's time
     sites = H * W * SWEEPS
     value = world * sites * a.steps / T_max
     launch_ms = 1e3 * T / (a.steps * SWEEPS)
@@ -277,7 +275,7 @@ def run_ours(a):
 
     gibbs = None
     if not a.no_gibbs:
-        gch = pc.Chain(noisy, m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream,
+        gch = pc.Chain(noisy, m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream,
                        sampler=pc.SAMPLER_GIBBS_CB)
         gsteps = max(2, a.steps // 2)
         gms, _ = timed(gch, gsteps, 1)
@@ -298,7 +296,7 @@ def run_ours(a):
     e2e_t = []
     for k in range(e2e_steps + 1):
         t0 = time.perf_counter()
-        ch = pc.Chain(g_host.numpy(), m, seed=2, chain_id=rank, burn_in=BURN_IN, stream=stream)
+        ch = pc.Chain(g_host.numpy(), m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream)
         ch.set_kernel(kind)
         ch.run(SWEEPS)
         pc.pcad_chain_read_mean(ch.h, H, W, out=mean_host.numpy())
@@ -366,12 +364,22 @@ def run_batch(a):
     import torch
 
     import paper_2507_14869_gb300 as pc
+    from paper_2507_14869_gb300 import replicas
     from pcad_inputs import batched_jobs
 
-    torch.cuda.set_device(0)
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    imgs = batched_jobs(seed=4, n_images=a.images, chains=4, sweeps=BATCH_SWEEPS,
-                        burn_in=BATCH_BURN)
+    all_imgs = batched_jobs(seed=4, n_images=a.images, chains=4, sweeps=BATCH_SWEEPS,
+                            burn_in=BATCH_BURN)
+    # each rank takes its share of the images (cost ~ sites x labels), no collective
+    mine = replicas.shard([j.noisy.size * j.model.L for j in all_imgs], world)[rank]
+    imgs = [all_imgs[i] for i in mine]
     jobs = [(j.noisy, j.model, j.seed, c, j.burn_in) for j in imgs for c in range(j.chains)]
     sites = sum(g.size for g, *_ in jobs)
     by_L = {}
@@ -384,7 +392,7 @@ def run_batch(a):
     pc.pcad_batch_reset(b)
     pc.pcad_batch_sync(b)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with ClockSampler(0) as clk:
+    with ClockSampler(local) as clk:
         ev[0].record(stream)
         pc.pcad_batch_run(b, BATCH_SWEEPS)
         ev[1].record(stream)
@@ -420,9 +428,23 @@ def run_batch(a):
     for ch in chains:
         ch.close()
     pc.pcad_batch_destroy(b)
-    n_img = len(imgs)
+    # whole job: every rank's images over the slowest rank's time
+    t_batch_all = replicas.max_time(t_batch)
+    t_plain_all = replicas.max_time(t_plain)
+    sites_all = replicas.gather({rank: sites})
+    psnr_all = replicas.gather({rank: psnr})
+    same_all = replicas.gather({rank: same})
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    n_img = len(all_imgs)
+    sites = sum(sites_all.values())
+    psnr = [v for r in sorted(psnr_all) for v in psnr_all[r]]
+    same = all(same_all.values())
+    t_batch, t_plain = t_batch_all, t_plain_all
     line = {"metric": "img/s (batched, 4 chains per image)", "value": n_img / t_batch,
-            "unit": "img/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "unit": "img/s", "n_gpus": world, "steps": 1, "warmup": 1,
             "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"{n_img} uneven images x 4 chains, {BATCH_SWEEPS} sweeps, "
@@ -437,7 +459,11 @@ def run_batch(a):
             "autotune": info, "fp64_redraw_fraction": fp64 / float(sites * BATCH_SWEEPS),
             "gpu_launches": -(-BATCH_SWEEPS // 16) * 17,
             "clocks": clk.summary()}
+    if world > 1:
+        line["config"]["parallelism"] = f"images sharded over {world} ranks (LPT by cost)"
     print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
 
 
 PROTO_CASES = ((5, 0.25), (9, 0.2), (33, 0.1))   # (levels, sigma in intensity units)
