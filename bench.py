@@ -48,24 +48,15 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
                     "the sweep touches")
 
 
-# The same for pca_tc_kernel<4>; None until an ncu capture of the current
-# kernel gives it.
+# The same for pca_tc_kernel<4> (None: not captured for this version) and
+# pca_wave_kernel<32,4> (one 32-sweep launch at 1024^2, per site-update).
 NCU_TC_DRAM_BYTES_PER_SITE = None
 NCU_TC_TRAFFIC_NOTE = "not captured for this kernel version"
+NCU_WAVE_DRAM_BYTES_PER_SITE = (6.363904e6 + 0.730112e6) / (32 * 1024 * 1024)
+NCU_WAVE_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 1024^2 L=256, per "
+                         "site-update, scaled to one 512^2 sweep (profiles/pca_wave_l256_1024sq.md)")
 
-KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2}
-
-
-def _tensor_path(kernel, m):
-    """Whether an unblocked PCA sweep of model m runs on the tensor-core kernel
-    (only on request; the default is the CUDA-core kernel)."""
-    T = 1 if m.pair == 0 else m.pair_T
-    o = (T - 1 + 15) // 16 * 16                       # band padding of the histogram
-    a_slabs = (64 * ((m.L + 63) // 64) + 2 * o + 63) // 64
-    b_slabs = (64 + 2 * o + 63) // 64
-    smem = 2 * a_slabs * 16384 + b_slabs * 8192 + 2 * ((m.L + 7) // 8) * 512 + 4 * 2048 + 240
-    eligible = m.L >= 64 and T <= 65 and smem <= 232448
-    return kernel == "tensor" and eligible
+KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3}
 
 
 def _args():
@@ -88,7 +79,7 @@ def _args():
                         "chains in one persistent launch vs one chain per launch; serve: "
                         "Poisson request stream through the continuous-batching server; "
                         "protocol: the paper's annealed runs on MRF images and the q grid")
-    p.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor"],
+    p.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor", "wave"],
                    help="kernel of the unblocked PCA sweep (chain workload and profile case): "
                         "auto = cuda_core; tensor = prior sums by tcgen05.mma")
     p.add_argument("--images", type=int, default=128, help="batch: number of images")
@@ -259,9 +250,9 @@ def run_ours(a):
         return ms, wall
 
     kind = KERNEL_KINDS[a.kernel]
-    on_tc = _tensor_path(a.kernel, m)
     pca = pc.Chain(noisy, m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream)
     pca.set_kernel(kind)
+    pca_kind = pca.kernel_in_use()
     with ClockSampler(local) as clk:
         ms, wall = timed(pca, a.steps, a.warmup)
     T = sum(ms) / 1e3
@@ -307,10 +298,20 @@ def run_ours(a):
 
     if rank != 0:
         return
-    per_launch_labels = H * W * m.L
-    achieved = per_launch_labels / (launch_ms * 1e-3) / 1e12
-    per_site = NCU_TC_DRAM_BYTES_PER_SITE if on_tc else NCU_DRAM_BYTES_PER_SITE
+    per_sweep_labels = H * W * m.L
+    achieved = per_sweep_labels / (launch_ms * 1e-3) / 1e12
+    in_use = pca_kind   # the kernel the timed chain ran
+    kernel_name = {1: "pca_direct_kernel<32,4> (one launch per sweep)",
+                   2: "pca_tc_kernel<4> (tcgen05 banded prior sums, CUDA-core CDF)",
+                   3: "pca_wave_kernel<32,4> (wavefront, one launch per 32 sweeps)"}[in_use]
+    per_site = {1: NCU_DRAM_BYTES_PER_SITE, 2: NCU_TC_DRAM_BYTES_PER_SITE,
+                3: NCU_WAVE_DRAM_BYTES_PER_SITE}[in_use]
+    note = {1: NCU_TRAFFIC_NOTE, 2: NCU_TC_TRAFFIC_NOTE, 3: NCU_WAVE_TRAFFIC_NOTE}[in_use]
     traffic = per_site * H * W if per_site else None
+    blocks, rest = divmod(SWEEPS, 32)
+    # per chain: the 32-sweep graphs (sweep launches + the counter advance) and the rest
+    launches = (blocks * (2 if in_use == 3 else 33) +
+                ((2 if in_use == 3 else rest + 1) if rest else 0))
     line = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -321,16 +322,13 @@ def run_ours(a):
                    "parallelism": "independent chain per GPU" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
                      "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
-                     "traffic": traffic,
-                     "traffic_source": NCU_TC_TRAFFIC_NOTE if on_tc else NCU_TRAFFIC_NOTE,
-                     "kernel": ("pca_tc_kernel<4> (tcgen05 banded prior sums, CUDA-core CDF)"
-                                if on_tc else "pca_direct_kernel<32,4>"),
+                     "traffic": traffic, "traffic_source": note, "kernel": kernel_name,
                      "work_per_unit": "one exponential (SFU) per label evaluation, L=256 per "
                                       "site-update",
                      "peak_source": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count x max "
                                     "clock; 29.9/clk/SM measured)",
-                     "ms_per_launch": launch_ms},
-        "gpu_launches": a.steps * (SWEEPS + (SWEEPS + 31) // 32),
+                     "ms_per_sweep": launch_ms},
+        "gpu_launches": a.steps * launches,
         "e2e": {"value": e2e_v, "unit": "site-updates/s", "h2d_bytes_per_step": H * W,
                 "d2h_bytes_per_step": H * W * 4, "steps": e2e_steps,
                 "ms_per_step": 1e3 * statistics.mean(e2e_t),

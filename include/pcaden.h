@@ -151,16 +151,33 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * T = 1), and two histogram operands of 128 x (64 ceil(L/64) + 2 o) FP16
  * (o = T - 1 rounded up to 16), the 64 x (64 + 2 o) band block and two
  * 128 x ceil(L/8) FP32 chunk-sum arrays within 227 KB of shared memory --
- * for L = 256 that is T <= 33.  PCAD_EINVAL for an unknown kind or
- * PCAD_KERNEL_TENSOR on a model outside those limits.
+ * for L = 256 that is T <= 33; with AUTO the unblocked PCA sweep runs
+ * the per-sweep or the wavefront CUDA-core kernel (see
+ * pcad_chain_kernel_in_use).  PCAD_EINVAL for an unknown kind or
+ * PCAD_KERNEL_TENSOR on a model outside those limits.  PCAD_KERNEL_WAVE
+ * runs the CUDA-core draw as one persistent launch per block of sweeps, a
+ * tile of 4 x 32 sites starting sweep k as soon as its 3 x 3 neighbouring
+ * tiles finished sweep k - 1 (no sweep-wide barrier, so one sweep's tail
+ * overlaps the next one's start); same labels; L0 price only (PCAD_EINVAL
+ * with an Lp norm); energy tracking falls back to one launch per sweep.
  * pcad_chain_sync reports PCAD_ETIMEOUT if a tensor-core completion wait
- * ever gave up. */
+ * or a wavefront dependency wait ever gave up. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
-    PCAD_KERNEL_TENSOR = 2
+    PCAD_KERNEL_TENSOR = 2,
+    PCAD_KERNEL_WAVE = 3
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
+
+/* The kernel the chain's next sweeps run: PCAD_KERNEL_CUDA_CORE (one launch
+ * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR, or
+ * -k for temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO
+ * the wavefront kernel is taken for L >= 16 when the image has between 1/2
+ * and 3 waves of 4 x 32 tiles at 10 resident tiles per multiprocessor (the
+ * sizes where it measured faster on GB300), the per-sweep kernel
+ * otherwise. */
+pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind);
 
 /* Change the model's coefficients (pair_coef, sigma, flip_p, inertia) for
  * the sweeps queued after this call; L, nbhd, pair, pair_T, noise and

@@ -100,6 +100,7 @@ def _declare(L):
         "pcad_chain_reset": [vp],
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
         "pcad_chain_set_kernel": [vp, ctypes.c_int],
+        "pcad_chain_kernel_in_use": [vp, ctypes.POINTER(ctypes.c_int)],
         "pcad_chain_energy": [vp, dp, u64p, u64p],
         "pcad_chain_set_model": [vp, mp],
         "pcad_chain_run_schedule": [vp, mp, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
@@ -373,6 +374,9 @@ class Chain:
         pcad_chain_run_schedule(self.h, [as_model(m, self.sampler) for m in models], sweeps)
         return self
 
+    def kernel_in_use(self) -> int:
+        return pcad_chain_kernel_in_use(self.h)
+
     def energy(self):
         """(H, pair_sum, data_sum) of the current sample."""
         return pcad_chain_energy(self.h)
@@ -554,6 +558,13 @@ def pcad_chain_set_blocking(h, k: int):
     _check("pcad_chain_set_blocking", lib().pcad_chain_set_blocking(h, int(k)))
 
 
+def pcad_chain_kernel_in_use(h) -> int:
+    """Kernel kind of the chain's next sweeps (-k: temporal blocking, k per launch)."""
+    k = ctypes.c_int()
+    _check("pcad_chain_kernel_in_use", lib().pcad_chain_kernel_in_use(h, ctypes.byref(k)))
+    return k.value
+
+
 def pcad_chain_set_model(h, model):
     """New coefficients (annealing); the model's structure must stay."""
     m = as_model(model)
@@ -612,6 +623,7 @@ def pcad_chain_read_min_state(h, H: int, W: int):
 PCAD_KERNEL_AUTO = 0
 PCAD_KERNEL_CUDA_CORE = 1
 PCAD_KERNEL_TENSOR = 2
+PCAD_KERNEL_WAVE = 3
 
 
 def pcad_chain_set_kernel(h, kind: int):

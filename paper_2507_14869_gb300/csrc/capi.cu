@@ -225,6 +225,9 @@ struct pcad_chain {
     unsigned long long *esums = nullptr;   // energy reduction sums (device, 2 x u64)
     EnergyCoef ecoef{};
     EnergyTrack track{};          // minimum-energy tracking (trace == nullptr: off)
+    unsigned int *wave = nullptr; // wavefront kernel: per-tile counters + work counter
+    int wave_tiles = 0;
+    int sms = 0;                  // multiprocessors of the chain's device
     void *track_block = nullptr;
 };
 
@@ -255,11 +258,40 @@ bool uses_tc(const pcad_chain *ch)
            pca_tc_eligible(ch->dm);
 }
 
+// Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
+// AUTO takes them where the measured GB300 sweep favoured them: L >= 16 and
+// between 1/2 and 3 waves of the per-sweep kernel (10 resident 4 x 32 tiles
+// per SM): there the per-sweep tail wave costs up to 25 %; with fewer tiles
+// or cheaper labels the wavefront's single work counter limits it.
+bool uses_wave(const pcad_chain *ch)
+{
+    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->dm.norm != 0 || ch->tb_k > 0 ||
+        ch->track.trace)
+        return false;
+    if (ch->kernel == PCAD_KERNEL_WAVE)
+        return true;
+    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0)
+        return false;
+    const long slots = 10L * ch->sms;
+    return 2L * ch->wave_tiles >= slots && ch->wave_tiles <= 3L * slots;
+}
+
 // Issue sweeps [*counter + off0, *counter + off0 + n) without advancing the counter.
 pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t st)
 {
     SweepArgs a = make_args(ch);
     const bool tc = uses_tc(ch);
+    if (uses_wave(ch) && n > 0) {
+        // one persistent launch for all n sweeps: counters zeroed first
+        a.sweep_off = (uint32_t)off0;
+        CUDA_TRY(cudaMemsetAsync(ch->wave, 0, (size_t)(ch->wave_tiles + 1) * sizeof(unsigned int),
+                                 st));
+        CUDA_TRY(launch_pca_wave(a, ch->x[cur], ch->x[cur ^ 1], n, ch->wave,
+                                 ch->wave + ch->wave_tiles, ch->err, st));
+        if (n & 1)
+            cur ^= 1;
+        return PCAD_OK;
+    }
     const int ncol = ch->model.nbhd == 4 ? 2 : 4;
     int done = 0;
     if (ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k > 0) {
@@ -366,7 +398,9 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
                           align_up(tabs.pr64.size() * sizeof(double), 256) +
                           sizeof(tabs.in64);
     const size_t misc = 256;
-    const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + misc;
+    const int ntiles = wave_tiles(H, W);
+    const size_t wbytes = align_up((size_t)(ntiles + 1) * sizeof(unsigned int), 256);
+    const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + misc;
     cudaError_t e = cudaMallocAsync(&ch->block, total, ch->stream);
     if (e != cudaSuccess) {
         delete ch;
@@ -384,6 +418,13 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->ta64 = (double *)p; p += align_up(kTable * sizeof(double), 256);
     ch->pr64 = (double *)p; p += align_up(tabs.pr64.size() * sizeof(double), 256);
     ch->in64 = (double *)p; p += sizeof(tabs.in64);
+    ch->wave = (unsigned int *)p; p += wbytes;
+    ch->wave_tiles = ntiles;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&ch->sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     ch->tdev = (uint32_t *)p;
     ch->fp64 = (unsigned long long *)(p + 8);
     ch->mscratch = (double *)(p + 16);
@@ -545,14 +586,14 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     CUDA_TRY(cudaStreamSynchronize(ch->stream));
-    if (ch->tb_k > 0 || uses_tc(ch)) {
+    if (ch->tb_k > 0 || uses_tc(ch) || uses_wave(ch)) {
         int e = 0;
         CUDA_TRY(cudaMemcpy(&e, ch->err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e == 2)
             return fail(PCAD_ECUDA, "tensor-core sweep: shared memory not 1024-byte aligned");
         if (e)
-            return fail(PCAD_ETIMEOUT, "a bounded wait of the sweep kernel (tile load or MMA "
-                                       "completion) gave up");
+            return fail(PCAD_ETIMEOUT, "a bounded wait of the sweep kernel (tile load, MMA "
+                                       "completion or wavefront dependency) gave up");
     }
     return PCAD_OK;
 }
@@ -619,6 +660,23 @@ pcad_status pcad_chain_run_schedule(pcad_chain *ch, const pcad_model *models, co
         if (st != PCAD_OK)
             return st;
     }
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
+{
+    if (!ch || !kind)
+        return fail(PCAD_EINVAL, "chain or kind is NULL");
+    if (ch->model.sampler != PCAD_SAMPLER_PCA)
+        *kind = PCAD_KERNEL_CUDA_CORE;
+    else if (ch->tb_k > 0)
+        *kind = -ch->tb_k;
+    else if (uses_tc(ch))
+        *kind = PCAD_KERNEL_TENSOR;
+    else if (uses_wave(ch))
+        *kind = PCAD_KERNEL_WAVE;
+    else
+        *kind = PCAD_KERNEL_CUDA_CORE;
     return PCAD_OK;
 }
 
@@ -729,8 +787,12 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
 {
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
-    if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE && kind != PCAD_KERNEL_TENSOR)
-        return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE or _TENSOR");
+    if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE &&
+        kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE)
+        return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR or "
+                                 "_WAVE");
+    if (kind == PCAD_KERNEL_WAVE && (ch->model.sampler != PCAD_SAMPLER_PCA || ch->dm.norm != 0))
+        return fail(PCAD_EINVAL, "the wavefront kernel needs the PCA sampler and the L0 price");
     if (kind == PCAD_KERNEL_TENSOR &&
         (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_tc_eligible(ch->dm)))
         return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, L >= 64, "

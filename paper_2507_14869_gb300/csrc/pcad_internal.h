@@ -45,21 +45,25 @@ __device__ __forceinline__ bool accumulate_after(const SweepArgs &a, uint32_t t)
 // Inputs of site (r, c) from the labels x at sweep t.  Neighbour order:
 // up, down, left, right, then the four diagonals; a neighbour outside the
 // image is "missing" (label 1024).
-template <int NB>
+// L2_ONLY: the labels may have been written by other SMs during the same
+// launch, so they are read through L2 (ld.global.cg), never from a possibly
+// stale L1 line.
+template <int NB, bool L2_ONLY = false>
 __device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__restrict__ x, int r,
                                           int c, uint32_t tag, uint32_t t, SiteIn<NB> &in)
 {
     constexpr int dr[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
     constexpr int dc[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+    const auto ld = [&](size_t i) -> int { return L2_ONLY ? (int)__ldcg(x + i) : (int)x[i]; };
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         const int rr = r + dr[j];
         const int cc = c + dc[j];
         const bool inside = rr >= 0 && rr < a.H && cc >= 0 && cc < a.W;
-        in.xni[j] = inside ? (int)x[(size_t)rr * a.pitch + cc] : kMissingLabelI;
+        in.xni[j] = inside ? ld((size_t)rr * a.pitch + cc) : kMissingLabelI;
     }
     const size_t idx = (size_t)r * a.pitch + c;
-    in.xi = x[idx];
+    in.xi = ld(idx);
     in.g = a.g[idx];
     in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
 }
@@ -169,6 +173,15 @@ cudaError_t launch_energy(const uint8_t *x, const uint8_t *g, int H, int W, int 
                           const EnergyCoef &k, unsigned long long *sums, double *out,
                           const EnergyTrack &tr, const uint32_t *tdev, uint32_t sweep_off,
                           cudaStream_t s);
+
+// Wavefront lazy-PCA: nsweeps sweeps in one persistent launch from plane x0
+// (sweep index *a.sweep_base + a.sweep_off + k reads x[k & 1] of {x0, x1});
+// a tile starts sweep k once the 3 x 3 neighbouring tiles finished sweep
+// k - 1.  done (one counter per 4 x 32 tile) and grab (the work counter)
+// must be zero on entry; *err is set if a bounded dependency wait gives up.
+cudaError_t launch_pca_wave(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
+                            unsigned int *done, unsigned int *grab, int *err, cudaStream_t s);
+int wave_tiles(int H, int W);
 
 // Tensor-core lazy-PCA sweep (prior sums by tcgen05.mma).  Eligible models:
 // L >= kTcMinLabels and truncation T <= kTcMaxT (the banded window must fit

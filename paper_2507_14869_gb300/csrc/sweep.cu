@@ -42,18 +42,22 @@ __device__ __forceinline__ int draw_site(const SweepArgs &a, bool valid, const S
 // One lazy-PCA site update (r, c) at sweep t: draw from x_in, write x_out,
 // accumulate after burn-in.  Every lane of the warp must call it (lanes
 // outside the image pass through the warp-level steps).
-template <int NC, int NB, int NORM = 0>
+// L2_ONLY: labels and accumulator written by other SMs in the same launch
+// are read through L2 (the wavefront kernel).
+template <int NC, int NB, int NORM = 0, bool L2_ONLY = false>
 __device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint32_t t, float *Gcol)
 {
     const bool valid = r < a.H && c < a.W;
     SiteIn<NB> in{};
     if (valid)
-        load_site<NB>(a, a.xin, r, c, kTagPCA, t, in);
+        load_site<NB, L2_ONLY>(a, a.xin, r, c, kTagPCA, t, in);
     const int s = draw_site<NC, NB, NORM>(a, valid, in, Gcol);
     if (valid) {
         a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-        if (accumulate_after(a, t))
-            a.acc[(size_t)r * a.W + c] += (float)s;
+        if (accumulate_after(a, t)) {
+            float *p = a.acc + (size_t)r * a.W + c;
+            *p = (L2_ONLY ? __ldcg(p) : *p) + (float)s;
+        }
     }
 }
 
@@ -65,6 +69,85 @@ __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
     const int c = blockIdx.x * kBX + threadIdx.x;
     const int r = blockIdx.y * kBY + threadIdx.y;
     pca_site<NC, NB, NORM>(a, r, c, sweep_index(a), G_s + tid);
+}
+
+// Wavefront lazy-PCA over nsweeps sweeps in one persistent launch.  Work
+// items (sweep k, tile j) of 4 x 32 sites are taken in increasing order from
+// an atomic counter; item (k, j) waits until the 3 x 3 tiles around j have
+// finished sweep k - 1 (done[] counts finished sweeps per tile).  The tiles
+// it reads (x of sweep k) and overwrites (x of sweep k - 1) are exactly
+// those, so no sweep-wide barrier is needed and the tail of one sweep
+// overlaps the start of the next.  Every item an item depends on has a
+// smaller index and was taken by a block that is resident (the grid is the
+// resident capacity), so the waits end; each is bounded anyway (error flag).
+// Draws are keyed by (sweep, site): results equal per-sweep launches.
+constexpr long long kWaveSpinLimit = 20000000;
+#ifndef PCAD_WAVE_MIN_BLOCKS
+#define PCAD_WAVE_MIN_BLOCKS 8   // resident blocks per SM the register budget targets
+#endif
+
+template <int NC, int NB>
+__global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kernel(const SweepArgs a, uint8_t *x0,
+                                                           uint8_t *x1, int nsweeps,
+                                                           int tiles_x, int tiles_y,
+                                                           unsigned int *done,
+                                                           unsigned int *grab, int *err)
+{
+    __shared__ float G_s[NC * kThreads];
+    __shared__ unsigned int s_next;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
+    const unsigned int total = ntiles * (unsigned int)nsweeps;
+    const uint32_t t0 = sweep_index(a);
+    if (tid == 0)
+        s_next = atomicAdd(grab, 1u);
+    __syncthreads();
+    unsigned int item = s_next;
+    while (item < total) {
+        const int k = (int)(item / ntiles);
+        const int j = (int)(item - (unsigned int)k * ntiles);
+        const int ty = j / tiles_x;
+        const int tx = j - ty * tiles_x;
+        __syncthreads();   // everyone has read s_next
+        if (threadIdx.y == 0) {
+            // lane 31 fetches the following item while lanes 0-8 each wait for
+            // one tile of the 3 x 3 neighbourhood to finish sweep k - 1
+            if (threadIdx.x == 31)
+                s_next = atomicAdd(grab, 1u);
+            bool ok = true;
+            if (k > 0 && threadIdx.x < 9) {
+                const int yy = ty + (int)threadIdx.x / 3 - 1;
+                const int xx = tx + (int)threadIdx.x % 3 - 1;
+                if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
+                    const volatile unsigned int *d = done + (size_t)yy * tiles_x + xx;
+                    long long spins = 0;
+                    while (*d < (unsigned int)k) {
+                        if (++spins > kWaveSpinLimit) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+            }
+            if (!ok)
+                atomicExch(err, 1);
+            __threadfence();   // order the observed counters before the reads below
+            __syncwarp();
+        }
+        __syncthreads();
+        SweepArgs b = a;
+        b.xin = (k & 1) ? x1 : x0;
+        b.xout = (k & 1) ? x0 : x1;
+        pca_site<NC, NB, 0, true>(b, ty * kBY + threadIdx.y, tx * kBX + threadIdx.x,
+                                  t0 + (uint32_t)k, G_s + tid);
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();   // the tile's labels and sums before its counter
+            atomicExch(done + j, (unsigned int)(k + 1));
+        }
+        item = s_next;
+    }
 }
 
 // Gibbs colour phase q.  A thread owns one "cell": a pair of columns
@@ -320,6 +403,76 @@ int batch_blocks_per_sm()
         cudaSuccess)
         nb = 1;
     return nb > 0 ? nb : 1;
+}
+
+namespace {
+
+template <int NC, int NB>
+cudaError_t launch_wave_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
+                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+{
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pca_wave_kernel<NC, NB>, kThreads,
+                                                          0);
+        if (e != cudaSuccess)
+            return e;
+        per_sm[dev] = n;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int tiles_x = (a.W + kBX - 1) / kBX;
+    const int tiles_y = (a.H + kBY - 1) / kBY;
+    const long long items = (long long)tiles_x * tiles_y * nsweeps;
+    if (items <= 0)
+        return cudaSuccess;
+    // at most the resident capacity: every block that takes an item runs
+    const long long cap = (long long)per_sm[dev] * sms;
+    const int grid = (int)(items < cap ? items : cap);
+    pca_wave_kernel<NC, NB><<<grid, dim3(kBX, kBY), 0, st>>>(a, x0, x1, nsweeps, tiles_x,
+                                                            tiles_y, done, grab, err);
+    return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t dispatch_wave(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int n, unsigned int *done,
+                          unsigned int *grab, int *err, cudaStream_t st)
+{
+    switch (chunk_class(a.m.L)) {
+    case 1: return launch_wave_t<1, NB>(a, x0, x1, n, done, grab, err, st);
+    case 2: return launch_wave_t<2, NB>(a, x0, x1, n, done, grab, err, st);
+    case 3: return launch_wave_t<3, NB>(a, x0, x1, n, done, grab, err, st);
+    case 4: return launch_wave_t<4, NB>(a, x0, x1, n, done, grab, err, st);
+    case 5: return launch_wave_t<5, NB>(a, x0, x1, n, done, grab, err, st);
+    case 8: return launch_wave_t<8, NB>(a, x0, x1, n, done, grab, err, st);
+    case 16: return launch_wave_t<16, NB>(a, x0, x1, n, done, grab, err, st);
+    default: return launch_wave_t<32, NB>(a, x0, x1, n, done, grab, err, st);
+    }
+}
+
+}  // namespace
+
+int wave_tiles(int H, int W)
+{
+    return ((W + kBX - 1) / kBX) * ((H + kBY - 1) / kBY);
+}
+
+cudaError_t launch_pca_wave(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
+                            unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+{
+    if (a.m.norm != 0)
+        return cudaErrorInvalidValue;   // the wavefront kernel runs the L0 price
+    return a.m.nbhd == 8 ? dispatch_wave<8>(a, x0, x1, nsweeps, done, grab, err, st)
+                         : dispatch_wave<4>(a, x0, x1, nsweeps, done, grab, err, st);
 }
 
 cudaError_t launch_pca_sweep(const SweepArgs &a, cudaStream_t st)
