@@ -299,9 +299,12 @@ typedef struct {
 typedef struct pcad_batch pcad_batch;
 
 /* Create a batch of n chains (one per job) on cuda_stream.  autotune != 0
- * times the tile height (4/8/16 rows of 32 sites per work item) and the
- * work order (costliest first or image order) on this batch and keeps the
- * fastest, cached per batch signature for the process. */
+ * times the tilings below on this batch and keeps the fastest, cached per
+ * batch signature for the process: one persistent launch per sweep with
+ * work items of 4/8/16 rows x 32 sites in cost order (order 1) or image
+ * order (order 0), or one wavefront launch per 16 sweeps with 4/8-row
+ * tiles (order 2; a tile's sweep starts when its 3 x 3 neighbourhood
+ * finished the previous one).  Without autotuning: 4 rows, order 1. */
 pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *cuda_stream,
                               pcad_batch **out);
 /* Advance every chain by nsweeps sweeps (asynchronous). */
@@ -313,12 +316,19 @@ pcad_status pcad_batch_run(pcad_batch *b, int nsweeps);
 pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m);
 /* Restart every chain from its observation (asynchronous). */
 pcad_status pcad_batch_reset(pcad_batch *b);
+/* Wait for the batch's queued work.  PCAD_ETIMEOUT: a bounded wait inside a
+ * wavefront launch gave up (the batch's results are invalid). */
 pcad_status pcad_batch_sync(pcad_batch *b);
+/* Choose the tiling: tile_rows a multiple of 4 in [4, 64], order 0 (image
+ * order), 1 (costliest first) or 2 (wavefront, one launch per 16 sweeps).
+ * Results do not depend on it.  Stream-ordered; PCAD_EINVAL otherwise. */
+pcad_status pcad_batch_set_tiling(pcad_batch *b, int tile_rows, int order);
 /* Current sample / posterior mean of chain i (host memory, as for a chain). */
 pcad_status pcad_batch_read_sample(pcad_batch *b, int i, uint8_t *host_out, int out_pitch);
 pcad_status pcad_batch_read_mean(pcad_batch *b, int i, float *host_out);
-/* Sweeps done, chosen tiling, grid size, autotuner's best slice time (ms per
- * 16 sweeps) and the FP64 re-draw count summed over chains. */
+/* Sweeps done, chosen tiling (tile rows, order 0/1/2 as for
+ * pcad_batch_set_tiling), per-sweep grid size, autotuner's best slice time
+ * (ms per 16 sweeps) and the FP64 re-draw count summed over chains. */
 pcad_status pcad_batch_info(pcad_batch *b, uint64_t *t, int *tile_rows, int *lpt_order,
                             int *grid, float *tune_ms, uint64_t *fp64_draws);
 void pcad_batch_destroy(pcad_batch *b);
@@ -338,8 +348,14 @@ pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cud
                                pcad_server **out);
 /* Queue a request for nsweeps sweeps (job->g_host is copied).  *id is its handle. */
 pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id);
-/* Admit, run one slice of slice_sweeps (1..16) sweeps, retire finished
- * requests; blocks until the slice is done. */
+/* Admit, run one slice of slice_sweeps (1..16) sweeps of every admitted
+ * request in one wavefront launch (tiles of 4 or 8 rows x 32 sites; a
+ * tile's sweep starts when its 3 x 3 neighbourhood finished the previous
+ * sweep), retire finished requests.  When the slice retires a request it
+ * returns after the slice is done (the outputs are then in host memory);
+ * otherwise it returns once the previous slice is done, so the host
+ * prepares the next slice while this one runs.  PCAD_ETIMEOUT: a bounded
+ * wait inside the launch gave up (the results of that slice are invalid). */
 pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, int *n_pending,
                              int *n_finished);
 /* *state: 0 queued, 1 running, 2 done.  When done and an output pointer is

@@ -19,6 +19,7 @@ from ._capi import (  # noqa: F401
     pcad_pca_run_noalloc, pcad_version,
     PcadJob, pcad_batch_create, pcad_batch_destroy, pcad_batch_info, pcad_batch_read_mean,
     pcad_batch_read_sample, pcad_batch_reset, pcad_batch_run, pcad_batch_sync,
+    pcad_batch_set_tiling,
     pcad_server_create, pcad_server_destroy, pcad_server_info, pcad_server_poll,
     pcad_server_step, pcad_server_submit,
 )

@@ -123,6 +123,7 @@ def _declare(L):
         "pcad_batch_run": [vp, ctypes.c_int],
         "pcad_batch_reset": [vp],
         "pcad_batch_sync": [vp],
+        "pcad_batch_set_tiling": [vp, ctypes.c_int, ctypes.c_int],
         "pcad_batch_read_sample": [vp, ctypes.c_int, u8p, ctypes.c_int],
         "pcad_batch_read_mean": [vp, ctypes.c_int, fp],
         "pcad_batch_info": [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -465,6 +466,12 @@ def pcad_batch_reset(h):
 
 def pcad_batch_sync(h):
     _check("pcad_batch_sync", lib().pcad_batch_sync(h))
+
+
+def pcad_batch_set_tiling(h, tile_rows: int, order: int):
+    """order 0: image order, 1: costliest first (one launch per sweep);
+    2: wavefront (one launch per 16 sweeps)."""
+    _check("pcad_batch_set_tiling", lib().pcad_batch_set_tiling(h, int(tile_rows), int(order)))
 
 
 def pcad_batch_read_sample(h, i: int, H: int, W: int) -> np.ndarray:

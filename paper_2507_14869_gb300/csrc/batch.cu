@@ -33,6 +33,13 @@ using namespace pcad;
 namespace {
 
 constexpr int kSlice = 16;        // sweeps per batch slice (one graph)
+constexpr int kOrderWave = 2;     // batch work order: one wavefront launch per slice
+// Tile height of the server's wavefront launches: 4 rows keep the slice's
+// critical path (one tile after another through its sweeps) short when
+// few tiles are active; 8 rows halve the per-tile synchronisation once the
+// active set has at least 4 tiles of 4 rows per resident block (measured on
+// single requests of 300^2..1376^2 and on a 50 req/s mix).
+constexpr int kServeTallTiles = 4;
 constexpr size_t kAlign = 256;
 constexpr int kTableBytes = 4096;  // 511 doubles
 
@@ -165,6 +172,81 @@ int grid_size()
     return sms * batch_blocks_per_sm();
 }
 
+// Wavefront work list in device memory: per-slot tile grids, the tiles of
+// one sweep and one done counter per tile, in one allocation (regrown).
+struct WaveBuf {
+    void *mem = nullptr;
+    size_t cap = 0;
+    WaveGeom *geom = nullptr;
+    WaveItem *items = nullptr;
+    unsigned int *done = nullptr;
+    int n_items = 0, n_tiles = 0;
+};
+
+// Fill `wb` for the given slots: slots in decreasing per-site cost, each
+// slot's tiles row-major, so a tile's neighbours are taken shortly before
+// or after it.  geom has one entry per slot of `d` (unused ones empty).
+pcad_status wave_upload(WaveBuf &wb, const std::vector<SlotDesc> &d, std::vector<int> active,
+                        int rows, cudaStream_t st)
+{
+    std::stable_sort(active.begin(), active.end(),
+                     [&](int a, int b) { return d[a].ncls > d[b].ncls; });
+    std::vector<WaveGeom> geom(d.size(), WaveGeom{0, 0, 0, rows});
+    std::vector<WaveItem> items;
+    long tiles = 0;
+    for (int i : active) {
+        WaveGeom g{(int)tiles, (d[i].W + 31) / 32, (d[i].H + rows - 1) / rows, rows};
+        geom[i] = g;
+        for (int j = 0; j < g.tiles_x * g.tiles_y; ++j)
+            items.push_back(WaveItem{i, j});
+        tiles += (long)g.tiles_x * g.tiles_y;
+        if (tiles > (1l << 30))
+            return set_error(PCAD_EINVAL, "too many tiles for one wavefront launch");
+    }
+    const size_t need = al(geom.size() * sizeof(WaveGeom)) + al(items.size() * sizeof(WaveItem)) +
+                        al((size_t)tiles * sizeof(unsigned int));
+    if (need > wb.cap) {
+        if (wb.mem)
+            B_TRY(cudaFreeAsync(wb.mem, st));
+        wb.mem = nullptr;
+        wb.cap = std::max(need, 2 * wb.cap);
+        B_TRY(cudaMallocAsync(&wb.mem, wb.cap, st));
+    }
+    char *p = (char *)wb.mem;
+    wb.geom = (WaveGeom *)p;
+    p += al(geom.size() * sizeof(WaveGeom));
+    wb.items = (WaveItem *)p;
+    p += al(items.size() * sizeof(WaveItem));
+    wb.done = (unsigned int *)p;
+    B_TRY(cudaMemcpyAsync(wb.geom, geom.data(), geom.size() * sizeof(WaveGeom),
+                          cudaMemcpyHostToDevice, st));
+    if (!items.empty())
+        B_TRY(cudaMemcpyAsync(wb.items, items.data(), items.size() * sizeof(WaveItem),
+                              cudaMemcpyHostToDevice, st));
+    wb.n_items = (int)items.size();
+    wb.n_tiles = (int)tiles;
+    return PCAD_OK;
+}
+
+// One wavefront launch of n sweeps over the list (counters zeroed first).
+pcad_status wave_issue(const WaveBuf &wb, const SlotDesc *slots, int n, int *grab, int *err,
+                       int grid, cudaStream_t st)
+{
+    B_TRY(cudaMemsetAsync(grab, 0, sizeof(int), st));
+    B_TRY(cudaMemsetAsync(wb.done, 0, (size_t)wb.n_tiles * sizeof(unsigned int), st));
+    B_TRY(launch_batch_wave(slots, wb.geom, wb.items, wb.n_items, n, wb.done,
+                            (unsigned int *)grab, err, grid, st));
+    return PCAD_OK;
+}
+
+int wave_grid()
+{
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms * batch_wave_blocks_per_sm();
+}
+
 struct TuneKey {
     int n;
     long sites[33];
@@ -205,7 +287,10 @@ struct pcad_batch {
     uint64_t t = 0;
     int grid = 0;
     int rows = 4;
-    int lpt = 1;
+    int lpt = 1;                     // work order: 0 image, 1 costliest first, 2 wavefront
+    WaveBuf wb;                      // order 2: the wavefront work list
+    int wgrid = 0;
+    int *d_err = nullptr;            // order 2: bounded-wait flag
     float tune_ms = 0.0f;
     cudaGraphExec_t graph = nullptr;
 };
@@ -217,16 +302,23 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
     std::vector<int> active(b->n);
     for (int i = 0; i < b->n; ++i)
         active[i] = i;
-    std::vector<WorkItem> items = make_items(b->desc, active, rows, lpt != 0);
-    if ((int)items.size() > b->n_items && b->d_items) {
-        B_TRY(cudaFreeAsync(b->d_items, b->stream));
-        b->d_items = nullptr;
+    if (lpt == kOrderWave) {
+        pcad_status st = wave_upload(b->wb, b->desc, active, rows, b->stream);
+        if (st != PCAD_OK)
+            return st;
+    } else {
+        std::vector<WorkItem> items = make_items(b->desc, active, rows, lpt != 0);
+        if ((int)items.size() > b->n_items && b->d_items) {
+            B_TRY(cudaFreeAsync(b->d_items, b->stream));
+            b->d_items = nullptr;
+        }
+        if (!b->d_items)
+            B_TRY(cudaMallocAsync((void **)&b->d_items, items.size() * sizeof(WorkItem),
+                                  b->stream));
+        B_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
+                              cudaMemcpyHostToDevice, b->stream));
+        b->n_items = (int)items.size();
     }
-    if (!b->d_items)
-        B_TRY(cudaMallocAsync((void **)&b->d_items, items.size() * sizeof(WorkItem), b->stream));
-    B_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
-                          cudaMemcpyHostToDevice, b->stream));
-    b->n_items = (int)items.size();
     b->rows = rows;
     b->lpt = lpt;
     if (b->graph) {
@@ -238,10 +330,16 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
 
 pcad_status batch_issue_slice(pcad_batch *b, cudaStream_t s)
 {
-    B_TRY(cudaMemsetAsync(b->d_grab, 0, kSlice * sizeof(int), s));
-    for (int k = 0; k < kSlice; ++k)
-        B_TRY(launch_batch_sweep(b->d_slots, b->d_items, b->n_items, b->d_grab + k, (uint32_t)k,
-                                 b->grid, s));
+    if (b->lpt == kOrderWave) {
+        pcad_status st = wave_issue(b->wb, b->d_slots, kSlice, b->d_grab, b->d_err, b->wgrid, s);
+        if (st != PCAD_OK)
+            return st;
+    } else {
+        B_TRY(cudaMemsetAsync(b->d_grab, 0, kSlice * sizeof(int), s));
+        for (int k = 0; k < kSlice; ++k)
+            B_TRY(launch_batch_sweep(b->d_slots, b->d_items, b->n_items, b->d_grab + k,
+                                     (uint32_t)k, b->grid, s));
+    }
     B_TRY(launch_batch_advance(b->d_slots, b->n, kSlice, s));
     return PCAD_OK;
 }
@@ -301,6 +399,17 @@ pcad_status batch_reset_state(pcad_batch *b)
     return PCAD_OK;
 }
 
+// Synchronise the stream and report a wavefront wait that gave up.
+pcad_status batch_check_err(pcad_batch *b)
+{
+    int err = 0;
+    B_TRY(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    B_TRY(cudaStreamSynchronize(b->stream));
+    if (err != 0)
+        return set_error(PCAD_ETIMEOUT, "wavefront wait for a neighbour tile gave up");
+    return PCAD_OK;
+}
+
 pcad_status batch_autotune(pcad_batch *b)
 {
     TuneKey key{};
@@ -318,32 +427,37 @@ pcad_status batch_autotune(pcad_batch *b)
     cudaEvent_t e0, e1;
     B_TRY(cudaEventCreate(&e0));
     B_TRY(cudaEventCreate(&e1));
-    const int cand_rows[3] = {4, 8, 16};
+    // per-sweep launches with 4/8/16-row tiles in cost or image order, and
+    // the wavefront with 4/8-row tiles
+    const int cands[8][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 0}, {8, 0}, {16, 0},
+                             {4, kOrderWave}, {8, kOrderWave}};
     TuneVal best{4, 1, 1e30f};
     pcad_status st = PCAD_OK;
-    for (int lpt = 1; lpt >= 0 && st == PCAD_OK; --lpt)
-        for (int r : cand_rows) {
-            st = batch_set_items(b, r, lpt);
-            if (st != PCAD_OK)
-                break;
-            st = batch_run_sweeps(b, kSlice);   // warm + graph
-            if (st == PCAD_OK && cudaEventRecord(e0, b->stream) != cudaSuccess)
-                st = set_error(PCAD_ECUDA, "event record");
-            if (st == PCAD_OK)
-                st = batch_run_sweeps(b, kSlice);
-            if (st == PCAD_OK && cudaEventRecord(e1, b->stream) != cudaSuccess)
-                st = set_error(PCAD_ECUDA, "event record");
-            float ms = 0.0f;
-            if (st == PCAD_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
-                                  cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
-                st = set_error(PCAD_ECUDA, "event timing");
-            if (st == PCAD_OK && ms < best.ms)
-                best = TuneVal{r, lpt, ms};
-            if (st == PCAD_OK)
-                st = batch_reset_state(b);
-            if (st != PCAD_OK)
-                break;
-        }
+    for (const auto &c : cands) {
+        const int r = c[0], lpt = c[1];
+        st = batch_set_items(b, r, lpt);
+        if (st != PCAD_OK)
+            break;
+        st = batch_run_sweeps(b, kSlice);   // warm + graph
+        if (st == PCAD_OK && cudaEventRecord(e0, b->stream) != cudaSuccess)
+            st = set_error(PCAD_ECUDA, "event record");
+        if (st == PCAD_OK)
+            st = batch_run_sweeps(b, kSlice);
+        if (st == PCAD_OK && cudaEventRecord(e1, b->stream) != cudaSuccess)
+            st = set_error(PCAD_ECUDA, "event record");
+        float ms = 0.0f;
+        if (st == PCAD_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+            st = set_error(PCAD_ECUDA, "event timing");
+        if (st == PCAD_OK)
+            st = batch_check_err(b);
+        if (st == PCAD_OK && ms < best.ms)
+            best = TuneVal{r, lpt, ms};
+        if (st == PCAD_OK)
+            st = batch_reset_state(b);
+        if (st != PCAD_OK)
+            break;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != PCAD_OK)
@@ -387,7 +501,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
     const size_t off_ctr = total;
     total += al(n * (2 * sizeof(uint32_t) + sizeof(unsigned long long)));
     const size_t off_grab = total;
-    total += al(kSlice * sizeof(int));
+    total += al((kSlice + 1) * sizeof(int));   // grab counters, wavefront error flag
     const size_t off_plane = total;
     total += al(max_plane * sizeof(float));
 
@@ -411,17 +525,23 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
     b->d_grab = (int *)(base + off_grab);
     b->d_plane = (float *)(base + off_plane);
     b->plane_floats = max_plane;
+    b->d_err = b->d_grab + kSlice;
     b->grid = grid_size();
+    b->wgrid = wave_grid();
     b->desc.resize(n);
     auto bail = [&](pcad_status st) {
         if (b->d_items)
             cudaFreeAsync(b->d_items, b->stream);
+        if (b->wb.mem)
+            cudaFreeAsync(b->wb.mem, b->stream);
         cudaFreeAsync(b->block, b->stream);
         cudaStreamSynchronize(b->stream);
         delete b;
         return st;
     };
     e = cudaMemsetAsync(base + off_ctr, 0, al(n * 16), b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(b->d_err, 0, sizeof(int), b->stream);
     if (e != cudaSuccess)
         return bail(set_error(PCAD_ECUDA, cudaGetErrorString(e)));
     for (int i = 0; i < n; ++i) {
@@ -509,8 +629,16 @@ pcad_status pcad_batch_sync(pcad_batch *b)
 {
     if (!b)
         return set_error(PCAD_EINVAL, "batch is NULL");
-    B_TRY(cudaStreamSynchronize(b->stream));
-    return PCAD_OK;
+    return batch_check_err(b);
+}
+
+pcad_status pcad_batch_set_tiling(pcad_batch *b, int tile_rows, int order)
+{
+    if (!b)
+        return set_error(PCAD_EINVAL, "batch is NULL");
+    if (tile_rows < 4 || tile_rows > 64 || tile_rows % 4 != 0 || order < 0 || order > kOrderWave)
+        return set_error(PCAD_EINVAL, "tile_rows a multiple of 4 in [4, 64], order 0..2");
+    return batch_set_items(b, tile_rows, order);
 }
 
 pcad_status pcad_batch_read_sample(pcad_batch *b, int i, uint8_t *host_out, int out_pitch)
@@ -579,6 +707,8 @@ void pcad_batch_destroy(pcad_batch *b)
         cudaGraphExecDestroy(b->graph);
     if (b->d_items)
         cudaFreeAsync(b->d_items, b->stream);
+    if (b->wb.mem)
+        cudaFreeAsync(b->wb.mem, b->stream);
     cudaFreeAsync(b->block, b->stream);
     cudaStreamSynchronize(b->stream);
     delete b;
@@ -615,10 +745,13 @@ struct pcad_server {
     uint32_t *d_t = nullptr, *d_budget = nullptr;
     unsigned long long *d_fp64 = nullptr;
     int *d_grab = nullptr;
-    WorkItem *d_items = nullptr;
-    int cap_items = 0, n_items = 0;
+    WaveBuf wb;                   // wavefront work list of the admitted requests
     bool items_dirty = true;
     int grid = 0;
+    int *d_err = nullptr;          // bounded-wait flag of the wavefront kernel
+    int *h_err = nullptr;          // pinned: the flag after each of the last two slices
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    bool in_flight = false;        // the previous slice may still be running
     std::vector<SlotDesc> desc;
     std::vector<uint64_t> slot_req;   // 0 = free
     std::deque<uint64_t> pending;
@@ -681,22 +814,26 @@ pcad_status server_admit(pcad_server *sv)
 pcad_status server_items(pcad_server *sv)
 {
     std::vector<int> active;
+    long tiles4 = 0;
     for (int i = 0; i < sv->max_slots; ++i)
-        if (sv->slot_req[i] != 0)
+        if (sv->slot_req[i] != 0) {
             active.push_back(i);
-    std::vector<WorkItem> items = make_items(sv->desc, active, 8, true);
-    if ((int)items.size() > sv->cap_items) {
-        if (sv->d_items)
-            B_TRY(cudaFreeAsync(sv->d_items, sv->stream));
-        sv->cap_items = std::max((int)items.size(), 2 * sv->cap_items);
-        B_TRY(cudaMallocAsync((void **)&sv->d_items, sv->cap_items * sizeof(WorkItem),
-                              sv->stream));
-    }
-    if (!items.empty())
-        B_TRY(cudaMemcpyAsync(sv->d_items, items.data(), items.size() * sizeof(WorkItem),
-                              cudaMemcpyHostToDevice, sv->stream));
-    sv->n_items = (int)items.size();
+            tiles4 += (long)((sv->desc[i].W + 31) / 32) * ((sv->desc[i].H + 3) / 4);
+        }
+    const int rows = tiles4 >= (long)kServeTallTiles * sv->grid ? 8 : 4;
+    pcad_status st = wave_upload(sv->wb, sv->desc, active, rows, sv->stream);
+    if (st != PCAD_OK)
+        return st;
     sv->items_dirty = false;
+    return PCAD_OK;
+}
+
+// Wait for slice `s` (its event) and report a bounded-wait timeout of it.
+pcad_status server_wait_slice(pcad_server *sv, uint64_t s)
+{
+    B_TRY(cudaEventSynchronize(sv->ev[s & 1]));
+    if (sv->h_err[s & 1] != 0)
+        return set_error(PCAD_ETIMEOUT, "wavefront wait for a neighbour tile gave up");
     return PCAD_OK;
 }
 
@@ -718,7 +855,7 @@ pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cud
     sv->stream = (cudaStream_t)cuda_stream;
     const size_t bytes = al(max_slots * sizeof(SlotDesc)) +
                          al(max_slots * (2 * sizeof(uint32_t) + sizeof(unsigned long long))) +
-                         al(kSlice * sizeof(int));
+                         al(kSlice * sizeof(int)) + al(sizeof(int));
     cudaError_t e = cudaMallocAsync(&sv->ctl, bytes, sv->stream);
     if (e != cudaSuccess) {
         delete sv;
@@ -733,17 +870,30 @@ pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cud
     sv->d_budget = sv->d_t + max_slots;
     p += al(max_slots * (2 * sizeof(uint32_t) + sizeof(unsigned long long)));
     sv->d_grab = (int *)p;
+    p += al(kSlice * sizeof(int));
+    sv->d_err = (int *)p;
     e = cudaMemsetAsync(sv->ctl, 0, bytes, sv->stream);
     if (e == cudaSuccess)
         e = cudaStreamSynchronize(sv->stream);
+    if (e == cudaSuccess)
+        e = cudaMallocHost((void **)&sv->h_err, 2 * sizeof(int));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        e = cudaEventCreateWithFlags(&sv->ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        for (int k = 0; k < 2; ++k)
+            if (sv->ev[k])
+                cudaEventDestroy(sv->ev[k]);
+        if (sv->h_err)
+            cudaFreeHost(sv->h_err);
         cudaFreeAsync(sv->ctl, sv->stream);
+        cudaStreamSynchronize(sv->stream);
         delete sv;
         return set_error(PCAD_ECUDA, cudaGetErrorString(e));
     }
+    sv->h_err[0] = sv->h_err[1] = 0;
     sv->desc.assign(max_slots, SlotDesc{});
     sv->slot_req.assign(max_slots, 0);
-    sv->grid = grid_size();
+    sv->grid = wave_grid();
     *out = sv;
     return PCAD_OK;
 }
@@ -791,15 +941,18 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
             return st;
     }
     int finished = 0, active = 0;
-    if (sv->n_items > 0) {
-        B_TRY(cudaMemsetAsync(sv->d_grab, 0, kSlice * sizeof(int), sv->stream));
-        for (int k = 0; k < slice_sweeps; ++k)
-            B_TRY(launch_batch_sweep(sv->d_slots, sv->d_items, sv->n_items, sv->d_grab + k,
-                                     (uint32_t)k, sv->grid, sv->stream));
+    if (sv->wb.n_items > 0) {
+        // one wavefront launch runs the slice for every admitted request
+        st = wave_issue(sv->wb, sv->d_slots, slice_sweeps, sv->d_grab, sv->d_err, sv->grid,
+                        sv->stream);
+        if (st != PCAD_OK)
+            return st;
         B_TRY(launch_batch_advance(sv->d_slots, sv->max_slots, (uint32_t)slice_sweeps,
                                    sv->stream));
-        ++sv->slices;
-        // harvest: chains whose budget is spent
+        const uint64_t s = sv->slices++;
+        B_TRY(cudaMemcpyAsync(sv->h_err + (s & 1), sv->d_err, sizeof(int),
+                              cudaMemcpyDeviceToHost, sv->stream));
+        // harvest: requests whose budget this slice spends
         for (int i = 0; i < sv->max_slots; ++i) {
             if (sv->slot_req[i] == 0)
                 continue;
@@ -834,7 +987,23 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
             sv->items_dirty = true;
             ++finished;
         }
-        B_TRY(cudaStreamSynchronize(sv->stream));
+        B_TRY(cudaEventRecord(sv->ev[s & 1], sv->stream));
+        // a finished request's outputs must be in host memory on return;
+        // otherwise only the previous slice is waited for, so the host
+        // prepares the next slice while this one runs
+        pcad_status ws = PCAD_OK;
+        if (sv->in_flight)
+            ws = server_wait_slice(sv, s - 1);
+        if (ws == PCAD_OK && finished > 0)
+            ws = server_wait_slice(sv, s);
+        sv->in_flight = finished == 0;
+        if (ws != PCAD_OK)
+            return ws;
+    } else if (sv->in_flight) {
+        sv->in_flight = false;
+        pcad_status ws = server_wait_slice(sv, sv->slices - 1);
+        if (ws != PCAD_OK)
+            return ws;
     }
     if (n_active)
         *n_active = active;
@@ -895,10 +1064,13 @@ void pcad_server_destroy(pcad_server *sv)
     for (auto &kv : sv->reqs)
         if (kv.second.mem)
             cudaFreeAsync(kv.second.mem, sv->stream);
-    if (sv->d_items)
-        cudaFreeAsync(sv->d_items, sv->stream);
+    if (sv->wb.mem)
+        cudaFreeAsync(sv->wb.mem, sv->stream);
     cudaFreeAsync(sv->ctl, sv->stream);
     cudaStreamSynchronize(sv->stream);
+    for (int k = 0; k < 2; ++k)
+        cudaEventDestroy(sv->ev[k]);
+    cudaFreeHost(sv->h_err);
     delete sv;
 }
 

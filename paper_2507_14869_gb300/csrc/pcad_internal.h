@@ -129,6 +129,30 @@ struct WorkItem {
 cudaError_t launch_batch_sweep(const SlotDesc *slots, const WorkItem *items, int n_items,
                                int *grab, uint32_t sweep_off, int grid, cudaStream_t s);
 
+// Tile grid of one slot for the wavefront batch kernel: tiles of `rows`
+// (a multiple of 4) x 32 sites, row-major; tile j's counter is done[base + j].
+struct WaveGeom {
+    int base;
+    int tiles_x, tiles_y;
+    int rows;
+};
+
+// One tile of one slot (one sweep of it; the list is repeated per sweep).
+struct WaveItem {
+    int slot;
+    int tile;
+};
+
+// nsweeps sweeps (indices *tdev + 0 .. nsweeps - 1 of every active slot,
+// each stopping at its budget) in one persistent launch of at most `grid`
+// blocks (the resident capacity, batch_wave_blocks_per_sm() x SMs); *grab
+// and done[] (every slot's tiles) are zeroed before it.  *err is set when a
+// bounded wait for a neighbour tile gives up.
+cudaError_t launch_batch_wave(const SlotDesc *slots, const WaveGeom *geom, const WaveItem *items,
+                              int n_items, int nsweeps, unsigned int *done, unsigned int *grab,
+                              int *err, int grid, cudaStream_t s);
+int batch_wave_blocks_per_sm();
+
 // For every active slot: *tdev += min(n, *budget - *tdev).
 cudaError_t launch_batch_advance(const SlotDesc *slots, int n_slots, uint32_t n, cudaStream_t s);
 

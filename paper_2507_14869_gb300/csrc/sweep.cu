@@ -207,30 +207,54 @@ __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, i
 // bit-identical to running the chain alone.
 // One tile of a chain for one (chunk class, neighbourhood) variant; not
 // inlined so each variant keeps the single-chain kernel's register budget.
-template <int NC, int NB>
+// L2_ONLY: the wavefront variant (labels of other tiles written in the same
+// launch).
+template <int NC, int NB, bool L2_ONLY>
 __device__ __noinline__ void batch_tile(const SweepArgs *sa, int row0, int col0, int rows,
                                         uint32_t t, float *Gcol)
 {
     const SweepArgs &a = *sa;
     const int c = col0 + (int)threadIdx.x;
     for (int rr = 0; rr < rows; rr += kBY)
-        pca_site<NC, NB>(a, row0 + rr + (int)threadIdx.y, c, t, Gcol);
+        pca_site<NC, NB, 0, L2_ONLY>(a, row0 + rr + (int)threadIdx.y, c, t, Gcol);
 }
 
-template <int NB>
+template <int NB, bool L2_ONLY = false>
 __device__ __forceinline__ void batch_dispatch(const SweepArgs *sa, int ncls, int row0, int col0,
                                                int rows, uint32_t t, float *Gcol)
 {
     switch (ncls) {
-    case 1: batch_tile<1, NB>(sa, row0, col0, rows, t, Gcol); break;
-    case 2: batch_tile<2, NB>(sa, row0, col0, rows, t, Gcol); break;
-    case 3: batch_tile<3, NB>(sa, row0, col0, rows, t, Gcol); break;
-    case 4: batch_tile<4, NB>(sa, row0, col0, rows, t, Gcol); break;
-    case 5: batch_tile<5, NB>(sa, row0, col0, rows, t, Gcol); break;
-    case 8: batch_tile<8, NB>(sa, row0, col0, rows, t, Gcol); break;
-    case 16: batch_tile<16, NB>(sa, row0, col0, rows, t, Gcol); break;
-    default: batch_tile<32, NB>(sa, row0, col0, rows, t, Gcol); break;
+    case 1: batch_tile<1, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 2: batch_tile<2, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 3: batch_tile<3, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 4: batch_tile<4, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 5: batch_tile<5, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 8: batch_tile<8, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 16: batch_tile<16, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    default: batch_tile<32, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
     }
+}
+
+// Chain descriptor -> sweep arguments of sweep t (the chunk class travels in
+// last_phase and the neighbourhood in sweep_off, which the tile code does
+// not read).
+__device__ __forceinline__ void slot_args(const SlotDesc &d, uint32_t t, SweepArgs &a)
+{
+    a = SweepArgs{};
+    a.xin = d.x[t & 1u];
+    a.xout = d.x[(t + 1u) & 1u];
+    a.g = d.g;
+    a.acc = d.acc;
+    a.fp64_draws = d.fp64_draws;
+    a.seed = d.seed;
+    a.H = d.H;
+    a.W = d.W;
+    a.pitch = d.pitch;
+    a.chain = d.chain;
+    a.burn_in = d.burn_in;
+    a.last_phase = d.ncls;
+    a.sweep_off = (uint32_t)d.nbhd;
+    a.m = d.m;
 }
 
 __global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *__restrict__ slots,
@@ -254,22 +278,7 @@ __global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *
                 const SlotDesc &d = slots[items[it].slot];
                 const uint32_t t = *d.tdev + sweep_off;
                 if (d.active && t < *d.budget) {
-                    SweepArgs a{};
-                    a.xin = d.x[t & 1u];
-                    a.xout = d.x[(t + 1u) & 1u];
-                    a.g = d.g;
-                    a.acc = d.acc;
-                    a.fp64_draws = d.fp64_draws;
-                    a.seed = d.seed;
-                    a.H = d.H;
-                    a.W = d.W;
-                    a.pitch = d.pitch;
-                    a.chain = d.chain;
-                    a.burn_in = d.burn_in;
-                    a.last_phase = d.ncls;      // carries the chunk class to the block
-                    a.sweep_off = (uint32_t)d.nbhd;
-                    a.m = d.m;
-                    s_args = a;
+                    slot_args(d, t, s_args);
                     s_t = t;
                     s_go = 1;
                 }
@@ -286,6 +295,96 @@ __global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *
             batch_dispatch<8>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid);
         else
             batch_dispatch<4>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid);
+    }
+}
+
+// Wavefront form of the batched sweep: nsweeps sweeps of every chain in one
+// persistent launch.  Items (sweep k, tile) are taken in increasing order,
+// sweep-major, so each item's 3 x 3 neighbourhood of tiles of the same chain
+// at sweep k - 1 was taken earlier by a resident block and the waits end
+// (each is bounded anyway: error flag).  A chain whose budget ends inside
+// the slice skips its remaining items without waiting; no later item waits
+// on a skipped one.  done[g.base + tile] counts the sweeps a tile finished
+// in this launch (zeroed before it).
+__global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
+    const SlotDesc *__restrict__ slots, const WaveGeom *__restrict__ geom,
+    const WaveItem *__restrict__ items, int n_items, int nsweeps, unsigned int *done,
+    unsigned int *grab, int *err)
+{
+    __shared__ float G_s[32 * kThreads];
+    __shared__ unsigned int s_next;
+    __shared__ int s_go;
+    __shared__ uint32_t s_t;
+    __shared__ SweepArgs s_args;
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const unsigned int total = (unsigned int)n_items * (unsigned int)nsweeps;
+    if (tid == 0)
+        s_next = atomicAdd(grab, 1u);
+    __syncthreads();
+    unsigned int item = s_next;
+    while (item < total) {
+        const int k = (int)(item / (unsigned int)n_items);
+        const WaveItem w = items[item - (unsigned int)k * (unsigned int)n_items];
+        const WaveGeom gm = geom[w.slot];
+        const int ty = w.tile / gm.tiles_x;
+        const int tx = w.tile - ty * gm.tiles_x;
+        __syncthreads();   // everyone has read s_next and is done with s_args
+        if (threadIdx.y == 0) {
+            if (threadIdx.x == 31)
+                s_next = atomicAdd(grab, 1u);
+            const SlotDesc &d = slots[w.slot];
+            uint32_t t = 0;
+            int go = 0;
+            if (threadIdx.x == 0 && d.active) {
+                t = *d.tdev + (uint32_t)k;
+                go = t < *d.budget;
+            }
+            go = __shfl_sync(0xFFFFFFFFu, go, 0);
+            bool ok = true;
+            if (go && k > 0 && threadIdx.x < 9) {
+                const int yy = ty + (int)threadIdx.x / 3 - 1;
+                const int xx = tx + (int)threadIdx.x % 3 - 1;
+                if (yy >= 0 && yy < gm.tiles_y && xx >= 0 && xx < gm.tiles_x) {
+                    const volatile unsigned int *c = done + gm.base + yy * gm.tiles_x + xx;
+                    long long spins = 0;
+                    while (*c < (unsigned int)k) {
+                        if (++spins > kWaveSpinLimit) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+            }
+            if (!ok)
+                atomicExch(err, 1);
+            if (threadIdx.x == 0) {
+                if (go) {
+                    slot_args(d, t, s_args);
+                    s_t = t;
+                }
+                s_go = go;
+            }
+            __threadfence();   // order the observed counters before the reads below
+            __syncwarp();
+        }
+        __syncthreads();
+        if (s_go) {
+            const int row0 = ty * gm.rows;
+            const int rows = min(gm.rows, (s_args.H - row0 + kBY - 1) / kBY * kBY);
+            if (s_args.sweep_off == 8u)
+                batch_dispatch<8, true>(&s_args, s_args.last_phase, row0, tx * kBX, rows, s_t,
+                                        G_s + tid);
+            else
+                batch_dispatch<4, true>(&s_args, s_args.last_phase, row0, tx * kBX, rows, s_t,
+                                        G_s + tid);
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();   // the tile's labels and sums before its counter
+                atomicExch(done + gm.base + w.tile, (unsigned int)(k + 1));
+            }
+        }
+        item = s_next;
     }
 }
 
@@ -394,6 +493,29 @@ cudaError_t launch_batch_advance(const SlotDesc *slots, int n_slots, uint32_t n,
     if (n_slots > 0)
         batch_advance_kernel<<<(n_slots + 127) / 128, 128, 0, s>>>(slots, n_slots, n);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch_wave(const SlotDesc *slots, const WaveGeom *geom, const WaveItem *items,
+                              int n_items, int nsweeps, unsigned int *done, unsigned int *grab,
+                              int *err, int grid, cudaStream_t s)
+{
+    const long long total = (long long)n_items * nsweeps;
+    if (total <= 0)
+        return cudaSuccess;
+    if (total >= (1ll << 32))
+        return cudaErrorInvalidValue;
+    batch_wave_kernel<<<(int)(total < grid ? total : grid), dim3(kBX, kBY), 0, s>>>(
+        slots, geom, items, n_items, nsweeps, done, grab, err);
+    return cudaGetLastError();
+}
+
+int batch_wave_blocks_per_sm()
+{
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_wave_kernel, kThreads, 0) !=
+        cudaSuccess)
+        nb = 1;
+    return nb > 0 ? nb : 1;
 }
 
 int batch_blocks_per_sm()

@@ -68,6 +68,30 @@ def test_batch_is_bit_identical_to_chains_alone(pc, autotune):
         pc.pcad_batch_destroy(b)
 
 
+@pytest.mark.parametrize("rows,order", [(4, 2), (8, 2), (12, 2), (16, 0), (8, 1)])
+def test_batch_tilings_are_bit_identical(pc, rows, order):
+    """Every tiling, the wavefront included, gives each chain's own result; a
+    run length that is not a multiple of 16 ends inside a wavefront slice."""
+    jobs = _jobs()
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_set_tiling(b, rows, order)
+        info = pc.pcad_batch_info(b)
+        assert (info["tile_rows"], info["lpt_order"]) == (rows, order)
+        pc.pcad_batch_run(b, 21)
+        pc.pcad_batch_run(b, 30)
+        pc.pcad_batch_sync(b)
+        for i, (g, m, seed, chain, burn) in enumerate(jobs):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, 51)
+            assert np.array_equal(pc.pcad_batch_read_sample(b, i, *g.shape), xs), i
+            assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
+        for bad in ((0, 2), (6, 1), (68, 0), (8, 3)):
+            with pytest.raises(pc.PcadError):
+                pc.pcad_batch_set_tiling(b, *bad)
+    finally:
+        pc.pcad_batch_destroy(b)
+
+
 def test_batch_chain_matches_oracle(pc):
     """One batched chain checked directly against the FP64 oracle."""
     jobs = _jobs()
@@ -153,3 +177,38 @@ def test_server_admission_waits_for_budget_and_slots(pc):
             pc.pcad_server_submit(sv, np.zeros((400, 400), np.uint8), m, 1, 0, 0, 10)
     finally:
         pc.pcad_server_destroy(sv)
+
+
+def test_server_wavefront_across_many_tiles(pc):
+    """Requests spanning hundreds of 4 x 32 tiles, so that a slice's sweeps of
+    one chain overlap inside the wavefront launch; budgets end inside slices."""
+    reqs = [
+        (_grey(11, 301, 257, 16, 1.0),
+         Model(L=16, nbhd=8, pair=TL, pair_coef=0.85, pair_T=2, sigma=1.0, inertia=2.0), 3, 1, 9, 48),
+        (_grey(12, 200, 333, 256, 20.0),
+         Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0), 4, 2, 5, 35),
+        (flip_noise(13, shapes_binary(14, 97, 640), 0.1),
+         Model(L=2, pair=POTTS, pair_coef=1.2, noise=FLIP, flip_p=0.1, inertia=1.0), 5, 3, 4, 40),
+        (_grey(15, 130, 7, 33, 3.0),
+         Model(L=33, nbhd=8, pair=POTTS, pair_coef=0.8, sigma=3.0, inertia=0.4), 6, 4, 2, 21),
+    ]
+    sv = pc.pcad_server_create(8, 1 << 31)
+    try:
+        ids, shapes = [], {}
+        for g, m, seed, chain, burn, n in reqs:
+            rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, n)
+            ids.append(rid)
+            shapes[rid] = g.shape
+        res = _serve_until_done(pc, sv, list(ids), shapes, slice_sweeps=16)
+        for rid, (g, m, seed, chain, burn, n) in zip(ids, reqs):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, n)
+            assert np.array_equal(res[rid][0], xs)
+            assert np.array_equal(res[rid][1], ms)
+        assert pc.pcad_server_info(sv)["hbm_used"] == 0
+    finally:
+        pc.pcad_server_destroy(sv)
+    # one of them straight against the oracle
+    g, m, seed, chain, burn, n = reqs[3]
+    x, acc, nacc, _ = oracle.run_chain(m, g, n, burn, seed=seed, chain=chain)
+    assert np.array_equal(res[ids[3]][0], x)
+    np.testing.assert_allclose(res[ids[3]][1], acc / nacc, rtol=1e-6, atol=0)
