@@ -280,7 +280,24 @@ bool uses_wave(const pcad_chain *ch)
 pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t st)
 {
     SweepArgs a = make_args(ch);
-    const bool tc = uses_tc(ch);
+    if (uses_tc(ch) && n > 0) {
+        // tensor-core wavefront: all n sweeps in one launch, or one launch
+        // per sweep when every sweep's state is needed (energy tracking)
+        const int per = ch->track.trace ? 1 : n;
+        for (int k = 0; k < n; k += per) {
+            a.sweep_off = (uint32_t)(off0 + k);
+            CUDA_TRY(cudaMemsetAsync(ch->wave, 0,
+                                     (size_t)(ch->wave_tiles + 1) * sizeof(unsigned int), st));
+            CUDA_TRY(launch_pca_tc(a, ch->x[cur], ch->x[cur ^ 1], per, ch->wave,
+                                   ch->wave + ch->wave_tiles, ch->err, st));
+            if (per & 1)
+                cur ^= 1;
+            if (ch->track.trace)
+                CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
+                                       ch->esums, nullptr, ch->track, ch->tdev, a.sweep_off, st));
+        }
+        return PCAD_OK;
+    }
     if (uses_wave(ch) && n > 0) {
         // one persistent launch for all n sweeps: counters zeroed first
         a.sweep_off = (uint32_t)off0;
@@ -309,7 +326,7 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
         if (ch->model.sampler == PCAD_SAMPLER_PCA) {
             a.xin = ch->x[cur];
             a.xout = ch->x[cur ^ 1];
-            CUDA_TRY(tc ? launch_pca_tc(a, ch->err, st) : launch_pca_sweep(a, st));
+            CUDA_TRY(launch_pca_sweep(a, st));
             cur ^= 1;
             if (ch->track.trace)
                 CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
@@ -795,8 +812,8 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         return fail(PCAD_EINVAL, "the wavefront kernel needs the PCA sampler and the L0 price");
     if (kind == PCAD_KERNEL_TENSOR &&
         (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_tc_eligible(ch->dm)))
-        return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, L >= 64, "
-                                 "T <= 65 and its banded operands within shared memory");
+        return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, 64 <= L <= 256, "
+                                 "T <= 33 and the L0 inertia price");
     if (kind != ch->kernel && ch->graph) {
         cudaStreamSynchronize(ch->stream);
         cudaGraphExecDestroy(ch->graph);

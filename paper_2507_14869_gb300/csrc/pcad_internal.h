@@ -207,14 +207,17 @@ cudaError_t launch_pca_wave(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int ns
                             unsigned int *done, unsigned int *grab, int *err, cudaStream_t s);
 int wave_tiles(int H, int W);
 
-// Tensor-core lazy-PCA sweep (prior sums by tcgen05.mma).  Eligible models:
-// L >= kTcMinLabels and truncation T <= kTcMaxT (the banded window must fit
-// shared memory).  *err is set (1: timeout, 2: misaligned shared memory)
-// when the kernel gives up.
+// Tensor-core lazy-PCA sweeps (windowed prior sums by tcgen05.mma), run as
+// a wavefront like launch_pca_wave: nsweeps sweeps from plane x0, done (one
+// counter per 4 x 32 tile) and grab zero on entry.  Eligible models: L in
+// [kTcMinLabels, 256], truncation T <= kTcMaxT (the 128-label window then
+// holds every tent of a 64-bin histogram), L0 price.  *err is set (1: a
+// bounded wait gave up, 2: misaligned shared memory).
 constexpr int kTcMinLabels = 64;
-constexpr int kTcMaxT = 65;
+constexpr int kTcMaxT = 33;
 bool pca_tc_eligible(const DevModel &m);
-cudaError_t launch_pca_tc(const SweepArgs &a, int *err, cudaStream_t s);
+cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
+                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t s);
 
 // TMA descriptor of a uint8 plane (box 96 x 48); false if the driver refuses.
 bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);

@@ -1,55 +1,54 @@
 // Lazy-PCA sweep with the prior sums on the tensor cores (Section 5.2, Eq.
-// posterior_pca_transition_matrix), for models with many labels.
+// posterior_pca_transition_matrix), for truncated-linear priors with many
+// labels.
 //
 // For label s the truncated-linear prior sum is
 //   P(s) = sum_j min(|x_j - s|, T) = n T - Pb(s),  Pb(s) = sum_j max(T - |x_j - s|, 0),
 // n the number of neighbours inside the image.  n T is the same for every
 // label of the site and cancels in the normalisation, so the weights are
 // built from Pb: w(s) = 2^(alpha (g - s)^2 + mu Pb(s)), mu = c log2(e).
-// Pb is the product of the site's neighbour-label histogram h (a row with at
-// most NB nonzero counts) and the banded Toeplitz matrix
-// K(t, s) = max(T - |t - s|, 0): a contraction whose operands are small
-// integers, exact with FP16 inputs and FP32 accumulation.
+// Every tent max(T - |x_j - s|, 0) is zero farther than T - 1 from x_j, so
+// Pb lives in a window of labels around the neighbours' labels:
 //
-// 128 sites (4 image rows x 32 columns) form the M dimension of one
-// tcgen05.mma, one TMEM lane per site.  Labels form N in tiles of 64.  K is
-// banded, so a label tile [s0, s0 + 64) only needs histogram columns
-// (s0 - T, s0 + 64 + T); with the histogram padded by o >= T - 1 columns on
-// both sides, the window [s0 - o, s0 + 64 + o) of every label tile meets
-// the same 64 x (64 + 2o) block of K, so one small B operand serves all
-// tiles.  For L = 256, T = 30: 32 MMAs of 128 x 64 x 16 per 128 sites.
+//   * window: each site takes its own base b = 8 m + T - 1 with
+//     m = floor((x_min - T + 1) / 8), x_min the smallest neighbour label, so
+//     b <= x_min < b + 8.  Neighbour labels x_j - b in [0, 64) go into a
+//     64-bin histogram h (at most NB nonzero counts); the window's labels
+//     are s = 8 m + c, c in [0, 128), and
+//       Pb(8 m + c) = sum_k h(k) K(k, c),  K(k, c) = max(T - |c - (T - 1) - k|, 0),
+//     which covers the whole support of the histogram's tents for T <= 33.
+//     One tcgen05.mma chain (M = 128 sites, N = 128 window labels, K = 64
+//     bins: four 128 x 128 x 16 steps) computes it; the operands are small
+//     integers, exact with FP16 inputs and FP32 accumulation.  K is the same
+//     matrix for every site and stays in shared memory.
+//   * outliers: neighbours with x_j - b >= 64 (wide neighbourhoods, image
+//     edges) add their tents on the CUDA cores in both label ranges.
+//   * outside the window Pb is the outliers' part only (zero for most
+//     sites): w(s) = 2^(alpha (g - s)^2), no prior arithmetic.
 //
-// One persistent CTA per SM runs a four-stage warp-specialised pipeline over
-// its tiles (128-site tiles strided over the grid), double-buffered in the
-// histogram operand A (shared memory), the accumulators (TMEM) and the
-// chunk sums G, with a ring of four slots of staged site inputs:
-//   * loader warps (4, one thread per site): read the site's labels,
-//     observation and uniform into the stage ring, write its histogram row
-//     of A[i & 1] (clearing the row's entries of tile i - 2) once the MMAs
-//     of tile i - 2 completed, arrive on barA and barS;
-//   * MMA warp (one elected thread): once A is written (barA) and pass 1 of
-//     tile i - 2 has read TMEM buffer i & 1 (barP), issue tile i's 32 MMAs
-//     into that buffer and commit them to barM;
-//   * pass-1 warps (16, four threads per site, one per quarter of the label
-//     groups): wait barM, read their part of the site's accumulator row
-//     (tcgen05.ld, 32 labels per load), evaluate exponent, exp2 and the
-//     Kahan chunk prefix sums into G[i & 1], arrive on barP;
-//   * selector warps (4, one thread per site): wait barS and barP, join the
-//     parts' prefix sums, add the inertia correction, select chunk and label
-//     (certified, pass 2 on the CUDA cores), arrive on barG (G free),
-//     re-draw uncertain draws in FP64 by the warp, write the label and the
-//     accumulator, arrive on barF (stage slot free).
-// Each buffer is released by the stage that last reads it, so no cycle of
-// the dependency graph runs through all four stages.  The tensor core, the
-// exp2/CDF work and the selection of consecutive tiles overlap.  Every wait
-// is bounded: on timeout a warp records an error flag and leaves its loop
-// (the others then time out in turn), the MMA warp waits (bounded) for the
-// MMAs it issued, and TMEM is freed before return.
+// The window is chunk-aligned (8 | 8 m), so every label chunk of the draw is
+// either a window chunk or an outside chunk of the site.  Pass 1 writes the
+// chunk sums in label order into shared memory; they are prefix-summed
+// (Kahan) and the certified inverse-CDF selection of the CUDA-core kernel
+// runs on them (same uniforms), with pass 2 recomputing the chosen chunk's
+// weights from exact prior sums on the CUDA cores (bit-identical: Pb is the
+// same integer either way and the weight formula is the same).
 //
-// The draw is the certified FP32 inverse CDF of the CUDA-core kernel (same
-// uniforms, same selection) with the error bound of this formulation; the
-// four parts' prefix sums are joined by three more roundings (24u of
-// summation).
+// CTA: 4 warpgroups (512 threads), one per SM; each group owns one 4 x 32
+// tile at a time, its histogram operand (16 KB) and 128 TMEM columns, so
+// four tiles are in flight.  A group: loads its sites, writes their
+// histogram rows, one thread issues the 4 MMAs and commits them to the
+// group's mbarrier; while the tensor core runs, the group computes the
+// outside chunks; then it reads the window from TMEM (4 x tcgen05.ld of 32
+// columns), selects, re-draws uncertain draws in FP64 and writes.
+//
+// Work items (sweep k, tile) are taken in increasing order, sweep-major,
+// from an atomic counter; item (k, tile) waits until the 3 x 3 tiles around
+// it finished sweep k - 1 (done[] counts finished sweeps per tile), so one
+// launch runs many sweeps with no sweep-wide barrier (as the wavefront
+// CUDA-core kernel).  Every item waited on was taken earlier by a resident
+// group, so the waits end; each wait is bounded anyway (error flag), and
+// TMEM is freed before return.
 #include <cuda_fp16.h>
 
 #include "async_ptx.cuh"
@@ -59,84 +58,40 @@ namespace pcad {
 
 namespace {
 
-constexpr int kSites = 128;                   // tile: 4 rows x 32 columns = MMA M
+constexpr int kSites = 128;                 // tile: 4 rows x 32 columns = MMA M = TMEM lanes
 constexpr int kTileRows = 4;
-// Warp roles: loader warps 0-3, pass-1 warps 4 .. 4 + 4 kP1Parts - 1,
-// selector warps (4), MMA warp.  Pass-1 warp 4 + 4h + q handles label part
-// h of the sites in TMEM lanes 32 q .. 32 q + 31 (a warp reaches the lane
-// quarter given by its index mod 4).
-constexpr int kLoadWarp0 = 0;
-constexpr int kP1Warp0 = 4;
-#ifndef PCAD_TC_PARTS
-#define PCAD_TC_PARTS 2
-#endif
-constexpr int kP1Parts = PCAD_TC_PARTS;
-constexpr int kSelWarp0 = kP1Warp0 + 4 * kP1Parts;
-constexpr int kMmaWarp = kSelWarp0 + 4;
-constexpr int kLoadThreads = kSites;
-constexpr int kSelThreads = kSites;
-constexpr int kTcThreads = (kMmaWarp + 1) * 32;
-constexpr int kLabelTile = 64;                // MMA N
-constexpr int kASlab = kSites * 128;          // bytes of a 64-column slab of A (128 rows)
-constexpr int kBSlab = kLabelTile * 128;      // bytes of a 64-column slab of B (64 rows)
-constexpr long long kTcSpinLimit = 20000000;  // ~1 s of polling
-constexpr uint32_t kIdesc = idesc_f16_f32(kSites, kLabelTile);
-constexpr int kSmemPerSM = 233472;            // shared memory of one SM (228 KB)
-constexpr int kSmemReserved = 1024;           // reserved per resident CTA
-constexpr int kSmemMax = kSmemPerSM - kSmemReserved;
-constexpr int kTmemCols = 512;
+constexpr int kGroups = 4;                  // warpgroups per CTA, one tile each
+constexpr int kThr = kGroups * kSites;      // 512 threads
+constexpr int kWin = 128;                   // window labels = MMA N = TMEM columns per group
+constexpr int kBins = 64;                   // histogram bins = MMA K (4 steps of 16)
+constexpr int kWinChunks = kWin / kChunk;   // 16
+constexpr int kOpBytes = kSites * kBins * 2;   // 16 KB: one operand (128 rows x 128 bytes)
+constexpr int kTmemCols = kGroups * kWin;   // 512
+constexpr long long kTcSpinLimit = 20000000;
+constexpr uint32_t kIdesc = idesc_f16_f32(kSites, kWin);
+constexpr float kNoLabel = -4096.0f;        // unused outlier slot: its tent is zero everywhere
 
-// Shape of one model's operands (host-computed).
-struct TcLayout {
-    int o;           // histogram padding: multiple of 16, >= T - 1
-    int kw;          // K window of one label tile: 64 + 2o
-    int nt;          // label tiles
-    int a_slabs;     // 64-column slabs of one A buffer (nt * 64 + 2o columns)
-    int b_slabs;     // 64-column slabs of B (kw columns)
-    int tmem_cols;   // accumulator columns of one buffer (power of two >= nt * 64)
-    int nc;          // 8-label chunks, ceil(L / 8)
-    int ng;          // 32-label groups, ceil(L / 32); part h takes [h ng / 4, (h + 1) ng / 4)
-    int smem;        // dynamic shared memory bytes
-};
+// Shared memory: B (16 KB), A[4] (64 KB), G [chunk][thread] floats, then
+// mbarriers, the groups' work items and the TMEM base.
+constexpr int kOffB = 0;
+constexpr int kOffA = kOpBytes;
+constexpr int kOffG = kOffA + kGroups * kOpBytes;
 
-// Ring of staged site inputs.
-constexpr int kRing = 4;
-constexpr int kStageBytes = 2048;   // per slot: see TcSmem
-
-TcLayout tc_layout(int L, int T)
+__host__ __device__ constexpr int tc_smem_bytes(int nc)
 {
-    TcLayout t{};
-    t.o = (T - 1 + 15) / 16 * 16;
-    t.kw = kLabelTile + 2 * t.o;
-    t.nt = (L + kLabelTile - 1) / kLabelTile;
-    t.a_slabs = (t.nt * kLabelTile + 2 * t.o + 63) / 64;
-    t.b_slabs = (t.kw + 63) / 64;
-    t.tmem_cols = 32;
-    while (t.tmem_cols < t.nt * kLabelTile)
-        t.tmem_cols *= 2;
-    t.nc = (L + kChunk - 1) / kChunk;
-    t.ng = (L + 31) / 32;
-    t.smem = 2 * t.a_slabs * kASlab + t.b_slabs * kBSlab + 2 * t.nc * kSites * 4 +
-             kRing * kStageBytes + 8 * (6 + 4 * kP1Parts + 2 * kRing) + 64;
-    // no more resident CTAs than TMEM can hold (two buffers each): pad the
-    // shared memory request
-    const int max_ctas = kTmemCols / (2 * t.tmem_cols);
-    const int min_smem = kSmemPerSM / (max_ctas + 1) - kSmemReserved + 1;
-    if (t.smem < min_smem)
-        t.smem = (min_smem + 15) / 16 * 16;
-    return t;
+    return kOffG + nc * kThr * 4 + 8 * kGroups + 4 * kGroups + 16;
 }
 
-// Byte offset of element (row, k) of a K-major, 128-byte-swizzled operand
-// stored as 64-column slabs of `slab` bytes (8-row groups 1024 bytes apart).
-__device__ __forceinline__ uint32_t sw128_offset(int row, int k, int slab)
+// Byte offset of element (row, k), k < 64, of a K-major operand in the
+// 128-byte swizzled layout (8-row groups 1024 bytes apart, the 16-byte
+// chunks of row r stored at chunk ^ (r mod 8)).
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k)
 {
-    return (uint32_t)((k >> 6) * slab + (row >> 3) * 1024 + (row & 7) * 128 +
-                      ((((k & 63) >> 3) ^ (row & 7)) << 4) + ((k & 7) << 1));
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 3) ^ (row & 7))) << 4) +
+                      ((k & 7) << 1));
 }
 
-// Weight of one label from the banded prior sum Pb (an exact integer):
-// 2^(alpha dg^2 + mu Pb).
+// Weight of one label from its tent sum Pb (an exact integer): 2^(alpha dg^2 + mu Pb).
 __device__ __forceinline__ float label_wb(float alpha, float mu, float Pb, float dg)
 {
     const float q = __fmul_rn(dg, dg);
@@ -144,658 +99,560 @@ __device__ __forceinline__ float label_wb(float alpha, float mu, float Pb, float
     return ex2_ftz(v);
 }
 
-// Inclusive prefix sums of chunk c's weights on the CUDA cores, bit-identical
-// to the tensor-core pass: Pb = NB T - P with P from the half-precision prior
-// (missing neighbours give T - T = 0 in both).
+// Exact tent sum of label s over the neighbours (missing ones, label 1024,
+// and unused outlier slots contribute zero).
+template <int N>
+__device__ __forceinline__ float tent_sum(const float (&x)[N], float Tf, float s, int n = N)
+{
+    float P = 0.0f;
+#pragma unroll
+    for (int j = 0; j < N; ++j)
+        if (j < n)
+            P = __fadd_rn(P, fmaxf(__fsub_rn(Tf, fabsf(__fsub_rn(s, x[j]))), 0.0f));
+    return P;
+}
+
+// Tile counters: published with a release store by one thread after a
+// group barrier, observed with relaxed loads and an acquire fence.
+__device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu()
+{
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+
+// Per-site state of one item.
 template <int NB>
-__device__ __forceinline__ void chunk_prefix_b(const DevModel &m, float mu, float nbT,
-                                               const __half2 (&xh)[NB], __half2 T2, float gf,
-                                               int c, float (&p)[kChunk])
-{
-    const float sbf = (float)(c * kChunk);
-    const __half2 sb2 = __float2half2_rn(sbf);
-    __half2 xr[NB];
-#pragma unroll
-    for (int j = 0; j < NB; ++j)
-        xr[j] = __hsub2(xh[j], sb2);
-    const float dgb = gf - sbf;
-    float S = 0.0f;
-#pragma unroll
-    for (int kk = 0; kk < kChunk; kk += 2) {
-        const float2 P = prior_pair<NB>(xr, __floats2half2_rn((float)kk, (float)(kk + 1)), T2);
-        float e0 = label_wb(m.alpha, mu, __fsub_rn(nbT, P.x), dgb - (float)kk);
-        float e1 = label_wb(m.alpha, mu, __fsub_rn(nbT, P.y), dgb - (float)(kk + 1));
-        if (c * kChunk + kk >= m.L)
-            e0 = 0.0f;
-        if (c * kChunk + kk + 1 >= m.L)
-            e1 = 0.0f;
-        S = __fadd_rn(S, e0);
-        p[kk] = S;
-        S = __fadd_rn(S, e1);
-        p[kk + 1] = S;
-    }
-}
-
-// Weight of the single label s (inertia correction), same formula.
-template <int NB>
-__device__ __forceinline__ float single_wb(const DevModel &m, float mu, float nbT,
-                                           const float (&xn)[NB], float gf, int s)
-{
-    const float sf = (float)s;
-    float P = fminf(fabsf(xn[0] - sf), m.Tf);
-#pragma unroll
-    for (int j = 1; j < NB; ++j)
-        P = __fadd_rn(P, fminf(fabsf(xn[j] - sf), m.Tf));
-    return label_wb(m.alpha, mu, __fsub_rn(nbT, P), gf - sf);
-}
-
-// Pass 1 over one group of 32 labels [32 grp, 32 grp + 32) whose banded
-// prior sums are in pb: four chunk sums, Kahan-accumulated into G and stored
-// as chunk prefix sums (stride kSites).  MASK zeroes labels >= L.
-template <bool MASK>
-__device__ __forceinline__ void group_pass(const DevModel &m, float mu, float gf, int grp,
-                                           const uint32_t (&pb)[32], int nc, float *Gcol,
-                                           float &G, float &comp)
-{
-    const float dgb = gf - (float)(grp * 32);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        float S = 0.0f;
-#pragma unroll
-        for (int k = 0; k < kChunk; ++k) {
-            const int kk = i * kChunk + k;
-            float e = label_wb(m.alpha, mu, __uint_as_float(pb[kk]), dgb - (float)kk);
-            if (MASK && grp * 32 + kk >= m.L)
-                e = 0.0f;
-            S = __fadd_rn(S, e);
-        }
-        const float y = __fsub_rn(S, comp);
-        const float tt = __fadd_rn(G, y);
-        comp = __fsub_rn(__fsub_rn(tt, G), y);
-        G = tt;
-        const int c = grp * 4 + i;
-        if (c < nc)
-            Gcol[c * kSites] = G;
-    }
-}
-
-// Shared-memory carve-up of one CTA:
-//   A[2]      histogram operands (buffer b at A0 + b * a_bytes)
-//   B         band block of K
-//   G[2]      chunk prefix sums [chunk][site] (buffer b at G0 + b * g_elems),
-//             each label part's chunks prefix-summed from its own start
-//   stage[4]  site inputs: uniform u32[128], neighbour labels u8[8][128],
-//             missing-neighbour bits u8[128], label u8[128], observation u8[128]
-//   barriers  barA[2] (A written, count kLoadThreads), barM[2][4] (MMAs of
-//             label tile / part h done, by commit), barP[2][4] (part h read
-//             its TMEM columns and wrote its chunk sums, kSites),
-//             barG[2] (selection done with G, kSelThreads), barS[4] (stage
-//             written, kLoadThreads), barF[4] (selection done with the stage,
-//             kSelThreads)
-struct TcSmem {
-    uint8_t *A0;
-    int a_bytes;
-    uint8_t *B;
-    float *G0;
-    int g_elems;
-    uint8_t *S0;
-    uint64_t *barA, *barM, *barP, *barG, *barS, *barF;
-    uint32_t *tmem_slot;
+struct TcSite {
+    SiteIn<NB> in;
+    float xn[NB];       // neighbour labels (missing: 1024)
+    float xo[NB];       // outlier labels (unused: kNoLabel)
+    int n_out;          // outliers of this site
+    int m;              // window = chunks [m, m + 16)
+    float gf;
 };
 
-constexpr int kStageXn = 4 * kSites;
-constexpr int kStageMiss = kStageXn + 8 * kSites;
-constexpr int kStageXi = kStageMiss + kSites;
-constexpr int kStageG = kStageXi + kSites;
-static_assert(kStageG + kSites <= kStageBytes, "stage slot");
-
-__device__ __forceinline__ TcSmem carve(uint8_t *base, const TcLayout &lay)
-{
-    TcSmem s;
-    s.a_bytes = lay.a_slabs * kASlab;
-    s.A0 = base;
-    s.B = base + 2 * s.a_bytes;
-    s.G0 = reinterpret_cast<float *>(s.B + lay.b_slabs * kBSlab);
-    s.g_elems = lay.nc * kSites;
-    s.S0 = reinterpret_cast<uint8_t *>(s.G0 + 2 * s.g_elems);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(s.S0 + kRing * kStageBytes);
-    s.barA = bars;                        // [b]
-    s.barM = bars + 2;                    // [b * kP1Parts + h]
-    s.barP = s.barM + 2 * kP1Parts;       // [b * kP1Parts + h]
-    s.barG = s.barP + 2 * kP1Parts;       // [b]
-    s.barS = s.barG + 2;                  // [slot]
-    s.barF = s.barS + kRing;              // [slot]
-    s.tmem_slot = reinterpret_cast<uint32_t *>(s.barF + kRing);
-    return s;
-}
-
-// Label groups [g_lo, g_hi) of pass-1 part h.
-__host__ __device__ __forceinline__ int part_lo(int ng, int h)
-{
-    return h * ng / kP1Parts;
-}
-
-__device__ __forceinline__ void tile_site(const SweepArgs &a, int tiles_x, int i, int site, int &r,
-                                          int &c)
-{
-    const int tile = (int)blockIdx.x + i * (int)gridDim.x;
-    r = (tile / tiles_x) * kTileRows + (site >> 5);
-    c = (tile % tiles_x) * 32 + (site & 31);
-}
-
-// Waits for phase `use` of a barrier that completes once per use (use 0, 1, ...).
-__device__ __forceinline__ bool wait_use(uint64_t *bar, int use)
-{
-    return mbar_wait_bounded(bar, (uint32_t)use & 1u, kTcSpinLimit);
-}
-
-// Site inputs of one site from a stage slot.
+// Window and histogram entries of one site: per neighbour the A byte offset
+// it sets (~0u: none) and the count stored there (one store per distinct
+// in-window label, of its multiplicity).
 template <int NB>
-__device__ __forceinline__ void stage_get(const uint8_t *S, int site, SiteIn<NB> &in)
+__device__ __forceinline__ void site_window(TcSite<NB> &st, int T, int row, bool valid,
+                                            uint32_t (&off)[NB], int (&cnt)[NB])
 {
-    in.ub = reinterpret_cast<const uint32_t *>(S)[site];
-    const uint32_t miss = S[kStageMiss + site];
+    int xmin = kMissingLabelI;
 #pragma unroll
     for (int j = 0; j < NB; ++j)
-        in.xni[j] = ((miss >> j) & 1u) ? kMissingLabelI : (int)S[kStageXn + j * kSites + site];
-    in.xi = S[kStageXi + site];
-    in.g = S[kStageG + site];
-}
-
-// Loader warps: inputs into the stage ring, histogram rows into A.
-template <int NB>
-__device__ __forceinline__ bool load_role(const SweepArgs &a, const TcLayout &lay,
-                                          const TcSmem &sm, int n_my, int tiles_x)
-{
-    const int site = (int)threadIdx.x - kLoadWarp0 * 32;
-    const uint32_t t = sweep_index(a);
-    // A entries this row set for the tiles two back (this iteration's
-    // buffer) and one back (~0u: none)
-    uint32_t off2[NB], off1[NB];
+        xmin = min(xmin, st.in.xni[j]);
+    // no neighbour inside the image: every tent sum is zero, any window works
+    st.m = xmin < kMissingLabelI ? (xmin - T + 1) >> 3 : 0;
+    const int b = 8 * st.m + T - 1;
+    st.n_out = 0;
 #pragma unroll
-    for (int j = 0; j < NB; ++j)
-        off2[j] = off1[j] = ~0u;
-    for (int i = 0; i < n_my; ++i) {
-        const int b = i & 1;
-        const int q = i & (kRing - 1);
-        int r, c;
-        tile_site(a, tiles_x, i, site, r, c);
-        const bool valid = r < a.H && c < a.W;
-        SiteIn<NB> in{};
-        if (valid)
-            load_site<NB>(a, a.xin, r, c, kTagPCA, t, in);
-        if (i >= 2 && !wait_use(&sm.barM[b * kP1Parts + kP1Parts - 1], (i - 2) >> 1))  // A[b] read
-            return false;
-        if (i >= kRing && !wait_use(&sm.barF[q], (i - kRing) >> 2))  // stage slot free
-            return false;
-        uint8_t *S = sm.S0 + q * kStageBytes;
-        reinterpret_cast<uint32_t *>(S)[site] = in.ub;
-        uint32_t miss = 0;
+    for (int j = 0; j < NB; ++j) {
+        st.xo[j] = kNoLabel;
+        off[j] = ~0u;
+        cnt[j] = 0;
+    }
 #pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            const bool m = in.xni[j] >= kMissingLabelI;
-            miss |= (m ? 1u : 0u) << j;
-            S[kStageXn + j * kSites + site] = m ? 0 : (uint8_t)in.xni[j];
-        }
-        S[kStageMiss + site] = (uint8_t)miss;
-        S[kStageXi + site] = (uint8_t)in.xi;
-        S[kStageG + site] = (uint8_t)in.g;
-        uint8_t *A = sm.A0 + b * sm.a_bytes;
+    for (int j = 0; j < NB; ++j) {
+        const int x = st.in.xni[j];
+        const bool inside = valid && x < kMissingLabelI;
+        const int kb = x - b;
+        if (inside && kb >= kBins) {
+            // outlier: kept for the CUDA-core tents (slots filled in order)
 #pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (off2[j] != ~0u)
-                *reinterpret_cast<__half *>(A + off2[j]) = __ushort_as_half((unsigned short)0);
-        // one store per distinct neighbour label, of its multiplicity
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            off2[j] = off1[j];
-            off1[j] = ~0u;
-            bool first = valid && in.xni[j] < kMissingLabelI;
-            int cnt = 1;
+            for (int o = 0; o < NB; ++o)
+                if (o == st.n_out)
+                    st.xo[o] = (float)x;
+            ++st.n_out;
+        } else if (inside) {
+            bool first = true;
+            int c = 1;
 #pragma unroll
             for (int k = 0; k < NB; ++k) {
-                if (k < j && in.xni[k] == in.xni[j])
+                if (k < j && st.in.xni[k] == x)
                     first = false;
-                if (k > j && in.xni[k] == in.xni[j])
-                    ++cnt;
+                if (k > j && st.in.xni[k] == x)
+                    ++c;
             }
             if (first) {
-                const uint32_t off = sw128_offset(site, in.xni[j] + lay.o, kASlab);
-                *reinterpret_cast<__half *>(A + off) = __int2half_rn(cnt);
-                off1[j] = off;
+                off[j] = sw128_offset(row, kb);
+                cnt[j] = c;
             }
         }
-        fence_async_smem();
-        mbar_arrive(&sm.barA[b]);
-        mbar_arrive(&sm.barS[q]);
     }
-    return true;
 }
 
-// Byte offsets (in 16-byte units, the descriptors' address unit) of the
-// K step at histogram column kp of A and window column kb of B.
-__host__ __device__ constexpr uint32_t a_step16(int kp)
+// Sum of the weights of absolute chunk c (labels 8c .. 8c + 7) outside the
+// window, where no in-window neighbour's tent reaches: 2^(alpha (g - s)^2).
+// LMASK zeroes labels >= L.
+template <bool LMASK>
+__device__ __forceinline__ float outside_chunk(const DevModel &m, float gf, int c)
 {
-    return (uint32_t)(((kp >> 6) * kASlab + (kp & 63) * 2) >> 4);
-}
-__host__ __device__ constexpr uint32_t b_step16(int kb)
-{
-    return (uint32_t)(((kb >> 6) * kBSlab + (kb & 63) * 2) >> 4);
-}
-
-// MMAs of label tile lt of one tile: its K window in ksteps steps into TMEM
-// columns [d0 + 64 lt, d0 + 64 lt + 64).  The start-address field of a
-// descriptor is its low 14 bits and every address stays below 256 KB, so
-// adding an offset to the descriptor moves its start.
-template <int KS>
-__device__ __forceinline__ void issue_label_tile(uint64_t adesc, uint64_t bdesc, uint32_t d0,
-                                                 int lt, int ksteps)
-{
-    if constexpr (KS > 0) {
+    const float dgb = __fsub_rn(gf, (float)(c * kChunk));
+    float S = 0.0f;
 #pragma unroll
-        for (int ks = 0; ks < KS; ++ks)
-            umma_f16_ss(d0 + (uint32_t)(lt * kLabelTile),
-                        adesc + a_step16(lt * kLabelTile + ks * 16), bdesc + b_step16(ks * 16),
-                        kIdesc, ks > 0 ? 1u : 0u);
-    } else {
-        for (int ks = 0; ks < ksteps; ++ks)
-            umma_f16_ss(d0 + (uint32_t)(lt * kLabelTile),
-                        adesc + a_step16(lt * kLabelTile + ks * 16), bdesc + b_step16(ks * 16),
-                        kIdesc, ks > 0 ? 1u : 0u);
+    for (int k = 0; k < kChunk; ++k) {
+        const float dg = __fsub_rn(dgb, (float)k);
+        float w = ex2_ftz(__fmul_rn(m.alpha, __fmul_rn(dg, dg)));
+        if (LMASK && c * kChunk + k >= m.L)
+            w = 0.0f;
+        S = __fadd_rn(S, w);
+    }
+    return S;
+}
+
+// Sum of the weights of window chunk c from 8 tent sums read from TMEM (pb,
+// raw FP32 bits).
+template <bool LMASK>
+__device__ __forceinline__ float window_chunk(const DevModel &m, float mu, float gf,
+                                              const uint32_t *pb, int c)
+{
+    const float dgb = __fsub_rn(gf, (float)(c * kChunk));
+    float S = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+        float w = label_wb(m.alpha, mu, __uint_as_float(pb[k]), __fsub_rn(dgb, (float)k));
+        if (LMASK && c * kChunk + k >= m.L)
+            w = 0.0f;
+        S = __fadd_rn(S, w);
+    }
+    return S;
+}
+
+// Chunks (bit c) that an outlier's tent reaches: labels within T - 1 of it.
+template <int NB>
+__device__ __forceinline__ uint32_t outlier_chunks(const TcSite<NB> &st, int T, int nc)
+{
+    uint32_t mask = 0u;
+#pragma unroll
+    for (int o = 0; o < NB; ++o) {
+        if (o < st.n_out) {
+            const int x = (int)st.xo[o];
+            const int c0 = max(x - T + 1, 0) >> 3;
+            const int c1 = min((x + T - 1) >> 3, nc - 1);
+            if (c1 >= c0)
+                mask |= (c1 - c0 >= 31 ? 0xFFFFFFFFu : ((2u << (c1 - c0)) - 1u)) << c0;
+        }
+    }
+    return mask;
+}
+
+// Inclusive prefix sums of absolute chunk c's weights from exact tent sums
+// (neighbour labels xn, observation gf) on the CUDA cores: bit-identical to
+// the pass-1 weights.
+template <int NB>
+__device__ __forceinline__ void chunk_prefix_exact(const DevModel &m, float mu,
+                                                   const float (&xn)[NB], float gf, int c,
+                                                   float (&p)[kChunk])
+{
+    float S = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+        const int s = c * kChunk + k;
+        const float sf = (float)s;
+        float w = label_wb(m.alpha, mu, tent_sum<NB>(xn, m.Tf, sf), __fsub_rn(gf, sf));
+        if (s >= m.L)
+            w = 0.0f;
+        S = __fadd_rn(S, w);
+        p[k] = S;
     }
 }
 
-// MMA warp: one elected thread issues each tile's MMAs once A is written
-// (barA) and TMEM buffer i & 1 has been read by pass 1 of tile i - 2
-// (barP).  With the fixed shape (NT = 4 label tiles = the 4 pass-1 parts,
-// KS K steps) label tile h waits only for part h and is committed on its
-// own (barM[b][h]), so pass 1 and the MMAs overlap inside a tile; other
-// shapes wait for all parts and commit once to every part.  Before
-// returning the thread waits (bounded) for the MMAs it issued, so TMEM can
-// be freed.
-template <int NT, int KS>
-__device__ __forceinline__ bool mma_role(const TcLayout &lay, const TcSmem &sm, uint32_t tmem,
-                                         int n_my)
+
+// Counter of the tile that lane `lane` (0-8) of warp 0 watches for item
+// (k, tile j): one of the 3 x 3 tiles around j, or nullptr (none: outside
+// the grid, k = 0, or lanes 9-31).
+__device__ __forceinline__ const unsigned int *dep_counter(const unsigned int *done, int k, int j,
+                                                           int tiles_x, int tiles_y, int lane)
 {
-    static_assert(NT % kP1Parts == 0, "fixed shape: whole label tiles per pass-1 part");
-    constexpr int kTpp = NT / kP1Parts;   // label tiles per part (fixed shape)
-    uint32_t ok = 1;
-    if ((threadIdx.x & 31) == 0) {
-        const uint64_t bdesc = sw128_kmajor_desc(smem_u32(sm.B));
-        const uint64_t adesc0 = sw128_kmajor_desc(smem_u32(sm.A0));
-        const uint64_t adesc1 = sw128_kmajor_desc(smem_u32(sm.A0 + sm.a_bytes));
-        const int ksteps = lay.kw / 16;
-        int issued = 0;
-        for (int i = 0; i < n_my && ok; ++i) {
-            const int b = i & 1;
-            const uint64_t adesc = b ? adesc1 : adesc0;
-            const uint32_t d0 = tmem + (uint32_t)(b * lay.tmem_cols);
-            if (!wait_use(&sm.barA[b], i >> 1)) {
-                ok = 0;
+    if (k == 0 || lane >= 9)
+        return nullptr;
+    const int ty = j / tiles_x;
+    const int tx = j - ty * tiles_x;
+    const int yy = ty + lane / 3 - 1;
+    const int xx = tx + lane % 3 - 1;
+    if (yy < 0 || yy >= tiles_y || xx < 0 || xx >= tiles_x)
+        return nullptr;
+    return done + (size_t)yy * tiles_x + xx;
+}
+
+// Wait (bounded) until *d >= k; `seen` is an earlier observation of *d.
+// Ends with an acquire fence, so the labels read after the group's next
+// barrier are those the tile published.  Returns false if the wait gave up.
+__device__ __forceinline__ bool wait_counter(const unsigned int *d, unsigned int k,
+                                             unsigned int seen)
+{
+    bool ok = true;
+    if (d) {
+        long long spins = 0;
+        while (seen < k) {
+            if (++spins > kTcSpinLimit) {
+                ok = false;
                 break;
             }
-            if constexpr (NT > 0) {
-#pragma unroll
-                for (int h = 0; h < kP1Parts; ++h) {
-                    if (i >= 2 && !wait_use(&sm.barP[b * kP1Parts + h], (i - 2) >> 1)) {
-                        ok = 0;
-                        break;
-                    }
-                    tc_fence_after_sync();
-#pragma unroll
-                    for (int lt = h * kTpp; lt < (h + 1) * kTpp; ++lt)
-                        issue_label_tile<KS>(adesc, bdesc, d0, lt, ksteps);
-                    umma_commit(&sm.barM[b * kP1Parts + h]);
-                }
-            } else {
-                for (int h = 0; h < kP1Parts && ok; ++h)
-                    if (i >= 2 && !wait_use(&sm.barP[b * kP1Parts + h], (i - 2) >> 1))
-                        ok = 0;
-                if (!ok)
-                    break;
-                tc_fence_after_sync();
-                for (int lt = 0; lt < lay.nt; ++lt)
-                    issue_label_tile<0>(adesc, bdesc, d0, lt, ksteps);
-                for (int h = 0; h < kP1Parts; ++h)
-                    umma_commit(&sm.barM[b * kP1Parts + h]);
-            }
-            if (ok)
-                ++issued;
+            __nanosleep(64);
+            seen = ld_relaxed_gpu(d);
         }
-        // every commit of the last tiles (a partly issued one included) has
-        // completed once the last label tile's barrier of each buffer has
-        for (int k = issued - 2; k < issued + (ok ? 0 : 1); ++k)
-            if (k >= 0 && k < n_my)
-                mbar_wait_bounded(&sm.barM[(k & 1) * kP1Parts + kP1Parts - 1],
-                                  (uint32_t)(k >> 1) & 1u, kTcSpinLimit);
     }
-    __syncwarp();
-    return __shfl_sync(0xFFFFFFFFu, ok, 0) != 0;
+    fence_acq_rel_gpu();
+    return ok;
 }
 
-// Pass-1 warps: exponent, exp2 and chunk prefix sums of one label part of
-// each site from the accumulators into G.
-__device__ __forceinline__ bool pass1_role(const SweepArgs &a, const TcLayout &lay,
-                                           const TcSmem &sm, uint32_t tmem, int n_my,
-                                           int tiles_x)
+template <int NB, bool LMASK>
+__global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uint8_t *x0,
+                                                          uint8_t *x1, int nsweeps, int tiles_x,
+                                                          int tiles_y, int nc, unsigned int *done,
+                                                          unsigned int *grab, int *err)
 {
-    const int idx = (int)(threadIdx.x >> 5) - kP1Warp0;   // 0..15
-    const int q = idx & 3;                                // lane quarter = warp index mod 4
-    const int part = idx >> 2;
-    const int site = q * 32 + (int)(threadIdx.x & 31);
-    const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    const int g_lo = part_lo(lay.ng, part);
-    const int g_hi = part_lo(lay.ng, part + 1);
-    const float mu = -a.m.gam;
-    for (int i = 0; i < n_my; ++i) {
-        const int b = i & 1;
-        int r, c;
-        tile_site(a, tiles_x, i, site, r, c);
-        const float gf = (r < a.H && c < a.W) ? (float)a.g[(size_t)r * a.pitch + c] : 0.0f;
-        bool ok = wait_use(&sm.barM[b * kP1Parts + part], i >> 1);
-        if (ok && i >= 2)   // the selection of tile i - 2 has read G[b]
-            ok = wait_use(&sm.barG[b], (i - 2) >> 1);
-        if (__any_sync(0xFFFFFFFFu, !ok))   // tcgen05.ld below is warp-collective
-            return false;
-        tc_fence_after_sync();
-        float *Gcol = sm.G0 + b * sm.g_elems + site;
-        float G = 0.0f, comp = 0.0f;
-        const uint32_t tb = trow + (uint32_t)(b * lay.tmem_cols);
-#pragma unroll 1
-        for (int grp = g_lo; grp < g_hi; ++grp) {
-            uint32_t pb[32];
-            tmem_ld32(tb + (uint32_t)(grp * 32), pb);
-            tmem_wait_ld(pb);
-            if ((grp + 1) * 32 > a.m.L)
-                group_pass<true>(a.m, mu, gf, grp, pb, lay.nc, Gcol, G, comp);
-            else
-                group_pass<false>(a.m, mu, gf, grp, pb, lay.nc, Gcol, G, comp);
-        }
-        tc_fence_before_sync();
-        mbar_arrive(&sm.barP[b * kP1Parts + part]);   // TMEM columns read, chunk sums written
-    }
-    return true;
-}
-
-// Selector warps: inertia, joining of the label parts' prefix sums, the
-// certified chunk and label selection (pass 2 on the CUDA cores), FP64
-// re-draws, writes.
-template <int NB>
-__device__ __forceinline__ bool select_role(const SweepArgs &a, const TcLayout &lay,
-                                            const TcSmem &sm, int n_my, int tiles_x)
-{
-    const int site = (int)threadIdx.x - kSelWarp0 * 32;   // 0..127
-    const uint32_t t = sweep_index(a);
-    const float mu = -a.m.gam;
-    const float nbT = (float)(NB * a.m.T);
-    const int nc = lay.nc;
-    // first group of every part and the last chunk of every part (-1: empty)
-    int gstart[kP1Parts];
-    int last[kP1Parts];
-#pragma unroll
-    for (int h = 0; h < kP1Parts; ++h) {
-        const int lo = part_lo(lay.ng, h), hi = part_lo(lay.ng, h + 1);
-        gstart[h] = lo;
-        last[h] = hi > lo ? min(4 * hi, nc) - 1 : -1;
-    }
-    for (int i = 0; i < n_my; ++i) {
-        const int b = i & 1;
-        const int rq = i & (kRing - 1);
-        int r, c;
-        tile_site(a, tiles_x, i, site, r, c);
-        const bool valid = r < a.H && c < a.W;
-        bool ok = wait_use(&sm.barS[rq], i >> 2);
-#pragma unroll
-        for (int h = 0; h < kP1Parts; ++h)
-            ok = ok && wait_use(&sm.barP[b * kP1Parts + h], i >> 1);
-        if (__any_sync(0xFFFFFFFFu, !ok))   // the re-draw below is warp-collective
-            return false;
-        SiteIn<NB> in;
-        stage_get<NB>(sm.S0 + rq * kStageBytes, site, in);
-        const float *Gcol = sm.G0 + b * sm.g_elems + site;
-        int s = 0;
-        bool certain = true;
-        float xn[NB];
-        __half2 xh[NB];
-#pragma unroll
-        for (int j = 0; j < NB; ++j) {
-            xn[j] = (float)in.xni[j];
-            xh[j] = __float2half2_rn(xn[j]);
-        }
-        const float gf = (float)in.g;
-        float delta = 0.0f, Z = 0.0f, tu = 0.0f, Gprev = 0.0f;
-        int cs = 0;
-        if (valid) {
-            // offsets of the parts: sums of the preceding parts' totals
-            float O[kP1Parts + 1];
-            O[0] = 0.0f;
-#pragma unroll
-            for (int h = 0; h < kP1Parts; ++h)
-                O[h + 1] = last[h] >= 0 ? __fadd_rn(O[h], Gcol[last[h] * kSites]) : O[h];
-            const auto Gc = [&](int cc) {
-                const int g = cc >> 2;
-                float off = O[0];
-#pragma unroll
-                for (int h = 1; h < kP1Parts; ++h)
-                    off = g >= gstart[h] ? O[h] : off;
-                return __fadd_rn(off, Gcol[cc * kSites]);
-            };
-            if (a.m.em1 != 0.0f)
-                delta = __fmul_rn(single_wb<NB>(a.m, mu, nbT, xn, gf, in.xi), a.m.em1);
-            // the steps of cdf_select, with G released after the chunk search
-            Z = __fadd_rn(O[kP1Parts], delta);
-            tu = __fmul_rn((float)in.ub * (1.0f / 16777216.0f), Z);
-            cs = cdf_find_chunk(Gc, nc, tu, delta, in.xi);
-            Gprev = cs > 0 ? Gc(cs - 1) : 0.0f;
-        }
-        mbar_arrive(&sm.barG[b]);   // G[b] may be overwritten
-        if (valid) {
-            const __half2 T2 = __float2half2_rn(a.m.Tf);
-            s = cdf_finish(a.m, a.m.eta_b, cs, Gprev, Z, tu, delta, in.xi, certain,
-                           [&](int cc, float (&pp)[kChunk]) {
-                               chunk_prefix_b<NB>(a.m, mu, nbT, xh, T2, gf, cc, pp);
-                           });
-        }
-        s = warp_redraw_fp64<NB>(a.m, valid && !certain, in, s, a.fp64_draws);
-        if (valid) {
-            a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-            if (accumulate_after(a, t))
-                a.acc[(size_t)r * a.W + c] += (float)s;
-        }
-        mbar_arrive(&sm.barF[rq]);
-    }
-    return true;
-}
-
-template <int NB, int NT, int KS>
-__global__ void __launch_bounds__(kTcThreads, 1) pca_tc_kernel(const SweepArgs a,
-                                                               const TcLayout lay, int *err)
-{
-    extern __shared__ __align__(1024) uint8_t tc_smem[];
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    if (smem_u32(tc_smem) & 1023u) {  // the swizzled operands need 1024-byte alignment
+    extern __shared__ __align__(1024) uint8_t smem[];
+    const int tid = (int)threadIdx.x;
+    const int grp = tid >> 7;          // warpgroup = tile slot
+    const int lt = tid & 127;          // site of the tile = TMEM lane
+    const int q = lt >> 5;             // warp of the group = lane quarter = tile row
+    const int lane = tid & 31;
+    if (smem_u32(smem) & 1023u) {      // the swizzled operands need 1024-byte alignment
         if (tid == 0)
             atomicExch(err, 2);
         return;
     }
-    const TcSmem sm = carve(tc_smem, lay);
+    uint8_t *B = smem + kOffB;
+    uint8_t *A = smem + kOffA + grp * kOpBytes;
+    float *Gcol = reinterpret_cast<float *>(smem + kOffG) + tid;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kOffG + nc * kThr * 4);
+    unsigned int *s_item = reinterpret_cast<unsigned int *>(mbar + kGroups);
+    uint32_t *tmem_slot = s_item + kGroups;
 
-    // A and B start zero; B holds K(t, s) for window column kk <-> t = s0 - o + kk
-    // and row n <-> s = s0 + n.
-    {
-        uint4 *z = reinterpret_cast<uint4 *>(tc_smem);
-        const int n16 = (2 * sm.a_bytes + lay.b_slabs * kBSlab) / 16;
-        for (int i = tid; i < n16; i += kTcThreads)
-            z[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
+    // A starts zero; B holds K(k, c) at row c (window label), column k (bin)
+    for (int i = tid; i < (kOpBytes * (1 + kGroups)) / 16; i += kThr)
+        reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
-    for (int i = tid; i < kLabelTile * lay.kw; i += kTcThreads) {
-        const int n = i / lay.kw;
-        const int kk = i - n * lay.kw;
-        const int v = max(a.m.T - abs(kk - lay.o - n), 0);
-        *reinterpret_cast<__half *>(sm.B + sw128_offset(n, kk, kBSlab)) = __int2half_rn(v);
+    for (int i = tid; i < kWin * kBins; i += kThr) {
+        const int c = i / kBins, k = i - (i / kBins) * kBins;
+        const int v = max(a.m.T - abs(c - (a.m.T - 1) - k), 0);
+        *reinterpret_cast<__half *>(B + sw128_offset(c, k)) = __int2half_rn(v);
     }
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&sm.barA[b], kLoadThreads);
-            mbar_init(&sm.barG[b], kSelThreads);
-            for (int h = 0; h < kP1Parts; ++h) {
-                mbar_init(&sm.barM[b * kP1Parts + h], 1);
-                mbar_init(&sm.barP[b * kP1Parts + h], kSites);
-            }
-        }
-        for (int k = 0; k < kRing; ++k) {
-            mbar_init(&sm.barS[k], kLoadThreads);
-            mbar_init(&sm.barF[k], kSelThreads);
-        }
+        for (int g = 0; g < kGroups; ++g)
+            mbar_init(&mbar[g], 1);
         mbar_init_fence();
     }
-    if (warp == 0) {
-        tmem_alloc(sm.tmem_slot, (uint32_t)(2 * lay.tmem_cols));
+    if (tid < 32) {
+        tmem_alloc(tmem_slot, (uint32_t)kTmemCols);
         tmem_relinquish();
     }
     fence_async_smem();
     tc_fence_before_sync();
     __syncthreads();
     tc_fence_after_sync();
-    const uint32_t tmem = *sm.tmem_slot;
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tcol = tmem + (uint32_t)(grp * kWin);          // the group's columns
+    const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);      // this warp's lanes
+    const int bar_id = 1 + grp;
+    const float mu = -a.m.gam;
+    const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
+    const unsigned int total = ntiles * (unsigned int)nsweeps;
+    const uint32_t t0 = sweep_index(a);
 
-    const int tiles_x = (a.W + 31) >> 5;
-    const int ntiles = tiles_x * ((a.H + kTileRows - 1) / kTileRows);
-    const int n_my = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1
-                                              : 0;
-    bool ok;
-    if (warp < kP1Warp0)
-        ok = load_role<NB>(a, lay, sm, n_my, tiles_x);
-    else if (warp < kSelWarp0)
-        ok = pass1_role(a, lay, sm, tmem, n_my, tiles_x);
-    else if (warp < kMmaWarp)
-        ok = select_role<NB>(a, lay, sm, n_my, tiles_x);
-    else
-        ok = mma_role<NT, KS>(lay, sm, tmem, n_my);
-    if (!ok && (tid & 31) == 0)
-        atomicExch(err, 1);
+    uint32_t prev_off[NB];   // A entries this thread set for its previous item
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        prev_off[j] = ~0u;
+    int uses = 0;            // completed phases of the group's mbarrier
+    bool ok = true;
+
+    // first item
+    if (q == 0) {
+        unsigned int it = 0;
+        if (lane == 0)
+            it = atomicAdd(grab, 1u);
+        it = __shfl_sync(0xFFFFFFFFu, it, 0);
+        if (it < total) {
+            const int k = (int)(it / ntiles);
+            const unsigned int *d =
+                dep_counter(done, k, (int)(it - (unsigned int)k * ntiles), tiles_x, tiles_y, lane);
+            if (!wait_counter(d, (unsigned int)k, d ? ld_relaxed_gpu(d) : 0u))
+                atomicExch(err, 1);
+        }
+        if (lane == 0)
+            s_item[grp] = it;
+    }
+    named_bar_sync(bar_id, kSites);
+    unsigned int item = s_item[grp];
+    unsigned int next = 0;   // warp 0, lane 0: the item taken for after this one
+
+    while (item < total) {
+        const int k = (int)(item / ntiles);
+        const int j = (int)(item - (unsigned int)k * ntiles);
+        const int ty = j / tiles_x;
+        const int tx = j - ty * tiles_x;
+        const int r = ty * kTileRows + q;
+        const int c = tx * 32 + lane;
+        const bool valid = r < a.H && c < a.W;
+        SweepArgs b = a;
+        b.xin = (k & 1) ? x1 : x0;
+        b.xout = (k & 1) ? x0 : x1;
+        const uint32_t t = t0 + (uint32_t)k;
+
+        // site inputs, window, histogram row
+        TcSite<NB> st;
+        st.in = SiteIn<NB>{};
+        if (valid)
+            load_site<NB, true>(b, b.xin, r, c, kTagPCA, t, st.in);
+        float *accp = a.acc + (size_t)r * a.W + c;
+        const bool acc_on = valid && accumulate_after(b, t);
+        const float acc_old = acc_on ? __ldcg(accp) : 0.0f;   // prefetched
+#pragma unroll
+        for (int jn = 0; jn < NB; ++jn)
+            st.xn[jn] = (float)st.in.xni[jn];
+        st.gf = (float)st.in.g;
+        uint32_t off[NB];
+        int cnt[NB];
+        site_window<NB>(st, a.m.T, lt, valid, off, cnt);
+#pragma unroll
+        for (int jn = 0; jn < NB; ++jn)
+            if (prev_off[jn] != ~0u)
+                *reinterpret_cast<__half *>(A + prev_off[jn]) = __ushort_as_half((unsigned short)0);
+#pragma unroll
+        for (int jn = 0; jn < NB; ++jn) {
+            if (off[jn] != ~0u)
+                *reinterpret_cast<__half *>(A + off[jn]) = __int2half_rn(cnt[jn]);
+            prev_off[jn] = off[jn];
+        }
+        fence_async_smem();
+        tc_fence_before_sync();
+        named_bar_sync(bar_id, kSites);   // rows written, the previous item's TMEM reads done
+        if (lt == 0) {
+            tc_fence_after_sync();
+            const uint64_t adesc = sw128_kmajor_desc(smem_u32(A));
+            const uint64_t bdesc = sw128_kmajor_desc(smem_u32(B));
+#pragma unroll
+            for (int ks = 0; ks < kBins / 16; ++ks)   // 32-byte K steps inside the row
+                umma_f16_ss(tcol, adesc + (uint64_t)(2 * ks), bdesc + (uint64_t)(2 * ks), kIdesc,
+                            ks > 0 ? 1u : 0u);
+            umma_commit(&mbar[grp]);
+            next = atomicAdd(grab, 1u);   // used at the end of this item
+        }
+
+        // outside chunks, while the tensor core runs
+        const int lo = max(st.m, 0);
+        const int hi = min(st.m + kWinChunks, nc);
+        const int n_oc = lo + nc - hi;
+        const int n_oc_w = __reduce_max_sync(0xFFFFFFFFu, n_oc);
+#pragma unroll 1
+        for (int jj = 0; jj < n_oc_w; ++jj) {
+            const int cc = jj < lo ? jj : hi + (jj - lo);
+            const float S = outside_chunk<LMASK>(a.m, st.gf, cc);
+            if (jj < n_oc)
+                Gcol[cc * kThr] = S;
+        }
+
+        // first look at the next item's neighbourhood (warp 0), used at the end
+        const unsigned int *dnext = nullptr;
+        unsigned int seen = 0u;
+        int knext = 0;
+        if (q == 0) {
+            const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
+            if (nx < total) {
+                knext = (int)(nx / ntiles);
+                dnext = dep_counter(done, knext, (int)(nx - (unsigned int)knext * ntiles), tiles_x,
+                                    tiles_y, lane);
+                if (dnext)
+                    seen = ld_relaxed_gpu(dnext);
+            }
+        }
+
+        // window chunks from TMEM
+        if (!mbar_wait_bounded(&mbar[grp], (uint32_t)(uses & 1), kTcSpinLimit)) {
+            atomicExch(err, 1);
+            ok = false;
+        }
+        ++uses;
+        tc_fence_after_sync();
+#pragma unroll 1
+        for (int h = 0; h < kWin / 32; ++h) {
+            uint32_t pb[32];
+            tmem_ld32(trow + (uint32_t)(32 * h), pb);
+            tmem_wait_ld(pb);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int cc = st.m + 4 * h + i;
+                const float S = window_chunk<LMASK>(a.m, mu, st.gf, pb + 8 * i, cc);
+                if (cc >= 0 && cc < nc)
+                    Gcol[cc * kThr] = S;
+            }
+        }
+        tc_fence_before_sync();
+
+        // chunks an outlier's tent reaches are recomputed from exact tent
+        // sums; the (site, chunk) tasks of the warp are dealt out to all 32
+        // lanes (a lane takes task lane + 32 r and writes the owner's column)
+        const uint32_t omask = outlier_chunks<NB>(st, a.m.T, nc);
+        if (__any_sync(0xFFFFFFFFu, omask != 0u)) {
+            const int cnt = __popc(omask);
+            int incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o)
+                    incl += v;
+            }
+            const int ntask = __shfl_sync(0xFFFFFFFFu, incl, 31);
+#pragma unroll 1
+            for (int base = 0; base < ntask; base += 32) {
+                const int tsk = base + lane;
+                int owner = 0;   // lanes whose inclusive count is <= tsk
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
+                    if (v <= tsk)
+                        owner += step;
+                }
+                owner = min(owner, 31);
+                const int o_excl = __shfl_sync(0xFFFFFFFFu, incl - cnt, owner);
+                const uint32_t o_mask = __shfl_sync(0xFFFFFFFFu, omask, owner);
+                const float o_gf = __shfl_sync(0xFFFFFFFFu, st.gf, owner);
+                float o_xn[NB];
+#pragma unroll
+                for (int jn = 0; jn < NB; ++jn)
+                    o_xn[jn] = __shfl_sync(0xFFFFFFFFu, st.xn[jn], owner);
+                const bool mine = tsk < ntask;
+                const int cc = mine ? (int)__fns(o_mask, 0u, tsk - o_excl + 1) : 0;
+                float p[kChunk];
+                chunk_prefix_exact<NB>(a.m, mu, o_xn, o_gf, cc, p);
+                if (mine)
+                    Gcol[cc * kThr + owner - lane] = p[kChunk - 1];
+            }
+        }
+
+        // chunk prefix sums in label order (Kahan), certified selection
+        float G = 0.0f, comp = 0.0f;
+#pragma unroll
+        for (int cc = 0; cc < 32; ++cc) {
+            if (cc < nc) {
+                const float y = __fsub_rn(Gcol[cc * kThr], comp);
+                const float tt = __fadd_rn(G, y);
+                comp = __fsub_rn(__fsub_rn(tt, G), y);
+                G = tt;
+                Gcol[cc * kThr] = G;
+            }
+        }
+        int s = 0;
+        bool certain = true;
+        if (valid) {
+            float delta = 0.0f;
+            if (a.m.em1 != 0.0f) {
+                const float xif = (float)st.in.xi;
+                delta = __fmul_rn(label_wb(a.m.alpha, mu, tent_sum<NB>(st.xn, a.m.Tf, xif),
+                                           __fsub_rn(st.gf, xif)),
+                                  a.m.em1);
+            }
+            s = cdf_select(a.m, a.m.eta_b, [&](int cc) { return Gcol[cc * kThr]; }, nc, G, delta,
+                           st.in.xi, st.in.ub, certain, [&](int cs, float (&p)[kChunk]) {
+                               chunk_prefix_exact<NB>(a.m, mu, st.xn, st.gf, cs, p);
+                           });
+        }
+        s = warp_redraw_fp64<NB>(a.m, valid && !certain, st.in, s, a.fp64_draws);
+        if (valid) {
+            b.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+            if (acc_on)
+                *accp = acc_old + (float)s;
+        }
+
+        // publish the tile's sweep, take the next item
+        named_bar_sync(bar_id, kSites);
+        if (q == 0) {
+            if (lane == 0) {
+                st_release_gpu(done + j, (unsigned int)(k + 1));   // after every output of the tile
+                s_item[grp] = next;
+            }
+            if (!wait_counter(dnext, (unsigned int)knext, seen))
+                atomicExch(err, 1);
+        }
+        named_bar_sync(bar_id, kSites);
+        item = s_item[grp];
+    }
+
+    // a timed-out wait may leave an MMA in flight: wait for it (bounded)
+    // before TMEM is freed
+    if (!ok && lt == 0 && uses > 0)
+        mbar_wait_bounded(&mbar[grp], (uint32_t)((uses - 1) & 1), kTcSpinLimit);
     tc_fence_before_sync();
     __syncthreads();
-    if (warp == 0) {
+    if (tid < 32) {
         tc_fence_after_sync();
-        tmem_dealloc(tmem, (uint32_t)(2 * lay.tmem_cols));
+        tmem_dealloc(tmem, (uint32_t)kTmemCols);
     }
 }
 
-// Per-(model shape, device) launch configuration.
-struct TcConfig {
-    int L = -1, T = -1, nbhd = -1, device = -1;
-    TcLayout lay{};
-    int grid = 0;
-};
-
-// The issue loop is unrolled for the shape of L in (192, 256] with T <= 33
-// (4 label tiles, K window 128); other shapes use the runtime loop.
-bool fixed_shape(const TcLayout &lay)
-{
-    return lay.nt == 4 && lay.kw == 128;
-}
-
-template <int NB, int NT, int KS>
-cudaError_t launch_tc_t(const SweepArgs &a, const TcLayout &lay, int grid, int *err,
-                        cudaStream_t st)
-{
-    pca_tc_kernel<NB, NT, KS><<<grid, kTcThreads, lay.smem, st>>>(a, lay, err);
-    return cudaGetLastError();
-}
-
-template <int NB>
-cudaError_t launch_tc(const SweepArgs &a, const TcLayout &lay, int grid, int *err,
-                      cudaStream_t st)
-{
-    return fixed_shape(lay) ? launch_tc_t<NB, 4, 8>(a, lay, grid, err, st)
-                            : launch_tc_t<NB, 0, 0>(a, lay, grid, err, st);
-}
-
-template <int NB, int NT, int KS>
-cudaError_t set_attributes()
-{
-    cudaError_t e = cudaFuncSetAttribute(pca_tc_kernel<NB, NT, KS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemMax);
-    if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(pca_tc_kernel<NB, NT, KS>,
-                                 cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
-    return e;
-}
-
-template <int NB>
-cudaError_t configure(TcConfig &cfg)
+template <int NB, bool LMASK>
+cudaError_t launch_tcw_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
+                         unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
 {
     static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
-    if (dev < 64 && !attr_set[dev]) {
-        e = set_attributes<NB, 4, 8>();
-        if (e == cudaSuccess)
-            e = set_attributes<NB, 0, 0>();
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    const int nc = (a.m.L + kChunk - 1) / kChunk;
+    const int smem = tc_smem_bytes(32);
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(pca_tcw_kernel<NB, LMASK>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess)
             return e;
         attr_set[dev] = true;
     }
-    int per_sm = 0;
-    e = fixed_shape(cfg.lay)
-            ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pca_tc_kernel<NB, 4, 8>,
-                                                            kTcThreads, cfg.lay.smem)
-            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pca_tc_kernel<NB, 0, 0>,
-                                                            kTcThreads, cfg.lay.smem);
-    if (e != cudaSuccess)
-        return e;
-    if (per_sm < 1 || per_sm * 2 * cfg.lay.tmem_cols > kTmemCols)
-        return cudaErrorInvalidConfiguration;
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess)
         return e;
-    cfg.grid = sms * per_sm;
-    cfg.device = dev;
-    return cudaSuccess;
+    const int tiles_x = (a.W + 31) / 32;
+    const int tiles_y = (a.H + kTileRows - 1) / kTileRows;
+    const long long items = (long long)tiles_x * tiles_y * nsweeps;
+    if (items <= 0)
+        return cudaSuccess;
+    if (items >= (1ll << 32))
+        return cudaErrorInvalidValue;
+    // one CTA per SM (TMEM: all 512 columns); no more CTAs than 4-item groups
+    const long long need = (items + kGroups - 1) / kGroups;
+    const int grid = (int)(need < sms ? need : sms);
+    pca_tcw_kernel<NB, LMASK><<<grid, kThr, tc_smem_bytes(nc), st>>>(
+        a, x0, x1, nsweeps, tiles_x, tiles_y, nc, done, grab, err);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool pca_tc_eligible(const DevModel &m)
 {
-    if (m.L < kTcMinLabels || m.L > 256 || m.T > kTcMaxT || m.norm != 0)
-        return false;
-    return tc_layout(m.L, m.T).smem <= kSmemMax;
+    return m.L >= kTcMinLabels && m.L <= 256 && m.T >= 1 && m.T <= kTcMaxT && m.norm == 0 &&
+           (m.nbhd == 4 || m.nbhd == 8);
 }
 
-cudaError_t launch_pca_tc(const SweepArgs &a, int *err, cudaStream_t st)
+cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
+                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
 {
     if (!pca_tc_eligible(a.m))
         return cudaErrorInvalidValue;
-    thread_local TcConfig cfg;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess)
-        return e;
-    if (cfg.L != a.m.L || cfg.T != a.m.T || cfg.nbhd != a.m.nbhd || cfg.device != dev) {
-        cfg.L = a.m.L;
-        cfg.T = a.m.T;
-        cfg.nbhd = a.m.nbhd;
-        cfg.lay = tc_layout(a.m.L, a.m.T);
-        e = a.m.nbhd == 8 ? configure<8>(cfg) : configure<4>(cfg);
-        if (e != cudaSuccess) {
-            cfg.L = -1;
-            return e;
-        }
-    }
-    const int tiles = ((a.W + 31) / 32) * ((a.H + kTileRows - 1) / kTileRows);
-    const int grid = tiles < cfg.grid ? tiles : cfg.grid;
-    if (grid <= 0)
-        return cudaSuccess;
-    return a.m.nbhd == 8 ? launch_tc<8>(a, cfg.lay, grid, err, st)
-                         : launch_tc<4>(a, cfg.lay, grid, err, st);
+    const bool lmask = (a.m.L % kChunk) != 0;
+    if (a.m.nbhd == 8)
+        return lmask ? launch_tcw_t<8, true>(a, x0, x1, nsweeps, done, grab, err, st)
+                     : launch_tcw_t<8, false>(a, x0, x1, nsweeps, done, grab, err, st);
+    return lmask ? launch_tcw_t<4, true>(a, x0, x1, nsweeps, done, grab, err, st)
+                 : launch_tcw_t<4, false>(a, x0, x1, nsweeps, done, grab, err, st);
 }
 
 }  // namespace pcad

@@ -1,9 +1,11 @@
-"""Tensor-core PCA sweep (banded prior sums by tcgen05.mma, CDF on the CUDA
-cores) against the CUDA-core sweep and the oracle: labels and posterior
-means must be bit-identical for tile-ragged images, label counts that are
-not multiples of 8 or 32, both neighbourhoods, Potts (T = 1) and the
-widest supported truncation, and images with more tiles than the
-persistent grid."""
+"""Tensor-core PCA sweeps (windowed prior sums by tcgen05.mma, CDF on the
+CUDA cores, many sweeps per wavefront launch) against the CUDA-core sweep
+and the oracle: labels and posterior means must be bit-identical for
+tile-ragged images, label counts that are not multiples of 8 or 32, both
+neighbourhoods, Potts (T = 1) and the widest supported truncation, sharp
+edges (neighbours outside a site's 64-label histogram window), images with
+more tiles than the persistent grid, and per-sweep launches under energy
+tracking."""
 import numpy as np
 import pytest
 
@@ -26,6 +28,15 @@ def _grey(seed, H, W, L, sigma):
     return gaussian_noise(seed + 1, greyscale_scene(seed, H, W, L, n_shapes=6), sigma, L)
 
 
+def _edges(seed, H, W):
+    """8 x 8 blocks of levels 10 and 240 with mild noise: neighbourhoods across
+    block edges span ~230 labels, beyond one site's histogram window."""
+    rng = np.random.default_rng(seed)
+    yy, xx = np.mgrid[0:H, 0:W]
+    clean = np.where(((yy // 8) + (xx // 8)) % 2 == 0, 10, 240)
+    return np.clip(np.rint(clean + rng.normal(0.0, 12.0, (H, W))), 0, 255).astype(np.uint8)
+
+
 CASES = [
     ("L256_37x70", lambda: (_grey(2, 37, 70, 256, 20.0),
                             Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0,
@@ -45,9 +56,15 @@ CASES = [
     ("L128_potts_30x40", lambda: (_grey(7, 30, 40, 128, 6.0),
                                   Model(L=128, pair=POTTS, pair_coef=1.1, sigma=6.0,
                                         inertia=1.0))),
-    ("L128_T65_21x53", lambda: (_grey(8, 21, 53, 128, 15.0),
-                                Model(L=128, pair=TL, pair_coef=0.02, pair_T=65, sigma=15.0,
+    ("L128_T33_21x53", lambda: (_grey(8, 21, 53, 128, 15.0),
+                                Model(L=128, pair=TL, pair_coef=0.02, pair_T=33, sigma=15.0,
                                       inertia=0.0))),
+    ("L256_edges_64x96", lambda: (_edges(15, 64, 96),
+                                  Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=12.0,
+                                        inertia=2.0))),
+    ("L256_8nb_edges_40x70", lambda: (_edges(16, 40, 70),
+                                      Model(L=256, nbhd=8, pair=TL, pair_coef=0.03, pair_T=25,
+                                            sigma=12.0, inertia=1.0))),
     ("L71_3x1", lambda: (_grey(9, 3, 1, 71, 5.0),
                          Model(L=71, pair=TL, pair_coef=0.3, pair_T=4, sigma=5.0, inertia=1.0))),
     ("L256_300x257", lambda: (_grey(10, 300, 257, 256, 20.0),
@@ -104,7 +121,7 @@ def test_set_kernel_rejects(pc):
         with pytest.raises(pc.PcadError):
             ch.set_kernel(7)
         ch.set_kernel(pc.PCAD_KERNEL_CUDA_CORE)
-    for T in (100, 40):   # T > 65; at L = 256 the band of T = 40 exceeds shared memory
+    for T in (100, 34):   # T > 33: the tents of a 64-bin histogram leave the 128-label window
         wide = Model(L=256, pair=TL, pair_coef=0.01, pair_T=T, sigma=20.0, inertia=1.0)
         with pc.Chain(_grey(13, 20, 20, 256, 20.0), wide, seed=1) as ch:
             with pytest.raises(pc.PcadError):
@@ -114,3 +131,19 @@ def test_set_kernel_rejects(pc):
     with pc.Chain(_grey(14, 20, 20, 256, 20.0), gibbs, seed=1) as ch:
         with pytest.raises(pc.PcadError):
             ch.set_kernel(pc.PCAD_KERNEL_TENSOR)
+
+
+def test_tensor_per_sweep_launches_under_energy_tracking(pc):
+    """Energy tracking needs every sweep's state: the tensor-core path then
+    launches one sweep at a time; energies and the minimum state must equal
+    the CUDA-core chain's."""
+    g, m = CASES[0][1]()
+    out = []
+    for kind in (pc.PCAD_KERNEL_CUDA_CORE, pc.PCAD_KERNEL_TENSOR):
+        with pc.Chain(g, m, seed=3, chain_id=2, burn_in=4) as ch:
+            ch.set_kernel(kind).track_energy(30)
+            ch.run(23)
+            out.append((ch.sample(), ch.energies(), ch.min_state()))
+    assert np.array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2][0], out[1][2][0]) and out[0][2][1:] == out[1][2][1:]
