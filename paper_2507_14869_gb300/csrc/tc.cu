@@ -71,15 +71,25 @@ constexpr long long kTcSpinLimit = 20000000;
 constexpr uint32_t kIdesc = idesc_f16_f32(kSites, kWin);
 constexpr float kNoLabel = -4096.0f;        // unused outlier slot: its tent is zero everywhere
 
-// Shared memory: B (16 KB), A[4] (64 KB), G [chunk][thread] floats, then
-// mbarriers, the groups' work items and the TMEM base.
+// Shared memory: B (16 KB), A[4] (64 KB), G [chunk][thread] floats, the
+// outside-chunk sums [chunk][observation], then mbarriers, the groups' work
+// items and the TMEM base.
 constexpr int kOffB = 0;
 constexpr int kOffA = kOpBytes;
 constexpr int kOffG = kOffA + kGroups * kOpBytes;
 
+constexpr int kTabRow = 257;   // outside-chunk table row: 256 observations + 1 (bank skew)
+
+// Floats of the outside-chunk table, rounded up so the mbarriers after it
+// stay 8-byte aligned.
+__host__ __device__ constexpr int tab_floats(int nc)
+{
+    return (nc * kTabRow + 1) & ~1;
+}
+
 __host__ __device__ constexpr int tc_smem_bytes(int nc)
 {
-    return kOffG + nc * kThr * 4 + 8 * kGroups + 4 * kGroups + 16;
+    return kOffG + nc * kThr * 4 + tab_floats(nc) * 4 + 8 * kGroups + 4 * kGroups + 16;
 }
 
 // Byte offset of element (row, k), k < 64, of a K-major operand in the
@@ -139,6 +149,7 @@ struct TcSite {
     float xo[NB];       // outlier labels (unused: kNoLabel)
     int n_out;          // outliers of this site
     int m;              // window = chunks [m, m + 16)
+    int wlast;          // last window chunk (relative) an in-window tent reaches, -1: none
     float gf;
 };
 
@@ -157,6 +168,7 @@ __device__ __forceinline__ void site_window(TcSite<NB> &st, int T, int row, bool
     st.m = xmin < kMissingLabelI ? (xmin - T + 1) >> 3 : 0;
     const int b = 8 * st.m + T - 1;
     st.n_out = 0;
+    int xmax_in = -1;
 #pragma unroll
     for (int j = 0; j < NB; ++j) {
         st.xo[j] = kNoLabel;
@@ -176,6 +188,7 @@ __device__ __forceinline__ void site_window(TcSite<NB> &st, int T, int row, bool
                     st.xo[o] = (float)x;
             ++st.n_out;
         } else if (inside) {
+            xmax_in = max(xmax_in, x);
             bool first = true;
             int c = 1;
 #pragma unroll
@@ -191,6 +204,8 @@ __device__ __forceinline__ void site_window(TcSite<NB> &st, int T, int row, bool
             }
         }
     }
+    // tents of in-window labels end at x + T - 1 <= 8 m + 127 (T <= 33)
+    st.wlast = xmax_in >= 0 ? (xmax_in + T - 1 - 8 * st.m) >> 3 : -1;
 }
 
 // Sum of the weights of absolute chunk c (labels 8c .. 8c + 7) outside the
@@ -329,7 +344,8 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
     uint8_t *B = smem + kOffB;
     uint8_t *A = smem + kOffA + grp * kOpBytes;
     float *Gcol = reinterpret_cast<float *>(smem + kOffG) + tid;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + kOffG + nc * kThr * 4);
+    float *Tab = reinterpret_cast<float *>(smem + kOffG + nc * kThr * 4);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(Tab + tab_floats(nc));
     unsigned int *s_item = reinterpret_cast<unsigned int *>(mbar + kGroups);
     uint32_t *tmem_slot = s_item + kGroups;
 
@@ -341,6 +357,12 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
         const int c = i / kBins, k = i - (i / kBins) * kBins;
         const int v = max(a.m.T - abs(c - (a.m.T - 1) - k), 0);
         *reinterpret_cast<__half *>(B + sw128_offset(c, k)) = __int2half_rn(v);
+    }
+    // outside-chunk sums: chunk c of observation g (the same function, hence
+    // the same values, as computing them per site)
+    for (int i = tid; i < nc * 256; i += kThr) {
+        const int c = i >> 8, gobs = i & 255;
+        Tab[c * kTabRow + gobs] = outside_chunk<LMASK>(a.m, (float)gobs, c);
     }
     if (tid == 0) {
         for (int g = 0; g < kGroups; ++g)
@@ -449,12 +471,12 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
         const int hi = min(st.m + kWinChunks, nc);
         const int n_oc = lo + nc - hi;
         const int n_oc_w = __reduce_max_sync(0xFFFFFFFFu, n_oc);
-#pragma unroll 1
+        const float *trow_g = Tab + st.in.g;
+#pragma unroll 4
         for (int jj = 0; jj < n_oc_w; ++jj) {
             const int cc = jj < lo ? jj : hi + (jj - lo);
-            const float S = outside_chunk<LMASK>(a.m, st.gf, cc);
             if (jj < n_oc)
-                Gcol[cc * kThr] = S;
+                Gcol[cc * kThr] = trow_g[cc * kTabRow];
         }
 
         // first look at the next item's neighbourhood (warp 0), used at the end
@@ -479,8 +501,11 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
         }
         ++uses;
         tc_fence_after_sync();
+        // 32-column groups up to the warp's last chunk with a tent; the
+        // window chunks after it hold zero tent sums: outside sums
+        const int ngrp = (__reduce_max_sync(0xFFFFFFFFu, st.wlast) >> 2) + 1;
 #pragma unroll 1
-        for (int h = 0; h < kWin / 32; ++h) {
+        for (int h = 0; h < ngrp; ++h) {
             uint32_t pb[32];
             tmem_ld32(trow + (uint32_t)(32 * h), pb);
             tmem_wait_ld(pb);
@@ -491,6 +516,12 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
                 if (cc >= 0 && cc < nc)
                     Gcol[cc * kThr] = S;
             }
+        }
+#pragma unroll 1
+        for (int i = 4 * ngrp; i < kWinChunks; ++i) {
+            const int cc = st.m + i;
+            if (cc >= 0 && cc < nc)
+                Gcol[cc * kThr] = trow_g[cc * kTabRow];
         }
         tc_fence_before_sync();
 
