@@ -50,8 +50,9 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
 
 # The same for pca_tc_kernel<4> (None: not captured for this version) and
 # pca_wave_kernel<32,4> (one 32-sweep launch at 1024^2, per site-update).
-NCU_TC_DRAM_BYTES_PER_SITE = None
-NCU_TC_TRAFFIC_NOTE = "not captured for this kernel version"
+NCU_TC_DRAM_BYTES_PER_SITE = (1.636608e6 + 0.055296e6) / (32 * 512 * 512)
+NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
+                       "161-192 of a chain), per site-update: the chain's planes stay in L2")
 NCU_WAVE_DRAM_BYTES_PER_SITE = (6.363904e6 + 0.730112e6) / (32 * 1024 * 1024)
 NCU_WAVE_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 1024^2 L=256, per "
                          "site-update, scaled to one 512^2 sweep (profiles/pca_wave_l256_1024sq.md)")
@@ -302,7 +303,8 @@ def run_ours(a):
     achieved = per_sweep_labels / (launch_ms * 1e-3) / 1e12
     in_use = pca_kind   # the kernel the timed chain ran
     kernel_name = {1: "pca_direct_kernel<32,4> (one launch per sweep)",
-                   2: "pca_tc_kernel<4> (tcgen05 banded prior sums, CUDA-core CDF)",
+                   2: "pca_tcw_kernel<4,0> (tcgen05 windowed tent sums, CUDA-core CDF, "
+                      "wavefront, one launch per 32 sweeps)",
                    3: "pca_wave_kernel<32,4> (wavefront, one launch per 32 sweeps)"}[in_use]
     per_site = {1: NCU_DRAM_BYTES_PER_SITE, 2: NCU_TC_DRAM_BYTES_PER_SITE,
                 3: NCU_WAVE_DRAM_BYTES_PER_SITE}[in_use]
@@ -310,8 +312,8 @@ def run_ours(a):
     traffic = per_site * H * W if per_site else None
     blocks, rest = divmod(SWEEPS, 32)
     # per chain: the 32-sweep graphs (sweep launches + the counter advance) and the rest
-    launches = (blocks * (2 if in_use == 3 else 33) +
-                ((2 if in_use == 3 else rest + 1) if rest else 0))
+    wave = in_use in (2, 3)   # one launch per block of sweeps + the advance
+    launches = (blocks * (2 if wave else 33) + ((2 if wave else rest + 1) if rest else 0))
     line = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
@@ -323,8 +325,11 @@ def run_ours(a):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
                      "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
                      "traffic": traffic, "traffic_source": note, "kernel": kernel_name,
-                     "work_per_unit": "one exponential (SFU) per label evaluation, L=256 per "
-                                      "site-update",
+                     "work_per_unit": "one label evaluation (one exponential on the SFU in "
+                                      "a direct evaluation), L=256 per site-update; the "
+                                      "tensor-core kernel takes the chunk sums outside a "
+                                      "site's 128-label window from a table, so it evaluates "
+                                      "fewer exponentials than labels",
                      "peak_source": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count x max "
                                     "clock; 29.9/clk/SM measured)",
                      "ms_per_sweep": launch_ms},

@@ -138,30 +138,29 @@ pcad_status pcad_chain_reset(pcad_chain *ch);
  * load ever failed to complete within its bounded wait. */
 pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
 
-/* Kernel of the unblocked PCA sweep (k = 0 above).  The prior sums of
- * Eq. posterior_pca_transition_matrix are, per site, the product of the
- * neighbour-label histogram with the banded matrix max(T - |t - s|, 0);
- * PCAD_KERNEL_TENSOR computes that product on the tensor cores (tcgen05)
- * and the rest of the draw on the CUDA cores; PCAD_KERNEL_CUDA_CORE
- * evaluates every label's prior on the CUDA cores.  Both draw exactly the
- * same labels.  PCAD_KERNEL_AUTO (the default) is the CUDA-core kernel,
- * which measured faster on GB300 for every model the tensor-core kernel
- * accepts (L = 256, 2048 x 2048: 8.1e9 against 6.4e9 site-updates/s).  The
- * tensor-core kernel accepts the PCA sampler with L >= 64, T <= 65 (Potts:
- * T = 1), and two histogram operands of 128 x (64 ceil(L/64) + 2 o) FP16
- * (o = T - 1 rounded up to 16), the 64 x (64 + 2 o) band block and two
- * 128 x ceil(L/8) FP32 chunk-sum arrays within 227 KB of shared memory --
- * for L = 256 that is T <= 33; with AUTO the unblocked PCA sweep runs
- * the per-sweep or the wavefront CUDA-core kernel (see
- * pcad_chain_kernel_in_use).  PCAD_EINVAL for an unknown kind or
- * PCAD_KERNEL_TENSOR on a model outside those limits.  PCAD_KERNEL_WAVE
- * runs the CUDA-core draw as one persistent launch per block of sweeps, a
- * tile of 4 x 32 sites starting sweep k as soon as its 3 x 3 neighbouring
- * tiles finished sweep k - 1 (no sweep-wide barrier, so one sweep's tail
+/* Kernel of the unblocked PCA sweep (k = 0 above).  The prior sum of
+ * Eq. posterior_pca_transition_matrix is a sum of tents
+ * max(T - |x_j - s|, 0) over the neighbours.  PCAD_KERNEL_TENSOR computes
+ * it on the tensor cores (tcgen05): each site histograms its neighbour
+ * labels relative to its own base label (64 bins), one MMA chain gives the
+ * tent sums over the 128-label window holding them, labels outside it take
+ * chunk sums of the Gaussian data term from a shared-memory table, and
+ * neighbours beyond the 64 bins are added on the CUDA cores; sweeps run as
+ * a wavefront (below).  PCAD_KERNEL_CUDA_CORE evaluates every label's prior
+ * on the CUDA cores.  All kernels draw exactly the same labels.  The
+ * tensor-core kernel accepts the PCA sampler with 64 <= L <= 256,
+ * truncation T <= 33 (Potts: T = 1) and the L0 price; PCAD_EINVAL for an
+ * unknown kind or PCAD_KERNEL_TENSOR on another model.  PCAD_KERNEL_AUTO
+ * (the default) takes it for L >= 192 without energy tracking (where it
+ * measured faster on GB300), else the per-sweep or the wavefront CUDA-core
+ * kernel (see pcad_chain_kernel_in_use).  PCAD_KERNEL_WAVE runs the
+ * CUDA-core draw as one persistent launch per block of sweeps, a tile of
+ * 4 x 32 sites starting sweep k as soon as its 3 x 3 neighbouring tiles
+ * finished sweep k - 1 (no sweep-wide barrier, so one sweep's tail
  * overlaps the next one's start); same labels; L0 price only (PCAD_EINVAL
- * with an Lp norm); energy tracking falls back to one launch per sweep.
- * pcad_chain_sync reports PCAD_ETIMEOUT if a tensor-core completion wait
- * or a wavefront dependency wait ever gave up. */
+ * with an Lp norm).  Energy tracking runs the wavefront kernels one sweep
+ * per launch.  pcad_chain_sync reports PCAD_ETIMEOUT if a tensor-core
+ * completion wait or a wavefront dependency wait ever gave up. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
@@ -173,10 +172,11 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 /* The kernel the chain's next sweeps run: PCAD_KERNEL_CUDA_CORE (one launch
  * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR, or
  * -k for temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO
- * the wavefront kernel is taken for L >= 16 when the image has between 1/2
- * and 3 waves of 4 x 32 tiles at 10 resident tiles per multiprocessor (the
- * sizes where it measured faster on GB300), the per-sweep kernel
- * otherwise. */
+ * the tensor-core kernel is taken for eligible models with L >= 192 and no
+ * energy tracking; otherwise the wavefront kernel for L >= 16 when the
+ * image has between 1/2 and 3 waves of 4 x 32 tiles at 10 resident tiles
+ * per multiprocessor (the sizes where it measured faster on GB300), the
+ * per-sweep kernel otherwise. */
 pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind);
 
 /* Change the model's coefficients (pair_coef, sigma, flip_p, inertia) for

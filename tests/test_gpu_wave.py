@@ -103,13 +103,22 @@ def test_kernel_in_use_auto_rule(pc):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     slots = 10 * sms
     m256 = Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0)
+    # L >= 192 and eligible for the tensor-core sweep: that one
+    for side in (128, 512, 2048):
+        g = np.zeros((side, side), np.uint8)
+        with pc.Chain(g, m256, seed=1) as ch:
+            assert ch.kernel_in_use() == pc.PCAD_KERNEL_TENSOR, side
+    # below L = 192 (or T > 33): the CUDA-core kernels by size
+    m128 = Model(L=128, pair=TL, pair_coef=0.1, pair_T=15, sigma=10.0, inertia=2.0)
+    wide = Model(L=256, pair=TL, pair_coef=0.05, pair_T=40, sigma=20.0, inertia=2.0)
     for side in (128, 512, 2048):
         tiles = (side // 32) * (side // 4)
         expect = pc.PCAD_KERNEL_WAVE if 2 * tiles >= slots and tiles <= 3 * slots \
             else pc.PCAD_KERNEL_CUDA_CORE
         g = np.zeros((side, side), np.uint8)
-        with pc.Chain(g, m256, seed=1) as ch:
-            assert ch.kernel_in_use() == expect, side
+        for mm in (m128, wide):
+            with pc.Chain(g, mm, seed=1) as ch:
+                assert ch.kernel_in_use() == expect, (side, mm.L, mm.pair_T)
     g = np.zeros((512, 512), np.uint8)
     with pc.Chain(g, m256, seed=1) as ch:
         ch.set_blocking(2)
@@ -118,6 +127,8 @@ def test_kernel_in_use_auto_rule(pc):
         ch.track_energy(4)
         assert ch.kernel_in_use() == pc.PCAD_KERNEL_CUDA_CORE   # every sweep's state needed
         ch.track_energy(0)
+        ch.set_kernel(pc.PCAD_KERNEL_WAVE)
+        assert ch.kernel_in_use() == pc.PCAD_KERNEL_WAVE
         ch.set_kernel(pc.PCAD_KERNEL_TENSOR)
         assert ch.kernel_in_use() == pc.PCAD_KERNEL_TENSOR
     binary = Model(L=2, pair=POTTS, pair_coef=1.2, noise=FLIP, flip_p=0.1, inertia=1.0)
