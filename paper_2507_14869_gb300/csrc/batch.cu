@@ -72,10 +72,21 @@ pcad_status check_job(const pcad_job &j)
 
 // Per-chain device layout inside one allocation.
 struct SlotMem {
-    size_t x0, x1, g, acc, ta, pr, end;
+    size_t x0, x1, g, acc, ta, pr, tab, end;   // tab == end: no tensor-core table
 };
 
-SlotMem slot_layout(int H, int W, int pitch, size_t pr_bytes, size_t base)
+// Whether a model runs on the batched tensor-core sweep (the automatic
+// kernel rule of the chains).
+bool model_tc(const pcad_model &m)
+{
+    double ta64[511];
+    std::vector<double> pr64;
+    DevModel dm{};
+    model_tables(m, ta64, pr64, dm);
+    return m.sampler == PCAD_SAMPLER_PCA && pca_tc_auto(dm);
+}
+
+SlotMem slot_layout(int H, int W, int pitch, size_t pr_bytes, size_t tab_bytes, size_t base)
 {
     SlotMem s;
     const size_t plane = al((size_t)pitch * H);
@@ -85,15 +96,22 @@ SlotMem slot_layout(int H, int W, int pitch, size_t pr_bytes, size_t base)
     s.acc = s.g + plane;
     s.ta = s.acc + al((size_t)H * W * sizeof(float));
     s.pr = s.ta + kTableBytes;
-    s.end = s.pr + al(pr_bytes);
+    s.tab = s.pr + al(pr_bytes);
+    s.end = s.tab + al(tab_bytes);
     return s;
+}
+
+SlotMem job_layout(const pcad_job &j, int pitch, size_t base)
+{
+    const int T = j.model.pair == PCAD_PAIR_POTTS ? 1 : j.model.pair_T;
+    const size_t tab = model_tc(j.model) ? (size_t)tc_table_floats(j.model.L) * sizeof(float) : 0;
+    return slot_layout(j.H, j.W, pitch, (size_t)(j.model.nbhd * T + 1) * sizeof(double), tab,
+                       base);
 }
 
 size_t slot_bytes(const pcad_job &j)
 {
-    const int pitch = (int)((j.W + 15) / 16 * 16);
-    const int T = j.model.pair == PCAD_PAIR_POTTS ? 1 : j.model.pair_T;
-    return slot_layout(j.H, j.W, pitch, (size_t)(j.model.nbhd * T + 1) * sizeof(double), 0).end;
+    return job_layout(j, (int)((j.W + 15) / 16 * 16), 0).end;
 }
 
 // Build a slot: copy g, x0 <- g, acc <- 0, tables; fill the descriptor.
@@ -133,6 +151,11 @@ pcad_status init_slot(const pcad_job &j, char *base, const SlotMem &sm, int pitc
     d.nbhd = j.model.nbhd;
     d.active = 1;
     d.m = dm;
+    d.tctab = nullptr;
+    if (sm.end > sm.tab && pca_tc_auto(dm)) {
+        d.tctab = (const float *)(base + sm.tab);
+        B_TRY(launch_tc_table(dm, (float *)(base + sm.tab), s));
+    }
     return PCAD_OK;
 }
 
@@ -247,6 +270,132 @@ int wave_grid()
     return sms * batch_wave_blocks_per_sm();
 }
 
+// Slots on the tensor-core sweep.  Large images (at least kTcBigTiles tiles
+// of 4 x 32 sites, two per resident warpgroup) fill the GPU alone and run
+// the one-chain kernel, one launch per slot and slice (its arguments are
+// baked into the launch, its planes follow the device sweep counter); the
+// others share one batched launch per (truncation, neighbourhood,
+// L % 8 != 0) group, where the per-item staging of a chain's arguments
+// costs less than the idle GPU of a small one-chain launch.
+constexpr long kTcBigTiles = 1216;
+
+struct TcGroup {
+    int T = 0, nbhd = 0;
+    bool lmask = false;
+    int nc_max = 0;
+    WaveBuf wb;
+};
+
+struct TcSet {
+    std::vector<TcGroup> groups;
+    std::vector<int> big;          // slots launched one at a time
+    unsigned int *ctr = nullptr;   // their tile counters and work counter (regrown)
+    long ctr_cap = 0;
+};
+
+// Split `active` into the tensor-core slots (those with a table: large ones
+// one by one, the others by group) and the rest (returned).
+pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
+                         const std::vector<int> &active, std::vector<int> &rest, cudaStream_t st)
+{
+    std::vector<std::vector<int>> members(ts.groups.size());
+    rest.clear();
+    ts.big.clear();
+    long big_tiles = 0;
+    for (int i : active) {
+        if (!d[i].tctab) {
+            rest.push_back(i);
+            continue;
+        }
+        const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 3) / 4);
+        if (tiles >= kTcBigTiles) {
+            ts.big.push_back(i);
+            big_tiles = std::max(big_tiles, tiles);
+            continue;
+        }
+        const bool lm = (d[i].m.L % kChunk) != 0;
+        size_t gi = 0;
+        while (gi < ts.groups.size() && !(ts.groups[gi].T == d[i].m.T &&
+                                          ts.groups[gi].nbhd == d[i].nbhd &&
+                                          ts.groups[gi].lmask == lm))
+            ++gi;
+        if (gi == ts.groups.size()) {
+            ts.groups.emplace_back();
+            ts.groups.back().T = d[i].m.T;
+            ts.groups.back().nbhd = d[i].nbhd;
+            ts.groups.back().lmask = lm;
+            members.emplace_back();
+        }
+        members[gi].push_back(i);
+    }
+    for (size_t gi = 0; gi < ts.groups.size(); ++gi) {
+        int ncm = 1;
+        for (int i : members[gi])
+            ncm = std::max(ncm, (d[i].m.L + kChunk - 1) / kChunk);
+        ts.groups[gi].nc_max = ncm;
+        pcad_status s = wave_upload(ts.groups[gi].wb, d, members[gi], 4, st);
+        if (s != PCAD_OK)
+            return s;
+    }
+    if (big_tiles + 1 > ts.ctr_cap) {
+        if (ts.ctr)
+            B_TRY(cudaFreeAsync(ts.ctr, st));
+        ts.ctr = nullptr;
+        ts.ctr_cap = std::max(big_tiles + 1, 2 * ts.ctr_cap);
+        B_TRY(cudaMallocAsync((void **)&ts.ctr, (size_t)ts.ctr_cap * sizeof(unsigned int), st));
+    }
+    return PCAD_OK;
+}
+
+// The tensor-core launches of n sweeps: one per large slot (desc: the host
+// copies of the descriptors), one per non-empty group.
+pcad_status tc_set_issue(const TcSet &ts, const std::vector<SlotDesc> &desc,
+                         const SlotDesc *slots, const uint32_t *t_arr, const uint32_t *budget_arr,
+                         int n, int *grab, int *err, cudaStream_t st)
+{
+    for (int i : ts.big) {
+        const SlotDesc &d = desc[i];
+        SweepArgs a{};
+        a.g = d.g;
+        a.acc = d.acc;
+        a.fp64_draws = d.fp64_draws;
+        a.sweep_base = d.tdev;
+        a.seed = d.seed;
+        a.H = d.H;
+        a.W = d.W;
+        a.pitch = d.pitch;
+        a.chain = d.chain;
+        a.burn_in = d.burn_in;
+        a.m = d.m;
+        const size_t tiles = (size_t)((d.W + 31) / 32) * ((d.H + 3) / 4);
+        B_TRY(cudaMemsetAsync(ts.ctr, 0, (tiles + 1) * sizeof(unsigned int), st));
+        B_TRY(launch_pca_tc(a, d.x[0], d.x[1], n, ts.ctr, ts.ctr + tiles, err, st, d.budget,
+                            true));
+    }
+    for (const TcGroup &g : ts.groups) {
+        if (g.wb.n_items == 0)
+            continue;
+        B_TRY(cudaMemsetAsync(grab, 0, sizeof(int), st));
+        B_TRY(cudaMemsetAsync(g.wb.done, 0, (size_t)g.wb.n_tiles * sizeof(unsigned int), st));
+        B_TRY(launch_batch_tc(slots, t_arr, budget_arr, g.wb.geom, g.wb.items, g.wb.n_items, n,
+                              g.T, g.nbhd, g.lmask, g.nc_max, g.wb.done, (unsigned int *)grab,
+                              err, st));
+    }
+    return PCAD_OK;
+}
+
+void tc_set_free(TcSet &ts, cudaStream_t st)
+{
+    for (TcGroup &g : ts.groups)
+        if (g.wb.mem)
+            cudaFreeAsync(g.wb.mem, st);
+    ts.groups.clear();
+    if (ts.ctr)
+        cudaFreeAsync(ts.ctr, st);
+    ts.ctr = nullptr;
+    ts.ctr_cap = 0;
+}
+
 struct TuneKey {
     int n;
     long sites[33];
@@ -290,7 +439,8 @@ struct pcad_batch {
     int lpt = 1;                     // work order: 0 image, 1 costliest first, 2 wavefront
     WaveBuf wb;                      // order 2: the wavefront work list
     int wgrid = 0;
-    int *d_err = nullptr;            // order 2: bounded-wait flag
+    int *d_err = nullptr;            // wavefront launches: bounded-wait flag
+    TcSet tc;                        // chains on the tensor-core sweep
     float tune_ms = 0.0f;
     cudaGraphExec_t graph = nullptr;
 };
@@ -299,15 +449,22 @@ namespace {
 
 pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
 {
-    std::vector<int> active(b->n);
+    std::vector<int> all(b->n), active;
     for (int i = 0; i < b->n; ++i)
-        active[i] = i;
+        all[i] = i;
+    // chains with a tensor-core table run on the batched tensor-core sweep;
+    // the tiling below applies to the others
+    pcad_status st0 = tc_set_build(b->tc, b->desc, all, active, b->stream);
+    if (st0 != PCAD_OK)
+        return st0;
     if (lpt == kOrderWave) {
         pcad_status st = wave_upload(b->wb, b->desc, active, rows, b->stream);
         if (st != PCAD_OK)
             return st;
     } else {
         std::vector<WorkItem> items = make_items(b->desc, active, rows, lpt != 0);
+        if (items.empty())
+            items.push_back(WorkItem{0, 0, 0, 0});   // placeholder: never launched
         if ((int)items.size() > b->n_items && b->d_items) {
             B_TRY(cudaFreeAsync(b->d_items, b->stream));
             b->d_items = nullptr;
@@ -317,7 +474,7 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
                                   b->stream));
         B_TRY(cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(WorkItem),
                               cudaMemcpyHostToDevice, b->stream));
-        b->n_items = (int)items.size();
+        b->n_items = active.empty() ? 0 : (int)items.size();
     }
     b->rows = rows;
     b->lpt = lpt;
@@ -330,11 +487,15 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
 
 pcad_status batch_issue_slice(pcad_batch *b, cudaStream_t s)
 {
+    pcad_status st0 = tc_set_issue(b->tc, b->desc, b->d_slots, b->d_t, b->d_budget, kSlice,
+                                   b->d_grab, b->d_err, s);
+    if (st0 != PCAD_OK)
+        return st0;
     if (b->lpt == kOrderWave) {
         pcad_status st = wave_issue(b->wb, b->d_slots, kSlice, b->d_grab, b->d_err, b->wgrid, s);
         if (st != PCAD_OK)
             return st;
-    } else {
+    } else if (b->n_items > 0) {
         B_TRY(cudaMemsetAsync(b->d_grab, 0, kSlice * sizeof(int), s));
         for (int k = 0; k < kSlice; ++k)
             B_TRY(launch_batch_sweep(b->d_slots, b->d_items, b->n_items, b->d_grab + k,
@@ -490,9 +651,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
         if (st != PCAD_OK)
             return st;
         const int pitch = (jobs[i].W + 15) / 16 * 16;
-        const int T = jobs[i].model.pair == PCAD_PAIR_POTTS ? 1 : jobs[i].model.pair_T;
-        mem[i] = slot_layout(jobs[i].H, jobs[i].W, pitch,
-                             (size_t)(jobs[i].model.nbhd * T + 1) * sizeof(double), total);
+        mem[i] = job_layout(jobs[i], pitch, total);
         total = mem[i].end;
         max_plane = std::max(max_plane, (size_t)jobs[i].H * jobs[i].W);
     }
@@ -534,6 +693,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
             cudaFreeAsync(b->d_items, b->stream);
         if (b->wb.mem)
             cudaFreeAsync(b->wb.mem, b->stream);
+        tc_set_free(b->tc, b->stream);
         cudaFreeAsync(b->block, b->stream);
         cudaStreamSynchronize(b->stream);
         delete b;
@@ -611,6 +771,15 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
     dm.ta64 = (const double *)(base + sm.ta);
     dm.pr64 = (const double *)(base + sm.pr);
     b->desc[i].m = dm;
+    if (b->desc[i].tctab) {   // the tensor-core sweep's outside sums follow the model
+        B_TRY(launch_tc_table(dm, const_cast<float *>(b->desc[i].tctab), b->stream));
+        // a large slot's launch carries the model: capture the slice again
+        if (b->graph && std::find(b->tc.big.begin(), b->tc.big.end(), i) != b->tc.big.end()) {
+            B_TRY(cudaStreamSynchronize(b->stream));
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+    }
     B_TRY(cudaMemcpyAsync(&b->d_slots[i], &b->desc[i], sizeof(SlotDesc), cudaMemcpyHostToDevice,
                           b->stream));
     B_TRY(cudaStreamSynchronize(b->stream));   // the host copies must outlive the transfers
@@ -709,6 +878,7 @@ void pcad_batch_destroy(pcad_batch *b)
         cudaFreeAsync(b->d_items, b->stream);
     if (b->wb.mem)
         cudaFreeAsync(b->wb.mem, b->stream);
+    tc_set_free(b->tc, b->stream);
     cudaFreeAsync(b->block, b->stream);
     cudaStreamSynchronize(b->stream);
     delete b;
@@ -746,9 +916,11 @@ struct pcad_server {
     unsigned long long *d_fp64 = nullptr;
     int *d_grab = nullptr;
     WaveBuf wb;                   // wavefront work list of the admitted requests
+    TcSet tc;                     // requests on the tensor-core sweep
     bool items_dirty = true;
     int grid = 0;
-    int *d_err = nullptr;          // bounded-wait flag of the wavefront kernel
+    int n_active = 0;              // admitted requests (both kinds of launch)
+    int *d_err = nullptr;          // bounded-wait flag of the wavefront kernels
     int *h_err = nullptr;          // pinned: the flag after each of the last two slices
     cudaEvent_t ev[2] = {nullptr, nullptr};
     bool in_flight = false;        // the previous slice may still be running
@@ -782,9 +954,7 @@ pcad_status server_admit(pcad_server *sv)
             return set_error(PCAD_ENOMEM, cudaGetErrorString(e));
         }
         const int pitch = (rq.job.W + 15) / 16 * 16;
-        const int T = rq.job.model.pair == PCAD_PAIR_POTTS ? 1 : rq.job.model.pair_T;
-        SlotMem sm = slot_layout(rq.job.H, rq.job.W, pitch,
-                                 (size_t)(rq.job.model.nbhd * T + 1) * sizeof(double), 0);
+        SlotMem sm = job_layout(rq.job, pitch, 0);
         pcad_job j = rq.job;
         j.g_host = rq.g.data();
         j.g_pitch = rq.job.W;
@@ -813,17 +983,22 @@ pcad_status server_admit(pcad_server *sv)
 
 pcad_status server_items(pcad_server *sv)
 {
-    std::vector<int> active;
-    long tiles4 = 0;
+    std::vector<int> all, active;
     for (int i = 0; i < sv->max_slots; ++i)
-        if (sv->slot_req[i] != 0) {
-            active.push_back(i);
-            tiles4 += (long)((sv->desc[i].W + 31) / 32) * ((sv->desc[i].H + 3) / 4);
-        }
-    const int rows = tiles4 >= (long)kServeTallTiles * sv->grid ? 8 : 4;
-    pcad_status st = wave_upload(sv->wb, sv->desc, active, rows, sv->stream);
+        if (sv->slot_req[i] != 0)
+            all.push_back(i);
+    // requests with a tensor-core table run on the batched tensor-core sweep
+    pcad_status st = tc_set_build(sv->tc, sv->desc, all, active, sv->stream);
     if (st != PCAD_OK)
         return st;
+    long tiles4 = 0;
+    for (int i : active)
+        tiles4 += (long)((sv->desc[i].W + 31) / 32) * ((sv->desc[i].H + 3) / 4);
+    const int rows = tiles4 >= (long)kServeTallTiles * sv->grid ? 8 : 4;
+    st = wave_upload(sv->wb, sv->desc, active, rows, sv->stream);
+    if (st != PCAD_OK)
+        return st;
+    sv->n_active = (int)all.size();
     sv->items_dirty = false;
     return PCAD_OK;
 }
@@ -941,10 +1116,13 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
             return st;
     }
     int finished = 0, active = 0;
-    if (sv->wb.n_items > 0) {
-        // one wavefront launch runs the slice for every admitted request
-        st = wave_issue(sv->wb, sv->d_slots, slice_sweeps, sv->d_grab, sv->d_err, sv->grid,
-                        sv->stream);
+    if (sv->n_active > 0) {
+        // one wavefront launch per kind runs the slice for every admitted request
+        st = tc_set_issue(sv->tc, sv->desc, sv->d_slots, sv->d_t, sv->d_budget, slice_sweeps,
+                          sv->d_grab, sv->d_err, sv->stream);
+        if (st == PCAD_OK && sv->wb.n_items > 0)
+            st = wave_issue(sv->wb, sv->d_slots, slice_sweeps, sv->d_grab, sv->d_err, sv->grid,
+                            sv->stream);
         if (st != PCAD_OK)
             return st;
         B_TRY(launch_batch_advance(sv->d_slots, sv->max_slots, (uint32_t)slice_sweeps,
@@ -1066,6 +1244,7 @@ void pcad_server_destroy(pcad_server *sv)
             cudaFreeAsync(kv.second.mem, sv->stream);
     if (sv->wb.mem)
         cudaFreeAsync(sv->wb.mem, sv->stream);
+    tc_set_free(sv->tc, sv->stream);
     cudaFreeAsync(sv->ctl, sv->stream);
     cudaStreamSynchronize(sv->stream);
     for (int k = 0; k < 2; ++k)

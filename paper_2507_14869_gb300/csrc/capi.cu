@@ -251,19 +251,15 @@ SweepArgs make_args(const pcad_chain *ch)
 }
 
 // Unblocked PCA sweeps on the tensor-core kernel: on request, or with AUTO
-// for eligible models with L >= kTcAutoLabels when every sweep's state is
-// not needed (energy tracking would force one launch per sweep).  On GB300
-// it measured 1.1-1.2x the CUDA-core kernels at L = 256 and slower below
-// L = 192 (the window's work does not shrink with L).
-constexpr int kTcAutoLabels = 192;
-
+// for the models pca_tc_auto accepts when every sweep's state is not needed
+// (energy tracking would force one launch per sweep).
 bool uses_tc(const pcad_chain *ch)
 {
     if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !pca_tc_eligible(ch->dm))
         return false;
     if (ch->kernel == PCAD_KERNEL_TENSOR)
         return true;
-    return ch->kernel == PCAD_KERNEL_AUTO && ch->model.L >= kTcAutoLabels && !ch->track.trace;
+    return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace;
 }
 
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).

@@ -115,7 +115,30 @@ struct SlotDesc {
     int nbhd;
     int active;        // 0: skip (free serving slot)
     DevModel m;
+    const float *tctab;   // tensor-core sweep: outside-window chunk sums of the model
 };
+
+// Chain descriptor -> sweep arguments of sweep t (the chunk class travels in
+// last_phase and the neighbourhood in sweep_off, which the tile code does
+// not read).
+__device__ __forceinline__ void slot_args(const SlotDesc &d, uint32_t t, SweepArgs &a)
+{
+    a = SweepArgs{};
+    a.xin = d.x[t & 1u];
+    a.xout = d.x[(t + 1u) & 1u];
+    a.g = d.g;
+    a.acc = d.acc;
+    a.fp64_draws = d.fp64_draws;
+    a.seed = d.seed;
+    a.H = d.H;
+    a.W = d.W;
+    a.pitch = d.pitch;
+    a.chain = d.chain;
+    a.burn_in = d.burn_in;
+    a.last_phase = d.ncls;
+    a.sweep_off = (uint32_t)d.nbhd;
+    a.m = d.m;
+}
 
 // A tile of `rows` x 32 sites of one slot.
 struct WorkItem {
@@ -216,8 +239,38 @@ int wave_tiles(int H, int W);
 constexpr int kTcMinLabels = 64;
 constexpr int kTcMaxT = 33;
 bool pca_tc_eligible(const DevModel &m);
+// budget (optional): sweeps with index >= *budget are skipped.  par_from_t:
+// x0 / x1 are the planes of even / odd sweep indices (else of sweeps 0 / 1
+// of the launch).
 cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
-                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t s);
+                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t s,
+                          const uint32_t *budget = nullptr, bool par_from_t = false);
+
+// Models the automatic kernel choice gives the tensor-core sweep: eligible
+// and L >= kTcAutoLabels (on GB300 it measured 1.1-1.2x the CUDA-core
+// kernels at L = 256 and slower below L = 192: the window's work does not
+// shrink with L).
+constexpr int kTcAutoLabels = 192;
+bool pca_tc_auto(const DevModel &m);
+
+// The outside-window chunk sums of a model, as the batched tensor-core
+// sweep reads them: tc_table_floats(L) floats (16-byte aligned), written by
+// launch_tc_table.
+int tc_table_floats(int L);
+cudaError_t launch_tc_table(const DevModel &m, float *out, cudaStream_t s);
+
+// Batched tensor-core sweeps: nsweeps sweeps of every slot listed in items
+// (tiles of 4 rows x 32 sites of the slot's grid in geom, rows = 4) in one
+// wavefront launch; slot s runs sweeps t_arr[s] + k while below
+// budget_arr[s] (the arrays behind its descriptor's tdev and budget).
+// Every slot of a launch has truncation T, neighbourhood nbhd, L % 8 != 0
+// exactly when lmask, at most nc_max chunks, a tensor-core eligible model
+// and its table in tctab.  done (every tile) and grab zero on entry.
+cudaError_t launch_batch_tc(const SlotDesc *slots, const uint32_t *t_arr,
+                            const uint32_t *budget_arr, const WaveGeom *geom,
+                            const WaveItem *items, int n_items, int nsweeps, int T, int nbhd,
+                            bool lmask, int nc_max, unsigned int *done, unsigned int *grab,
+                            int *err, cudaStream_t s);
 
 // TMA descriptor of a uint8 plane (box 96 x 48); false if the driver refuses.
 bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);

@@ -235,27 +235,6 @@ __device__ __forceinline__ void batch_dispatch(const SweepArgs *sa, int ncls, in
     }
 }
 
-// Chain descriptor -> sweep arguments of sweep t (the chunk class travels in
-// last_phase and the neighbourhood in sweep_off, which the tile code does
-// not read).
-__device__ __forceinline__ void slot_args(const SlotDesc &d, uint32_t t, SweepArgs &a)
-{
-    a = SweepArgs{};
-    a.xin = d.x[t & 1u];
-    a.xout = d.x[(t + 1u) & 1u];
-    a.g = d.g;
-    a.acc = d.acc;
-    a.fp64_draws = d.fp64_draws;
-    a.seed = d.seed;
-    a.H = d.H;
-    a.W = d.W;
-    a.pitch = d.pitch;
-    a.chain = d.chain;
-    a.burn_in = d.burn_in;
-    a.last_phase = d.ncls;
-    a.sweep_off = (uint32_t)d.nbhd;
-    a.m = d.m;
-}
 
 __global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *__restrict__ slots,
                                                              const WorkItem *__restrict__ items,

@@ -78,18 +78,32 @@ constexpr int kOffB = 0;
 constexpr int kOffA = kOpBytes;
 constexpr int kOffG = kOffA + kGroups * kOpBytes;
 
-constexpr int kTabRow = 257;   // outside-chunk table row: 256 observations + 1 (bank skew)
+// Outside-chunk table of a model: the sum of chunk c for observation g is
+// F(g - 8c), F(d) = sum_k 2^(alpha (d - k)^2), at [d + 255] (d in
+// [-255, 255]); when L % 8 != 0 the last chunk's masked sums follow at
+// [kTabLast + g].  768 floats (3 KB).
+constexpr int kTabLast = 512;
+constexpr int kTabF = 768;
 
-// Floats of the outside-chunk table, rounded up so the mbarriers after it
-// stay 8-byte aligned.
-__host__ __device__ constexpr int tab_floats(int nc)
+// After G (and the one-chain table): mbarriers, work items and the TMEM
+// base (64 bytes), then for batched chains the staged items of each group.
+constexpr int kTcCtlBytes = 64;
+constexpr int kTcStageBytes = 2 * kGroups * ((int)sizeof(SweepArgs) + 4 + 4);
+
+// One chain keeps the outside sums as a [chunk][observation] table (row
+// stride 257 against bank conflicts), rounded to an even float count.
+constexpr int kTabRow = 257;
+__host__ __device__ constexpr int tab2_floats(int nc)
 {
     return (nc * kTabRow + 1) & ~1;
 }
 
-__host__ __device__ constexpr int tc_smem_bytes(int nc)
+// G, then the tables (one chain: the 2-D table; batched chains: two 1-D
+// tables per group), control, stage.
+__host__ __device__ constexpr int tc_smem_bytes(int nc, bool batch)
 {
-    return kOffG + nc * kThr * 4 + tab_floats(nc) * 4 + 8 * kGroups + 4 * kGroups + 16;
+    return kOffG + nc * kThr * 4 + (batch ? 2 * kGroups * kTabF : tab2_floats(nc)) * 4 +
+           kTcCtlBytes + (batch ? kTcStageBytes : 0);
 }
 
 // Byte offset of element (row, k), k < 64, of a K-major operand in the
@@ -227,6 +241,27 @@ __device__ __forceinline__ float outside_chunk(const DevModel &m, float gf, int 
     return S;
 }
 
+// Entry i of the outside-chunk table (the same operations as outside_chunk,
+// hence the same values).
+template <bool LMASK>
+__device__ __forceinline__ float tab_entry(const DevModel &m, int i)
+{
+    if (i < 2 * 255 + 1)
+        return outside_chunk<false>(m, (float)(i - 255), 0);
+    if (LMASK && i >= kTabLast && i < kTabLast + 256)
+        return outside_chunk<true>(m, (float)(i - kTabLast), (m.L - 1) / kChunk);
+    return 0.0f;
+}
+
+// Outside sum of chunk c (of nc) for observation g.
+template <bool LMASK>
+__device__ __forceinline__ float tab_sum(const float *tab, int g, int c, int nc)
+{
+    if (LMASK && c == nc - 1)
+        return tab[kTabLast + g];
+    return tab[g - kChunk * c + 255];
+}
+
 // Sum of the weights of window chunk c from 8 tent sums read from TMEM (pb,
 // raw FP32 bits).
 template <bool LMASK>
@@ -324,11 +359,119 @@ __device__ __forceinline__ bool wait_counter(const unsigned int *d, unsigned int
     return ok;
 }
 
-template <int NB, bool LMASK>
-__global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uint8_t *x0,
-                                                          uint8_t *x1, int nsweeps, int tiles_x,
-                                                          int tiles_y, int nc, unsigned int *done,
-                                                          unsigned int *grab, int *err)
+// Launch parameters.  One chain (BATCH false): a, the planes and the tile
+// grid.  Batched chains (BATCH true): slot descriptors with their tile grids
+// (4-row tiles, counters done[base + tile]) and the tiles of one sweep; the
+// sweep index of slot s is *tdev + k and a slot stops at its budget.
+struct TcParams {
+    SweepArgs a;
+    uint8_t *x0, *x1;    // planes of sweep 0 and 1 of the launch, or (par_from_t) of even and odd t
+    const uint32_t *budget;   // one chain: sweeps t >= *budget are skipped (nullptr: none)
+    int par_from_t;
+    int tiles_x, tiles_y;
+    const SlotDesc *slots;
+    const uint32_t *t_arr, *budget_arr;   // slot s: sweep counter t_arr[s], budget budget_arr[s]
+    const WaveGeom *geom;
+    const WaveItem *items;
+    int n_items;
+    int nsweeps;
+    int T;               // truncation shared by every chain of the launch (B operand)
+    int nc_max;          // largest chunk count of the launch's chains
+    unsigned int *done, *grab;
+    int *err;
+};
+
+// One work item: sweep k of `tile` (of a tiles_x x tiles_y grid whose
+// counters start at done + base) of chain `slot`.
+struct TcItem {
+    int k, tile, tx, ty, tiles_x, tiles_y, base, slot;
+};
+
+template <bool BATCH>
+__device__ __forceinline__ TcItem tc_decode(const TcParams &p, unsigned int item)
+{
+    TcItem it;
+    if constexpr (BATCH) {
+        it.k = (int)(item / (unsigned int)p.n_items);
+        const WaveItem w = p.items[item - (unsigned int)it.k * (unsigned int)p.n_items];
+        const WaveGeom g = p.geom[w.slot];
+        it.slot = w.slot;
+        it.tile = w.tile;
+        it.tiles_x = g.tiles_x;
+        it.tiles_y = g.tiles_y;
+        it.base = g.base;
+    } else {
+        const unsigned int ntiles = (unsigned int)(p.tiles_x * p.tiles_y);
+        it.k = (int)(item / ntiles);
+        it.tile = (int)(item - (unsigned int)it.k * ntiles);
+        it.slot = 0;
+        it.tiles_x = p.tiles_x;
+        it.tiles_y = p.tiles_y;
+        it.base = 0;
+    }
+    it.ty = it.tile / it.tiles_x;
+    it.tx = it.tile - it.ty * it.tiles_x;
+    return it;
+}
+
+// Batched chains, warp 0 of a group: stage item ii (lane 0: its arguments,
+// sweep and run flag; every lane: its chain's outside-chunk table into
+// `tab`).  Returns whether the chain runs that sweep (active and within its
+// budget).
+__device__ __forceinline__ bool tc_stage_warp(const TcParams &p, const TcItem &ii, int lane,
+                                              SweepArgs *sa, uint32_t *tt, int *go, float *tab)
+{
+    int run = 0;
+    unsigned long long src = 0ull;
+    if (lane == 0) {
+        const SlotDesc &d = p.slots[ii.slot];
+        const uint32_t t = p.t_arr[ii.slot] + (uint32_t)ii.k;
+        if (d.active && t < p.budget_arr[ii.slot]) {
+            slot_args(d, t, *sa);
+            *tt = t;
+            run = 1;
+            src = reinterpret_cast<unsigned long long>(d.tctab);
+        }
+        *go = run;
+    }
+    run = __shfl_sync(0xFFFFFFFFu, run, 0);
+    if (run) {
+        src = __shfl_sync(0xFFFFFFFFu, src, 0);
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(tab);
+        for (int i = lane; i < kTabF / 4; i += 32)
+            d4[i] = __ldg(s4 + i);
+    }
+    return run != 0;
+}
+
+// Warp 0 of a group, lanes 0-8: wait for the 3 x 3 tiles around item ii to
+// finish sweep k - 1 (pre_d, pre: an earlier look at a counter).
+template <bool BATCH>
+__device__ __forceinline__ void tc_wait_item(const TcParams &p, const TcItem &ii, int lane,
+                                             const unsigned int *pre_d, unsigned int pre)
+{
+    const unsigned int *d =
+        dep_counter(p.done + ii.base, ii.k, ii.tile, ii.tiles_x, ii.tiles_y, lane);
+    const unsigned int seen = (d && d == pre_d) ? pre : (d ? ld_relaxed_gpu(d) : 0u);
+    if (!wait_counter(d, (unsigned int)ii.k, seen))
+        atomicExch(p.err, 1);
+}
+
+// The arguments of the current item: the launch's (one chain, read from
+// the kernel parameters) or the staged ones (batched chains).
+template <bool BATCH>
+__device__ __forceinline__ const SweepArgs &item_args(const TcParams &p, const SweepArgs *staged)
+{
+    if constexpr (BATCH)
+        return *staged;
+    else
+        return p.a;
+}
+
+// BUDGET (one chain): sweeps with index >= *p.budget are skipped.
+template <int NB, bool LMASK, bool BATCH, bool BUDGET>
+__global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
     const int tid = (int)threadIdx.x;
@@ -338,16 +481,25 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
     const int lane = tid & 31;
     if (smem_u32(smem) & 1023u) {      // the swizzled operands need 1024-byte alignment
         if (tid == 0)
-            atomicExch(err, 2);
+            atomicExch(p.err, 2);
         return;
     }
+    const int ncm = p.nc_max;
     uint8_t *B = smem + kOffB;
     uint8_t *A = smem + kOffA + grp * kOpBytes;
     float *Gcol = reinterpret_cast<float *>(smem + kOffG) + tid;
-    float *Tab = reinterpret_cast<float *>(smem + kOffG + nc * kThr * 4);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(Tab + tab_floats(nc));
+    // outside-chunk tables: the chain's, or two per group (staged items)
+    float *tabs = reinterpret_cast<float *>(smem + kOffG + ncm * kThr * 4);
+    uint64_t *mbar =
+        reinterpret_cast<uint64_t *>(tabs + (BATCH ? 2 * kGroups * kTabF : tab2_floats(ncm)));
     unsigned int *s_item = reinterpret_cast<unsigned int *>(mbar + kGroups);
     uint32_t *tmem_slot = s_item + kGroups;
+    // batched chains: per group, two staged items (arguments, sweep, run flag)
+    SweepArgs *s_args = reinterpret_cast<SweepArgs *>(
+        reinterpret_cast<uint8_t *>(mbar) + kTcCtlBytes);
+    uint32_t *s_t = reinterpret_cast<uint32_t *>(s_args + 2 * kGroups);
+    int *s_go = reinterpret_cast<int *>(s_t + 2 * kGroups);
+    float *gtabs = tabs + grp * 2 * kTabF;   // batched chains: this group's two tables
 
     // A starts zero; B holds K(k, c) at row c (window label), column k (bin)
     for (int i = tid; i < (kOpBytes * (1 + kGroups)) / 16; i += kThr)
@@ -355,14 +507,16 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
     __syncthreads();
     for (int i = tid; i < kWin * kBins; i += kThr) {
         const int c = i / kBins, k = i - (i / kBins) * kBins;
-        const int v = max(a.m.T - abs(c - (a.m.T - 1) - k), 0);
+        const int v = max(p.T - abs(c - (p.T - 1) - k), 0);
         *reinterpret_cast<__half *>(B + sw128_offset(c, k)) = __int2half_rn(v);
     }
-    // outside-chunk sums: chunk c of observation g (the same function, hence
-    // the same values, as computing them per site)
-    for (int i = tid; i < nc * 256; i += kThr) {
-        const int c = i >> 8, gobs = i & 255;
-        Tab[c * kTabRow + gobs] = outside_chunk<LMASK>(a.m, (float)gobs, c);
+    if constexpr (!BATCH) {
+        // outside-chunk sums: chunk c of observation g (the same function,
+        // hence the same values, as computing them per site)
+        for (int i = tid; i < ncm * 256; i += kThr) {
+            const int c = i >> 8, gobs = i & 255;
+            tabs[c * kTabRow + gobs] = outside_chunk<LMASK>(p.a.m, (float)gobs, c);
+        }
     }
     if (tid == 0) {
         for (int g = 0; g < kGroups; ++g)
@@ -381,10 +535,10 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
     const uint32_t tcol = tmem + (uint32_t)(grp * kWin);          // the group's columns
     const uint32_t trow = tcol + ((uint32_t)(q * 32) << 16);      // this warp's lanes
     const int bar_id = 1 + grp;
-    const float mu = -a.m.gam;
-    const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
-    const unsigned int total = ntiles * (unsigned int)nsweeps;
-    const uint32_t t0 = sweep_index(a);
+    const unsigned int total =
+        (unsigned int)(BATCH ? p.n_items : p.tiles_x * p.tiles_y) * (unsigned int)p.nsweeps;
+    const uint32_t t0 = BATCH ? 0u : sweep_index(p.a);
+    const uint32_t tlim = BUDGET ? *p.budget : 0xFFFFFFFFu;   // one chain
 
     uint32_t prev_off[NB];   // A entries this thread set for its previous item
 #pragma unroll
@@ -392,19 +546,22 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
         prev_off[j] = ~0u;
     int uses = 0;            // completed phases of the group's mbarrier
     bool ok = true;
+    unsigned int seq = 0;    // items this group took (parity: staging buffer)
 
-    // first item
+    // first item (warp 0 waits for its neighbourhood; thread 0 stages it)
     if (q == 0) {
         unsigned int it = 0;
         if (lane == 0)
-            it = atomicAdd(grab, 1u);
+            it = atomicAdd(p.grab, 1u);
         it = __shfl_sync(0xFFFFFFFFu, it, 0);
         if (it < total) {
-            const int k = (int)(it / ntiles);
-            const unsigned int *d =
-                dep_counter(done, k, (int)(it - (unsigned int)k * ntiles), tiles_x, tiles_y, lane);
-            if (!wait_counter(d, (unsigned int)k, d ? ld_relaxed_gpu(d) : 0u))
-                atomicExch(err, 1);
+            const TcItem ii = tc_decode<BATCH>(p, it);
+            bool run = !BUDGET || t0 + (uint32_t)ii.k < tlim;
+            if constexpr (BATCH)
+                run = tc_stage_warp(p, ii, lane, s_args + grp * 2, s_t + grp * 2, s_go + grp * 2,
+                                    gtabs);
+            if (run)
+                tc_wait_item<BATCH>(p, ii, lane, nullptr, 0u);
         }
         if (lane == 0)
             s_item[grp] = it;
@@ -414,204 +571,273 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
     unsigned int next = 0;   // warp 0, lane 0: the item taken for after this one
 
     while (item < total) {
-        const int k = (int)(item / ntiles);
-        const int j = (int)(item - (unsigned int)k * ntiles);
-        const int ty = j / tiles_x;
-        const int tx = j - ty * tiles_x;
-        const int r = ty * kTileRows + q;
-        const int c = tx * 32 + lane;
-        const bool valid = r < a.H && c < a.W;
-        SweepArgs b = a;
-        b.xin = (k & 1) ? x1 : x0;
-        b.xout = (k & 1) ? x0 : x1;
-        const uint32_t t = t0 + (uint32_t)k;
-
-        // site inputs, window, histogram row
-        TcSite<NB> st;
-        st.in = SiteIn<NB>{};
-        if (valid)
-            load_site<NB, true>(b, b.xin, r, c, kTagPCA, t, st.in);
-        float *accp = a.acc + (size_t)r * a.W + c;
-        const bool acc_on = valid && accumulate_after(b, t);
-        const float acc_old = acc_on ? __ldcg(accp) : 0.0f;   // prefetched
-#pragma unroll
-        for (int jn = 0; jn < NB; ++jn)
-            st.xn[jn] = (float)st.in.xni[jn];
-        st.gf = (float)st.in.g;
-        uint32_t off[NB];
-        int cnt[NB];
-        site_window<NB>(st, a.m.T, lt, valid, off, cnt);
-#pragma unroll
-        for (int jn = 0; jn < NB; ++jn)
-            if (prev_off[jn] != ~0u)
-                *reinterpret_cast<__half *>(A + prev_off[jn]) = __ushort_as_half((unsigned short)0);
-#pragma unroll
-        for (int jn = 0; jn < NB; ++jn) {
-            if (off[jn] != ~0u)
-                *reinterpret_cast<__half *>(A + off[jn]) = __int2half_rn(cnt[jn]);
-            prev_off[jn] = off[jn];
+        const unsigned int par = seq & 1u;
+        const TcItem ii = tc_decode<BATCH>(p, item);
+        const int k = ii.k;
+        const int r = ii.ty * kTileRows + q;
+        const int c = ii.tx * 32 + lane;
+        bool go = true;
+        const SweepArgs *bp = nullptr;   // batched chains: the staged arguments
+        const float *tab;        // outside-chunk sums (shared memory)
+        const uint8_t *xin;      // planes of this sweep
+        uint8_t *xout;
+        uint32_t t;
+        if constexpr (BATCH) {
+            go = s_go[grp * 2 + par] != 0;
+            bp = &s_args[grp * 2 + par];
+            tab = gtabs + par * kTabF;
+            t = s_t[grp * 2 + par];
+            xin = bp->xin;
+            xout = bp->xout;
+        } else {
+            t = t0 + (uint32_t)k;
+            const uint32_t ph = p.par_from_t ? (t & 1u) : (uint32_t)(k & 1);
+            xin = ph ? p.x1 : p.x0;
+            xout = ph ? p.x0 : p.x1;
+            tab = tabs;
+            if constexpr (BUDGET)
+                go = t < tlim;
         }
-        fence_async_smem();
-        tc_fence_before_sync();
-        named_bar_sync(bar_id, kSites);   // rows written, the previous item's TMEM reads done
-        if (lt == 0) {
-            tc_fence_after_sync();
-            const uint64_t adesc = sw128_kmajor_desc(smem_u32(A));
-            const uint64_t bdesc = sw128_kmajor_desc(smem_u32(B));
-#pragma unroll
-            for (int ks = 0; ks < kBins / 16; ++ks)   // 32-byte K steps inside the row
-                umma_f16_ss(tcol, adesc + (uint64_t)(2 * ks), bdesc + (uint64_t)(2 * ks), kIdesc,
-                            ks > 0 ? 1u : 0u);
-            umma_commit(&mbar[grp]);
-            next = atomicAdd(grab, 1u);   // used at the end of this item
-        }
-
-        // outside chunks, while the tensor core runs
-        const int lo = max(st.m, 0);
-        const int hi = min(st.m + kWinChunks, nc);
-        const int n_oc = lo + nc - hi;
-        const int n_oc_w = __reduce_max_sync(0xFFFFFFFFu, n_oc);
-        const float *trow_g = Tab + st.in.g;
-#pragma unroll 4
-        for (int jj = 0; jj < n_oc_w; ++jj) {
-            const int cc = jj < lo ? jj : hi + (jj - lo);
-            if (jj < n_oc)
-                Gcol[cc * kThr] = trow_g[cc * kTabRow];
-        }
-
-        // first look at the next item's neighbourhood (warp 0), used at the end
-        const unsigned int *dnext = nullptr;
+        const unsigned int *dnext = nullptr;   // warp 0: an early look at the next item
         unsigned int seen = 0u;
-        int knext = 0;
-        if (q == 0) {
-            const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
-            if (nx < total) {
-                knext = (int)(nx / ntiles);
-                dnext = dep_counter(done, knext, (int)(nx - (unsigned int)knext * ntiles), tiles_x,
-                                    tiles_y, lane);
-                if (dnext)
-                    seen = ld_relaxed_gpu(dnext);
-            }
-        }
+        int knext = -1;                        // its sweep (-1: no look taken)
 
-        // window chunks from TMEM
-        if (!mbar_wait_bounded(&mbar[grp], (uint32_t)(uses & 1), kTcSpinLimit)) {
-            atomicExch(err, 1);
-            ok = false;
-        }
-        ++uses;
-        tc_fence_after_sync();
-        // 32-column groups up to the warp's last chunk with a tent; the
-        // window chunks after it hold zero tent sums: outside sums
-        const int ngrp = (__reduce_max_sync(0xFFFFFFFFu, st.wlast) >> 2) + 1;
-#pragma unroll 1
-        for (int h = 0; h < ngrp; ++h) {
-            uint32_t pb[32];
-            tmem_ld32(trow + (uint32_t)(32 * h), pb);
-            tmem_wait_ld(pb);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int cc = st.m + 4 * h + i;
-                const float S = window_chunk<LMASK>(a.m, mu, st.gf, pb + 8 * i, cc);
-                if (cc >= 0 && cc < nc)
-                    Gcol[cc * kThr] = S;
-            }
-        }
-#pragma unroll 1
-        for (int i = 4 * ngrp; i < kWinChunks; ++i) {
-            const int cc = st.m + i;
-            if (cc >= 0 && cc < nc)
-                Gcol[cc * kThr] = trow_g[cc * kTabRow];
-        }
-        tc_fence_before_sync();
+        if (go) {
+            const SweepArgs &b = item_args<BATCH>(p, bp);
+            const DevModel &m = b.m;
+            const float mu = -m.gam;
+            const int nc = (m.L + kChunk - 1) / kChunk;
+            const bool valid = r < b.H && c < b.W;
 
-        // chunks an outlier's tent reaches are recomputed from exact tent
-        // sums; the (site, chunk) tasks of the warp are dealt out to all 32
-        // lanes (a lane takes task lane + 32 r and writes the owner's column)
-        const uint32_t omask = outlier_chunks<NB>(st, a.m.T, nc);
-        if (__any_sync(0xFFFFFFFFu, omask != 0u)) {
-            const int cnt = __popc(omask);
-            int incl = cnt;
+            // site inputs, window, histogram row
+            TcSite<NB> st;
+            st.in = SiteIn<NB>{};
+            if (valid)
+                load_site<NB, true>(b, xin, r, c, kTagPCA, t, st.in);
+            float *accp = b.acc + (size_t)r * b.W + c;
+            const bool acc_on = valid && accumulate_after(b, t);
+            const float acc_old = acc_on ? __ldcg(accp) : 0.0f;   // prefetched
 #pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-                if (lane >= o)
-                    incl += v;
+            for (int jn = 0; jn < NB; ++jn)
+                st.xn[jn] = (float)st.in.xni[jn];
+            st.gf = (float)st.in.g;
+            uint32_t off[NB];
+            int cnt[NB];
+            site_window<NB>(st, m.T, lt, valid, off, cnt);
+#pragma unroll
+            for (int jn = 0; jn < NB; ++jn)
+                if (prev_off[jn] != ~0u)
+                    *reinterpret_cast<__half *>(A + prev_off[jn]) =
+                        __ushort_as_half((unsigned short)0);
+#pragma unroll
+            for (int jn = 0; jn < NB; ++jn) {
+                if (off[jn] != ~0u)
+                    *reinterpret_cast<__half *>(A + off[jn]) = __int2half_rn(cnt[jn]);
+                prev_off[jn] = off[jn];
             }
-            const int ntask = __shfl_sync(0xFFFFFFFFu, incl, 31);
-#pragma unroll 1
-            for (int base = 0; base < ntask; base += 32) {
-                const int tsk = base + lane;
-                int owner = 0;   // lanes whose inclusive count is <= tsk
+            fence_async_smem();
+            tc_fence_before_sync();
+            named_bar_sync(bar_id, kSites);   // rows written, the previous item's TMEM reads done
+            if (lt == 0) {
+                tc_fence_after_sync();
+                const uint64_t adesc = sw128_kmajor_desc(smem_u32(A));
+                const uint64_t bdesc = sw128_kmajor_desc(smem_u32(B));
 #pragma unroll
-                for (int step = 16; step >= 1; step >>= 1) {
-                    const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
-                    if (v <= tsk)
-                        owner += step;
+                for (int ks = 0; ks < kBins / 16; ++ks)   // 32-byte K steps inside the row
+                    umma_f16_ss(tcol, adesc + (uint64_t)(2 * ks), bdesc + (uint64_t)(2 * ks),
+                                kIdesc, ks > 0 ? 1u : 0u);
+                umma_commit(&mbar[grp]);
+                next = atomicAdd(p.grab, 1u);   // used at the end of this item
+            }
+            if constexpr (BATCH) {
+                // stage the next item now, off the group's critical path
+                if (q == 0) {
+                    const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
+                    if (nx < total)
+                        tc_stage_warp(p, tc_decode<BATCH>(p, nx), lane, s_args + grp * 2 + (par ^ 1u),
+                                      s_t + grp * 2 + (par ^ 1u), s_go + grp * 2 + (par ^ 1u),
+                                      gtabs + (par ^ 1u) * kTabF);
                 }
-                owner = min(owner, 31);
-                const int o_excl = __shfl_sync(0xFFFFFFFFu, incl - cnt, owner);
-                const uint32_t o_mask = __shfl_sync(0xFFFFFFFFu, omask, owner);
-                const float o_gf = __shfl_sync(0xFFFFFFFFu, st.gf, owner);
-                float o_xn[NB];
-#pragma unroll
-                for (int jn = 0; jn < NB; ++jn)
-                    o_xn[jn] = __shfl_sync(0xFFFFFFFFu, st.xn[jn], owner);
-                const bool mine = tsk < ntask;
-                const int cc = mine ? (int)__fns(o_mask, 0u, tsk - o_excl + 1) : 0;
-                float p[kChunk];
-                chunk_prefix_exact<NB>(a.m, mu, o_xn, o_gf, cc, p);
-                if (mine)
-                    Gcol[cc * kThr + owner - lane] = p[kChunk - 1];
             }
-        }
 
-        // chunk prefix sums in label order (Kahan), certified selection
-        float G = 0.0f, comp = 0.0f;
+            // outside chunks, while the tensor core runs
+            const int lo = max(st.m, 0);
+            const int hi = min(st.m + kWinChunks, nc);
+            const int n_oc = lo + nc - hi;
+            const int n_oc_w = __reduce_max_sync(0xFFFFFFFFu, n_oc);
+            // outside sum of chunk cc: the chain's 2-D table or the staged 1-D one
+            const auto outside = [&](int cc) {
+                if constexpr (BATCH)
+                    return tab_sum<LMASK>(tab, st.in.g, cc, nc);
+                else
+                    return tab[cc * kTabRow + st.in.g];
+            };
+#pragma unroll 4
+            for (int jj = 0; jj < n_oc_w; ++jj) {
+                const int cc = jj < lo ? jj : hi + (jj - lo);
+                if (jj < n_oc)
+                    Gcol[cc * kThr] = outside(cc);
+            }
+
+            // an early look at the next item's neighbourhood (warp 0)
+            if (q == 0) {
+                const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
+                if (nx < total) {
+                    const TcItem in2 = tc_decode<BATCH>(p, nx);
+                    knext = in2.k;
+                    dnext = dep_counter(p.done + in2.base, in2.k, in2.tile, in2.tiles_x,
+                                        in2.tiles_y, lane);
+                    if (dnext)
+                        seen = ld_relaxed_gpu(dnext);
+                }
+            }
+
+            // window chunks from TMEM
+            if (!mbar_wait_bounded(&mbar[grp], (uint32_t)(uses & 1), kTcSpinLimit)) {
+                atomicExch(p.err, 1);
+                ok = false;
+            }
+            ++uses;
+            tc_fence_after_sync();
+            // 32-column groups up to the warp's last chunk with a tent; the
+            // window chunks after it hold zero tent sums: outside sums
+            const int ngrp = (__reduce_max_sync(0xFFFFFFFFu, st.wlast) >> 2) + 1;
+#pragma unroll 1
+            for (int h = 0; h < ngrp; ++h) {
+                uint32_t pb[32];
+                tmem_ld32(trow + (uint32_t)(32 * h), pb);
+                tmem_wait_ld(pb);
 #pragma unroll
-        for (int cc = 0; cc < 32; ++cc) {
-            if (cc < nc) {
-                const float y = __fsub_rn(Gcol[cc * kThr], comp);
-                const float tt = __fadd_rn(G, y);
-                comp = __fsub_rn(__fsub_rn(tt, G), y);
-                G = tt;
-                Gcol[cc * kThr] = G;
+                for (int i = 0; i < 4; ++i) {
+                    const int cc = st.m + 4 * h + i;
+                    const float S = window_chunk<LMASK>(m, mu, st.gf, pb + 8 * i, cc);
+                    if (cc >= 0 && cc < nc)
+                        Gcol[cc * kThr] = S;
+                }
             }
-        }
-        int s = 0;
-        bool certain = true;
-        if (valid) {
-            float delta = 0.0f;
-            if (a.m.em1 != 0.0f) {
-                const float xif = (float)st.in.xi;
-                delta = __fmul_rn(label_wb(a.m.alpha, mu, tent_sum<NB>(st.xn, a.m.Tf, xif),
-                                           __fsub_rn(st.gf, xif)),
-                                  a.m.em1);
+#pragma unroll 1
+            for (int i = 4 * ngrp; i < kWinChunks; ++i) {
+                const int cc = st.m + i;
+                if (cc >= 0 && cc < nc)
+                    Gcol[cc * kThr] = outside(cc);
             }
-            s = cdf_select(a.m, a.m.eta_b, [&](int cc) { return Gcol[cc * kThr]; }, nc, G, delta,
-                           st.in.xi, st.in.ub, certain, [&](int cs, float (&p)[kChunk]) {
-                               chunk_prefix_exact<NB>(a.m, mu, st.xn, st.gf, cs, p);
-                           });
-        }
-        s = warp_redraw_fp64<NB>(a.m, valid && !certain, st.in, s, a.fp64_draws);
-        if (valid) {
-            b.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-            if (acc_on)
-                *accp = acc_old + (float)s;
+            tc_fence_before_sync();
+
+            // chunks an outlier's tent reaches are recomputed from exact tent
+            // sums; the (site, chunk) tasks of the warp are dealt out to all
+            // 32 lanes (a lane takes task lane + 32 r and writes the owner's
+            // column)
+            const uint32_t omask = outlier_chunks<NB>(st, m.T, nc);
+            if (__any_sync(0xFFFFFFFFu, omask != 0u)) {
+                const int cntb = __popc(omask);
+                int incl = cntb;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                    if (lane >= o)
+                        incl += v;
+                }
+                const int ntask = __shfl_sync(0xFFFFFFFFu, incl, 31);
+#pragma unroll 1
+                for (int base = 0; base < ntask; base += 32) {
+                    const int tsk = base + lane;
+                    int owner = 0;   // lanes whose inclusive count is <= tsk
+#pragma unroll
+                    for (int step = 16; step >= 1; step >>= 1) {
+                        const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
+                        if (v <= tsk)
+                            owner += step;
+                    }
+                    owner = min(owner, 31);
+                    const int o_excl = __shfl_sync(0xFFFFFFFFu, incl - cntb, owner);
+                    const uint32_t o_mask = __shfl_sync(0xFFFFFFFFu, omask, owner);
+                    const float o_gf = __shfl_sync(0xFFFFFFFFu, st.gf, owner);
+                    float o_xn[NB];
+#pragma unroll
+                    for (int jn = 0; jn < NB; ++jn)
+                        o_xn[jn] = __shfl_sync(0xFFFFFFFFu, st.xn[jn], owner);
+                    const bool mine = tsk < ntask;
+                    const int cc = mine ? (int)__fns(o_mask, 0u, tsk - o_excl + 1) : 0;
+                    float pp[kChunk];
+                    chunk_prefix_exact<NB>(m, mu, o_xn, o_gf, cc, pp);
+                    if (mine)
+                        Gcol[cc * kThr + owner - lane] = pp[kChunk - 1];
+                }
+                __syncwarp();   // the owners read their columns below
+            }
+
+            // chunk prefix sums in label order (Kahan), certified selection
+            float G = 0.0f, comp = 0.0f;
+#pragma unroll
+            for (int cc = 0; cc < 32; ++cc) {
+                if (cc < nc) {
+                    const float y = __fsub_rn(Gcol[cc * kThr], comp);
+                    const float tt = __fadd_rn(G, y);
+                    comp = __fsub_rn(__fsub_rn(tt, G), y);
+                    G = tt;
+                    Gcol[cc * kThr] = G;
+                }
+            }
+            int s = 0;
+            bool certain = true;
+            if (valid) {
+                float delta = 0.0f;
+                if (m.em1 != 0.0f) {
+                    const float xif = (float)st.in.xi;
+                    delta = __fmul_rn(label_wb(m.alpha, mu, tent_sum<NB>(st.xn, m.Tf, xif),
+                                               __fsub_rn(st.gf, xif)),
+                                      m.em1);
+                }
+                s = cdf_select(m, m.eta_b, [&](int cc) { return Gcol[cc * kThr]; }, nc, G, delta,
+                               st.in.xi, st.in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
+                                   chunk_prefix_exact<NB>(m, mu, st.xn, st.gf, cs, pp);
+                               });
+            }
+            s = warp_redraw_fp64<NB>(m, valid && !certain, st.in, s, b.fp64_draws);
+            if (valid) {
+                xout[(size_t)r * b.pitch + c] = (uint8_t)s;
+                if (acc_on)
+                    *accp = acc_old + (float)s;
+            }
+        } else if (lt == 0) {
+            next = atomicAdd(p.grab, 1u);   // a skipped item: take the next one here
         }
 
         // publish the tile's sweep, take the next item
         named_bar_sync(bar_id, kSites);
         if (q == 0) {
             if (lane == 0) {
-                st_release_gpu(done + j, (unsigned int)(k + 1));   // after every output of the tile
+                if (go)   // after every output of the tile
+                    st_release_gpu(p.done + ii.base + ii.tile, (unsigned int)(k + 1));
                 s_item[grp] = next;
             }
-            if (!wait_counter(dnext, (unsigned int)knext, seen))
-                atomicExch(err, 1);
+            const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
+            if (nx < total) {
+                if constexpr (BATCH) {
+                    const TcItem in2 = tc_decode<BATCH>(p, nx);
+                    const unsigned int pn = par ^ 1u;
+                    bool run;
+                    if (go)   // staged when this item issued its MMA
+                        run = __shfl_sync(0xFFFFFFFFu, s_go[grp * 2 + pn], 0) != 0;
+                    else
+                        run = tc_stage_warp(p, in2, lane, s_args + grp * 2 + pn, s_t + grp * 2 + pn,
+                                            s_go + grp * 2 + pn, gtabs + pn * kTabF);
+                    if (run)
+                        tc_wait_item<BATCH>(p, in2, lane, dnext, seen);
+                } else if (knext >= 0) {   // looked at during this item
+                    if (!BUDGET || t0 + (uint32_t)knext < tlim)
+                        if (!wait_counter(dnext, (unsigned int)knext, seen))
+                            atomicExch(p.err, 1);
+                } else {
+                    const TcItem in2 = tc_decode<BATCH>(p, nx);
+                    if (!BUDGET || t0 + (uint32_t)in2.k < tlim)
+                        tc_wait_item<BATCH>(p, in2, lane, nullptr, 0u);
+                }
+            }
         }
         named_bar_sync(bar_id, kSites);
         item = s_item[grp];
+        ++seq;
     }
 
     // a timed-out wait may leave an MMA in flight: wait for it (bounded)
@@ -626,9 +852,8 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const SweepArgs a, uin
     }
 }
 
-template <int NB, bool LMASK>
-cudaError_t launch_tcw_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
-                         unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+template <int NB, bool LMASK, bool BATCH, bool BUDGET>
+cudaError_t launch_tcw_t(const TcParams &p, long long items, cudaStream_t st)
 {
     static bool attr_set[64] = {};
     int dev = 0;
@@ -637,11 +862,10 @@ cudaError_t launch_tcw_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nswee
         return e;
     if (dev >= 64)
         return cudaErrorInvalidDevice;
-    const int nc = (a.m.L + kChunk - 1) / kChunk;
-    const int smem = tc_smem_bytes(32);
     if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(pca_tcw_kernel<NB, LMASK>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = cudaFuncSetAttribute(pca_tcw_kernel<NB, LMASK, BATCH, BUDGET>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 tc_smem_bytes(32, BATCH));
         if (e != cudaSuccess)
             return e;
         attr_set[dev] = true;
@@ -650,9 +874,6 @@ cudaError_t launch_tcw_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nswee
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess)
         return e;
-    const int tiles_x = (a.W + 31) / 32;
-    const int tiles_y = (a.H + kTileRows - 1) / kTileRows;
-    const long long items = (long long)tiles_x * tiles_y * nsweeps;
     if (items <= 0)
         return cudaSuccess;
     if (items >= (1ll << 32))
@@ -660,9 +881,27 @@ cudaError_t launch_tcw_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nswee
     // one CTA per SM (TMEM: all 512 columns); no more CTAs than 4-item groups
     const long long need = (items + kGroups - 1) / kGroups;
     const int grid = (int)(need < sms ? need : sms);
-    pca_tcw_kernel<NB, LMASK><<<grid, kThr, tc_smem_bytes(nc), st>>>(
-        a, x0, x1, nsweeps, tiles_x, tiles_y, nc, done, grab, err);
+    pca_tcw_kernel<NB, LMASK, BATCH, BUDGET><<<grid, kThr, tc_smem_bytes(p.nc_max, BATCH), st>>>(
+        p);
     return cudaGetLastError();
+}
+
+template <bool BATCH, bool BUDGET>
+cudaError_t launch_tcw(const TcParams &p, int nbhd, bool lmask, long long items, cudaStream_t st)
+{
+    if (nbhd == 8)
+        return lmask ? launch_tcw_t<8, true, BATCH, BUDGET>(p, items, st)
+                     : launch_tcw_t<8, false, BATCH, BUDGET>(p, items, st);
+    return lmask ? launch_tcw_t<4, true, BATCH, BUDGET>(p, items, st)
+                 : launch_tcw_t<4, false, BATCH, BUDGET>(p, items, st);
+}
+
+template <bool LMASK>
+__global__ void tc_table_kernel(const DevModel m, float *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kTabF)
+        out[i] = tab_entry<LMASK>(m, i);
 }
 
 }  // namespace
@@ -673,17 +912,74 @@ bool pca_tc_eligible(const DevModel &m)
            (m.nbhd == 4 || m.nbhd == 8);
 }
 
+bool pca_tc_auto(const DevModel &m)
+{
+    return pca_tc_eligible(m) && m.L >= kTcAutoLabels;
+}
+
+int tc_table_floats(int)
+{
+    return kTabF;
+}
+
+cudaError_t launch_tc_table(const DevModel &m, float *out, cudaStream_t st)
+{
+    if (m.L % kChunk)
+        tc_table_kernel<true><<<(kTabF + 255) / 256, 256, 0, st>>>(m, out);
+    else
+        tc_table_kernel<false><<<(kTabF + 255) / 256, 256, 0, st>>>(m, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
-                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t st,
+                          const uint32_t *budget, bool par_from_t)
 {
     if (!pca_tc_eligible(a.m))
         return cudaErrorInvalidValue;
-    const bool lmask = (a.m.L % kChunk) != 0;
-    if (a.m.nbhd == 8)
-        return lmask ? launch_tcw_t<8, true>(a, x0, x1, nsweeps, done, grab, err, st)
-                     : launch_tcw_t<8, false>(a, x0, x1, nsweeps, done, grab, err, st);
-    return lmask ? launch_tcw_t<4, true>(a, x0, x1, nsweeps, done, grab, err, st)
-                 : launch_tcw_t<4, false>(a, x0, x1, nsweeps, done, grab, err, st);
+    TcParams p{};
+    p.a = a;
+    p.x0 = x0;
+    p.x1 = x1;
+    p.budget = budget;
+    p.par_from_t = par_from_t ? 1 : 0;
+    p.tiles_x = (a.W + 31) / 32;
+    p.tiles_y = (a.H + kTileRows - 1) / kTileRows;
+    p.nsweeps = nsweeps;
+    p.T = a.m.T;
+    p.nc_max = (a.m.L + kChunk - 1) / kChunk;
+    p.done = done;
+    p.grab = grab;
+    p.err = err;
+    const long long items = (long long)p.tiles_x * p.tiles_y * nsweeps;
+    if (budget)
+        return launch_tcw<false, true>(p, a.m.nbhd, (a.m.L % kChunk) != 0, items, st);
+    return launch_tcw<false, false>(p, a.m.nbhd, (a.m.L % kChunk) != 0,
+                             (long long)p.tiles_x * p.tiles_y * nsweeps, st);
+}
+
+cudaError_t launch_batch_tc(const SlotDesc *slots, const uint32_t *t_arr,
+                            const uint32_t *budget_arr, const WaveGeom *geom,
+                            const WaveItem *items, int n_items, int nsweeps, int T, int nbhd,
+                            bool lmask, int nc_max, unsigned int *done, unsigned int *grab,
+                            int *err, cudaStream_t st)
+{
+    if (T < 1 || T > kTcMaxT || (nbhd != 4 && nbhd != 8) || nc_max < 1 || nc_max > 32)
+        return cudaErrorInvalidValue;
+    TcParams p{};
+    p.slots = slots;
+    p.t_arr = t_arr;
+    p.budget_arr = budget_arr;
+    p.geom = geom;
+    p.items = items;
+    p.n_items = n_items;
+    p.nsweeps = nsweeps;
+    p.T = T;
+    p.nc_max = nc_max;
+    p.done = done;
+    p.grab = grab;
+    p.err = err;
+    return launch_tcw<true, false>(p, nbhd, lmask, (long long)n_items * nsweeps, st);
 }
 
 }  // namespace pcad

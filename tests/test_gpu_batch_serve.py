@@ -35,6 +35,8 @@ def _jobs():
         (_grey(6, 45, 52, 5, 1.0), Model(L=5, nbhd=8, pair=POTTS, pair_coef=0.8, sigma=1.0, inertia=0.7), 7, 7, 3),
         (_grey(7, 29, 64, 33, 3.0), Model(L=33, nbhd=8, pair=POTTS, pair_coef=0.8, sigma=3.0, inertia=0.4), 7, 8, 3),
         (_grey(8, 100, 100, 16, 1.2), Model(L=16, pair=TL, pair_coef=0.6, pair_T=3, sigma=1.2, inertia=0.0), 9, 9, 20),
+        # a second tensor-core group (8-neighbourhood, T = 25, L % 8 != 0)
+        (_grey(10, 50, 61, 201, 18.0), Model(L=201, nbhd=8, pair=TL, pair_coef=0.05, pair_T=25, sigma=18.0, inertia=1.5), 11, 10, 6),
     ]
 
 
@@ -123,7 +125,7 @@ def _serve_until_done(pc, sv, ids, shapes, slice_sweeps=16, max_steps=10000):
 
 def test_server_result_is_the_same_alone_and_in_the_mix(pc):
     jobs = _jobs()
-    budgets = [40, 73, 16, 5, 33, 29, 50, 21, 64]
+    budgets = [40, 73, 16, 5, 33, 29, 50, 21, 64, 27]
     target = 5
     g, m, seed, chain, burn = jobs[target]
     ref = _alone(pc, g, m, seed, chain, burn, budgets[target])
@@ -138,7 +140,7 @@ def test_server_result_is_the_same_alone_and_in_the_mix(pc):
     # in a mix: others arrive before and after, with other slice lengths
     sv = pc.pcad_server_create(4, 1 << 30)
     try:
-        shapes, ids, order = {}, [], [0, 2, 6, target, 1, 3, 4, 7, 8]
+        shapes, ids, order = {}, [], [0, 2, 6, target, 1, 9, 3, 4, 7, 8]
         for k, i in enumerate(order):
             gi, mi, si, ci, bi = jobs[i]
             rid = pc.pcad_server_submit(sv, gi, mi, si, ci, bi, budgets[i])
@@ -212,3 +214,43 @@ def test_server_wavefront_across_many_tiles(pc):
     x, acc, nacc, _ = oracle.run_chain(m, g, n, burn, seed=seed, chain=chain)
     assert np.array_equal(res[ids[3]][0], x)
     np.testing.assert_allclose(res[ids[3]][1], acc / nacc, rtol=1e-6, atol=0)
+
+
+def test_large_tensor_core_slots_in_batch_and_server(pc):
+    """A tensor-core eligible image of at least 1216 tiles runs as its own
+    launch inside the batch's and the server's slices (planes chosen by the
+    device sweep counter, the budget capping the last slice): results equal
+    the chains run alone, for runs and budgets that end inside slices."""
+    big = (_grey(20, 330, 512, 256, 20.0),
+           Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0), 21, 3, 7)
+    small = (_grey(21, 40, 33, 256, 15.0),
+             Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=15.0, inertia=2.0), 22, 4, 5)
+    other = (_grey(22, 100, 100, 16, 1.2),
+             Model(L=16, pair=TL, pair_coef=0.6, pair_T=3, sigma=1.2, inertia=1.0), 23, 5, 9)
+    jobs = [big, small, other]
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_run(b, 21)
+        pc.pcad_batch_run(b, 30)
+        pc.pcad_batch_sync(b)
+        for i, (g, m, seed, chain, burn) in enumerate(jobs):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, 51)
+            assert np.array_equal(pc.pcad_batch_read_sample(b, i, *g.shape), xs), i
+            assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
+    finally:
+        pc.pcad_batch_destroy(b)
+    budgets = [37, 20, 45]
+    sv = pc.pcad_server_create(8, 1 << 31)
+    try:
+        ids, shapes = [], {}
+        for (g, m, seed, chain, burn), n in zip(jobs, budgets):
+            rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, n)
+            ids.append(rid)
+            shapes[rid] = g.shape
+        res = _serve_until_done(pc, sv, list(ids), shapes, slice_sweeps=16)
+        for rid, (g, m, seed, chain, burn), n in zip(ids, jobs, budgets):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, n)
+            assert np.array_equal(res[rid][0], xs)
+            assert np.array_equal(res[rid][1], ms)
+    finally:
+        pc.pcad_server_destroy(sv)
