@@ -50,7 +50,7 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
 
 # The same for pca_tc_kernel<4> (None: not captured for this version) and
 # pca_wave_kernel<32,4> (one 32-sweep launch at 1024^2, per site-update).
-NCU_TC_DRAM_BYTES_PER_SITE = (1.636608e6 + 0.055296e6) / (32 * 512 * 512)
+NCU_TC_DRAM_BYTES_PER_SITE = (1.639168e6 + 0.155392e6) / (32 * 512 * 512)
 NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
                        "161-192 of a chain), per site-update: the chain's planes stay in L2")
 NCU_WAVE_DRAM_BYTES_PER_SITE = (6.363904e6 + 0.730112e6) / (32 * 1024 * 1024)
@@ -303,7 +303,7 @@ def run_ours(a):
     achieved = per_sweep_labels / (launch_ms * 1e-3) / 1e12
     in_use = pca_kind   # the kernel the timed chain ran
     kernel_name = {1: "pca_direct_kernel<32,4> (one launch per sweep)",
-                   2: "pca_tcw_kernel<4,0> (tcgen05 windowed tent sums, CUDA-core CDF, "
+                   2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, "
                       "wavefront, one launch per 32 sweeps)",
                    3: "pca_wave_kernel<32,4> (wavefront, one launch per 32 sweeps)"}[in_use]
     per_site = {1: NCU_DRAM_BYTES_PER_SITE, 2: NCU_TC_DRAM_BYTES_PER_SITE,
