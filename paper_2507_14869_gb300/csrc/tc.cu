@@ -88,6 +88,10 @@ constexpr int kTabF = 768;
 // After G (and the one-chain table): mbarriers, work items and the TMEM
 // base (64 bytes), then for batched chains the staged items of each group.
 constexpr int kTcCtlBytes = 64;
+// Per group: the sites' inputs for the group's FP64 re-draws (g, xi, ub,
+// the neighbour labels), the warps' need masks, partial sums and result.
+constexpr int kRedrawInts = 3 + 8;
+constexpr int kRedrawBytes = kGroups * (kSites * kRedrawInts * 4 + 4 * 4 + 4 * 8 + 16);
 constexpr int kTcStageBytes = 2 * kGroups * ((int)sizeof(SweepArgs) + 4 + 4);
 
 // One chain keeps the outside sums as a [chunk][observation] table (row
@@ -103,7 +107,7 @@ __host__ __device__ constexpr int tab2_floats(int nc)
 __host__ __device__ constexpr int tc_smem_bytes(int nc, bool batch)
 {
     return kOffG + nc * kThr * 4 + (batch ? 2 * kGroups * kTabF : tab2_floats(nc)) * 4 +
-           kTcCtlBytes + (batch ? kTcStageBytes : 0);
+           kTcCtlBytes + (batch ? kTcStageBytes : 0) + kRedrawBytes;
 }
 
 // Byte offset of element (row, k), k < 64, of a K-major operand in the
@@ -458,6 +462,107 @@ __device__ __forceinline__ void tc_wait_item(const TcParams &p, const TcItem &ii
         atomicExch(p.err, 1);
 }
 
+// Shared memory of one group's FP64 re-draws.
+struct GroupRedraw {
+    int *site;          // [kSites][kRedrawInts]: g, xi, ub, neighbour labels
+    unsigned int *need; // [4] the warps' masks of sites to re-draw
+    double *wsum;       // [4] the warps' sums of the site's weights
+    int *res;           // the re-drawn label
+};
+
+// FP64 re-draw of the group's uncertain draws by all 128 threads: per site
+// in turn, thread lt evaluates labels 2 lt and 2 lt + 1 (weight64, the FP64
+// tables), a warp scan and the warps' prefix give the CDF, and the thread
+// holding u Z finds the label (as warp_redraw_fp64, over 128 threads, so
+// the FP64 work of a re-draw spreads over the four schedulers of the
+// group's warps).  Every thread of the group calls it; returns s or the
+// re-drawn label.
+template <int NB>
+__device__ __forceinline__ int group_redraw_fp64(const DevModel &m, bool need,
+                                                 const SiteIn<NB> &in, int s,
+                                                 unsigned long long *counter, const GroupRedraw &gr,
+                                                 int lt, int bar_id)
+{
+    constexpr unsigned kFull = 0xFFFFFFFFu;
+    const int lane = lt & 31, q = lt >> 5;
+    const unsigned mask = __ballot_sync(kFull, need);
+    if (need) {
+        int *row = gr.site + lt * kRedrawInts;
+        row[0] = in.g;
+        row[1] = in.xi;
+        row[2] = (int)in.ub;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            row[3 + j] = in.xni[j];
+    }
+    if (lane == 0) {
+        gr.need[q] = mask;
+        if (mask)
+            atomicAdd(counter, (unsigned long long)__popc(mask));
+    }
+    if (!named_bar_or(bar_id, kSites, need))   // the masks and inputs are visible after it
+        return s;
+    unsigned masks[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+        masks[w] = gr.need[w];
+#pragma unroll 1
+    for (int w = 0; w < 4; ++w) {
+#pragma unroll 1
+        while (masks[w]) {
+            const int ol = __ffs((int)masks[w]) - 1;
+            masks[w] &= masks[w] - 1u;
+            const int owner = w * 32 + ol;
+            const int *row = gr.site + owner * kRedrawInts;
+            const int lg = row[0], lxi = row[1];
+            const uint32_t lub = (uint32_t)row[2];
+            int lx[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                lx[j] = row[3 + j];
+            const int s0 = 2 * lt, s1 = 2 * lt + 1;
+            const double w0 = s0 < m.L ? weight64<NB>(m, lg, lxi, lx, s0) : 0.0;
+            const double w1 = s1 < m.L ? weight64<NB>(m, lg, lxi, lx, s1) : 0.0;
+            const double part = __dadd_rn(w0, w1);
+            double incl = part;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double v = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o)
+                    incl = __dadd_rn(incl, v);
+            }
+            double excl = __shfl_up_sync(kFull, incl, 1);
+            if (lane == 31)
+                gr.wsum[q] = incl;
+            named_bar_sync(bar_id, kSites);
+            double pre = 0.0, Z = 0.0;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const double ws = gr.wsum[v];
+                if (v < q)
+                    pre = __dadd_rn(pre, ws);
+                Z = __dadd_rn(Z, ws);
+            }
+            incl = __dadd_rn(pre, incl);
+            excl = lane == 0 ? pre : __dadd_rn(pre, excl);
+            const double t = __dmul_rn((double)lub * (1.0 / 16777216.0), Z);
+            if (lt == 0)
+                *gr.res = m.L - 1;   // no label below t: the last one
+            named_bar_sync(bar_id, kSites);
+            if (excl <= t && t < incl) {
+                const double c0 = __dadd_rn(excl, w0);
+                *gr.res = (t < c0 && s0 < m.L) ? s0 : min(s1, m.L - 1);
+            }
+            named_bar_sync(bar_id, kSites);
+            const int r = *gr.res;
+            if (lt == owner)
+                s = r;
+            named_bar_sync(bar_id, kSites);   // wsum and res are free again
+        }
+    }
+    return s;
+}
+
 // The arguments of the current item: the launch's (one chain, read from
 // the kernel parameters) or the staged ones (batched chains).
 template <bool BATCH>
@@ -500,6 +605,15 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
     uint32_t *s_t = reinterpret_cast<uint32_t *>(s_args + 2 * kGroups);
     int *s_go = reinterpret_cast<int *>(s_t + 2 * kGroups);
     float *gtabs = tabs + grp * 2 * kTabF;   // batched chains: this group's two tables
+    GroupRedraw gr;
+    {
+        uint8_t *rb = reinterpret_cast<uint8_t *>(mbar) + kTcCtlBytes + (BATCH ? kTcStageBytes : 0) +
+                      grp * (kSites * kRedrawInts * 4 + 4 * 4 + 4 * 8 + 16);
+        gr.wsum = reinterpret_cast<double *>(rb);
+        gr.need = reinterpret_cast<unsigned int *>(rb + 4 * 8);
+        gr.res = reinterpret_cast<int *>(rb + 4 * 8 + 4 * 4);
+        gr.site = reinterpret_cast<int *>(rb + 4 * 8 + 4 * 4 + 16);
+    }
 
     // A starts zero; B holds K(k, c) at row c (window label), column k (bin)
     for (int i = tid; i < (kOpBytes * (1 + kGroups)) / 16; i += kThr)
@@ -793,7 +907,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
                                    chunk_prefix_exact<NB>(m, mu, st.xn, st.gf, cs, pp);
                                });
             }
-            s = warp_redraw_fp64<NB>(m, valid && !certain, st.in, s, b.fp64_draws);
+            s = group_redraw_fp64<NB>(m, valid && !certain, st.in, s, b.fp64_draws, gr, lt, bar_id);
             if (valid) {
                 xout[(size_t)r * b.pitch + c] = (uint8_t)s;
                 if (acc_on)
