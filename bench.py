@@ -50,7 +50,7 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
 
 # The same for pca_tc_kernel<4> (None: not captured for this version) and
 # pca_wave_kernel<32,4> (one 32-sweep launch at 1024^2, per site-update).
-NCU_TC_DRAM_BYTES_PER_SITE = (1.639168e6 + 0.155392e6) / (32 * 512 * 512)
+NCU_TC_DRAM_BYTES_PER_SITE = (1.636864e6 + 0.098816e6) / (32 * 512 * 512)
 NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
                        "161-192 of a chain), per site-update: the chain's planes stay in L2")
 NCU_WAVE_DRAM_BYTES_PER_SITE = (6.363904e6 + 0.730112e6) / (32 * 1024 * 1024)

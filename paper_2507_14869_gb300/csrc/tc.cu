@@ -476,12 +476,14 @@ struct GroupRedraw {
 // holding u Z finds the label (as warp_redraw_fp64, over 128 threads, so
 // the FP64 work of a re-draw spreads over the four schedulers of the
 // group's warps).  Every thread of the group calls it; returns s or the
-// re-drawn label.
+// re-drawn label.  Its first step is a group barrier (any: whether any
+// draw of the group is re-drawn), which also orders the memory writes made
+// before the call.
 template <int NB>
 __device__ __forceinline__ int group_redraw_fp64(const DevModel &m, bool need,
                                                  const SiteIn<NB> &in, int s,
                                                  unsigned long long *counter, const GroupRedraw &gr,
-                                                 int lt, int bar_id)
+                                                 int lt, int bar_id, bool &any)
 {
     constexpr unsigned kFull = 0xFFFFFFFFu;
     const int lane = lt & 31, q = lt >> 5;
@@ -500,7 +502,8 @@ __device__ __forceinline__ int group_redraw_fp64(const DevModel &m, bool need,
         if (mask)
             atomicAdd(counter, (unsigned long long)__popc(mask));
     }
-    if (!named_bar_or(bar_id, kSites, need))   // the masks and inputs are visible after it
+    any = named_bar_or(bar_id, kSites, need);   // the masks and inputs are visible after it
+    if (!any)
         return s;
     unsigned masks[4];
 #pragma unroll
@@ -907,18 +910,31 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
                                    chunk_prefix_exact<NB>(m, mu, st.xn, st.gf, cs, pp);
                                });
             }
-            s = group_redraw_fp64<NB>(m, valid && !certain, st.in, s, b.fp64_draws, gr, lt, bar_id);
-            if (valid) {
+            // certain draws are written now; the re-draw's first barrier
+            // orders them before the tile is published; re-drawn ones
+            // follow with one more barrier
+            const bool need = valid && !certain;
+            const auto write_site = [&]() {
                 xout[(size_t)r * b.pitch + c] = (uint8_t)s;
                 if (acc_on)
                     *accp = acc_old + (float)s;
+            };
+            if (valid && !need)
+                write_site();
+            bool any = false;
+            s = group_redraw_fp64<NB>(m, need, st.in, s, b.fp64_draws, gr, lt, bar_id, any);
+            if (any) {
+                if (need)
+                    write_site();
+                named_bar_sync(bar_id, kSites);
             }
-        } else if (lt == 0) {
-            next = atomicAdd(p.grab, 1u);   // a skipped item: take the next one here
+        } else {
+            if (lt == 0)
+                next = atomicAdd(p.grab, 1u);   // a skipped item: take the next one here
+            named_bar_sync(bar_id, kSites);
         }
 
-        // publish the tile's sweep, take the next item
-        named_bar_sync(bar_id, kSites);
+        // publish the tile's sweep (every output written), take the next item
         if (q == 0) {
             if (lane == 0) {
                 if (go)   // after every output of the tile
