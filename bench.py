@@ -625,6 +625,11 @@ def run_serve(a):
             lat, span, res = _serve_stream(pc, sv, reqs)
             info = pc.pcad_server_info(sv)
             pc.pcad_server_destroy(sv)
+            # the same stream with admission capped at 2M sites of admitted work
+            sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
+            pc.pcad_server_set_limits(sv, 2 << 20)
+            clat, cspan, _ = _serve_stream(pc, sv, reqs)
+            pc.pcad_server_destroy(sv)
             plat, pspan, pres, busy = _plain_fifo(pc, reqs, stream)
             same = all(np.array_equal(res[i][0], pres[i][0]) and
                        np.array_equal(res[i][1], pres[i][1]) for i in res)
@@ -638,6 +643,9 @@ def run_serve(a):
                 "site_updates_per_s": work / span, "slices": info["slices"],
                 "plain": {"img_s": len(reqs) / pspan, "p50_s": float(np.percentile(plat, 50)),
                           "p99_s": float(np.percentile(plat, 99)), "busy_s": busy},
+                "capped_2M_sites": {"img_s": len(reqs) / cspan,
+                                    "p50_s": float(np.percentile(clat, 50)),
+                                    "p99_s": float(np.percentile(clat, 99))},
                 "identical_outputs": same, "psnr_db_first": psnr})
     head = per_rate[-1]
     line = {"metric": "served img/s (continuous batching)", "value": head["img_s"],

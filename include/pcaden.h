@@ -346,6 +346,13 @@ typedef struct pcad_server pcad_server;
 
 pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cuda_stream,
                                pcad_server **out);
+/* Admission cap: a queued request waits while the admitted requests hold
+ * max_active_sites sites or more (its own included), unless none is
+ * admitted; 0 (the default) admits whenever a slot and the HBM budget
+ * allow.  With a cap the GPU still runs full slices while early long
+ * requests are not diluted by every later arrival (tail latency under
+ * overload).  Takes effect at the next step. */
+pcad_status pcad_server_set_limits(pcad_server *sv, size_t max_active_sites);
 /* Queue a request for nsweeps sweeps (job->g_host is copied).  *id is its handle. */
 pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id);
 /* Admit, run one slice of slice_sweeps (1..16) sweeps of every admitted

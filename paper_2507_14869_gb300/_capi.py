@@ -130,6 +130,7 @@ def _declare(L):
                             ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_float), u64p],
         "pcad_server_create": [ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pcad_server_submit": [vp, ctypes.POINTER(PcadJob), ctypes.c_int, u64p],
+        "pcad_server_set_limits": [vp, ctypes.c_size_t],
         "pcad_server_step": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pcad_server_poll": [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), u8p, fp],
@@ -512,6 +513,11 @@ def pcad_server_create(max_slots: int, hbm_budget_bytes: int, stream=None):
     _check("pcad_server_create", lib().pcad_server_create(int(max_slots), int(hbm_budget_bytes),
                                                           _stream(stream), ctypes.byref(h)))
     return h
+
+
+def pcad_server_set_limits(h, max_active_sites: int):
+    """Admit while the admitted requests hold fewer sites (0: no cap)."""
+    _check("pcad_server_set_limits", lib().pcad_server_set_limits(h, int(max_active_sites)))
 
 
 def pcad_server_submit(h, g, model, seed, chain_id, burn_in, nsweeps) -> int:

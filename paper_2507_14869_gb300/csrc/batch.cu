@@ -924,6 +924,8 @@ struct pcad_server {
     int *h_err = nullptr;          // pinned: the flag after each of the last two slices
     cudaEvent_t ev[2] = {nullptr, nullptr};
     bool in_flight = false;        // the previous slice may still be running
+    size_t max_active_sites = 0;   // admission cap on the admitted requests' sites (0: none)
+    size_t active_sites = 0;
     std::vector<SlotDesc> desc;
     std::vector<uint64_t> slot_req;   // 0 = free
     std::deque<uint64_t> pending;
@@ -944,8 +946,13 @@ pcad_status server_admit(pcad_server *sv)
                 slot = i;
                 break;
             }
+        const size_t sites = (size_t)rq.job.H * rq.job.W;
         if (slot < 0 || sv->used + rq.bytes > sv->budget)
             break;   // first-come first-served: wait for slots or memory
+        if (sv->max_active_sites && sv->active_sites > 0 &&
+            sv->active_sites + sites > sv->max_active_sites)
+            break;   // enough work admitted: the GPU is full, the next one waits
+        sv->active_sites += sites;
         sv->pending.pop_front();
         cudaError_t e = cudaMallocAsync(&rq.mem, rq.bytes, sv->stream);
         if (e != cudaSuccess) {
@@ -1073,6 +1080,14 @@ pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cud
     return PCAD_OK;
 }
 
+pcad_status pcad_server_set_limits(pcad_server *sv, size_t max_active_sites)
+{
+    if (!sv)
+        return set_error(PCAD_EINVAL, "server is NULL");
+    sv->max_active_sites = max_active_sites;
+    return PCAD_OK;
+}
+
 pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id)
 {
     if (!sv || !job || !id)
@@ -1159,6 +1174,7 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
             B_TRY(cudaFreeAsync(rq.mem, sv->stream));
             rq.mem = nullptr;
             sv->used -= rq.bytes;
+            sv->active_sites -= (size_t)d.H * d.W;
             sv->slot_req[i] = 0;
             rq.state = 2;
             rq.slot = -1;

@@ -254,3 +254,28 @@ def test_large_tensor_core_slots_in_batch_and_server(pc):
             assert np.array_equal(res[rid][1], ms)
     finally:
         pc.pcad_server_destroy(sv)
+
+
+def test_server_admission_cap(pc):
+    """With an admission cap, a request waits while the admitted ones hold
+    enough sites (but is admitted when nothing else runs); results are the
+    same as without the cap."""
+    jobs = _jobs()
+    g, m, seed, chain, burn = jobs[8]            # 100 x 100
+    sv = pc.pcad_server_create(16, 1 << 30)
+    try:
+        pc.pcad_server_set_limits(sv, 15_000)     # one 100 x 100 request at a time
+        ids = [pc.pcad_server_submit(sv, g, m, seed, chain + k, burn, 32) for k in range(3)]
+        act, pend, fin = pc.pcad_server_step(sv, 16)
+        assert act == 1 and pend == 2 and fin == 0
+        res = _serve_until_done(pc, sv, list(ids), {r: g.shape for r in ids})
+        for k, rid in enumerate(ids):
+            xs, ms = _alone(pc, g, m, seed, chain + k, burn, 32)
+            assert np.array_equal(res[rid][0], xs) and np.array_equal(res[rid][1], ms)
+        # a request larger than the cap still runs when nothing else is admitted
+        pc.pcad_server_set_limits(sv, 100)
+        rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, 25)
+        res = _serve_until_done(pc, sv, [rid], {rid: g.shape})
+        assert np.array_equal(res[rid][0], _alone(pc, g, m, seed, chain, burn, 25)[0])
+    finally:
+        pc.pcad_server_destroy(sv)
