@@ -405,6 +405,20 @@ const char *pcad_last_error(void);
 /* Library version string. */
 const char *pcad_version(void);
 
+/* The FP32 constants behind the certified draw of model m (host only, no
+ * device work; the paper fixes no precision, so these are this library's):
+ * out[0] alpha and out[1] gam, the data and prior exponent coefficients in
+ * base 2 (alpha = -log2(e) / (2 sigma^2), gam = -c log2(e)); out[2] eta, the
+ * CUDA-core kernels' CDF margin (a draw is re-done in FP64 when u Z lies
+ * within eta Z of the chosen label's CDF interval); out[3..7] cb, hb, kb0,
+ * kb1, kbr of the tensor-core sweep: window weights 2^(alpha (g - s)^2 +
+ * mu Pb + cb) (mu = -gam, Pb the tent sum), per-site margin
+ * eta = kb1 (hb - log2 Z) + kb0 + kbr delta / Z (Z the site's total with the
+ * inertia weight delta).  out must hold n >= PCAD_N_MARGINS doubles.
+ * PCAD_EINVAL for an invalid model or buffer. */
+#define PCAD_N_MARGINS 8
+pcad_status pcad_model_margins(const pcad_model *m, double *out, int n);
+
 #ifdef __cplusplus
 }
 #endif

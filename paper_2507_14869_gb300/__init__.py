@@ -16,7 +16,7 @@ from ._capi import (  # noqa: F401
     pcad_chain_read_min_state, pcad_chain_kernel_in_use, pcad_chain_set_model, pcad_chain_run_schedule,
     pcad_batch_set_model,
     pcad_chain_sync, pcad_chain_write_sample, pcad_last_error, pcad_metrics, pcad_status_str,
-    pcad_pca_run_noalloc, pcad_version,
+    pcad_pca_run_noalloc, pcad_version, pcad_model_margins, N_MARGINS,
     PcadJob, pcad_batch_create, pcad_batch_destroy, pcad_batch_info, pcad_batch_read_mean,
     pcad_batch_read_sample, pcad_batch_reset, pcad_batch_run, pcad_batch_sync,
     pcad_batch_set_tiling,

@@ -96,6 +96,7 @@ def _declare(L):
                                   ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, vp,
                                   ctypes.POINTER(vp)],
         "pcad_chain_run": [vp, ctypes.c_int],
+        "pcad_model_margins": [mp, dp, ctypes.c_int],
         "pcad_chain_sync": [vp],
         "pcad_chain_reset": [vp],
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
@@ -321,6 +322,18 @@ def pcad_last_error() -> str:
 
 def pcad_version() -> str:
     return lib().pcad_version().decode()
+
+
+N_MARGINS = 8
+_MARGIN_KEYS = ("alpha", "gam", "eta", "cb", "hb", "kb0", "kb1", "kbr")
+
+
+def pcad_model_margins(model) -> dict:
+    """The FP32 coefficients and certified-draw margins of a model (host only)."""
+    m = as_model(model)
+    out = (ctypes.c_double * N_MARGINS)()
+    _check("pcad_model_margins", lib().pcad_model_margins(ctypes.byref(m), out, N_MARGINS))
+    return dict(zip(_MARGIN_KEYS, list(out)))
 
 
 class Chain:

@@ -179,15 +179,41 @@ void build_tables(const pcad_model &m, ModelTables &t)
                             4.0 * u;
         d.eta = (float)(1.5 * 2.0 * (2.0 * e_wn + gsum) + 8.0 * u);
     }
-    // Tensor-core sweep: v' = alpha Q + mu Pb with mu = -gam and Pb = nT - P
-    // (n neighbours inside the image), i.e. v' = v + mu n T.  |dv'| <= u (2|v'|
-    // + 3 mu Pb) and E_p|v'| <= E_p|v| + A <= 2A + log2 L, so the weight part
-    // becomes u ln2 (7A + 2 log2 L) + e_ex2.  Its chunk sums come in up to
-    // four label ranges, each Kahan-summed, joined by three more additions:
-    // 24u of summation.
-    const double e_wb = u * 0.6931471805599453 * (7.0 * A + 2.0 * std::log2((double)m.L)) +
-                        4.0 * u;
-    d.eta_b = (float)(1.5 * 2.0 * (2.0 * e_wb + 24.0 * u) + 8.0 * u);
+    // Tensor-core sweep, per-site margin.  Window labels take
+    // v = fl(alpha q + fl(mu Pb + cb)) (q = (g - s)^2 and the tent sum Pb
+    // exact integers, mu = -gam), outside labels (Pb = 0) v = fl(alpha q + cb),
+    // with cb = -fl(mu nbhd T) for mu > 0 (else 0), the same float for every
+    // label: up to one common shift K, v is alpha q - |mu| R with R =
+    // nbhd T - Pb (mu > 0) or Pb (mu <= 0), both terms <= 0, so |alpha q| +
+    // |mu| R = |v| and the roundings give |dv| <= u (|alpha q| + 2 |mu| R +
+    // |v|) <= 3u |v|.  The common shift 2^K scales every weight alike and
+    // leaves all ratios unchanged.  Mixture p~ of the L labels and the
+    // inertia atom (weight (e^lambda - 1) w_xi, delta = fl(w_xi em1), 2u
+    // more): a relative weight error theta_a moves every CDF value by at
+    // most sum_a p~_a |theta_a| (not twice: F~ - F = ((1 - F) a - F (b - a))
+    // / (1 + b) with a, b - a the errors below and above k), and with
+    // log-weights v_a <= 0 (v of the atom: v_xi + J, J = log2(e^lambda - 1))
+    // E|v| = H(p~) - log2 Z + rho J <= log2(L + 1) - log2 Z + rho J+ (Z the
+    // exact total, rho = delta / Z the atom's mass).  So
+    //   E_w <= 3u ln2 (log2(L + 1) - log2 Z + rho J+) + e_ex2 + 2u rho.
+    // Summation: chunk sums (7 roundings), Kahan prefix (2u), pass-2 prefix
+    // (7), the joins with Gprev and delta (2): C_k within 11u, Z within 10u,
+    // their ratio within 21u; t = fl(u Z) one more u.  eta = 1.5 (E_w +
+    // 22u), 1.5 the slack for second-order terms, the FP32 evaluation of
+    // eta and of the margin comparison, and log2 Z from lg2.approx of the
+    // computed Z (within 2^-22 absolute; the computed Z is within 1e-4 of
+    // 2^K Z, |K| <= u |mu| nbhd T) with 1/64 added.  Per site:
+    //   eta = kb1 (hb - lg2(Z)) + kb0 + kbr delta / Z.
+    {
+        const double mu_f = -(double)d.gam;
+        d.cb = mu_f > 0.0 ? (float)(-mu_f * (double)pmax) : 0.0f;
+        const double ln2 = 0.6931471805599453;
+        const double J = lam > 0.0 ? std::log2(std::expm1(lam)) : 0.0;
+        d.hb = (float)(std::log2((double)m.L + 1.0) + 1.0 / 64.0);
+        d.kb1 = (float)(1.5 * 3.0 * u * ln2);
+        d.kb0 = (float)(1.5 * (4.0 + 22.0) * u);
+        d.kbr = (float)(1.01 * 1.5 * (3.0 * u * ln2 * std::fmax(J, 0.0) + 2.0 * u));
+    }
     d.ta64 = nullptr;
     d.pr64 = nullptr;
 }
@@ -1129,6 +1155,22 @@ const char *pcad_status_str(pcad_status s)
 const char *pcad_last_error(void) { return g_err.c_str(); }
 
 const char *pcad_version(void) { return "pcaden 0.1.0 (sm_103a)"; }
+
+pcad_status pcad_model_margins(const pcad_model *m, double *out, int n)
+{
+    if (!m || !out || n < PCAD_N_MARGINS)
+        return fail(PCAD_EINVAL, "model_margins: null argument or n < %d", PCAD_N_MARGINS);
+    pcad_status st = validate_model(m);
+    if (st != PCAD_OK)
+        return st;
+    ModelTables t;
+    build_tables(*m, t);
+    const DevModel &d = t.dm;
+    const float v[PCAD_N_MARGINS] = {d.alpha, d.gam, d.eta, d.cb, d.hb, d.kb0, d.kb1, d.kbr};
+    for (int i = 0; i < PCAD_N_MARGINS; ++i)
+        out[i] = (double)v[i];
+    return PCAD_OK;
+}
 
 }  // extern "C"
 

@@ -51,7 +51,8 @@ struct DevModel {
     float Tf;          // (float)T
     float em1;         // e^lambda - 1 (0: no inertia)
     float eta;         // FP32 error bound of the normalised CDF
-    float eta_b;       // the same for the banded-prior weights of the tensor-core sweep
+    float cb;          // tensor-core sweep: common exponent offset (-mu nbhd T, mu > 0)
+    float hb, kb0, kb1, kbr;   // its per-site margin kb1 (hb - log2 Z) + kb0 + kbr delta / Z
     int norm;          // inertia price: 0 L0 (via em1 / el64), 1 or 2 Lp (via kappa / in64)
     float kappa;       // Lp price exponent coefficient, -lambda log2(e) / (L - 1)^p
     const double *ta64;  // [511] data factor exp(-(U(g, g-d) - U(g,g))) at d + 255, FP64
@@ -109,6 +110,13 @@ __device__ __forceinline__ float ex2_ftz(float x)
 {
     float y;
     asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float lg2_ftz(float x)
+{
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
 }
 

@@ -119,11 +119,14 @@ __device__ __forceinline__ uint32_t sw128_offset(int row, int k)
                       ((k & 7) << 1));
 }
 
-// Weight of one label from its tent sum Pb (an exact integer): 2^(alpha dg^2 + mu Pb).
-__device__ __forceinline__ float label_wb(float alpha, float mu, float Pb, float dg)
+// Weight of one label from its tent sum Pb (an exact integer):
+// 2^(alpha dg^2 + mu Pb + cb).  The common offset cb = -mu nbhd T keeps both
+// terms of the exponent non-positive (mu > 0), so its rounding error stays
+// proportional to the exponent itself.
+__device__ __forceinline__ float label_wb(const DevModel &m, float mu, float Pb, float dg)
 {
     const float q = __fmul_rn(dg, dg);
-    const float v = __fmaf_rn(alpha, q, __fmul_rn(mu, Pb));
+    const float v = __fmaf_rn(m.alpha, q, __fmaf_rn(mu, Pb, m.cb));
     return ex2_ftz(v);
 }
 
@@ -227,8 +230,8 @@ __device__ __forceinline__ void site_window(TcSite<NB> &st, int T, int row, bool
 }
 
 // Sum of the weights of absolute chunk c (labels 8c .. 8c + 7) outside the
-// window, where no in-window neighbour's tent reaches: 2^(alpha (g - s)^2).
-// LMASK zeroes labels >= L.
+// window, where no in-window neighbour's tent reaches: 2^(alpha (g - s)^2 +
+// cb), label_wb at Pb = 0.  LMASK zeroes labels >= L.
 template <bool LMASK>
 __device__ __forceinline__ float outside_chunk(const DevModel &m, float gf, int c)
 {
@@ -237,7 +240,7 @@ __device__ __forceinline__ float outside_chunk(const DevModel &m, float gf, int 
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
         const float dg = __fsub_rn(dgb, (float)k);
-        float w = ex2_ftz(__fmul_rn(m.alpha, __fmul_rn(dg, dg)));
+        float w = ex2_ftz(__fmaf_rn(m.alpha, __fmul_rn(dg, dg), m.cb));
         if (LMASK && c * kChunk + k >= m.L)
             w = 0.0f;
         S = __fadd_rn(S, w);
@@ -276,7 +279,7 @@ __device__ __forceinline__ float window_chunk(const DevModel &m, float mu, float
     float S = 0.0f;
 #pragma unroll
     for (int k = 0; k < kChunk; ++k) {
-        float w = label_wb(m.alpha, mu, __uint_as_float(pb[k]), __fsub_rn(dgb, (float)k));
+        float w = label_wb(m, mu, __uint_as_float(pb[k]), __fsub_rn(dgb, (float)k));
         if (LMASK && c * kChunk + k >= m.L)
             w = 0.0f;
         S = __fadd_rn(S, w);
@@ -315,7 +318,7 @@ __device__ __forceinline__ void chunk_prefix_exact(const DevModel &m, float mu,
     for (int k = 0; k < kChunk; ++k) {
         const int s = c * kChunk + k;
         const float sf = (float)s;
-        float w = label_wb(m.alpha, mu, tent_sum<NB>(xn, m.Tf, sf), __fsub_rn(gf, sf));
+        float w = label_wb(m, mu, tent_sum<NB>(xn, m.Tf, sf), __fsub_rn(gf, sf));
         if (s >= m.L)
             w = 0.0f;
         S = __fadd_rn(S, w);
@@ -901,11 +904,15 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
                 float delta = 0.0f;
                 if (m.em1 != 0.0f) {
                     const float xif = (float)st.in.xi;
-                    delta = __fmul_rn(label_wb(m.alpha, mu, tent_sum<NB>(st.xn, m.Tf, xif),
+                    delta = __fmul_rn(label_wb(m, mu, tent_sum<NB>(st.xn, m.Tf, xif),
                                                __fsub_rn(st.gf, xif)),
                                       m.em1);
                 }
-                s = cdf_select(m, m.eta_b, [&](int cc) { return Gcol[cc * kThr]; }, nc, G, delta,
+                // the site's certified margin from its own total (entropy bound)
+                const float Zs = __fadd_rn(G, delta);
+                const float eta = __fmaf_rn(m.kb1, __fsub_rn(m.hb, lg2_ftz(Zs)), m.kb0) +
+                                  m.kbr * __fdividef(delta, Zs);
+                s = cdf_select(m, eta, [&](int cc) { return Gcol[cc * kThr]; }, nc, G, delta,
                                st.in.xi, st.in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
                                    chunk_prefix_exact<NB>(m, mu, st.xn, st.gf, cs, pp);
                                });

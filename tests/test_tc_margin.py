@@ -1,0 +1,153 @@
+"""The certified margin of the tensor-core sweep's FP32 draw, checked by
+brute force on the CPU.
+
+For random sites of several models, the FP32 arithmetic of the window
+weights (2^(alpha (g-s)^2 + mu Pb + cb) with two roundings, ex2 off by up to
+2 ulp in the direction that hurts most), the chunk sums, the Kahan prefix and
+the inertia correction is replayed in numpy and every CDF value C_k / Z is
+compared with the exact conditional CDF of Eq. posterior_pca_transition_matrix
+(§5.2; FP64).  The library's per-site margin (pcad_model_margins: eta =
+kb1 (hb - log2 Z) + kb0 + kbr delta / Z, of which two thirds are the bound and
+one third slack) must exceed the worst error plus the rounding of t = u Z at
+every site.  CPU only: the coefficients come from the host side of the
+library, no kernel runs."""
+import numpy as np
+import pytest
+
+U = 2.0 ** -24
+LOG2E = 1.4426950408889634074
+f32, f64 = np.float32, np.float64
+
+
+@pytest.fixture(scope="module")
+def pc():
+    import paper_2507_14869_gb300 as pc
+    pc.lib()
+    return pc
+
+
+def _fma32(a, b, c):
+    # exact in FP64 for these magnitudes (24-bit x 24-bit products, integer
+    # q and Pb), then one rounding: the FP32 fused multiply-add
+    return (np.asarray(a, f64) * np.asarray(b, f64) + np.asarray(c, f64)).astype(f32)
+
+
+def _sites(rng, n, L, nbhd, spread):
+    x = np.where(rng.random((n, 1)) < 0.5,
+                 rng.integers(0, L, (n, nbhd)),
+                 np.clip(rng.integers(0, L, (n, 1)) + rng.integers(-spread, spread + 1, (n, nbhd)),
+                         0, L - 1))
+    present = rng.random((n, nbhd)) < 0.9            # missing neighbours: image border
+    present[:, 0] = True
+    g = np.where(rng.random(n) < 0.7, np.clip(x[:, 0] + rng.integers(-40, 41, n), 0, L - 1),
+                 rng.integers(0, L, n))
+    xi = np.where(rng.random(n) < 0.6, x[:, 0], rng.integers(0, L, n))
+    return x, present, g, xi
+
+
+def _worst_error(mg, model, x, present, g, xi, sign_split):
+    """Max over k of |C_k / Z - F_k| with the FP32 replay and the site's margin."""
+    L, T, nbhd = model["L"], model["T"], model["nbhd"]
+    s = np.arange(L)
+    Pb = (np.maximum(T - np.abs(s[None, None, :] - x[:, :, None]), 0) * present[:, :, None]).sum(1)
+    q = (g[:, None] - s[None, :]) ** 2
+    alpha, gam, cb = f32(mg["alpha"]), f32(mg["gam"]), f32(mg["cb"])
+    mu = -gam
+    v = _fma32(alpha, q, _fma32(mu, Pb, cb))
+    # ex2 within 2 ulp: correctly rounded, moved by 2u up for labels <= the
+    # split and down above it, rounded again
+    w = np.exp2(v.astype(f64)).astype(f32)
+    up = s[None, :] <= sign_split[:, None]
+    w = (w.astype(f64) * np.where(up, 1.0 + 2 * U, 1.0 - 2 * U)).astype(f32)
+    w = np.where(v < -126.0, f32(0.0), w)
+    n = len(g)
+    nc = (L + 7) // 8
+    wp = np.zeros((n, nc * 8), f32)
+    wp[:, :L] = w
+    # chunk sums (sequential), Kahan prefix over chunks, in-chunk prefixes
+    pref = np.zeros((n, nc * 8), f32)
+    S = np.zeros(n, f32)
+    for k in range(nc * 8):
+        S = S + wp[:, k] if k % 8 else wp[:, k].copy()
+        pref[:, k] = S
+    chunk = pref[:, 7::8]
+    G = np.zeros(n, f32)
+    comp = np.zeros(n, f32)
+    Gc = np.zeros((n, nc), f32)
+    for c in range(nc):
+        y = chunk[:, c] - comp
+        tt = G + y
+        comp = (tt - G) - y
+        G = tt
+        Gc[:, c] = G
+    # the model's parameters as the library receives them (FP32 fields)
+    lam = float(f32(model["inertia"]))
+    c_e, sig_e = float(f32(model["pair_coef"])), float(f32(model["sigma"]))
+    em1 = f32(np.expm1(lam))
+    delta = (w[np.arange(n), xi].astype(f64) * f64(em1)).astype(f32) if lam > 0 else np.zeros(n, f32)
+    Z = (G + delta).astype(f32)
+    Gprev = np.concatenate([np.zeros((n, 1), f32), Gc[:, :-1]], axis=1)
+    C = (np.repeat(Gprev, 8, axis=1)[:, :L] + pref[:, :L]).astype(f32)
+    C = (C + np.where(s[None, :] >= xi[:, None], delta[:, None], f32(0.0))).astype(f32)
+    # exact conditional
+    mu_e = c_e * LOG2E
+    alpha_e = -LOG2E / (2.0 * sig_e ** 2) if model["noise"] == 0 else 0.0
+    R = nbhd * T - Pb if mu_e > 0 else Pb
+    W = np.exp2(alpha_e * q - abs(mu_e) * R)
+    dW = np.expm1(lam) * W[np.arange(n), xi]
+    Fk = (np.cumsum(W, axis=1) + np.where(s[None, :] >= xi[:, None], dW[:, None], 0.0)) / \
+         (W.sum(1) + dW)[:, None]
+    err = np.abs(C.astype(f64) / Z.astype(f64)[:, None] - Fk).max(1)
+    eta = mg["kb1"] * (mg["hb"] - np.log2(Z.astype(f64))) + mg["kb0"] + \
+        mg["kbr"] * delta.astype(f64) / Z.astype(f64)
+    return err, eta, Fk
+
+
+MODELS = [
+    dict(L=256, nbhd=4, pair=1, pair_coef=0.05, pair_T=30, noise=0, sigma=20.0, inertia=2.0),
+    dict(L=256, nbhd=8, pair=1, pair_coef=0.15, pair_T=33, noise=0, sigma=25.0, inertia=1.0),
+    dict(L=100, nbhd=4, pair=1, pair_coef=0.5, pair_T=10, noise=0, sigma=4.0, inertia=0.3),
+    dict(L=64, nbhd=4, pair=1, pair_coef=4.9, pair_T=2, noise=0, sigma=2.0, inertia=5.0),
+    dict(L=128, nbhd=8, pair=0, pair_coef=4.5, pair_T=1, noise=0, sigma=6.0, inertia=0.0),
+    dict(L=256, nbhd=4, pair=1, pair_coef=-0.08, pair_T=30, noise=0, sigma=30.0, inertia=1.5),
+    dict(L=200, nbhd=4, pair=1, pair_coef=0.3, pair_T=20, noise=2, sigma=1.0, inertia=2.5),
+    dict(L=256, nbhd=8, pair=1, pair_coef=0.02, pair_T=25, noise=0, sigma=200.0, inertia=0.05),
+]
+
+
+@pytest.mark.parametrize("i", range(len(MODELS)))
+def test_margin_covers_worst_fp32_error(pc, i):
+    model = dict(MODELS[i])
+    model["T"] = 1 if model["pair"] == 0 else model["pair_T"]
+    mg = pc.pcad_model_margins(dict(model, flip_p=0.1, sampler=0))
+    assert mg["alpha"] == pytest.approx(-LOG2E / (2 * model["sigma"] ** 2) if model["noise"] == 0
+                                        else 0.0, rel=1e-6)
+    rng = np.random.default_rng(100 + i)
+    x, present, g, xi = _sites(rng, 600, model["L"], model["nbhd"], spread=6)
+    worst = 0.0
+    for split_kind in range(3):
+        if split_kind == 0:
+            split = np.full(len(g), -1)                # every weight low
+        elif split_kind == 1:
+            split = np.full(len(g), model["L"])        # every weight high
+        else:                                          # around each site's median
+            _, _, Fk = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1))
+            split = (Fk < 0.5).sum(1)
+        err, eta, _ = _worst_error(mg, model, x, present, g, xi, split)
+        bound = eta / 1.5 - U                          # without the slack, less t's rounding
+        assert np.all(err <= bound), (float(err.max()), float(bound[np.argmax(err / bound)]))
+        worst = max(worst, float((err / bound).max()))
+    assert worst < 1.0
+
+
+def test_margin_is_tighter_than_worst_case_constant(pc):
+    """At the bench model the per-site margin of typical sites is a small
+    multiple of 2^-24, well below the worst-case constant margin of the
+    CUDA-core kernels."""
+    model = dict(MODELS[0], T=30)
+    mg = pc.pcad_model_margins(dict(model, flip_p=0.1, sampler=0))
+    rng = np.random.default_rng(7)
+    x, present, g, xi = _sites(rng, 400, 256, 4, spread=4)
+    _, eta, _ = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1))
+    assert np.median(eta) < 0.5 * mg["eta"]
+    assert mg["cb"] == pytest.approx(-0.05 * LOG2E * 120, rel=1e-6)
