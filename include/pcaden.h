@@ -410,9 +410,11 @@ const char *pcad_version(void);
  * out[0] alpha and out[1] gam, the data and prior exponent coefficients in
  * base 2 (alpha = -log2(e) / (2 sigma^2), gam = -c log2(e)); out[2] eta, the
  * CUDA-core kernels' CDF margin (a draw is re-done in FP64 when u Z lies
- * within eta Z of the chosen label's CDF interval); out[3..7] cb, hb, kb0,
- * kb1, kbr of the tensor-core sweep: window weights 2^(alpha (g - s)^2 +
- * mu Pb + cb) (mu = -gam, Pb the tent sum), per-site margin
+ * within eta Z of the chosen label's CDF interval; the constant margin,
+ * used by the Lp prices, the two-label draw and gam > 0); out[3..7] cb, hb,
+ * kb0, kb1, kbr: the tensor-core window weights are 2^(alpha (g - s)^2 +
+ * mu Pb + cb) (mu = -gam, Pb the tent sum), and the tensor-core sweep and
+ * the CUDA-core sweeps with gam <= 0 take the per-site margin
  * eta = kb1 (hb - log2 Z) + kb0 + kbr delta / Z (Z the site's total with the
  * inertia weight delta).  out must hold n >= PCAD_N_MARGINS doubles.
  * PCAD_EINVAL for an invalid model or buffer. */

@@ -179,7 +179,9 @@ void build_tables(const pcad_model &m, ModelTables &t)
                             4.0 * u;
         d.eta = (float)(1.5 * 2.0 * (2.0 * e_wn + gsum) + 8.0 * u);
     }
-    // Tensor-core sweep, per-site margin.  Window labels take
+    // Per-site margin (the tensor-core sweep; the CUDA-core sweeps' weights
+    // 2^fl(alpha q + fl(gam P)) with gam <= 0 satisfy the same |dv| <= 3u |v|
+    // with cb = 0 and R = P, and take it too).  Tensor-core window labels take
     // v = fl(alpha q + fl(mu Pb + cb)) (q = (g - s)^2 and the tent sum Pb
     // exact integers, mu = -gam), outside labels (Pb = 0) v = fl(alpha q + cb),
     // with cb = -fl(mu nbhd T) for mu > 0 (else 0), the same float for every

@@ -120,6 +120,17 @@ __device__ __forceinline__ float lg2_ftz(float x)
     return y;
 }
 
+// Certified CDF margin of one site's draw from its own total Z = G + delta
+// (the weights' exponents must be sums of non-positive terms, each label's
+// exponent error within 3u |v|: the tensor-core weights, and the CUDA-core
+// weights when gam <= 0):
+// eta = kb1 (log2(L + 1) + slack - log2 Z) + kb0 + kbr delta / Z.
+__device__ __forceinline__ float site_margin(const DevModel &m, float G, float delta)
+{
+    const float Z = __fadd_rn(G, delta);
+    return __fmaf_rn(m.kb1, __fsub_rn(m.hb, lg2_ftz(Z)), m.kb0) + m.kbr * __fdividef(delta, Z);
+}
+
 // Weight 2^v of one label: v = alpha (g - s)^2 + gam P(s).  dg = g - s and
 // P are exact small integers; (g - s)^2 <= 65025 is exact in FP32.
 __device__ __forceinline__ float label_w(const DevModel &m, float P, float dg)
@@ -393,7 +404,9 @@ __device__ __forceinline__ int draw_fp32(const DevModel &m, float *Gcol, int gst
     float delta = 0.0f;
     if (m.em1 != 0.0f)
         delta = __fmul_rn(single_w<NB>(m, xn, gf, xi), m.em1);
-    return cdf_select(m, m.eta, [&](int c) { return Gcol[c * gstride]; }, NC, G, delta, xi,
+    // gam <= 0: both exponent terms are non-positive, the per-site margin holds
+    const float eta = m.gam <= 0.0f ? site_margin(m, G, delta) : m.eta;
+    return cdf_select(m, eta, [&](int c) { return Gcol[c * gstride]; }, NC, G, delta, xi,
                       in.ub, certain, [&](int cs, float (&p)[kChunk]) {
                           chunk_weights<NB, true, true>(m, xh, T2, gf, cs, p);
                       });

@@ -270,21 +270,36 @@ __device__ __forceinline__ float tab_sum(const float *tab, int g, int c, int nc)
 }
 
 // Sum of the weights of window chunk c from 8 tent sums read from TMEM (pb,
-// raw FP32 bits).
+// raw FP32 bits).  Two labels per packed FP32x2 instruction (each lane of a
+// pair rounds as the scalar operation: the weights equal label_wb's); the
+// chunk sum is a pairwise tree (3 roundings per weight).
 template <bool LMASK>
 __device__ __forceinline__ float window_chunk(const DevModel &m, float mu, float gf,
                                               const uint32_t *pb, int c)
 {
     const float dgb = __fsub_rn(gf, (float)(c * kChunk));
-    float S = 0.0f;
+    const float2 a2 = make_float2(m.alpha, m.alpha), mu2 = make_float2(mu, mu),
+                 cb2 = make_float2(m.cb, m.cb);
+    const float2 dgb2 = make_float2(dgb, __fsub_rn(dgb, 1.0f));
+    float2 wv[4];
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-        float w = label_wb(m, mu, __uint_as_float(pb[k]), __fsub_rn(dgb, (float)k));
+    for (int k = 0; k < kChunk; k += 2) {
+        const float2 dg = __fadd2_rn(dgb2, make_float2(-(float)k, -(float)k));
+        const float2 qq = __fmul2_rn(dg, dg);
+        const float2 pb2 = make_float2(__uint_as_float(pb[k]), __uint_as_float(pb[k + 1]));
+        const float2 in2 = __ffma2_rn(mu2, pb2, cb2);
+        const float2 v = __ffma2_rn(a2, qq, in2);
+        float w0 = ex2_ftz(v.x), w1 = ex2_ftz(v.y);
         if (LMASK && c * kChunk + k >= m.L)
-            w = 0.0f;
-        S = __fadd_rn(S, w);
+            w0 = 0.0f;
+        if (LMASK && c * kChunk + k + 1 >= m.L)
+            w1 = 0.0f;
+        wv[k >> 1] = make_float2(w0, w1);
     }
-    return S;
+    const float2 a = __fadd2_rn(make_float2(wv[0].x, wv[2].x), make_float2(wv[0].y, wv[2].y));
+    const float2 b = __fadd2_rn(make_float2(wv[1].x, wv[3].x), make_float2(wv[1].y, wv[3].y));
+    const float2 t2 = __fadd2_rn(a, b);
+    return __fadd_rn(t2.x, t2.y);
 }
 
 // Chunks (bit c) that an outlier's tent reaches: labels within T - 1 of it.
@@ -307,22 +322,45 @@ __device__ __forceinline__ uint32_t outlier_chunks(const TcSite<NB> &st, int T, 
 
 // Inclusive prefix sums of absolute chunk c's weights from exact tent sums
 // (neighbour labels xn, observation gf) on the CUDA cores: bit-identical to
-// the pass-1 weights.
+// the pass-1 weights.  The tents of two labels at once in half2 (integers up
+// to 2048 are exact: neighbour labels, 1024 for a missing one, less 8c), the
+// weights as window_chunk's.
 template <int NB>
 __device__ __forceinline__ void chunk_prefix_exact(const DevModel &m, float mu,
                                                    const float (&xn)[NB], float gf, int c,
                                                    float (&p)[kChunk])
 {
+    const float sb = (float)(c * kChunk);
+    const __half2 T2 = __float2half2_rn(m.Tf), z2 = __float2half2_rn(0.0f);
+    __half2 xr[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        xr[j] = __float2half2_rn(__fsub_rn(xn[j], sb));
+    const float dgb = __fsub_rn(gf, sb);
+    const float2 a2 = make_float2(m.alpha, m.alpha), mu2 = make_float2(mu, mu),
+                 cb2 = make_float2(m.cb, m.cb);
+    const float2 dgb2 = make_float2(dgb, __fsub_rn(dgb, 1.0f));
     float S = 0.0f;
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-        const int s = c * kChunk + k;
-        const float sf = (float)s;
-        float w = label_wb(m, mu, tent_sum<NB>(xn, m.Tf, sf), __fsub_rn(gf, sf));
-        if (s >= m.L)
-            w = 0.0f;
-        S = __fadd_rn(S, w);
+    for (int k = 0; k < kChunk; k += 2) {
+        const __half2 k2 = __floats2half2_rn((float)k, (float)(k + 1));
+        __half2 P2 = z2;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            P2 = __hadd2(P2, __hmax2(__hsub2(T2, __habs2(__hsub2(k2, xr[j]))), z2));
+        const float2 dg = __fadd2_rn(dgb2, make_float2(-(float)k, -(float)k));
+        const float2 qq = __fmul2_rn(dg, dg);
+        const float2 in2 = __ffma2_rn(mu2, __half22float2(P2), cb2);
+        const float2 v = __ffma2_rn(a2, qq, in2);
+        float w0 = ex2_ftz(v.x), w1 = ex2_ftz(v.y);
+        if (c * kChunk + k >= m.L)
+            w0 = 0.0f;
+        if (c * kChunk + k + 1 >= m.L)
+            w1 = 0.0f;
+        S = __fadd_rn(S, w0);
         p[k] = S;
+        S = __fadd_rn(S, w1);
+        p[k + 1] = S;
     }
 }
 
@@ -909,10 +947,8 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
                                       m.em1);
                 }
                 // the site's certified margin from its own total (entropy bound)
-                const float Zs = __fadd_rn(G, delta);
-                const float eta = __fmaf_rn(m.kb1, __fsub_rn(m.hb, lg2_ftz(Zs)), m.kb0) +
-                                  m.kbr * __fdividef(delta, Zs);
-                s = cdf_select(m, eta, [&](int cc) { return Gcol[cc * kThr]; }, nc, G, delta,
+                s = cdf_select(m, site_margin(m, G, delta), [&](int cc) { return Gcol[cc * kThr]; },
+                               nc, G, delta,
                                st.in.xi, st.in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
                                    chunk_prefix_exact<NB>(m, mu, st.xn, st.gf, cs, pp);
                                });

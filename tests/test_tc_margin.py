@@ -1,5 +1,6 @@
-"""The certified margin of the tensor-core sweep's FP32 draw, checked by
-brute force on the CPU.
+"""The per-site certified margin of the FP32 draw (tensor-core sweep, and
+CUDA-core sweeps with a non-negative prior coefficient), checked by brute
+force on the CPU.
 
 For random sites of several models, the FP32 arithmetic of the window
 weights (2^(alpha (g-s)^2 + mu Pb + cb) with two roundings, ex2 off by up to
@@ -45,15 +46,24 @@ def _sites(rng, n, L, nbhd, spread):
     return x, present, g, xi
 
 
-def _worst_error(mg, model, x, present, g, xi, sign_split):
-    """Max over k of |C_k / Z - F_k| with the FP32 replay and the site's margin."""
+def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
+    """Max over k of |C_k / Z - F_k| with the FP32 replay and the site's
+    margin.  form "tc": the tensor-core weights 2^fl(alpha q + fl(mu Pb + cb))
+    (Pb the tent sum of the present neighbours); "cc": the CUDA-core weights
+    2^fl(alpha q + fl(gam P)) (P = sum of min(|x_j - s|, T), T for a missing
+    neighbour)."""
     L, T, nbhd = model["L"], model["T"], model["nbhd"]
     s = np.arange(L)
     Pb = (np.maximum(T - np.abs(s[None, None, :] - x[:, :, None]), 0) * present[:, :, None]).sum(1)
     q = (g[:, None] - s[None, :]) ** 2
     alpha, gam, cb = f32(mg["alpha"]), f32(mg["gam"]), f32(mg["cb"])
     mu = -gam
-    v = _fma32(alpha, q, _fma32(mu, Pb, cb))
+    if form == "tc":
+        v = _fma32(alpha, q, _fma32(mu, Pb, cb))
+    else:
+        P = (np.where(present[:, :, None], np.minimum(np.abs(s[None, None, :] - x[:, :, None]), T),
+                      T)).sum(1)
+        v = _fma32(alpha, q, (f64(gam) * P).astype(f32))
     # ex2 within 2 ulp: correctly rounded, moved by 2u up for labels <= the
     # split and down above it, rounded again
     w = np.exp2(v.astype(f64)).astype(f32)
@@ -71,6 +81,10 @@ def _worst_error(mg, model, x, present, g, xi, sign_split):
         S = S + wp[:, k] if k % 8 else wp[:, k].copy()
         pref[:, k] = S
     chunk = pref[:, 7::8]
+    if form == "tc":   # window chunk sums: a pairwise tree ((w0+w1)+(w2+w3))+((w4+w5)+(w6+w7))
+        w8 = wp.reshape(n, nc, 8)
+        pairs = w8[:, :, 0::2] + w8[:, :, 1::2]
+        chunk = (pairs[:, :, 0] + pairs[:, :, 1]) + (pairs[:, :, 2] + pairs[:, :, 3])
     G = np.zeros(n, f32)
     comp = np.zeros(n, f32)
     Gc = np.zeros((n, nc), f32)
@@ -115,8 +129,12 @@ MODELS = [
 ]
 
 
-@pytest.mark.parametrize("i", range(len(MODELS)))
-def test_margin_covers_worst_fp32_error(pc, i):
+CASES = [(i, "tc") for i in range(len(MODELS))] + \
+    [(i, "cc") for i, m in enumerate(MODELS) if m["pair_coef"] >= 0]
+
+
+@pytest.mark.parametrize("i,form", CASES, ids=[f"{f}{i}" for i, f in CASES])
+def test_margin_covers_worst_fp32_error(pc, i, form):
     model = dict(MODELS[i])
     model["T"] = 1 if model["pair"] == 0 else model["pair_T"]
     mg = pc.pcad_model_margins(dict(model, flip_p=0.1, sampler=0))
@@ -131,9 +149,9 @@ def test_margin_covers_worst_fp32_error(pc, i):
         elif split_kind == 1:
             split = np.full(len(g), model["L"])        # every weight high
         else:                                          # around each site's median
-            _, _, Fk = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1))
+            _, _, Fk = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1), form)
             split = (Fk < 0.5).sum(1)
-        err, eta, _ = _worst_error(mg, model, x, present, g, xi, split)
+        err, eta, _ = _worst_error(mg, model, x, present, g, xi, split, form)
         bound = eta / 1.5 - U                          # without the slack, less t's rounding
         assert np.all(err <= bound), (float(err.max()), float(bound[np.argmax(err / bound)]))
         worst = max(worst, float((err / bound).max()))
