@@ -81,6 +81,15 @@ __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 // smaller index and was taken by a block that is resident (the grid is the
 // resident capacity), so the waits end; each is bounded anyway (error flag).
 // Draws are keyed by (sweep, site): results equal per-sweep launches.
+// Tile counters are observed with acquire loads: a waiting lane's label
+// reads after the block barrier see what the tile published.
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 constexpr long long kWaveSpinLimit = 20000000;
 #ifndef PCAD_WAVE_MIN_BLOCKS
 #define PCAD_WAVE_MIN_BLOCKS 8   // resident blocks per SM the register budget targets
@@ -119,9 +128,9 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
                 const int yy = ty + (int)threadIdx.x / 3 - 1;
                 const int xx = tx + (int)threadIdx.x % 3 - 1;
                 if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
-                    const volatile unsigned int *d = done + (size_t)yy * tiles_x + xx;
+                    const unsigned int *d = done + (size_t)yy * tiles_x + xx;
                     long long spins = 0;
-                    while (*d < (unsigned int)k) {
+                    while (ld_acquire_gpu(d) < (unsigned int)k) {
                         if (++spins > kWaveSpinLimit) {
                             ok = false;
                             break;
@@ -132,7 +141,6 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
             }
             if (!ok)
                 atomicExch(err, 1);
-            __threadfence();   // order the observed counters before the reads below
             __syncwarp();
         }
         __syncthreads();
@@ -324,9 +332,9 @@ __global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
                 const int yy = ty + (int)threadIdx.x / 3 - 1;
                 const int xx = tx + (int)threadIdx.x % 3 - 1;
                 if (yy >= 0 && yy < gm.tiles_y && xx >= 0 && xx < gm.tiles_x) {
-                    const volatile unsigned int *c = done + gm.base + yy * gm.tiles_x + xx;
+                    const unsigned int *c = done + gm.base + yy * gm.tiles_x + xx;
                     long long spins = 0;
-                    while (*c < (unsigned int)k) {
+                    while (ld_acquire_gpu(c) < (unsigned int)k) {
                         if (++spins > kWaveSpinLimit) {
                             ok = false;
                             break;
@@ -344,7 +352,6 @@ __global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
                 }
                 s_go = go;
             }
-            __threadfence();   // order the observed counters before the reads below
             __syncwarp();
         }
         __syncthreads();

@@ -144,22 +144,18 @@ __device__ __forceinline__ float tent_sum(const float (&x)[N], float Tf, float s
 }
 
 // Tile counters: published with a release store by one thread after a
-// group barrier, observed with relaxed loads and an acquire fence.
+// group barrier, observed with acquire loads (the first one early, while the
+// group still works on its current item).
 __device__ __forceinline__ void st_release_gpu(unsigned int *p, unsigned int v)
 {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int *p)
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
 {
     unsigned int v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
-}
-
-__device__ __forceinline__ void fence_acq_rel_gpu()
-{
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 // Per-site state of one item.
@@ -382,9 +378,11 @@ __device__ __forceinline__ const unsigned int *dep_counter(const unsigned int *d
     return done + (size_t)yy * tiles_x + xx;
 }
 
-// Wait (bounded) until *d >= k; `seen` is an earlier observation of *d.
-// Ends with an acquire fence, so the labels read after the group's next
-// barrier are those the tile published.  Returns false if the wait gave up.
+// Wait (bounded) until *d >= k; `seen` is an earlier acquire load of *d.
+// Every observation is an acquire load, so the labels read after the
+// group's next barrier are those the tile published (the publisher's
+// release store) without a fence on this path.  Returns false if the wait
+// gave up.
 __device__ __forceinline__ bool wait_counter(const unsigned int *d, unsigned int k,
                                              unsigned int seen)
 {
@@ -397,10 +395,9 @@ __device__ __forceinline__ bool wait_counter(const unsigned int *d, unsigned int
                 break;
             }
             __nanosleep(64);
-            seen = ld_relaxed_gpu(d);
+            seen = ld_acquire_gpu(d);
         }
     }
-    fence_acq_rel_gpu();
     return ok;
 }
 
@@ -498,7 +495,7 @@ __device__ __forceinline__ void tc_wait_item(const TcParams &p, const TcItem &ii
 {
     const unsigned int *d =
         dep_counter(p.done + ii.base, ii.k, ii.tile, ii.tiles_x, ii.tiles_y, lane);
-    const unsigned int seen = (d && d == pre_d) ? pre : (d ? ld_relaxed_gpu(d) : 0u);
+    const unsigned int seen = (d && d == pre_d) ? pre : (d ? ld_acquire_gpu(d) : 0u);
     if (!wait_counter(d, (unsigned int)ii.k, seen))
         atomicExch(p.err, 1);
 }
@@ -846,7 +843,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
                     dnext = dep_counter(p.done + in2.base, in2.k, in2.tile, in2.tiles_x,
                                         in2.tiles_y, lane);
                     if (dnext)
-                        seen = ld_relaxed_gpu(dnext);
+                        seen = ld_acquire_gpu(dnext);
                 }
             }
 
