@@ -975,12 +975,13 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
         }
 
         // publish the tile's sweep (every output written), take the next item
+        // warp 1 publishes (its release store waits for the tile's writes to
+        // drain) while warp 0 takes the next item
+        if (q == 1 && lane == 0 && go)   // after every output of the tile
+            st_release_gpu(p.done + ii.base + ii.tile, (unsigned int)(k + 1));
         if (q == 0) {
-            if (lane == 0) {
-                if (go)   // after every output of the tile
-                    st_release_gpu(p.done + ii.base + ii.tile, (unsigned int)(k + 1));
+            if (lane == 0)
                 s_item[grp] = next;
-            }
             const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
             if (nx < total) {
                 if constexpr (BATCH) {
