@@ -51,7 +51,7 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
 # The same for pca_tcw_kernel<4,0,0,0> (one 32-sweep launch at 512^2,
 # profiles/pca_tc_l256_512sq.md) and pca_wave_kernel<32,4> (one 32-sweep
 # launch at 1024^2, per site-update).
-NCU_TC_DRAM_BYTES_PER_SITE = (1.632512e6 + 0.068352e6) / (32 * 512 * 512)
+NCU_TC_DRAM_BYTES_PER_SITE = (1.637888e6 + 0.122880e6) / (32 * 512 * 512)
 NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
                        "161-192 of a chain), per site-update: the chain's planes stay in L2")
 NCU_WAVE_DRAM_BYTES_PER_SITE = (6.371584e6 + 0.745728e6) / (32 * 1024 * 1024)

@@ -405,10 +405,12 @@ const char *pcad_last_error(void);
 /* Library version string. */
 const char *pcad_version(void);
 
-/* The FP32 constants behind the certified draw of model m (host only, no
- * device work; the paper fixes no precision, so these are this library's):
+/* The FP32 constants behind the certified draw of model m from its
+ * conditional (Section 5.2, Eq. posterior_pca_transition_matrix; host only,
+ * no device work; the paper fixes no precision, so these are this library's):
  * out[0] alpha and out[1] gam, the data and prior exponent coefficients in
- * base 2 (alpha = -log2(e) / (2 sigma^2), gam = -c log2(e)); out[2] eta, the
+ * base 2 (alpha = -log2(e) / (2 sigma^2) for Gaussian noise, -log2(e)
+ * ln((1 - p) / p) for flips, 0 without a likelihood; gam = -c log2(e)); out[2] eta, the
  * CUDA-core kernels' CDF margin (a draw is re-done in FP64 when u Z lies
  * within eta Z of the chosen label's CDF interval; the constant margin,
  * used by the Lp prices, the two-label draw and gam > 0); out[3..7] cb, hb,

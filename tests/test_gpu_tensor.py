@@ -2,7 +2,9 @@
 CUDA cores, many sweeps per wavefront launch) against the CUDA-core sweep
 and the oracle: labels and posterior means must be bit-identical for
 tile-ragged images, label counts that are not multiples of 8 or 32, both
-neighbourhoods, Potts (T = 1) and the widest supported truncation, sharp
+neighbourhoods, Potts (T = 1), a negative (repulsive) prior coefficient
+(no exponent offset, constant CUDA-core margin) and the widest supported
+truncation, sharp
 edges (neighbours outside a site's 64-label histogram window), images with
 more tiles than the persistent grid, and per-sweep launches under energy
 tracking."""
@@ -65,6 +67,9 @@ CASES = [
     ("L256_8nb_edges_40x70", lambda: (_edges(16, 40, 70),
                                       Model(L=256, nbhd=8, pair=TL, pair_coef=0.03, pair_T=25,
                                             sigma=12.0, inertia=1.0))),
+    ("L256_repulsive_45x38", lambda: (_grey(17, 45, 38, 256, 20.0),
+                                      Model(L=256, pair=TL, pair_coef=-0.02, pair_T=30,
+                                            sigma=20.0, inertia=1.5))),
     ("L71_3x1", lambda: (_grey(9, 3, 1, 71, 5.0),
                          Model(L=71, pair=TL, pair_coef=0.3, pair_T=4, sigma=5.0, inertia=1.0))),
     ("L256_300x257", lambda: (_grey(10, 300, 257, 256, 20.0),

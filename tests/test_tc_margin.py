@@ -169,3 +169,17 @@ def test_margin_is_tighter_than_worst_case_constant(pc):
     _, eta, _ = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1))
     assert np.median(eta) < 0.5 * mg["eta"]
     assert mg["cb"] == pytest.approx(-0.05 * LOG2E * 120, rel=1e-6)
+
+
+def test_model_margins_rejects_bad_arguments(pc):
+    import ctypes
+    good = dict(MODELS[0], flip_p=0.1, sampler=0)
+    m = pc.as_model(good)
+    out = (ctypes.c_double * 4)()
+    assert pc.lib().pcad_model_margins(ctypes.byref(m), out, 4) == 1     # n < PCAD_N_MARGINS
+    with pytest.raises(pc.PcadError):
+        pc.pcad_model_margins(dict(good, pair_coef=1.0))                 # prior range > 40
+    with pytest.raises(pc.PcadError):
+        pc.pcad_model_margins(dict(good, sigma=-1.0))
+    mg = pc.pcad_model_margins(dict(good, pair_coef=-0.05))
+    assert mg["cb"] == 0.0 and mg["gam"] > 0                             # c < 0: no offset
