@@ -274,10 +274,16 @@ def run_ours(a):
         gms, _ = timed(gch, gsteps, 1)
         gT = sum(gms) / 1e3
         gp, gs = gch.metrics(clean, 0)
+        g_tc = gch.kernel_in_use() == pc.PCAD_KERNEL_TENSOR
+        gblocks = (SWEEPS + 31) // 32
         gibbs = {"value": sites * gsteps / gT, "unit": "site-updates/s",
                  "ms_per_step": 1e3 * gT / gsteps, "steps": gsteps, "psnr_db": gp, "ssim": gs,
-                 "launches_per_step": 2 * SWEEPS + (SWEEPS + 31) // 32,
-                 "kernel": "gibbs_cb_kernel<32,4> (2 colour phases per sweep)"}
+                 # per 32-sweep graph: the wavefront launch (or 2 colour-phase launches per
+                 # sweep), the counter reset and the sweep-counter advance
+                 "launches_per_step": gblocks * 2 if g_tc else 2 * SWEEPS + gblocks,
+                 "kernel": ("pca_tcw_kernel<4,0,0,0,1> (checkerboard Gibbs on the tensor-core "
+                            "wavefront, 2 colour phases per sweep)") if g_tc else
+                           "gibbs_cb_kernel<32,4> (2 colour phases per sweep)"}
         gch.close()
 
     # end to end through the public API with host buffers (pinned)

@@ -138,7 +138,7 @@ pcad_status pcad_chain_reset(pcad_chain *ch);
  * load ever failed to complete within its bounded wait. */
 pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
 
-/* Kernel of the unblocked PCA sweep (k = 0 above).  The prior sum of
+/* Kernel of the unblocked PCA sweep (k = 0 above) and of the Gibbs sweep.  The prior sum of
  * Eq. posterior_pca_transition_matrix is a sum of tents
  * max(T - |x_j - s|, 0) over the neighbours.  PCAD_KERNEL_TENSOR computes
  * it on the tensor cores (tcgen05): each site histograms its neighbour
@@ -148,8 +148,10 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * neighbours beyond the 64 bins are added on the CUDA cores; sweeps run as
  * a wavefront (below).  PCAD_KERNEL_CUDA_CORE evaluates every label's prior
  * on the CUDA cores.  All kernels draw exactly the same labels.  The
- * tensor-core kernel accepts the PCA sampler with 64 <= L <= 256,
- * truncation T <= 33 (Potts: T = 1) and the L0 price; PCAD_EINVAL for an
+ * tensor-core kernel accepts 64 <= L <= 256, truncation T <= 33 (Potts:
+ * T = 1) and the L0 price, for the PCA sampler and for the checkerboard
+ * Gibbs sampler with the 4-neighbourhood (colour phases over 8 x 32 tiles,
+ * in place, as a wavefront of phases; Section 5.1); PCAD_EINVAL for an
  * unknown kind or PCAD_KERNEL_TENSOR on another model.  PCAD_KERNEL_AUTO
  * (the default) takes it for L >= 192 without energy tracking (where it
  * measured faster on GB300), else the per-sweep or the wavefront CUDA-core

@@ -278,12 +278,15 @@ SweepArgs make_args(const pcad_chain *ch)
     return a;
 }
 
-// Unblocked PCA sweeps on the tensor-core kernel: on request, or with AUTO
-// for the models pca_tc_auto accepts when every sweep's state is not needed
-// (energy tracking would force one launch per sweep).
+// Unblocked PCA sweeps, and 4-neighbourhood checkerboard Gibbs sweeps, on the
+// tensor-core kernel: on request, or with AUTO for the models pca_tc_auto
+// accepts when every sweep's state is not needed (energy tracking would force
+// one launch per sweep).
 bool uses_tc(const pcad_chain *ch)
 {
-    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !pca_tc_eligible(ch->dm))
+    if (!pca_tc_eligible(ch->dm))
+        return false;
+    if (ch->model.sampler == PCAD_SAMPLER_PCA ? ch->tb_k > 0 : ch->model.nbhd != 4)
         return false;
     if (ch->kernel == PCAD_KERNEL_TENSOR)
         return true;
@@ -320,10 +323,15 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
             a.sweep_off = (uint32_t)(off0 + k);
             CUDA_TRY(cudaMemsetAsync(ch->wave, 0,
                                      (size_t)(ch->wave_tiles + 1) * sizeof(unsigned int), st));
-            CUDA_TRY(launch_pca_tc(a, ch->x[cur], ch->x[cur ^ 1], per, ch->wave,
-                                   ch->wave + ch->wave_tiles, ch->err, st));
-            if (per & 1)
-                cur ^= 1;
+            if (ch->model.sampler == PCAD_SAMPLER_PCA) {
+                CUDA_TRY(launch_pca_tc(a, ch->x[cur], ch->x[cur ^ 1], per, ch->wave,
+                                       ch->wave + ch->wave_tiles, ch->err, st));
+                if (per & 1)
+                    cur ^= 1;
+            } else {   // checkerboard Gibbs, in place
+                CUDA_TRY(launch_gibbs_tc(a, ch->x[cur], per, ch->wave, ch->wave + ch->wave_tiles,
+                                         ch->err, st));
+            }
             if (ch->track.trace)
                 CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
                                        ch->esums, nullptr, ch->track, ch->tdev, a.sweep_off, st));
@@ -717,7 +725,7 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
     if (!ch || !kind)
         return fail(PCAD_EINVAL, "chain or kind is NULL");
     if (ch->model.sampler != PCAD_SAMPLER_PCA)
-        *kind = PCAD_KERNEL_CUDA_CORE;
+        *kind = uses_tc(ch) ? PCAD_KERNEL_TENSOR : PCAD_KERNEL_CUDA_CORE;
     else if (ch->tb_k > 0)
         *kind = -ch->tb_k;
     else if (uses_tc(ch))
@@ -843,9 +851,10 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
     if (kind == PCAD_KERNEL_WAVE && (ch->model.sampler != PCAD_SAMPLER_PCA || ch->dm.norm != 0))
         return fail(PCAD_EINVAL, "the wavefront kernel needs the PCA sampler and the L0 price");
     if (kind == PCAD_KERNEL_TENSOR &&
-        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_tc_eligible(ch->dm)))
-        return fail(PCAD_EINVAL, "the tensor-core sweep needs the PCA sampler, 64 <= L <= 256, "
-                                 "T <= 33 and the L0 inertia price");
+        (!pca_tc_eligible(ch->dm) ||
+         (ch->model.sampler != PCAD_SAMPLER_PCA && ch->model.nbhd != 4)))
+        return fail(PCAD_EINVAL, "the tensor-core sweep needs 64 <= L <= 256, T <= 33, the L0 "
+                                 "inertia price and, for Gibbs, the 4-neighbourhood");
     if (kind != ch->kernel && ch->graph) {
         cudaStreamSynchronize(ch->stream);
         cudaGraphExecDestroy(ch->graph);

@@ -245,11 +245,17 @@ bool pca_tc_eligible(const DevModel &m);
 cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nsweeps,
                           unsigned int *done, unsigned int *grab, int *err, cudaStream_t s,
                           const uint32_t *budget = nullptr, bool par_from_t = false);
+// nsweeps checkerboard Gibbs sweeps (4-neighbourhood, 2 colour phases each)
+// of one chain in place on x, on the same tensor-core kernel: 8 x 32 tiles,
+// one counter per tile in done[] (at least ceil(H / 8) * ceil(W / 32)
+// zeroed entries), grab zeroed.
+cudaError_t launch_gibbs_tc(const SweepArgs &a, uint8_t *x, int nsweeps, unsigned int *done,
+                            unsigned int *grab, int *err, cudaStream_t s);
 
 // Models the automatic kernel choice gives the tensor-core sweep: eligible
-// and L >= kTcAutoLabels (on GB300 it measured 1.1-1.2x the CUDA-core
-// kernels at L = 256 and slower below L = 192: the window's work does not
-// shrink with L).
+// and L >= kTcAutoLabels (on GB300 it measured 1.4-1.6x the CUDA-core
+// kernels at L = 256, level at L = 128 and slower below: the window's work
+// does not shrink with L).
 constexpr int kTcAutoLabels = 192;
 bool pca_tc_auto(const DevModel &m);
 

@@ -60,6 +60,7 @@ namespace {
 
 constexpr int kSites = 128;                 // tile: 4 rows x 32 columns = MMA M = TMEM lanes
 constexpr int kTileRows = 4;
+constexpr int kGibbsRows = 8;    // Gibbs tiles: 8 x 32 sites, 128 of each colour
 constexpr int kGroups = 4;                  // warpgroups per CTA, one tile each
 constexpr int kThr = kGroups * kSites;      // 512 threads
 constexpr int kWin = 128;                   // window labels = MMA N = TMEM columns per group
@@ -615,8 +616,11 @@ __device__ __forceinline__ const SweepArgs &item_args(const TcParams &p, const S
         return p.a;
 }
 
-// BUDGET (one chain): sweeps with index >= *p.budget are skipped.
-template <int NB, bool LMASK, bool BATCH, bool BUDGET>
+// BUDGET (one chain): sweeps with index >= *p.budget are skipped.  GIBBS
+// (one chain, 4-neighbourhood): the checkerboard Gibbs sweep in place on
+// p.x0; item k is colour phase k & 1 of sweep k >> 1 over 8 x 32 tiles,
+// whose 128 sites of that colour are the group's sites.
+template <int NB, bool LMASK, bool BATCH, bool BUDGET, bool GIBBS = false>
 __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
 {
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -729,8 +733,11 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
         const unsigned int par = seq & 1u;
         const TcItem ii = tc_decode<BATCH>(p, item);
         const int k = ii.k;
-        const int r = ii.ty * kTileRows + q;
-        const int c = ii.tx * 32 + lane;
+        // Gibbs: thread lt takes tile row lt / 16 and, in column pair lt % 16,
+        // the site of the phase's colour ((r + c) mod 2 = colour)
+        const int colour = GIBBS ? (k & 1) : 0;
+        const int r = GIBBS ? ii.ty * kGibbsRows + (lt >> 4) : ii.ty * kTileRows + q;
+        const int c = GIBBS ? ii.tx * 32 + 2 * (lt & 15) + ((r + colour) & 1) : ii.tx * 32 + lane;
         bool go = true;
         const SweepArgs *bp = nullptr;   // batched chains: the staged arguments
         const float *tab;        // outside-chunk sums (shared memory)
@@ -744,6 +751,11 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
             t = s_t[grp * 2 + par];
             xin = bp->xin;
             xout = bp->xout;
+        } else if constexpr (GIBBS) {
+            t = t0 + (uint32_t)(k >> 1);
+            xin = p.x0;   // in place: a phase reads the other colour only
+            xout = p.x0;
+            tab = tabs;
         } else {
             t = t0 + (uint32_t)k;
             const uint32_t ph = p.par_from_t ? (t & 1u) : (uint32_t)(k & 1);
@@ -768,10 +780,19 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
             TcSite<NB> st;
             st.in = SiteIn<NB>{};
             if (valid)
-                load_site<NB, true>(b, xin, r, c, kTagPCA, t, st.in);
+                load_site<NB, true>(b, xin, r, c, GIBBS ? kTagGibbs : kTagPCA, t, st.in);
             float *accp = b.acc + (size_t)r * b.W + c;
-            const bool acc_on = valid && accumulate_after(b, t);
+            // Gibbs accumulates after the last phase: this site and its pair's
+            // colour-0 site, final since phase 0 of this sweep
+            const bool acc_on = valid && (!GIBBS || colour == 1) && accumulate_after(b, t);
             const float acc_old = acc_on ? __ldcg(accp) : 0.0f;   // prefetched
+            if constexpr (GIBBS) {
+                const int cp = c ^ 1;
+                if (colour == 1 && r < b.H && cp < b.W && accumulate_after(b, t)) {
+                    float *ap = b.acc + (size_t)r * b.W + cp;
+                    *ap = __ldcg(ap) + (float)__ldcg(xin + (size_t)r * b.pitch + cp);
+                }
+            }
 #pragma unroll
             for (int jn = 0; jn < NB; ++jn)
                 st.xn[jn] = (float)st.in.xni[jn];
@@ -1023,7 +1044,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
     }
 }
 
-template <int NB, bool LMASK, bool BATCH, bool BUDGET>
+template <int NB, bool LMASK, bool BATCH, bool BUDGET, bool GIBBS = false>
 cudaError_t launch_tcw_t(const TcParams &p, long long items, cudaStream_t st)
 {
     static bool attr_set[64] = {};
@@ -1034,7 +1055,7 @@ cudaError_t launch_tcw_t(const TcParams &p, long long items, cudaStream_t st)
     if (dev >= 64)
         return cudaErrorInvalidDevice;
     if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(pca_tcw_kernel<NB, LMASK, BATCH, BUDGET>,
+        e = cudaFuncSetAttribute(pca_tcw_kernel<NB, LMASK, BATCH, BUDGET, GIBBS>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  tc_smem_bytes(32, BATCH));
         if (e != cudaSuccess)
@@ -1052,7 +1073,7 @@ cudaError_t launch_tcw_t(const TcParams &p, long long items, cudaStream_t st)
     // one CTA per SM (TMEM: all 512 columns); no more CTAs than 4-item groups
     const long long need = (items + kGroups - 1) / kGroups;
     const int grid = (int)(need < sms ? need : sms);
-    pca_tcw_kernel<NB, LMASK, BATCH, BUDGET><<<grid, kThr, tc_smem_bytes(p.nc_max, BATCH), st>>>(
+    pca_tcw_kernel<NB, LMASK, BATCH, BUDGET, GIBBS><<<grid, kThr, tc_smem_bytes(p.nc_max, BATCH), st>>>(
         p);
     return cudaGetLastError();
 }
@@ -1127,6 +1148,28 @@ cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nswe
         return launch_tcw<false, true>(p, a.m.nbhd, (a.m.L % kChunk) != 0, items, st);
     return launch_tcw<false, false>(p, a.m.nbhd, (a.m.L % kChunk) != 0,
                              (long long)p.tiles_x * p.tiles_y * nsweeps, st);
+}
+
+cudaError_t launch_gibbs_tc(const SweepArgs &a, uint8_t *x, int nsweeps, unsigned int *done,
+                            unsigned int *grab, int *err, cudaStream_t st)
+{
+    if (!pca_tc_eligible(a.m) || a.m.nbhd != 4)
+        return cudaErrorInvalidValue;
+    TcParams p{};
+    p.a = a;
+    p.x0 = x;
+    p.x1 = x;
+    p.tiles_x = (a.W + 31) / 32;
+    p.tiles_y = (a.H + kGibbsRows - 1) / kGibbsRows;
+    p.nsweeps = 2 * nsweeps;   // colour phases
+    p.T = a.m.T;
+    p.nc_max = (a.m.L + kChunk - 1) / kChunk;
+    p.done = done;
+    p.grab = grab;
+    p.err = err;
+    const long long items = (long long)p.tiles_x * p.tiles_y * p.nsweeps;
+    return (a.m.L % kChunk) != 0 ? launch_tcw_t<4, true, false, false, true>(p, items, st)
+                                 : launch_tcw_t<4, false, false, false, true>(p, items, st);
 }
 
 cudaError_t launch_batch_tc(const SlotDesc *slots, const uint32_t *t_arr,

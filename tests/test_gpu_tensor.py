@@ -7,7 +7,7 @@ neighbourhoods, Potts (T = 1), a negative (repulsive) prior coefficient
 truncation, sharp
 edges (neighbours outside a site's 64-label histogram window), images with
 more tiles than the persistent grid, and per-sweep launches under energy
-tracking."""
+tracking; and the checkerboard Gibbs sweep on the same kernel."""
 import numpy as np
 import pytest
 
@@ -132,10 +132,11 @@ def test_set_kernel_rejects(pc):
             with pytest.raises(pc.PcadError):
                 ch.set_kernel(pc.PCAD_KERNEL_TENSOR)
             ch.run(3)                                  # the CUDA-core kernel
-    gibbs = Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
-    with pc.Chain(_grey(14, 20, 20, 256, 20.0), gibbs, seed=1) as ch:
-        with pytest.raises(pc.PcadError):
+    gibbs8 = Model(L=256, nbhd=8, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
+    with pc.Chain(_grey(14, 20, 20, 256, 20.0), gibbs8, seed=1) as ch:
+        with pytest.raises(pc.PcadError):   # the Gibbs form covers the 4-neighbourhood only
             ch.set_kernel(pc.PCAD_KERNEL_TENSOR)
+        assert ch.kernel_in_use() == pc.PCAD_KERNEL_CUDA_CORE
 
 
 def test_tensor_per_sweep_launches_under_energy_tracking(pc):
@@ -152,3 +153,65 @@ def test_tensor_per_sweep_launches_under_energy_tracking(pc):
     assert np.array_equal(out[0][0], out[1][0])
     np.testing.assert_array_equal(out[0][1], out[1][1])
     assert np.array_equal(out[0][2][0], out[1][2][0]) and out[0][2][1:] == out[1][2][1:]
+
+
+# Checkerboard Gibbs on the tensor-core kernel (4-neighbourhood): colour
+# phases over 8 x 32 tiles, in place; must equal the CUDA-core colour phases
+# and the oracle's colour-order Gibbs sweep bit for bit.
+GIBBS_CASES = [
+    ("L256_37x70", lambda: (_grey(2, 37, 70, 256, 20.0),
+                            Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0,
+                                  sampler=1))),
+    ("L203_odd_41x67", lambda: (_grey(21, 41, 67, 203, 15.0),
+                                Model(L=203, pair=TL, pair_coef=0.06, pair_T=25, sigma=15.0,
+                                      sampler=1))),
+    ("L64_T2_50x97", lambda: (_grey(4, 50, 97, 64, 4.0),
+                              Model(L=64, pair=TL, pair_coef=0.5, pair_T=2, sigma=4.0,
+                                    sampler=1))),
+    ("L128_potts_30x40", lambda: (_grey(7, 30, 40, 128, 6.0),
+                                  Model(L=128, pair=POTTS, pair_coef=1.1, sigma=6.0, sampler=1))),
+    ("L256_edges_64x96", lambda: (_edges(15, 64, 96),
+                                  Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=12.0,
+                                        sampler=1))),
+    ("L256_1x33", lambda: (_grey(22, 1, 33, 256, 20.0),
+                           Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0,
+                                 sampler=1))),
+    ("L256_300x257", lambda: (_grey(10, 300, 257, 256, 20.0),
+                              Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0,
+                                    sampler=1))),
+]
+
+
+@pytest.mark.parametrize("name,make", GIBBS_CASES, ids=[c[0] for c in GIBBS_CASES])
+def test_tensor_gibbs_equals_cuda_core(pc, name, make):
+    g, m = make()
+    x_ref, m_ref, _ = _run(pc, g, m, pc.PCAD_KERNEL_CUDA_CORE)
+    x_tc, m_tc, _ = _run(pc, g, m, pc.PCAD_KERNEL_TENSOR)
+    assert np.array_equal(x_tc, x_ref)
+    assert np.array_equal(m_tc, m_ref)
+
+
+def test_tensor_gibbs_matches_oracle_and_auto(pc):
+    g = _grey(23, 29, 51, 256, 20.0)
+    m = Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
+    with pc.Chain(g, m, seed=9, chain_id=2, burn_in=3) as ch:
+        assert ch.kernel_in_use() == pc.PCAD_KERNEL_TENSOR   # AUTO: L >= 192
+        ch.run(12)
+        xg, mg = ch.sample(), ch.mean()
+    x, acc, nacc, _ = oracle.run_chain(m, g, 12, 3, seed=9, chain=2, sampler=1,
+                                       order=oracle.ORDER_COLOUR)
+    assert np.array_equal(xg, x)
+    np.testing.assert_allclose(mg, acc / nacc, rtol=1e-6, atol=0)
+
+
+def test_tensor_gibbs_under_energy_tracking(pc):
+    g, m = GIBBS_CASES[0][1]()
+    out = []
+    for kind in (pc.PCAD_KERNEL_CUDA_CORE, pc.PCAD_KERNEL_TENSOR):
+        with pc.Chain(g, m, seed=3, chain_id=2, burn_in=4) as ch:
+            ch.set_kernel(kind).track_energy(30)
+            ch.run(17)
+            out.append((ch.sample(), ch.energies(), ch.mean()))
+    assert np.array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert np.array_equal(out[0][2], out[1][2])
