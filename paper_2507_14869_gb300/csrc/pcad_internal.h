@@ -48,7 +48,7 @@ __device__ __forceinline__ bool accumulate_after(const SweepArgs &a, uint32_t t)
 // L2_ONLY: the labels may have been written by other SMs during the same
 // launch, so they are read through L2 (ld.global.cg), never from a possibly
 // stale L1 line.
-template <int NB, bool L2_ONLY = false>
+template <int NB, bool L2_ONLY = false, bool UNIFORM = true>
 __device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__restrict__ x, int r,
                                           int c, uint32_t tag, uint32_t t, SiteIn<NB> &in)
 {
@@ -65,7 +65,8 @@ __device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__r
     const size_t idx = (size_t)r * a.pitch + c;
     in.xi = ld(idx);
     in.g = a.g[idx];
-    in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
+    if constexpr (UNIFORM)
+        in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
 }
 
 // *counter += n (one thread).

@@ -45,12 +45,19 @@ __device__ __forceinline__ int draw_site(const SweepArgs &a, bool valid, const S
 // L2_ONLY: labels and accumulator written by other SMs in the same launch
 // are read through L2 (the wavefront kernel).
 template <int NC, int NB, int NORM = 0, bool L2_ONLY = false>
-__device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint32_t t, float *Gcol)
+__device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint32_t t, float *Gcol,
+                                         const uint32_t *u_s = nullptr)
 {
     const bool valid = r < a.H && c < a.W;
     SiteIn<NB> in{};
-    if (valid)
-        load_site<NB, L2_ONLY>(a, a.xin, r, c, kTagPCA, t, in);
+    if (valid) {
+        if (u_s) {
+            load_site<NB, L2_ONLY, false>(a, a.xin, r, c, kTagPCA, t, in);
+            in.ub = *u_s;
+        } else {
+            load_site<NB, L2_ONLY>(a, a.xin, r, c, kTagPCA, t, in);
+        }
+    }
     const int s = draw_site<NC, NB, NORM>(a, valid, in, Gcol);
     if (valid) {
         a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
@@ -61,14 +68,35 @@ __device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint3
     }
 }
 
+
+// The uniforms of a 4 x 32 block of sites (rows r0.., columns c0.., c0 a
+// multiple of 4): lane l of the calling warp computes the Philox block of row
+// r0 + l / 8, columns c0 + 4 (l % 8) .. + 3 (one call serves 4 sites) into
+// u_s[32 * (l / 8) + 4 (l % 8) ..], i.e. u_s[32 * row + column].
+__device__ __forceinline__ void block_uniforms(const SweepArgs &a, int r0, int c0, uint32_t t,
+                                               uint32_t *u_s)
+{
+    const int l = (int)(threadIdx.x & 31);
+    uint32_t o0, o1, o2, o3;
+    philox4x32_10((uint32_t)((c0 >> 2) + (l & 7)), (uint32_t)(r0 + (l >> 3)), t,
+                  (kTagPCA << 24) | (a.chain & 0xFFFFFFu), (uint32_t)(a.seed & 0xFFFFFFFFull),
+                  (uint32_t)(a.seed >> 32), o0, o1, o2, o3);
+    reinterpret_cast<uint4 *>(u_s)[l] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
+}
+
 template <int NC, int NB, int NORM>
 __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 {
     __shared__ float G_s[NC * kThreads];
+    __shared__ __align__(16) uint32_t U_s[kBY * kBX];
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const int c = blockIdx.x * kBX + threadIdx.x;
     const int r = blockIdx.y * kBY + threadIdx.y;
-    pca_site<NC, NB, NORM>(a, r, c, sweep_index(a), G_s + tid);
+    const uint32_t t = sweep_index(a);
+    if (threadIdx.y == 0)
+        block_uniforms(a, blockIdx.y * kBY, blockIdx.x * kBX, t, U_s);
+    __syncthreads();
+    pca_site<NC, NB, NORM>(a, r, c, t, G_s + tid, U_s + tid);
 }
 
 // Wavefront lazy-PCA over nsweeps sweeps in one persistent launch.  Work
@@ -103,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
                                                            unsigned int *grab, int *err)
 {
     __shared__ float G_s[NC * kThreads];
+    __shared__ __align__(16) uint32_t U_s[kBY * kBX];
     __shared__ unsigned int s_next;
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
@@ -142,13 +171,15 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
             if (!ok)
                 atomicExch(err, 1);
             __syncwarp();
+        } else if (threadIdx.y == 1) {
+            block_uniforms(a, ty * kBY, tx * kBX, t0 + (uint32_t)k, U_s);
         }
         __syncthreads();
         SweepArgs b = a;
         b.xin = (k & 1) ? x1 : x0;
         b.xout = (k & 1) ? x0 : x1;
         pca_site<NC, NB, 0, true>(b, ty * kBY + threadIdx.y, tx * kBX + threadIdx.x,
-                                  t0 + (uint32_t)k, G_s + tid);
+                                  t0 + (uint32_t)k, G_s + tid, U_s + tid);
         __syncthreads();
         if (tid == 0) {
             __threadfence();   // the tile's labels and sums before its counter
@@ -217,29 +248,44 @@ __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, i
 // inlined so each variant keeps the single-chain kernel's register budget.
 // L2_ONLY: the wavefront variant (labels of other tiles written in the same
 // launch).
+constexpr int kGroupRows = 4 * kBY;   // rows whose uniforms one pass computes (u_s size)
+
 template <int NC, int NB, bool L2_ONLY>
 __device__ __noinline__ void batch_tile(const SweepArgs *sa, int row0, int col0, int rows,
-                                        uint32_t t, float *Gcol)
+                                        uint32_t t, float *Gcol, uint32_t *u_s)
 {
     const SweepArgs &a = *sa;
     const int c = col0 + (int)threadIdx.x;
-    for (int rr = 0; rr < rows; rr += kBY)
-        pca_site<NC, NB, 0, L2_ONLY>(a, row0 + rr + (int)threadIdx.y, c, t, Gcol);
+    const int tid = (int)threadIdx.y * kBX + (int)threadIdx.x;
+    // per 16 rows: the uniforms first, warp w the Philox blocks of rows
+    // 4w .. 4w + 3 (col0 a multiple of 32; one call per 4 sites), then the
+    // sites; every thread of the block takes every barrier
+    for (int rb = 0; rb < rows; rb += kGroupRows) {
+        if (rb + (int)threadIdx.y * kBY < rows)
+            block_uniforms(a, row0 + rb + (int)threadIdx.y * kBY, col0, t,
+                           u_s + threadIdx.y * kBY * kBX);
+        __syncthreads();
+        const int re = min(rows, rb + kGroupRows);
+        for (int rr = rb; rr < re; rr += kBY)
+            pca_site<NC, NB, 0, L2_ONLY>(a, row0 + rr + (int)threadIdx.y, c, t, Gcol,
+                                         u_s + (rr - rb) * kBX + tid);
+        __syncthreads();   // u_s is free again
+    }
 }
 
 template <int NB, bool L2_ONLY = false>
 __device__ __forceinline__ void batch_dispatch(const SweepArgs *sa, int ncls, int row0, int col0,
-                                               int rows, uint32_t t, float *Gcol)
+                                               int rows, uint32_t t, float *Gcol, uint32_t *u_s)
 {
     switch (ncls) {
-    case 1: batch_tile<1, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    case 2: batch_tile<2, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    case 3: batch_tile<3, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    case 4: batch_tile<4, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    case 5: batch_tile<5, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    case 8: batch_tile<8, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    case 16: batch_tile<16, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
-    default: batch_tile<32, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol); break;
+    case 1: batch_tile<1, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    case 2: batch_tile<2, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    case 3: batch_tile<3, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    case 4: batch_tile<4, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    case 5: batch_tile<5, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    case 8: batch_tile<8, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    case 16: batch_tile<16, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
+    default: batch_tile<32, NB, L2_ONLY>(sa, row0, col0, rows, t, Gcol, u_s); break;
     }
 }
 
@@ -250,6 +296,7 @@ __global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *
                                                              uint32_t sweep_off)
 {
     __shared__ float G_s[32 * kThreads];
+    __shared__ __align__(16) uint32_t U_s[kGroupRows * kBX];   // uniforms of 16 tile rows
     __shared__ int s_item;
     __shared__ uint32_t s_t;
     __shared__ int s_go;
@@ -279,9 +326,9 @@ __global__ void __launch_bounds__(kThreads, 8) batch_pca_kernel(const SlotDesc *
         const WorkItem w = items[s_item];
         const int ncls = s_args.last_phase;
         if (s_args.sweep_off == 8u)
-            batch_dispatch<8>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid);
+            batch_dispatch<8>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid, U_s);
         else
-            batch_dispatch<4>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid);
+            batch_dispatch<4>(&s_args, ncls, w.row0, w.col0, w.rows, s_t, G_s + tid, U_s);
     }
 }
 
@@ -299,6 +346,7 @@ __global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
     unsigned int *grab, int *err)
 {
     __shared__ float G_s[32 * kThreads];
+    __shared__ __align__(16) uint32_t U_s[kGroupRows * kBX];   // uniforms of 16 tile rows
     __shared__ unsigned int s_next;
     __shared__ int s_go;
     __shared__ uint32_t s_t;
@@ -360,10 +408,10 @@ __global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
             const int rows = min(gm.rows, (s_args.H - row0 + kBY - 1) / kBY * kBY);
             if (s_args.sweep_off == 8u)
                 batch_dispatch<8, true>(&s_args, s_args.last_phase, row0, tx * kBX, rows, s_t,
-                                        G_s + tid);
+                                        G_s + tid, U_s);
             else
                 batch_dispatch<4, true>(&s_args, s_args.last_phase, row0, tx * kBX, rows, s_t,
-                                        G_s + tid);
+                                        G_s + tid, U_s);
             __syncthreads();
             if (tid == 0) {
                 __threadfence();   // the tile's labels and sums before its counter

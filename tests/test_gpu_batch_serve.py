@@ -70,7 +70,7 @@ def test_batch_is_bit_identical_to_chains_alone(pc, autotune):
         pc.pcad_batch_destroy(b)
 
 
-@pytest.mark.parametrize("rows,order", [(4, 2), (8, 2), (12, 2), (16, 0), (8, 1)])
+@pytest.mark.parametrize("rows,order", [(4, 2), (8, 2), (12, 2), (16, 0), (8, 1), (24, 2), (64, 0)])
 def test_batch_tilings_are_bit_identical(pc, rows, order):
     """Every tiling, the wavefront included, gives each chain's own result; a
     run length that is not a multiple of 16 ends inside a wavefront slice."""
