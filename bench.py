@@ -42,7 +42,7 @@ SFU_PEAK_T = 152 * 32 * 2.070e9 / 1e12
 # from the ncu capture in profiles/pca_direct_l256_1024sq.md (6.33 MB over
 # 1024^2 sites), scaled by the sites of a 512^2 launch.  Set to None when the
 # kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_SITE = 6.326272e6 / (1024 * 1024)
+NCU_DRAM_BYTES_PER_SITE = 6.326784e6 / (1024 * 1024)
 NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scaled by sites; "
                     "the working set is L2-resident, so DRAM traffic is below the 3-11 B/site "
                     "the sweep touches")
@@ -54,7 +54,7 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
 NCU_TC_DRAM_BYTES_PER_SITE = (1.637888e6 + 0.122880e6) / (32 * 512 * 512)
 NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
                        "161-192 of a chain), per site-update: the chain's planes stay in L2")
-NCU_WAVE_DRAM_BYTES_PER_SITE = (6.371584e6 + 0.745728e6) / (32 * 1024 * 1024)
+NCU_WAVE_DRAM_BYTES_PER_SITE = (6.372096e6 + 0.761856e6) / (32 * 1024 * 1024)
 NCU_WAVE_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 1024^2 L=256, per "
                          "site-update, scaled to one 512^2 sweep (profiles/pca_wave_l256_1024sq.md)")
 
