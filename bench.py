@@ -744,7 +744,7 @@ def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0
                   sigma=sig, inertia=2.0, sampler=sampler)
     with pc.Chain(noisy, m, seed=1, chain_id=0, burn_in=0) as ch:
         ch.set_blocking(blocking)
-        if sampler == 0:
+        if sampler == 0 or kernel != "auto":
             ch.set_kernel(KERNEL_KINDS[kernel])
         ch.run(sweeps)
         ch.sync()

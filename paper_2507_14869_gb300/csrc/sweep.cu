@@ -199,6 +199,7 @@ template <int NC, int NB>
 __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, int q)
 {
     __shared__ float G_s[NC * kThreads];
+    __shared__ __align__(16) uint32_t U_s[kBY * 2 * kBX];   // 4 site rows x 64 columns
     const int tid = threadIdx.y * kBX + threadIdx.x;
     const int cx = blockIdx.x * kBX + threadIdx.x;
     const int cy = blockIdx.y * kBY + threadIdx.y;
@@ -218,9 +219,26 @@ __global__ void __launch_bounds__(kThreads) gibbs_cb_kernel(const SweepArgs a, i
     const bool cell = r0 < a.H && c0 < a.W;
     const bool valid = cell && r < a.H && c < a.W;
     const uint32_t t = sweep_index(a);
+    // The block's phase sites lie in 4 rows (one per threadIdx.y) and 64
+    // columns: 64 Philox blocks (one per 4 columns), computed by warps 0 and 1
+    // (warp w, lane l: row (32 w + l) / 16, columns 4 ((32 w + l) % 16) ..).
+    if (threadIdx.y < 2) {
+        const int i = (int)threadIdx.y * 32 + (int)threadIdx.x;
+        const int ri = i >> 4;
+        const int row = NB == 4 ? (int)blockIdx.y * kBY + ri
+                                : 2 * ((int)blockIdx.y * kBY + ri) + (q >> 1);
+        uint32_t o0, o1, o2, o3;
+        philox4x32_10((uint32_t)(16 * (int)blockIdx.x + (i & 15)), (uint32_t)row, t,
+                      (kTagGibbs << 24) | (a.chain & 0xFFFFFFu),
+                      (uint32_t)(a.seed & 0xFFFFFFFFull), (uint32_t)(a.seed >> 32), o0, o1, o2, o3);
+        reinterpret_cast<uint4 *>(U_s)[i] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
+    }
+    __syncthreads();
     SiteIn<NB> in{};
-    if (valid)
-        load_site<NB>(a, x, r, c, kTagGibbs, t, in);
+    if (valid) {
+        load_site<NB, false, false>(a, x, r, c, kTagGibbs, t, in);
+        in.ub = U_s[threadIdx.y * 2 * kBX + (c - 2 * kBX * (int)blockIdx.x)];
+    }
     const int s = draw_site<NC, NB>(a, valid, in, G_s + tid);
     if (valid)
         x[(size_t)r * a.pitch + c] = (uint8_t)s;
