@@ -6,7 +6,9 @@
 //   P(s) = sum_j min(|x_j - s|, T) = n T - Pb(s),  Pb(s) = sum_j max(T - |x_j - s|, 0),
 // n the number of neighbours inside the image.  n T is the same for every
 // label of the site and cancels in the normalisation, so the weights are
-// built from Pb: w(s) = 2^(alpha (g - s)^2 + mu Pb(s)), mu = c log2(e).
+// built from Pb: w(s) = 2^(alpha (g - s)^2 + mu Pb(s) + cb), mu = c log2(e),
+// with one offset cb = -mu nbhd T for every label (mu > 0) that keeps both
+// exponent terms non-positive and the per-site certified margin small.
 // Every tent max(T - |x_j - s|, 0) is zero farther than T - 1 from x_j, so
 // Pb lives in a window of labels around the neighbours' labels:
 //
@@ -24,7 +26,8 @@
 //   * outliers: neighbours with x_j - b >= 64 (wide neighbourhoods, image
 //     edges) add their tents on the CUDA cores in both label ranges.
 //   * outside the window Pb is the outliers' part only (zero for most
-//     sites): w(s) = 2^(alpha (g - s)^2), no prior arithmetic.
+//     sites): w(s) = 2^(alpha (g - s)^2 + cb), no prior arithmetic; the
+//     chunk sums come from a table of (observation, chunk).
 //
 // The window is chunk-aligned (8 | 8 m), so every label chunk of the draw is
 // either a window chunk or an outside chunk of the site.  Pass 1 writes the
@@ -38,13 +41,19 @@
 // tile at a time, its histogram operand (16 KB) and 128 TMEM columns, so
 // four tiles are in flight.  A group: loads its sites, writes their
 // histogram rows, one thread issues the 4 MMAs and commits them to the
-// group's mbarrier; while the tensor core runs, the group computes the
-// outside chunks; then it reads the window from TMEM (4 x tcgen05.ld of 32
-// columns), selects, re-draws uncertain draws in FP64 and writes.
+// group's mbarrier; while the tensor core runs, the group reads the
+// outside chunks from the table; then it reads the window from TMEM (up
+// to 4 x tcgen05.ld of 32 columns; two labels per packed FP32x2
+// instruction), selects, re-draws uncertain draws in FP64 with the whole
+// group and writes.
+//
+// The same kernel runs the 4-neighbourhood checkerboard Gibbs sweep (GIBBS):
+// items are colour phases over 8 x 32 tiles, updated in place.
 //
 // Work items (sweep k, tile) are taken in increasing order, sweep-major,
 // from an atomic counter; item (k, tile) waits until the 3 x 3 tiles around
-// it finished sweep k - 1 (done[] counts finished sweeps per tile), so one
+// it finished sweep k - 1 (done[] counts finished sweeps per tile; acquire
+// loads observe them, a release store publishes), so one
 // launch runs many sweeps with no sweep-wide barrier (as the wavefront
 // CUDA-core kernel).  Every item waited on was taken earlier by a resident
 // group, so the waits end; each wait is bounded anyway (error flag), and
