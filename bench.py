@@ -53,10 +53,10 @@ NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scale
 # launch at 1024^2, per site-update).
 NCU_TC_DRAM_BYTES_PER_SITE = (1.637888e6 + 0.122880e6) / (32 * 512 * 512)
 NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
-                       "161-192 of a chain), per site-update: the chain's planes stay in L2")
+                       "161-192 of a chain): the chain's planes stay in L2")
 NCU_WAVE_DRAM_BYTES_PER_SITE = (6.372096e6 + 0.761856e6) / (32 * 1024 * 1024)
-NCU_WAVE_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 1024^2 L=256, per "
-                         "site-update, scaled to one 512^2 sweep (profiles/pca_wave_l256_1024sq.md)")
+NCU_WAVE_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 1024^2 L=256, "
+                         "scaled by sites to a 512^2 launch (profiles/pca_wave_l256_1024sq.md)")
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3}
 
@@ -316,7 +316,9 @@ def run_ours(a):
     per_site = {1: NCU_DRAM_BYTES_PER_SITE, 2: NCU_TC_DRAM_BYTES_PER_SITE,
                 3: NCU_WAVE_DRAM_BYTES_PER_SITE}[in_use]
     note = {1: NCU_TRAFFIC_NOTE, 2: NCU_TC_TRAFFIC_NOTE, 3: NCU_WAVE_TRAFFIC_NOTE}[in_use]
-    traffic = per_site * H * W if per_site else None
+    # per launch, like achieved: 32 sweeps per wavefront launch, one otherwise
+    sweeps_per_launch = 32 if in_use in (2, 3) else 1
+    traffic = per_site * H * W * sweeps_per_launch if per_site else None
     blocks, rest = divmod(SWEEPS, 32)
     # per chain: the 32-sweep graphs (sweep launches + the counter advance) and the rest
     wave = in_use in (2, 3)   # one launch per block of sweeps + the advance
@@ -331,7 +333,13 @@ def run_ours(a):
                    "parallelism": "independent chain per GPU" if world > 1 else "1 GPU"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
                      "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
-                     "traffic": traffic, "traffic_source": note, "kernel": kernel_name,
+                     "traffic": traffic, "traffic_source": note,
+                     "traffic_unit": f"DRAM bytes per launch ({sweeps_per_launch} sweeps of "
+                                     f"{H}x{W})",
+                     # 1 B label + 1 B observation in, 1 B label + 8 B accumulator RMW
+                     # after burn-in per site-update
+                     "algorithmic_bytes_per_launch": 11 * H * W * sweeps_per_launch,
+                     "kernel": kernel_name,
                      "work_per_unit": "one label evaluation (one exponential on the SFU in "
                                       "a direct evaluation), L=256 per site-update; the "
                                       "tensor-core kernel takes the chunk sums outside a "
