@@ -1,6 +1,7 @@
-"""The per-site certified margin of the FP32 draw (tensor-core sweep, and
-CUDA-core sweeps with a non-negative prior coefficient), checked by brute
-force on the CPU.
+"""The certified margins of the FP32 draw, checked by brute force on the CPU:
+the per-site margin (tensor-core sweep, and CUDA-core sweeps with a
+non-negative prior coefficient) and the constant margin the CUDA-core sweeps
+keep for a negative one.
 
 For random sites of several models, the FP32 arithmetic of the window
 weights (2^(alpha (g-s)^2 + mu Pb + cb) with two roundings, ex2 off by up to
@@ -106,14 +107,20 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
     # exact conditional
     mu_e = c_e * LOG2E
     alpha_e = -LOG2E / (2.0 * sig_e ** 2) if model["noise"] == 0 else 0.0
-    R = nbhd * T - Pb if mu_e > 0 else Pb
-    W = np.exp2(alpha_e * q - abs(mu_e) * R)
+    # every label's prior sum, a missing neighbour contributing T (a constant)
+    P_all = np.where(present[:, :, None], np.minimum(np.abs(s[None, None, :] - x[:, :, None]), T),
+                     T).sum(1)
+    W = np.exp2(alpha_e * q - mu_e * P_all - np.max(alpha_e * q - mu_e * P_all, axis=1,
+                                                       keepdims=True))
     dW = np.expm1(lam) * W[np.arange(n), xi]
     Fk = (np.cumsum(W, axis=1) + np.where(s[None, :] >= xi[:, None], dW[:, None], 0.0)) / \
          (W.sum(1) + dW)[:, None]
     err = np.abs(C.astype(f64) / Z.astype(f64)[:, None] - Fk).max(1)
-    eta = mg["kb1"] * (mg["hb"] - np.log2(Z.astype(f64))) + mg["kb0"] + \
-        mg["kbr"] * delta.astype(f64) / Z.astype(f64)
+    if form == "cc" and mg["gam"] > 0:   # c < 0 on the CUDA cores: the constant margin
+        eta = np.full(n, mg["eta"])
+    else:
+        eta = mg["kb1"] * (mg["hb"] - np.log2(Z.astype(f64))) + mg["kb0"] + \
+            mg["kbr"] * delta.astype(f64) / Z.astype(f64)
     return err, eta, Fk
 
 
@@ -129,8 +136,7 @@ MODELS = [
 ]
 
 
-CASES = [(i, "tc") for i in range(len(MODELS))] + \
-    [(i, "cc") for i, m in enumerate(MODELS) if m["pair_coef"] >= 0]
+CASES = [(i, "tc") for i in range(len(MODELS))] + [(i, "cc") for i in range(len(MODELS))]
 
 
 @pytest.mark.parametrize("i,form", CASES, ids=[f"{f}{i}" for i, f in CASES])
