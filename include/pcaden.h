@@ -230,6 +230,27 @@ pcad_status pcad_chain_read_energies(pcad_chain *ch, double *host, int max, int 
 pcad_status pcad_chain_read_min_state(pcad_chain *ch, uint8_t *host_out, int out_pitch,
                                       double *energy, uint64_t *sweep);
 
+/* Failure detection (no counterpart in the paper: the sweep of Section 5.2
+ * needs no waits, but the wavefront, tensor-core and TMA-tiled kernels
+ * that run it wait on one another's tiles, on MMA completion and on tile
+ * loads).  Every such device-side wait is bounded by elapsed time: after
+ * `seconds` (default 1.0; accepted range [1e-4, 60], PCAD_EINVAL outside)
+ * it gives up and sets the chain's error flag, every other wait and work
+ * item of the launch stops as soon as it sees the flag, the kernel returns
+ * and pcad_chain_sync reports PCAD_ETIMEOUT.  The sample and accumulator
+ * are then undefined; pcad_chain_reset clears the flag and restarts the
+ * chain.  Applies to sweeps queued after the call. */
+pcad_status pcad_chain_set_wait_limit(pcad_chain *ch, double seconds);
+
+/* Test aid for the failure path above: with tile >= 0, tile `tile` of the
+ * wavefront CUDA-core kernel's and the tensor-core kernel's grid (4 x 32
+ * sites, row-major; Gibbs: 8 x 32) never reports a finished sweep, so the
+ * tiles around it wait for a dependency that never arrives until their
+ * bounded wait runs out.  tile = -1 (the default) turns it off; PCAD_EINVAL
+ * for tile outside [-1, tiles).  Applies to sweeps queued after the call;
+ * no other kernel is affected. */
+pcad_status pcad_chain_inject_stall(pcad_chain *ch, int tile);
+
 /* Block until the chain's queued work is done. */
 pcad_status pcad_chain_sync(pcad_chain *ch);
 
@@ -388,11 +409,16 @@ void pcad_server_destroy(pcad_server *sv);
  * cuda_stream.  The second label plane, the model tables and the counters
  * live in one 8 MiB array in the library's own device memory, held by every
  * GPU that loads the library until the process exits: pitch * H may not
- * exceed 8,355,840 bytes (PCAD_EINVAL otherwise), and m->sampler must be
- * PCAD_SAMPLER_PCA.  All calls share that array, so calls whose GPU work
- * overlaps (unordered streams) race.  The first call on a device looks up
- * the array's address (make it before any stream capture).  No allocation
- * of any kind is made. */
+ * exceed 8,355,840 bytes, m->sampler must be PCAD_SAMPLER_PCA and the
+ * inertia price the L0 one (inertia_norm 0), and g_dev, sample_dev and
+ * mean_dev must not overlap (PCAD_EINVAL otherwise).  All calls share that
+ * array, so calls whose GPU work overlaps (unordered streams) race.  The
+ * first call on a device looks up the array's address with that device
+ * current and keeps it with the device's context; a call that finds another
+ * context current (after cudaDeviceReset, say) looks it up again.  Make the
+ * first call on a device before any stream capture.  The model tables travel
+ * as a kernel parameter, so the call reads no host memory after it returns.
+ * No allocation of any kind is made. */
 pcad_status pcad_pca_run_noalloc(const uint8_t *g_dev, int H, int W, int pitch,
                                  const pcad_model *m, uint64_t seed, uint32_t chain_id,
                                  int nsweeps, int burn_in, uint8_t *sample_dev,

@@ -101,6 +101,8 @@ def _declare(L):
         "pcad_chain_reset": [vp],
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
         "pcad_chain_set_kernel": [vp, ctypes.c_int],
+        "pcad_chain_set_wait_limit": [vp, ctypes.c_double],
+        "pcad_chain_inject_stall": [vp, ctypes.c_int],
         "pcad_chain_kernel_in_use": [vp, ctypes.POINTER(ctypes.c_int)],
         "pcad_chain_energy": [vp, dp, u64p, u64p],
         "pcad_chain_set_model": [vp, mp],
@@ -380,6 +382,14 @@ class Chain:
         pcad_chain_set_kernel(self.h, kind)
         return self
 
+    def set_wait_limit(self, seconds: float):
+        pcad_chain_set_wait_limit(self.h, seconds)
+        return self
+
+    def inject_stall(self, tile: int):
+        pcad_chain_inject_stall(self.h, tile)
+        return self
+
     def set_model(self, model):
         """New coefficients; the chain's sampler is kept."""
         pcad_chain_set_model(self.h, as_model(model, self.sampler))
@@ -655,3 +665,13 @@ PCAD_KERNEL_WAVE = 3
 def pcad_chain_set_kernel(h, kind: int):
     """Kernel of unblocked PCA sweeps: auto, CUDA cores, or tensor-core prior sums."""
     _check("pcad_chain_set_kernel", lib().pcad_chain_set_kernel(h, int(kind)))
+
+
+def pcad_chain_set_wait_limit(h, seconds: float):
+    """Elapsed-time limit of every bounded device-side wait of the chain's sweeps."""
+    _check("pcad_chain_set_wait_limit", lib().pcad_chain_set_wait_limit(h, float(seconds)))
+
+
+def pcad_chain_inject_stall(h, tile: int):
+    """Test aid: wavefront tile `tile` never reports a finished sweep (-1: off)."""
+    _check("pcad_chain_inject_stall", lib().pcad_chain_inject_stall(h, int(tile)))

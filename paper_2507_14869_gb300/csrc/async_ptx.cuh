@@ -79,13 +79,24 @@ __device__ __forceinline__ bool named_bar_or(int id, int n, bool pred)
     return r != 0;
 }
 
-// Poll until phase `parity` of *bar completes, at most `limit` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, long long limit)
+// Poll until phase `parity` of *bar completes; give up after limit_ns
+// nanoseconds of %globaltimer time.
+__device__ __forceinline__ bool mbar_wait_timed(uint64_t *bar, uint32_t parity, long long limit_ns)
 {
-    for (long long i = 0; i < limit; ++i)
+    if (mbar_try_wait(bar, parity))
+        return true;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    for (unsigned int i = 1;; ++i) {
         if (mbar_try_wait(bar, parity))
             return true;
-    return false;
+        if ((i & 15u) == 0u) {
+            unsigned long long t;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+            if ((long long)(t - t0) > limit_ns)
+                return false;
+        }
+    }
 }
 
 // ------------------------------------------------------------------ TMA

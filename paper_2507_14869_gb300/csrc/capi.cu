@@ -250,6 +250,8 @@ struct pcad_chain {
     CUtensorMap xmap[2];          // TMA descriptors of the two label planes
     CUtensorMap gmap;             // and of the observation
     int *err = nullptr;           // bounded-wait timeout flag (device)
+    long long wait_ns = 0;        // limit of each bounded device wait (0: the default, 1 s)
+    int stall_tile = 0;           // test aid: wavefront tile stall_tile - 1 never publishes
     unsigned long long *esums = nullptr;   // energy reduction sums (device, 2 x u64)
     EnergyCoef ecoef{};
     EnergyTrack track{};          // minimum-energy tracking (trace == nullptr: off)
@@ -274,6 +276,8 @@ SweepArgs make_args(const pcad_chain *ch)
     a.pitch = ch->pitch;
     a.chain = ch->chain_id;
     a.burn_in = ch->burn_in;
+    a.wait_ns = ch->wait_ns;
+    a.stall_tile = ch->stall_tile;
     a.m = ch->dm;
     return a;
 }
@@ -630,6 +634,7 @@ pcad_status pcad_chain_reset(pcad_chain *ch)
                                cudaMemcpyDeviceToDevice, ch->stream));
     CUDA_TRY(cudaMemsetAsync(ch->acc, 0, n * sizeof(float), ch->stream));
     CUDA_TRY(cudaMemsetAsync(ch->tdev, 0, 16, ch->stream));
+    CUDA_TRY(cudaMemsetAsync(ch->err, 0, sizeof(int), ch->stream));
     ch->cur = 0;
     ch->t = 0;
     ch->n_acc = 0;
@@ -861,6 +866,47 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         ch->graph = nullptr;
     }
     ch->kernel = kind;
+    return PCAD_OK;
+}
+
+namespace {
+
+// Captured sweeps hold the launch arguments: rebuild them on next use.
+void drop_graph(pcad_chain *ch)
+{
+    if (ch->graph) {
+        cudaStreamSynchronize(ch->stream);
+        cudaGraphExecDestroy(ch->graph);
+        ch->graph = nullptr;
+    }
+}
+
+}  // namespace
+
+pcad_status pcad_chain_set_wait_limit(pcad_chain *ch, double seconds)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (!(seconds >= 1e-4 && seconds <= 60.0))
+        return fail(PCAD_EINVAL, "wait limit must lie in [1e-4, 60] seconds");
+    const long long ns = (long long)(seconds * 1e9);
+    if (ns != ch->wait_ns) {
+        drop_graph(ch);
+        ch->wait_ns = ns;
+    }
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_inject_stall(pcad_chain *ch, int tile)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (tile < -1 || tile >= ch->wave_tiles)
+        return fail(PCAD_EINVAL, "tile must be -1 (off) or a tile index below %d", ch->wave_tiles);
+    if (tile + 1 != ch->stall_tile) {
+        drop_graph(ch);
+        ch->stall_tile = tile + 1;
+    }
     return PCAD_OK;
 }
 

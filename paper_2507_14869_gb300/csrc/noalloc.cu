@@ -16,9 +16,16 @@
 // the caller's mean buffer) before its sweeps start.
 //
 // The host needs the array's device address: the first call on a device,
-// with that device current, looks it up once with cudaGetSymbolAddress and
-// keeps it (the array's host-side name is only a stand-in, not a device
-// pointer).  Make that first call before any CUDA stream capture.
+// with that device current, looks it up with cudaGetSymbolAddress and keeps
+// it together with the device's current context (the array's host-side
+// name is only a stand-in, not a device pointer).  If that context is later
+// replaced (cudaDeviceReset, or a primary context released and created
+// again, which reloads the module) the next call sees a different context
+// and looks the address up again.  Make the first call on a device before
+// any CUDA stream capture.
+//
+// The model tables reach the device as a kernel parameter, not by a copy
+// from host memory, so no call reads host memory after it returns.
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -31,14 +38,56 @@ constexpr size_t kScratchBytes = 8u << 20;             // 8 MiB
 constexpr size_t kOffCounters = 0;                      // u32 sweep base, u64 FP64 re-draws
 constexpr size_t kOffTa64 = 256;                        // 511 doubles
 constexpr size_t kOffPr64 = kOffTa64 + 4096;            // up to 2041 doubles
+constexpr int kPrMax = 2041;                            // nbhd * T + 1 with T <= 255
 constexpr size_t kOffPlane = 32768;                     // the second label plane
 constexpr size_t kPlaneMax = kScratchBytes - kOffPlane; // 8,355,840 bytes
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
+// The FP64 tables of one call, passed by value (20 KB of kernel parameters).
+struct NoallocTables {
+    double ta64[511];
+    double pr64[kPrMax];
+    int npr;
+};
+
+__global__ void noalloc_tables_kernel(const __grid_constant__ NoallocTables t, double *ta,
+                                      double *pr)
+{
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 511 + t.npr;
+         i += gridDim.x * blockDim.x) {
+        if (i < 511)
+            ta[i] = t.ta64[i];
+        else
+            pr[i - 511] = t.pr64[i - 511];
+    }
+}
+
 std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 unsigned char *g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+
+// The calling thread's current context (nullptr if it cannot be read).
+CUcontext current_context()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS)
+        return nullptr;
+    return c;
+}
 
 pcad_status scratch_address(unsigned char **out)
 {
@@ -48,17 +97,26 @@ pcad_status scratch_address(unsigned char **out)
         return pcad::set_error(PCAD_ECUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices)
         return pcad::set_error(PCAD_EINVAL, "device ordinal beyond 63");
+    const CUcontext ctx = current_context();   // nullptr before the thread's first CUDA work
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || !ctx || ctx != g_scratch_ctx[dev]) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);   // binds the device's context
         if (e != cudaSuccess || !p)
             return pcad::set_error(PCAD_ECUDA, e != cudaSuccess ? cudaGetErrorString(e)
                                                                 : "symbol address is NULL");
         g_scratch_addr[dev] = (unsigned char *)p;
+        g_scratch_ctx[dev] = current_context();
     }
     *out = g_scratch_addr[dev];
     return PCAD_OK;
+}
+
+// [a, a + na) and [b, b + nb) share a byte.
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
 }
 
 #define NA_TRY(call)                                                    \
@@ -94,16 +152,24 @@ extern "C" pcad_status pcad_pca_run_noalloc(const uint8_t *g_dev, int H, int W, 
         return set_error(PCAD_EINVAL, "the allocation-free entry point runs the PCA sampler");
     if (m->inertia_norm != 0 && m->L > 2 && m->inertia > 0.0f)
         return set_error(PCAD_EINVAL, "the allocation-free entry point runs the L0 inertia price");
+    const size_t plane_bytes = (size_t)pitch * (size_t)(H - 1) + (size_t)W;
+    const size_t mean_bytes = (size_t)H * (size_t)W * sizeof(float);
+    if (overlap(g_dev, plane_bytes, sample_dev, plane_bytes) ||
+        overlap(g_dev, plane_bytes, mean_dev, mean_bytes) ||
+        overlap(sample_dev, plane_bytes, mean_dev, mean_bytes))
+        return set_error(PCAD_EINVAL, "g_dev, sample_dev and mean_dev must not overlap");
     const uint64_t n_acc = nsweeps > burn_in ? (uint64_t)(nsweeps - burn_in) : 0;
     if ((uint64_t)(m->L - 1) * n_acc >= (1ull << 24))
         return set_error(PCAD_EINVAL, "accumulator would leave the exact FP32 range");
 
-    double ta64[511];
+    NoallocTables tabs{};
     std::vector<double> pr64;
     DevModel dm{};
-    model_tables(*m, ta64, pr64, dm);
-    if (pr64.size() * sizeof(double) > kOffPlane - kOffPr64)
+    model_tables(*m, tabs.ta64, pr64, dm);
+    if (pr64.size() > (size_t)kPrMax)
         return set_error(PCAD_EINVAL, "prior table exceeds its scratch slot");
+    std::memcpy(tabs.pr64, pr64.data(), pr64.size() * sizeof(double));
+    tabs.npr = (int)pr64.size();
 
     unsigned char *scr = nullptr;
     st = scratch_address(&scr);
@@ -117,9 +183,9 @@ extern "C" pcad_status pcad_pca_run_noalloc(const uint8_t *g_dev, int H, int W, 
     uint8_t *planes[2] = {sample_dev, (uint8_t *)(scr + kOffPlane)};
 
     NA_TRY(cudaMemsetAsync(scr + kOffCounters, 0, 16, s));
-    NA_TRY(cudaMemcpyAsync(scr + kOffTa64, ta64, sizeof(ta64), cudaMemcpyHostToDevice, s));
-    NA_TRY(cudaMemcpyAsync(scr + kOffPr64, pr64.data(), pr64.size() * sizeof(double),
-                           cudaMemcpyHostToDevice, s));
+    noalloc_tables_kernel<<<4, 256, 0, s>>>(tabs, (double *)(scr + kOffTa64),
+                                           (double *)(scr + kOffPr64));
+    NA_TRY(cudaGetLastError());
     NA_TRY(cudaMemsetAsync(mean_dev, 0, (size_t)H * W * sizeof(float), s));
     NA_TRY(cudaMemcpy2DAsync(sample_dev, pitch, g_dev, pitch, W, H, cudaMemcpyDeviceToDevice, s));
 

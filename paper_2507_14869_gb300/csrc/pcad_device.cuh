@@ -61,6 +61,61 @@ struct DevModel {
     double el64;         // e^lambda, FP64
 };
 
+// ------------------------------------------------------------ bounded waits
+// Every device-side wait of the library (a wavefront dependency, a TMA tile
+// load, an MMA completion) is bounded by elapsed time, read from the
+// nanosecond %globaltimer, and gives up at once when the launch's error
+// flag is already set.  One lost dependency therefore ends the whole
+// launch within about one limit: the first wait that runs out sets the
+// flag, every other wait and every later item sees it and stops.
+constexpr long long kWaitLimitNs = 1000000000ll;   // default limit: 1 s
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The error flag, read past L1 (another SM may have set it).
+__device__ __forceinline__ int ld_flag(const int *p)
+{
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p)
+{
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// The limit a launch uses: its own (nanoseconds, > 0) or the default.
+__device__ __forceinline__ long long wait_limit(long long ns)
+{
+    return ns > 0 ? ns : kWaitLimitNs;
+}
+
+// Wait until *d >= k (acquire loads); `seen` is an earlier observation of
+// *d.  Returns false if the wait ran out of time or *err was set meanwhile.
+__device__ __forceinline__ bool wait_ge(const unsigned int *d, unsigned int k, unsigned int seen,
+                                        const int *err, long long limit_ns)
+{
+    if (seen >= k)
+        return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (unsigned int i = 1;; ++i) {
+        __nanosleep(64);
+        if (ld_acquire_u32(d) >= k)
+            return true;
+        if ((i & 15u) == 0u &&
+            (ld_flag(err) != 0 || (long long)(globaltimer_ns() - t0) > limit_ns))
+            return false;
+    }
+}
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC 2011): 10 rounds of two 32x32->64-bit
 // multiplications (multipliers 0xD2511F53, 0xCD9E8D57) with a Weyl key

@@ -28,6 +28,8 @@ struct SweepArgs {
     uint32_t chain;
     int burn_in;              // sweeps not accumulated
     int last_phase;           // Gibbs: this phase completes the sweep
+    long long wait_ns;        // limit of each bounded device wait (0: kWaitLimitNs)
+    int stall_tile;           // test aid: wavefront tile stall_tile - 1 never publishes (0: off)
     DevModel m;
 };
 

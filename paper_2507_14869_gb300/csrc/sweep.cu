@@ -110,15 +110,9 @@ __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 // resident capacity), so the waits end; each is bounded anyway (error flag).
 // Draws are keyed by (sweep, site): results equal per-sweep launches.
 // Tile counters are observed with acquire loads: a waiting lane's label
-// reads after the block barrier see what the tile published.
-__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p)
-{
-    unsigned int v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-constexpr long long kWaveSpinLimit = 20000000;
+// reads after the block barrier see what the tile published.  A wait that
+// runs out sets *err; the block then takes no further item, and every other
+// block stops at its next wait or item.
 #ifndef PCAD_WAVE_MIN_BLOCKS
 #define PCAD_WAVE_MIN_BLOCKS 8   // resident blocks per SM the register budget targets
 #endif
@@ -137,6 +131,7 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
     const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
     const unsigned int total = ntiles * (unsigned int)nsweeps;
     const uint32_t t0 = sweep_index(a);
+    const long long limit = wait_limit(a.wait_ns);
     if (tid == 0)
         s_next = atomicAdd(grab, 1u);
     __syncthreads();
@@ -148,24 +143,18 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
         const int tx = j - ty * tiles_x;
         __syncthreads();   // everyone has read s_next
         if (threadIdx.y == 0) {
-            // lane 31 fetches the following item while lanes 0-8 each wait for
-            // one tile of the 3 x 3 neighbourhood to finish sweep k - 1
+            // lane 31 fetches the following item (none once a wait of the
+            // launch gave up) while lanes 0-8 each wait for one tile of the
+            // 3 x 3 neighbourhood to finish sweep k - 1
             if (threadIdx.x == 31)
-                s_next = atomicAdd(grab, 1u);
+                s_next = ld_flag(err) ? total : atomicAdd(grab, 1u);
             bool ok = true;
             if (k > 0 && threadIdx.x < 9) {
                 const int yy = ty + (int)threadIdx.x / 3 - 1;
                 const int xx = tx + (int)threadIdx.x % 3 - 1;
                 if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
                     const unsigned int *d = done + (size_t)yy * tiles_x + xx;
-                    long long spins = 0;
-                    while (ld_acquire_gpu(d) < (unsigned int)k) {
-                        if (++spins > kWaveSpinLimit) {
-                            ok = false;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
+                    ok = wait_ge(d, (unsigned int)k, ld_acquire_u32(d), err, limit);
                 }
             }
             if (!ok)
@@ -181,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, PCAD_WAVE_MIN_BLOCKS) pca_wave_kerne
         pca_site<NC, NB, 0, true>(b, ty * kBY + threadIdx.y, tx * kBX + threadIdx.x,
                                   t0 + (uint32_t)k, G_s + tid, U_s + tid);
         __syncthreads();
-        if (tid == 0) {
+        if (tid == 0 && j != a.stall_tile - 1) {
             __threadfence();   // the tile's labels and sums before its counter
             atomicExch(done + j, (unsigned int)(k + 1));
         }
@@ -383,8 +372,8 @@ __global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
         const int tx = w.tile - ty * gm.tiles_x;
         __syncthreads();   // everyone has read s_next and is done with s_args
         if (threadIdx.y == 0) {
-            if (threadIdx.x == 31)
-                s_next = atomicAdd(grab, 1u);
+            if (threadIdx.x == 31)   // no further item once a wait gave up
+                s_next = ld_flag(err) ? total : atomicAdd(grab, 1u);
             const SlotDesc &d = slots[w.slot];
             uint32_t t = 0;
             int go = 0;
@@ -399,14 +388,7 @@ __global__ void __launch_bounds__(kThreads, 8) batch_wave_kernel(
                 const int xx = tx + (int)threadIdx.x % 3 - 1;
                 if (yy >= 0 && yy < gm.tiles_y && xx >= 0 && xx < gm.tiles_x) {
                     const unsigned int *c = done + gm.base + yy * gm.tiles_x + xx;
-                    long long spins = 0;
-                    while (ld_acquire_gpu(c) < (unsigned int)k) {
-                        if (++spins > kWaveSpinLimit) {
-                            ok = false;
-                            break;
-                        }
-                        __nanosleep(64);
-                    }
+                    ok = wait_ge(c, (unsigned int)k, ld_acquire_u32(c), err, kWaitLimitNs);
                 }
             }
             if (!ok)

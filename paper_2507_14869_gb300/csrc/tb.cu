@@ -28,7 +28,6 @@ constexpr int kBoxH = 48;          // loaded rows
 constexpr int kOutW = 64;          // output columns
 constexpr int kColOff = 16;        // output column offset inside the box
 constexpr int kPlane = kBoxW * kBoxH;
-constexpr long long kSpinLimit = 20000000;   // ~1 s of polling
 
 // Inputs of site (lr, lc) of the box from the shared planes; neighbours
 // outside the image are "missing" (label 1024).
@@ -89,18 +88,14 @@ __global__ void __launch_bounds__(kTbThreads)
         tma_load_2d(xs[0], &xmap, bx, by, &bar);
         tma_load_2d(gs, &gmap, bx, by, &bar);
     }
-    bool ok = true;
-    for (long long spins = 0; !mbar_try_wait(&bar, 0u);) {
-        if (++spins > kSpinLimit) {
-            ok = false;
-            break;
-        }
-    }
+    const long long limit = wait_limit(a.wait_ns);
+    const bool ok = mbar_wait_timed(&bar, 0u, limit);
     if (!__syncthreads_and(ok)) {
+        // the copies may still land: wait for them (bounded again) before the
+        // block's shared memory is released
         if (tid == 0)
             atomicExch(err, 1);
-        for (long long spins = 0; !mbar_try_wait(&bar, 0u) && spins < kSpinLimit; ++spins) {
-        }
+        mbar_wait_timed(&bar, 0u, limit);
         return;
     }
 

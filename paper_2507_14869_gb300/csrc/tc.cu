@@ -77,7 +77,6 @@ constexpr int kBins = 64;                   // histogram bins = MMA K (4 steps o
 constexpr int kWinChunks = kWin / kChunk;   // 16
 constexpr int kOpBytes = kSites * kBins * 2;   // 16 KB: one operand (128 rows x 128 bytes)
 constexpr int kTmemCols = kGroups * kWin;   // 512
-constexpr long long kTcSpinLimit = 20000000;
 constexpr uint32_t kIdesc = idesc_f16_f32(kSites, kWin);
 constexpr float kNoLabel = -4096.0f;        // unused outlier slot: its tent is zero everywhere
 
@@ -392,23 +391,11 @@ __device__ __forceinline__ const unsigned int *dep_counter(const unsigned int *d
 // Every observation is an acquire load, so the labels read after the
 // group's next barrier are those the tile published (the publisher's
 // release store) without a fence on this path.  Returns false if the wait
-// gave up.
+// ran out of time or another wait of the launch already gave up.
 __device__ __forceinline__ bool wait_counter(const unsigned int *d, unsigned int k,
-                                             unsigned int seen)
+                                             unsigned int seen, const int *err, long long limit)
 {
-    bool ok = true;
-    if (d) {
-        long long spins = 0;
-        while (seen < k) {
-            if (++spins > kTcSpinLimit) {
-                ok = false;
-                break;
-            }
-            __nanosleep(64);
-            seen = ld_acquire_gpu(d);
-        }
-    }
-    return ok;
+    return d == nullptr || wait_ge(d, k, seen, err, limit);
 }
 
 // Launch parameters.  One chain (BATCH false): a, the planes and the tile
@@ -431,6 +418,7 @@ struct TcParams {
     int nc_max;          // largest chunk count of the launch's chains
     unsigned int *done, *grab;
     int *err;
+    long long wait_ns;   // limit of each bounded wait (0: kWaitLimitNs)
 };
 
 // One work item: sweep k of `tile` (of a tiles_x x tiles_y grid whose
@@ -506,7 +494,7 @@ __device__ __forceinline__ void tc_wait_item(const TcParams &p, const TcItem &ii
     const unsigned int *d =
         dep_counter(p.done + ii.base, ii.k, ii.tile, ii.tiles_x, ii.tiles_y, lane);
     const unsigned int seen = (d && d == pre_d) ? pre : (d ? ld_acquire_gpu(d) : 0u);
-    if (!wait_counter(d, (unsigned int)ii.k, seen))
+    if (!wait_counter(d, (unsigned int)ii.k, seen, p.err, wait_limit(p.wait_ns)))
         atomicExch(p.err, 1);
 }
 
@@ -707,6 +695,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
         (unsigned int)(BATCH ? p.n_items : p.tiles_x * p.tiles_y) * (unsigned int)p.nsweeps;
     const uint32_t t0 = BATCH ? 0u : sweep_index(p.a);
     const uint32_t tlim = BUDGET ? *p.budget : 0xFFFFFFFFu;   // one chain
+    const long long limit = wait_limit(p.wait_ns);
 
     uint32_t prev_off[NB];   // A entries this thread set for its previous item
 #pragma unroll
@@ -878,7 +867,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
             }
 
             // window chunks from TMEM
-            if (!mbar_wait_bounded(&mbar[grp], (uint32_t)(uses & 1), kTcSpinLimit)) {
+            if (!mbar_wait_timed(&mbar[grp], (uint32_t)(uses & 1), limit)) {
                 atomicExch(p.err, 1);
                 ok = false;
             }
@@ -1007,11 +996,12 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
         // publish the tile's sweep (every output written), take the next item
         // warp 1 publishes (its release store waits for the tile's writes to
         // drain) while warp 0 takes the next item
-        if (q == 1 && lane == 0 && go)   // after every output of the tile
+        if (q == 1 && lane == 0 && go &&   // after every output of the tile
+            (BATCH || ii.tile != p.a.stall_tile - 1))
             st_release_gpu(p.done + ii.base + ii.tile, (unsigned int)(k + 1));
         if (q == 0) {
-            if (lane == 0)
-                s_item[grp] = next;
+            if (lane == 0)   // no further item once a wait of the launch gave up
+                s_item[grp] = ld_flag(p.err) ? total : next;
             const unsigned int nx = __shfl_sync(0xFFFFFFFFu, next, 0);
             if (nx < total) {
                 if constexpr (BATCH) {
@@ -1027,7 +1017,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
                         tc_wait_item<BATCH>(p, in2, lane, dnext, seen);
                 } else if (knext >= 0) {   // looked at during this item
                     if (!BUDGET || t0 + (uint32_t)knext < tlim)
-                        if (!wait_counter(dnext, (unsigned int)knext, seen))
+                        if (!wait_counter(dnext, (unsigned int)knext, seen, p.err, limit))
                             atomicExch(p.err, 1);
                 } else {
                     const TcItem in2 = tc_decode<BATCH>(p, nx);
@@ -1044,7 +1034,7 @@ __global__ void __launch_bounds__(kThr, 1) pca_tcw_kernel(const TcParams p)
     // a timed-out wait may leave an MMA in flight: wait for it (bounded)
     // before TMEM is freed
     if (!ok && lt == 0 && uses > 0)
-        mbar_wait_bounded(&mbar[grp], (uint32_t)((uses - 1) & 1), kTcSpinLimit);
+        mbar_wait_timed(&mbar[grp], (uint32_t)((uses - 1) & 1), limit);
     tc_fence_before_sync();
     __syncthreads();
     if (tid < 32) {
@@ -1152,6 +1142,7 @@ cudaError_t launch_pca_tc(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int nswe
     p.done = done;
     p.grab = grab;
     p.err = err;
+    p.wait_ns = a.wait_ns;
     const long long items = (long long)p.tiles_x * p.tiles_y * nsweeps;
     if (budget)
         return launch_tcw<false, true>(p, a.m.nbhd, (a.m.L % kChunk) != 0, items, st);
@@ -1176,6 +1167,7 @@ cudaError_t launch_gibbs_tc(const SweepArgs &a, uint8_t *x, int nsweeps, unsigne
     p.done = done;
     p.grab = grab;
     p.err = err;
+    p.wait_ns = a.wait_ns;
     const long long items = (long long)p.tiles_x * p.tiles_y * p.nsweeps;
     return (a.m.L % kChunk) != 0 ? launch_tcw_t<4, true, false, false, true>(p, items, st)
                                  : launch_tcw_t<4, false, false, false, true>(p, items, st);
