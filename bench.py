@@ -1,20 +1,28 @@
-"""Benchmark: lazy-PCA denoising chain on one GB300 (plus Gibbs on the same GPU).
+"""Benchmark: lazy-PCA denoising on one GB300, against its roofline, with
+checkerboard Gibbs on the same GPU, a batched and a served form.
 
-Workload (one "step"): the greyscale 512x512 chain with L = 256 labels --
-smooth gradients plus 20 rectangles/disks, additive Gaussian noise sigma = 20
-(clipped, rounded), truncated-linear prior c_T = 0.05, T = 30 on the
-4-neighbourhood, inertia lambda = 2.0; 2000 lazy-PCA sweeps from the
-observation with burn-in 500 and the FP32 posterior-mean accumulator.
-Synthetic, seeded inputs (the paper's images are not public).
+Headline workload (one "step"): the large single image of the roofline
+run -- 8192 x 8192, L = 256 labels (uint8), smooth gradients plus 20
+rectangles/disks, additive Gaussian noise sigma = 25 (label units, clipped,
+rounded), truncated-linear prior c_T = 0.05, T = 30 on the 4-neighbourhood,
+inertia lambda = 2.0 -- 200 lazy-PCA sweeps from the observation with
+burn-in 50 and the FP32 posterior-mean accumulator.  Synthetic, seeded
+inputs (the paper's images are not public).
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
 Prints one JSON line.  `value` is site-updates/s with the inputs resident in
 HBM (CUDA events on the chain's stream, L2 flushed between steps); `e2e` is
 the same metric through the public C ABI with host buffers (create from
-pinned host memory, run, read the mean back).  `--impl reference` times the
-FP64 CPU oracle on the host cores on bounded samples of the same workload.
-Under torchrun each rank runs its own independent chain (weak scaling).
+pinned host memory, run, read the mean back).  Beside it, each measured
+once or twice: the same image at L = 16 and with k = 4 / 8 sweeps per
+TMA-tiled launch (`config3`), checkerboard Gibbs on the same image
+(`gibbs`), the 512 x 512 L = 256 chain of 2000 sweeps (`greyscale512`),
+128 uneven images x 4 chains in one batch against one chain per launch
+(`batch`), a Poisson request stream through the continuous-batching server
+against one request at a time (`serve`), and the FP64 oracle on the host
+cores (`cpu_baseline`).  `--impl reference` times the oracle alone.  Under
+torchrun each rank runs its own independent chain (weak scaling).
 """
 from __future__ import annotations
 
@@ -32,33 +40,36 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-SWEEPS = 2000
-BURN_IN = 500
-WORKLOAD = ("greyscale 512x512, L=256 (uint8), Gaussian sigma=20, truncated-linear "
-            "c_T=0.05 T=30 4-nbhd, lambda=2.0, 2000 sweeps, burn-in 500, FP32 posterior mean")
+SIDE, LABELS, SWEEPS, BURN_IN = 8192, 256, 200, 50
+WORKLOAD = ("large single image 8192x8192, L=256 (uint8), Gaussian sigma=25, truncated-linear "
+            "c_T=0.05 T=30 4-nbhd, lambda=2.0, 200 sweeps, burn-in 50, FP32 posterior mean")
+G512_SWEEPS, G512_BURN = 2000, 500
+G512_WORKLOAD = ("greyscale 512x512, L=256 (uint8), Gaussian sigma=20, truncated-linear "
+                 "c_T=0.05 T=30 4-nbhd, lambda=2.0, 2000 sweeps, burn-in 500")
 # SFU ex2 issue: 32 per SM per clock (4 SM sub-partitions x 8) x 152 SMs x 2070 MHz
 SFU_PEAK_T = 152 * 32 * 2.070e9 / 1e12
-# DRAM bytes (read + write) per site of one pca_direct_kernel<32,4> launch,
-# from the ncu capture in profiles/pca_direct_l256_1024sq.md (6.33 MB over
-# 1024^2 sites), scaled by the sites of a 512^2 launch.  Set to None when the
-# kernel changes until it is captured again.
-NCU_DRAM_BYTES_PER_SITE = 6.326784e6 / (1024 * 1024)
-NCU_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of the 1024^2 L=256 launch scaled by sites; "
-                    "the working set is L2-resident, so DRAM traffic is below the 3-11 B/site "
-                    "the sweep touches")
+SFU_PEAK_SOURCE = ("152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count x max clock; an "
+                   "ex2.approx.ftz loop measured 29.9/clk/SM)")
+HBM_PEAK_FALLBACK = 6800.0   # GB/s, used only if MEASURED_PEAKS.json is absent
 
-
-# The same for pca_tcw_kernel<4,0,0,0> (one 32-sweep launch at 512^2,
-# profiles/pca_tc_l256_512sq.md) and pca_wave_kernel<32,4> (one 32-sweep
-# launch at 1024^2, per site-update).
-NCU_TC_DRAM_BYTES_PER_SITE = (1.637888e6 + 0.122880e6) / (32 * 512 * 512)
-NCU_TC_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 512^2 L=256 (sweeps "
-                       "161-192 of a chain): the chain's planes stay in L2")
-NCU_WAVE_DRAM_BYTES_PER_SITE = (6.372096e6 + 0.761856e6) / (32 * 1024 * 1024)
-NCU_WAVE_TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one 32-sweep launch at 1024^2 L=256, "
-                         "scaled by sites to a 512^2 launch (profiles/pca_wave_l256_1024sq.md)")
+# DRAM bytes (read + write) per site-update of each kernel, from ncu captures
+# (profiles/); None until the current kernel is captured.  The tensor-core
+# figure is one 32-sweep launch at 4096^2 (planes, observation and
+# accumulator exceed L2), the CUDA-core figure one per-sweep launch at
+# 8192^2 L = 16.
+NCU_TC_BYTES_PER_SITE = (3.213934e9 + 2.634401e9) / (32 * 4096 * 4096)
+NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_kernel launch "
+               "at 4096^2 L=256 (profiles/pca_tc_l256_4096sq.md), scaled by sites to 8192^2")
+NCU_DIRECT_BYTES_PER_SITE = None
+NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at 8192^2 L=16"
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3}
+KERNEL_NAMES = {
+    1: "pca_direct_kernel (CUDA cores, one launch per sweep)",
+    2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
+       "one launch per 32 sweeps)",
+    3: "pca_wave_kernel (CUDA cores, wavefront, one launch per 32 sweeps)",
+}
 
 
 def _args():
@@ -69,6 +80,9 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-gibbs", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--only-head", action="store_true",
+                   help="print the headline line without the side measurements (config3 "
+                        "variants, Gibbs, 512^2 chain, batch, serve)")
     p.add_argument("--profile-case", nargs=3, type=int, metavar=("SIDE", "L", "SWEEPS"),
                    help="run one SIDE x SIDE chain with L labels for SWEEPS sweeps and exit "
                         "(the small case ncu captures; prints no JSON line)")
@@ -77,16 +91,20 @@ def _args():
                    help="profile case: sweeps per TMA-tiled launch (0: unblocked)")
     p.add_argument("--workload", default="chain",
                    choices=["chain", "batch", "serve", "blocking", "protocol"],
-                   help="chain: the 512x512 L=256 chain (default); batch: uneven images x 4 "
-                        "chains in one persistent launch vs one chain per launch; serve: "
-                        "Poisson request stream through the continuous-batching server; "
-                        "protocol: the paper's annealed runs on MRF images and the q grid")
+                   help="chain: the default line; batch: uneven images x 4 chains in one "
+                        "persistent launch vs one chain per launch; serve: Poisson request "
+                        "stream through the continuous-batching server; blocking: 8192^2 "
+                        "unblocked vs k = 1..8; protocol: the paper's annealed runs on MRF "
+                        "images and the q grid")
     p.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor", "wave"],
-                   help="kernel of the unblocked PCA sweep (chain workload and profile case): "
-                        "auto = cuda_core; tensor = prior sums by tcgen05.mma")
+                   help="kernel of the unblocked PCA sweep (headline chain and profile case): "
+                        "auto = the tensor-core sweep for eligible models with L >= 192, else "
+                        "the per-sweep or wavefront CUDA-core kernel; tensor = prior sums by "
+                        "tcgen05.mma")
     p.add_argument("--images", type=int, default=128, help="batch: number of images")
-    p.add_argument("--requests", type=int, default=24, help="serve: requests per rate")
-    p.add_argument("--rates", default="2,50", help="serve: comma-separated arrival rates (req/s)")
+    p.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
+    p.add_argument("--rates", default="10,50,200",
+                   help="serve: comma-separated arrival rates (req/s)")
     return p.parse_args()
 
 
@@ -150,28 +168,61 @@ def _dist():
     return world, rank, local
 
 
-def _inputs():
-    from pcad_inputs import greyscale_512
-    return greyscale_512(seed=2)
+def _hbm_peak():
+    """Measured copy bandwidth (GB/s) and where it came from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, KeyError, ValueError):
+        return HBM_PEAK_FALLBACK, "fallback"
 
 
-def cpu_baseline(seconds: float = 12.0):
-    """FP64 oracle PCA sweeps of the 512x512 L=256 image on all host cores."""
+def _inputs(L=LABELS):
+    from pcad_inputs import large_image
+    return large_image(seed=3, side=SIDE, L=L)
+
+
+def _algo_bytes(sites, sweeps, burn):
+    """Algorithmic DRAM bytes of `sweeps` sweeps from sweep 0: per site-update
+    1 B label and 1 B observation in, 1 B label out, plus the 8 B FP32
+    accumulator read-modify-write once past burn-in."""
+    return sites * (3 * sweeps + 8 * max(0, sweeps - burn))
+
+
+def _sfu_roofline(sites, L, ms_per_sweep, kernel, traffic=None, traffic_note=None,
+                  sweeps_per_launch=1):
+    """The exponential-per-label bound: one label evaluation = one ex2."""
+    achieved = sites * L / (ms_per_sweep * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T, "unit": "T ex2/s",
+            "frac": achieved / SFU_PEAK_T, "traffic": traffic, "traffic_source": traffic_note,
+            "traffic_unit": f"DRAM bytes per launch ({sweeps_per_launch} sweeps)",
+            "kernel": kernel, "peak_source": SFU_PEAK_SOURCE, "ms_per_sweep": ms_per_sweep,
+            "work_per_unit": f"one label evaluation (one exponential on the SFU in a direct "
+                             f"evaluation), L={L} per site-update"}
+
+
+def _crop(a, side):
+    return a[:side, :side].copy()
+
+
+def cpu_baseline(seconds: float = 10.0):
+    """FP64 oracle lazy-PCA sweeps of a 2048 x 2048 crop of the headline image
+    on all host cores (OpenMP over rows)."""
     import oracle
     clean, noisy, m = _inputs()
-    x = noisy.copy()
+    g = _crop(noisy, 2048)
+    x = g.copy()
     t0 = time.perf_counter()
     n = 0
     while True:
-        x, _ = oracle.pca_sweep(m, noisy, x, 2, 0, n)
+        x, _ = oracle.pca_sweep(m, g, x, 3, 0, n)
         n += 1
         if time.perf_counter() - t0 > seconds or n >= 64:
             break
     dt = time.perf_counter() - t0
-    H, W = noisy.shape
-    return {"value": H * W * n / dt, "unit": "site-updates/s", "cores": oracle.num_threads(),
-            "kind": "oracle", "sample": f"{n} lazy-PCA sweeps of the 512x512 L=256 image "
-                                        f"({dt:.1f} s, OpenMP over rows)"}
+    return {"value": g.size * n / dt, "unit": "site-updates/s", "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"{n} lazy-PCA sweeps of a 2048x2048 crop of the "
+                                        f"8192x8192 L=256 image ({dt:.1f} s, OpenMP over rows)"}
 
 
 def run_reference(a):
@@ -180,29 +231,50 @@ def run_reference(a):
         return
     import oracle
     clean, noisy, m = _inputs()
-    H, W = noisy.shape
-    x = noisy.copy()
+    g = _crop(noisy, 2048)
+    x = g.copy()
     for t in range(a.warmup):
-        x, _ = oracle.pca_sweep(m, noisy, x, 2, 0, t)
+        x, _ = oracle.pca_sweep(m, g, x, 3, 0, t)
     times = []
     for k in range(a.steps):
         t0 = time.perf_counter()
-        x, _ = oracle.pca_sweep(m, noisy, x, 2, 0, a.warmup + k)
+        x, _ = oracle.pca_sweep(m, g, x, 3, 0, a.warmup + k)
         times.append(time.perf_counter() - t0)
     T = sum(times)
-    v = H * W * a.steps / T
+    v = g.size * a.steps / T
     cores = oracle.num_threads()
     line = {"impl": "reference", "metric": "site-updates/s", "value": v,
             "unit": "site-updates/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * T / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step": "one lazy-PCA sweep of the full image "
-                                                    "(bounded sample of the 2000-sweep chain)"},
+            "config": {"workload": WORKLOAD, "step": "one lazy-PCA sweep of a 2048x2048 crop "
+                                                    "(bounded sample of the 200-sweep chain)"},
             "cpu_baseline": {"kind": "oracle", "cores": cores, "value": v,
-                             "sample": f"{a.steps} sweeps of the 512x512 L=256 image"},
+                             "sample": f"{a.steps} sweeps of a 2048x2048 crop of the "
+                                       f"8192x8192 L=256 image"},
             "e2e": {"value": v, "unit": "site-updates/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _launches_per_run(kind, sweeps, sampler=0):
+    """Kernel launches of one `sweeps`-sweep run: 32-sweep captured blocks
+    plus the rest.  Wavefront kernels: one sweep launch and the counter
+    advance per block; per-sweep kernels: one launch per sweep (or per Gibbs
+    colour phase) plus the advance."""
+    blocks, rest = divmod(sweeps, 32)
+    if kind in (2, 3):
+        return 2 * blocks + (2 if rest else 0)
+    per = 2 if sampler else 1
+    return blocks * (32 * per + 1) + ((rest * per + 1) if rest else 0)
+
+
+def _safe(fn, *args, **kw):
+    """A side measurement that fails is recorded, not fatal to the line."""
+    try:
+        return fn(*args, **kw)
+    except Exception as e:   # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def run_ours(a):
@@ -222,16 +294,19 @@ def run_ours(a):
     torch.cuda.set_device(dev)
     clean, noisy, m = _inputs()
     H, W = noisy.shape
+    sites = H * W
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    hbm_peak, hbm_src = _hbm_peak()
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    def timed(chain, steps, warm):
+    def timed(chain, sweeps, steps, warm):
+        """K timed runs of `sweeps` sweeps from a reset, L2 flushed before each."""
         for _ in range(warm):
-            chain.reset().run(SWEEPS)
+            chain.reset().run(sweeps)
         chain.sync()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
@@ -241,127 +316,101 @@ def run_ours(a):
         wall0 = time.perf_counter()
         with torch.cuda.stream(stream):
             for k in range(steps):
+                chain.reset()
                 flush.fill_(k & 0xFF)              # L2 flush between timed steps
                 evs[k][0].record(stream)
-                chain.reset().run(SWEEPS)
+                chain.run(sweeps)
                 evs[k][1].record(stream)
         torch.cuda.synchronize(dev)
+        chain.sync()
         barrier()
         wall = time.perf_counter() - wall0
-        ms = [e0.elapsed_time(e1) for e0, e1 in evs]
-        return ms, wall
+        return [e0.elapsed_time(e1) for e0, e1 in evs], wall
 
+    # ---- headline: 8192^2, L = 256, 200 sweeps (default kernel)
     kind = KERNEL_KINDS[a.kernel]
-    pca = pc.Chain(noisy, m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream)
+    pca = pc.Chain(noisy, m, seed=3, chain_id=cid, burn_in=BURN_IN, stream=stream)
     pca.set_kernel(kind)
     pca_kind = pca.kernel_in_use()
     with ClockSampler(local) as clk:
-        ms, wall = timed(pca, a.steps, a.warmup)
+        ms, wall = timed(pca, SWEEPS, a.steps, a.warmup)
     T = sum(ms) / 1e3
     T_max = replicas.max_time(T)   # the slowest rank's time
-    sites = H * W * SWEEPS
-    value = world * sites * a.steps / T_max
-    launch_ms = 1e3 * T / (a.steps * SWEEPS)
+    value = world * sites * SWEEPS * a.steps / T_max
+    ms_sweep = 1e3 * T / (a.steps * SWEEPS)
     fp64 = pca.fp64_draws()
     psnr, ssim = pca.metrics(clean, 0)
-    pca_sample_psnr, _ = pca.metrics(clean, 1)
+    last_psnr, _ = pca.metrics(clean, 1)
+    x_head = pca.sample()
+    pca.close()
+    spl = 32 if pca_kind in (2, 3) else 1          # sweeps per launch
+    per_site = NCU_TC_BYTES_PER_SITE if pca_kind == 2 else (
+        NCU_DIRECT_BYTES_PER_SITE if pca_kind == 1 else None)
+    traffic = per_site * sites * spl if per_site else None
+    roof = _sfu_roofline(sites, LABELS, ms_sweep, KERNEL_NAMES.get(pca_kind, str(pca_kind)),
+                         traffic, NCU_TC_NOTE if pca_kind == 2 else NCU_DIRECT_NOTE, spl)
+    roof["algorithmic_bytes_per_launch"] = 11 * sites * spl
+    roof["hbm_frac"] = (_algo_bytes(sites, SWEEPS, BURN_IN) / (ms_sweep * SWEEPS * 1e-3) / 1e9
+                        / hbm_peak)
 
-    gibbs = None
-    if not a.no_gibbs:
-        gch = pc.Chain(noisy, m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream,
-                       sampler=pc.SAMPLER_GIBBS_CB)
-        gsteps = max(2, a.steps // 2)
-        gms, _ = timed(gch, gsteps, 1)
-        gT = sum(gms) / 1e3
-        gp, gs = gch.metrics(clean, 0)
-        g_tc = gch.kernel_in_use() == pc.PCAD_KERNEL_TENSOR
-        gblocks = (SWEEPS + 31) // 32
-        gibbs = {"value": sites * gsteps / gT, "unit": "site-updates/s",
-                 "ms_per_step": 1e3 * gT / gsteps, "steps": gsteps, "psnr_db": gp, "ssim": gs,
-                 # per 32-sweep graph: the wavefront launch (or 2 colour-phase launches per
-                 # sweep), the counter reset and the sweep-counter advance
-                 "launches_per_step": gblocks * 2 if g_tc else 2 * SWEEPS + gblocks,
-                 "kernel": ("pca_tcw_kernel<4,0,0,0,1> (checkerboard Gibbs on the tensor-core "
-                            "wavefront, 2 colour phases per sweep)") if g_tc else
-                           "gibbs_cb_kernel<32,4> (2 colour phases per sweep)"}
-        gch.close()
-
-    # end to end through the public API with host buffers (pinned)
+    # ---- end to end through the public API with host buffers (pinned)
     g_host = torch.empty((H, W), dtype=torch.uint8, pin_memory=True)
     g_host.numpy()[:] = noisy
     mean_host = torch.empty((H, W), dtype=torch.float32, pin_memory=True)
-    e2e_steps = max(2, min(a.steps, 5))
+    e2e_steps = 2
     torch.cuda.synchronize(dev)
     e2e_t = []
     for k in range(e2e_steps + 1):
         t0 = time.perf_counter()
-        ch = pc.Chain(g_host.numpy(), m, seed=2, chain_id=cid, burn_in=BURN_IN, stream=stream)
+        ch = pc.Chain(g_host.numpy(), m, seed=3, chain_id=cid, burn_in=BURN_IN, stream=stream)
         ch.set_kernel(kind)
         ch.run(SWEEPS)
         pc.pcad_chain_read_mean(ch.h, H, W, out=mean_host.numpy())
         ch.close()
         if k > 0:                                     # first one warms the allocator
             e2e_t.append(time.perf_counter() - t0)
-    e2e_v = world * sites / statistics.mean(e2e_t)
+    e2e_v = world * sites * SWEEPS / statistics.mean(e2e_t)
+
+    side = {}
+    if not a.only_head:
+        side["config3"] = _safe(_config3, pc, stream, timed, x_head, ms_sweep, pca_kind,
+                                hbm_peak, cid)
+        if not a.no_gibbs:
+            side["gibbs"] = _safe(_gibbs_8192, pc, stream, timed, noisy, m, clean, cid)
+        side["greyscale512"] = _safe(_greyscale512, pc, stream, timed, cid, a.no_gibbs)
+        if world == 1:
+            side["batch"] = _safe(_batch_object, pc, torch, stream, a.images)
+            rates = [float(x) for x in a.rates.split(",") if x]
+            side["serve"] = _safe(_serve_object, pc, torch, stream, rates, a.requests)
 
     if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
-    per_sweep_labels = H * W * m.L
-    achieved = per_sweep_labels / (launch_ms * 1e-3) / 1e12
-    in_use = pca_kind   # the kernel the timed chain ran
-    kernel_name = {1: "pca_direct_kernel<32,4> (one launch per sweep)",
-                   2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, "
-                      "wavefront, one launch per 32 sweeps)",
-                   3: "pca_wave_kernel<32,4> (wavefront, one launch per 32 sweeps)"}[in_use]
-    per_site = {1: NCU_DRAM_BYTES_PER_SITE, 2: NCU_TC_DRAM_BYTES_PER_SITE,
-                3: NCU_WAVE_DRAM_BYTES_PER_SITE}[in_use]
-    note = {1: NCU_TRAFFIC_NOTE, 2: NCU_TC_TRAFFIC_NOTE, 3: NCU_WAVE_TRAFFIC_NOTE}[in_use]
-    # per launch, like achieved: 32 sweeps per wavefront launch, one otherwise
-    sweeps_per_launch = 32 if in_use in (2, 3) else 1
-    traffic = per_site * H * W * sweeps_per_launch if per_site else None
-    blocks, rest = divmod(SWEEPS, 32)
-    # per chain: the 32-sweep graphs (sweep launches + the counter advance) and the rest
-    wave = in_use in (2, 3)   # one launch per block of sweeps + the advance
-    launches = (blocks * (2 if wave else 33) + ((2 if wave else rest + 1) if rest else 0))
     line = {
         "metric": "site-updates/s", "value": value, "unit": "site-updates/s",
         "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * T_max / a.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sites": H * W, "sweeps_per_step": SWEEPS,
-                   "burn_in": BURN_IN, "l2": "flushed between timed steps (256 MiB write)",
+        "config": {"workload": WORKLOAD, "sites": sites, "sweeps_per_step": SWEEPS,
+                   "burn_in": BURN_IN,
+                   "l2": "inputs larger than L2 (8192^2 planes, 256 MiB accumulator) and a "
+                         "256 MiB flush write before each timed step",
                    "parallelism": "independent chain per GPU" if world > 1 else "1 GPU"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": SFU_PEAK_T,
-                     "unit": "T ex2/s", "frac": achieved / SFU_PEAK_T,
-                     "traffic": traffic, "traffic_source": note,
-                     "traffic_unit": f"DRAM bytes per launch ({sweeps_per_launch} sweeps of "
-                                     f"{H}x{W})",
-                     # 1 B label + 1 B observation in, 1 B label + 8 B accumulator RMW
-                     # after burn-in per site-update
-                     "algorithmic_bytes_per_launch": 11 * H * W * sweeps_per_launch,
-                     "kernel": kernel_name,
-                     "work_per_unit": "one label evaluation (one exponential on the SFU in "
-                                      "a direct evaluation), L=256 per site-update; the "
-                                      "tensor-core kernel takes the chunk sums outside a "
-                                      "site's 128-label window from a table, so it evaluates "
-                                      "fewer exponentials than labels",
-                     "peak_source": "152 SMs x 32 ex2/clk/SM x 2070 MHz (unit count x max "
-                                    "clock; 29.9/clk/SM measured)",
-                     "ms_per_sweep": launch_ms},
-        "gpu_launches": a.steps * launches,
-        "e2e": {"value": e2e_v, "unit": "site-updates/s", "h2d_bytes_per_step": H * W,
-                "d2h_bytes_per_step": H * W * 4, "steps": e2e_steps,
+        "roofline": roof,
+        "gpu_launches": a.steps * _launches_per_run(pca_kind, SWEEPS),
+        "e2e": {"value": e2e_v, "unit": "site-updates/s", "h2d_bytes_per_step": sites,
+                "d2h_bytes_per_step": sites * 4, "steps": e2e_steps,
                 "ms_per_step": 1e3 * statistics.mean(e2e_t),
                 "path": "pcad_chain_create(host) + pcad_chain_run + pcad_chain_read_mean(host)"},
-        "label_evals_per_s": value * m.L,
-        "fp64_redraw_fraction": fp64 / float(H * W * SWEEPS),   # counter restarts each step
-        "psnr_db": psnr, "ssim": ssim, "last_sample_psnr_db": pca_sample_psnr,
-        "wall_s_timed": wall,
+        "label_evals_per_s": value * LABELS,
+        "fp64_redraw_fraction": fp64 / float(sites * SWEEPS),   # counter restarts each step
+        "psnr_db": psnr, "ssim": ssim, "last_sample_psnr_db": last_psnr,
+        "wall_s_timed": wall, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+        "kernel": KERNEL_NAMES.get(pca_kind, str(pca_kind)),
     }
-    if gibbs:
-        line["gibbs"] = gibbs
-    clocks = clk.summary()
-    line["clocks"] = clocks
+    line.update(side)
+    line["clocks"] = clk.summary()
     if world == 1 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline()
     print(json.dumps(line), flush=True)
@@ -369,31 +418,113 @@ def run_ours(a):
         torch.distributed.destroy_process_group()
 
 
+def _config3(pc, stream, timed, x_head, ms_head, head_kind, hbm_peak, cid):
+    """The roofline workload's other runs: L = 256 with k = 4 and 8 sweeps per
+    TMA-tiled launch, and L = 16 (sigma 1.0) unblocked and with k = 4, 8;
+    each a 200-sweep chain from the observation, burn-in 50.  Labels are
+    bit-identical across k (checked)."""
+    import numpy as np
+    out = {"L=256": {"unblocked": {"site_updates_per_s": SIDE * SIDE / (ms_head * 1e-3),
+                                   "ms_per_sweep": ms_head, "kernel": head_kind,
+                                   "note": "the headline run"}}}
+    for L, ks, steps in ((256, (4, 8), 1), (16, (0, 4, 8), 2)):
+        clean, noisy, m = _inputs(L)
+        sites = noisy.size
+        ref = x_head if L == 256 else None
+        rows = out.setdefault(f"L={L}", {})
+        for k in ks:
+            ch = pc.Chain(noisy, m, seed=3, chain_id=cid, burn_in=BURN_IN, stream=stream)
+            ch.set_blocking(k)
+            ms, _ = timed(ch, SWEEPS, steps, 1)
+            kind = ch.kernel_in_use()
+            x = ch.sample()
+            ch.close()
+            same = True if ref is None else bool(np.array_equal(x, ref))
+            ref = x if ref is None else ref
+            ms_sweep = sum(ms) / (steps * SWEEPS)
+            name = "unblocked" if k == 0 else f"k={k}"
+            r = {"site_updates_per_s": sites / (ms_sweep * 1e-3), "ms_per_sweep": ms_sweep,
+                 "kernel": kind, "identical_labels": same}
+            sfu = _sfu_roofline(sites, L, ms_sweep, str(kind))
+            gbs = _algo_bytes(sites, SWEEPS, BURN_IN) / (ms_sweep * SWEEPS * 1e-3) / 1e9
+            hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": gbs / hbm_peak,
+                   "algorithmic_bytes_per_site_update": _algo_bytes(1, SWEEPS, BURN_IN) / SWEEPS}
+            if L == 16 and k == 0:
+                per_site = NCU_DIRECT_BYTES_PER_SITE
+                hbm["traffic"] = per_site * sites if per_site else None
+                hbm["traffic_source"] = NCU_DIRECT_NOTE
+                r["roofline"] = hbm
+                r["sfu_frac"] = sfu["frac"]
+                # the binding bound: min(HBM / B, SFU / L) site-updates/s
+                bound = min(hbm_peak * 1e9 / hbm["algorithmic_bytes_per_site_update"],
+                            SFU_PEAK_T * 1e12 / L)
+                r["frac_of_binding_bound"] = r["site_updates_per_s"] / bound
+            else:
+                r["roofline"] = {k2: sfu[k2] for k2 in ("bound", "achieved", "peak", "unit",
+                                                        "frac")}
+                r["hbm_frac"] = hbm["frac"]
+            rows[name] = r
+    return out
+
+
+def _gibbs_8192(pc, stream, timed, noisy, m, clean, cid, steps=2):
+    """Checkerboard Gibbs (2 colour phases per sweep) on the headline image."""
+    ch = pc.Chain(noisy, m, seed=3, chain_id=cid, burn_in=BURN_IN, stream=stream,
+                  sampler=pc.SAMPLER_GIBBS_CB)
+    ms, _ = timed(ch, SWEEPS, steps, 1)
+    kind = ch.kernel_in_use()
+    p, s = ch.metrics(clean, 0)
+    ch.close()
+    ms_sweep = sum(ms) / (steps * SWEEPS)
+    sites = noisy.size
+    name = ("pca_tcw_kernel<4,0,0,0,1> (checkerboard Gibbs on the tensor-core wavefront, 2 "
+            "colour phases per sweep)") if kind == 2 else "gibbs_cb_kernel (2 colour phases)"
+    return {"value": sites / (ms_sweep * 1e-3), "unit": "site-updates/s",
+            "ms_per_step": sum(ms) / steps, "ms_per_sweep": ms_sweep, "steps": steps,
+            "psnr_db": p, "ssim": s, "kernel": name,
+            "launches_per_step": _launches_per_run(kind, SWEEPS, sampler=1),
+            "roofline": _sfu_roofline(sites, LABELS, ms_sweep, name)}
+
+
+def _greyscale512(pc, stream, timed, cid, no_gibbs, steps=5):
+    """The 512 x 512 L = 256 chain, 2000 sweeps, burn-in 500 (L2-resident)."""
+    from pcad_inputs import greyscale_512
+    clean, noisy, m = greyscale_512(seed=2)
+    out = {"workload": G512_WORKLOAD}
+    for name, sampler in (("pca", pc.SAMPLER_PCA), ("gibbs", pc.SAMPLER_GIBBS_CB)):
+        if no_gibbs and sampler:
+            continue
+        ch = pc.Chain(noisy, m, seed=2, chain_id=cid, burn_in=G512_BURN, stream=stream,
+                      sampler=sampler)
+        ms, _ = timed(ch, G512_SWEEPS, steps, 2)
+        p, s = ch.metrics(clean, 0)
+        kind = ch.kernel_in_use()
+        ch.close()
+        ms_sweep = sum(ms) / (steps * G512_SWEEPS)
+        out[name] = {"value": noisy.size / (ms_sweep * 1e-3), "unit": "site-updates/s",
+                     "ms_per_step": sum(ms) / steps, "psnr_db": p, "ssim": s, "kernel": kind,
+                     "roofline": {k: v for k, v in _sfu_roofline(
+                         noisy.size, 256, ms_sweep, str(kind)).items()
+                         if k in ("bound", "achieved", "peak", "unit", "frac", "ms_per_sweep")}}
+    return out
+
+
 BATCH_SWEEPS, BATCH_BURN = 200, 50
 
 
-def run_batch(a):
+def _batch_object(pc, torch, stream, n_images, rank=0, world=1):
     """Uneven images (short side log-uniform 64..2048, aspect 1..3, L in
     {2, 16, 256}, per-image prior/inertia), 4 chains each, 200 sweeps with
-    burn-in 50: one persistent launch per sweep for all chains, against the
-    same chains run one after another through the chain API on the same GPU.
+    burn-in 50: the batch (autotuned, 16-sweep graph slices) against the same
+    chains run one after another through the chain API on the same GPU.
     Outputs are bit-identical, so PSNR is equal by construction (checked)."""
     import numpy as np
-    import torch
 
-    import paper_2507_14869_gb300 as pc
     from paper_2507_14869_gb300 import replicas
     from pcad_inputs import batched_jobs
 
-    world, rank, local = _dist()
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    all_imgs = batched_jobs(seed=4, n_images=a.images, chains=4, sweeps=BATCH_SWEEPS,
+    all_imgs = batched_jobs(seed=4, n_images=n_images, chains=4, sweeps=BATCH_SWEEPS,
                             burn_in=BATCH_BURN)
     # each rank takes its share of the images (cost ~ sites x labels), no collective
     mine = replicas.shard([j.noisy.size * j.model.L for j in all_imgs], world)[rank]
@@ -410,11 +541,11 @@ def run_batch(a):
     pc.pcad_batch_reset(b)
     pc.pcad_batch_sync(b)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
-    with ClockSampler(local) as clk:
-        ev[0].record(stream)
-        pc.pcad_batch_run(b, BATCH_SWEEPS)
-        ev[1].record(stream)
-        torch.cuda.synchronize()
+    ev[0].record(stream)
+    pc.pcad_batch_run(b, BATCH_SWEEPS)
+    ev[1].record(stream)
+    torch.cuda.synchronize()
+    pc.pcad_batch_sync(b)
     t_batch = ev[0].elapsed_time(ev[1]) / 1e3
     fp64 = pc.pcad_batch_info(b)["fp64_draws"]
 
@@ -441,42 +572,57 @@ def run_batch(a):
         mb = pc.pcad_batch_read_mean(b, k, *g.shape)
         same &= bool(np.array_equal(mb, chains[k].mean()))
     for i, j in enumerate(imgs):
-        k = 4 * i
-        psnr.append(chains[k].metrics(j.clean, 0)[0])
+        psnr.append(chains[4 * i].metrics(j.clean, 0)[0])
     for ch in chains:
         ch.close()
     pc.pcad_batch_destroy(b)
     # whole job: every rank's images over the slowest rank's time
-    t_batch_all = replicas.max_time(t_batch)
-    t_plain_all = replicas.max_time(t_plain)
-    sites_all = replicas.gather({rank: sites})
+    t_batch = replicas.max_time(t_batch)
+    t_plain = replicas.max_time(t_plain)
+    sites = sum(replicas.gather({rank: sites}).values())
     psnr_all = replicas.gather({rank: psnr})
-    same_all = replicas.gather({rank: same})
-    if rank != 0:
-        if world > 1:
-            torch.distributed.destroy_process_group()
-        return
-    n_img = len(all_imgs)
-    sites = sum(sites_all.values())
     psnr = [v for r in sorted(psnr_all) for v in psnr_all[r]]
-    same = all(same_all.values())
-    t_batch, t_plain = t_batch_all, t_plain_all
-    line = {"metric": "img/s (batched, 4 chains per image)", "value": n_img / t_batch,
-            "unit": "img/s", "n_gpus": world, "steps": 1, "warmup": 1,
-            "ms_per_step": 1e3 * t_batch, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"{n_img} uneven images x 4 chains, {BATCH_SWEEPS} sweeps, "
-                                   f"burn-in {BATCH_BURN}", "chain_sites": sites,
-                       "sites_by_L": {str(k): v for k, v in sorted(by_L.items())}},
-            "site_updates_per_s": sites * BATCH_SWEEPS / t_batch,
+    same = all(replicas.gather({rank: same}).values())
+    n_img = len(all_imgs)
+    return {"value": n_img / t_batch, "unit": "img/s",
+            "workload": f"{n_img} uneven images x 4 chains, {BATCH_SWEEPS} sweeps, burn-in "
+                        f"{BATCH_BURN}", "chain_sites": sites,
+            "sites_by_L": {str(k): v for k, v in sorted(by_L.items())},
+            "ms": 1e3 * t_batch, "site_updates_per_s": sites * BATCH_SWEEPS / t_batch,
             "plain_one_chain_per_launch": {"value": n_img / t_plain, "unit": "img/s",
                                            "ms": 1e3 * t_plain,
                                            "site_updates_per_s": sites * BATCH_SWEEPS / t_plain},
             "speedup_vs_plain": t_plain / t_batch,
             "identical_outputs": same, "mean_psnr_db": float(np.mean(psnr)),
-            "autotune": info, "fp64_redraw_fraction": fp64 / float(sites * BATCH_SWEEPS),
-            "gpu_launches": -(-BATCH_SWEEPS // 16) * 17,
-            "clocks": clk.summary()}
+            "autotune": info, "fp64_redraw_fraction": fp64 / float(sites * BATCH_SWEEPS)}
+
+
+def run_batch(a):
+    import torch
+
+    import paper_2507_14869_gb300 as pc
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    with ClockSampler(local) as clk:
+        obj = _batch_object(pc, torch, stream, a.images, rank, world)
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    line = {"metric": "img/s (batched, 4 chains per image)", "value": obj["value"],
+            "unit": "img/s", "n_gpus": world, "steps": 1, "warmup": 1,
+            "ms_per_step": obj["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": obj["workload"], "chain_sites": obj["chain_sites"]},
+            **{k: v for k, v in obj.items() if k not in ("value", "unit", "workload")},
+            "gpu_launches": -(-BATCH_SWEEPS // 16) * 17, "clocks": clk.summary()}
     if world > 1:
         line["config"]["parallelism"] = f"images sharded over {world} ranks (LPT by cost)"
     print(json.dumps(line), flush=True)
@@ -592,11 +738,9 @@ def _serve_stream(pc, sv, reqs, slice_sweeps=16):
     return [lat[i] for i in range(len(reqs))], time.perf_counter() - t0, res
 
 
-def _plain_fifo(pc, reqs, stream):
-    """The same requests one at a time through the chain API, first come first
-    served: each request's service time is measured alone; latency is the
-    queueing simulation over the real arrival times."""
-    import torch
+def _plain_service(pc, torch, reqs, stream):
+    """Each request alone through the chain API, one after another: its
+    service time and result."""
     service, out = [], {}
     for i, r in enumerate(reqs):
         j = r["job"]
@@ -607,71 +751,80 @@ def _plain_fifo(pc, reqs, stream):
             out[i] = (ch.sample(), ch.mean())
         torch.cuda.synchronize()
         service.append(time.perf_counter() - t)
-    free, lat = 0.0, []
-    for i in sorted(range(len(reqs)), key=lambda k: reqs[k]["arrival"]):
-        start = max(free, reqs[i]["arrival"])
+    return service, out
+
+
+def _fifo_latencies(arrivals, service):
+    """First come, first served, one request at a time: latency of each
+    request and the makespan, from the measured service times."""
+    free, lat = 0.0, [0.0] * len(arrivals)
+    for i in sorted(range(len(arrivals)), key=lambda k: arrivals[k]):
+        start = max(free, arrivals[i])
         free = start + service[i]
-        lat.append((i, free - reqs[i]["arrival"]))
-    lat = [v for _, v in sorted(lat)]
-    return lat, free, out, sum(service)
+        lat[i] = free - arrivals[i]
+    return lat, free
 
 
-def run_serve(a):
+def _serve_object(pc, torch, stream, rates, n, seed=50):
     """Poisson arrivals of denoising requests (square side log-uniform
     128..2048, L in {16, 256}, sigma uniform [5, 40] on the 0..255 scale,
     300..3000 sweeps, burn-in a quarter, one chain each) through the
-    continuous-batching server with a 150 GB HBM budget; the same stream one
-    request at a time through the chain API is the comparison.  Results are
+    continuous-batching server (150 GB HBM budget, 16-sweep slices), and the
+    same requests one at a time through the chain API, first come first
+    served.  One request set serves every rate (the arrival times scale with
+    1/rate); the one-at-a-time service times are measured once.  Results are
     bit-identical (checked), so PSNR is equal."""
     import numpy as np
+
+    from pcad_inputs import serving_requests
+    base = serving_requests(seed=seed, rate=1.0, n=n)
+    service, pres = _plain_service(pc, torch, base, stream)
+    work = sum(r["job"].noisy.size * r["job"].sweeps for r in base)
+    psnr = [pc.pcad_metrics(pres[i][1], r["job"].clean, r["job"].model.L)[0]
+            for i, r in enumerate(base)]
+    per_rate = []
+    for rate in rates:
+        reqs = [dict(r, arrival=r["arrival"] / rate) for r in base]
+        sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
+        lat, span, res = _serve_stream(pc, sv, reqs)
+        info = pc.pcad_server_info(sv)
+        pc.pcad_server_destroy(sv)
+        same = all(np.array_equal(res[i][0], pres[i][0]) and np.array_equal(res[i][1], pres[i][1])
+                   for i in res)
+        flat, fspan = _fifo_latencies([r["arrival"] for r in reqs], service)
+        per_rate.append({
+            "rate_req_s": rate, "requests": n, "img_s": n / span,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "makespan_s": span, "site_updates_per_s": work / span, "slices": info["slices"],
+            "plain_fifo": {"img_s": n / fspan, "p50_s": float(np.percentile(flat, 50)),
+                           "p99_s": float(np.percentile(flat, 99)), "makespan_s": fspan},
+            "identical_outputs": same})
+    return {"workload": "Poisson requests, side 128..2048 (square), L in {16,256}, sigma "
+                        "5..40, 300..3000 sweeps, 150 GB HBM budget, 16-sweep slices",
+            "requests_per_rate": n, "capacity_img_s_one_at_a_time": n / sum(service),
+            "work_site_updates": work, "mean_psnr_db": float(np.mean(psnr)),
+            "per_rate": per_rate}
+
+
+def run_serve(a):
+    """The served form alone (see _serve_object), one JSON line."""
     import torch
 
     import paper_2507_14869_gb300 as pc
-    from pcad_inputs import serving_requests
 
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     rates = [float(x) for x in a.rates.split(",") if x]
-    per_rate = []
     with ClockSampler(0) as clk:
-        for k, rate in enumerate(rates):
-            reqs = serving_requests(seed=50 + k, rate=rate, n=a.requests)
-            sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
-            lat, span, res = _serve_stream(pc, sv, reqs)
-            info = pc.pcad_server_info(sv)
-            pc.pcad_server_destroy(sv)
-            # the same stream with admission capped at 2M sites of admitted work
-            sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
-            pc.pcad_server_set_limits(sv, 2 << 20)
-            clat, cspan, _ = _serve_stream(pc, sv, reqs)
-            pc.pcad_server_destroy(sv)
-            plat, pspan, pres, busy = _plain_fifo(pc, reqs, stream)
-            same = all(np.array_equal(res[i][0], pres[i][0]) and
-                       np.array_equal(res[i][1], pres[i][1]) for i in res)
-            work = sum(r["job"].noisy.size * r["job"].sweeps for r in reqs)
-            psnr = [pc.pcad_metrics(res[i][1], reqs[i]["job"].clean, reqs[i]["job"].model.L)[0]
-                    for i in range(min(4, len(reqs)))]
-            per_rate.append({
-                "rate_req_s": rate, "requests": len(reqs),
-                "img_s": len(reqs) / span, "p50_s": float(np.percentile(lat, 50)),
-                "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
-                "site_updates_per_s": work / span, "slices": info["slices"],
-                "plain": {"img_s": len(reqs) / pspan, "p50_s": float(np.percentile(plat, 50)),
-                          "p99_s": float(np.percentile(plat, 99)), "busy_s": busy},
-                "capped_2M_sites": {"img_s": len(reqs) / cspan,
-                                    "p50_s": float(np.percentile(clat, 50)),
-                                    "p99_s": float(np.percentile(clat, 99))},
-                "identical_outputs": same, "psnr_db_first": psnr})
-    head = per_rate[-1]
+        obj = _serve_object(pc, torch, stream, rates, a.requests)
+    head = obj["per_rate"][-1]
     line = {"metric": "served img/s (continuous batching)", "value": head["img_s"],
             "unit": "img/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,
             "ms_per_step": 1e3 * head["makespan_s"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "Poisson requests, side 128..2048, L in {16,256}, "
-                                   "300..3000 sweeps, 150 GB HBM budget, 16-sweep slices",
-                       "rates": rates, "requests_per_rate": a.requests},
-            "p50_s": head["p50_s"], "p99_s": head["p99_s"], "per_rate": per_rate,
-            "clocks": clk.summary()}
+            "config": {"workload": obj["workload"], "rates": rates,
+                       "requests_per_rate": a.requests},
+            "p50_s": head["p50_s"], "p99_s": head["p99_s"], **obj, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -736,9 +889,10 @@ def run_blocking(a):
 def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0,
                  kernel: str = "auto"):
     """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
-    L > 16, else 1), truncated-linear prior (c_T 0.05, T 30 for L > 16; 0.85,
-    2 otherwise), lambda 2.0; L = 2 uses the binary flip-noise scene (Ising
-    c_P 1.2, p 0.1, lambda 1.0).  blocking: sweeps per TMA-tiled launch."""
+    L > 16, else 1), truncated-linear prior c_T 0.05, T 30 (the roofline
+    workload's prior), lambda 2.0; L = 2 uses the binary flip-noise scene
+    (Ising c_P 1.2, p 0.1, lambda 1.0).  blocking: sweeps per TMA-tiled
+    launch."""
     import paper_2507_14869_gb300 as pc
     from pcad_inputs import Model, flip_noise, gaussian_noise, greyscale_scene, shapes_binary
     if L == 2:
@@ -748,8 +902,8 @@ def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0
         sig = 20.0 if L > 16 else 1.0
         clean = greyscale_scene(3, side, side, L)
         noisy = gaussian_noise(4, clean, sig, L)
-        m = Model(L=L, pair=1, pair_coef=0.05 if L > 16 else 0.85, pair_T=30 if L > 16 else 2,
-                  sigma=sig, inertia=2.0, sampler=sampler)
+        m = Model(L=L, pair=1, pair_coef=0.05, pair_T=30, sigma=sig, inertia=2.0,
+                  sampler=sampler)
     with pc.Chain(noisy, m, seed=1, chain_id=0, burn_in=0) as ch:
         ch.set_blocking(blocking)
         if sampler == 0 or kernel != "auto":
