@@ -105,6 +105,9 @@ def _args():
     p.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
     p.add_argument("--rates", default="10,50,200",
                    help="serve: comma-separated arrival rates (req/s)")
+    p.add_argument("--aging", type=float, default=0.2,
+                   help="serve: priority seconds a waiting request gains per second "
+                        "(shortest-remaining-work scheduling)")
     return p.parse_args()
 
 
@@ -381,7 +384,8 @@ def run_ours(a):
         if world == 1:
             side["batch"] = _safe(_batch_object, pc, torch, stream, a.images)
             rates = [float(x) for x in a.rates.split(",") if x]
-            side["serve"] = _safe(_serve_object, pc, torch, stream, rates, a.requests)
+            side["serve"] = _safe(_serve_object, pc, torch, stream, rates, a.requests,
+                                  aging=a.aging)
 
     if rank != 0:
         if world > 1:
@@ -726,8 +730,10 @@ def _serve_stream(pc, sv, reqs, slice_sweeps=16):
         if not live:
             time.sleep(max(0.0, reqs[order[nxt]]["arrival"] - now))
             continue
-        pc.pcad_server_step(sv, slice_sweeps)
+        _, _, fin = pc.pcad_server_step(sv, slice_sweeps)
         done_t = time.perf_counter() - t0
+        if fin == 0:
+            continue
         for rid in list(live):
             i = live[rid]
             st, smp, mean = pc.pcad_server_poll(sv, rid, *reqs[i]["job"].noisy.shape)
@@ -765,7 +771,7 @@ def _fifo_latencies(arrivals, service):
     return lat, free
 
 
-def _serve_object(pc, torch, stream, rates, n, seed=50):
+def _serve_object(pc, torch, stream, rates, n, seed=50, aging=0.2, shared_rate=50.0):
     """Poisson arrivals of denoising requests (square side log-uniform
     128..2048, L in {16, 256}, sigma uniform [5, 40] on the 0..255 scale,
     300..3000 sweeps, burn-in a quarter, one chain each) through the
@@ -786,21 +792,33 @@ def _serve_object(pc, torch, stream, rates, n, seed=50):
     for rate in rates:
         reqs = [dict(r, arrival=r["arrival"] / rate) for r in base]
         sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
+        pc.pcad_server_set_policy(sv, pc.SERVE_SRPT, aging)
         lat, span, res = _serve_stream(pc, sv, reqs)
         info = pc.pcad_server_info(sv)
         pc.pcad_server_destroy(sv)
         same = all(np.array_equal(res[i][0], pres[i][0]) and np.array_equal(res[i][1], pres[i][1])
                    for i in res)
         flat, fspan = _fifo_latencies([r["arrival"] for r in reqs], service)
-        per_rate.append({
+        row = {
             "rate_req_s": rate, "requests": n, "img_s": n / span,
             "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "makespan_s": span, "site_updates_per_s": work / span, "slices": info["slices"],
             "plain_fifo": {"img_s": n / fspan, "p50_s": float(np.percentile(flat, 50)),
                            "p99_s": float(np.percentile(flat, 99)), "makespan_s": fspan},
-            "identical_outputs": same})
+            "identical_outputs": same}
+        if rate == shared_rate:
+            # the same server sharing the GPU among every admitted request
+            sv = pc.pcad_server_create(256, 150 * 10 ** 9, stream)
+            pc.pcad_server_set_policy(sv, pc.SERVE_FIFO, 0.0)
+            slat, sspan, _ = _serve_stream(pc, sv, reqs)
+            pc.pcad_server_destroy(sv)
+            row["server_shared_fifo"] = {"img_s": n / sspan,
+                                         "p50_s": float(np.percentile(slat, 50)),
+                                         "p99_s": float(np.percentile(slat, 99))}
+        per_rate.append(row)
     return {"workload": "Poisson requests, side 128..2048 (square), L in {16,256}, sigma "
                         "5..40, 300..3000 sweeps, 150 GB HBM budget, 16-sweep slices",
+            "policy": f"shortest remaining work first, aging {aging}",
             "requests_per_rate": n, "capacity_img_s_one_at_a_time": n / sum(service),
             "work_site_updates": work, "mean_psnr_db": float(np.mean(psnr)),
             "per_rate": per_rate}
@@ -816,7 +834,7 @@ def run_serve(a):
     stream = torch.cuda.Stream()
     rates = [float(x) for x in a.rates.split(",") if x]
     with ClockSampler(0) as clk:
-        obj = _serve_object(pc, torch, stream, rates, a.requests)
+        obj = _serve_object(pc, torch, stream, rates, a.requests, aging=a.aging)
     head = obj["per_rate"][-1]
     line = {"metric": "served img/s (continuous batching)", "value": head["img_s"],
             "unit": "img/s", "n_gpus": 1, "steps": len(rates), "warmup": 0,

@@ -357,29 +357,42 @@ pcad_status pcad_batch_info(pcad_batch *b, uint64_t *t, int *tile_rows, int *lpt
 void pcad_batch_destroy(pcad_batch *b);
 
 /* -------------------------------------------------------------- server
- * Continuous batching of denoising requests.  Submitted requests wait in a
- * first-come first-served queue and are admitted when a slot is free and
- * their device memory fits the HBM budget; every pcad_server_step admits what
- * it can, advances every admitted request by one slice of sweeps in shared
- * launches, and retires the requests whose sweep budget is spent (their
- * sample and posterior mean are copied to host memory held by the server
- * until polled).  State and sweep counters stay on the device between
- * slices; a request's results do not depend on what else was running. */
+ * Continuous batching of denoising requests (no counterpart in the paper:
+ * a serving loop around the sweep of Section 5.2).  Submitted requests are
+ * admitted into slots as slots free up and their device memory fits the HBM
+ * budget; every pcad_server_step chooses the requests to run, advances them
+ * by one slice of sweeps in shared launches, and retires the requests whose
+ * sweep budget is spent (their sample and posterior mean are copied to host
+ * memory held by the server until polled).  State and sweep counters stay
+ * on the device between slices; a request's results do not depend on what
+ * else was running, nor on the policy below. */
 typedef struct pcad_server pcad_server;
+
+/* Scheduling policy.  PCAD_SERVE_FIFO: admit first come first served and
+ * run every admitted request in every slice (the GPU is shared among all
+ * of them).  PCAD_SERVE_SRPT (the default): shortest remaining work first
+ * -- each step orders queued and admitted requests by estimated remaining
+ * GPU time (sites x sweeps left x a per-label-count cost) minus `aging` x
+ * the seconds since submission, and runs the shortest ones until they hold
+ * the fill target of sites (pcad_server_set_limits; by default two waves
+ * of 4 x 32-site tiles); admitted requests outside that set keep their
+ * device state and pause.  Default aging 0.2.  PCAD_EINVAL for an unknown
+ * policy or aging outside [0, 1e6].  Takes effect at the next step. */
+typedef enum { PCAD_SERVE_FIFO = 0, PCAD_SERVE_SRPT = 1 } pcad_serve_policy;
 
 pcad_status pcad_server_create(int max_slots, size_t hbm_budget_bytes, void *cuda_stream,
                                pcad_server **out);
-/* Admission cap: a queued request waits while the admitted requests hold
- * max_active_sites sites or more (its own included), unless none is
- * admitted; 0 (the default) admits whenever a slot and the HBM budget
- * allow.  With a cap the GPU still runs full slices while early long
- * requests are not diluted by every later arrival (tail latency under
- * overload).  Takes effect at the next step. */
+/* How much work runs at once.  FIFO: a queued request waits while the
+ * admitted requests hold max_active_sites sites or more (its own included),
+ * unless none is admitted; 0 (the default) admits whenever a slot and the
+ * HBM budget allow.  SRPT: the run set is filled up to max_active_sites
+ * sites (0: the default fill target).  Takes effect at the next step. */
 pcad_status pcad_server_set_limits(pcad_server *sv, size_t max_active_sites);
+pcad_status pcad_server_set_policy(pcad_server *sv, int policy, double aging);
 /* Queue a request for nsweeps sweeps (job->g_host is copied).  *id is its handle. */
 pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id);
-/* Admit, run one slice of slice_sweeps (1..16) sweeps of every admitted
- * request in one wavefront launch (tiles of 4 or 8 rows x 32 sites; a
+/* Admit, run one slice of slice_sweeps (1..16) sweeps of every request in
+ * the run set in one wavefront launch (tiles of 4 or 8 rows x 32 sites; a
  * tile's sweep starts when its 3 x 3 neighbourhood finished the previous
  * sweep), retire finished requests.  When the slice retires a request it
  * returns after the slice is done (the outputs are then in host memory);

@@ -21,5 +21,6 @@ from ._capi import (  # noqa: F401
     pcad_batch_read_sample, pcad_batch_reset, pcad_batch_run, pcad_batch_sync,
     pcad_batch_set_tiling,
     pcad_server_create, pcad_server_destroy, pcad_server_info, pcad_server_poll,
-    pcad_server_step, pcad_server_submit, pcad_server_set_limits,
+    pcad_server_step, pcad_server_submit, pcad_server_set_limits, pcad_server_set_policy,
+    SERVE_FIFO, SERVE_SRPT,
 )

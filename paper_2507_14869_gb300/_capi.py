@@ -134,6 +134,7 @@ def _declare(L):
         "pcad_server_create": [ctypes.c_int, ctypes.c_size_t, vp, ctypes.POINTER(vp)],
         "pcad_server_submit": [vp, ctypes.POINTER(PcadJob), ctypes.c_int, u64p],
         "pcad_server_set_limits": [vp, ctypes.c_size_t],
+        "pcad_server_set_policy": [vp, ctypes.c_int, ctypes.c_double],
         "pcad_server_step": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "pcad_server_poll": [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int), u8p, fp],
@@ -541,6 +542,14 @@ def pcad_server_create(max_slots: int, hbm_budget_bytes: int, stream=None):
 def pcad_server_set_limits(h, max_active_sites: int):
     """Admit while the admitted requests hold fewer sites (0: no cap)."""
     _check("pcad_server_set_limits", lib().pcad_server_set_limits(h, int(max_active_sites)))
+
+
+SERVE_FIFO, SERVE_SRPT = 0, 1
+
+
+def pcad_server_set_policy(h, policy: int, aging: float = 0.2):
+    """FIFO (every admitted request runs) or shortest remaining work first."""
+    _check("pcad_server_set_policy", lib().pcad_server_set_policy(h, int(policy), float(aging)))
 
 
 def pcad_server_submit(h, g, model, seed, chain_id, burn_in, nsweeps) -> int:

@@ -18,6 +18,7 @@
 // next to whatever else is active, and leave when their budget is spent; the
 // caller collects results with pcad_server_poll.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -40,6 +41,8 @@ constexpr int kOrderWave = 2;     // batch work order: one wavefront launch per 
 // active set has at least 4 tiles of 4 rows per resident block (measured on
 // single requests of 300^2..1376^2 and on a 50 req/s mix).
 constexpr int kServeTallTiles = 4;
+// SRPT server: least estimated GPU time of a full slice of the run set.
+constexpr double kMinSliceSeconds = 1e-3;
 constexpr size_t kAlign = 256;
 constexpr int kTableBytes = 4096;  // 511 doubles
 
@@ -895,14 +898,35 @@ struct Request {
     pcad_job job{};
     std::vector<uint8_t> g;      // host copy of the observation (pitch W)
     int nsweeps = 0;
-    int state = 0;               // 0 pending, 1 running, 2 done
+    int state = 0;               // 0 pending, 1 admitted (slot and memory held), 2 done
+    bool running = false;        // admitted and in the current slice's run set
     int slot = -1;
     uint64_t t = 0;              // sweeps done (host mirror)
     size_t bytes = 0;
     void *mem = nullptr;
+    double t_submit = 0.0;       // seconds (steady clock)
+    double unit_cost = 0.0;      // estimated seconds per site-update
     std::vector<uint8_t> sample;
     std::vector<float> mean;
 };
+
+double now_s()
+{
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// Estimated GB300 seconds per site-update of a model, for the scheduling
+// order only (results never depend on it): the tensor-core sweep at
+// L >= 192 (1.07e10 site-updates/s), else the CUDA-core kernels, whose time
+// grows with L (measured 1.1e11 at L = 2, 4.9e10 at L = 16).
+double unit_cost(const pcad_model &m)
+{
+    const int T = m.pair == PCAD_PAIR_POTTS ? 1 : m.pair_T;
+    if (m.L >= kTcAutoLabels && T <= kTcMaxT && m.inertia_norm == 0)
+        return 9.3e-11;
+    return 7.4e-12 + 8.1e-13 * m.L;
+}
 
 }  // namespace
 
@@ -924,8 +948,11 @@ struct pcad_server {
     int *h_err = nullptr;          // pinned: the flag after each of the last two slices
     cudaEvent_t ev[2] = {nullptr, nullptr};
     bool in_flight = false;        // the previous slice may still be running
-    size_t max_active_sites = 0;   // admission cap on the admitted requests' sites (0: none)
+    size_t max_active_sites = 0;   // FIFO: admission cap on the admitted requests' sites (0: none)
+                                   // SRPT: run-set size in sites (0: two waves of tiles)
     size_t active_sites = 0;
+    int policy = PCAD_SERVE_SRPT;
+    double aging = 0.2;            // SRPT: priority seconds gained per second waited
     std::vector<SlotDesc> desc;
     std::vector<uint64_t> slot_req;   // 0 = free
     std::deque<uint64_t> pending;
@@ -936,53 +963,143 @@ struct pcad_server {
 
 namespace {
 
-pcad_status server_admit(pcad_server *sv)
+int free_slot(const pcad_server *sv)
+{
+    for (int i = 0; i < sv->max_slots; ++i)
+        if (sv->slot_req[i] == 0)
+            return i;
+    return -1;
+}
+
+// Give request rq (pending, taken off the queue by the caller) slot `slot`
+// and its device memory, copy its observation and initialise its state.
+pcad_status admit_one(pcad_server *sv, Request &rq, int slot)
+{
+    cudaError_t e = cudaMallocAsync(&rq.mem, rq.bytes, sv->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(PCAD_ENOMEM, cudaGetErrorString(e));
+    }
+    const int pitch = (rq.job.W + 15) / 16 * 16;
+    SlotMem sm = job_layout(rq.job, pitch, 0);
+    pcad_job j = rq.job;
+    j.g_host = rq.g.data();
+    j.g_pitch = rq.job.W;
+    SlotDesc d{};
+    pcad_status st = init_slot(j, (char *)rq.mem, sm, pitch, sv->d_t + slot,
+                               sv->d_budget + slot, sv->d_fp64 + slot, sv->stream, d);
+    if (st != PCAD_OK)
+        return st;
+    const uint32_t zero = 0, bud = (uint32_t)rq.nsweeps;
+    const unsigned long long z64 = 0;
+    B_TRY(cudaMemcpyAsync(sv->d_t + slot, &zero, 4, cudaMemcpyHostToDevice, sv->stream));
+    B_TRY(cudaMemcpyAsync(sv->d_budget + slot, &bud, 4, cudaMemcpyHostToDevice, sv->stream));
+    B_TRY(cudaMemcpyAsync(sv->d_fp64 + slot, &z64, 8, cudaMemcpyHostToDevice, sv->stream));
+    B_TRY(cudaMemcpyAsync(sv->d_slots + slot, &d, sizeof(d), cudaMemcpyHostToDevice,
+                          sv->stream));
+    sv->desc[slot] = d;
+    sv->slot_req[slot] = rq.id;
+    sv->used += rq.bytes;
+    sv->active_sites += (size_t)rq.job.H * rq.job.W;
+    rq.slot = slot;
+    rq.state = 1;
+    rq.running = true;
+    rq.t = 0;
+    sv->items_dirty = true;
+    return PCAD_OK;
+}
+
+// First come, first served: admit from the head of the queue while a slot,
+// the HBM budget and the admission cap allow; every admitted request runs.
+pcad_status server_admit_fifo(pcad_server *sv)
 {
     while (!sv->pending.empty()) {
         Request &rq = sv->reqs[sv->pending.front()];
-        int slot = -1;
-        for (int i = 0; i < sv->max_slots; ++i)
-            if (sv->slot_req[i] == 0) {
-                slot = i;
-                break;
-            }
+        const int slot = free_slot(sv);
         const size_t sites = (size_t)rq.job.H * rq.job.W;
         if (slot < 0 || sv->used + rq.bytes > sv->budget)
-            break;   // first-come first-served: wait for slots or memory
+            break;   // wait for slots or memory
         if (sv->max_active_sites && sv->active_sites > 0 &&
             sv->active_sites + sites > sv->max_active_sites)
             break;   // enough work admitted: the GPU is full, the next one waits
-        sv->active_sites += sites;
         sv->pending.pop_front();
-        cudaError_t e = cudaMallocAsync(&rq.mem, rq.bytes, sv->stream);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
+        pcad_status st = admit_one(sv, rq, slot);
+        if (st != PCAD_OK) {
             sv->pending.push_front(rq.id);
-            return set_error(PCAD_ENOMEM, cudaGetErrorString(e));
-        }
-        const int pitch = (rq.job.W + 15) / 16 * 16;
-        SlotMem sm = job_layout(rq.job, pitch, 0);
-        pcad_job j = rq.job;
-        j.g_host = rq.g.data();
-        j.g_pitch = rq.job.W;
-        SlotDesc d{};
-        pcad_status st = init_slot(j, (char *)rq.mem, sm, pitch, sv->d_t + slot,
-                                   sv->d_budget + slot, sv->d_fp64 + slot, sv->stream, d);
-        if (st != PCAD_OK)
             return st;
-        const uint32_t zero = 0, bud = (uint32_t)rq.nsweeps;
-        const unsigned long long z64 = 0;
-        B_TRY(cudaMemcpyAsync(sv->d_t + slot, &zero, 4, cudaMemcpyHostToDevice, sv->stream));
-        B_TRY(cudaMemcpyAsync(sv->d_budget + slot, &bud, 4, cudaMemcpyHostToDevice, sv->stream));
-        B_TRY(cudaMemcpyAsync(sv->d_fp64 + slot, &z64, 8, cudaMemcpyHostToDevice, sv->stream));
-        B_TRY(cudaMemcpyAsync(sv->d_slots + slot, &d, sizeof(d), cudaMemcpyHostToDevice,
-                              sv->stream));
-        sv->desc[slot] = d;
-        sv->slot_req[slot] = rq.id;
-        sv->used += rq.bytes;
-        rq.slot = slot;
-        rq.state = 1;
-        rq.t = 0;
+        }
+    }
+    return PCAD_OK;
+}
+
+// Shortest remaining work first, with aging: every step orders the queued
+// and admitted requests by estimated remaining GPU time (sites x sweeps
+// left x unit cost) minus `aging` x time waited since submission, and runs
+// the shortest ones until the run set holds the fill target of sites (at
+// least one request), admitting queued ones as slots and the HBM budget
+// allow.  Admitted requests outside the run set keep their state on the
+// device and pause (their descriptor is marked inactive, so the slice's
+// launches and the counter advance skip them).  Under overload this
+// finishes short requests first instead of sharing the GPU among all of
+// them; aging bounds how long a long request can be passed over.
+pcad_status server_schedule_srpt(pcad_server *sv)
+{
+    const double now = now_s();
+    std::vector<std::pair<double, uint64_t>> order;
+    order.reserve(sv->reqs.size());
+    for (auto &kv : sv->reqs) {
+        const Request &rq = kv.second;
+        if (rq.state == 2)
+            continue;
+        const double left = (double)rq.job.H * rq.job.W * (double)(rq.nsweeps - rq.t);
+        order.emplace_back(left * rq.unit_cost - sv->aging * (now - rq.t_submit), rq.id);
+    }
+    std::sort(order.begin(), order.end());
+    const size_t fill = sv->max_active_sites
+                            ? sv->max_active_sites
+                            : (size_t)2 * (size_t)std::max(sv->grid, 1) * 128;
+    // without an explicit target, also at least kMinSliceSeconds of estimated
+    // work per slice, so the host's per-slice cost stays small against it
+    const double min_time = sv->max_active_sites ? 0.0 : kMinSliceSeconds;
+    size_t run_sites = 0;
+    double run_time = 0.0;    // estimated seconds per sweep of the run set
+    std::vector<uint64_t> run;
+    for (const auto &pr : order) {
+        if (!run.empty() && run_sites >= fill && run_time * kSlice >= min_time)
+            break;
+        Request &rq = sv->reqs[pr.second];
+        if (rq.state == 0) {
+            const int slot = free_slot(sv);
+            if (slot < 0 || sv->used + rq.bytes > sv->budget)
+                continue;   // no room now: a shorter one may still fit
+            auto it = std::find(sv->pending.begin(), sv->pending.end(), rq.id);
+            if (it != sv->pending.end())
+                sv->pending.erase(it);
+            pcad_status st = admit_one(sv, rq, slot);
+            if (st != PCAD_OK) {
+                sv->pending.push_front(rq.id);
+                return st;
+            }
+        }
+        run.push_back(rq.id);
+        run_sites += (size_t)rq.job.H * rq.job.W;
+        run_time += (double)rq.job.H * rq.job.W * rq.unit_cost;
+    }
+    // pause or resume the admitted requests
+    std::vector<char> in_run(sv->max_slots, 0);
+    for (uint64_t id : run)
+        in_run[sv->reqs[id].slot] = 1;
+    for (int i = 0; i < sv->max_slots; ++i) {
+        if (sv->slot_req[i] == 0)
+            continue;
+        Request &rq = sv->reqs[sv->slot_req[i]];
+        const bool want = in_run[i] != 0;
+        if (want == rq.running && sv->desc[i].active == (want ? 1 : 0))
+            continue;
+        rq.running = want;
+        sv->desc[i].active = want ? 1 : 0;
+        B_TRY(cudaMemcpyAsync(sv->d_slots + i, &sv->desc[i], sizeof(SlotDesc),
+                              cudaMemcpyHostToDevice, sv->stream));
         sv->items_dirty = true;
     }
     return PCAD_OK;
@@ -990,9 +1107,9 @@ pcad_status server_admit(pcad_server *sv)
 
 pcad_status server_items(pcad_server *sv)
 {
-    std::vector<int> all, active;
+    std::vector<int> all, active;   // the run set, then those not on the tensor-core sweep
     for (int i = 0; i < sv->max_slots; ++i)
-        if (sv->slot_req[i] != 0)
+        if (sv->slot_req[i] != 0 && sv->reqs[sv->slot_req[i]].running)
             all.push_back(i);
     // requests with a tensor-core table run on the batched tensor-core sweep
     pcad_status st = tc_set_build(sv->tc, sv->desc, all, active, sv->stream);
@@ -1088,6 +1205,31 @@ pcad_status pcad_server_set_limits(pcad_server *sv, size_t max_active_sites)
     return PCAD_OK;
 }
 
+pcad_status pcad_server_set_policy(pcad_server *sv, int policy, double aging)
+{
+    if (!sv)
+        return set_error(PCAD_EINVAL, "server is NULL");
+    if (policy != PCAD_SERVE_FIFO && policy != PCAD_SERVE_SRPT)
+        return set_error(PCAD_EINVAL, "policy must be PCAD_SERVE_FIFO or PCAD_SERVE_SRPT");
+    if (!(aging >= 0.0 && aging <= 1e6))
+        return set_error(PCAD_EINVAL, "aging must lie in [0, 1e6]");
+    if (policy == PCAD_SERVE_FIFO && sv->policy != PCAD_SERVE_FIFO) {
+        // every admitted request runs again under FIFO
+        for (int i = 0; i < sv->max_slots; ++i) {
+            if (sv->slot_req[i] == 0 || sv->desc[i].active)
+                continue;
+            sv->reqs[sv->slot_req[i]].running = true;
+            sv->desc[i].active = 1;
+            B_TRY(cudaMemcpyAsync(sv->d_slots + i, &sv->desc[i], sizeof(SlotDesc),
+                                  cudaMemcpyHostToDevice, sv->stream));
+            sv->items_dirty = true;
+        }
+    }
+    sv->policy = policy;
+    sv->aging = aging;
+    return PCAD_OK;
+}
+
 pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps, uint64_t *id)
 {
     if (!sv || !job || !id)
@@ -1106,6 +1248,8 @@ pcad_status pcad_server_submit(pcad_server *sv, const pcad_job *job, int nsweeps
     rq.job.g_host = nullptr;
     rq.nsweeps = nsweeps;
     rq.bytes = slot_bytes(*job);
+    rq.t_submit = now_s();
+    rq.unit_cost = unit_cost(job->model);
     if (rq.bytes > sv->budget)
         return set_error(PCAD_ENOMEM, "request larger than the whole HBM budget");
     rq.g.resize((size_t)job->H * job->W);
@@ -1122,7 +1266,8 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
 {
     if (!sv || slice_sweeps < 1 || slice_sweeps > kSlice)
         return set_error(PCAD_EINVAL, "slice_sweeps must be in [1, 16]");
-    pcad_status st = server_admit(sv);
+    pcad_status st =
+        sv->policy == PCAD_SERVE_FIFO ? server_admit_fifo(sv) : server_schedule_srpt(sv);
     if (st != PCAD_OK)
         return st;
     if (sv->items_dirty) {
@@ -1150,6 +1295,10 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
             if (sv->slot_req[i] == 0)
                 continue;
             Request &rq = sv->reqs[sv->slot_req[i]];
+            if (!rq.running) {   // paused this slice
+                ++active;
+                continue;
+            }
             rq.t = std::min<uint64_t>(rq.t + slice_sweeps, (uint64_t)rq.nsweeps);
             if (rq.t < (uint64_t)rq.nsweeps) {
                 ++active;
@@ -1177,6 +1326,7 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
             sv->active_sites -= (size_t)d.H * d.W;
             sv->slot_req[i] = 0;
             rq.state = 2;
+            rq.running = false;
             rq.slot = -1;
             sv->items_dirty = true;
             ++finished;

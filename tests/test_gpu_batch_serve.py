@@ -264,6 +264,7 @@ def test_server_admission_cap(pc):
     g, m, seed, chain, burn = jobs[8]            # 100 x 100
     sv = pc.pcad_server_create(16, 1 << 30)
     try:
+        pc.pcad_server_set_policy(sv, pc.SERVE_FIFO)
         pc.pcad_server_set_limits(sv, 15_000)     # one 100 x 100 request at a time
         ids = [pc.pcad_server_submit(sv, g, m, seed, chain + k, burn, 32) for k in range(3)]
         act, pend, fin = pc.pcad_server_step(sv, 16)
@@ -277,5 +278,63 @@ def test_server_admission_cap(pc):
         rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, 25)
         res = _serve_until_done(pc, sv, [rid], {rid: g.shape})
         assert np.array_equal(res[rid][0], _alone(pc, g, m, seed, chain, burn, 25)[0])
+    finally:
+        pc.pcad_server_destroy(sv)
+
+
+def test_server_srpt_runs_short_requests_first_and_pauses_long_ones(pc):
+    """Shortest remaining work first: with a run set of one request, a short
+    request submitted while a long one runs preempts it and finishes first;
+    the long one pauses (its state stays on the device) and resumes.  Both
+    results equal the chains run alone, and equal the FIFO server's."""
+    jobs = _jobs()
+    lg, lm, ls, lc, lb = jobs[8]            # 100 x 100, L = 16
+    sg, sm, ss, sc, sb = jobs[2]            # 67 x 45, L = 16
+    outs = {}
+    for policy in (pc.SERVE_SRPT, pc.SERVE_FIFO):
+        sv = pc.pcad_server_create(8, 1 << 30)
+        try:
+            pc.pcad_server_set_policy(sv, policy, 0.0)
+            pc.pcad_server_set_limits(sv, 1)  # SRPT: one request per slice; FIFO: one admitted
+            lid = pc.pcad_server_submit(sv, lg, lm, ls, lc, lb, 80)
+            pc.pcad_server_step(sv, 16)       # the long request runs 16 sweeps
+            sid = pc.pcad_server_submit(sv, sg, sm, ss, sc, sb, 32)
+            finished_first = None
+            res = {}
+            for _ in range(100):
+                pc.pcad_server_step(sv, 16)
+                for rid, shape in ((lid, lg.shape), (sid, sg.shape)):
+                    if rid in res:
+                        continue
+                    st, smp, mean = pc.pcad_server_poll(sv, rid, *shape)
+                    if st == 2:
+                        res[rid] = (smp, mean)
+                        finished_first = finished_first or rid
+                if len(res) == 2:
+                    break
+            assert len(res) == 2
+            if policy == pc.SERVE_SRPT:
+                assert finished_first == sid   # 32 x 3015 sites left against 64 x 10^4
+            else:
+                assert finished_first == lid
+            outs[policy] = (res[lid], res[sid])
+        finally:
+            pc.pcad_server_destroy(sv)
+    xl, ml = _alone(pc, lg, lm, ls, lc, lb, 80)
+    xs, ms = _alone(pc, sg, sm, ss, sc, sb, 32)
+    for (l_out, s_out) in outs.values():
+        assert np.array_equal(l_out[0], xl) and np.array_equal(l_out[1], ml)
+        assert np.array_equal(s_out[0], xs) and np.array_equal(s_out[1], ms)
+
+
+def test_server_policy_is_validated(pc):
+    sv = pc.pcad_server_create(2, 1 << 20)
+    try:
+        for policy, aging in ((2, 0.1), (-1, 0.1), (1, -0.5), (1, float("nan"))):
+            with pytest.raises(pc.PcadError) as e:
+                pc.pcad_server_set_policy(sv, policy, aging)
+            assert e.value.status == 1
+        pc.pcad_server_set_policy(sv, pc.SERVE_FIFO, 0.0)
+        pc.pcad_server_set_policy(sv, pc.SERVE_SRPT, 3.0)
     finally:
         pc.pcad_server_destroy(sv)
