@@ -378,6 +378,7 @@ def run_ours(a):
     if not a.only_head:
         side["config3"] = _safe(_config3, pc, stream, timed, x_head, ms_sweep, pca_kind,
                                 hbm_peak, cid)
+        side["bands"] = _safe(_bands_8192, pc, torch, noisy, m, cid, x_head, value / world)
         if not a.no_gibbs:
             side["gibbs"] = _safe(_gibbs_8192, pc, stream, timed, noisy, m, clean, cid)
         side["greyscale512"] = _safe(_greyscale512, pc, stream, timed, cid, a.no_gibbs)
@@ -470,6 +471,36 @@ def _config3(pc, stream, timed, x_head, ms_head, head_kind, hbm_peak, cid):
                 r["hbm_frac"] = hbm["frac"]
             rows[name] = r
     return out
+
+
+def _bands_8192(pc, torch, noisy, m, cid, x_head, head_rate, nbands=2, halo=32):
+    """The headline chain split into row bands on this one GPU (one chain and
+    stream per band, halo rows exchanged after every 32 sweeps): the cost of
+    the decomposition a multi-GPU run would use, and its bit-identity."""
+    import numpy as np
+    H, W = noisy.shape
+    b = pc.pcad_bands_create(noisy, m, seed=3, chain_id=cid, burn_in=BURN_IN, nbands=nbands,
+                             halo=halo)
+    try:
+        pc.pcad_bands_run(b, 32)
+        pc.pcad_bands_sync(b)
+        b2 = pc.pcad_bands_create(noisy, m, seed=3, chain_id=cid, burn_in=BURN_IN,
+                                  nbands=nbands, halo=halo)
+    finally:
+        pc.pcad_bands_destroy(b)
+    try:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pc.pcad_bands_run(b2, SWEEPS)
+        pc.pcad_bands_sync(b2)
+        dt = time.perf_counter() - t0
+        same = bool(np.array_equal(pc.pcad_bands_read_sample(b2, H, W), x_head))
+    finally:
+        pc.pcad_bands_destroy(b2)
+    rate = H * W * SWEEPS / dt
+    return {"nbands": nbands, "halo_rows": halo, "site_updates_per_s": rate,
+            "vs_whole_image": rate / head_rate, "identical_labels": same,
+            "note": "host-timed; both bands on one GPU, each on its own stream"}
 
 
 def _gibbs_8192(pc, stream, timed, noisy, m, clean, cid, steps=2):

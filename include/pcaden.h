@@ -251,6 +251,25 @@ pcad_status pcad_chain_set_wait_limit(pcad_chain *ch, double seconds);
  * no other kernel is affected. */
 pcad_status pcad_chain_inject_stall(pcad_chain *ch, int tile);
 
+/* Row offset of a chain that holds a band of rows of a larger image: its
+ * local row r is global row r + row_off, and the Philox counter of every
+ * draw uses the global row (DRAWS), so a band draws what the whole-image
+ * chain draws at those rows.  row_off in [0, 2^30]; PCAD_EINVAL otherwise
+ * or for the Gibbs sampler (its colour classes follow the local rows).
+ * Exported with the chain.  Applies to sweeps queued after the call.  The
+ * row-band runner below uses it; a multi-process runner (one band per
+ * rank) uses it with pcad_chain_write_rows_dev for its halo exchange. */
+pcad_status pcad_chain_set_row_offset(pcad_chain *ch, int row_off);
+
+/* Overwrite rows [row0, row0 + nrows) of the current state with nrows rows
+ * of W labels from device (or peer / host-mapped) memory at src_dev, row
+ * pitch src_pitch; stream-ordered on the chain's stream, asynchronous.  The
+ * labels must be < L (not checked here: a halo exchange copies labels that
+ * another band of the same model drew).  PCAD_EINVAL for rows outside the
+ * chain or src_pitch < W. */
+pcad_status pcad_chain_write_rows_dev(pcad_chain *ch, int row0, int nrows, const uint8_t *src_dev,
+                                      int src_pitch);
+
 /* Block until the chain's queued work is done. */
 pcad_status pcad_chain_sync(pcad_chain *ch);
 
@@ -409,6 +428,39 @@ pcad_status pcad_server_poll(pcad_server *sv, uint64_t id, int *state, uint8_t *
 pcad_status pcad_server_info(pcad_server *sv, size_t *hbm_used, uint64_t *slices,
                              uint64_t *fp64_draws);
 void pcad_server_destroy(pcad_server *sv);
+
+/* ------------------------------------------------------------ row bands
+ * One image split into nbands bands of whole rows, each run by its own chain
+ * (on its own stream, and on devices[b] when devices is not NULL; NULL puts
+ * every band on the current device).  The lazy PCA updates every site from
+ * the previous state only (Section 3, Eq. general_pca_definition), so a
+ * label after k sweeps depends only on sites within k rows: band b owns rows
+ * [floor(b H / nbands), floor((b + 1) H / nbands)) and its chain holds
+ * `halo` extra rows on each inner side; after every block of `halo` sweeps
+ * each band copies its neighbours' owned rows into its halo rows (device to
+ * device, peer copies across devices).  Draws are keyed by the global row,
+ * so the sample and posterior mean equal the whole-image chain's bit for
+ * bit.  Limits: 1 <= nbands <= 64, 1 <= halo <= 64, every band owns at
+ * least `halo` rows, lazy PCA only (PCAD_EINVAL otherwise).  g_host is
+ * copied; the image size limits of pcad_chain_create apply per band. */
+typedef struct pcad_bands pcad_bands;
+pcad_status pcad_bands_create(const uint8_t *g_host, int H, int W, int g_pitch,
+                              const pcad_model *m, uint64_t seed, uint32_t chain_id, int burn_in,
+                              int nbands, int halo, const int *devices, pcad_bands **out);
+/* nsweeps sweeps of every band, in blocks of `halo` with an exchange after
+ * each (asynchronous on the bands' streams). */
+pcad_status pcad_bands_run(pcad_bands *b, int nsweeps);
+/* Wait for every band; PCAD_ETIMEOUT if a band's bounded wait gave up. */
+pcad_status pcad_bands_sync(pcad_bands *b);
+/* The whole image's sample (H rows of W bytes, pitch out_pitch) and posterior
+ * mean (H x W floats) assembled from the bands' owned rows (synchronous). */
+pcad_status pcad_bands_read_sample(pcad_bands *b, uint8_t *host_out, int out_pitch);
+pcad_status pcad_bands_read_mean(pcad_bands *b, float *host_out);
+/* Band `band`'s owned rows [*own_row0, *own_row1), its chain's rows
+ * [*buf_row0, *buf_row1) and the sweeps run so far (any pointer may be NULL). */
+pcad_status pcad_bands_info(const pcad_bands *b, int band, int *own_row0, int *own_row1,
+                            int *buf_row0, int *buf_row1, uint64_t *t);
+void pcad_bands_destroy(pcad_bands *b);
 
 /* Allocation-free lazy-PCA run (no counterpart in the paper: a library
  * convenience).  For callers that must not allocate device memory: the GPU

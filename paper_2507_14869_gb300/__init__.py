@@ -11,7 +11,10 @@ from ._capi import (  # noqa: F401
     pcad_chain_create, pcad_chain_create_dev, pcad_chain_destroy, pcad_chain_export,
     pcad_chain_import, pcad_chain_metrics, pcad_chain_read_mean, pcad_chain_read_sample,
     pcad_chain_read_sample_dev, pcad_chain_reset, pcad_chain_run, pcad_chain_set_blocking, pcad_chain_stats, pcad_chain_sweeps,
-    pcad_chain_set_kernel, pcad_chain_set_wait_limit, pcad_chain_inject_stall, PCAD_KERNEL_AUTO, PCAD_KERNEL_CUDA_CORE, PCAD_KERNEL_TENSOR, PCAD_KERNEL_WAVE,
+    pcad_chain_set_kernel, pcad_chain_set_wait_limit, pcad_chain_inject_stall, PCAD_KERNEL_AUTO,
+    pcad_chain_set_row_offset, pcad_chain_write_rows_dev,
+    pcad_bands_create, pcad_bands_run, pcad_bands_sync, pcad_bands_read_sample,
+    pcad_bands_read_mean, pcad_bands_info, pcad_bands_destroy, PCAD_KERNEL_CUDA_CORE, PCAD_KERNEL_TENSOR, PCAD_KERNEL_WAVE,
     pcad_chain_energy, pcad_chain_track_energy, pcad_chain_read_energies,
     pcad_chain_read_min_state, pcad_chain_kernel_in_use, pcad_chain_set_model, pcad_chain_run_schedule,
     pcad_batch_set_model,

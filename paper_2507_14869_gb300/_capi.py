@@ -102,6 +102,18 @@ def _declare(L):
         "pcad_chain_set_blocking": [vp, ctypes.c_int],
         "pcad_chain_set_kernel": [vp, ctypes.c_int],
         "pcad_chain_set_wait_limit": [vp, ctypes.c_double],
+        "pcad_chain_set_row_offset": [vp, ctypes.c_int],
+        "pcad_chain_write_rows_dev": [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int],
+        "pcad_bands_create": [u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, mp, ctypes.c_uint64,
+                              ctypes.c_uint32, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                              ctypes.POINTER(ctypes.c_int), ctypes.POINTER(vp)],
+        "pcad_bands_run": [vp, ctypes.c_int],
+        "pcad_bands_sync": [vp],
+        "pcad_bands_read_sample": [vp, u8p, ctypes.c_int],
+        "pcad_bands_read_mean": [vp, fp],
+        "pcad_bands_info": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int), u64p],
         "pcad_chain_inject_stall": [vp, ctypes.c_int],
         "pcad_chain_kernel_in_use": [vp, ctypes.POINTER(ctypes.c_int)],
         "pcad_chain_energy": [vp, dp, u64p, u64p],
@@ -153,6 +165,8 @@ def _declare(L):
     L.pcad_batch_destroy.restype = None
     L.pcad_server_destroy.argtypes = [vp]
     L.pcad_server_destroy.restype = None
+    L.pcad_bands_destroy.argtypes = [vp]
+    L.pcad_bands_destroy.restype = None
     L.pcad_status_str.argtypes = [ctypes.c_int]
     L.pcad_status_str.restype = ctypes.c_char_p
     L.pcad_last_error.argtypes = []
@@ -389,6 +403,14 @@ class Chain:
 
     def inject_stall(self, tile: int):
         pcad_chain_inject_stall(self.h, tile)
+        return self
+
+    def set_row_offset(self, row_off: int):
+        pcad_chain_set_row_offset(self.h, row_off)
+        return self
+
+    def write_rows_dev(self, row0: int, nrows: int, src_ptr: int, src_pitch: int):
+        pcad_chain_write_rows_dev(self.h, row0, nrows, src_ptr, src_pitch)
         return self
 
     def set_model(self, model):
@@ -679,6 +701,67 @@ def pcad_chain_set_kernel(h, kind: int):
 def pcad_chain_set_wait_limit(h, seconds: float):
     """Elapsed-time limit of every bounded device-side wait of the chain's sweeps."""
     _check("pcad_chain_set_wait_limit", lib().pcad_chain_set_wait_limit(h, float(seconds)))
+
+
+def pcad_chain_set_row_offset(h, row_off: int):
+    """Global row of the chain's local row 0 (a band of a larger image)."""
+    _check("pcad_chain_set_row_offset", lib().pcad_chain_set_row_offset(h, int(row_off)))
+
+
+def pcad_chain_write_rows_dev(h, row0: int, nrows: int, src_ptr: int, src_pitch: int):
+    """Overwrite rows of the current state from device memory (stream-ordered)."""
+    _check("pcad_chain_write_rows_dev",
+           lib().pcad_chain_write_rows_dev(h, int(row0), int(nrows), ctypes.c_void_p(int(src_ptr)),
+                                           int(src_pitch)))
+
+
+def pcad_bands_create(g, model, seed: int, chain_id: int = 0, burn_in: int = 0, nbands: int = 2,
+                      halo: int = 32, devices=None):
+    g = _u8(g)
+    H, W = g.shape
+    m = as_model(model)
+    h = ctypes.c_void_p()
+    dv = None if devices is None else (ctypes.c_int * len(devices))(*[int(d) for d in devices])
+    _check("pcad_bands_create",
+           lib().pcad_bands_create(g.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), H, W, W,
+                                   ctypes.byref(m), int(seed), int(chain_id), int(burn_in),
+                                   int(nbands), int(halo), dv, ctypes.byref(h)))
+    return h
+
+
+def pcad_bands_run(h, nsweeps: int):
+    _check("pcad_bands_run", lib().pcad_bands_run(h, int(nsweeps)))
+
+
+def pcad_bands_sync(h):
+    _check("pcad_bands_sync", lib().pcad_bands_sync(h))
+
+
+def pcad_bands_read_sample(h, H: int, W: int) -> np.ndarray:
+    out = np.zeros((H, W), dtype=np.uint8)
+    _check("pcad_bands_read_sample",
+           lib().pcad_bands_read_sample(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), W))
+    return out
+
+
+def pcad_bands_read_mean(h, H: int, W: int) -> np.ndarray:
+    out = np.zeros((H, W), dtype=np.float32)
+    _check("pcad_bands_read_mean",
+           lib().pcad_bands_read_mean(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+    return out
+
+
+def pcad_bands_info(h, band: int) -> dict:
+    v = [ctypes.c_int() for _ in range(4)]
+    t = ctypes.c_uint64()
+    _check("pcad_bands_info", lib().pcad_bands_info(h, int(band), *[ctypes.byref(x) for x in v],
+                                                    ctypes.byref(t)))
+    return dict(own0=v[0].value, own1=v[1].value, buf0=v[2].value, buf1=v[3].value, t=t.value)
+
+
+def pcad_bands_destroy(h):
+    if h is not None and h.value:
+        lib().pcad_bands_destroy(h)
 
 
 def pcad_chain_inject_stall(h, tile: int):

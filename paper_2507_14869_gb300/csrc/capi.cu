@@ -251,6 +251,7 @@ struct pcad_chain {
     CUtensorMap gmap;             // and of the observation
     int *err = nullptr;           // bounded-wait timeout flag (device)
     long long wait_ns = 0;        // limit of each bounded device wait (0: the default, 1 s)
+    int row_off = 0;              // global row of local row 0 (a band of a larger image)
     int stall_tile = 0;           // test aid: wavefront tile stall_tile - 1 never publishes
     unsigned long long *esums = nullptr;   // energy reduction sums (device, 2 x u64)
     EnergyCoef ecoef{};
@@ -278,6 +279,7 @@ SweepArgs make_args(const pcad_chain *ch)
     a.burn_in = ch->burn_in;
     a.wait_ns = ch->wait_ns;
     a.stall_tile = ch->stall_tile;
+    a.row_off = ch->row_off;
     a.m = ch->dm;
     return a;
 }
@@ -910,6 +912,36 @@ pcad_status pcad_chain_inject_stall(pcad_chain *ch, int tile)
     return PCAD_OK;
 }
 
+pcad_status pcad_chain_set_row_offset(pcad_chain *ch, int row_off)
+{
+    if (!ch)
+        return fail(PCAD_EINVAL, "chain is NULL");
+    if (row_off < 0 || row_off > kMaxRowOffset)
+        return fail(PCAD_EINVAL, "row offset must lie in [0, %d]", kMaxRowOffset);
+    if (ch->model.sampler != PCAD_SAMPLER_PCA && row_off != 0)
+        return fail(PCAD_EINVAL, "row bands run the lazy PCA sampler");
+    if (row_off != ch->row_off) {
+        drop_graph(ch);
+        ch->row_off = row_off;
+    }
+    return PCAD_OK;
+}
+
+pcad_status pcad_chain_write_rows_dev(pcad_chain *ch, int row0, int nrows, const uint8_t *src_dev,
+                                      int src_pitch)
+{
+    if (!ch || !src_dev)
+        return fail(PCAD_EINVAL, "NULL argument");
+    if (row0 < 0 || nrows < 0 || row0 + nrows > ch->H || src_pitch < ch->W)
+        return fail(PCAD_EINVAL, "rows [%d, %d) outside the chain's %d rows or src_pitch < W",
+                    row0, row0 + nrows, ch->H);
+    if (nrows == 0)
+        return PCAD_OK;
+    CUDA_TRY(cudaMemcpy2DAsync(ch->x[ch->cur] + (size_t)row0 * ch->pitch, ch->pitch, src_dev,
+                               src_pitch, ch->W, nrows, cudaMemcpyDefault, ch->stream));
+    return PCAD_OK;
+}
+
 pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k)
 {
     if (!ch)
@@ -1088,7 +1120,7 @@ struct BlobHeader {
     pcad_model model;
     uint64_t seed;
     uint32_t chain_id;
-    uint32_t pad;
+    int32_t row_off;     // 0 for a whole image
     uint64_t t, n_acc, fp64;
 };
 const char kMagic[8] = {'P', 'C', 'A', 'D', 'C', 'H', 'N', '1'};
@@ -1115,6 +1147,7 @@ pcad_status pcad_chain_export(pcad_chain *ch, void *host_blob, size_t *bytes)
     h.model = ch->model;
     h.seed = ch->seed;
     h.chain_id = ch->chain_id;
+    h.row_off = ch->row_off;
     h.t = ch->t;
     h.n_acc = ch->n_acc;
     pcad_status st = pcad_chain_stats(ch, &h.fp64);
@@ -1146,7 +1179,8 @@ pcad_status pcad_chain_import(const void *host_blob, size_t bytes, void *cuda_st
     memcpy(&h, host_blob, sizeof(h));
     if (memcmp(h.magic, kMagic, 8) != 0 || h.version != 1)
         return fail(PCAD_EINVAL, "not a pcaden chain blob");
-    if (h.H < 1 || h.W < 1 || h.H > 65535 || h.W > 65535 || h.t > 0xFFFFFFFFull)
+    if (h.H < 1 || h.W < 1 || h.H > 65535 || h.W > 65535 || h.t > 0xFFFFFFFFull ||
+        h.row_off < 0 || h.row_off > kMaxRowOffset)
         return fail(PCAD_EINVAL, "corrupt blob header");
     const size_t n = (size_t)h.H * h.W;
     if (bytes < sizeof(h) + 2 * n + n * sizeof(float))
@@ -1157,6 +1191,7 @@ pcad_status pcad_chain_import(const void *host_blob, size_t bytes, void *cuda_st
                                        &h.model, h.seed, h.chain_id, h.burn_in, cuda_stream, &ch);
     if (st != PCAD_OK)
         return st;
+    ch->row_off = h.row_off;
     st = pcad_chain_write_sample(ch, (const uint8_t *)(b + sizeof(h)), h.W);
     if (st != PCAD_OK) {
         pcad_chain_destroy(ch);
@@ -1246,5 +1281,9 @@ void model_tables(const pcad_model &m, double *ta64, std::vector<double> &pr64, 
 }
 
 pcad_status set_error(pcad_status st, const char *msg) { return fail(st, "%s", msg); }
+
+uint8_t *chain_state(pcad_chain *ch) { return ch->x[ch->cur]; }
+int chain_pitch(const pcad_chain *ch) { return ch->pitch; }
+cudaStream_t chain_stream(const pcad_chain *ch) { return ch->stream; }
 
 }  // namespace pcad

@@ -28,6 +28,7 @@ struct SweepArgs {
     uint32_t chain;
     int burn_in;              // sweeps not accumulated
     int last_phase;           // Gibbs: this phase completes the sweep
+    int row_off;              // global row of local row 0 (row bands): Philox rows are global
     long long wait_ns;        // limit of each bounded device wait (0: kWaitLimitNs)
     int stall_tile;           // test aid: wavefront tile stall_tile - 1 never publishes (0: off)
     DevModel m;
@@ -68,7 +69,7 @@ __device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__r
     in.xi = ld(idx);
     in.g = a.g[idx];
     if constexpr (UNIFORM)
-        in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)r, (uint32_t)c);
+        in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)(r + a.row_off), (uint32_t)c);
 }
 
 // *counter += n (one thread).
@@ -283,6 +284,16 @@ cudaError_t launch_batch_tc(const SlotDesc *slots, const uint32_t *t_arr,
 
 // TMA descriptor of a uint8 plane (box 96 x 48); false if the driver refuses.
 bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);
+
+// Largest row offset of a band chain (Philox rows are 32-bit).
+constexpr int kMaxRowOffset = 1 << 30;
+
+// Accessors of a chain for the row-band runner: the plane holding the
+// current state (stream-ordered: valid for work queued after the chain's
+// last run), its row pitch and the chain's stream.
+uint8_t *chain_state(pcad_chain *ch);
+int chain_pitch(const pcad_chain *ch);
+cudaStream_t chain_stream(const pcad_chain *ch);
 
 // Model validation, host tables and error reporting shared by the entry points.
 pcad_status check_model(const pcad_model *m);

@@ -78,7 +78,7 @@ __device__ __forceinline__ void block_uniforms(const SweepArgs &a, int r0, int c
 {
     const int l = (int)(threadIdx.x & 31);
     uint32_t o0, o1, o2, o3;
-    philox4x32_10((uint32_t)((c0 >> 2) + (l & 7)), (uint32_t)(r0 + (l >> 3)), t,
+    philox4x32_10((uint32_t)((c0 >> 2) + (l & 7)), (uint32_t)(r0 + a.row_off + (l >> 3)), t,
                   (kTagPCA << 24) | (a.chain & 0xFFFFFFu), (uint32_t)(a.seed & 0xFFFFFFFFull),
                   (uint32_t)(a.seed >> 32), o0, o1, o2, o3);
     reinterpret_cast<uint4 *>(u_s)[l] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);

@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kTbThreads)
             const int gr = by + lr, gc0 = bx + lcg;
             uint32_t w0 = 0, w1 = 0, w2 = 0, w3 = 0;
             if (pvalid && gr >= 0 && gr < a.H && gc0 + 3 >= 0 && gc0 < a.W)
-                philox4x32_10((uint32_t)gc0 >> 2, (uint32_t)gr, t, c3, key0, key1, w0, w1, w2, w3);
+                philox4x32_10((uint32_t)gc0 >> 2, (uint32_t)(gr + a.row_off), t, c3, key0, key1,
+                              w0, w1, w2, w3);
 #pragma unroll 1
             for (int q = 0; q < 4; ++q) {
                 const int lc = lcg + q, gc = gc0 + q;
