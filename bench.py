@@ -63,12 +63,13 @@ NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_
 NCU_DIRECT_BYTES_PER_SITE = None
 NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at 8192^2 L=16"
 
-KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3}
+KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4}
 KERNEL_NAMES = {
     1: "pca_direct_kernel (CUDA cores, one launch per sweep)",
     2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
        "one launch per 32 sweeps)",
     3: "pca_wave_kernel (CUDA cores, wavefront, one launch per 32 sweeps)",
+    4: "pca_small_kernel (CUDA cores, prior sums from a pair table, one launch per sweep)",
 }
 
 
@@ -96,7 +97,8 @@ def _args():
                         "stream through the continuous-batching server; blocking: 8192^2 "
                         "unblocked vs k = 1..8; protocol: the paper's annealed runs on MRF "
                         "images and the q grid")
-    p.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor", "wave"],
+    p.add_argument("--kernel", default="auto",
+                   choices=["auto", "cuda_core", "tensor", "wave", "small"],
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
                         "auto = the tensor-core sweep for eligible models with L >= 192, else "
                         "the per-sweep or wavefront CUDA-core kernel; tensor = prior sums by "

@@ -162,12 +162,19 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * overlaps the next one's start); same labels; L0 price only (PCAD_EINVAL
  * with an Lp norm).  Energy tracking runs the wavefront kernels one sweep
  * per launch.  pcad_chain_sync reports PCAD_ETIMEOUT if a tensor-core
- * completion wait or a wavefront dependency wait ever gave up. */
+ * completion wait or a wavefront dependency wait ever gave up.
+ * PCAD_KERNEL_SMALL (3 <= L <= 16, pair_coef >= 0, L0 price, PCA sampler;
+ * PCAD_EINVAL otherwise) runs one launch per sweep that takes the prior sums
+ * of all labels of a site from a table of neighbour pairs (16 bytes per pair
+ * of labels, in shared memory) and draws from chunk prefix sums in
+ * registers; same labels as the other kernels.  AUTO takes it for every
+ * model it accepts. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
     PCAD_KERNEL_TENSOR = 2,
-    PCAD_KERNEL_WAVE = 3
+    PCAD_KERNEL_WAVE = 3,
+    PCAD_KERNEL_SMALL = 4
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 
@@ -175,7 +182,8 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR, or
  * -k for temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO
  * the tensor-core kernel is taken for eligible models with L >= 192 and no
- * energy tracking; otherwise the wavefront kernel for L >= 16 when the
+ * energy tracking; PCAD_KERNEL_SMALL for the models it accepts; otherwise
+ * the wavefront kernel for L >= 16 when the
  * image has between 1/2 and 3 waves of 4 x 32 tiles at 10 resident tiles
  * per multiprocessor (the sizes where it measured faster on GB300), the
  * per-sweep kernel otherwise. */

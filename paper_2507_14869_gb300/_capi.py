@@ -691,6 +691,7 @@ PCAD_KERNEL_AUTO = 0
 PCAD_KERNEL_CUDA_CORE = 1
 PCAD_KERNEL_TENSOR = 2
 PCAD_KERNEL_WAVE = 3
+PCAD_KERNEL_SMALL = 4
 
 
 def pcad_chain_set_kernel(h, kind: int):

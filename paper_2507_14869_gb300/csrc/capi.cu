@@ -242,6 +242,7 @@ struct pcad_chain {
     unsigned long long *fp64 = nullptr;
     double *mscratch = nullptr;   // 8 scratch + 2 results
     double *ta64 = nullptr, *pr64 = nullptr, *in64 = nullptr;
+    uint32_t *ptab = nullptr;     // small-L sweep: pair prior table
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
     int tb_k = 0;                 // sweeps per temporally blocked launch (0: one per launch)
@@ -299,6 +300,17 @@ bool uses_tc(const pcad_chain *ch)
     return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace;
 }
 
+// Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
+// for every model it accepts (3 <= L <= 16, c >= 0, L0 price), where it
+// measured faster on GB300 than the general per-sweep and the wavefront
+// CUDA-core kernels.
+bool uses_small(const pcad_chain *ch)
+{
+    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !pca_small_eligible(ch->dm))
+        return false;
+    return ch->kernel == PCAD_KERNEL_SMALL || ch->kernel == PCAD_KERNEL_AUTO;
+}
+
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
 // AUTO takes them where the measured GB300 sweep favoured them: L >= 16 and
 // between 1/2 and 3 waves of the per-sweep kernel (10 resident 4 x 32 tiles
@@ -311,7 +323,7 @@ bool uses_wave(const pcad_chain *ch)
         return false;
     if (ch->kernel == PCAD_KERNEL_WAVE)
         return true;
-    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0)
+    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0 || uses_small(ch))
         return false;
     const long slots = 10L * ch->sms;
     return 2L * ch->wave_tiles >= slots && ch->wave_tiles <= 3L * slots;
@@ -372,7 +384,10 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
         if (ch->model.sampler == PCAD_SAMPLER_PCA) {
             a.xin = ch->x[cur];
             a.xout = ch->x[cur ^ 1];
-            CUDA_TRY(launch_pca_sweep(a, st));
+            if (uses_small(ch))
+                CUDA_TRY(launch_pca_small(a, st));
+            else
+                CUDA_TRY(launch_pca_sweep(a, st));
             cur ^= 1;
             if (ch->track.trace)
                 CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
@@ -463,7 +478,8 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     const size_t misc = 256;
     const int ntiles = wave_tiles(H, W);
     const size_t wbytes = align_up((size_t)(ntiles + 1) * sizeof(unsigned int), 256);
-    const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + misc;
+    const size_t pbytes = align_up((size_t)ptab_words() * sizeof(uint32_t), 256);
+    const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + pbytes + misc;
     cudaError_t e = cudaMallocAsync(&ch->block, total, ch->stream);
     if (e != cudaSuccess) {
         delete ch;
@@ -482,6 +498,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->pr64 = (double *)p; p += align_up(tabs.pr64.size() * sizeof(double), 256);
     ch->in64 = (double *)p; p += sizeof(tabs.in64);
     ch->wave = (unsigned int *)p; p += wbytes;
+    ch->ptab = (uint32_t *)p; p += pbytes;
     ch->wave_tiles = ntiles;
     {
         int dev = 0;
@@ -519,6 +536,8 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
                             cudaMemcpyHostToDevice, ch->stream);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(ch->tdev, 0, misc, ch->stream);
+    if (e == cudaSuccess && m->L <= kSmallMaxLabels)
+        e = launch_ptab(tabs.dm.T, ch->ptab, ch->stream);
     if (e == cudaSuccess) {
         int *bad = (int *)(ch->mscratch);
         e = launch_check_labels(ch->g, ch->pitch, H, W, m->L, bad, ch->stream);
@@ -536,6 +555,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->dm.ta64 = ch->ta64;
     ch->dm.pr64 = ch->pr64;
     ch->dm.in64 = ch->in64;
+    ch->dm.ptab = m->L <= kSmallMaxLabels ? ch->ptab : nullptr;
     *out = ch;
     return PCAD_OK;
 }
@@ -705,6 +725,7 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
     ch->dm.ta64 = ch->ta64;
     ch->dm.pr64 = ch->pr64;
     ch->dm.in64 = ch->in64;
+    ch->dm.ptab = m->L <= kSmallMaxLabels ? ch->ptab : nullptr;   // T is unchanged
     ch->ecoef = energy_coef(*m, (long)ch->H * ch->W);
     return PCAD_OK;
 }
@@ -737,6 +758,8 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
         *kind = -ch->tb_k;
     else if (uses_tc(ch))
         *kind = PCAD_KERNEL_TENSOR;
+    else if (uses_small(ch))
+        *kind = PCAD_KERNEL_SMALL;
     else if (uses_wave(ch))
         *kind = PCAD_KERNEL_WAVE;
     else
@@ -852,9 +875,13 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE &&
-        kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE)
-        return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR or "
-                                 "_WAVE");
+        kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE && kind != PCAD_KERNEL_SMALL)
+        return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
+                                 "_WAVE or _SMALL");
+    if (kind == PCAD_KERNEL_SMALL &&
+        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_small_eligible(ch->dm)))
+        return fail(PCAD_EINVAL, "the small-label kernel needs the PCA sampler, 3 <= L <= 16, "
+                                 "pair_coef >= 0 and the L0 inertia price");
     if (kind == PCAD_KERNEL_WAVE && (ch->model.sampler != PCAD_SAMPLER_PCA || ch->dm.norm != 0))
         return fail(PCAD_EINVAL, "the wavefront kernel needs the PCA sampler and the L0 price");
     if (kind == PCAD_KERNEL_TENSOR &&

@@ -59,6 +59,7 @@ struct DevModel {
     const double *pr64;  // [pmax + 1] exp(-c P), FP64
     const double *in64;  // [256] Lp price factor exp(-lambda (d / (L - 1))^p), FP64
     double el64;         // e^lambda, FP64
+    const uint32_t *ptab;  // small-L sweep: pair prior table (nullptr: not built)
 };
 
 // ------------------------------------------------------------ bounded waits

@@ -72,6 +72,21 @@ __device__ __forceinline__ void load_site(const SweepArgs &a, const uint8_t *__r
         in.ub = site_u24(a.seed, a.chain, tag, t, (uint32_t)(r + a.row_off), (uint32_t)c);
 }
 
+// The uniforms of a 4 x 32 block of sites (rows r0.., columns c0.., c0 a
+// multiple of 4): lane l of the calling warp computes the Philox block of row
+// r0 + l / 8, columns c0 + 4 (l % 8) .. + 3 (one call serves 4 sites) into
+// u_s[32 * (l / 8) + 4 (l % 8) ..], i.e. u_s[32 * row + column].
+__device__ __forceinline__ void block_uniforms(const SweepArgs &a, int r0, int c0, uint32_t t,
+                                               uint32_t *u_s)
+{
+    const int l = (int)(threadIdx.x & 31);
+    uint32_t o0, o1, o2, o3;
+    philox4x32_10((uint32_t)((c0 >> 2) + (l & 7)), (uint32_t)(r0 + a.row_off + (l >> 3)), t,
+                  (kTagPCA << 24) | (a.chain & 0xFFFFFFu), (uint32_t)(a.seed & 0xFFFFFFFFull),
+                  (uint32_t)(a.seed >> 32), o0, o1, o2, o3);
+    reinterpret_cast<uint4 *>(u_s)[l] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
+}
+
 // *counter += n (one thread).
 cudaError_t launch_advance(uint32_t *counter, uint32_t n, cudaStream_t s);
 
@@ -284,6 +299,17 @@ cudaError_t launch_batch_tc(const SlotDesc *slots, const uint32_t *t_arr,
 
 // TMA descriptor of a uint8 plane (box 96 x 48); false if the driver refuses.
 bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);
+
+// Small label counts (kSmallMinLabels <= L <= kSmallMaxLabels, gam <= 0,
+// alpha <= 0, L0 price): one-launch-per-sweep kernel with the prior sums of
+// all labels from a pair table (ptab_words() words, built by launch_ptab for
+// the truncation T; the model's ptab points at it).
+constexpr int kSmallMinLabels = 3;
+constexpr int kSmallMaxLabels = 16;
+int ptab_words();
+cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t s);
+bool pca_small_eligible(const DevModel &m);
+cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s);
 
 // Largest row offset of a band chain (Philox rows are 32-bit).
 constexpr int kMaxRowOffset = 1 << 30;

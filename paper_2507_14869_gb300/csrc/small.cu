@@ -1,0 +1,359 @@
+// Lazy-PCA sweep for small label counts (3 <= L <= 16) on the CUDA cores
+// (Section 5.2, Eq. posterior_pca_transition_matrix).
+//
+// With few labels the per-label work of the general kernel (4 neighbour
+// terms per label, chunked two-pass CDF) is dominated by fixed costs.  Here:
+//
+//   * Prior sums from a pair table.  P(s) = sum_j min(|s - x_j|, T) splits
+//     into pairs of neighbours (up + down, left + right, and the two
+//     diagonal pairs for the 8-neighbourhood).  For every pair of labels
+//     (a, b), a, b in [0, 16] with 16 standing for a neighbour outside the
+//     image, the table holds min(|s - a|, T) + min(|s - b|, T) for s = 0..15
+//     as 16 bytes (a missing neighbour contributes 0: its term is the same
+//     for every s and cancels in the normalisation).  One 16-byte shared-
+//     memory read per pair and four integer adds give the exact P(s) of all
+//     16 labels, four per 32-bit word (every byte <= 120, no carries).
+//   * Weights by the formula of the general kernel, w(s) =
+//     2^fl(alpha q + fl(gam P)), q = (g - s)^2 and P exact integers, two
+//     labels per packed FP32x2 instruction (every lane rounds as the scalar
+//     operation).  A byte of P becomes an exact float by placing it in the
+//     mantissa of 2^23 and subtracting 2^23.
+//   * Inverse CDF over chunks of 4 labels: in-chunk prefix sums (3
+//     roundings), chunk prefix (3 more), one join per probed label and one
+//     for the inertia correction delta = w(x_i)(e^lambda - 1): every C_k
+//     within 8u and Z within 7u of exact, inside the 22u summation budget of
+//     the per-site certified margin (valid because gam <= 0 and alpha <= 0
+//     keep both exponent terms non-positive).  The chunk, then the label in
+//     it, are found by comparisons in registers; draws within the margin of
+//     a CDF boundary are re-drawn by the warp in FP64.
+//
+// Persistent blocks of 4 x 32 sites: each copies the table (4.6 KB) into
+// shared memory once and takes tiles in a grid-stride loop.  Per tile, warp
+// 0 computes the uniforms (one Philox call per 4 sites) while warps 2 and 3
+// stage the tile's labels with a one-site halo as table codes (aligned
+// 32-bit loads), so the neighbour reads are shared-memory byte loads with
+// no bounds tests.
+#include "pcad_internal.h"
+
+namespace pcad {
+
+namespace {
+
+constexpr int kBX = 32;
+constexpr int kBY = 4;
+constexpr int kThreads = kBX * kBY;
+constexpr int kCodes = 17;                      // labels 0..15 and "missing"
+constexpr int kPtabWords = kCodes * kCodes * 4; // 16 bytes per pair
+
+__global__ void ptab_kernel(int T, uint32_t *out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kPtabWords)
+        return;
+    const int e = i >> 2, w = i & 3;
+    const int a = e / kCodes, b = e - (e / kCodes) * kCodes;
+    uint32_t word = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int s = 4 * w + k;
+        const int da = a == 16 ? 0 : min(abs(s - a), T);
+        const int db = b == 16 ? 0 : min(abs(s - b), T);
+        word |= (uint32_t)(da + db) << (8 * k);
+    }
+    out[i] = word;
+}
+
+// Exact float of byte k (0..3) of word p.
+__device__ __forceinline__ float byte_f(uint32_t p, int k)
+{
+    return __fsub_rn(__uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)k)),
+                     8388608.0f);
+}
+
+// Codes of the label tile a block stages: rows r0 - 1 .. r0 + 4 and columns
+// c0 - 4 .. c0 + 35 of the state (10 aligned words per row), a label or 16
+// outside the image.
+constexpr int kTileRowsS = kBY + 2;
+constexpr int kTileColsS = kBX + 8;
+constexpr int kPrefixStride = 20;   // floats per thread row of prefix sums (conflict-free)
+
+// The draw of one site from its neighbour codes nc[] and observation g.
+// Returns the label; `certain` is false when the uniform lies within the
+// certified margin of the chosen label's CDF interval (the caller re-draws
+// it in FP64).  pre: this thread's row of shared memory for the prefix sums.
+template <int LMAX, int NB, bool MASK>
+__device__ __forceinline__ int draw_small(const DevModel &m, const uint32_t *pt, const int (&nc)[NB],
+                                          int g, int xi, uint32_t ub, float *pre, bool &certain)
+{
+    constexpr int NW = LMAX / 4;      // table words used per pair = chunks of 4 labels
+    uint32_t P[NW];
+    {
+        const int e0 = (nc[0] * kCodes + nc[1]) * 4;
+        const int e1 = (nc[2] * kCodes + nc[3]) * 4;
+        if constexpr (NW == 4) {
+            uint4 a = *reinterpret_cast<const uint4 *>(pt + e0);
+            const uint4 b = *reinterpret_cast<const uint4 *>(pt + e1);
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+            if constexpr (NB == 8) {
+                const uint4 c = *reinterpret_cast<const uint4 *>(pt + (nc[4] * kCodes + nc[5]) * 4);
+                const uint4 d = *reinterpret_cast<const uint4 *>(pt + (nc[6] * kCodes + nc[7]) * 4);
+                a.x += c.x + d.x;
+                a.y += c.y + d.y;
+                a.z += c.z + d.z;
+                a.w += c.w + d.w;
+            }
+            P[0] = a.x;
+            P[1] = a.y;
+            P[2] = a.z;
+            P[3] = a.w;
+        } else {
+            uint2 a = *reinterpret_cast<const uint2 *>(pt + e0);
+            const uint2 b = *reinterpret_cast<const uint2 *>(pt + e1);
+            a.x += b.x;
+            a.y += b.y;
+            if constexpr (NB == 8) {
+                const uint2 c = *reinterpret_cast<const uint2 *>(pt + (nc[4] * kCodes + nc[5]) * 4);
+                const uint2 d = *reinterpret_cast<const uint2 *>(pt + (nc[6] * kCodes + nc[7]) * 4);
+                a.x += c.x + d.x;
+                a.y += c.y + d.y;
+            }
+            P[0] = a.x;
+            P[1] = a.y;
+        }
+    }
+    const float gf = (float)g;
+    const float2 a2 = make_float2(m.alpha, m.alpha), g2 = make_float2(m.gam, m.gam);
+    const float2 off2 = make_float2(-8388608.0f, -8388608.0f);
+    const float2 gg = make_float2(gf, gf);
+    float w[LMAX];
+#pragma unroll
+    for (int s = 0; s < LMAX; s += 2) {
+        const uint32_t p = P[s >> 2];
+        const float2 pm = make_float2(
+            __uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)(s & 3))),
+            __uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)((s + 1) & 3))));
+        const float2 Pf = __fadd2_rn(pm, off2);
+        const float2 dg = __fadd2_rn(gg, make_float2(-(float)s, -(float)(s + 1)));
+        const float2 v = __ffma2_rn(a2, __fmul2_rn(dg, dg), __fmul2_rn(g2, Pf));
+        w[s] = ex2_ftz(v.x);
+        w[s + 1] = ex2_ftz(v.y);
+        if (MASK) {
+            w[s] = s < m.L ? w[s] : 0.0f;
+            w[s + 1] = s + 1 < m.L ? w[s + 1] : 0.0f;
+        }
+    }
+    // in-chunk inclusive prefix sums (to shared memory) and the chunk prefix G
+    float G[NW];
+#pragma unroll
+    for (int c = 0; c < NW; ++c) {
+        const float p1 = __fadd_rn(w[4 * c], w[4 * c + 1]);
+        const float p2 = __fadd_rn(p1, w[4 * c + 2]);
+        const float p3 = __fadd_rn(p2, w[4 * c + 3]);
+        reinterpret_cast<float4 *>(pre)[c] = make_float4(w[4 * c], p1, p2, p3);
+        G[c] = c == 0 ? p3 : __fadd_rn(G[c - 1], p3);
+    }
+    float delta = 0.0f;
+    if (m.em1 != 0.0f) {
+        // w(x_i), bit-identical to the packed evaluation above
+        uint32_t pw;
+        if constexpr (NW == 4) {
+            const uint32_t lo = (xi & 4) ? P[1] : P[0], hi = (xi & 4) ? P[3] : P[2];
+            pw = (xi & 8) ? hi : lo;
+        } else {
+            pw = (xi & 4) ? P[1] : P[0];
+        }
+        const float dg = __fsub_rn(gf, (float)xi);
+        const float v = __fmaf_rn(m.alpha, __fmul_rn(dg, dg), __fmul_rn(m.gam, byte_f(pw, xi & 3)));
+        delta = __fmul_rn(ex2_ftz(v), m.em1);
+    }
+    const float G0 = G[NW - 1];
+    const float Z = __fadd_rn(G0, delta);
+    const float t = __fmul_rn((float)ub * (1.0f / 16777216.0f), Z);
+    const float margin = __fmul_rn(site_margin(m, G0, delta), Z);
+    // chunk: the number of chunk ends (with delta at and above x_i) <= t;
+    // Gp: the chunk prefix before it
+    int cs = 0;
+    float Gp = 0.0f;
+#pragma unroll
+    for (int c = 0; c + 1 < NW; ++c) {
+        const bool below = __fadd_rn(G[c], (4 * c + 3 >= xi) ? delta : 0.0f) <= t;
+        cs += below ? 1 : 0;
+        Gp = below ? G[c] : Gp;
+    }
+    const float4 pc = reinterpret_cast<const float4 *>(pre)[cs];
+    const int base = 4 * cs;
+    const float C0 = __fadd_rn(__fadd_rn(Gp, pc.x), (base >= xi) ? delta : 0.0f);
+    const float C1 = __fadd_rn(__fadd_rn(Gp, pc.y), (base + 1 >= xi) ? delta : 0.0f);
+    const float C2 = __fadd_rn(__fadd_rn(Gp, pc.z), (base + 2 >= xi) ? delta : 0.0f);
+    const float C3 = __fadd_rn(__fadd_rn(Gp, pc.w), (base + 3 >= xi) ? delta : 0.0f);
+    const bool b0 = C0 <= t, b1 = C1 <= t, b2 = C2 <= t;
+    const int k = (int)b0 + (int)b1 + (int)b2;
+    const float hiC = b2 ? C3 : (b1 ? C2 : (b0 ? C1 : C0));
+    const float Cm = __fadd_rn(Gp, (base - 1 >= xi) ? delta : 0.0f);   // before the chunk
+    const float loC = b2 ? C2 : (b1 ? C1 : (b0 ? C0 : Cm));
+    const int s = base + k;
+    certain = (t < hiC) & (s < m.L) & ((s == m.L - 1) | (__fsub_rn(hiC, t) > margin)) &
+              ((s == 0) | (__fsub_rn(t, loC) > margin));
+    return min(s, m.L - 1);
+}
+
+template <int LMAX, int NB, bool MASK>
+__global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, int tiles_x,
+                                                             int ntiles)
+{
+    __shared__ __align__(16) uint32_t pt[kPtabWords];
+    __shared__ __align__(16) uint32_t U_s[kBY * kBX];
+    __shared__ __align__(16) uint32_t codes[kTileRowsS * kTileColsS / 4];
+    __shared__ __align__(16) float pre_s[kThreads * kPrefixStride];
+    const int tid = threadIdx.y * kBX + threadIdx.x;
+    for (int i = tid; i < kPtabWords / 4; i += kThreads)
+        reinterpret_cast<uint4 *>(pt)[i] = __ldg(reinterpret_cast<const uint4 *>(a.m.ptab) + i);
+    const uint32_t t = sweep_index(a);
+    const bool acc_on = accumulate_after(a, t);
+    const uint8_t *cb = reinterpret_cast<const uint8_t *>(codes);
+    float *pre = pre_s + tid * kPrefixStride;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int ty = tile / tiles_x, tx = tile - (tile / tiles_x) * tiles_x;
+        const int r0 = ty * kBY, c0 = tx * kBX;
+        const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;
+        const bool valid = r < a.H && c < a.W;
+        // the site's observation and accumulator: issued before the barrier
+        int g = 0;
+        float acc_old = 0.0f;
+        if (valid) {
+            g = a.g[(size_t)r * a.pitch + c];
+            if (acc_on)
+                acc_old = a.acc[(size_t)r * a.W + c];
+        }
+        __syncthreads();   // the table is in place; the previous tile's codes and uniforms are read
+        if (threadIdx.y == 0) {
+            block_uniforms(a, r0, c0, t, U_s);
+        } else if (tid >= 64 && tid < 64 + kTileRowsS * kTileColsS / 4) {
+            // warps 2 and 3 stage the label codes, one aligned word each
+            const int i = tid - 64, wr = i / (kTileColsS / 4), wc = i - wr * (kTileColsS / 4);
+            const int gr = r0 - 1 + wr, gc = c0 - 4 + 4 * wc;
+            uint32_t word = 0x10101010u;
+            if (gr >= 0 && gr < a.H && gc >= 0 && gc < a.W) {
+                word = *reinterpret_cast<const uint32_t *>(a.xin + (size_t)gr * a.pitch + gc);
+                if (gc + 3 >= a.W) {   // the image's right edge inside this word
+                    const uint32_t keep = a.W - gc;   // 1..3 bytes
+                    const uint32_t mask = (1u << (8 * keep)) - 1u;
+                    word = (word & mask) | (0x10101010u & ~mask);
+                }
+            }
+            codes[i] = word;
+        }
+        __syncthreads();
+        // neighbour codes: up, down, left, right, then the diagonals
+        const uint8_t *me = cb + (1 + (int)threadIdx.y) * kTileColsS + 4 + (int)threadIdx.x;
+        int nc[NB];
+        nc[0] = me[-kTileColsS];
+        nc[1] = me[kTileColsS];
+        nc[2] = me[-1];
+        nc[3] = me[1];
+        if constexpr (NB == 8) {
+            nc[4] = me[-kTileColsS - 1];
+            nc[5] = me[-kTileColsS + 1];
+            nc[6] = me[kTileColsS - 1];
+            nc[7] = me[kTileColsS + 1];
+        }
+        const int xi = me[0];
+        const uint32_t ub = U_s[tid];
+        int s = 0;
+        bool certain = true;
+        if (valid)
+            s = draw_small<LMAX, NB, MASK>(a.m, pt, nc, g, xi, ub, pre, certain);
+        const bool need = valid && !certain;
+        if (__any_sync(0xFFFFFFFFu, need)) {
+            SiteIn<NB> in{};
+            in.g = g;
+            in.xi = xi;
+            in.ub = ub;
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                in.xni[j] = nc[j] == 16 ? kMissingLabelI : nc[j];
+            s = warp_redraw_fp64<NB>(a.m, need, in, s, a.fp64_draws);
+        }
+        if (valid) {
+            a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+            if (acc_on)
+                a.acc[(size_t)r * a.W + c] = acc_old + (float)s;
+        }
+    }
+}
+
+template <int LMAX, int NB, bool MASK>
+cudaError_t launch_small_t(const SweepArgs &a, cudaStream_t st)
+{
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pca_small_kernel<LMAX, NB, MASK>,
+                                                          kThreads, 0);
+        if (e != cudaSuccess)
+            return e;
+        per_sm[dev] = n > 0 ? n : 1;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int tiles_x = (a.W + kBX - 1) / kBX;
+    const long long ntiles = (long long)tiles_x * ((a.H + kBY - 1) / kBY);
+    if (ntiles <= 0)
+        return cudaSuccess;
+    if (ntiles >= (1ll << 31))
+        return cudaErrorInvalidValue;
+    const long long cap = (long long)per_sm[dev] * sms;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    pca_small_kernel<LMAX, NB, MASK><<<grid, dim3(kBX, kBY), 0, st>>>(a, tiles_x, (int)ntiles);
+    return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t dispatch_small(const SweepArgs &a, cudaStream_t st)
+{
+    if (a.m.L <= 8)
+        return a.m.L == 8 ? launch_small_t<8, NB, false>(a, st) : launch_small_t<8, NB, true>(a, st);
+    return a.m.L == 16 ? launch_small_t<16, NB, false>(a, st) : launch_small_t<16, NB, true>(a, st);
+}
+
+}  // namespace
+
+int ptab_words()
+{
+    return kPtabWords;
+}
+
+cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t st)
+{
+    ptab_kernel<<<(kPtabWords + 255) / 256, 256, 0, st>>>(T, out);
+    return cudaGetLastError();
+}
+
+bool pca_small_eligible(const DevModel &m)
+{
+    return m.ptab != nullptr && m.L >= kSmallMinLabels && m.L <= kSmallMaxLabels &&
+           m.norm == 0 && m.gam <= 0.0f && m.alpha <= 0.0f && (m.nbhd == 4 || m.nbhd == 8);
+}
+
+cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t st)
+{
+    if (!pca_small_eligible(a.m))
+        return cudaErrorInvalidValue;
+    // the label tile is staged with aligned 32-bit loads
+    if ((a.pitch & 3) != 0 || (reinterpret_cast<uintptr_t>(a.xin) & 3u) != 0)
+        return cudaErrorMisalignedAddress;
+    return a.m.nbhd == 8 ? dispatch_small<8>(a, st) : dispatch_small<4>(a, st);
+}
+
+}  // namespace pcad

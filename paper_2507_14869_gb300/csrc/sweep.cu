@@ -69,21 +69,6 @@ __device__ __forceinline__ void pca_site(const SweepArgs &a, int r, int c, uint3
 }
 
 
-// The uniforms of a 4 x 32 block of sites (rows r0.., columns c0.., c0 a
-// multiple of 4): lane l of the calling warp computes the Philox block of row
-// r0 + l / 8, columns c0 + 4 (l % 8) .. + 3 (one call serves 4 sites) into
-// u_s[32 * (l / 8) + 4 (l % 8) ..], i.e. u_s[32 * row + column].
-__device__ __forceinline__ void block_uniforms(const SweepArgs &a, int r0, int c0, uint32_t t,
-                                               uint32_t *u_s)
-{
-    const int l = (int)(threadIdx.x & 31);
-    uint32_t o0, o1, o2, o3;
-    philox4x32_10((uint32_t)((c0 >> 2) + (l & 7)), (uint32_t)(r0 + a.row_off + (l >> 3)), t,
-                  (kTagPCA << 24) | (a.chain & 0xFFFFFFu), (uint32_t)(a.seed & 0xFFFFFFFFull),
-                  (uint32_t)(a.seed >> 32), o0, o1, o2, o3);
-    reinterpret_cast<uint4 *>(u_s)[l] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
-}
-
 template <int NC, int NB, int NORM>
 __global__ void __launch_bounds__(kThreads) pca_direct_kernel(const SweepArgs a)
 {

@@ -62,8 +62,10 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
     if form == "tc":
         v = _fma32(alpha, q, _fma32(mu, Pb, cb))
     else:
+        # "cc": a missing neighbour contributes T; "small" (the small-label
+        # kernel's pair table): it contributes nothing
         P = (np.where(present[:, :, None], np.minimum(np.abs(s[None, None, :] - x[:, :, None]), T),
-                      T)).sum(1)
+                      T if form == "cc" else 0)).sum(1)
         v = _fma32(alpha, q, (f64(gam) * P).astype(f32))
     # ex2 within 2 ulp: correctly rounded, moved by 2u up for labels <= the
     # split and down above it, rounded again
@@ -95,6 +97,19 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
         comp = (tt - G) - y
         G = tt
         Gc[:, c] = G
+    if form == "small":
+        # chunks of 4 labels: in-chunk sequential prefix, sequential chunk
+        # prefix, no compensation
+        nc = (L + 3) // 4
+        wp = np.zeros((n, nc * 4), f32)
+        wp[:, :L] = w
+        pref = np.zeros((n, nc * 4), f32)
+        for k in range(nc * 4):
+            pref[:, k] = pref[:, k - 1] + wp[:, k] if k % 4 else wp[:, k]
+        Gc = np.zeros((n, nc), f32)
+        for c in range(nc):
+            Gc[:, c] = pref[:, 4 * c + 3] if c == 0 else Gc[:, c - 1] + pref[:, 4 * c + 3]
+        G = Gc[:, -1].copy()
     # the model's parameters as the library receives them (FP32 fields)
     lam = float(f32(model["inertia"]))
     c_e, sig_e = float(f32(model["pair_coef"])), float(f32(model["sigma"]))
@@ -102,7 +117,7 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
     delta = (w[np.arange(n), xi].astype(f64) * f64(em1)).astype(f32) if lam > 0 else np.zeros(n, f32)
     Z = (G + delta).astype(f32)
     Gprev = np.concatenate([np.zeros((n, 1), f32), Gc[:, :-1]], axis=1)
-    C = (np.repeat(Gprev, 8, axis=1)[:, :L] + pref[:, :L]).astype(f32)
+    C = (np.repeat(Gprev, 4 if form == "small" else 8, axis=1)[:, :L] + pref[:, :L]).astype(f32)
     C = (C + np.where(s[None, :] >= xi[:, None], delta[:, None], f32(0.0))).astype(f32)
     # exact conditional
     mu_e = c_e * LOG2E
@@ -159,6 +174,44 @@ def test_margin_covers_worst_fp32_error(pc, i, form):
             split = (Fk < 0.5).sum(1)
         err, eta, _ = _worst_error(mg, model, x, present, g, xi, split, form)
         bound = eta / 1.5 - U                          # without the slack, less t's rounding
+        assert np.all(err <= bound), (float(err.max()), float(bound[np.argmax(err / bound)]))
+        worst = max(worst, float((err / bound).max()))
+    assert worst < 1.0
+
+
+SMALL_MODELS = [
+    dict(L=16, nbhd=4, pair=1, pair_coef=0.05, pair_T=30, noise=0, sigma=1.0, inertia=2.0),
+    dict(L=16, nbhd=8, pair=1, pair_coef=0.6, pair_T=4, noise=0, sigma=4.0, inertia=0.5),
+    dict(L=5, nbhd=8, pair=0, pair_coef=0.833, pair_T=1, noise=0, sigma=1.0, inertia=0.7),
+    dict(L=9, nbhd=4, pair=1, pair_coef=0.85, pair_T=2, noise=0, sigma=1.6, inertia=0.26),
+    dict(L=13, nbhd=4, pair=1, pair_coef=2.4, pair_T=3, noise=0, sigma=0.7, inertia=4.0),
+    dict(L=3, nbhd=4, pair=1, pair_coef=0.3, pair_T=1, noise=2, sigma=1.0, inertia=1.0),
+    dict(L=16, nbhd=4, pair=1, pair_coef=0.0, pair_T=3, noise=0, sigma=60.0, inertia=0.0),
+]
+
+
+@pytest.mark.parametrize("i", range(len(SMALL_MODELS)))
+def test_margin_covers_the_small_label_kernel(pc, i):
+    """The small-label kernel: the same weight formula with a missing
+    neighbour contributing nothing, chunks of 4 labels summed without
+    compensation -- inside the same per-site margin."""
+    model = dict(SMALL_MODELS[i])
+    model["T"] = 1 if model["pair"] == 0 else model["pair_T"]
+    mg = pc.pcad_model_margins(dict(model, flip_p=0.1, sampler=0))
+    assert mg["gam"] <= 0
+    rng = np.random.default_rng(300 + i)
+    x, present, g, xi = _sites(rng, 1500, model["L"], model["nbhd"], spread=3)
+    worst = 0.0
+    for split_kind in range(3):
+        if split_kind == 0:
+            split = np.full(len(g), -1)
+        elif split_kind == 1:
+            split = np.full(len(g), model["L"])
+        else:
+            _, _, Fk = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1), "small")
+            split = (Fk < 0.5).sum(1)
+        err, eta, _ = _worst_error(mg, model, x, present, g, xi, split, "small")
+        bound = eta / 1.5 - U
         assert np.all(err <= bound), (float(err.max()), float(bound[np.argmax(err / bound)]))
         worst = max(worst, float((err / bound).max()))
     assert worst < 1.0
