@@ -300,15 +300,20 @@ bool uses_tc(const pcad_chain *ch)
     return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace;
 }
 
+bool uses_wave(const pcad_chain *ch);
+
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
-// for every model it accepts (3 <= L <= 16, c >= 0, L0 price), where it
-// measured faster on GB300 than the general per-sweep and the wavefront
-// CUDA-core kernels.
+// for the models it accepts (3 <= L <= 16, c >= 0, L0 price) unless the
+// wavefront kernel is chosen (L = 16 at 1/2 to 3 waves of 4 x 32 tiles,
+// where the small-label kernel's 16 x 32 tiles leave SMs idle).  Measured on
+// GB300 at L = 16: 9.1e10 site-updates/s at 8192^2 and 6.6e10 at 1024^2
+// against 4.9e10 and 4.1e10 for the general per-sweep kernel; 3.2e10 at
+// 512^2 against 3.7e10 for the wavefront kernel.
 bool uses_small(const pcad_chain *ch)
 {
     if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !pca_small_eligible(ch->dm))
         return false;
-    return ch->kernel == PCAD_KERNEL_SMALL || ch->kernel == PCAD_KERNEL_AUTO;
+    return ch->kernel == PCAD_KERNEL_SMALL || (ch->kernel == PCAD_KERNEL_AUTO && !uses_wave(ch));
 }
 
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
@@ -323,7 +328,7 @@ bool uses_wave(const pcad_chain *ch)
         return false;
     if (ch->kernel == PCAD_KERNEL_WAVE)
         return true;
-    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0 || uses_small(ch))
+    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0)
         return false;
     const long slots = 10L * ch->sms;
     return 2L * ch->wave_tiles >= slots && ch->wave_tiles <= 3L * slots;
@@ -758,10 +763,10 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
         *kind = -ch->tb_k;
     else if (uses_tc(ch))
         *kind = PCAD_KERNEL_TENSOR;
-    else if (uses_small(ch))
-        *kind = PCAD_KERNEL_SMALL;
     else if (uses_wave(ch))
         *kind = PCAD_KERNEL_WAVE;
+    else if (uses_small(ch))
+        *kind = PCAD_KERNEL_SMALL;
     else
         *kind = PCAD_KERNEL_CUDA_CORE;
     return PCAD_OK;

@@ -17,22 +17,25 @@
 //     2^fl(alpha q + fl(gam P)), q = (g - s)^2 and P exact integers, two
 //     labels per packed FP32x2 instruction (every lane rounds as the scalar
 //     operation).  A byte of P becomes an exact float by placing it in the
-//     mantissa of 2^23 and subtracting 2^23.
+//     mantissa of 2^23 and subtracting 2^23.  (Products of two table
+//     factors per label measured slower: the per-lane table reads conflict
+//     in shared memory, while the exponential unit has room.)
 //   * Inverse CDF over chunks of 4 labels: in-chunk prefix sums (3
 //     roundings), chunk prefix (3 more), one join per probed label and one
 //     for the inertia correction delta = w(x_i)(e^lambda - 1): every C_k
 //     within 8u and Z within 7u of exact, inside the 22u summation budget of
 //     the per-site certified margin (valid because gam <= 0 and alpha <= 0
 //     keep both exponent terms non-positive).  The chunk, then the label in
-//     it, are found by comparisons in registers; draws within the margin of
-//     a CDF boundary are re-drawn by the warp in FP64.
+//     it, are found by comparisons; draws within the margin of a CDF
+//     boundary are re-drawn by the warp in FP64.
 //
-// Persistent blocks of 4 x 32 sites: each copies the table (4.6 KB) into
-// shared memory once and takes tiles in a grid-stride loop.  Per tile, warp
-// 0 computes the uniforms (one Philox call per 4 sites) while warps 2 and 3
-// stage the tile's labels with a one-site halo as table codes (aligned
-// 32-bit loads), so the neighbour reads are shared-memory byte loads with
-// no bounds tests.
+// Persistent blocks of 128 threads take tiles of 16 x 32 sites in a
+// grid-stride loop; a thread updates the 4 sites of its column in rows
+// w, w + 4, w + 8, w + 12 of the tile (w its warp).  Each block copies the
+// pair table (4.6 KB) into shared memory once.  Per tile, the block stages
+// the tile's labels with a one-site halo as table codes (aligned 32-bit
+// loads, one barrier), and each warp computes the uniforms of its own 4 rows
+// (one Philox call per 4 sites, one per lane).
 #include "pcad_internal.h"
 
 namespace pcad {
@@ -40,10 +43,16 @@ namespace pcad {
 namespace {
 
 constexpr int kBX = 32;
-constexpr int kBY = 4;
-constexpr int kThreads = kBX * kBY;
-constexpr int kCodes = 17;                      // labels 0..15 and "missing"
-constexpr int kPtabWords = kCodes * kCodes * 4; // 16 bytes per pair
+constexpr int kWarps = 4;
+constexpr int kThreads = kBX * kWarps;
+constexpr int kSPT = 4;                          // sites per thread (rows w + 4 i)
+constexpr int kTileR = kWarps * kSPT;            // 16 rows per tile
+constexpr int kCodes = 17;                       // labels 0..15 and "missing"
+constexpr int kPtabWords = kCodes * kCodes * 4;  // 16 bytes per pair
+constexpr int kCodeCols = kBX + 8;               // columns c0 - 4 .. c0 + 35
+constexpr int kCodeRows = kTileR + 2;            // rows r0 - 1 .. r0 + 16
+constexpr int kCodeWords = kCodeRows * kCodeCols / 4;
+constexpr int kPrefixStride = 20;                // floats per thread row (conflict-free)
 
 __global__ void ptab_kernel(int T, uint32_t *out)
 {
@@ -69,13 +78,6 @@ __device__ __forceinline__ float byte_f(uint32_t p, int k)
     return __fsub_rn(__uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)k)),
                      8388608.0f);
 }
-
-// Codes of the label tile a block stages: rows r0 - 1 .. r0 + 4 and columns
-// c0 - 4 .. c0 + 35 of the state (10 aligned words per row), a label or 16
-// outside the image.
-constexpr int kTileRowsS = kBY + 2;
-constexpr int kTileColsS = kBX + 8;
-constexpr int kPrefixStride = 20;   // floats per thread row of prefix sums (conflict-free)
 
 // The draw of one site from its neighbour codes nc[] and observation g.
 // Returns the label; `certain` is false when the uniform lies within the
@@ -205,82 +207,109 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
                                                              int ntiles)
 {
     __shared__ __align__(16) uint32_t pt[kPtabWords];
-    __shared__ __align__(16) uint32_t U_s[kBY * kBX];
-    __shared__ __align__(16) uint32_t codes[kTileRowsS * kTileColsS / 4];
+    __shared__ __align__(16) uint32_t U_s[kWarps * kSPT * kBX];
+    __shared__ __align__(16) uint32_t codes[kCodeWords];
     __shared__ __align__(16) float pre_s[kThreads * kPrefixStride];
-    const int tid = threadIdx.y * kBX + threadIdx.x;
+    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
+    const int tid = wp * kBX + lane;
     for (int i = tid; i < kPtabWords / 4; i += kThreads)
         reinterpret_cast<uint4 *>(pt)[i] = __ldg(reinterpret_cast<const uint4 *>(a.m.ptab) + i);
     const uint32_t t = sweep_index(a);
     const bool acc_on = accumulate_after(a, t);
     const uint8_t *cb = reinterpret_cast<const uint8_t *>(codes);
     float *pre = pre_s + tid * kPrefixStride;
+    uint32_t *Uw = U_s + wp * kSPT * kBX;
+    const uint32_t key0 = (uint32_t)(a.seed & 0xFFFFFFFFull), key1 = (uint32_t)(a.seed >> 32);
+    const uint32_t ctr3 = (kTagPCA << 24) | (a.chain & 0xFFFFFFu);
+    // tiles in a grid-stride loop, walked as (row, column) without division
+    const int step_y = (int)gridDim.x / tiles_x, step_x = (int)gridDim.x - step_y * tiles_x;
+    int ty = (int)blockIdx.x / tiles_x, tx = (int)blockIdx.x - ty * tiles_x;
     for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int ty = tile / tiles_x, tx = tile - (tile / tiles_x) * tiles_x;
-        const int r0 = ty * kBY, c0 = tx * kBX;
-        const int r = r0 + threadIdx.y, c = c0 + threadIdx.x;
-        const bool valid = r < a.H && c < a.W;
-        // the site's observation and accumulator: issued before the barrier
-        int g = 0;
-        float acc_old = 0.0f;
-        if (valid) {
-            g = a.g[(size_t)r * a.pitch + c];
-            if (acc_on)
-                acc_old = a.acc[(size_t)r * a.W + c];
+        const int r0 = ty * kTileR, c0 = tx * kBX;
+        const int c = c0 + lane;
+        // this thread's observations and accumulators, issued early
+        int g[kSPT];
+        float acc_old[kSPT];
+#pragma unroll
+        for (int i = 0; i < kSPT; ++i) {
+            const int r = r0 + wp + kWarps * i;
+            g[i] = 0;
+            acc_old[i] = 0.0f;
+            if (r < a.H && c < a.W) {
+                g[i] = a.g[(size_t)r * a.pitch + c];
+                if (acc_on)
+                    acc_old[i] = a.acc[(size_t)r * a.W + c];
+            }
         }
-        __syncthreads();   // the table is in place; the previous tile's codes and uniforms are read
-        if (threadIdx.y == 0) {
-            block_uniforms(a, r0, c0, t, U_s);
-        } else if (tid >= 64 && tid < 64 + kTileRowsS * kTileColsS / 4) {
-            // warps 2 and 3 stage the label codes, one aligned word each
-            const int i = tid - 64, wr = i / (kTileColsS / 4), wc = i - wr * (kTileColsS / 4);
+        __syncthreads();   // tables in place; the previous tile's codes are read
+        // the tile's label codes, one aligned word per thread and round
+        for (int i = tid; i < kCodeWords; i += kThreads) {
+            const int wr = i / (kCodeCols / 4), wc = i - wr * (kCodeCols / 4);
             const int gr = r0 - 1 + wr, gc = c0 - 4 + 4 * wc;
             uint32_t word = 0x10101010u;
             if (gr >= 0 && gr < a.H && gc >= 0 && gc < a.W) {
                 word = *reinterpret_cast<const uint32_t *>(a.xin + (size_t)gr * a.pitch + gc);
                 if (gc + 3 >= a.W) {   // the image's right edge inside this word
-                    const uint32_t keep = a.W - gc;   // 1..3 bytes
-                    const uint32_t mask = (1u << (8 * keep)) - 1u;
+                    const uint32_t mask = (1u << (8 * (a.W - gc))) - 1u;
                     word = (word & mask) | (0x10101010u & ~mask);
                 }
             }
             codes[i] = word;
         }
+        // this warp's uniforms: rows wp + 4 i, one Philox call per lane
+        {
+            const int i = lane >> 3, q = lane & 7;
+            uint32_t o0, o1, o2, o3;
+            philox4x32_10((uint32_t)((c0 >> 2) + q), (uint32_t)(r0 + wp + kWarps * i + a.row_off),
+                          t, ctr3, key0, key1, o0, o1, o2, o3);
+            reinterpret_cast<uint4 *>(Uw)[lane] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
+        }
         __syncthreads();
-        // neighbour codes: up, down, left, right, then the diagonals
-        const uint8_t *me = cb + (1 + (int)threadIdx.y) * kTileColsS + 4 + (int)threadIdx.x;
-        int nc[NB];
-        nc[0] = me[-kTileColsS];
-        nc[1] = me[kTileColsS];
-        nc[2] = me[-1];
-        nc[3] = me[1];
-        if constexpr (NB == 8) {
-            nc[4] = me[-kTileColsS - 1];
-            nc[5] = me[-kTileColsS + 1];
-            nc[6] = me[kTileColsS - 1];
-            nc[7] = me[kTileColsS + 1];
-        }
-        const int xi = me[0];
-        const uint32_t ub = U_s[tid];
-        int s = 0;
-        bool certain = true;
-        if (valid)
-            s = draw_small<LMAX, NB, MASK>(a.m, pt, nc, g, xi, ub, pre, certain);
-        const bool need = valid && !certain;
-        if (__any_sync(0xFFFFFFFFu, need)) {
-            SiteIn<NB> in{};
-            in.g = g;
-            in.xi = xi;
-            in.ub = ub;
 #pragma unroll
-            for (int j = 0; j < NB; ++j)
-                in.xni[j] = nc[j] == 16 ? kMissingLabelI : nc[j];
-            s = warp_redraw_fp64<NB>(a.m, need, in, s, a.fp64_draws);
+        for (int i = 0; i < kSPT; ++i) {
+            const int lr = wp + kWarps * i;
+            const int r = r0 + lr;
+            const bool valid = r < a.H && c < a.W;
+            const uint8_t *me = cb + (1 + lr) * kCodeCols + 4 + lane;
+            int nc[NB];
+            nc[0] = me[-kCodeCols];
+            nc[1] = me[kCodeCols];
+            nc[2] = me[-1];
+            nc[3] = me[1];
+            if constexpr (NB == 8) {
+                nc[4] = me[-kCodeCols - 1];
+                nc[5] = me[-kCodeCols + 1];
+                nc[6] = me[kCodeCols - 1];
+                nc[7] = me[kCodeCols + 1];
+            }
+            const int xi = me[0];
+            const uint32_t ub = Uw[i * kBX + lane];
+            int s = 0;
+            bool certain = true;
+            if (valid)
+                s = draw_small<LMAX, NB, MASK>(a.m, pt, nc, g[i], xi, ub, pre, certain);
+            const bool need = valid && !certain;
+            if (__any_sync(0xFFFFFFFFu, need)) {
+                SiteIn<NB> in{};
+                in.g = g[i];
+                in.xi = xi;
+                in.ub = ub;
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    in.xni[j] = nc[j] == 16 ? kMissingLabelI : nc[j];
+                s = warp_redraw_fp64<NB>(a.m, need, in, s, a.fp64_draws);
+            }
+            if (valid) {
+                a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+                if (acc_on)
+                    a.acc[(size_t)r * a.W + c] = acc_old[i] + (float)s;
+            }
         }
-        if (valid) {
-            a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-            if (acc_on)
-                a.acc[(size_t)r * a.W + c] = acc_old + (float)s;
+        tx += step_x;
+        ty += step_y;
+        if (tx >= tiles_x) {
+            tx -= tiles_x;
+            ++ty;
         }
     }
 }
@@ -308,14 +337,15 @@ cudaError_t launch_small_t(const SweepArgs &a, cudaStream_t st)
     if (e != cudaSuccess)
         return e;
     const int tiles_x = (a.W + kBX - 1) / kBX;
-    const long long ntiles = (long long)tiles_x * ((a.H + kBY - 1) / kBY);
+    const long long ntiles = (long long)tiles_x * ((a.H + kTileR - 1) / kTileR);
     if (ntiles <= 0)
         return cudaSuccess;
     if (ntiles >= (1ll << 31))
         return cudaErrorInvalidValue;
     const long long cap = (long long)per_sm[dev] * sms;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    pca_small_kernel<LMAX, NB, MASK><<<grid, dim3(kBX, kBY), 0, st>>>(a, tiles_x, (int)ntiles);
+    pca_small_kernel<LMAX, NB, MASK><<<grid, dim3(kBX, kWarps), 0, st>>>(a, tiles_x,
+                                                                      (int)ntiles);
     return cudaGetLastError();
 }
 
@@ -342,8 +372,9 @@ cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t st)
 
 bool pca_small_eligible(const DevModel &m)
 {
-    return m.ptab != nullptr && m.L >= kSmallMinLabels && m.L <= kSmallMaxLabels &&
-           m.norm == 0 && m.gam <= 0.0f && m.alpha <= 0.0f && (m.nbhd == 4 || m.nbhd == 8);
+    return m.ptab != nullptr && m.ta64 != nullptr && m.pr64 != nullptr &&
+           m.L >= kSmallMinLabels && m.L <= kSmallMaxLabels && m.norm == 0 && m.gam <= 0.0f &&
+           m.alpha <= 0.0f && (m.nbhd == 4 || m.nbhd == 8);
 }
 
 cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t st)
