@@ -91,12 +91,13 @@ def _args():
     p.add_argument("--blocking", type=int, default=0,
                    help="profile case: sweeps per TMA-tiled launch (0: unblocked)")
     p.add_argument("--workload", default="chain",
-                   choices=["chain", "batch", "serve", "blocking", "protocol"],
+                   choices=["chain", "batch", "serve", "blocking", "protocol", "cpu"],
                    help="chain: the default line; batch: uneven images x 4 chains in one "
                         "persistent launch vs one chain per launch; serve: Poisson request "
                         "stream through the continuous-batching server; blocking: 8192^2 "
                         "unblocked vs k = 1..8; protocol: the paper's annealed runs on MRF "
-                        "images and the q grid")
+                        "images and the q grid; cpu: the FP64 oracle on the host cores "
+                        "(single-threaded Gibbs and PCA, OpenMP PCA) beside the GPU chain")
     p.add_argument("--kernel", default="auto",
                    choices=["auto", "cuda_core", "tensor", "wave", "small"],
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
@@ -937,6 +938,79 @@ def run_blocking(a):
     print(json.dumps(line), flush=True)
 
 
+def run_cpu_baselines(a):
+    """The CPU baseline table: the FP64 oracle on this machine's host cores --
+    sequential single-site Gibbs in column-major order (the paper's CPU
+    baseline) and lazy PCA single-threaded and with OpenMP over rows (the
+    same labels either way) -- for the binary 64x64 chain (500 sweeps, in
+    full), the 512x512 L=256 chain (bounded samples, and the full 2000-sweep
+    PCA run with OpenMP) and 1024x1024 crops of the 8192x8192 images (5
+    sweeps), next to the same chains on the GPU."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import paper_2507_14869_gb300 as pc
+    from pcad_inputs import binary_64, greyscale_512
+
+    torch.cuda.set_device(0)
+    cores = os.cpu_count()
+    omp = oracle.num_threads()
+
+    def orc_rate(fn, sites, sweeps, threads):
+        oracle.set_threads(threads)
+        t0 = time.perf_counter()
+        fn()
+        dt = time.perf_counter() - t0
+        oracle.set_threads(omp)
+        return {"s": dt, "site_updates_per_s": sites * sweeps / dt, "threads": threads,
+                "sweeps": sweeps}
+
+    def gpu_wall(g, m, n, burn, sampler=0, reps=3):
+        ts = []
+        for r in range(reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with pc.Chain(g, m, seed=1, chain_id=0, burn_in=burn, sampler=sampler) as ch:
+                ch.run(n)
+                ch.mean()
+            if r:
+                ts.append(time.perf_counter() - t0)
+        return {"s": min(ts), "site_updates_per_s": g.size * n / min(ts),
+                "path": "create + run + read mean (wall clock)"}
+
+    rows = {}
+    clean, g1, m1 = binary_64()
+    rows["binary_64"] = {
+        "workload": "64x64 binary, Ising c_P=1.2, flip p=0.1, lambda=1.0, 500 sweeps",
+        "gibbs_column_major_1_thread": orc_rate(
+            lambda: oracle.run_chain(m1, g1, 500, 100, seed=1, sampler=1, order=oracle.ORDER_COL),
+            g1.size, 500, 1),
+        "pca_1_thread": orc_rate(lambda: oracle.run_chain(m1, g1, 500, 100, seed=1), g1.size,
+                                 500, 1),
+        "gpu_pca": gpu_wall(g1, m1, 500, 100), "gpu_gibbs": gpu_wall(g1, m1, 500, 100, 1)}
+    clean2, g2, m2 = greyscale_512(seed=2)
+    rows["greyscale_512_L256"] = {
+        "workload": G512_WORKLOAD,
+        "gibbs_column_major_1_thread": orc_rate(
+            lambda: oracle.run_chain(m2, g2, 4, 0, seed=2, sampler=1, order=oracle.ORDER_COL),
+            g2.size, 4, 1),
+        "pca_1_thread": orc_rate(lambda: oracle.run_chain(m2, g2, 4, 0, seed=2), g2.size, 4, 1),
+        "pca_openmp_full_2000": orc_rate(lambda: oracle.run_chain(m2, g2, 2000, 500, seed=2),
+                                         g2.size, 2000, omp),
+        "gpu_pca": gpu_wall(g2, m2, 2000, 500)}
+    for L in (16, 256):
+        _, g3, m3 = _inputs(L)
+        crop = _crop(g3, 1024)
+        rows[f"crop_1024_of_8192_L{L}"] = {
+            "pca_1_thread": orc_rate(lambda: oracle.run_chain(m3, crop, 5, 0, seed=3), crop.size,
+                                     5, 1),
+            "pca_openmp": orc_rate(lambda: oracle.run_chain(m3, crop, 5, 0, seed=3), crop.size,
+                                   5, omp)}
+    print(json.dumps({"metric": "CPU baseline (FP64 oracle) beside the GPU", "cores": cores,
+                      "openmp_threads": omp, "rows": rows}), flush=True)
+
+
 def profile_case(side: int, L: int, sweeps: int, sampler: int, blocking: int = 0,
                  kernel: str = "auto"):
     """Small seeded case for ncu: greyscale scene at L labels (sigma 20 for
@@ -980,6 +1054,8 @@ def main():
         run_blocking(a)
     elif a.workload == "protocol":
         run_protocol(a)
+    elif a.workload == "cpu":
+        run_cpu_baselines(a)
     else:
         run_ours(a)
 
