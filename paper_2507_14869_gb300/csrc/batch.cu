@@ -387,6 +387,91 @@ pcad_status tc_set_issue(const TcSet &ts, const std::vector<SlotDesc> &desc,
     return PCAD_OK;
 }
 
+// Large chains with small-label models (3 <= L <= 16, c >= 0) run the
+// small-label kernel, one launch per chain and sweep: a chain of at least
+// kSmallBigTiles tiles of 16 x 32 sites fills the GPU alone, and the
+// small-label kernel measured about twice the batched CUDA-core kernel's
+// rate at L = 16 on GB300.  Planes follow the device sweep counter and each
+// launch skips sweeps at or past the chain's budget, so a captured slice
+// stays valid for any start.  One pair table per distinct truncation T.
+constexpr long kSmallBigTiles = 1216;
+
+struct SmallSet {
+    std::vector<int> big;          // slots launched one at a time
+    std::vector<int> table_T;      // T of each pair table
+    uint32_t *tables = nullptr;    // the pair tables, ptab_words() words each
+    size_t cap = 0;                // tables allocated
+};
+
+// Split `in` into the small-label slots launched one at a time and the rest.
+pcad_status small_set_build(SmallSet &ss, const std::vector<SlotDesc> &d,
+                            const std::vector<int> &in, std::vector<int> &rest, cudaStream_t st)
+{
+    ss.big.clear();
+    ss.table_T.clear();
+    rest.clear();
+    for (int i : in) {
+        DevModel m = d[i].m;
+        m.ptab = reinterpret_cast<const uint32_t *>(&ss);   // eligibility of the model only
+        const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 15) / 16);
+        if (tiles >= kSmallBigTiles && pca_small_eligible(m)) {
+            ss.big.push_back(i);
+            if (std::find(ss.table_T.begin(), ss.table_T.end(), m.T) == ss.table_T.end())
+                ss.table_T.push_back(m.T);
+        } else {
+            rest.push_back(i);
+        }
+    }
+    if (ss.table_T.size() > ss.cap) {
+        if (ss.tables)
+            B_TRY(cudaFreeAsync(ss.tables, st));
+        ss.tables = nullptr;
+        ss.cap = std::max(ss.table_T.size(), 2 * ss.cap);
+        B_TRY(cudaMallocAsync((void **)&ss.tables, ss.cap * ptab_words() * sizeof(uint32_t), st));
+    }
+    for (size_t k = 0; k < ss.table_T.size(); ++k)
+        B_TRY(launch_ptab(ss.table_T[k], ss.tables + k * ptab_words(), st));
+    return PCAD_OK;
+}
+
+// n sweeps of every small-label slot launched one at a time.
+pcad_status small_set_issue(const SmallSet &ss, const std::vector<SlotDesc> &desc, int n,
+                            cudaStream_t st)
+{
+    for (int i : ss.big) {
+        const SlotDesc &d = desc[i];
+        SweepArgs a{};
+        a.g = d.g;
+        a.acc = d.acc;
+        a.fp64_draws = d.fp64_draws;
+        a.sweep_base = d.tdev;
+        a.seed = d.seed;
+        a.H = d.H;
+        a.W = d.W;
+        a.pitch = d.pitch;
+        a.chain = d.chain;
+        a.burn_in = d.burn_in;
+        a.m = d.m;
+        const size_t k = std::find(ss.table_T.begin(), ss.table_T.end(), d.m.T) - ss.table_T.begin();
+        a.m.ptab = ss.tables + k * ptab_words();
+        for (int s = 0; s < n; ++s) {
+            a.sweep_off = (uint32_t)s;
+            B_TRY(launch_pca_small(a, st, d.x[0], d.x[1], d.budget));
+        }
+    }
+    return PCAD_OK;
+}
+
+void small_set_free(SmallSet &ss, cudaStream_t st)
+{
+    if (ss.tables)
+        cudaFreeAsync(ss.tables, st);
+    ss.tables = nullptr;
+    ss.cap = 0;
+    ss.big.clear();
+    ss.table_T.clear();
+}
+
 void tc_set_free(TcSet &ts, cudaStream_t st)
 {
     for (TcGroup &g : ts.groups)
@@ -444,6 +529,7 @@ struct pcad_batch {
     int wgrid = 0;
     int *d_err = nullptr;            // wavefront launches: bounded-wait flag
     TcSet tc;                        // chains on the tensor-core sweep
+    SmallSet small;                  // large small-label chains, launched one at a time
     float tune_ms = 0.0f;
     cudaGraphExec_t graph = nullptr;
 };
@@ -452,12 +538,15 @@ namespace {
 
 pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
 {
-    std::vector<int> all(b->n), active;
+    std::vector<int> all(b->n), others, active;
     for (int i = 0; i < b->n; ++i)
         all[i] = i;
-    // chains with a tensor-core table run on the batched tensor-core sweep;
-    // the tiling below applies to the others
-    pcad_status st0 = tc_set_build(b->tc, b->desc, all, active, b->stream);
+    // chains with a tensor-core table run on the batched tensor-core sweep,
+    // large small-label chains on their own launches; the tiling below
+    // applies to the others
+    pcad_status st0 = tc_set_build(b->tc, b->desc, all, others, b->stream);
+    if (st0 == PCAD_OK)
+        st0 = small_set_build(b->small, b->desc, others, active, b->stream);
     if (st0 != PCAD_OK)
         return st0;
     if (lpt == kOrderWave) {
@@ -492,6 +581,8 @@ pcad_status batch_issue_slice(pcad_batch *b, cudaStream_t s)
 {
     pcad_status st0 = tc_set_issue(b->tc, b->desc, b->d_slots, b->d_t, b->d_budget, kSlice,
                                    b->d_grab, b->d_err, s);
+    if (st0 == PCAD_OK)
+        st0 = small_set_issue(b->small, b->desc, kSlice, s);
     if (st0 != PCAD_OK)
         return st0;
     if (b->lpt == kOrderWave) {
@@ -697,6 +788,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
         if (b->wb.mem)
             cudaFreeAsync(b->wb.mem, b->stream);
         tc_set_free(b->tc, b->stream);
+        small_set_free(b->small, b->stream);
         cudaFreeAsync(b->block, b->stream);
         cudaStreamSynchronize(b->stream);
         delete b;
@@ -882,6 +974,7 @@ void pcad_batch_destroy(pcad_batch *b)
     if (b->wb.mem)
         cudaFreeAsync(b->wb.mem, b->stream);
     tc_set_free(b->tc, b->stream);
+    small_set_free(b->small, b->stream);
     cudaFreeAsync(b->block, b->stream);
     cudaStreamSynchronize(b->stream);
     delete b;
@@ -941,6 +1034,7 @@ struct pcad_server {
     int *d_grab = nullptr;
     WaveBuf wb;                   // wavefront work list of the admitted requests
     TcSet tc;                     // requests on the tensor-core sweep
+    SmallSet small;               // large small-label requests, launched one at a time
     bool items_dirty = true;
     int grid = 0;
     int n_active = 0;              // admitted requests (both kinds of launch)
@@ -1112,7 +1206,10 @@ pcad_status server_items(pcad_server *sv)
         if (sv->slot_req[i] != 0 && sv->reqs[sv->slot_req[i]].running)
             all.push_back(i);
     // requests with a tensor-core table run on the batched tensor-core sweep
-    pcad_status st = tc_set_build(sv->tc, sv->desc, all, active, sv->stream);
+    std::vector<int> others;
+    pcad_status st = tc_set_build(sv->tc, sv->desc, all, others, sv->stream);
+    if (st == PCAD_OK)
+        st = small_set_build(sv->small, sv->desc, others, active, sv->stream);
     if (st != PCAD_OK)
         return st;
     long tiles4 = 0;
@@ -1280,6 +1377,8 @@ pcad_status pcad_server_step(pcad_server *sv, int slice_sweeps, int *n_active, i
         // one wavefront launch per kind runs the slice for every admitted request
         st = tc_set_issue(sv->tc, sv->desc, sv->d_slots, sv->d_t, sv->d_budget, slice_sweeps,
                           sv->d_grab, sv->d_err, sv->stream);
+        if (st == PCAD_OK)
+            st = small_set_issue(sv->small, sv->desc, slice_sweeps, sv->stream);
         if (st == PCAD_OK && sv->wb.n_items > 0)
             st = wave_issue(sv->wb, sv->d_slots, slice_sweeps, sv->d_grab, sv->d_err, sv->grid,
                             sv->stream);
@@ -1411,6 +1510,7 @@ void pcad_server_destroy(pcad_server *sv)
     if (sv->wb.mem)
         cudaFreeAsync(sv->wb.mem, sv->stream);
     tc_set_free(sv->tc, sv->stream);
+    small_set_free(sv->small, sv->stream);
     cudaFreeAsync(sv->ctl, sv->stream);
     cudaStreamSynchronize(sv->stream);
     for (int k = 0; k < 2; ++k)

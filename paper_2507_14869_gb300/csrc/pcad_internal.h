@@ -309,7 +309,10 @@ constexpr int kSmallMaxLabels = 16;
 int ptab_words();
 cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t s);
 bool pca_small_eligible(const DevModel &m);
-cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s);
+// x0 / x1 (optional): the planes of even / odd sweep indices, used in place of
+// a.xin / a.xout; budget (optional): sweeps with index >= *budget are skipped.
+cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s, uint8_t *x0 = nullptr,
+                             uint8_t *x1 = nullptr, const uint32_t *budget = nullptr);
 
 // Largest row offset of a band chain (Philox rows are 32-bit).
 constexpr int kMaxRowOffset = 1 << 30;

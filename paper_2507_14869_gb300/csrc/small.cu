@@ -202,9 +202,14 @@ __device__ __forceinline__ int draw_small(const DevModel &m, const uint32_t *pt,
     return min(s, m.L - 1);
 }
 
+// planes: a.xin -> a.xout, or (par_from_t) x0 / x1 holding the states of
+// even / odd sweep indices; budget (optional): sweeps with index >= *budget
+// are skipped (a chain of a batch or of the server).
 template <int LMAX, int NB, bool MASK>
 __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, int tiles_x,
-                                                             int ntiles)
+                                                             int ntiles, uint8_t *x0, uint8_t *x1,
+                                                             int par_from_t,
+                                                             const uint32_t *budget)
 {
     __shared__ __align__(16) uint32_t pt[kPtabWords];
     __shared__ __align__(16) uint32_t U_s[kWarps * kSPT * kBX];
@@ -215,6 +220,10 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
     for (int i = tid; i < kPtabWords / 4; i += kThreads)
         reinterpret_cast<uint4 *>(pt)[i] = __ldg(reinterpret_cast<const uint4 *>(a.m.ptab) + i);
     const uint32_t t = sweep_index(a);
+    if (budget && t >= *budget)
+        return;   // the whole launch: before any barrier
+    const uint8_t *xin = par_from_t ? ((t & 1u) ? x1 : x0) : a.xin;
+    uint8_t *xout = par_from_t ? ((t & 1u) ? x0 : x1) : a.xout;
     const bool acc_on = accumulate_after(a, t);
     const uint8_t *cb = reinterpret_cast<const uint8_t *>(codes);
     float *pre = pre_s + tid * kPrefixStride;
@@ -248,7 +257,7 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
             const int gr = r0 - 1 + wr, gc = c0 - 4 + 4 * wc;
             uint32_t word = 0x10101010u;
             if (gr >= 0 && gr < a.H && gc >= 0 && gc < a.W) {
-                word = *reinterpret_cast<const uint32_t *>(a.xin + (size_t)gr * a.pitch + gc);
+                word = *reinterpret_cast<const uint32_t *>(xin + (size_t)gr * a.pitch + gc);
                 if (gc + 3 >= a.W) {   // the image's right edge inside this word
                     const uint32_t mask = (1u << (8 * (a.W - gc))) - 1u;
                     word = (word & mask) | (0x10101010u & ~mask);
@@ -300,7 +309,7 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
                 s = warp_redraw_fp64<NB>(a.m, need, in, s, a.fp64_draws);
             }
             if (valid) {
-                a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+                xout[(size_t)r * a.pitch + c] = (uint8_t)s;
                 if (acc_on)
                     a.acc[(size_t)r * a.W + c] = acc_old[i] + (float)s;
             }
@@ -315,7 +324,8 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
 }
 
 template <int LMAX, int NB, bool MASK>
-cudaError_t launch_small_t(const SweepArgs &a, cudaStream_t st)
+cudaError_t launch_small_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int par_from_t,
+                           const uint32_t *budget, cudaStream_t st)
 {
     static int per_sm[64] = {};
     int dev = 0;
@@ -344,17 +354,20 @@ cudaError_t launch_small_t(const SweepArgs &a, cudaStream_t st)
         return cudaErrorInvalidValue;
     const long long cap = (long long)per_sm[dev] * sms;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    pca_small_kernel<LMAX, NB, MASK><<<grid, dim3(kBX, kWarps), 0, st>>>(a, tiles_x,
-                                                                      (int)ntiles);
+    pca_small_kernel<LMAX, NB, MASK><<<grid, dim3(kBX, kWarps), 0, st>>>(
+        a, tiles_x, (int)ntiles, x0, x1, par_from_t, budget);
     return cudaGetLastError();
 }
 
 template <int NB>
-cudaError_t dispatch_small(const SweepArgs &a, cudaStream_t st)
+cudaError_t dispatch_small(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int par_from_t,
+                           const uint32_t *budget, cudaStream_t st)
 {
     if (a.m.L <= 8)
-        return a.m.L == 8 ? launch_small_t<8, NB, false>(a, st) : launch_small_t<8, NB, true>(a, st);
-    return a.m.L == 16 ? launch_small_t<16, NB, false>(a, st) : launch_small_t<16, NB, true>(a, st);
+        return a.m.L == 8 ? launch_small_t<8, NB, false>(a, x0, x1, par_from_t, budget, st)
+                          : launch_small_t<8, NB, true>(a, x0, x1, par_from_t, budget, st);
+    return a.m.L == 16 ? launch_small_t<16, NB, false>(a, x0, x1, par_from_t, budget, st)
+                       : launch_small_t<16, NB, true>(a, x0, x1, par_from_t, budget, st);
 }
 
 }  // namespace
@@ -377,14 +390,19 @@ bool pca_small_eligible(const DevModel &m)
            m.alpha <= 0.0f && (m.nbhd == 4 || m.nbhd == 8);
 }
 
-cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t st)
+cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t st, uint8_t *x0, uint8_t *x1,
+                             const uint32_t *budget)
 {
     if (!pca_small_eligible(a.m))
         return cudaErrorInvalidValue;
+    const int par = x0 != nullptr ? 1 : 0;
     // the label tile is staged with aligned 32-bit loads
-    if ((a.pitch & 3) != 0 || (reinterpret_cast<uintptr_t>(a.xin) & 3u) != 0)
+    const uintptr_t align = par ? (reinterpret_cast<uintptr_t>(x0) | reinterpret_cast<uintptr_t>(x1))
+                                : reinterpret_cast<uintptr_t>(a.xin);
+    if ((a.pitch & 3) != 0 || (align & 3u) != 0)
         return cudaErrorMisalignedAddress;
-    return a.m.nbhd == 8 ? dispatch_small<8>(a, st) : dispatch_small<4>(a, st);
+    return a.m.nbhd == 8 ? dispatch_small<8>(a, x0, x1, par, budget, st)
+                         : dispatch_small<4>(a, x0, x1, par, budget, st);
 }
 
 }  // namespace pcad

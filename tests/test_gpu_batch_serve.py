@@ -338,3 +338,44 @@ def test_server_policy_is_validated(pc):
         pc.pcad_server_set_policy(sv, pc.SERVE_SRPT, 3.0)
     finally:
         pc.pcad_server_destroy(sv)
+
+
+def test_large_small_label_slots_in_batch_and_server(pc):
+    """Chains of at least 1216 tiles of 16 x 32 sites with a small-label model
+    (3 <= L <= 16) run the small-label kernel as their own launches inside the
+    batch's and the server's slices (planes chosen by the device sweep
+    counter, budgets ending inside slices): results equal the chains run
+    alone."""
+    big16 = (_grey(30, 800, 800, 16, 1.0),
+             Model(L=16, pair=TL, pair_coef=0.05, pair_T=30, sigma=1.0, inertia=2.0), 31, 6, 9)
+    big8 = (_grey(31, 640, 1000, 8, 1.5),
+            Model(L=8, nbhd=8, pair=POTTS, pair_coef=0.7, sigma=1.5, inertia=0.6), 32, 7, 4)
+    other = (_grey(32, 90, 70, 16, 1.2),
+             Model(L=16, pair=TL, pair_coef=0.6, pair_T=3, sigma=1.2, inertia=1.0), 33, 8, 5)
+    jobs = [big16, big8, other]
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_run(b, 21)
+        pc.pcad_batch_run(b, 30)
+        pc.pcad_batch_sync(b)
+        for i, (g, m, seed, chain, burn) in enumerate(jobs):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, 51)
+            assert np.array_equal(pc.pcad_batch_read_sample(b, i, *g.shape), xs), i
+            assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
+    finally:
+        pc.pcad_batch_destroy(b)
+    budgets = [37, 20, 45]
+    sv = pc.pcad_server_create(8, 1 << 31)
+    try:
+        ids, shapes = [], {}
+        for (g, m, seed, chain, burn), n in zip(jobs, budgets):
+            rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, n)
+            ids.append(rid)
+            shapes[rid] = g.shape
+        res = _serve_until_done(pc, sv, list(ids), shapes, slice_sweeps=16)
+        for rid, (g, m, seed, chain, burn), n in zip(ids, jobs, budgets):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, n)
+            assert np.array_equal(res[rid][0], xs)
+            assert np.array_equal(res[rid][1], ms)
+    finally:
+        pc.pcad_server_destroy(sv)
