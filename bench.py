@@ -63,7 +63,7 @@ NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_
 NCU_DIRECT_BYTES_PER_SITE = None
 NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at 8192^2 L=16"
 
-KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4}
+KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5}
 KERNEL_NAMES = {
     1: "pca_direct_kernel (CUDA cores, one launch per sweep)",
     2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
@@ -99,7 +99,7 @@ def _args():
                         "images and the q grid; cpu: the FP64 oracle on the host cores "
                         "(single-threaded Gibbs and PCA, OpenMP PCA) beside the GPU chain")
     p.add_argument("--kernel", default="auto",
-                   choices=["auto", "cuda_core", "tensor", "wave", "small"],
+                   choices=["auto", "cuda_core", "tensor", "wave", "small", "resident"],
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
                         "auto = the tensor-core sweep for eligible models with L >= 192, else "
                         "the per-sweep or wavefront CUDA-core kernel; tensor = prior sums by "
@@ -575,6 +575,7 @@ def _batch_object(pc, torch, stream, n_images, rank=0, world=1):
 
     b = pc.pcad_batch_create(jobs, autotune=True, stream=stream)
     info = pc.pcad_batch_info(b)
+    info["sweeps_per_slice"] = pc.pcad_batch_slice(b)
     pc.pcad_batch_run(b, 16)
     pc.pcad_batch_reset(b)
     pc.pcad_batch_sync(b)

@@ -168,21 +168,33 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * of all labels of a site from a table of neighbour pairs (16 bytes per pair
  * of labels, in shared memory) and draws from chunk prefix sums in
  * registers; same labels as the other kernels.  AUTO takes it for every
- * model it accepts. */
+ * model it accepts.  PCAD_KERNEL_RESIDENT (L = 2, 4- or 8-neighbourhood,
+ * either sampler, H * ceil(W / 4) <= 4096, e.g. up to 128 x 128, and at most
+ * 200 KB of shared memory; PCAD_EINVAL otherwise) runs all the sweeps of a
+ * run in one launch of one 1024-thread CTA that keeps the state in shared
+ * memory and draws each site from a table of exact thresholds on its
+ * uniform, one per site configuration (x_i, g_i, label-1 neighbours,
+ * neighbours outside the image), computed at set-up from the FP32 draw and
+ * FP64 re-draw of the other kernels; same labels and the same FP64 re-draw
+ * count (with two labels every inertia price is the L0 one).  AUTO takes it
+ * for the images it accepts (no energy tracking, no temporal blocking). */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
     PCAD_KERNEL_TENSOR = 2,
     PCAD_KERNEL_WAVE = 3,
-    PCAD_KERNEL_SMALL = 4
+    PCAD_KERNEL_SMALL = 4,
+    PCAD_KERNEL_RESIDENT = 5
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 
 /* The kernel the chain's next sweeps run: PCAD_KERNEL_CUDA_CORE (one launch
- * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR, or
- * -k for temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO
- * the tensor-core kernel is taken for eligible models with L >= 192 and no
- * energy tracking; PCAD_KERNEL_SMALL for the models it accepts; otherwise
+ * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR,
+ * PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT, or -k for temporal blocking with
+ * k sweeps per launch.  With PCAD_KERNEL_AUTO the resident kernel
+ * is taken for the two-label images it accepts without energy tracking; the
+ * tensor-core kernel for eligible models with L >= 192 and no energy
+ * tracking; PCAD_KERNEL_SMALL for the models it accepts; otherwise
  * the wavefront kernel for L >= 16 when the
  * image has between 1/2 and 3 waves of 4 x 32 tiles at 10 resident tiles
  * per multiprocessor (the sizes where it measured faster on GB300), the
@@ -373,6 +385,13 @@ pcad_status pcad_batch_sync(pcad_batch *b);
  * order), 1 (costliest first) or 2 (wavefront, one launch per 16 sweeps).
  * Results do not depend on it.  Stream-ordered; PCAD_EINVAL otherwise. */
 pcad_status pcad_batch_set_tiling(pcad_batch *b, int tile_rows, int order);
+/* Sweeps per captured slice: 8, 16 (the default) or 32; a wavefront slice
+ * is one persistent launch, so this is the number of sweeps per launch.
+ * sweeps > 0 sets it, 0 keeps it; *current (may be NULL) receives the value
+ * in use.  The autotuner chooses it together with the tiling (wavefront
+ * orders try 8, 16 and 32, per-sweep orders 16).  Results do not depend on
+ * it.  PCAD_EINVAL for other values. */
+pcad_status pcad_batch_slice(pcad_batch *b, int sweeps, int *current);
 /* Current sample / posterior mean of chain i (host memory, as for a chain). */
 pcad_status pcad_batch_read_sample(pcad_batch *b, int i, uint8_t *host_out, int out_pitch);
 pcad_status pcad_batch_read_mean(pcad_batch *b, int i, float *host_out);

@@ -15,7 +15,7 @@ from ._capi import (  # noqa: F401
     pcad_chain_set_row_offset, pcad_chain_write_rows_dev,
     pcad_bands_create, pcad_bands_run, pcad_bands_sync, pcad_bands_read_sample,
     pcad_bands_read_mean, pcad_bands_info, pcad_bands_destroy, PCAD_KERNEL_CUDA_CORE, PCAD_KERNEL_TENSOR, PCAD_KERNEL_WAVE,
-    PCAD_KERNEL_SMALL,
+    PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT,
     pcad_chain_energy, pcad_chain_track_energy, pcad_chain_read_energies,
     pcad_chain_read_min_state, pcad_chain_kernel_in_use, pcad_chain_set_model, pcad_chain_run_schedule,
     pcad_batch_set_model,
@@ -23,7 +23,7 @@ from ._capi import (  # noqa: F401
     pcad_pca_run_noalloc, pcad_version, pcad_model_margins, N_MARGINS,
     PcadJob, pcad_batch_create, pcad_batch_destroy, pcad_batch_info, pcad_batch_read_mean,
     pcad_batch_read_sample, pcad_batch_reset, pcad_batch_run, pcad_batch_sync,
-    pcad_batch_set_tiling,
+    pcad_batch_set_tiling, pcad_batch_slice,
     pcad_server_create, pcad_server_destroy, pcad_server_info, pcad_server_poll,
     pcad_server_step, pcad_server_submit, pcad_server_set_limits, pcad_server_set_policy,
     SERVE_FIFO, SERVE_SRPT,

@@ -139,6 +139,7 @@ def _declare(L):
         "pcad_batch_reset": [vp],
         "pcad_batch_sync": [vp],
         "pcad_batch_set_tiling": [vp, ctypes.c_int, ctypes.c_int],
+        "pcad_batch_slice": [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
         "pcad_batch_read_sample": [vp, ctypes.c_int, u8p, ctypes.c_int],
         "pcad_batch_read_mean": [vp, ctypes.c_int, fp],
         "pcad_batch_info": [vp, u64p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -537,6 +538,13 @@ def pcad_batch_read_mean(h, i: int, H: int, W: int) -> np.ndarray:
     return out
 
 
+def pcad_batch_slice(h, sweeps: int = 0) -> int:
+    """Set (8, 16 or 32; 0 keeps) and return the batch's sweeps per slice."""
+    cur = ctypes.c_int()
+    _check("pcad_batch_slice", lib().pcad_batch_slice(h, int(sweeps), ctypes.byref(cur)))
+    return cur.value
+
+
 def pcad_batch_info(h) -> dict:
     t = ctypes.c_uint64()
     rows, lpt, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
@@ -692,6 +700,7 @@ PCAD_KERNEL_CUDA_CORE = 1
 PCAD_KERNEL_TENSOR = 2
 PCAD_KERNEL_WAVE = 3
 PCAD_KERNEL_SMALL = 4
+PCAD_KERNEL_RESIDENT = 5
 
 
 def pcad_chain_set_kernel(h, kind: int):

@@ -9,9 +9,11 @@
 // the launch.
 //
 // pcad_batch: a fixed set of chains run in lockstep; sweeps are issued in
-// slices of kSlice captured once into a CUDA graph.  At creation an optional
-// autotuner times the tile height and the work-list order on the batch itself
-// and caches the choice per batch signature.
+// slices of 8, 16 or 32 sweeps captured once into a CUDA graph (a wavefront
+// slice is one persistent launch, so the slice length is the number of
+// sweeps per launch).  At creation an optional autotuner times the tile
+// height, the work-list order and the slice length on the batch itself and
+// caches the choice per batch signature.
 //
 // pcad_server: requests of different sizes, models and sweep budgets are
 // admitted into free slots while the HBM budget allows, run slice by slice
@@ -33,7 +35,8 @@ using namespace pcad;
 
 namespace {
 
-constexpr int kSlice = 16;        // sweeps per batch slice (one graph)
+constexpr int kSlice = 16;        // default sweeps per batch slice (one graph)
+constexpr int kMaxSlice = 32;     // longest slice (sizes the per-sweep work counters)
 constexpr int kOrderWave = 2;     // batch work order: one wavefront launch per slice
 // Tile height of the server's wavefront launches: 4 rows keep the slice's
 // critical path (one tile after another through its sweeps) short when
@@ -497,7 +500,8 @@ struct TuneKey {
 struct TuneVal {
     int rows;
     int lpt;
-    float ms;
+    int slice;
+    float ms;     // per sweep
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneVal> g_tune_cache;
@@ -525,6 +529,7 @@ struct pcad_batch {
     int grid = 0;
     int rows = 4;
     int lpt = 1;                     // work order: 0 image, 1 costliest first, 2 wavefront
+    int slice = kSlice;              // sweeps per captured slice (per wavefront launch)
     WaveBuf wb;                      // order 2: the wavefront work list
     int wgrid = 0;
     int *d_err = nullptr;            // wavefront launches: bounded-wait flag
@@ -536,7 +541,7 @@ struct pcad_batch {
 
 namespace {
 
-pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
+pcad_status batch_set_items(pcad_batch *b, int rows, int lpt, int slice)
 {
     std::vector<int> all(b->n), others, active;
     for (int i = 0; i < b->n; ++i)
@@ -570,6 +575,7 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
     }
     b->rows = rows;
     b->lpt = lpt;
+    b->slice = slice;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -579,23 +585,24 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt)
 
 pcad_status batch_issue_slice(pcad_batch *b, cudaStream_t s)
 {
-    pcad_status st0 = tc_set_issue(b->tc, b->desc, b->d_slots, b->d_t, b->d_budget, kSlice,
+    const int n = b->slice;
+    pcad_status st0 = tc_set_issue(b->tc, b->desc, b->d_slots, b->d_t, b->d_budget, n,
                                    b->d_grab, b->d_err, s);
     if (st0 == PCAD_OK)
-        st0 = small_set_issue(b->small, b->desc, kSlice, s);
+        st0 = small_set_issue(b->small, b->desc, n, s);
     if (st0 != PCAD_OK)
         return st0;
     if (b->lpt == kOrderWave) {
-        pcad_status st = wave_issue(b->wb, b->d_slots, kSlice, b->d_grab, b->d_err, b->wgrid, s);
+        pcad_status st = wave_issue(b->wb, b->d_slots, n, b->d_grab, b->d_err, b->wgrid, s);
         if (st != PCAD_OK)
             return st;
     } else if (b->n_items > 0) {
-        B_TRY(cudaMemsetAsync(b->d_grab, 0, kSlice * sizeof(int), s));
-        for (int k = 0; k < kSlice; ++k)
+        B_TRY(cudaMemsetAsync(b->d_grab, 0, n * sizeof(int), s));
+        for (int k = 0; k < n; ++k)
             B_TRY(launch_batch_sweep(b->d_slots, b->d_items, b->n_items, b->d_grab + k,
                                      (uint32_t)k, b->grid, s));
     }
-    B_TRY(launch_batch_advance(b->d_slots, b->n, kSlice, s));
+    B_TRY(launch_batch_advance(b->d_slots, b->n, (uint32_t)n, s));
     return PCAD_OK;
 }
 
@@ -633,7 +640,7 @@ pcad_status batch_run_sweeps(pcad_batch *b, int nsweeps)
         if (st != PCAD_OK)
             return st;
     }
-    for (int left = nsweeps; left > 0; left -= kSlice)
+    for (int left = nsweeps; left > 0; left -= b->slice)
         B_TRY(cudaGraphLaunch(b->graph, b->stream));
     b->t += (uint64_t)nsweeps;
     return PCAD_OK;
@@ -676,28 +683,31 @@ pcad_status batch_autotune(pcad_batch *b)
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             b->tune_ms = it->second.ms;
-            return batch_set_items(b, it->second.rows, it->second.lpt);
+            return batch_set_items(b, it->second.rows, it->second.lpt, it->second.slice);
         }
     }
     cudaEvent_t e0, e1;
     B_TRY(cudaEventCreate(&e0));
     B_TRY(cudaEventCreate(&e1));
-    // per-sweep launches with 4/8/16-row tiles in cost or image order, and
-    // the wavefront with 4/8-row tiles
-    const int cands[8][2] = {{4, 1}, {8, 1}, {16, 1}, {4, 0}, {8, 0}, {16, 0},
-                             {4, kOrderWave}, {8, kOrderWave}};
-    TuneVal best{4, 1, 1e30f};
+    // per-sweep launches with 4/8/16-row tiles in cost or image order
+    // (16-sweep graphs), and the wavefront with 4/8-row tiles and 8, 16 or 32
+    // sweeps per launch; compared per sweep
+    const int cands[12][3] = {{4, 1, 16},          {8, 1, 16},          {16, 1, 16},
+                              {4, 0, 16},          {8, 0, 16},          {16, 0, 16},
+                              {4, kOrderWave, 8},  {8, kOrderWave, 8},  {4, kOrderWave, 16},
+                              {8, kOrderWave, 16}, {4, kOrderWave, 32}, {8, kOrderWave, 32}};
+    TuneVal best{4, 1, kSlice, 1e30f};
     pcad_status st = PCAD_OK;
     for (const auto &c : cands) {
-        const int r = c[0], lpt = c[1];
-        st = batch_set_items(b, r, lpt);
+        const int r = c[0], lpt = c[1], sl = c[2];
+        st = batch_set_items(b, r, lpt, sl);
         if (st != PCAD_OK)
             break;
-        st = batch_run_sweeps(b, kSlice);   // warm + graph
+        st = batch_run_sweeps(b, sl);   // warm + graph
         if (st == PCAD_OK && cudaEventRecord(e0, b->stream) != cudaSuccess)
             st = set_error(PCAD_ECUDA, "event record");
         if (st == PCAD_OK)
-            st = batch_run_sweeps(b, kSlice);
+            st = batch_run_sweeps(b, sl);
         if (st == PCAD_OK && cudaEventRecord(e1, b->stream) != cudaSuccess)
             st = set_error(PCAD_ECUDA, "event record");
         float ms = 0.0f;
@@ -706,8 +716,8 @@ pcad_status batch_autotune(pcad_batch *b)
             st = set_error(PCAD_ECUDA, "event timing");
         if (st == PCAD_OK)
             st = batch_check_err(b);
-        if (st == PCAD_OK && ms < best.ms)
-            best = TuneVal{r, lpt, ms};
+        if (st == PCAD_OK && ms / sl < best.ms)
+            best = TuneVal{r, lpt, sl, ms / sl};
         if (st == PCAD_OK)
             st = batch_reset_state(b);
         if (st != PCAD_OK)
@@ -722,7 +732,7 @@ pcad_status batch_autotune(pcad_batch *b)
         g_tune_cache[key] = best;
     }
     b->tune_ms = best.ms;
-    return batch_set_items(b, best.rows, best.lpt);
+    return batch_set_items(b, best.rows, best.lpt, best.slice);
 }
 
 }  // namespace
@@ -754,7 +764,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
     const size_t off_ctr = total;
     total += al(n * (2 * sizeof(uint32_t) + sizeof(unsigned long long)));
     const size_t off_grab = total;
-    total += al((kSlice + 1) * sizeof(int));   // grab counters, wavefront error flag
+    total += al((kMaxSlice + 1) * sizeof(int));   // grab counters, wavefront error flag
     const size_t off_plane = total;
     total += al(max_plane * sizeof(float));
 
@@ -778,7 +788,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
     b->d_grab = (int *)(base + off_grab);
     b->d_plane = (float *)(base + off_plane);
     b->plane_floats = max_plane;
-    b->d_err = b->d_grab + kSlice;
+    b->d_err = b->d_grab + kMaxSlice;
     b->grid = grid_size();
     b->wgrid = wave_grid();
     b->desc.resize(n);
@@ -812,7 +822,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
                         b->stream);
     if (e != cudaSuccess)
         return bail(set_error(PCAD_ECUDA, cudaGetErrorString(e)));
-    pcad_status st = autotune ? batch_autotune(b) : batch_set_items(b, 4, 1);
+    pcad_status st = autotune ? batch_autotune(b) : batch_set_items(b, 4, 1, kSlice);
     if (st == PCAD_OK && cudaStreamSynchronize(b->stream) != cudaSuccess)
         st = set_error(PCAD_ECUDA, "batch set-up failed");
     if (st != PCAD_OK)
@@ -902,7 +912,23 @@ pcad_status pcad_batch_set_tiling(pcad_batch *b, int tile_rows, int order)
         return set_error(PCAD_EINVAL, "batch is NULL");
     if (tile_rows < 4 || tile_rows > 64 || tile_rows % 4 != 0 || order < 0 || order > kOrderWave)
         return set_error(PCAD_EINVAL, "tile_rows a multiple of 4 in [4, 64], order 0..2");
-    return batch_set_items(b, tile_rows, order);
+    return batch_set_items(b, tile_rows, order, b->slice);
+}
+
+pcad_status pcad_batch_slice(pcad_batch *b, int sweeps, int *current)
+{
+    if (!b)
+        return set_error(PCAD_EINVAL, "batch is NULL");
+    if (sweeps != 0 && sweeps != 8 && sweeps != 16 && sweeps != 32)
+        return set_error(PCAD_EINVAL, "sweeps per slice must be 8, 16 or 32 (0: keep)");
+    if (sweeps != 0 && sweeps != b->slice) {
+        pcad_status st = batch_set_items(b, b->rows, b->lpt, sweeps);
+        if (st != PCAD_OK)
+            return st;
+    }
+    if (current)
+        *current = b->slice;
+    return PCAD_OK;
 }
 
 pcad_status pcad_batch_read_sample(pcad_batch *b, int i, uint8_t *host_out, int out_pitch)

@@ -243,6 +243,7 @@ struct pcad_chain {
     double *mscratch = nullptr;   // 8 scratch + 2 results
     double *ta64 = nullptr, *pr64 = nullptr, *in64 = nullptr;
     uint32_t *ptab = nullptr;     // small-L sweep: pair prior table
+    uint4 *btab = nullptr;        // two-label draw thresholds (L = 2)
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
     int tb_k = 0;                 // sweeps per temporally blocked launch (0: one per launch)
@@ -300,6 +301,16 @@ bool uses_tc(const pcad_chain *ch)
     return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace;
 }
 
+// Whole runs of sweeps of small two-label images in one single-CTA launch
+// (state in shared memory): on request, or with AUTO for every image it
+// accepts, without energy tracking or temporal blocking.
+bool uses_resident(const pcad_chain *ch)
+{
+    if (ch->tb_k > 0 || ch->track.trace || !resident_eligible(ch->dm, ch->H, ch->W))
+        return false;
+    return ch->kernel == PCAD_KERNEL_RESIDENT || ch->kernel == PCAD_KERNEL_AUTO;
+}
+
 bool uses_wave(const pcad_chain *ch);
 
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
@@ -338,6 +349,16 @@ bool uses_wave(const pcad_chain *ch)
 pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t st)
 {
     SweepArgs a = make_args(ch);
+    if (uses_resident(ch) && n > 0) {
+        // all n sweeps in one single-CTA launch; PCA ends in the other plane
+        // when n is odd, Gibbs in place
+        a.sweep_off = (uint32_t)off0;
+        const bool gibbs = ch->model.sampler != PCAD_SAMPLER_PCA;
+        const int out = gibbs ? cur : cur ^ (n & 1);
+        CUDA_TRY(launch_resident(a, ch->x[cur], ch->x[out], n, gibbs, st));
+        cur = out;
+        return PCAD_OK;
+    }
     if (uses_tc(ch) && n > 0) {
         // tensor-core wavefront: all n sweeps in one launch, or one launch
         // per sweep when every sweep's state is needed (energy tracking)
@@ -484,7 +505,9 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     const int ntiles = wave_tiles(H, W);
     const size_t wbytes = align_up((size_t)(ntiles + 1) * sizeof(unsigned int), 256);
     const size_t pbytes = align_up((size_t)ptab_words() * sizeof(uint32_t), 256);
-    const size_t total = 3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + pbytes + misc;
+    const size_t bbytes = align_up((size_t)btab_bytes(), 256);
+    const size_t total =
+        3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + pbytes + bbytes + misc;
     cudaError_t e = cudaMallocAsync(&ch->block, total, ch->stream);
     if (e != cudaSuccess) {
         delete ch;
@@ -504,6 +527,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->in64 = (double *)p; p += sizeof(tabs.in64);
     ch->wave = (unsigned int *)p; p += wbytes;
     ch->ptab = (uint32_t *)p; p += pbytes;
+    ch->btab = (uint4 *)p; p += bbytes;
     ch->wave_tiles = ntiles;
     {
         int dev = 0;
@@ -543,6 +567,13 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
         e = cudaMemsetAsync(ch->tdev, 0, misc, ch->stream);
     if (e == cudaSuccess && m->L <= kSmallMaxLabels)
         e = launch_ptab(tabs.dm.T, ch->ptab, ch->stream);
+    if (e == cudaSuccess && m->L == 2) {
+        DevModel dm = tabs.dm;
+        dm.ta64 = ch->ta64;
+        dm.pr64 = ch->pr64;
+        dm.in64 = ch->in64;
+        e = launch_btab(dm, ch->btab, ch->stream);
+    }
     if (e == cudaSuccess) {
         int *bad = (int *)(ch->mscratch);
         e = launch_check_labels(ch->g, ch->pitch, H, W, m->L, bad, ch->stream);
@@ -561,6 +592,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->dm.pr64 = ch->pr64;
     ch->dm.in64 = ch->in64;
     ch->dm.ptab = m->L <= kSmallMaxLabels ? ch->ptab : nullptr;
+    ch->dm.btab = m->L == 2 ? ch->btab : nullptr;
     *out = ch;
     return PCAD_OK;
 }
@@ -606,9 +638,10 @@ pcad_status pcad_chain_run(pcad_chain *ch, int nsweeps)
     if (acc_would_overflow(ch, (uint64_t)nsweeps))
         return fail(PCAD_EINVAL, "accumulator would leave the exact FP32 range");
     int left = nsweeps;
-    // Whole captured blocks need the ping-pong parity at 0 (always true for Gibbs).
+    // Whole captured blocks need the ping-pong parity at 0 (always true for
+    // Gibbs); the resident kernel runs any number of sweeps in one launch.
     const bool parity_ok = ch->model.sampler != PCAD_SAMPLER_PCA || ch->cur == 0;
-    if (left >= kGraphSweeps && parity_ok) {
+    if (left >= kGraphSweeps && parity_ok && !uses_resident(ch)) {
         if (!ch->graph) {
             pcad_status st = build_graph(ch);
             if (st != PCAD_OK)
@@ -731,6 +764,9 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
     ch->dm.pr64 = ch->pr64;
     ch->dm.in64 = ch->in64;
     ch->dm.ptab = m->L <= kSmallMaxLabels ? ch->ptab : nullptr;   // T is unchanged
+    ch->dm.btab = m->L == 2 ? ch->btab : nullptr;
+    if (m->L == 2)   // stream-ordered after the new FP64 tables
+        CUDA_TRY(launch_btab(ch->dm, ch->btab, ch->stream));
     ch->ecoef = energy_coef(*m, (long)ch->H * ch->W);
     return PCAD_OK;
 }
@@ -757,7 +793,9 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
 {
     if (!ch || !kind)
         return fail(PCAD_EINVAL, "chain or kind is NULL");
-    if (ch->model.sampler != PCAD_SAMPLER_PCA)
+    if (uses_resident(ch))
+        *kind = PCAD_KERNEL_RESIDENT;
+    else if (ch->model.sampler != PCAD_SAMPLER_PCA)
         *kind = uses_tc(ch) ? PCAD_KERNEL_TENSOR : PCAD_KERNEL_CUDA_CORE;
     else if (ch->tb_k > 0)
         *kind = -ch->tb_k;
@@ -880,9 +918,13 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE &&
-        kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE && kind != PCAD_KERNEL_SMALL)
+        kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE && kind != PCAD_KERNEL_SMALL &&
+        kind != PCAD_KERNEL_RESIDENT)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
-                                 "_WAVE or _SMALL");
+                                 "_WAVE, _SMALL or _RESIDENT");
+    if (kind == PCAD_KERNEL_RESIDENT && !resident_eligible(ch->dm, ch->H, ch->W))
+        return fail(PCAD_EINVAL, "the resident kernel needs L = 2, 4 or 8 neighbours and at most "
+                                 "4096 quads of 4 sites (H * ceil(W / 4))");
     if (kind == PCAD_KERNEL_SMALL &&
         (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_small_eligible(ch->dm)))
         return fail(PCAD_EINVAL, "the small-label kernel needs the PCA sampler, 3 <= L <= 16, "

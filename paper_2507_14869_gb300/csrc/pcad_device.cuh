@@ -60,6 +60,7 @@ struct DevModel {
     const double *in64;  // [256] Lp price factor exp(-lambda (d / (L - 1))^p), FP64
     double el64;         // e^lambda, FP64
     const uint32_t *ptab;  // small-L sweep: pair prior table (nullptr: not built)
+    const uint4 *btab;     // two-label draw thresholds per site configuration (nullptr: not built)
 };
 
 // ------------------------------------------------------------ bounded waits

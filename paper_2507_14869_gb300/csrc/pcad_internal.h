@@ -314,6 +314,20 @@ bool pca_small_eligible(const DevModel &m);
 cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s, uint8_t *x0 = nullptr,
                              uint8_t *x1 = nullptr, const uint32_t *budget = nullptr);
 
+// Whole chains of small two-label images in one CTA (state in shared
+// memory): L = 2, 4 or 8 neighbours, the thresholds table m.btab built, at
+// most 4096 quads of 4 sites (H * ceil(W / 4)) and 200 KB of shared memory.
+// nsweeps sweeps from plane x_in (the current state) in one launch; the
+// final state goes to x_out (x_in itself for Gibbs, the other plane when
+// nsweeps is odd for PCA).
+bool resident_eligible(const DevModel &m, int H, int W);
+cudaError_t launch_resident(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_out, int nsweeps,
+                            bool gibbs, cudaStream_t s);
+// The two-label draw thresholds of every site configuration (L = 2), from
+// the model's FP32 draw and FP64 re-draw; btab_bytes() of device memory.
+int btab_bytes();
+cudaError_t launch_btab(const DevModel &m, uint4 *out, cudaStream_t s);
+
 // Largest row offset of a band chain (Philox rows are 32-bit).
 constexpr int kMaxRowOffset = 1 << 30;
 

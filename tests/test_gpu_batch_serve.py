@@ -379,3 +379,27 @@ def test_large_small_label_slots_in_batch_and_server(pc):
             assert np.array_equal(res[rid][1], ms)
     finally:
         pc.pcad_server_destroy(sv)
+
+
+@pytest.mark.parametrize("slice_sweeps,rows,order", [(8, 4, 2), (32, 8, 2), (32, 16, 0)])
+def test_batch_slice_lengths_are_bit_identical(pc, slice_sweeps, rows, order):
+    """Every slice length (sweeps per captured slice, sweeps per wavefront
+    launch) gives each chain its own result, for runs ending inside a slice."""
+    jobs = _jobs()
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_set_tiling(b, rows, order)
+        assert pc.pcad_batch_slice(b, slice_sweeps) == slice_sweeps
+        pc.pcad_batch_run(b, 21)
+        pc.pcad_batch_run(b, 30)
+        pc.pcad_batch_sync(b)
+        for i, (g, m, seed, chain, burn) in enumerate(jobs):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, 51)
+            assert np.array_equal(pc.pcad_batch_read_sample(b, i, *g.shape), xs), i
+            assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
+        assert pc.pcad_batch_slice(b) == slice_sweeps
+        for bad in (1, 12, 64, -8):
+            with pytest.raises(pc.PcadError):
+                pc.pcad_batch_slice(b, bad)
+    finally:
+        pc.pcad_batch_destroy(b)
