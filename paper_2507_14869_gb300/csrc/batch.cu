@@ -465,6 +465,104 @@ pcad_status small_set_issue(const SmallSet &ss, const std::vector<SlotDesc> &des
     return PCAD_OK;
 }
 
+// Two-label chains small enough to keep their state in one CTA's shared
+// memory (64 x 64 and the like) run the resident kernel: one launch per
+// neighbourhood holds every such chain, one CTA each, for all the sweeps of
+// a slice.  Each chain has its own threshold table (it follows the chain's
+// coefficients).
+struct ResSet {
+    std::vector<int> slots[2];     // chains with 4 and with 8 neighbours
+    int smem[2] = {0, 0};          // shared memory of each launch
+    int *d_idx = nullptr;          // slot indices: slots[0], then slots[1]
+    uint4 *tabs = nullptr;         // one threshold table per chain, same order
+    size_t cap = 0;                // chains the buffers hold
+};
+
+size_t res_tab_entries()
+{
+    return (size_t)btab_bytes() / sizeof(uint4);
+}
+
+// Split `in` into the resident two-label chains and the rest; build their
+// tables (kept when the set is unchanged).
+pcad_status res_set_build(ResSet &rs, const std::vector<SlotDesc> &d, const std::vector<int> &in,
+                          std::vector<int> &rest, cudaStream_t st)
+{
+    std::vector<int> sl[2];
+    int smem[2] = {0, 0};
+    rest.clear();
+    for (int i : in) {
+        if (resident_fits(d[i].m.L, d[i].nbhd, d[i].H, d[i].W)) {
+            const int k = d[i].nbhd == 8 ? 1 : 0;
+            sl[k].push_back(i);
+            smem[k] = std::max(smem[k], resident_smem_bytes(d[i].nbhd, d[i].H, d[i].W));
+        } else {
+            rest.push_back(i);
+        }
+    }
+    if (sl[0] == rs.slots[0] && sl[1] == rs.slots[1] && (rs.tabs || sl[0].size() + sl[1].size() == 0))
+        return PCAD_OK;
+    rs.slots[0] = sl[0];
+    rs.slots[1] = sl[1];
+    rs.smem[0] = smem[0];
+    rs.smem[1] = smem[1];
+    std::vector<int> idx(sl[0]);
+    idx.insert(idx.end(), sl[1].begin(), sl[1].end());
+    if (idx.size() > rs.cap) {
+        if (rs.d_idx)
+            B_TRY(cudaFreeAsync(rs.d_idx, st));
+        if (rs.tabs)
+            B_TRY(cudaFreeAsync(rs.tabs, st));
+        rs.d_idx = nullptr;
+        rs.tabs = nullptr;
+        rs.cap = std::max(idx.size(), 2 * rs.cap);
+        B_TRY(cudaMallocAsync((void **)&rs.d_idx, rs.cap * sizeof(int), st));
+        B_TRY(cudaMallocAsync((void **)&rs.tabs, rs.cap * res_tab_entries() * sizeof(uint4), st));
+    }
+    if (idx.empty())
+        return PCAD_OK;
+    B_TRY(cudaMemcpyAsync(rs.d_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice,
+                          st));
+    for (size_t p = 0; p < idx.size(); ++p)
+        B_TRY(launch_btab(d[idx[p]].m, rs.tabs + p * res_tab_entries(), st));
+    return PCAD_OK;
+}
+
+// The table of slot i again (its coefficients changed); no-op for other slots.
+pcad_status res_set_retable(const ResSet &rs, const SlotDesc &d, int i, cudaStream_t st)
+{
+    size_t p = 0;
+    for (int k = 0; k < 2; ++k)
+        for (int j : rs.slots[k]) {
+            if (j == i)
+                B_TRY(launch_btab(d.m, rs.tabs + p * res_tab_entries(), st));
+            ++p;
+        }
+    return PCAD_OK;
+}
+
+pcad_status res_set_issue(const ResSet &rs, const SlotDesc *d_slots, int n, cudaStream_t st)
+{
+    size_t off = 0;
+    for (int k = 0; k < 2; ++k) {
+        const int cnt = (int)rs.slots[k].size();
+        if (cnt > 0)
+            B_TRY(launch_resident_batch(d_slots, rs.d_idx + off, rs.tabs + off * res_tab_entries(),
+                                        cnt, k ? 8 : 4, n, rs.smem[k], st));
+        off += (size_t)cnt;
+    }
+    return PCAD_OK;
+}
+
+void res_set_free(ResSet &rs, cudaStream_t st)
+{
+    if (rs.d_idx)
+        cudaFreeAsync(rs.d_idx, st);
+    if (rs.tabs)
+        cudaFreeAsync(rs.tabs, st);
+    rs = ResSet{};
+}
+
 void small_set_free(SmallSet &ss, cudaStream_t st)
 {
     if (ss.tables)
@@ -535,6 +633,7 @@ struct pcad_batch {
     int *d_err = nullptr;            // wavefront launches: bounded-wait flag
     TcSet tc;                        // chains on the tensor-core sweep
     SmallSet small;                  // large small-label chains, launched one at a time
+    ResSet res;                      // small two-label chains, one CTA each
     float tune_ms = 0.0f;
     cudaGraphExec_t graph = nullptr;
 };
@@ -543,13 +642,15 @@ namespace {
 
 pcad_status batch_set_items(pcad_batch *b, int rows, int lpt, int slice)
 {
-    std::vector<int> all(b->n), others, active;
+    std::vector<int> all(b->n), not_res, others, active;
     for (int i = 0; i < b->n; ++i)
         all[i] = i;
-    // chains with a tensor-core table run on the batched tensor-core sweep,
-    // large small-label chains on their own launches; the tiling below
-    // applies to the others
-    pcad_status st0 = tc_set_build(b->tc, b->desc, all, others, b->stream);
+    // small two-label chains run resident, chains with a tensor-core table
+    // on the batched tensor-core sweep, large small-label chains on their
+    // own launches; the tiling below applies to the others
+    pcad_status st0 = res_set_build(b->res, b->desc, all, not_res, b->stream);
+    if (st0 == PCAD_OK)
+        st0 = tc_set_build(b->tc, b->desc, not_res, others, b->stream);
     if (st0 == PCAD_OK)
         st0 = small_set_build(b->small, b->desc, others, active, b->stream);
     if (st0 != PCAD_OK)
@@ -586,8 +687,10 @@ pcad_status batch_set_items(pcad_batch *b, int rows, int lpt, int slice)
 pcad_status batch_issue_slice(pcad_batch *b, cudaStream_t s)
 {
     const int n = b->slice;
-    pcad_status st0 = tc_set_issue(b->tc, b->desc, b->d_slots, b->d_t, b->d_budget, n,
-                                   b->d_grab, b->d_err, s);
+    pcad_status st0 = res_set_issue(b->res, b->d_slots, n, s);
+    if (st0 == PCAD_OK)
+        st0 = tc_set_issue(b->tc, b->desc, b->d_slots, b->d_t, b->d_budget, n, b->d_grab,
+                           b->d_err, s);
     if (st0 == PCAD_OK)
         st0 = small_set_issue(b->small, b->desc, n, s);
     if (st0 != PCAD_OK)
@@ -799,6 +902,7 @@ pcad_status pcad_batch_create(const pcad_job *jobs, int n, int autotune, void *c
             cudaFreeAsync(b->wb.mem, b->stream);
         tc_set_free(b->tc, b->stream);
         small_set_free(b->small, b->stream);
+        res_set_free(b->res, b->stream);
         cudaFreeAsync(b->block, b->stream);
         cudaStreamSynchronize(b->stream);
         delete b;
@@ -887,6 +991,11 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
     }
     B_TRY(cudaMemcpyAsync(&b->d_slots[i], &b->desc[i], sizeof(SlotDesc), cudaMemcpyHostToDevice,
                           b->stream));
+    {
+        pcad_status st2 = res_set_retable(b->res, b->desc[i], i, b->stream);
+        if (st2 != PCAD_OK)
+            return st2;
+    }
     B_TRY(cudaStreamSynchronize(b->stream));   // the host copies must outlive the transfers
     b->jobs[i].model = *m;
     return PCAD_OK;
@@ -1001,6 +1110,7 @@ void pcad_batch_destroy(pcad_batch *b)
         cudaFreeAsync(b->wb.mem, b->stream);
     tc_set_free(b->tc, b->stream);
     small_set_free(b->small, b->stream);
+    res_set_free(b->res, b->stream);
     cudaFreeAsync(b->block, b->stream);
     cudaStreamSynchronize(b->stream);
     delete b;

@@ -327,6 +327,14 @@ cudaError_t launch_resident(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_
 // the model's FP32 draw and FP64 re-draw; btab_bytes() of device memory.
 int btab_bytes();
 cudaError_t launch_btab(const DevModel &m, uint4 *out, cudaStream_t s);
+// Batched form: whether a two-label chain of this size runs resident, its
+// shared memory, and one launch of `count` chains (slot indices idx[0..count),
+// all with nbhd neighbours, tables at tabs + b * btab_bytes()) for n sweeps
+// below each slot's budget, smem the largest of their resident_smem_bytes.
+bool resident_fits(int L, int nbhd, int H, int W);
+int resident_smem_bytes(int nbhd, int H, int W);
+cudaError_t launch_resident_batch(const SlotDesc *slots, const int *idx, const uint4 *tabs,
+                                  int count, int nbhd, int n, int smem, cudaStream_t s);
 
 // Largest row offset of a band chain (Philox rows are 32-bit).
 constexpr int kMaxRowOffset = 1 << 30;

@@ -46,6 +46,7 @@ constexpr int btab_entries()
 {
     return 4 * (NB + 1) * (NB + 1);
 }
+constexpr int kBtabStride = 4 * 9 * 9;   // entries per table in a batch's table array
 
 __device__ unsigned long long g_btab_redraws;   // re-draw counter of the bisection (unused)
 
@@ -177,13 +178,14 @@ __device__ __forceinline__ uint32_t phase_mask(int r, int ph)
     return (ph & 1) ? 0xFF00FF00u : 0x00FF00FFu;
 }
 
-// One CTA runs nsweeps sweeps of one chain from plane xg_in; the final
-// labels go to xg_out (pitch a.pitch), the posterior-mean counts are added
-// to a.acc and the re-draw count to a.fp64_draws.  Thread i takes the quads
-// i, i + 1024, ... (QPT at most), a quad being 4 adjacent sites of a row.
+// One CTA runs nsweeps sweeps of one chain from plane xg_in with the
+// threshold table btab; the final labels go to xg_out (pitch a.pitch), the
+// posterior-mean counts are added to a.acc and the re-draw count to
+// a.fp64_draws.  Thread i takes the quads i, i + 1024, ... (QPT at most), a
+// quad being 4 adjacent sites of a row.
 template <int NB, bool GIBBS, int QPT>
-__global__ void __launch_bounds__(kResThreads, 1)
-    resident_kernel(const SweepArgs a, const uint8_t *xg_in, uint8_t *xg_out, int nsweeps)
+__device__ __forceinline__ void resident_run(const SweepArgs &a, const uint4 *btab,
+                                             const uint8_t *xg_in, uint8_t *xg_out, int nsweeps)
 {
     extern __shared__ __align__(16) uint8_t sm[];
     constexpr int NE = btab_entries<NB>();
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kResThreads, 1)
         for (int i = tid; i < nz; i += kResThreads)
             z[i] = 0u;   // borders, row padding and the base bytes of padding sites stay 0
         for (int i = tid; i < NE; i += kResThreads)
-            tab[i] = a.m.btab[i];
+            tab[i] = btab[i];
     }
     __syncthreads();
     for (int i = tid; i < H * W; i += kResThreads) {
@@ -327,6 +329,37 @@ __global__ void __launch_bounds__(kResThreads, 1)
 }
 
 template <int NB, bool GIBBS, int QPT>
+__global__ void __launch_bounds__(kResThreads, 1)
+    resident_kernel(const SweepArgs a, const uint8_t *xg_in, uint8_t *xg_out, int nsweeps)
+{
+    resident_run<NB, GIBBS, QPT>(a, a.m.btab, xg_in, xg_out, nsweeps);
+}
+
+// Batched chains: CTA b runs chain idx[b] (a PCA slot) with the table
+// tabs + b * kBtabStride, for the sweeps t0 .. t0 + n - 1 below the slot's
+// budget (t0 its device sweep counter); the planes follow the counter.
+template <int NB>
+__global__ void __launch_bounds__(kResThreads, 1)
+    resident_batch_kernel(const SlotDesc *slots, const int *idx, const uint4 *tabs, int n)
+{
+    const SlotDesc &d = slots[idx[blockIdx.x]];
+    if (!d.active)
+        return;
+    const uint32_t t0 = *d.tdev, bud = *d.budget;
+    const int nb = bud > t0 ? (int)min((uint32_t)n, bud - t0) : 0;
+    if (nb == 0)
+        return;
+    SweepArgs a;
+    slot_args(d, t0, a);
+    a.sweep_base = d.tdev;
+    a.sweep_off = 0u;
+    a.last_phase = 0;
+    resident_run<NB, false, kResMaxQuadsPerThread>(a, tabs + (size_t)blockIdx.x * kBtabStride,
+                                                   d.x[t0 & 1u], d.x[(t0 + (uint32_t)nb) & 1u],
+                                                   nb);
+}
+
+template <int NB, bool GIBBS, int QPT>
 cudaError_t launch_res_t(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_out, int n,
                          cudaStream_t st)
 {
@@ -365,7 +398,7 @@ cudaError_t launch_res_q(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_out
 
 int btab_bytes()
 {
-    return btab_entries<8>() * 16;
+    return kBtabStride * 16;
 }
 
 cudaError_t launch_btab(const DevModel &m, uint4 *out, cudaStream_t st)
@@ -378,6 +411,53 @@ cudaError_t launch_btab(const DevModel &m, uint4 *out, cudaStream_t st)
         btab_kernel<8><<<grid, 256, 0, st>>>(m, out);
     else
         btab_kernel<4><<<grid, 256, 0, st>>>(m, out);
+    return cudaGetLastError();
+}
+
+bool resident_fits(int L, int nbhd, int H, int W)
+{
+    if (L != 2 || (nbhd != 4 && nbhd != 8))
+        return false;
+    if ((long long)H * (((W + 3) & ~3) >> 2) > (long long)kResMaxQuadsPerThread * kResThreads)
+        return false;
+    return res_smem_bytes(nbhd, false, H, W) <= kResMaxSmem;
+}
+
+int resident_smem_bytes(int nbhd, int H, int W)
+{
+    return res_smem_bytes(nbhd, false, H, W);
+}
+
+cudaError_t launch_resident_batch(const SlotDesc *slots, const int *idx, const uint4 *tabs,
+                                  int count, int nbhd, int n, int smem, cudaStream_t st)
+{
+    if (count <= 0 || n <= 0)
+        return cudaSuccess;
+    if ((nbhd != 4 && nbhd != 8) || smem > kResMaxSmem)
+        return cudaErrorInvalidValue;
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    const int k = nbhd == 8 ? 1 : 0;
+    if (!attr_set[k][dev]) {
+        e = nbhd == 8 ? cudaFuncSetAttribute(resident_batch_kernel<8>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kResMaxSmem)
+                      : cudaFuncSetAttribute(resident_batch_kernel<4>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kResMaxSmem);
+        if (e != cudaSuccess)
+            return e;
+        attr_set[k][dev] = true;
+    }
+    if (nbhd == 8)
+        resident_batch_kernel<8><<<count, kResThreads, smem, st>>>(slots, idx, tabs, n);
+    else
+        resident_batch_kernel<4><<<count, kResThreads, smem, st>>>(slots, idx, tabs, n);
     return cudaGetLastError();
 }
 

@@ -161,3 +161,44 @@ def test_resident_follows_model_changes(pc):
     assert np.array_equal(outs[RESIDENT][0], outs[CUDA_CORE][0])
     assert np.array_equal(outs[RESIDENT][1], outs[CUDA_CORE][1])
     assert outs[RESIDENT][2] == outs[CUDA_CORE][2]
+
+
+def test_batched_resident_chains_equal_single_chains(pc):
+    """Small two-label chains in a batch run one CTA each in one launch per
+    neighbourhood, next to a two-label chain too large for it and a
+    16-label chain; runs end inside slices and one chain's coefficients
+    change between runs.  Every chain's sample, mean and the batch's FP64
+    re-draw count equal the chains run alone."""
+    shapes = [(64, 64, 4), (33, 65, 4), (45, 77, 8), (1, 1, 4), (7, 3, 8), (128, 128, 4),
+              (130, 130, 4)]
+    jobs = []
+    for k, (H, W, nb) in enumerate(shapes):
+        g, m = _ising(40 + k, H, W, nbhd=nb, flip=k % 2 == 0)
+        jobs.append((g, m, 50 + k, k, 6))
+    from pcad_inputs import gaussian_noise, greyscale_scene
+    g16 = gaussian_noise(61, greyscale_scene(60, 40, 50, 16, n_shapes=4), 1.0, 16)
+    jobs.append((g16, Model(L=16, pair=1, pair_coef=0.6, pair_T=3, sigma=1.0, inertia=1.0),
+                 70, 9, 5))
+    m_new = Model(L=2, nbhd=8, pair=POTTS, pair_coef=1.4, noise=1, flip_p=0.15, inertia=0.2)
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_run(b, 21)
+        pc.pcad_batch_set_model(b, 2, m_new)
+        pc.pcad_batch_run(b, 30)
+        pc.pcad_batch_sync(b)
+        fp64 = 0
+        for i, (g, m, seed, chain, burn) in enumerate(jobs):
+            with pc.Chain(g, m, seed=seed, chain_id=chain, burn_in=burn) as ch:
+                if m.L == 16:   # the batch's general kernel: the same re-draw count
+                    ch.set_kernel(CUDA_CORE)
+                ch.run(21)
+                if i == 2:
+                    ch.set_model(m_new)
+                ch.run(30)
+                xs, ms = ch.sample(), ch.mean()
+                fp64 += ch.fp64_draws()
+            assert np.array_equal(pc.pcad_batch_read_sample(b, i, *g.shape), xs), i
+            assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
+        assert pc.pcad_batch_info(b)["fp64_draws"] == fp64
+    finally:
+        pc.pcad_batch_destroy(b)
