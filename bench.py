@@ -70,6 +70,8 @@ KERNEL_NAMES = {
        "one launch per 32 sweeps)",
     3: "pca_wave_kernel (CUDA cores, wavefront, one launch per 32 sweeps)",
     4: "pca_small_kernel (CUDA cores, prior sums from a pair table, one launch per sweep)",
+    5: "resident_kernel (two labels, whole run in one single-CTA launch, state in shared "
+       "memory, exact per-configuration thresholds)",
 }
 
 
@@ -268,6 +270,8 @@ def _launches_per_run(kind, sweeps, sampler=0):
     plus the rest.  Wavefront kernels: one sweep launch and the counter
     advance per block; per-sweep kernels: one launch per sweep (or per Gibbs
     colour phase) plus the advance."""
+    if kind == 5:
+        return 2                       # the run's launch and the counter advance
     blocks, rest = divmod(sweeps, 32)
     if kind in (2, 3):
         return 2 * blocks + (2 if rest else 0)
@@ -385,6 +389,8 @@ def run_ours(a):
         if not a.no_gibbs:
             side["gibbs"] = _safe(_gibbs_8192, pc, stream, timed, noisy, m, clean, cid)
         side["greyscale512"] = _safe(_greyscale512, pc, stream, timed, cid, a.no_gibbs)
+        if world == 1:
+            side["binary64"] = _safe(_binary64, pc, torch, stream)
         if world == 1:
             side["batch"] = _safe(_batch_object, pc, torch, stream, a.images)
             rates = [float(x) for x in a.rates.split(",") if x]
@@ -549,6 +555,105 @@ def _greyscale512(pc, stream, timed, cid, no_gibbs, steps=5):
 
 
 BATCH_SWEEPS, BATCH_BURN = 200, 50
+
+
+def _binary64(pc, torch, stream, n_batch=512, reps=5):
+    """The two-label image workload (64 x 64, Ising c_P = 1.2, flip p = 0.1,
+    lambda = 1, 500 sweeps, burn-in 100): one chain on the default kernel
+    (the resident one: the whole run in one single-CTA launch) against
+    per-sweep launches in CUDA graphs, lazy PCA and checkerboard Gibbs,
+    device-timed; the wall clock of create (host image) + run + read mean;
+    then n_batch such chains (distinct images) as one batch against the same
+    chains run one after another."""
+    import numpy as np
+
+    from pcad_inputs import binary_64
+
+    sweeps, burn = 500, 100
+    clean, g, m = binary_64()
+    out = {"workload": "64x64 binary, Ising c_P=1.2, flip p=0.1, lambda=1.0, 500 sweeps, "
+                       "burn-in 100"}
+
+    def dev_ms(ch):
+        ch.run(sweeps)
+        ch.sync()
+        ts = []
+        for _ in range(reps):
+            ch.reset()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ch.run(sweeps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for name, sampler in (("pca", 0), ("gibbs", 1)):
+        row = {}
+        for label, kind in (("default", 0), ("per_sweep_graphs", 1)):
+            with pc.Chain(g, m, seed=1, chain_id=0, burn_in=burn, sampler=sampler,
+                          stream=stream) as ch:
+                ch.set_kernel(kind)
+                k_used = ch.kernel_in_use()
+                ms = dev_ms(ch)
+                psnr = ch.metrics(clean, 0)[0]
+            kname = KERNEL_NAMES.get(k_used, str(k_used))
+            if sampler and k_used == 1:
+                kname = "gibbs_cb_kernel (CUDA cores, one launch per colour phase)"
+            row[label] = {"ms": ms, "site_updates_per_s": 4096 * sweeps / (ms * 1e-3),
+                          "kernel": kname, "psnr_db": psnr}
+        walls = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            with pc.Chain(g, m, seed=1, chain_id=0, burn_in=burn, sampler=sampler,
+                          stream=stream) as ch:
+                ch.run(sweeps)
+                ch.mean()
+            walls.append(time.perf_counter() - t0)
+        row["e2e_wall_ms"] = 1e3 * statistics.median(walls)
+        row["speedup_vs_per_sweep"] = row["per_sweep_graphs"]["ms"] / row["default"]["ms"]
+        out[name] = row
+
+    jobs = [(binary_64(seed=1 + i)[1], m, 1, i, burn) for i in range(n_batch)]
+    b = pc.pcad_batch_create(jobs, autotune=False, stream=stream.cuda_stream)
+    try:
+        pc.pcad_batch_run(b, 32)
+        pc.pcad_batch_reset(b)
+        pc.pcad_batch_sync(b)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pc.pcad_batch_run(b, sweeps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_batch = e0.elapsed_time(e1) * 1e-3
+        chains = [pc.Chain(gg, mm, seed=sd, chain_id=c, burn_in=bi, stream=stream)
+                  for gg, mm, sd, c, bi in jobs]
+        try:
+            for ch in chains[:4]:
+                ch.run(16)
+            for ch in chains:
+                ch.reset()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for ch in chains:
+                ch.run(sweeps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_plain = e0.elapsed_time(e1) * 1e-3
+            same = all(np.array_equal(pc.pcad_batch_read_mean(b, k, 64, 64), chains[k].mean())
+                       for k in range(0, n_batch, 17))
+        finally:
+            for ch in chains:
+                ch.close()
+    finally:
+        pc.pcad_batch_destroy(b)
+    out["batch"] = {"chains": n_batch, "ms": 1e3 * t_batch, "img_per_s": n_batch / t_batch,
+                    "site_updates_per_s": n_batch * 4096 * sweeps / t_batch,
+                    "one_after_another_ms": 1e3 * t_plain,
+                    "one_after_another_img_per_s": n_batch / t_plain,
+                    "speedup_vs_one_after_another": t_plain / t_batch,
+                    "identical_means": bool(same)}
+    return out
 
 
 def _batch_object(pc, torch, stream, n_images, rank=0, world=1):
