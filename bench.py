@@ -55,13 +55,17 @@ HBM_PEAK_FALLBACK = 6800.0   # GB/s, used only if MEASURED_PEAKS.json is absent
 # DRAM bytes (read + write) per site-update of each kernel, from ncu captures
 # (profiles/); None until the current kernel is captured.  The tensor-core
 # figure is one 32-sweep launch at 4096^2 (planes, observation and
-# accumulator exceed L2), the CUDA-core figure one per-sweep launch at
-# 8192^2 L = 16.
+# accumulator exceed L2); the small-label figure one accumulating per-sweep
+# launch at 8192^2 L = 16; the per-sweep CUDA-core kernel has no current
+# capture at 8192^2.
 NCU_TC_BYTES_PER_SITE = (3.213934e9 + 2.634401e9) / (32 * 4096 * 4096)
 NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_kernel launch "
                "at 4096^2 L=256 (profiles/pca_tc_l256_4096sq.md), scaled by sites to 8192^2")
 NCU_DIRECT_BYTES_PER_SITE = None
 NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at 8192^2 L=16"
+NCU_SMALL_BYTES_PER_SITE = (407.3e6 + 282.3e6) / (8192 * 8192)
+NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_small_kernel launch at "
+                  "8192^2 L=16 (profiles/pca_small_l16_4096sq.md)")
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5}
 KERNEL_NAMES = {
@@ -465,9 +469,10 @@ def _config3(pc, stream, timed, x_head, ms_head, head_kind, hbm_peak, cid):
                    "frac": gbs / hbm_peak,
                    "algorithmic_bytes_per_site_update": _algo_bytes(1, SWEEPS, BURN_IN) / SWEEPS}
             if L == 16 and k == 0:
-                per_site = NCU_DIRECT_BYTES_PER_SITE
+                per_site = NCU_SMALL_BYTES_PER_SITE if kind == 4 else (
+                    NCU_DIRECT_BYTES_PER_SITE if kind == 1 else None)
                 hbm["traffic"] = per_site * sites if per_site else None
-                hbm["traffic_source"] = NCU_DIRECT_NOTE
+                hbm["traffic_source"] = NCU_SMALL_NOTE if kind == 4 else NCU_DIRECT_NOTE
                 r["roofline"] = hbm
                 r["sfu_frac"] = sfu["frac"]
                 # the binding bound: min(HBM / B, SFU / L) site-updates/s
