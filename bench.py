@@ -63,11 +63,15 @@ NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_
                "at 4096^2 L=256 (profiles/pca_tc_l256_4096sq.md), scaled by sites to 8192^2")
 NCU_DIRECT_BYTES_PER_SITE = None
 NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at 8192^2 L=16"
+NCU_WIN_BYTES_PER_SITE = (404017152 + 289024512) / (8192 * 8192)
+NCU_WIN_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_win_kernel launch at "
+                "8192^2 L=256 (profiles/pca_win_l256_8192sq.md)")
 NCU_SMALL_BYTES_PER_SITE = (407.3e6 + 282.3e6) / (8192 * 8192)
 NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_small_kernel launch at "
                   "8192^2 L=16 (profiles/pca_small_l16_4096sq.md)")
 
-KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5}
+KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5,
+                "window": 6}
 KERNEL_NAMES = {
     1: "pca_direct_kernel (CUDA cores, one launch per sweep)",
     2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
@@ -76,6 +80,7 @@ KERNEL_NAMES = {
     4: "pca_small_kernel (CUDA cores, prior sums from a pair table, one launch per sweep)",
     5: "resident_kernel (two labels, whole run in one single-CTA launch, state in shared "
        "memory, exact per-configuration thresholds)",
+    6: "pca_win_kernel (CUDA cores, hull chunks from a tent-byte table, one launch per sweep)",
 }
 
 
@@ -105,7 +110,7 @@ def _args():
                         "images and the q grid; cpu: the FP64 oracle on the host cores "
                         "(single-threaded Gibbs and PCA, OpenMP PCA) beside the GPU chain")
     p.add_argument("--kernel", default="auto",
-                   choices=["auto", "cuda_core", "tensor", "wave", "small", "resident"],
+                   choices=["auto", "cuda_core", "tensor", "wave", "small", "resident", "window"],
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
                         "auto = the tensor-core sweep for eligible models with L >= 192, else "
                         "the per-sweep or wavefront CUDA-core kernel; tensor = prior sums by "
@@ -358,11 +363,12 @@ def run_ours(a):
     x_head = pca.sample()
     pca.close()
     spl = 32 if pca_kind in (2, 3) else 1          # sweeps per launch
-    per_site = NCU_TC_BYTES_PER_SITE if pca_kind == 2 else (
-        NCU_DIRECT_BYTES_PER_SITE if pca_kind == 1 else None)
+    per_site = {2: NCU_TC_BYTES_PER_SITE, 1: NCU_DIRECT_BYTES_PER_SITE,
+                6: NCU_WIN_BYTES_PER_SITE}.get(pca_kind)
     traffic = per_site * sites * spl if per_site else None
+    note = {2: NCU_TC_NOTE, 6: NCU_WIN_NOTE}.get(pca_kind, NCU_DIRECT_NOTE)
     roof = _sfu_roofline(sites, LABELS, ms_sweep, KERNEL_NAMES.get(pca_kind, str(pca_kind)),
-                         traffic, NCU_TC_NOTE if pca_kind == 2 else NCU_DIRECT_NOTE, spl)
+                         traffic, note, spl)
     roof["algorithmic_bytes_per_launch"] = 11 * sites * spl
     roof["hbm_frac"] = (_algo_bytes(sites, SWEEPS, BURN_IN) / (ms_sweep * SWEEPS * 1e-3) / 1e9
                         / hbm_peak)

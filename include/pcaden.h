@@ -154,7 +154,9 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * in place, as a wavefront of phases; Section 5.1); PCAD_EINVAL for an
  * unknown kind or PCAD_KERNEL_TENSOR on another model.  PCAD_KERNEL_AUTO
  * (the default) takes it for L >= 192 without energy tracking (where it
- * measured faster on GB300), else the per-sweep or the wavefront CUDA-core
+ * measured faster on GB300), except lazy-PCA chains on images of at least
+ * 54 blocks of 4 x 32 sites per multiprocessor, which take
+ * PCAD_KERNEL_WINDOW (below); else the per-sweep or the wavefront CUDA-core
  * kernel (see pcad_chain_kernel_in_use).  PCAD_KERNEL_WAVE runs the
  * CUDA-core draw as one persistent launch per block of sweeps, a tile of
  * 4 x 32 sites starting sweep k as soon as its 3 x 3 neighbouring tiles
@@ -177,24 +179,35 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * neighbours outside the image), computed at set-up from the FP32 draw and
  * FP64 re-draw of the other kernels; same labels and the same FP64 re-draw
  * count (with two labels every inertia price is the L0 one).  AUTO takes it
- * for the images it accepts (no energy tracking, no temporal blocking). */
+ * for the images it accepts (no energy tracking, no temporal blocking).
+ * PCAD_KERNEL_WINDOW (PCA sampler, the models PCAD_KERNEL_TENSOR accepts
+ * with nbhd T <= 255; PCAD_EINVAL otherwise) runs one launch per sweep on the
+ * CUDA cores with the tensor-core sweep's weights: each site evaluates only
+ * the label chunks its neighbours' tents reach, their tent sums read from a
+ * table of 8 tents per shared-memory word, the other chunks' sums from a
+ * table of the observation; same labels. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
     PCAD_KERNEL_TENSOR = 2,
     PCAD_KERNEL_WAVE = 3,
     PCAD_KERNEL_SMALL = 4,
-    PCAD_KERNEL_RESIDENT = 5
+    PCAD_KERNEL_RESIDENT = 5,
+    PCAD_KERNEL_WINDOW = 6
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 
 /* The kernel the chain's next sweeps run: PCAD_KERNEL_CUDA_CORE (one launch
  * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR,
- * PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT, or -k for temporal blocking with
- * k sweeps per launch.  With PCAD_KERNEL_AUTO the resident kernel
+ * PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT, PCAD_KERNEL_WINDOW, or -k for
+ * temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO the
+ * resident kernel
  * is taken for the two-label images it accepts without energy tracking; the
- * tensor-core kernel for eligible models with L >= 192 and no energy
- * tracking; PCAD_KERNEL_SMALL for the models it accepts; otherwise
+ * windowed kernel for lazy-PCA chains of models the tensor-core kernel takes
+ * with L >= 192 on images of at least 54 blocks of 4 x 32 sites per
+ * multiprocessor, without energy tracking; the tensor-core kernel for the
+ * other eligible models with L >= 192 and no energy tracking;
+ * PCAD_KERNEL_SMALL for the models it accepts; otherwise
  * the wavefront kernel for L >= 16 when the
  * image has between 1/2 and 3 waves of 4 x 32 tiles at 10 resident tiles
  * per multiprocessor (the sizes where it measured faster on GB300), the

@@ -701,6 +701,7 @@ PCAD_KERNEL_TENSOR = 2
 PCAD_KERNEL_WAVE = 3
 PCAD_KERNEL_SMALL = 4
 PCAD_KERNEL_RESIDENT = 5
+PCAD_KERNEL_WINDOW = 6
 
 
 def pcad_chain_set_kernel(h, kind: int):

@@ -244,6 +244,7 @@ struct pcad_chain {
     double *ta64 = nullptr, *pr64 = nullptr, *in64 = nullptr;
     uint32_t *ptab = nullptr;     // small-L sweep: pair prior table
     uint4 *btab = nullptr;        // two-label draw thresholds (L = 2)
+    float *ftab = nullptr;        // outside-chunk sums of the windowed sweeps
     DevModel dm{};
     cudaGraphExec_t graph = nullptr;
     int tb_k = 0;                 // sweeps per temporally blocked launch (0: one per launch)
@@ -286,6 +287,25 @@ SweepArgs make_args(const pcad_chain *ch)
     return a;
 }
 
+// PCA chains AUTO gives the CUDA-core windowed sweep instead of the
+// tensor-core one: the same models, without energy tracking, on images of
+// at least 54 blocks of 4 x 32 sites per multiprocessor (six waves at 9
+// resident blocks).  Measured on GB300 at L = 256 (site-updates/s): 8192^2
+// 1.28e10 against 1.07e10, 2048^2 1.37e10 against 1.13e10, 1024^2 1.20e10
+// against 1.11e10; at 768^2 and below the tensor-core wavefront is ahead
+// (512^2: 1.08e10 against 0.89e10), the per-sweep launches' last wave then
+// leaving SMs idle.
+bool win_auto(const pcad_chain *ch)
+{
+    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || ch->track.trace ||
+        ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
+        return false;
+    if (!pca_tc_auto(ch->dm) || !pca_win_eligible(ch->dm))
+        return false;
+    const long long blocks = (long long)((ch->W + 31) / 32) * ((ch->H + 3) / 4);
+    return blocks >= 54LL * ch->sms;
+}
+
 // Unblocked PCA sweeps, and 4-neighbourhood checkerboard Gibbs sweeps, on the
 // tensor-core kernel: on request, or with AUTO for the models pca_tc_auto
 // accepts when every sweep's state is not needed (energy tracking would force
@@ -298,7 +318,8 @@ bool uses_tc(const pcad_chain *ch)
         return false;
     if (ch->kernel == PCAD_KERNEL_TENSOR)
         return true;
-    return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace;
+    return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace &&
+           !win_auto(ch);
 }
 
 // Whole runs of sweeps of small two-label images in one single-CTA launch
@@ -312,6 +333,16 @@ bool uses_resident(const pcad_chain *ch)
 }
 
 bool uses_wave(const pcad_chain *ch);
+
+// Unblocked PCA sweeps on the CUDA-core windowed kernel: on request, or
+// with AUTO where win_auto takes it.
+bool uses_win(const pcad_chain *ch)
+{
+    if (win_auto(ch))
+        return true;
+    return ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k == 0 &&
+           ch->kernel == PCAD_KERNEL_WINDOW && pca_win_eligible(ch->dm);
+}
 
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
 // for the models it accepts (3 <= L <= 16, c >= 0, L0 price) unless the
@@ -412,6 +443,8 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
             a.xout = ch->x[cur ^ 1];
             if (uses_small(ch))
                 CUDA_TRY(launch_pca_small(a, st));
+            else if (uses_win(ch))
+                CUDA_TRY(launch_pca_win(a, ch->ftab, st));
             else
                 CUDA_TRY(launch_pca_sweep(a, st));
             cur ^= 1;
@@ -506,8 +539,9 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     const size_t wbytes = align_up((size_t)(ntiles + 1) * sizeof(unsigned int), 256);
     const size_t pbytes = align_up((size_t)ptab_words() * sizeof(uint32_t), 256);
     const size_t bbytes = align_up((size_t)btab_bytes(), 256);
+    const size_t obytes = align_up((size_t)tc_table_floats(m->L) * sizeof(float), 256);
     const size_t total =
-        3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + pbytes + bbytes + misc;
+        3 * plane + 2 * fbytes + cbytes + tbytes + wbytes + pbytes + bbytes + obytes + misc;
     cudaError_t e = cudaMallocAsync(&ch->block, total, ch->stream);
     if (e != cudaSuccess) {
         delete ch;
@@ -528,6 +562,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->wave = (unsigned int *)p; p += wbytes;
     ch->ptab = (uint32_t *)p; p += pbytes;
     ch->btab = (uint4 *)p; p += bbytes;
+    ch->ftab = (float *)p; p += obytes;
     ch->wave_tiles = ntiles;
     {
         int dev = 0;
@@ -567,6 +602,8 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
         e = cudaMemsetAsync(ch->tdev, 0, misc, ch->stream);
     if (e == cudaSuccess && m->L <= kSmallMaxLabels)
         e = launch_ptab(tabs.dm.T, ch->ptab, ch->stream);
+    if (e == cudaSuccess && pca_tc_eligible(tabs.dm))
+        e = launch_tc_table(tabs.dm, ch->ftab, ch->stream);
     if (e == cudaSuccess && m->L == 2) {
         DevModel dm = tabs.dm;
         dm.ta64 = ch->ta64;
@@ -767,6 +804,8 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
     ch->dm.btab = m->L == 2 ? ch->btab : nullptr;
     if (m->L == 2)   // stream-ordered after the new FP64 tables
         CUDA_TRY(launch_btab(ch->dm, ch->btab, ch->stream));
+    if (pca_tc_eligible(ch->dm))
+        CUDA_TRY(launch_tc_table(ch->dm, ch->ftab, ch->stream));
     ch->ecoef = energy_coef(*m, (long)ch->H * ch->W);
     return PCAD_OK;
 }
@@ -805,6 +844,8 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
         *kind = PCAD_KERNEL_WAVE;
     else if (uses_small(ch))
         *kind = PCAD_KERNEL_SMALL;
+    else if (uses_win(ch))
+        *kind = PCAD_KERNEL_WINDOW;
     else
         *kind = PCAD_KERNEL_CUDA_CORE;
     return PCAD_OK;
@@ -919,9 +960,13 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         return fail(PCAD_EINVAL, "chain is NULL");
     if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE &&
         kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE && kind != PCAD_KERNEL_SMALL &&
-        kind != PCAD_KERNEL_RESIDENT)
+        kind != PCAD_KERNEL_RESIDENT && kind != PCAD_KERNEL_WINDOW)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
-                                 "_WAVE, _SMALL or _RESIDENT");
+                                 "_WAVE, _SMALL, _RESIDENT or _WINDOW");
+    if (kind == PCAD_KERNEL_WINDOW &&
+        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_win_eligible(ch->dm)))
+        return fail(PCAD_EINVAL, "the windowed sweep needs the PCA sampler, 64 <= L <= 256, "
+                                 "T <= 33, nbhd T <= 255 and the L0 inertia price");
     if (kind == PCAD_KERNEL_RESIDENT && !resident_eligible(ch->dm, ch->H, ch->W))
         return fail(PCAD_EINVAL, "the resident kernel needs L = 2, 4 or 8 neighbours and at most "
                                  "4096 quads of 4 sites (H * ceil(W / 4))");

@@ -284,6 +284,13 @@ bool pca_tc_auto(const DevModel &m);
 int tc_table_floats(int L);
 cudaError_t launch_tc_table(const DevModel &m, float *out, cudaStream_t s);
 
+// The CUDA-core windowed sweep (the tensor-core sweep's weights, tent sums
+// from a byte table over each site's hull of labels, outside chunks from
+// ftab = launch_tc_table's table): one sweep a.xin -> a.xout.  Models the
+// tensor-core sweep accepts with nbhd T <= 255.
+bool pca_win_eligible(const DevModel &m);
+cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s);
+
 // Batched tensor-core sweeps: nsweeps sweeps of every slot listed in items
 // (tiles of 4 rows x 32 sites of the slot's grid in geom, rows = 4) in one
 // wavefront launch; slot s runs sweeps t_arr[s] + k while below

@@ -1,0 +1,268 @@
+// Lazy-PCA sweep for many labels on the CUDA cores with a per-site label
+// window (Section 5.2, Eq. posterior_pca_transition_matrix), truncated-linear
+// or Potts priors with 64 <= L <= 256.
+//
+// The weights are those of the tensor-core sweep, w(s) = 2^fl(alpha (g-s)^2 +
+// fl(mu Pb(s) + cb)) with the tent sum Pb(s) = sum_j max(T - |x_j - s|, 0)
+// (see tc_math.cuh), so the same per-site certified margin holds.  Pb is zero
+// outside the hull [x_min - T + 1, x_max + T - 1] of the present neighbours:
+// there the chunk sums depend on g only and come from the model's outside
+// table.  Only the hull's chunks (about 11 of 32 at L = 256, T = 30) are
+// evaluated, and without tensor cores:
+//
+//   * Tent bytes.  For a neighbour x_j and a chunk of labels 8c .. 8c + 7,
+//     the 8 tents max(T - |x_j - 8c - k|, 0) are a function of d = x_j - 8c
+//     alone, zero unless -T < d < T + 7.  A 2T + 8 entry table holds them as
+//     8 bytes; one 8-byte shared-memory read per neighbour and two integer
+//     adds give Pb of the chunk's 8 labels, a byte each (at most
+//     nbhd T <= 255, no carries).
+//   * Load balance.  The hull size varies from site to site (one far-off
+//     neighbour widens it), so a warp's (site, chunk) tasks are dealt out to
+//     its 32 lanes in turn: a lane evaluates the chunk of whichever site the
+//     task belongs to and writes the sum into that site's column.
+//   * The rest is the CUDA-core draw: chunk sums in label order with Kahan
+//     compensation (outside chunks from the table), the inertia correction,
+//     the certified inverse-CDF selection with the chosen chunk's weights
+//     recomputed exactly, FP64 re-draws of uncertain draws by the warp.
+//
+// One thread per site, 32 x 4 blocks, one launch per sweep; a warp of each
+// block computes the block's uniforms (one Philox call per 4 sites).
+#include "tc_math.cuh"
+
+namespace pcad {
+
+namespace {
+
+using namespace tcm;
+
+constexpr int kWX = 32;
+constexpr int kWY = 4;
+constexpr int kWThreads = kWX * kWY;
+constexpr int kWMaxChunks = 32;
+// Stride of the [chunk][thread] sums: one more than the block's threads, so
+// the tasks of one site (consecutive chunks) write to different banks.
+constexpr int kGStride = kWThreads + 1;
+constexpr int kTentMax = 2 * 33 + 8;   // entries of the tent-byte table (T <= 33)
+
+// Entry i (d = i - T) of the tent-byte table: byte k = max(T - |d - k|, 0).
+__device__ __forceinline__ uint2 tent_entry(int T, int i)
+{
+    const int d = i - T;
+    uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        lo |= (uint32_t)max(T - abs(d - k), 0) << (8 * k);
+        hi |= (uint32_t)max(T - abs(d - 4 - k), 0) << (8 * k);
+    }
+    return make_uint2(lo, hi);
+}
+
+// Exact float of byte k of p (the byte placed in the mantissa of 2^23).
+__device__ __forceinline__ float pb_byte(uint32_t p, int k)
+{
+    return __uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)k));
+}
+
+// Sum of the weights of chunk c (labels 8c .. 8c + 7) of a site with
+// observation gf and neighbour labels x (1024: missing).  The tent sums come
+// from the byte table (exact integers), the weights and their pairwise tree
+// sum are window_chunk's, so the value equals the tensor-core sweep's for
+// the same chunk.
+template <int NB, bool LMASK>
+__device__ __forceinline__ float win_chunk_sum(const DevModel &m, float mu, float gf,
+                                               const int (&x)[NB], int c, const uint2 *tent,
+                                               uint32_t zero_i)
+{
+    uint32_t lo = 0u, hi = 0u;
+    const int off = m.T - kChunk * c;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const uint32_t i = min((uint32_t)(x[j] + off), zero_i);
+        const uint2 e = tent[i];
+        lo += e.x;
+        hi += e.y;
+    }
+    const float dgb = __fsub_rn(gf, (float)(c * kChunk));
+    const float2 a2 = make_float2(m.alpha, m.alpha), mu2 = make_float2(mu, mu),
+                 cb2 = make_float2(m.cb, m.cb), mag2 = make_float2(-8388608.0f, -8388608.0f);
+    const float2 dgb2 = make_float2(dgb, __fsub_rn(dgb, 1.0f));
+    float2 wv[4];
+#pragma unroll
+    for (int k = 0; k < kChunk; k += 2) {
+        const uint32_t p = k < 4 ? lo : hi;
+        const float2 pb2 =
+            __fadd2_rn(make_float2(pb_byte(p, k & 3), pb_byte(p, (k + 1) & 3)), mag2);
+        const float2 dg = __fadd2_rn(dgb2, make_float2(-(float)k, -(float)k));
+        const float2 qq = __fmul2_rn(dg, dg);
+        const float2 in2 = __ffma2_rn(mu2, pb2, cb2);
+        const float2 v = __ffma2_rn(a2, qq, in2);
+        float w0 = ex2_ftz(v.x), w1 = ex2_ftz(v.y);
+        if (LMASK && c * kChunk + k >= m.L)
+            w0 = 0.0f;
+        if (LMASK && c * kChunk + k + 1 >= m.L)
+            w1 = 0.0f;
+        wv[k >> 1] = make_float2(w0, w1);
+    }
+    const float2 a = __fadd2_rn(make_float2(wv[0].x, wv[2].x), make_float2(wv[0].y, wv[2].y));
+    const float2 b = __fadd2_rn(make_float2(wv[1].x, wv[3].x), make_float2(wv[1].y, wv[3].y));
+    const float2 t2 = __fadd2_rn(a, b);
+    return __fadd_rn(t2.x, t2.y);
+}
+
+// One sweep: a.xin -> a.xout, accumulate after burn-in.  ftab: the model's
+// outside-chunk table (tc_table_floats floats, launch_tc_table).
+template <int NB, bool LMASK>
+__global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a,
+                                                               const float *ftab)
+{
+    __shared__ float G_s[kWMaxChunks * kGStride];
+    __shared__ __align__(16) uint32_t U_s[kWY * kWX];
+    __shared__ __align__(16) float F_s[kTabF];
+    __shared__ __align__(8) uint2 tent_s[kTentMax];
+    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
+    const int tid = wp * kWX + lane;
+    const int c = (int)blockIdx.x * kWX + lane;
+    const int r = (int)blockIdx.y * kWY + wp;
+    const DevModel &m = a.m;
+    const int T = m.T;
+    const uint32_t zero_i = (uint32_t)(2 * T + 7);   // an all-zero entry
+    for (int i = tid; i < kTabF / 4; i += kWThreads)
+        reinterpret_cast<float4 *>(F_s)[i] = __ldg(reinterpret_cast<const float4 *>(ftab) + i);
+    for (int i = tid; i < 2 * T + 8; i += kWThreads)
+        tent_s[i] = tent_entry(T, i);
+    const uint32_t t = sweep_index(a);
+    if (wp == 0)
+        block_uniforms(a, (int)blockIdx.y * kWY, (int)blockIdx.x * kWX, t, U_s);
+    __syncthreads();
+
+    const bool valid = r < a.H && c < a.W;
+    SiteIn<NB> in{};
+    if (valid) {
+        load_site<NB, false, false>(a, a.xin, r, c, kTagPCA, t, in);
+        in.ub = U_s[tid];
+    }
+    const float mu = -m.gam;
+    const int nc = (m.L + kChunk - 1) / kChunk;
+    const float gf = (float)in.g;
+    // the hull's chunks: where some present neighbour's tent is nonzero
+    int xmin = kMissingLabelI, xmax = -1;
+#pragma unroll
+    for (int j = 0; j < NB; ++j)
+        if (in.xni[j] < kMissingLabelI) {
+            xmin = min(xmin, in.xni[j]);
+            xmax = max(xmax, in.xni[j]);
+        }
+    int clo = 0, cnt = 0;
+    if (valid && xmax >= 0) {
+        clo = max(xmin - T + 1, 0) >> 3;
+        cnt = min((xmax + T - 1) >> 3, nc - 1) - clo + 1;
+    }
+    // the warp's (site, chunk) tasks, dealt out to its lanes in turn; a lane
+    // writes each sum into the owning site's column
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o)
+            incl += v;
+    }
+    const int ntask = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    float *Gcol = G_s + tid;
+#pragma unroll 1
+    for (int base = 0; base < ntask; base += 32) {
+        const int tsk = base + lane;
+        int owner = 0;   // the first lane whose inclusive count exceeds tsk
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
+            if (v <= tsk)
+                owner += step;
+        }
+        owner = min(owner, 31);
+        const int o_excl = __shfl_sync(0xFFFFFFFFu, incl - cnt, owner);
+        const int o_clo = __shfl_sync(0xFFFFFFFFu, clo, owner);
+        const float o_gf = __shfl_sync(0xFFFFFFFFu, gf, owner);
+        int o_x[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            o_x[j] = __shfl_sync(0xFFFFFFFFu, in.xni[j], owner);
+        const bool mine = tsk < ntask;
+        const int cc = mine ? o_clo + (tsk - o_excl) : 0;
+        const float S = win_chunk_sum<NB, LMASK>(m, mu, o_gf, o_x, cc, tent_s, zero_i);
+        if (mine)
+            Gcol[cc * kGStride + owner - lane] = S;
+    }
+    __syncwarp();
+
+    // chunk prefix sums in label order (Kahan), outside chunks from the table
+    float G = 0.0f, comp = 0.0f;
+    const int chi = clo + cnt - 1;
+#pragma unroll 4
+    for (int cc = 0; cc < nc; ++cc) {
+        const float S = (cc >= clo && cc <= chi) ? Gcol[cc * kGStride]
+                                                 : tab_sum<LMASK>(F_s, in.g, cc, nc);
+        const float y = __fsub_rn(S, comp);
+        const float tt = __fadd_rn(G, y);
+        comp = __fsub_rn(__fsub_rn(tt, G), y);
+        G = tt;
+        Gcol[cc * kGStride] = G;
+    }
+    int s = 0;
+    bool certain = true;
+    if (valid) {
+        float xn[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            xn[j] = (float)in.xni[j];
+        float delta = 0.0f;
+        if (m.em1 != 0.0f) {
+            const float xif = (float)in.xi;
+            delta = __fmul_rn(label_wb(m, mu, tent_sum<NB>(xn, m.Tf, xif), __fsub_rn(gf, xif)),
+                              m.em1);
+        }
+        s = cdf_select(m, site_margin(m, G, delta), [&](int cc) { return Gcol[cc * kGStride]; },
+                       nc, G, delta, in.xi, in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
+                           chunk_prefix_exact<NB>(m, mu, xn, gf, cs, pp);
+                       });
+    }
+    s = warp_redraw_fp64<NB>(m, valid && !certain, in, s, a.fp64_draws);
+    if (valid) {
+        a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+        if (accumulate_after(a, t)) {
+            float *p = a.acc + (size_t)r * a.W + c;
+            *p = *p + (float)s;
+        }
+    }
+}
+
+template <int NB, bool LMASK>
+cudaError_t launch_win_t(const SweepArgs &a, const float *ftab, cudaStream_t st)
+{
+    const dim3 block(kWX, kWY);
+    const dim3 grid((a.W + kWX - 1) / kWX, (a.H + kWY - 1) / kWY);
+    if (grid.y > 65535u)
+        return cudaErrorInvalidValue;
+    pca_win_kernel<NB, LMASK><<<grid, block, 0, st>>>(a, ftab);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool pca_win_eligible(const DevModel &m)
+{
+    return pca_tc_eligible(m) && m.nbhd * m.T <= 255;
+}
+
+cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t st)
+{
+    if (!pca_win_eligible(a.m) || ftab == nullptr)
+        return cudaErrorInvalidValue;
+    if (a.H <= 0 || a.W <= 0)
+        return cudaSuccess;
+    const bool lmask = (a.m.L % kChunk) != 0;
+    if (a.m.nbhd == 8)
+        return lmask ? launch_win_t<8, true>(a, ftab, st) : launch_win_t<8, false>(a, ftab, st);
+    return lmask ? launch_win_t<4, true>(a, ftab, st) : launch_win_t<4, false>(a, ftab, st);
+}
+
+}  // namespace pcad
