@@ -155,7 +155,7 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * unknown kind or PCAD_KERNEL_TENSOR on another model.  PCAD_KERNEL_AUTO
  * (the default) takes it for L >= 192 without energy tracking (where it
  * measured faster on GB300), except lazy-PCA chains on images of at least
- * 54 blocks of 4 x 32 sites per multiprocessor, which take
+ * 16 blocks of 4 x 32 sites per multiprocessor, which take
  * PCAD_KERNEL_WINDOW (below); else the per-sweep or the wavefront CUDA-core
  * kernel (see pcad_chain_kernel_in_use).  PCAD_KERNEL_WAVE runs the
  * CUDA-core draw as one persistent launch per block of sweeps, a tile of
@@ -204,7 +204,7 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * resident kernel
  * is taken for the two-label images it accepts without energy tracking; the
  * windowed kernel for lazy-PCA chains of models the tensor-core kernel takes
- * with L >= 192 on images of at least 54 blocks of 4 x 32 sites per
+ * with L >= 192 on images of at least 16 blocks of 4 x 32 sites per
  * multiprocessor, without energy tracking; the tensor-core kernel for the
  * other eligible models with L >= 192 and no energy tracking;
  * PCAD_KERNEL_SMALL for the models it accepts; otherwise

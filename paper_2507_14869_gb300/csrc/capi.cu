@@ -289,12 +289,11 @@ SweepArgs make_args(const pcad_chain *ch)
 
 // PCA chains AUTO gives the CUDA-core windowed sweep instead of the
 // tensor-core one: the same models, without energy tracking, on images of
-// at least 54 blocks of 4 x 32 sites per multiprocessor (six waves at 9
-// resident blocks).  Measured on GB300 at L = 256 (site-updates/s): 8192^2
-// 1.28e10 against 1.07e10, 2048^2 1.37e10 against 1.13e10, 1024^2 1.20e10
-// against 1.11e10; at 768^2 and below the tensor-core wavefront is ahead
-// (512^2: 1.08e10 against 0.89e10), the per-sweep launches' last wave then
-// leaving SMs idle.
+// at least 16 blocks of 4 x 32 sites per multiprocessor.  Measured on GB300
+// at L = 256 (site-updates/s): 8192^2 1.51e10 against 1.07e10, 2048^2
+// 1.61e10 against 1.14e10, 1024^2 1.44e10 against 1.11e10; level at 512^2
+// (1.08e10 each), where the per-sweep launches' last wave leaves SMs idle
+// and the tensor-core wavefront does not.
 bool win_auto(const pcad_chain *ch)
 {
     if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || ch->track.trace ||
@@ -303,7 +302,7 @@ bool win_auto(const pcad_chain *ch)
     if (!pca_tc_auto(ch->dm) || !pca_win_eligible(ch->dm))
         return false;
     const long long blocks = (long long)((ch->W + 31) / 32) * ((ch->H + 3) / 4);
-    return blocks >= 54LL * ch->sms;
+    return blocks >= 16LL * ch->sms;
 }
 
 // Unblocked PCA sweeps, and 4-neighbourhood checkerboard Gibbs sweeps, on the

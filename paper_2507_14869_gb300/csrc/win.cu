@@ -16,17 +16,17 @@
 //     8 bytes; one 8-byte shared-memory read per neighbour and two integer
 //     adds give Pb of the chunk's 8 labels, a byte each (at most
 //     nbhd T <= 255, no carries).
-//   * Load balance.  The hull size varies from site to site (one far-off
-//     neighbour widens it), so a warp's (site, chunk) tasks are dealt out to
-//     its 32 lanes in turn: a lane evaluates the chunk of whichever site the
-//     task belongs to and writes the sum into that site's column.
+//   * Balanced warps.  The hull size varies from site to site (one far-off
+//     neighbour widens it) and a warp runs as long as its widest hull, so
+//     the block sorts its 128 sites by hull size and warp w evaluates the
+//     chunks of the w-th quarter.
 //   * The rest is the CUDA-core draw: chunk sums in label order with Kahan
 //     compensation (outside chunks from the table), the inertia correction,
 //     the certified inverse-CDF selection with the chosen chunk's weights
 //     recomputed exactly, FP64 re-draws of uncertain draws by the warp.
 //
-// One thread per site, 32 x 4 blocks, one launch per sweep; a warp of each
-// block computes the block's uniforms (one Philox call per 4 sites).
+// One thread per site, blocks of 4 x 32 sites, one launch per sweep; a warp
+// of each block computes the block's uniforms (one Philox call per 4 sites).
 #include "tc_math.cuh"
 
 namespace pcad {
@@ -39,12 +39,14 @@ constexpr int kWX = 32;
 constexpr int kWY = 4;
 constexpr int kWThreads = kWX * kWY;
 constexpr int kWMaxChunks = 32;
-// Stride of the [chunk][thread] sums: one more than the block's threads, so
-// the tasks of one site (consecutive chunks) write to different banks.
-constexpr int kGStride = kWThreads + 1;
 constexpr int kTentMax = 2 * 33 + 8;   // entries of the tent-byte table (T <= 33)
 
 // Entry i (d = i - T) of the tent-byte table: byte k = max(T - |d - k|, 0).
+// d = x_j - 8c outside (-T, T + 7) gives all zeros: such an index is
+// clamped to the last entry (2T + 7, itself zero).  Most lanes of a warp
+// then read the same zero entry, which shared memory broadcasts (a table
+// over every d without the clamp measured 5 % slower: more distinct
+// addresses per read, more bank conflicts).
 __device__ __forceinline__ uint2 tent_entry(int T, int i)
 {
     const int d = i - T;
@@ -64,24 +66,13 @@ __device__ __forceinline__ float pb_byte(uint32_t p, int k)
 }
 
 // Sum of the weights of chunk c (labels 8c .. 8c + 7) of a site with
-// observation gf and neighbour labels x (1024: missing).  The tent sums come
-// from the byte table (exact integers), the weights and their pairwise tree
-// sum are window_chunk's, so the value equals the tensor-core sweep's for
-// the same chunk.
-template <int NB, bool LMASK>
-__device__ __forceinline__ float win_chunk_sum(const DevModel &m, float mu, float gf,
-                                               const int (&x)[NB], int c, const uint2 *tent,
-                                               uint32_t zero_i)
+// observation gf from its 8 tent sums (bytes of lo, hi: exact integers).
+// The weights and their pairwise tree sum are window_chunk's, so the value
+// equals the tensor-core sweep's for the same chunk.
+template <bool LMASK>
+__device__ __forceinline__ float win_chunk_sum(const DevModel &m, float mu, float gf, int c,
+                                               uint32_t lo, uint32_t hi)
 {
-    uint32_t lo = 0u, hi = 0u;
-    const int off = m.T - kChunk * c;
-#pragma unroll
-    for (int j = 0; j < NB; ++j) {
-        const uint32_t i = min((uint32_t)(x[j] + off), zero_i);
-        const uint2 e = tent[i];
-        lo += e.x;
-        hi += e.y;
-    }
     const float dgb = __fsub_rn(gf, (float)(c * kChunk));
     const float2 a2 = make_float2(m.alpha, m.alpha), mu2 = make_float2(mu, mu),
                  cb2 = make_float2(m.cb, m.cb), mag2 = make_float2(-8388608.0f, -8388608.0f);
@@ -109,27 +100,82 @@ __device__ __forceinline__ float win_chunk_sum(const DevModel &m, float mu, floa
     return __fadd_rn(t2.x, t2.y);
 }
 
+// The 8 tent sums of chunk c from neighbour labels x (bytes of lo, hi).
+template <int NB>
+__device__ __forceinline__ void chunk_tents(const int (&x)[NB], int c, int T, const uint2 *tent,
+                                            uint32_t &lo, uint32_t &hi)
+{
+    const uint32_t zero_i = (uint32_t)(2 * T + 7);   // an all-zero entry
+    const int off = T - kChunk * c;
+    lo = hi = 0u;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const uint2 e = tent[min((uint32_t)(x[j] + off), zero_i)];
+        lo += e.x;
+        hi += e.y;
+    }
+}
+
+// Inclusive prefix sums p[0..7] of chunk c's weights (from its tent sums lo,
+// hi): the operations of chunk_prefix_exact on the same exact tent sums,
+// hence the same values.
+__device__ __forceinline__ void win_chunk_prefix(const DevModel &m, float mu, float gf, int c,
+                                                 uint32_t lo, uint32_t hi, float (&p)[kChunk])
+{
+    const float dgb = __fsub_rn(gf, (float)(c * kChunk));
+    const float2 a2 = make_float2(m.alpha, m.alpha), mu2 = make_float2(mu, mu),
+                 cb2 = make_float2(m.cb, m.cb), mag2 = make_float2(-8388608.0f, -8388608.0f);
+    const float2 dgb2 = make_float2(dgb, __fsub_rn(dgb, 1.0f));
+    float S = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kChunk; k += 2) {
+        const uint32_t pw = k < 4 ? lo : hi;
+        const float2 pb2 =
+            __fadd2_rn(make_float2(pb_byte(pw, k & 3), pb_byte(pw, (k + 1) & 3)), mag2);
+        const float2 dg = __fadd2_rn(dgb2, make_float2(-(float)k, -(float)k));
+        const float2 qq = __fmul2_rn(dg, dg);
+        const float2 in2 = __ffma2_rn(mu2, pb2, cb2);
+        const float2 v = __ffma2_rn(a2, qq, in2);
+        float w0 = ex2_ftz(v.x), w1 = ex2_ftz(v.y);
+        if (c * kChunk + k >= m.L)
+            w0 = 0.0f;
+        if (c * kChunk + k + 1 >= m.L)
+            w1 = 0.0f;
+        S = __fadd_rn(S, w0);
+        p[k] = S;
+        S = __fadd_rn(S, w1);
+        p[k + 1] = S;
+    }
+}
+
 // One sweep: a.xin -> a.xout, accumulate after burn-in.  ftab: the model's
 // outside-chunk table (tc_table_floats floats, launch_tc_table).
 template <int NB, bool LMASK>
 __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a,
                                                                const float *ftab)
 {
-    __shared__ float G_s[kWMaxChunks * kGStride];
+    __shared__ float G_s[kWMaxChunks * kWThreads];
     __shared__ __align__(16) uint32_t U_s[kWY * kWX];
     __shared__ __align__(16) float F_s[kTabF];
-    __shared__ __align__(8) uint2 tent_s[kTentMax];
+    __shared__ __align__(16) uint2 tent_s[kTentMax];
+    __shared__ int rec_s[NB + 1][kWThreads];   // per site: neighbour labels; g | clo << 9 | cnt << 16
+    __shared__ int bins_s[kWMaxChunks + 1];    // hull sizes 0..32: counts, then offsets
+    __shared__ uint8_t perm_s[kWThreads];      // sites in increasing hull size
+    // warp wp takes the block's columns 8 wp .. 8 wp + 7 over its 4 rows (a
+    // compact tile: neighbouring sites have similar hulls)
     const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
     const int tid = wp * kWX + lane;
-    const int c = (int)blockIdx.x * kWX + lane;
-    const int r = (int)blockIdx.y * kWY + wp;
+    const int lr = lane >> 3, lc = 8 * wp + (lane & 7);
+    const int c = (int)blockIdx.x * kWX + lc;
+    const int r = (int)blockIdx.y * kWY + lr;
     const DevModel &m = a.m;
     const int T = m.T;
-    const uint32_t zero_i = (uint32_t)(2 * T + 7);   // an all-zero entry
     for (int i = tid; i < kTabF / 4; i += kWThreads)
         reinterpret_cast<float4 *>(F_s)[i] = __ldg(reinterpret_cast<const float4 *>(ftab) + i);
     for (int i = tid; i < 2 * T + 8; i += kWThreads)
         tent_s[i] = tent_entry(T, i);
+    if (tid <= kWMaxChunks)
+        bins_s[tid] = 0;
     const uint32_t t = sweep_index(a);
     if (wp == 0)
         block_uniforms(a, (int)blockIdx.y * kWY, (int)blockIdx.x * kWX, t, U_s);
@@ -139,7 +185,7 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
     SiteIn<NB> in{};
     if (valid) {
         load_site<NB, false, false>(a, a.xin, r, c, kTagPCA, t, in);
-        in.ub = U_s[tid];
+        in.ub = U_s[lr * kWX + lc];
     }
     const float mu = -m.gam;
     const int nc = (m.L + kChunk - 1) / kChunk;
@@ -157,55 +203,68 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
         clo = max(xmin - T + 1, 0) >> 3;
         cnt = min((xmax + T - 1) >> 3, nc - 1) - clo + 1;
     }
-    // the warp's (site, chunk) tasks, dealt out to its lanes in turn; a lane
-    // writes each sum into the owning site's column
-    int incl = cnt;
+    // The block's sites sorted by hull size (a counting sort): thread i
+    // evaluates the chunks of the i-th smallest hull and writes them into that
+    // site's column, so a warp's longest hull is close to its other lanes'.
+    // (Dealing (site, chunk) tasks out over a warp with shuffles measured
+    // slower: they cost more than the imbalance they remove.)
+    for (int j = 0; j < NB; ++j)
+        rec_s[j][tid] = in.xni[j];
+    rec_s[NB][tid] = in.g | (clo << 9) | (cnt << 16);
+    const int rank = atomicAdd(&bins_s[cnt], 1);
+    __syncthreads();
+    if (wp == 0) {   // exclusive offsets of the bins 0..32
+        const int b = bins_s[lane];
+        int inc = b;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o)
-            incl += v;
-    }
-    const int ntask = __shfl_sync(0xFFFFFFFFu, incl, 31);
-    float *Gcol = G_s + tid;
-#pragma unroll 1
-    for (int base = 0; base < ntask; base += 32) {
-        const int tsk = base + lane;
-        int owner = 0;   // the first lane whose inclusive count exceeds tsk
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const int v = __shfl_sync(0xFFFFFFFFu, incl, owner + step - 1);
-            if (v <= tsk)
-                owner += step;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o)
+                inc += v;
         }
-        owner = min(owner, 31);
-        const int o_excl = __shfl_sync(0xFFFFFFFFu, incl - cnt, owner);
-        const int o_clo = __shfl_sync(0xFFFFFFFFu, clo, owner);
-        const float o_gf = __shfl_sync(0xFFFFFFFFu, gf, owner);
-        int o_x[NB];
+        __syncwarp();
+        bins_s[lane] = inc - b;
+        if (lane == 31)
+            bins_s[32] = inc;
+    }
+    __syncthreads();
+    perm_s[bins_s[cnt] + rank] = (uint8_t)tid;
+    __syncthreads();
+    {
+        const int sid = perm_s[tid];
+        int sx[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-            o_x[j] = __shfl_sync(0xFFFFFFFFu, in.xni[j], owner);
-        const bool mine = tsk < ntask;
-        const int cc = mine ? o_clo + (tsk - o_excl) : 0;
-        const float S = win_chunk_sum<NB, LMASK>(m, mu, o_gf, o_x, cc, tent_s, zero_i);
-        if (mine)
-            Gcol[cc * kGStride + owner - lane] = S;
+            sx[j] = rec_s[j][sid];
+        const int pk = rec_s[NB][sid];
+        const int sclo = (pk >> 9) & 127, scnt = pk >> 16;
+        const float sgf = (float)(pk & 511);
+        const int maxcnt = __reduce_max_sync(0xFFFFFFFFu, scnt);
+#pragma unroll 1
+        for (int k = 0; k < maxcnt; ++k) {
+            if (k < scnt) {
+                const int cc = sclo + k;
+                uint32_t lo, hi;
+                chunk_tents<NB>(sx, cc, T, tent_s, lo, hi);
+                G_s[cc * kWThreads + sid] = win_chunk_sum<LMASK>(m, mu, sgf, cc, lo, hi);
+            }
+        }
     }
-    __syncwarp();
+    __syncthreads();
+    float *Gcol = G_s + tid;
 
     // chunk prefix sums in label order (Kahan), outside chunks from the table
     float G = 0.0f, comp = 0.0f;
     const int chi = clo + cnt - 1;
 #pragma unroll 4
     for (int cc = 0; cc < nc; ++cc) {
-        const float S = (cc >= clo && cc <= chi) ? Gcol[cc * kGStride]
+        const float S = (cc >= clo && cc <= chi) ? Gcol[cc * kWThreads]
                                                  : tab_sum<LMASK>(F_s, in.g, cc, nc);
         const float y = __fsub_rn(S, comp);
         const float tt = __fadd_rn(G, y);
         comp = __fsub_rn(__fsub_rn(tt, G), y);
         G = tt;
-        Gcol[cc * kGStride] = G;
+        Gcol[cc * kWThreads] = G;
     }
     int s = 0;
     bool certain = true;
@@ -220,9 +279,11 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
             delta = __fmul_rn(label_wb(m, mu, tent_sum<NB>(xn, m.Tf, xif), __fsub_rn(gf, xif)),
                               m.em1);
         }
-        s = cdf_select(m, site_margin(m, G, delta), [&](int cc) { return Gcol[cc * kGStride]; },
+        s = cdf_select(m, site_margin(m, G, delta), [&](int cc) { return Gcol[cc * kWThreads]; },
                        nc, G, delta, in.xi, in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
-                           chunk_prefix_exact<NB>(m, mu, xn, gf, cs, pp);
+                           uint32_t lo, hi;
+                           chunk_tents<NB>(in.xni, cs, T, tent_s, lo, hi);
+                           win_chunk_prefix(m, mu, gf, cs, lo, hi, pp);
                        });
     }
     s = warp_redraw_fp64<NB>(m, valid && !certain, in, s, a.fp64_draws);

@@ -104,10 +104,10 @@ def test_kernel_in_use_auto_rule(pc):
     slots = 10 * sms
     m256 = Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0)
     # L >= 192 and eligible for the tensor-core sweep: that one, or the
-    # CUDA-core windowed sweep from 54 blocks of 4 x 32 sites per SM on
+    # CUDA-core windowed sweep from 16 blocks of 4 x 32 sites per SM on
     for side in (128, 512, 2048):
         g = np.zeros((side, side), np.uint8)
-        big = (side // 32) * (side // 4) >= 54 * sms
+        big = (side // 32) * (side // 4) >= 16 * sms
         with pc.Chain(g, m256, seed=1) as ch:
             assert ch.kernel_in_use() == (pc.PCAD_KERNEL_WINDOW if big
                                           else pc.PCAD_KERNEL_TENSOR), side
