@@ -154,7 +154,7 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * in place, as a wavefront of phases; Section 5.1); PCAD_EINVAL for an
  * unknown kind or PCAD_KERNEL_TENSOR on another model.  PCAD_KERNEL_AUTO
  * (the default) takes it for L >= 192 without energy tracking (where it
- * measured faster on GB300), except lazy-PCA chains on images of at least
+ * measured faster on GB300), except chains on images of at least
  * 16 blocks of 4 x 32 sites per multiprocessor, which take
  * PCAD_KERNEL_WINDOW (below); else the per-sweep or the wavefront CUDA-core
  * kernel (see pcad_chain_kernel_in_use).  PCAD_KERNEL_WAVE runs the
@@ -180,12 +180,14 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * FP64 re-draw of the other kernels; same labels and the same FP64 re-draw
  * count (with two labels every inertia price is the L0 one).  AUTO takes it
  * for the images it accepts (no energy tracking, no temporal blocking).
- * PCAD_KERNEL_WINDOW (PCA sampler, the models PCAD_KERNEL_TENSOR accepts
- * with nbhd T <= 255; PCAD_EINVAL otherwise) runs one launch per sweep on the
- * CUDA cores with the tensor-core sweep's weights: each site evaluates only
- * the label chunks its neighbours' tents reach, their tent sums read from a
- * table of 8 tents per shared-memory word, the other chunks' sums from a
- * table of the observation; same labels. */
+ * PCAD_KERNEL_WINDOW (the models PCAD_KERNEL_TENSOR accepts with
+ * nbhd T <= 255, either sampler and neighbourhood; PCAD_EINVAL otherwise)
+ * runs one launch per sweep (per Gibbs colour phase) on the CUDA cores with
+ * the tensor-core sweep's weights: each site evaluates only the label chunks
+ * its neighbours' tents reach, their tent sums read from a table of 8 tents
+ * per 8-byte shared-memory entry, the other chunks' sums from a table of the
+ * observation, the sites of a block sorted by the number of such chunks so
+ * that a warp's lanes do similar work; same labels. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
@@ -203,9 +205,10 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO the
  * resident kernel
  * is taken for the two-label images it accepts without energy tracking; the
- * windowed kernel for lazy-PCA chains of models the tensor-core kernel takes
- * with L >= 192 on images of at least 16 blocks of 4 x 32 sites per
- * multiprocessor, without energy tracking; the tensor-core kernel for the
+ * windowed kernel for chains of models the tensor-core kernel takes (any
+ * neighbourhood for Gibbs) with L >= 192 on images of at least 16 blocks of
+ * 4 x 32 sites per multiprocessor, without energy tracking; the tensor-core
+ * kernel for the
  * other eligible models with L >= 192 and no energy tracking;
  * PCAD_KERNEL_SMALL for the models it accepts; otherwise
  * the wavefront kernel for L >= 16 when the

@@ -287,8 +287,10 @@ SweepArgs make_args(const pcad_chain *ch)
     return a;
 }
 
-// PCA chains AUTO gives the CUDA-core windowed sweep instead of the
-// tensor-core one: the same models, without energy tracking, on images of
+// Chains AUTO gives the CUDA-core windowed sweep (lazy PCA, or checkerboard
+// Gibbs colour phases) instead of the tensor-core one: the same models (and
+// the 8-neighbourhood Gibbs the tensor-core sweep lacks), without energy
+// tracking, on images of
 // at least 16 blocks of 4 x 32 sites per multiprocessor.  Measured on GB300
 // at L = 256 (site-updates/s): 8192^2 1.51e10 against 1.07e10, 2048^2
 // 1.61e10 against 1.14e10, 1024^2 1.44e10 against 1.11e10; level at 512^2
@@ -296,8 +298,7 @@ SweepArgs make_args(const pcad_chain *ch)
 // and the tensor-core wavefront does not.
 bool win_auto(const pcad_chain *ch)
 {
-    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || ch->track.trace ||
-        ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
+    if (ch->tb_k > 0 || ch->track.trace || ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
         return false;
     if (!pca_tc_auto(ch->dm) || !pca_win_eligible(ch->dm))
         return false;
@@ -333,14 +334,13 @@ bool uses_resident(const pcad_chain *ch)
 
 bool uses_wave(const pcad_chain *ch);
 
-// Unblocked PCA sweeps on the CUDA-core windowed kernel: on request, or
-// with AUTO where win_auto takes it.
+// Unblocked sweeps (PCA or Gibbs) on the CUDA-core windowed kernels: on
+// request, or with AUTO where win_auto takes them.
 bool uses_win(const pcad_chain *ch)
 {
     if (win_auto(ch))
         return true;
-    return ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k == 0 &&
-           ch->kernel == PCAD_KERNEL_WINDOW && pca_win_eligible(ch->dm);
+    return ch->tb_k == 0 && ch->kernel == PCAD_KERNEL_WINDOW && pca_win_eligible(ch->dm);
 }
 
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
@@ -453,9 +453,13 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
         } else {
             a.xin = ch->x[cur];
             a.xout = nullptr;
+            const bool win = uses_win(ch);
             for (int q = 0; q < ncol; ++q) {
                 a.last_phase = q == ncol - 1;
-                CUDA_TRY(launch_gibbs_phase(a, q, st));
+                if (win)
+                    CUDA_TRY(launch_gibbs_win(a, q, ch->ftab, st));
+                else
+                    CUDA_TRY(launch_gibbs_phase(a, q, st));
             }
             if (ch->track.trace)
                 CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
@@ -834,7 +838,8 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
     if (uses_resident(ch))
         *kind = PCAD_KERNEL_RESIDENT;
     else if (ch->model.sampler != PCAD_SAMPLER_PCA)
-        *kind = uses_tc(ch) ? PCAD_KERNEL_TENSOR : PCAD_KERNEL_CUDA_CORE;
+        *kind = uses_tc(ch) ? PCAD_KERNEL_TENSOR
+                            : (uses_win(ch) ? PCAD_KERNEL_WINDOW : PCAD_KERNEL_CUDA_CORE);
     else if (ch->tb_k > 0)
         *kind = -ch->tb_k;
     else if (uses_tc(ch))
@@ -962,10 +967,9 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         kind != PCAD_KERNEL_RESIDENT && kind != PCAD_KERNEL_WINDOW)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
                                  "_WAVE, _SMALL, _RESIDENT or _WINDOW");
-    if (kind == PCAD_KERNEL_WINDOW &&
-        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_win_eligible(ch->dm)))
-        return fail(PCAD_EINVAL, "the windowed sweep needs the PCA sampler, 64 <= L <= 256, "
-                                 "T <= 33, nbhd T <= 255 and the L0 inertia price");
+    if (kind == PCAD_KERNEL_WINDOW && !pca_win_eligible(ch->dm))
+        return fail(PCAD_EINVAL, "the windowed sweep needs 64 <= L <= 256, T <= 33, "
+                                 "nbhd T <= 255 and the L0 inertia price");
     if (kind == PCAD_KERNEL_RESIDENT && !resident_eligible(ch->dm, ch->H, ch->W))
         return fail(PCAD_EINVAL, "the resident kernel needs L = 2, 4 or 8 neighbours and at most "
                                  "4096 quads of 4 sites (H * ceil(W / 4))");

@@ -290,6 +290,9 @@ cudaError_t launch_tc_table(const DevModel &m, float *out, cudaStream_t s);
 // tensor-core sweep accepts with nbhd T <= 255.
 bool pca_win_eligible(const DevModel &m);
 cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s);
+// Checkerboard Gibbs colour phase q (0..nbhd/2 - 1) in place on a.xin with
+// the windowed draw; a.last_phase: accumulate the cells after it.
+cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t s);
 
 // Batched tensor-core sweeps: nsweeps sweeps of every slot listed in items
 // (tiles of 4 rows x 32 sites of the slot's grid in geom, rows = 4) in one

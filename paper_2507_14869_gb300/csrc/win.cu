@@ -148,45 +148,39 @@ __device__ __forceinline__ void win_chunk_prefix(const DevModel &m, float mu, fl
     }
 }
 
-// One sweep: a.xin -> a.xout, accumulate after burn-in.  ftab: the model's
-// outside-chunk table (tc_table_floats floats, launch_tc_table).
-template <int NB, bool LMASK>
-__global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a,
-                                                               const float *ftab)
-{
-    __shared__ float G_s[kWMaxChunks * kWThreads];
-    __shared__ __align__(16) uint32_t U_s[kWY * kWX];
-    __shared__ __align__(16) float F_s[kTabF];
-    __shared__ __align__(16) uint2 tent_s[kTentMax];
-    __shared__ int rec_s[NB + 1][kWThreads];   // per site: neighbour labels; g | clo << 9 | cnt << 16
-    __shared__ int bins_s[kWMaxChunks + 1];    // hull sizes 0..32: counts, then offsets
-    __shared__ uint8_t perm_s[kWThreads];      // sites in increasing hull size
-    // warp wp takes the block's columns 8 wp .. 8 wp + 7 over its 4 rows (a
-    // compact tile: neighbouring sites have similar hulls)
-    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
-    const int tid = wp * kWX + lane;
-    const int lr = lane >> 3, lc = 8 * wp + (lane & 7);
-    const int c = (int)blockIdx.x * kWX + lc;
-    const int r = (int)blockIdx.y * kWY + lr;
-    const DevModel &m = a.m;
-    const int T = m.T;
-    for (int i = tid; i < kTabF / 4; i += kWThreads)
-        reinterpret_cast<float4 *>(F_s)[i] = __ldg(reinterpret_cast<const float4 *>(ftab) + i);
-    for (int i = tid; i < 2 * T + 8; i += kWThreads)
-        tent_s[i] = tent_entry(T, i);
-    if (tid <= kWMaxChunks)
-        bins_s[tid] = 0;
-    const uint32_t t = sweep_index(a);
-    if (wp == 0)
-        block_uniforms(a, (int)blockIdx.y * kWY, (int)blockIdx.x * kWX, t, U_s);
-    __syncthreads();
+// Shared memory of a windowed draw block (128 threads).
+template <int NB>
+struct __align__(16) WinShared {
+    float G[kWMaxChunks * kWThreads];   // [chunk][thread]: chunk sums, then prefix sums
+    float F[kTabF];                     // outside-chunk sums
+    uint2 tent[kTentMax];               // tent bytes
+    int rec[NB + 1][kWThreads];         // per site: neighbour labels; g | clo << 9 | cnt << 16
+    int bins[kWMaxChunks + 1];          // hull sizes 0..32: counts, then offsets
+    uint8_t perm[kWThreads];            // sites in increasing hull size
+};
 
-    const bool valid = r < a.H && c < a.W;
-    SiteIn<NB> in{};
-    if (valid) {
-        load_site<NB, false, false>(a, a.xin, r, c, kTagPCA, t, in);
-        in.ub = U_s[lr * kWX + lc];
-    }
+// Tables into shared memory (the caller's barrier follows).
+template <int NB>
+__device__ __forceinline__ void win_setup(WinShared<NB> &sh, int T, const float *ftab, int tid)
+{
+    for (int i = tid; i < kTabF / 4; i += kWThreads)
+        reinterpret_cast<float4 *>(sh.F)[i] = __ldg(reinterpret_cast<const float4 *>(ftab) + i);
+    for (int i = tid; i < 2 * T + 8; i += kWThreads)
+        sh.tent[i] = tent_entry(T, i);
+    if (tid <= kWMaxChunks)
+        sh.bins[tid] = 0;
+}
+
+// The draw of every site of the block (thread tid: site inputs `in`, valid
+// or not).  Every thread of the block calls it (block barriers inside).
+// Returns the label (0 for an invalid site); uncertain FP32 draws are
+// re-drawn in FP64 by the warp, counted in *fp64.
+template <int NB, bool LMASK>
+__device__ __forceinline__ int win_draw(WinShared<NB> &sh, const DevModel &m, const SiteIn<NB> &in,
+                                        bool valid, int tid, unsigned long long *fp64)
+{
+    const int lane = tid & 31, wp = tid >> 5;
+    const int T = m.T;
     const float mu = -m.gam;
     const int nc = (m.L + kChunk - 1) / kChunk;
     const float gf = (float)in.g;
@@ -209,12 +203,12 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
     // (Dealing (site, chunk) tasks out over a warp with shuffles measured
     // slower: they cost more than the imbalance they remove.)
     for (int j = 0; j < NB; ++j)
-        rec_s[j][tid] = in.xni[j];
-    rec_s[NB][tid] = in.g | (clo << 9) | (cnt << 16);
-    const int rank = atomicAdd(&bins_s[cnt], 1);
+        sh.rec[j][tid] = in.xni[j];
+    sh.rec[NB][tid] = in.g | (clo << 9) | (cnt << 16);
+    const int rank = atomicAdd(&sh.bins[cnt], 1);
     __syncthreads();
     if (wp == 0) {   // exclusive offsets of the bins 0..32
-        const int b = bins_s[lane];
+        const int b = sh.bins[lane];
         int inc = b;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -223,20 +217,20 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
                 inc += v;
         }
         __syncwarp();
-        bins_s[lane] = inc - b;
+        sh.bins[lane] = inc - b;
         if (lane == 31)
-            bins_s[32] = inc;
+            sh.bins[32] = inc;
     }
     __syncthreads();
-    perm_s[bins_s[cnt] + rank] = (uint8_t)tid;
+    sh.perm[sh.bins[cnt] + rank] = (uint8_t)tid;
     __syncthreads();
     {
-        const int sid = perm_s[tid];
+        const int sid = sh.perm[tid];
         int sx[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j)
-            sx[j] = rec_s[j][sid];
-        const int pk = rec_s[NB][sid];
+            sx[j] = sh.rec[j][sid];
+        const int pk = sh.rec[NB][sid];
         const int sclo = (pk >> 9) & 127, scnt = pk >> 16;
         const float sgf = (float)(pk & 511);
         const int maxcnt = __reduce_max_sync(0xFFFFFFFFu, scnt);
@@ -245,13 +239,13 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
             if (k < scnt) {
                 const int cc = sclo + k;
                 uint32_t lo, hi;
-                chunk_tents<NB>(sx, cc, T, tent_s, lo, hi);
-                G_s[cc * kWThreads + sid] = win_chunk_sum<LMASK>(m, mu, sgf, cc, lo, hi);
+                chunk_tents<NB>(sx, cc, T, sh.tent, lo, hi);
+                sh.G[cc * kWThreads + sid] = win_chunk_sum<LMASK>(m, mu, sgf, cc, lo, hi);
             }
         }
     }
     __syncthreads();
-    float *Gcol = G_s + tid;
+    float *Gcol = sh.G + tid;
 
     // chunk prefix sums in label order (Kahan), outside chunks from the table
     float G = 0.0f, comp = 0.0f;
@@ -259,7 +253,7 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
 #pragma unroll 4
     for (int cc = 0; cc < nc; ++cc) {
         const float S = (cc >= clo && cc <= chi) ? Gcol[cc * kWThreads]
-                                                 : tab_sum<LMASK>(F_s, in.g, cc, nc);
+                                                 : tab_sum<LMASK>(sh.F, in.g, cc, nc);
         const float y = __fsub_rn(S, comp);
         const float tt = __fadd_rn(G, y);
         comp = __fsub_rn(__fsub_rn(tt, G), y);
@@ -282,11 +276,39 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
         s = cdf_select(m, site_margin(m, G, delta), [&](int cc) { return Gcol[cc * kWThreads]; },
                        nc, G, delta, in.xi, in.ub, certain, [&](int cs, float (&pp)[kChunk]) {
                            uint32_t lo, hi;
-                           chunk_tents<NB>(in.xni, cs, T, tent_s, lo, hi);
+                           chunk_tents<NB>(in.xni, cs, T, sh.tent, lo, hi);
                            win_chunk_prefix(m, mu, gf, cs, lo, hi, pp);
                        });
     }
-    s = warp_redraw_fp64<NB>(m, valid && !certain, in, s, a.fp64_draws);
+    return warp_redraw_fp64<NB>(m, valid && !certain, in, s, fp64);
+}
+
+// One lazy-PCA sweep: a.xin -> a.xout, accumulate after burn-in.  ftab: the
+// model's outside-chunk table (tc_table_floats floats, launch_tc_table).
+// Warp wp takes the block's columns 8 wp .. 8 wp + 7 over its 4 rows.
+template <int NB, bool LMASK>
+__global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a,
+                                                               const float *ftab)
+{
+    __shared__ WinShared<NB> sh;
+    __shared__ __align__(16) uint32_t U_s[kWY * kWX];
+    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
+    const int tid = wp * kWX + lane;
+    const int lr = lane >> 3, lc = 8 * wp + (lane & 7);
+    const int c = (int)blockIdx.x * kWX + lc;
+    const int r = (int)blockIdx.y * kWY + lr;
+    win_setup(sh, a.m.T, ftab, tid);
+    const uint32_t t = sweep_index(a);
+    if (wp == 0)
+        block_uniforms(a, (int)blockIdx.y * kWY, (int)blockIdx.x * kWX, t, U_s);
+    __syncthreads();
+    const bool valid = r < a.H && c < a.W;
+    SiteIn<NB> in{};
+    if (valid) {
+        load_site<NB, false, false>(a, a.xin, r, c, kTagPCA, t, in);
+        in.ub = U_s[lr * kWX + lc];
+    }
+    const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
     if (valid) {
         a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
         if (accumulate_after(a, t)) {
@@ -294,6 +316,83 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
             *p = *p + (float)s;
         }
     }
+}
+
+// Checkerboard Gibbs colour phase q in place on a.xin (Section 5.1): thread
+// (x, y) owns a cell, two columns of a row (4 neighbours, colours (r + c)
+// mod 2) or a 2 x 2 block (8 neighbours, colours (r mod 2, c mod 2)), and
+// draws its site of colour q with the windowed draw; after the last phase
+// (a.last_phase) it accumulates the whole cell.  A block covers 64 columns
+// and 4 (8) rows; its phase sites' uniforms come from 64 Philox calls.
+template <int NB, bool LMASK>
+__global__ void __launch_bounds__(kWThreads, 8) gibbs_win_kernel(const SweepArgs a, int q,
+                                                                 const float *ftab)
+{
+    __shared__ WinShared<NB> sh;
+    __shared__ __align__(16) uint32_t U_s[kWY * 2 * kWX];   // 4 site rows x 64 columns
+    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
+    const int tid = wp * kWX + lane;
+    const int cx = (int)blockIdx.x * kWX + lane, cy = (int)blockIdx.y * kWY + wp;
+    int r0, c0, r, c;
+    if (NB == 4) {
+        r0 = cy;
+        c0 = 2 * cx;
+        r = r0;
+        c = c0 + ((r + q) & 1);
+    } else {
+        r0 = 2 * cy;
+        c0 = 2 * cx;
+        r = r0 + (q >> 1);
+        c = c0 + (q & 1);
+    }
+    uint8_t *x = const_cast<uint8_t *>(a.xin);
+    win_setup(sh, a.m.T, ftab, tid);
+    const uint32_t t = sweep_index(a);
+    if (wp < 2) {   // warp w, lane l: site row (32 w + l) / 16, columns 4 ((32 w + l) % 16) ..
+        const int i = wp * 32 + lane;
+        const int ri = i >> 4;
+        const int row = NB == 4 ? (int)blockIdx.y * kWY + ri
+                                : 2 * ((int)blockIdx.y * kWY + ri) + (q >> 1);
+        uint32_t o0, o1, o2, o3;
+        philox4x32_10((uint32_t)(16 * (int)blockIdx.x + (i & 15)), (uint32_t)(row + a.row_off), t,
+                      (kTagGibbs << 24) | (a.chain & 0xFFFFFFu), (uint32_t)(a.seed & 0xFFFFFFFFull),
+                      (uint32_t)(a.seed >> 32), o0, o1, o2, o3);
+        reinterpret_cast<uint4 *>(U_s)[i] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
+    }
+    __syncthreads();
+    const bool cell = r0 < a.H && c0 < a.W;
+    const bool valid = cell && r < a.H && c < a.W;
+    SiteIn<NB> in{};
+    if (valid) {
+        load_site<NB, false, false>(a, x, r, c, kTagGibbs, t, in);
+        in.ub = U_s[wp * 2 * kWX + (c - 2 * kWX * (int)blockIdx.x)];
+    }
+    const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
+    if (valid)
+        x[(size_t)r * a.pitch + c] = (uint8_t)s;
+    if (cell && a.last_phase && accumulate_after(a, t)) {
+        const int nr = NB == 4 ? 1 : 2;
+#pragma unroll
+        for (int dr = 0; dr < nr; ++dr)
+#pragma unroll
+            for (int dc = 0; dc < 2; ++dc) {
+                const int rr = r0 + dr, cc = c0 + dc;
+                if (rr < a.H && cc < a.W)
+                    a.acc[(size_t)rr * a.W + cc] += (float)x[(size_t)rr * a.pitch + cc];
+            }
+    }
+}
+
+template <int NB, bool LMASK>
+cudaError_t launch_gibbs_win_t(const SweepArgs &a, int q, const float *ftab, cudaStream_t st)
+{
+    const dim3 block(kWX, kWY);
+    const int rows = NB == 4 ? kWY : 2 * kWY;
+    const dim3 grid((a.W + 2 * kWX - 1) / (2 * kWX), (a.H + rows - 1) / rows);
+    if (grid.y > 65535u)
+        return cudaErrorInvalidValue;
+    gibbs_win_kernel<NB, LMASK><<<grid, block, 0, st>>>(a, q, ftab);
+    return cudaGetLastError();
 }
 
 template <int NB, bool LMASK>
@@ -308,6 +407,20 @@ cudaError_t launch_win_t(const SweepArgs &a, const float *ftab, cudaStream_t st)
 }
 
 }  // namespace
+
+cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t st)
+{
+    if (!pca_win_eligible(a.m) || ftab == nullptr || q < 0 || q >= (a.m.nbhd == 8 ? 4 : 2))
+        return cudaErrorInvalidValue;
+    if (a.H <= 0 || a.W <= 0)
+        return cudaSuccess;
+    const bool lmask = (a.m.L % kChunk) != 0;
+    if (a.m.nbhd == 8)
+        return lmask ? launch_gibbs_win_t<8, true>(a, q, ftab, st)
+                     : launch_gibbs_win_t<8, false>(a, q, ftab, st);
+    return lmask ? launch_gibbs_win_t<4, true>(a, q, ftab, st)
+                 : launch_gibbs_win_t<4, false>(a, q, ftab, st);
+}
 
 bool pca_win_eligible(const DevModel &m)
 {

@@ -1,9 +1,10 @@
-"""The CUDA-core windowed sweep (PCAD_KERNEL_WINDOW: the tensor-core sweep's
+"""The CUDA-core windowed sweeps (PCAD_KERNEL_WINDOW: the tensor-core sweep's
 weights, tent sums of each site's hull of labels from a byte table, the
-other chunks from the outside table) against the FP64 oracle and the other
-kernels: free-running chains are label for label the oracle's, on ragged
-sizes, both neighbourhoods, Potts and truncated-linear priors, L not a
-multiple of 8, one row, one column and one pixel."""
+other chunks from the outside table; lazy PCA and checkerboard Gibbs colour
+phases) against the FP64 oracle and the other kernels: free-running chains
+are label for label the oracle's, on ragged sizes, both neighbourhoods,
+Potts and truncated-linear priors, L not a multiple of 8, one row, one
+column and one pixel."""
 import numpy as np
 import pytest
 
@@ -51,18 +52,24 @@ CASES = [
 
 
 @pytest.mark.parametrize("name,make,m", CASES, ids=[c[0] for c in CASES])
-def test_window_kernel_matches_oracle_and_other_kernels(pc, name, make, m):
+@pytest.mark.parametrize("sampler", [0, 1], ids=["pca", "gibbs"])
+def test_window_kernel_matches_oracle_and_other_kernels(pc, name, make, m, sampler):
     g = make()
     sweeps, burn = 14, 5
+    kinds = [WINDOW, CUDA_CORE]
+    if sampler == 0 or m.nbhd == 4:
+        kinds.append(TENSOR)
     outs = {}
-    for kind in (WINDOW, TENSOR, CUDA_CORE):
-        with pc.Chain(g, m, seed=17, chain_id=3, burn_in=burn) as ch:
+    for kind in kinds:
+        with pc.Chain(g, m, seed=17, chain_id=3, burn_in=burn, sampler=sampler) as ch:
             ch.set_kernel(kind)
             assert ch.kernel_in_use() == kind
             ch.run(9)
             ch.run(sweeps - 9)
             outs[kind] = (ch.sample(), ch.mean())
-    xo, acc, nacc, _ = oracle.run_chain(m, g, sweeps, burn, seed=17, chain=3)
+    kw = {} if sampler == 0 else {"order": oracle.ORDER_COLOUR}
+    xo, acc, nacc, _ = oracle.run_chain(m, g, sweeps, burn, seed=17, chain=3, sampler=sampler,
+                                        **kw)
     for kind in outs:
         assert np.array_equal(outs[kind][0], xo), kind
         np.testing.assert_allclose(outs[kind][1], acc / nacc, rtol=1e-6, atol=0)
@@ -87,10 +94,22 @@ def test_window_kernel_long_chain_and_model_change(pc):
 def test_window_kernel_is_validated(pc):
     g = _grey(99, 20, 30, 16, 1.0)
     for m, sampler in ((Model(L=16, pair=TL, pair_coef=0.1, pair_T=3, sigma=1.0), 0),
-                       (Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0), 1),
+                       (Model(L=256, pair=TL, pair_coef=0.05, pair_T=40, sigma=20.0), 1),
                        (Model(L=256, nbhd=8, pair=TL, pair_coef=0.05, pair_T=33, sigma=20.0), 0)):
         with pc.Chain(np.minimum(g * 16, m.L - 1).astype(np.uint8), m, seed=1,
                       sampler=sampler) as ch:
             with pytest.raises(pc.PcadError) as e:
                 ch.set_kernel(WINDOW)
             assert e.value.status == 1
+
+
+def test_auto_takes_the_windowed_gibbs_sweep_on_large_images(pc):
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    side = 1024
+    assert (side // 32) * (side // 4) >= 16 * sms
+    g = np.zeros((side, side), np.uint8)
+    for nbhd in (4, 8):
+        m = Model(L=256, nbhd=nbhd, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
+        with pc.Chain(g, m, seed=1, sampler=1) as ch:
+            assert ch.kernel_in_use() == WINDOW
