@@ -533,8 +533,10 @@ def _gibbs_8192(pc, stream, timed, noisy, m, clean, cid, steps=2):
     ch.close()
     ms_sweep = sum(ms) / (steps * SWEEPS)
     sites = noisy.size
-    name = ("pca_tcw_kernel<4,0,0,0,1> (checkerboard Gibbs on the tensor-core wavefront, 2 "
-            "colour phases per sweep)") if kind == 2 else "gibbs_cb_kernel (2 colour phases)"
+    name = {2: "pca_tcw_kernel<4,0,0,0,1> (checkerboard Gibbs on the tensor-core wavefront, 2 "
+               "colour phases per sweep)",
+            6: "gibbs_win_kernel (CUDA cores, windowed draw, one launch per colour phase, 2 "
+               "phases per sweep)"}.get(kind, "gibbs_cb_kernel (2 colour phases)")
     return {"value": sites / (ms_sweep * 1e-3), "unit": "site-updates/s",
             "ms_per_step": sum(ms) / steps, "ms_per_sweep": ms_sweep, "steps": steps,
             "psnr_db": p, "ssim": s, "kernel": name,

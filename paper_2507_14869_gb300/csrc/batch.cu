@@ -292,8 +292,16 @@ struct TcGroup {
     WaveBuf wb;
 };
 
+// Large chains the windowed sweep takes (at least kWinBigBlocks blocks of
+// 4 x 32 sites per multiprocessor) run it one launch per chain and sweep,
+// as the chain API does for such images (on GB300 it measured about 1.5x
+// the tensor-core sweep there); planes by the device sweep counter,
+// budget-aware.
+constexpr long kWinBigBlocks = 16;
+
 struct TcSet {
     std::vector<TcGroup> groups;
+    std::vector<int> win;          // slots on the windowed sweep, launched one at a time
     std::vector<int> big;          // slots launched one at a time
     unsigned int *ctr = nullptr;   // their tile counters and work counter (regrown)
     long ctr_cap = 0;
@@ -307,6 +315,10 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
     std::vector<std::vector<int>> members(ts.groups.size());
     rest.clear();
     ts.big.clear();
+    ts.win.clear();
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     long big_tiles = 0;
     for (int i : active) {
         if (!d[i].tctab) {
@@ -314,6 +326,10 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
             continue;
         }
         const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 3) / 4);
+        if (sms > 0 && tiles >= kWinBigBlocks * sms && pca_win_eligible(d[i].m)) {
+            ts.win.push_back(i);
+            continue;
+        }
         if (tiles >= kTcBigTiles) {
             ts.big.push_back(i);
             big_tiles = std::max(big_tiles, tiles);
@@ -359,6 +375,25 @@ pcad_status tc_set_issue(const TcSet &ts, const std::vector<SlotDesc> &desc,
                          const SlotDesc *slots, const uint32_t *t_arr, const uint32_t *budget_arr,
                          int n, int *grab, int *err, cudaStream_t st)
 {
+    for (int i : ts.win) {
+        const SlotDesc &d = desc[i];
+        SweepArgs a{};
+        a.g = d.g;
+        a.acc = d.acc;
+        a.fp64_draws = d.fp64_draws;
+        a.sweep_base = d.tdev;
+        a.seed = d.seed;
+        a.H = d.H;
+        a.W = d.W;
+        a.pitch = d.pitch;
+        a.chain = d.chain;
+        a.burn_in = d.burn_in;
+        a.m = d.m;
+        for (int k = 0; k < n; ++k) {
+            a.sweep_off = (uint32_t)k;
+            B_TRY(launch_pca_win(a, d.tctab, st, d.x[0], d.x[1], d.budget));
+        }
+    }
     for (int i : ts.big) {
         const SlotDesc &d = desc[i];
         SweepArgs a{};
@@ -983,7 +1018,10 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
     if (b->desc[i].tctab) {   // the tensor-core sweep's outside sums follow the model
         B_TRY(launch_tc_table(dm, const_cast<float *>(b->desc[i].tctab), b->stream));
         // a large slot's launch carries the model: capture the slice again
-        if (b->graph && std::find(b->tc.big.begin(), b->tc.big.end(), i) != b->tc.big.end()) {
+        const bool own_launch =
+            std::find(b->tc.big.begin(), b->tc.big.end(), i) != b->tc.big.end() ||
+            std::find(b->tc.win.begin(), b->tc.win.end(), i) != b->tc.win.end();
+        if (b->graph && own_launch) {
             B_TRY(cudaStreamSynchronize(b->stream));
             cudaGraphExecDestroy(b->graph);
             b->graph = nullptr;

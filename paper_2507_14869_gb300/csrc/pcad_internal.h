@@ -286,10 +286,14 @@ cudaError_t launch_tc_table(const DevModel &m, float *out, cudaStream_t s);
 
 // The CUDA-core windowed sweep (the tensor-core sweep's weights, tent sums
 // from a byte table over each site's hull of labels, outside chunks from
-// ftab = launch_tc_table's table): one sweep a.xin -> a.xout.  Models the
+// ftab = launch_tc_table's table): one sweep a.xin -> a.xout, or (x0 set)
+// from the plane of the sweep index's parity (x0 even, x1 odd) to the
+// other, skipped at or past *budget (budget optional).  Models the
 // tensor-core sweep accepts with nbhd T <= 255.
 bool pca_win_eligible(const DevModel &m);
-cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s);
+cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s,
+                           uint8_t *x0 = nullptr, uint8_t *x1 = nullptr,
+                           const uint32_t *budget = nullptr);
 // Checkerboard Gibbs colour phase q (0..nbhd/2 - 1) in place on a.xin with
 // the windowed draw; a.last_phase: accumulate the cells after it.
 cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t s);

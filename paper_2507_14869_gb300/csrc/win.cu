@@ -286,10 +286,19 @@ __device__ __forceinline__ int win_draw(WinShared<NB> &sh, const DevModel &m, co
 // One lazy-PCA sweep: a.xin -> a.xout, accumulate after burn-in.  ftab: the
 // model's outside-chunk table (tc_table_floats floats, launch_tc_table).
 // Warp wp takes the block's columns 8 wp .. 8 wp + 7 over its 4 rows.
+// Planes: a.xin -> a.xout, or (x0 != nullptr) x0 / x1 holding the states of
+// even / odd sweep indices; budget (optional): a sweep with index >= *budget
+// is skipped (a chain of a batch or of the server).
 template <int NB, bool LMASK>
 __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a,
-                                                               const float *ftab)
+                                                               const float *ftab, uint8_t *x0,
+                                                               uint8_t *x1, const uint32_t *budget)
 {
+    const uint32_t t = sweep_index(a);
+    if (budget && t >= *budget)
+        return;   // the whole launch, before any barrier
+    const uint8_t *xin = x0 ? ((t & 1u) ? x1 : x0) : a.xin;
+    uint8_t *xout = x0 ? ((t & 1u) ? x0 : x1) : a.xout;
     __shared__ WinShared<NB> sh;
     __shared__ __align__(16) uint32_t U_s[kWY * kWX];
     const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
@@ -298,19 +307,18 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
     const int c = (int)blockIdx.x * kWX + lc;
     const int r = (int)blockIdx.y * kWY + lr;
     win_setup(sh, a.m.T, ftab, tid);
-    const uint32_t t = sweep_index(a);
     if (wp == 0)
         block_uniforms(a, (int)blockIdx.y * kWY, (int)blockIdx.x * kWX, t, U_s);
     __syncthreads();
     const bool valid = r < a.H && c < a.W;
     SiteIn<NB> in{};
     if (valid) {
-        load_site<NB, false, false>(a, a.xin, r, c, kTagPCA, t, in);
+        load_site<NB, false, false>(a, xin, r, c, kTagPCA, t, in);
         in.ub = U_s[lr * kWX + lc];
     }
     const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
     if (valid) {
-        a.xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+        xout[(size_t)r * a.pitch + c] = (uint8_t)s;
         if (accumulate_after(a, t)) {
             float *p = a.acc + (size_t)r * a.W + c;
             *p = *p + (float)s;
@@ -396,13 +404,14 @@ cudaError_t launch_gibbs_win_t(const SweepArgs &a, int q, const float *ftab, cud
 }
 
 template <int NB, bool LMASK>
-cudaError_t launch_win_t(const SweepArgs &a, const float *ftab, cudaStream_t st)
+cudaError_t launch_win_t(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1,
+                         const uint32_t *budget, cudaStream_t st)
 {
     const dim3 block(kWX, kWY);
     const dim3 grid((a.W + kWX - 1) / kWX, (a.H + kWY - 1) / kWY);
     if (grid.y > 65535u)
         return cudaErrorInvalidValue;
-    pca_win_kernel<NB, LMASK><<<grid, block, 0, st>>>(a, ftab);
+    pca_win_kernel<NB, LMASK><<<grid, block, 0, st>>>(a, ftab, x0, x1, budget);
     return cudaGetLastError();
 }
 
@@ -427,16 +436,19 @@ bool pca_win_eligible(const DevModel &m)
     return pca_tc_eligible(m) && m.nbhd * m.T <= 255;
 }
 
-cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t st)
+cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t st, uint8_t *x0,
+                           uint8_t *x1, const uint32_t *budget)
 {
-    if (!pca_win_eligible(a.m) || ftab == nullptr)
+    if (!pca_win_eligible(a.m) || ftab == nullptr || (x0 == nullptr) != (x1 == nullptr))
         return cudaErrorInvalidValue;
     if (a.H <= 0 || a.W <= 0)
         return cudaSuccess;
     const bool lmask = (a.m.L % kChunk) != 0;
     if (a.m.nbhd == 8)
-        return lmask ? launch_win_t<8, true>(a, ftab, st) : launch_win_t<8, false>(a, ftab, st);
-    return lmask ? launch_win_t<4, true>(a, ftab, st) : launch_win_t<4, false>(a, ftab, st);
+        return lmask ? launch_win_t<8, true>(a, ftab, x0, x1, budget, st)
+                     : launch_win_t<8, false>(a, ftab, x0, x1, budget, st);
+    return lmask ? launch_win_t<4, true>(a, ftab, x0, x1, budget, st)
+                 : launch_win_t<4, false>(a, ftab, x0, x1, budget, st);
 }
 
 }  // namespace pcad

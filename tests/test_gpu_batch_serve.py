@@ -403,3 +403,56 @@ def test_batch_slice_lengths_are_bit_identical(pc, slice_sweeps, rows, order):
                 pc.pcad_batch_slice(b, bad)
     finally:
         pc.pcad_batch_destroy(b)
+
+
+def test_large_windowed_slots_in_batch_and_server(pc):
+    """Tensor-core eligible images of at least 16 blocks of 4 x 32 sites per
+    SM run the windowed sweep as their own per-sweep launches inside the
+    batch's and the server's slices (planes chosen by the device sweep
+    counter, budgets ending inside slices), one of them changing its
+    coefficients between runs: results equal the chains run alone."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    big4 = (_grey(40, 640, 520, 256, 20.0),
+            Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0), 41, 3, 7)
+    big8 = (_grey(41, 700, 500, 201, 18.0),
+            Model(L=201, nbhd=8, pair=TL, pair_coef=0.05, pair_T=25, sigma=18.0, inertia=1.5),
+            42, 4, 5)
+    small = (_grey(42, 40, 33, 256, 15.0),
+             Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=15.0, inertia=2.0), 43, 5, 5)
+    jobs = [big4, big8, small]
+    for g, *_ in jobs[:2]:
+        assert ((g.shape[1] + 31) // 32) * ((g.shape[0] + 3) // 4) >= 16 * sms
+    m_new = Model(L=256, pair=TL, pair_coef=0.08, pair_T=30, sigma=20.0, inertia=1.0)
+    b = pc.pcad_batch_create(jobs, autotune=False)
+    try:
+        pc.pcad_batch_run(b, 21)
+        pc.pcad_batch_set_model(b, 0, m_new)
+        pc.pcad_batch_run(b, 30)
+        pc.pcad_batch_sync(b)
+        for i, (g, m, seed, chain, burn) in enumerate(jobs):
+            with pc.Chain(g, m, seed=seed, chain_id=chain, burn_in=burn) as ch:
+                ch.run(21)
+                if i == 0:
+                    ch.set_model(m_new)
+                ch.run(30)
+                xs, ms = ch.sample(), ch.mean()
+            assert np.array_equal(pc.pcad_batch_read_sample(b, i, *g.shape), xs), i
+            assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
+    finally:
+        pc.pcad_batch_destroy(b)
+    budgets = [37, 20, 45]
+    sv = pc.pcad_server_create(8, 1 << 31)
+    try:
+        ids, shapes = [], {}
+        for (g, m, seed, chain, burn), n in zip(jobs, budgets):
+            rid = pc.pcad_server_submit(sv, g, m, seed, chain, burn, n)
+            ids.append(rid)
+            shapes[rid] = g.shape
+        res = _serve_until_done(pc, sv, list(ids), shapes, slice_sweeps=16)
+        for rid, (g, m, seed, chain, burn), n in zip(ids, jobs, budgets):
+            xs, ms = _alone(pc, g, m, seed, chain, burn, n)
+            assert np.array_equal(res[rid][0], xs)
+            assert np.array_equal(res[rid][1], ms)
+    finally:
+        pc.pcad_server_destroy(sv)
