@@ -112,12 +112,13 @@ def _args():
     p.add_argument("--kernel", default="auto",
                    choices=["auto", "cuda_core", "tensor", "wave", "small", "resident", "window"],
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
-                        "auto = the tensor-core sweep for eligible models with L >= 192, else "
-                        "the per-sweep or wavefront CUDA-core kernel; tensor = prior sums by "
-                        "tcgen05.mma")
+                        "auto = for eligible models with L >= 192 the windowed CUDA-core sweep "
+                        "on large images and the tensor-core sweep on small ones, else the "
+                        "small-label, resident, per-sweep or wavefront CUDA-core kernel; "
+                        "tensor = prior sums by tcgen05.mma; window = the windowed sweep")
     p.add_argument("--images", type=int, default=128, help="batch: number of images")
     p.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
-    p.add_argument("--rates", default="10,50,200",
+    p.add_argument("--rates", default="10,25,50,200",
                    help="serve: comma-separated arrival rates (req/s)")
     p.add_argument("--aging", type=float, default=0.2,
                    help="serve: priority seconds a waiting request gains per second "
