@@ -63,7 +63,7 @@ NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_
                "at 4096^2 L=256 (profiles/pca_tc_l256_4096sq.md), scaled by sites to 8192^2")
 NCU_DIRECT_BYTES_PER_SITE = None
 NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at 8192^2 L=16"
-NCU_WIN_BYTES_PER_SITE = (404017152 + 289024512) / (8192 * 8192)
+NCU_WIN_BYTES_PER_SITE = (402903040 + 286483712) / (8192 * 8192)
 NCU_WIN_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_win_kernel launch at "
                 "8192^2 L=256 (profiles/pca_win_l256_8192sq.md)")
 NCU_SMALL_BYTES_PER_SITE = (407.3e6 + 282.3e6) / (8192 * 8192)
