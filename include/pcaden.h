@@ -205,10 +205,10 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO the
  * resident kernel
  * is taken for the two-label images it accepts without energy tracking; the
- * windowed kernel for chains of models the tensor-core kernel takes (any
- * neighbourhood for Gibbs) with L >= 192 on images of at least 16 blocks of
- * 4 x 32 sites per multiprocessor, without energy tracking; the tensor-core
- * kernel for the
+ * windowed kernel for chains of models the tensor-core kernel takes with
+ * nbhd T <= 255 (any neighbourhood for Gibbs, 64 <= L <= 256) on images of
+ * at least 16 blocks of 4 x 32 sites per multiprocessor, without energy
+ * tracking; the tensor-core kernel for the
  * other eligible models with L >= 192 and no energy tracking;
  * PCAD_KERNEL_SMALL for the models it accepts; otherwise
  * the wavefront kernel for L >= 16 when the

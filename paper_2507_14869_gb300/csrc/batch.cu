@@ -81,15 +81,16 @@ struct SlotMem {
     size_t x0, x1, g, acc, ta, pr, tab, end;   // tab == end: no tensor-core table
 };
 
-// Whether a model runs on the batched tensor-core sweep (the automatic
-// kernel rule of the chains).
+// Whether a model's slot keeps an outside-chunk table: the models of the
+// batched tensor-core sweep (the automatic kernel rule of the chains) and
+// those the windowed sweep takes when their image is large.
 bool model_tc(const pcad_model &m)
 {
     double ta64[511];
     std::vector<double> pr64;
     DevModel dm{};
     model_tables(m, ta64, pr64, dm);
-    return m.sampler == PCAD_SAMPLER_PCA && pca_tc_auto(dm);
+    return m.sampler == PCAD_SAMPLER_PCA && (pca_tc_auto(dm) || pca_win_eligible(dm));
 }
 
 SlotMem slot_layout(int H, int W, int pitch, size_t pr_bytes, size_t tab_bytes, size_t base)
@@ -158,7 +159,7 @@ pcad_status init_slot(const pcad_job &j, char *base, const SlotMem &sm, int pitc
     d.active = 1;
     d.m = dm;
     d.tctab = nullptr;
-    if (sm.end > sm.tab && pca_tc_auto(dm)) {
+    if (sm.end > sm.tab && (pca_tc_auto(dm) || pca_win_eligible(dm))) {
         d.tctab = (const float *)(base + sm.tab);
         B_TRY(launch_tc_table(dm, (float *)(base + sm.tab), s));
     }
@@ -328,6 +329,10 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
         const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 3) / 4);
         if (sms > 0 && tiles >= kWinBigBlocks * sms && pca_win_eligible(d[i].m)) {
             ts.win.push_back(i);
+            continue;
+        }
+        if (!pca_tc_auto(d[i].m)) {   // a table for the windowed sweep only
+            rest.push_back(i);
             continue;
         }
         if (tiles >= kTcBigTiles) {

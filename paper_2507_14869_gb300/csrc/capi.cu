@@ -288,19 +288,21 @@ SweepArgs make_args(const pcad_chain *ch)
 }
 
 // Chains AUTO gives the CUDA-core windowed sweep (lazy PCA, or checkerboard
-// Gibbs colour phases) instead of the tensor-core one: the same models (and
-// the 8-neighbourhood Gibbs the tensor-core sweep lacks), without energy
-// tracking, on images of
-// at least 16 blocks of 4 x 32 sites per multiprocessor.  Measured on GB300
-// at L = 256 (site-updates/s): 8192^2 1.51e10 against 1.07e10, 2048^2
-// 1.61e10 against 1.14e10, 1024^2 1.44e10 against 1.11e10; level at 512^2
-// (1.08e10 each), where the per-sweep launches' last wave leaves SMs idle
-// and the tensor-core wavefront does not.
+// Gibbs colour phases): the models the tensor-core sweep accepts with
+// nbhd T <= 255 (64 <= L <= 256), either neighbourhood, without energy
+// tracking, on images of at least 16 blocks of 4 x 32 sites per
+// multiprocessor.  Measured on GB300 (site-updates/s) at L = 256: 8192^2
+// 1.63e10 against 1.07e10 for the tensor-core sweep, 2048^2 1.70e10 against
+// 1.14e10, 1.51e10 against 1.11e10 at 1024^2, level at 512^2 (1.10e10 and
+// 1.08e10, the per-sweep launches' last wave leaving SMs idle); at 2048^2
+// and L = 64, 96 (T = 8), 128, 160: 2.67e10, 3.08e10, 2.24e10, 1.96e10
+// against 2.25e10, 1.49e10, 1.43e10, 0.80e10 for the per-sweep CUDA-core
+// kernel.
 bool win_auto(const pcad_chain *ch)
 {
     if (ch->tb_k > 0 || ch->track.trace || ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
         return false;
-    if (!pca_tc_auto(ch->dm) || !pca_win_eligible(ch->dm))
+    if (!pca_win_eligible(ch->dm))
         return false;
     const long long blocks = (long long)((ch->W + 31) / 32) * ((ch->H + 3) / 4);
     return blocks >= 16LL * ch->sms;
@@ -369,7 +371,7 @@ bool uses_wave(const pcad_chain *ch)
         return false;
     if (ch->kernel == PCAD_KERNEL_WAVE)
         return true;
-    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0)
+    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0 || win_auto(ch))
         return false;
     const long slots = 10L * ch->sms;
     return 2L * ch->wave_tiles >= slots && ch->wave_tiles <= 3L * slots;
