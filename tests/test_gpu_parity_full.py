@@ -7,13 +7,15 @@ oracle.
   oracle's chain.
 * Teacher-forced, every site, at least 4.2e6 draws per case (512^2 L = 256
   PCA and checkerboard Gibbs on the tensor-core kernel, 1024^2 L = 16 PCA on
-  the CUDA cores): the mismatch count (zero expected), the fraction of draws
+  the small-label kernel, 1024^2 L = 256 PCA and Gibbs on the windowed CUDA-
+  core kernels): the mismatch count (zero expected), the fraction of draws
   the oracle flags as lying within 1e-6 of an FP64 CDF boundary, and the
   FP64 re-draws are printed.  With no mismatch in n >= 4.2e6 draws the
   one-sided 95 % bound on the mismatch rate is 3/n < 1e-6.
 * The whole 512^2 workload -- 2000 sweeps, burn-in 500 -- against the
   oracle's OpenMP chain: identical labels, posterior mean and PSNR.
-* 8192^2, L = 256 and L = 16, 32 sweeps in one launch (one captured graph),
+* 8192^2, L = 256 and L = 16, 32 sweeps in one captured graph (the headline
+  L = 256 chain on the windowed sweep),
   checked at sampled sites through the sweeps' light cone: the oracle
   recomputes, sweep by sweep, only the sites within 31 - t of a sample, so
   the comparison after 32 sweeps is exact without running the whole image.
@@ -83,10 +85,18 @@ def _l16_1024():
     return noisy, Model(L=16, pair=1, pair_coef=0.05, pair_T=30, sigma=1.0, inertia=2.0)
 
 
+def _l256_1024():
+    """The roofline scene and prior at 1024^2: AUTO runs the windowed sweep."""
+    _, noisy, m = large_image(seed=3, side=1024, L=256)
+    return noisy, m
+
+
 MANY = {
     "pca_512_L256": (lambda: greyscale_512()[1:], 0, 16),
     "gibbs_512_L256": (lambda: greyscale_512()[1:], 1, 16),
     "pca_1024_L16": (_l16_1024, 0, 4),
+    "pca_1024_L256_windowed": (_l256_1024, 0, 4),
+    "gibbs_1024_L256_windowed": (_l256_1024, 1, 4),
 }
 
 
@@ -95,6 +105,8 @@ def test_teacher_forced_many_draws(pc, name):
     make, sampler, sweeps = MANY[name]
     g, m = make()
     kind, mism, unflagged, near, total, fp64 = _teacher_forced(pc, m, g, sweeps, sampler, 2, 0)
+    if name.endswith("windowed"):
+        assert kind == pc.PCAD_KERNEL_WINDOW
     print(f"\n[parity] {name}: kernel {kind}, {total} draws, {mism} mismatches, "
           f"{near} near-boundary ({near / total:.3e}), {fp64} FP64 re-draws "
           f"({fp64 / total:.3e}); 95% bound on the mismatch rate {3.0 / total:.2e}")
