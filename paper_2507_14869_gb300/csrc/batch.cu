@@ -327,7 +327,8 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
             continue;
         }
         const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 3) / 4);
-        if (sms > 0 && tiles >= kWinBigBlocks * sms && pca_win_eligible(d[i].m)) {
+        if (sms > 0 && tiles >= kWinBigBlocks * sms && (d[i].H + 3) / 4 <= 65535 &&
+            pca_win_eligible(d[i].m)) {
             ts.win.push_back(i);
             continue;
         }

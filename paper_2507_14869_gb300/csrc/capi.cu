@@ -304,6 +304,10 @@ bool win_auto(const pcad_chain *ch)
         return false;
     if (!pca_win_eligible(ch->dm))
         return false;
+    // launch grids: (W / 32) x (H / 4) blocks (Gibbs: H / 8 for 8
+    // neighbours); the second dimension is at most 65535
+    if ((ch->H + 3) / 4 > 65535)
+        return false;
     const long long blocks = (long long)((ch->W + 31) / 32) * ((ch->H + 3) / 4);
     return blocks >= 16LL * ch->sms;
 }
