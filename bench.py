@@ -71,7 +71,7 @@ NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_small_kern
                   "8192^2 L=16 (profiles/pca_small_l16_4096sq.md)")
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5,
-                "window": 6}
+                "window": 6, "window_wave": 7}
 KERNEL_NAMES = {
     1: "pca_direct_kernel (CUDA cores, one launch per sweep)",
     2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
@@ -81,6 +81,7 @@ KERNEL_NAMES = {
     5: "resident_kernel (two labels, whole run in one single-CTA launch, state in shared "
        "memory, exact per-configuration thresholds)",
     6: "pca_win_kernel (CUDA cores, hull chunks from a tent-byte table, one launch per sweep)",
+    7: "pca_winw_kernel (the windowed draw as a wavefront, one launch per 32 sweeps)",
 }
 
 
@@ -110,7 +111,8 @@ def _args():
                         "images and the q grid; cpu: the FP64 oracle on the host cores "
                         "(single-threaded Gibbs and PCA, OpenMP PCA) beside the GPU chain")
     p.add_argument("--kernel", default="auto",
-                   choices=["auto", "cuda_core", "tensor", "wave", "small", "resident", "window"],
+                   choices=["auto", "cuda_core", "tensor", "wave", "small", "resident", "window",
+                            "window_wave"],
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
                         "auto = for eligible models with L >= 192 the windowed CUDA-core sweep "
                         "on large images and the tensor-core sweep on small ones, else the "
@@ -283,7 +285,7 @@ def _launches_per_run(kind, sweeps, sampler=0):
     if kind == 5:
         return 2                       # the run's launch and the counter advance
     blocks, rest = divmod(sweeps, 32)
-    if kind in (2, 3):
+    if kind in (2, 3, 7):
         return 2 * blocks + (2 if rest else 0)
     per = 2 if sampler else 1
     return blocks * (32 * per + 1) + ((rest * per + 1) if rest else 0)
@@ -363,7 +365,7 @@ def run_ours(a):
     last_psnr, _ = pca.metrics(clean, 1)
     x_head = pca.sample()
     pca.close()
-    spl = 32 if pca_kind in (2, 3) else 1          # sweeps per launch
+    spl = 32 if pca_kind in (2, 3, 7) else 1       # sweeps per launch
     per_site = {2: NCU_TC_BYTES_PER_SITE, 1: NCU_DIRECT_BYTES_PER_SITE,
                 6: NCU_WIN_BYTES_PER_SITE}.get(pca_kind)
     traffic = per_site * sites * spl if per_site else None

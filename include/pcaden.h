@@ -154,10 +154,10 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * in place, as a wavefront of phases; Section 5.1); PCAD_EINVAL for an
  * unknown kind or PCAD_KERNEL_TENSOR on another model.  PCAD_KERNEL_AUTO
  * (the default) takes it for L >= 192 without energy tracking (where it
- * measured faster on GB300), except chains on images of at least
- * 16 blocks of 4 x 32 sites per multiprocessor, which take
- * PCAD_KERNEL_WINDOW (below); else the per-sweep or the wavefront CUDA-core
- * kernel (see pcad_chain_kernel_in_use).  PCAD_KERNEL_WAVE runs the
+ * measured faster on GB300), except on images of at least 8 blocks of
+ * 4 x 32 sites per multiprocessor, which take the windowed kernels (below;
+ * see pcad_chain_kernel_in_use); else the per-sweep or the wavefront
+ * CUDA-core kernel.  PCAD_KERNEL_WAVE runs the
  * CUDA-core draw as one persistent launch per block of sweeps, a tile of
  * 4 x 32 sites starting sweep k as soon as its 3 x 3 neighbouring tiles
  * finished sweep k - 1 (no sweep-wide barrier, so one sweep's tail
@@ -187,7 +187,10 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * its neighbours' tents reach, their tent sums read from a table of 8 tents
  * per 8-byte shared-memory entry, the other chunks' sums from a table of the
  * observation, the sites of a block sorted by the number of such chunks so
- * that a warp's lanes do similar work; same labels. */
+ * that a warp's lanes do similar work; same labels.  PCAD_KERNEL_WINDOW_WAVE
+ * (PCA sampler, the same models) runs the windowed draw as one persistent
+ * wavefront launch per block of sweeps, as PCAD_KERNEL_WAVE does the
+ * CUDA-core draw (energy tracking: one sweep per launch); same labels. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
@@ -195,7 +198,8 @@ typedef enum {
     PCAD_KERNEL_WAVE = 3,
     PCAD_KERNEL_SMALL = 4,
     PCAD_KERNEL_RESIDENT = 5,
-    PCAD_KERNEL_WINDOW = 6
+    PCAD_KERNEL_WINDOW = 6,
+    PCAD_KERNEL_WINDOW_WAVE = 7
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 
@@ -205,10 +209,11 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO the
  * resident kernel
  * is taken for the two-label images it accepts without energy tracking; the
- * windowed kernel for chains of models the tensor-core kernel takes with
- * nbhd T <= 255 (any neighbourhood for Gibbs, 64 <= L <= 256) on images of
- * at least 16 blocks of 4 x 32 sites per multiprocessor, without energy
- * tracking; the tensor-core kernel for the
+ * windowed kernels for chains of models the tensor-core kernel takes with
+ * nbhd T <= 255 (64 <= L <= 256, any neighbourhood for Gibbs) without
+ * energy tracking, by image size in blocks of 4 x 32 sites per
+ * multiprocessor: lazy PCA PCAD_KERNEL_WINDOW from 100, PCAD_KERNEL_WINDOW_WAVE
+ * from 8, Gibbs PCAD_KERNEL_WINDOW from 16; the tensor-core kernel for the
  * other eligible models with L >= 192 and no energy tracking;
  * PCAD_KERNEL_SMALL for the models it accepts; otherwise
  * the wavefront kernel for L >= 16 when the

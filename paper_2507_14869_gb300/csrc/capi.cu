@@ -287,29 +287,40 @@ SweepArgs make_args(const pcad_chain *ch)
     return a;
 }
 
-// Chains AUTO gives the CUDA-core windowed sweep (lazy PCA, or checkerboard
-// Gibbs colour phases): the models the tensor-core sweep accepts with
-// nbhd T <= 255 (64 <= L <= 256), either neighbourhood, without energy
-// tracking, on images of at least 16 blocks of 4 x 32 sites per
-// multiprocessor.  Measured on GB300 (site-updates/s) at L = 256: 8192^2
-// 1.63e10 against 1.07e10 for the tensor-core sweep, 2048^2 1.70e10 against
-// 1.14e10, 1.51e10 against 1.11e10 at 1024^2, level at 512^2 (1.10e10 and
-// 1.08e10, the per-sweep launches' last wave leaving SMs idle); at 2048^2
-// and L = 64, 96 (T = 8), 128, 160: 2.67e10, 3.08e10, 2.24e10, 1.96e10
-// against 2.25e10, 1.49e10, 1.43e10, 0.80e10 for the per-sweep CUDA-core
-// kernel.
-bool win_auto(const pcad_chain *ch)
+// The windowed sweeps AUTO takes (0: none, 1: one launch per sweep or
+// Gibbs colour phase, 2: the lazy-PCA wavefront), for the models the
+// tensor-core sweep accepts with nbhd T <= 255 (64 <= L <= 256), either
+// neighbourhood, without energy tracking, by image size in blocks of 4 x 32
+// sites per multiprocessor.  Lazy PCA: per-sweep launches from 100 blocks per
+// SM, the wavefront from 8.  Gibbs: per-phase launches from 16.  Measured on
+// GB300 at L = 256 (site-updates/s; per-sweep / wavefront / tensor-core):
+// 8192^2 1.63e10 / - / 1.07e10; 2048^2 1.70e10 / 1.63e10 / 1.14e10; 1024^2
+// 1.51e10 / 1.58e10 / 1.11e10; 768^2 1.38e10 / 1.54e10 / 1.10e10; 512^2
+// 1.11e10 / 1.45e10 / 1.08e10; 256^2 0.54e10 / 0.59e10 / 0.63e10.  At 2048^2
+// and L = 64, 96 (T = 8), 128, 160 the per-sweep windowed sweep ran 2.67e10,
+// 3.08e10, 2.24e10, 1.96e10 against 2.25e10, 1.49e10, 1.43e10, 0.80e10 for
+// the per-sweep CUDA-core kernel.
+int win_auto_mode(const pcad_chain *ch)
 {
     if (ch->tb_k > 0 || ch->track.trace || ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
-        return false;
+        return 0;
     if (!pca_win_eligible(ch->dm))
-        return false;
+        return 0;
     // launch grids: (W / 32) x (H / 4) blocks (Gibbs: H / 8 for 8
     // neighbours); the second dimension is at most 65535
     if ((ch->H + 3) / 4 > 65535)
-        return false;
+        return 0;
     const long long blocks = (long long)((ch->W + 31) / 32) * ((ch->H + 3) / 4);
-    return blocks >= 16LL * ch->sms;
+    if (ch->model.sampler != PCAD_SAMPLER_PCA)
+        return blocks >= 16LL * ch->sms ? 1 : 0;
+    if (blocks >= 100LL * ch->sms)
+        return 1;
+    return blocks >= 8LL * ch->sms ? 2 : 0;
+}
+
+bool win_auto(const pcad_chain *ch)
+{
+    return win_auto_mode(ch) == 1;
 }
 
 // Unblocked PCA sweeps, and 4-neighbourhood checkerboard Gibbs sweeps, on the
@@ -325,7 +336,7 @@ bool uses_tc(const pcad_chain *ch)
     if (ch->kernel == PCAD_KERNEL_TENSOR)
         return true;
     return ch->kernel == PCAD_KERNEL_AUTO && pca_tc_auto(ch->dm) && !ch->track.trace &&
-           !win_auto(ch);
+           win_auto_mode(ch) == 0;
 }
 
 // Whole runs of sweeps of small two-label images in one single-CTA launch
@@ -346,7 +357,21 @@ bool uses_win(const pcad_chain *ch)
 {
     if (win_auto(ch))
         return true;
-    return ch->tb_k == 0 && ch->kernel == PCAD_KERNEL_WINDOW && pca_win_eligible(ch->dm);
+    return ch->tb_k == 0 &&
+           (ch->kernel == PCAD_KERNEL_WINDOW || ch->kernel == PCAD_KERNEL_WINDOW_WAVE) &&
+           pca_win_eligible(ch->dm);
+}
+
+// Lazy-PCA sweeps of the windowed kernel as one wavefront launch per block
+// of sweeps: on request, without energy tracking (which needs every sweep's
+// state: then one windowed launch per sweep), or with AUTO where
+// win_auto_mode takes it.
+bool uses_winw(const pcad_chain *ch)
+{
+    if (win_auto_mode(ch) == 2)
+        return true;
+    return ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k == 0 && !ch->track.trace &&
+           ch->kernel == PCAD_KERNEL_WINDOW_WAVE && pca_win_eligible(ch->dm);
 }
 
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
@@ -375,7 +400,8 @@ bool uses_wave(const pcad_chain *ch)
         return false;
     if (ch->kernel == PCAD_KERNEL_WAVE)
         return true;
-    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0 || win_auto(ch))
+    if (ch->kernel != PCAD_KERNEL_AUTO || ch->model.L < 16 || ch->sms <= 0 ||
+        win_auto_mode(ch) != 0)
         return false;
     const long slots = 10L * ch->sms;
     return 2L * ch->wave_tiles >= slots && ch->wave_tiles <= 3L * slots;
@@ -416,6 +442,16 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
                 CUDA_TRY(launch_energy(ch->x[cur], ch->g, ch->H, ch->W, ch->pitch, ch->ecoef,
                                        ch->esums, nullptr, ch->track, ch->tdev, a.sweep_off, st));
         }
+        return PCAD_OK;
+    }
+    if (uses_winw(ch) && n > 0) {
+        a.sweep_off = (uint32_t)off0;
+        CUDA_TRY(cudaMemsetAsync(ch->wave, 0, (size_t)(ch->wave_tiles + 1) * sizeof(unsigned int),
+                                 st));
+        CUDA_TRY(launch_pca_winw(a, ch->ftab, ch->x[cur], ch->x[cur ^ 1], n, ch->wave,
+                                 ch->wave + ch->wave_tiles, ch->err, st));
+        if (n & 1)
+            cur ^= 1;
         return PCAD_OK;
     }
     if (uses_wave(ch) && n > 0) {
@@ -754,7 +790,7 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     CUDA_TRY(cudaStreamSynchronize(ch->stream));
-    if (ch->tb_k > 0 || uses_tc(ch) || uses_wave(ch)) {
+    if (ch->tb_k > 0 || uses_tc(ch) || uses_wave(ch) || uses_winw(ch)) {
         int e = 0;
         CUDA_TRY(cudaMemcpy(&e, ch->err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e == 2)
@@ -850,6 +886,8 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
         *kind = -ch->tb_k;
     else if (uses_tc(ch))
         *kind = PCAD_KERNEL_TENSOR;
+    else if (uses_winw(ch))
+        *kind = PCAD_KERNEL_WINDOW_WAVE;
     else if (uses_wave(ch))
         *kind = PCAD_KERNEL_WAVE;
     else if (uses_small(ch))
@@ -970,9 +1008,14 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         return fail(PCAD_EINVAL, "chain is NULL");
     if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE &&
         kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE && kind != PCAD_KERNEL_SMALL &&
-        kind != PCAD_KERNEL_RESIDENT && kind != PCAD_KERNEL_WINDOW)
+        kind != PCAD_KERNEL_RESIDENT && kind != PCAD_KERNEL_WINDOW &&
+        kind != PCAD_KERNEL_WINDOW_WAVE)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
-                                 "_WAVE, _SMALL, _RESIDENT or _WINDOW");
+                                 "_WAVE, _SMALL, _RESIDENT, _WINDOW or _WINDOW_WAVE");
+    if (kind == PCAD_KERNEL_WINDOW_WAVE &&
+        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_win_eligible(ch->dm)))
+        return fail(PCAD_EINVAL, "the windowed wavefront sweep needs the PCA sampler, "
+                                 "64 <= L <= 256, T <= 33, nbhd T <= 255 and the L0 price");
     if (kind == PCAD_KERNEL_WINDOW && !pca_win_eligible(ch->dm))
         return fail(PCAD_EINVAL, "the windowed sweep needs 64 <= L <= 256, T <= 33, "
                                  "nbhd T <= 255 and the L0 inertia price");

@@ -294,6 +294,13 @@ bool pca_win_eligible(const DevModel &m);
 cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s,
                            uint8_t *x0 = nullptr, uint8_t *x1 = nullptr,
                            const uint32_t *budget = nullptr);
+// The windowed sweep as one persistent wavefront launch of nsweeps sweeps
+// (planes x0 for even, x1 for odd sweeps of the launch): tiles of 4 x 32
+// sites, counters done[] (ceil(H / 4) * ceil(W / 32) zeroed entries), grab
+// zeroed, *err set when a bounded dependency wait gave up.
+cudaError_t launch_pca_winw(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1,
+                            int nsweeps, unsigned int *done, unsigned int *grab, int *err,
+                            cudaStream_t s);
 // Checkerboard Gibbs colour phase q (0..nbhd/2 - 1) in place on a.xin with
 // the windowed draw; a.last_phase: accumulate the cells after it.
 cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t s);

@@ -326,6 +326,92 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
     }
 }
 
+// Wavefront form for images of few tiles: the nsweeps sweeps of a block in
+// one persistent launch.  Items (sweep k, tile j) of 4 x 32 sites are taken
+// in increasing order from an atomic counter; item (k, j) waits until the
+// 3 x 3 tiles around j have finished sweep k - 1 (done[] counts finished
+// sweeps per tile, observed with acquire loads, each wait bounded; a wait
+// that runs out sets *err and no block takes a further item).  Every item an
+// item depends on has a smaller index and was taken by a resident block (the
+// grid is the resident capacity), so the waits end.  Labels and sums written
+// by other blocks in the launch are read through L2.  Plane of sweep k: x0
+// for even k, x1 for odd.
+template <int NB, bool LMASK>
+__global__ void __launch_bounds__(kWThreads, 8)
+    pca_winw_kernel(const SweepArgs a, const float *ftab, uint8_t *x0, uint8_t *x1, int nsweeps,
+                    int tiles_x, int tiles_y, unsigned int *done, unsigned int *grab, int *err)
+{
+    __shared__ WinShared<NB> sh;
+    __shared__ __align__(16) uint32_t U_s[kWY * kWX];
+    __shared__ unsigned int s_next;
+    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
+    const int tid = wp * kWX + lane;
+    const int lr = lane >> 3, lc = 8 * wp + (lane & 7);
+    const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
+    const unsigned int total = ntiles * (unsigned int)nsweeps;
+    const uint32_t t0 = sweep_index(a);
+    const long long limit = wait_limit(a.wait_ns);
+    win_setup(sh, a.m.T, ftab, tid);
+    if (tid == 0)
+        s_next = atomicAdd(grab, 1u);
+    __syncthreads();
+    unsigned int item = s_next;
+    while (item < total) {
+        const int k = (int)(item / ntiles);
+        const int j = (int)(item - (unsigned int)k * ntiles);
+        const int ty = j / tiles_x;
+        const int tx = j - ty * tiles_x;
+        const uint32_t t = t0 + (uint32_t)k;
+        __syncthreads();   // s_next read; the previous item's draw is complete
+        if (tid <= kWMaxChunks)
+            sh.bins[tid] = 0;
+        if (wp == 0) {
+            // lane 31 takes the following item (none once a wait of the
+            // launch gave up); lanes 0-8 wait for the 3 x 3 tiles around j
+            if (lane == 31)
+                s_next = ld_flag(err) ? total : atomicAdd(grab, 1u);
+            bool ok = true;
+            if (k > 0 && lane < 9) {
+                const int yy = ty + lane / 3 - 1;
+                const int xx = tx + lane % 3 - 1;
+                if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
+                    const unsigned int *d = done + (size_t)yy * tiles_x + xx;
+                    ok = wait_ge(d, (unsigned int)k, ld_acquire_u32(d), err, limit);
+                }
+            }
+            if (!ok)
+                atomicExch(err, 1);
+            __syncwarp();
+        } else if (wp == 1) {
+            block_uniforms(a, ty * kWY, tx * kWX, t, U_s);
+        }
+        __syncthreads();
+        const uint8_t *xin = (k & 1) ? x1 : x0;
+        uint8_t *xout = (k & 1) ? x0 : x1;
+        const int r = ty * kWY + lr, c = tx * kWX + lc;
+        const bool valid = r < a.H && c < a.W;
+        SiteIn<NB> in{};
+        if (valid) {
+            load_site<NB, true, false>(a, xin, r, c, kTagPCA, t, in);
+            in.ub = U_s[lr * kWX + lc];
+        }
+        const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
+        if (valid) {
+            xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+            if (accumulate_after(a, t)) {
+                float *p = a.acc + (size_t)r * a.W + c;
+                *p = __ldcg(p) + (float)s;
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && j != a.stall_tile - 1) {
+            __threadfence();   // the tile's labels and sums before its counter
+            atomicExch(done + j, (unsigned int)(k + 1));
+        }
+        item = s_next;
+    }
+}
+
 // Checkerboard Gibbs colour phase q in place on a.xin (Section 5.1): thread
 // (x, y) owns a cell, two columns of a row (4 neighbours, colours (r + c)
 // mod 2) or a 2 x 2 block (8 neighbours, colours (r mod 2, c mod 2)), and
@@ -415,7 +501,61 @@ cudaError_t launch_win_t(const SweepArgs &a, const float *ftab, uint8_t *x0, uin
     return cudaGetLastError();
 }
 
+template <int NB, bool LMASK>
+cudaError_t launch_winw_t(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1, int n,
+                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+{
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pca_winw_kernel<NB, LMASK>,
+                                                          kWThreads, 0);
+        if (e != cudaSuccess)
+            return e;
+        per_sm[dev] = nb > 0 ? nb : 1;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int tiles_x = (a.W + kWX - 1) / kWX;
+    const int tiles_y = (a.H + kWY - 1) / kWY;
+    const long long items = (long long)tiles_x * tiles_y * n;
+    if (items <= 0)
+        return cudaSuccess;
+    if (items >= (1ll << 32))
+        return cudaErrorInvalidValue;
+    // at most the resident capacity: every block that takes an item runs
+    const long long cap = (long long)per_sm[dev] * sms;
+    const int grid = (int)(items < cap ? items : cap);
+    pca_winw_kernel<NB, LMASK><<<grid, dim3(kWX, kWY), 0, st>>>(a, ftab, x0, x1, n, tiles_x,
+                                                                tiles_y, done, grab, err);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_pca_winw(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1,
+                            int nsweeps, unsigned int *done, unsigned int *grab, int *err,
+                            cudaStream_t st)
+{
+    if (!pca_win_eligible(a.m) || ftab == nullptr || nsweeps < 0)
+        return cudaErrorInvalidValue;
+    if (a.H <= 0 || a.W <= 0 || nsweeps == 0)
+        return cudaSuccess;
+    const bool lmask = (a.m.L % kChunk) != 0;
+    if (a.m.nbhd == 8)
+        return lmask ? launch_winw_t<8, true>(a, ftab, x0, x1, nsweeps, done, grab, err, st)
+                     : launch_winw_t<8, false>(a, ftab, x0, x1, nsweeps, done, grab, err, st);
+    return lmask ? launch_winw_t<4, true>(a, ftab, x0, x1, nsweeps, done, grab, err, st)
+                 : launch_winw_t<4, false>(a, ftab, x0, x1, nsweeps, done, grab, err, st);
+}
 
 cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t st)
 {

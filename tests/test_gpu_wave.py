@@ -103,14 +103,17 @@ def test_kernel_in_use_auto_rule(pc):
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     slots = 10 * sms
     m256 = Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0)
-    # L >= 192 and eligible for the tensor-core sweep: that one, or the
-    # CUDA-core windowed sweep from 16 blocks of 4 x 32 sites per SM on
+    # L >= 192 and eligible for the tensor-core sweep: that one on small
+    # images, the windowed wavefront from 8 blocks of 4 x 32 sites per SM,
+    # the per-sweep windowed sweep from 100
     for side in (128, 512, 2048):
         g = np.zeros((side, side), np.uint8)
-        big = (side // 32) * (side // 4) >= 16 * sms
+        blocks = (side // 32) * (side // 4)
+        big = blocks >= 8 * sms
+        expect = (pc.PCAD_KERNEL_WINDOW if blocks >= 100 * sms else pc.PCAD_KERNEL_WINDOW_WAVE
+                  if big else pc.PCAD_KERNEL_TENSOR)
         with pc.Chain(g, m256, seed=1) as ch:
-            assert ch.kernel_in_use() == (pc.PCAD_KERNEL_WINDOW if big
-                                          else pc.PCAD_KERNEL_TENSOR), side
+            assert ch.kernel_in_use() == expect, side
             if big:
                 ch.track_energy(4)   # every sweep's state: not the tensor-core wavefront
                 assert ch.kernel_in_use() == pc.PCAD_KERNEL_CUDA_CORE
@@ -123,8 +126,10 @@ def test_kernel_in_use_auto_rule(pc):
             else pc.PCAD_KERNEL_CUDA_CORE
         g = np.zeros((side, side), np.uint8)
         for mm in (m128, wide):
-            # T <= 33 on a large image: the windowed sweep (64 <= L <= 256)
-            e = pc.PCAD_KERNEL_WINDOW if mm is m128 and tiles >= 16 * sms else expect
+            # T <= 33 on a large image: the windowed sweeps (64 <= L <= 256)
+            e = expect
+            if mm is m128 and tiles >= 8 * sms:
+                e = pc.PCAD_KERNEL_WINDOW if tiles >= 100 * sms else pc.PCAD_KERNEL_WINDOW_WAVE
             with pc.Chain(g, mm, seed=1) as ch:
                 assert ch.kernel_in_use() == e, (side, mm.L, mm.pair_T)
     g = np.zeros((512, 512), np.uint8)

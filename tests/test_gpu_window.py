@@ -113,3 +113,25 @@ def test_auto_takes_the_windowed_gibbs_sweep_on_large_images(pc):
         m = Model(L=256, nbhd=nbhd, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
         with pc.Chain(g, m, seed=1, sampler=1) as ch:
             assert ch.kernel_in_use() == WINDOW
+
+
+@pytest.mark.parametrize("name,make,m", CASES[:6], ids=[c[0] for c in CASES[:6]])
+def test_window_wavefront_matches_per_sweep_and_oracle(pc, name, make, m):
+    """PCAD_KERNEL_WINDOW_WAVE: the windowed draw as one persistent wavefront
+    launch per block of sweeps (a captured 32-sweep block, then odd and
+    single sweeps): the per-sweep windowed kernel's labels, means and FP64
+    re-draw counts, and the oracle's labels."""
+    g = make()
+    outs = {}
+    for kind in (pc.PCAD_KERNEL_WINDOW_WAVE, WINDOW):
+        with pc.Chain(g, m, seed=11, chain_id=2, burn_in=4) as ch:
+            ch.set_kernel(kind)
+            assert ch.kernel_in_use() == kind
+            for n in (32, 3, 1):
+                ch.run(n)
+            outs[kind] = (ch.sample(), ch.mean(), ch.fp64_draws())
+            ch.sync()
+    a, b = outs[pc.PCAD_KERNEL_WINDOW_WAVE], outs[WINDOW]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
+    xo, _, _, _ = oracle.run_chain(m, g, 36, 4, seed=11, chain=2)
+    assert np.array_equal(a[0], xo)
