@@ -293,16 +293,18 @@ struct TcGroup {
     WaveBuf wb;
 };
 
-// Large chains the windowed sweep takes (at least kWinBigBlocks blocks of
-// 4 x 32 sites per multiprocessor) run it one launch per chain and sweep,
-// as the chain API does for such images (on GB300 it measured about 1.5x
-// the tensor-core sweep there); planes by the device sweep counter,
-// budget-aware.
-constexpr long kWinBigBlocks = 16;
+// Chains the windowed sweep takes run it as their own launches, as the
+// chain API does for such images: from kWinBigBlocks blocks of 4 x 32 sites
+// per multiprocessor one launch per sweep, from kWinWaveBlocks one
+// wavefront launch per slice (on GB300 1.3-1.5x the tensor-core sweep
+// there); planes by the device sweep counter, budget-aware.
+constexpr long kWinBigBlocks = 100;
+constexpr long kWinWaveBlocks = 8;
 
 struct TcSet {
     std::vector<TcGroup> groups;
     std::vector<int> win;          // slots on the windowed sweep, launched one at a time
+    std::vector<int> winw;         // slots on the windowed wavefront, launched one at a time
     std::vector<int> big;          // slots launched one at a time
     unsigned int *ctr = nullptr;   // their tile counters and work counter (regrown)
     long ctr_cap = 0;
@@ -317,6 +319,7 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
     rest.clear();
     ts.big.clear();
     ts.win.clear();
+    ts.winw.clear();
     int sms = 0, dev = 0;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -327,9 +330,14 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
             continue;
         }
         const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 3) / 4);
-        if (sms > 0 && tiles >= kWinBigBlocks * sms && (d[i].H + 3) / 4 <= 65535 &&
+        if (sms > 0 && tiles >= kWinWaveBlocks * sms && (d[i].H + 3) / 4 <= 65535 &&
             pca_win_eligible(d[i].m)) {
-            ts.win.push_back(i);
+            if (tiles >= kWinBigBlocks * sms) {
+                ts.win.push_back(i);
+            } else {
+                ts.winw.push_back(i);
+                big_tiles = std::max(big_tiles, tiles);
+            }
             continue;
         }
         if (!pca_tc_auto(d[i].m)) {   // a table for the windowed sweep only
@@ -399,6 +407,25 @@ pcad_status tc_set_issue(const TcSet &ts, const std::vector<SlotDesc> &desc,
             a.sweep_off = (uint32_t)k;
             B_TRY(launch_pca_win(a, d.tctab, st, d.x[0], d.x[1], d.budget));
         }
+    }
+    for (int i : ts.winw) {
+        const SlotDesc &d = desc[i];
+        SweepArgs a{};
+        a.g = d.g;
+        a.acc = d.acc;
+        a.fp64_draws = d.fp64_draws;
+        a.sweep_base = d.tdev;
+        a.seed = d.seed;
+        a.H = d.H;
+        a.W = d.W;
+        a.pitch = d.pitch;
+        a.chain = d.chain;
+        a.burn_in = d.burn_in;
+        a.m = d.m;
+        const size_t tiles = (size_t)((d.W + 31) / 32) * ((d.H + 3) / 4);
+        B_TRY(cudaMemsetAsync(ts.ctr, 0, (tiles + 1) * sizeof(unsigned int), st));
+        B_TRY(launch_pca_winw(a, d.tctab, d.x[0], d.x[1], n, ts.ctr, ts.ctr + tiles, err, st,
+                              d.budget, true));
     }
     for (int i : ts.big) {
         const SlotDesc &d = desc[i];
@@ -1026,7 +1053,8 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
         // a large slot's launch carries the model: capture the slice again
         const bool own_launch =
             std::find(b->tc.big.begin(), b->tc.big.end(), i) != b->tc.big.end() ||
-            std::find(b->tc.win.begin(), b->tc.win.end(), i) != b->tc.win.end();
+            std::find(b->tc.win.begin(), b->tc.win.end(), i) != b->tc.win.end() ||
+            std::find(b->tc.winw.begin(), b->tc.winw.end(), i) != b->tc.winw.end();
         if (b->graph && own_launch) {
             B_TRY(cudaStreamSynchronize(b->stream));
             cudaGraphExecDestroy(b->graph);

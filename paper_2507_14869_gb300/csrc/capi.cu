@@ -291,15 +291,21 @@ SweepArgs make_args(const pcad_chain *ch)
 // Gibbs colour phase, 2: the lazy-PCA wavefront), for the models the
 // tensor-core sweep accepts with nbhd T <= 255 (64 <= L <= 256), either
 // neighbourhood, without energy tracking, by image size in blocks of 4 x 32
-// sites per multiprocessor.  Lazy PCA: per-sweep launches from 100 blocks per
-// SM, the wavefront from 8.  Gibbs: per-phase launches from 16.  Measured on
-// GB300 at L = 256 (site-updates/s; per-sweep / wavefront / tensor-core):
+// sites per multiprocessor: per-sweep (per-phase) launches from 100 blocks
+// per SM, the wavefront from 8; 8-neighbourhood Gibbs the wavefront from 3.
+// Measured on GB300 at L = 256, lazy PCA (site-updates/s; per-sweep /
+// wavefront / tensor-core):
 // 8192^2 1.63e10 / - / 1.07e10; 2048^2 1.70e10 / 1.63e10 / 1.14e10; 1024^2
 // 1.51e10 / 1.58e10 / 1.11e10; 768^2 1.38e10 / 1.54e10 / 1.10e10; 512^2
 // 1.11e10 / 1.45e10 / 1.08e10; 256^2 0.54e10 / 0.59e10 / 0.63e10.  At 2048^2
 // and L = 64, 96 (T = 8), 128, 160 the per-sweep windowed sweep ran 2.67e10,
 // 3.08e10, 2.24e10, 1.96e10 against 2.25e10, 1.49e10, 1.43e10, 0.80e10 for
-// the per-sweep CUDA-core kernel.
+// the per-sweep CUDA-core kernel.  Gibbs, 4 neighbours (per-phase /
+// wavefront / tensor-core phases): 2048^2 1.68e10 / 1.61e10 / 1.11e10,
+// 1024^2 1.39e10 / 1.55e10 / 1.09e10, 512^2 0.89e10 / 1.04e10 / 1.01e10,
+// 256^2 0.32e10 / 0.33e10 / 0.34e10; 8 neighbours (per-phase / wavefront /
+// CUDA-core phases): 2048^2 1.47e10 / 1.56e10 / 0.64e10, 256^2 0.17e10 /
+// 0.19e10 / 0.15e10.
 int win_auto_mode(const pcad_chain *ch)
 {
     if (ch->tb_k > 0 || ch->track.trace || ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
@@ -311,8 +317,8 @@ int win_auto_mode(const pcad_chain *ch)
     if ((ch->H + 3) / 4 > 65535)
         return 0;
     const long long blocks = (long long)((ch->W + 31) / 32) * ((ch->H + 3) / 4);
-    if (ch->model.sampler != PCAD_SAMPLER_PCA)
-        return blocks >= 16LL * ch->sms ? 1 : 0;
+    if (ch->model.sampler != PCAD_SAMPLER_PCA && ch->model.nbhd == 8)
+        return blocks >= 3LL * ch->sms ? 2 : 0;   // no tensor-core Gibbs form to compare
     if (blocks >= 100LL * ch->sms)
         return 1;
     return blocks >= 8LL * ch->sms ? 2 : 0;
@@ -362,16 +368,16 @@ bool uses_win(const pcad_chain *ch)
            pca_win_eligible(ch->dm);
 }
 
-// Lazy-PCA sweeps of the windowed kernel as one wavefront launch per block
-// of sweeps: on request, without energy tracking (which needs every sweep's
+// Sweeps of the windowed kernels as one wavefront launch per block of sweeps
+// (lazy PCA, or Gibbs colour phases): on request, without energy tracking (which needs every sweep's
 // state: then one windowed launch per sweep), or with AUTO where
 // win_auto_mode takes it.
 bool uses_winw(const pcad_chain *ch)
 {
     if (win_auto_mode(ch) == 2)
         return true;
-    return ch->model.sampler == PCAD_SAMPLER_PCA && ch->tb_k == 0 && !ch->track.trace &&
-           ch->kernel == PCAD_KERNEL_WINDOW_WAVE && pca_win_eligible(ch->dm);
+    return ch->tb_k == 0 && !ch->track.trace && ch->kernel == PCAD_KERNEL_WINDOW_WAVE &&
+           pca_win_eligible(ch->dm);
 }
 
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
@@ -448,10 +454,15 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
         a.sweep_off = (uint32_t)off0;
         CUDA_TRY(cudaMemsetAsync(ch->wave, 0, (size_t)(ch->wave_tiles + 1) * sizeof(unsigned int),
                                  st));
-        CUDA_TRY(launch_pca_winw(a, ch->ftab, ch->x[cur], ch->x[cur ^ 1], n, ch->wave,
-                                 ch->wave + ch->wave_tiles, ch->err, st));
-        if (n & 1)
-            cur ^= 1;
+        if (ch->model.sampler == PCAD_SAMPLER_PCA) {
+            CUDA_TRY(launch_pca_winw(a, ch->ftab, ch->x[cur], ch->x[cur ^ 1], n, ch->wave,
+                                     ch->wave + ch->wave_tiles, ch->err, st));
+            if (n & 1)
+                cur ^= 1;
+        } else {   // colour phases in place
+            CUDA_TRY(launch_gibbs_winw(a, ch->ftab, ch->x[cur], n, ch->wave,
+                                       ch->wave + ch->wave_tiles, ch->err, st));
+        }
         return PCAD_OK;
     }
     if (uses_wave(ch) && n > 0) {
@@ -881,7 +892,8 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
         *kind = PCAD_KERNEL_RESIDENT;
     else if (ch->model.sampler != PCAD_SAMPLER_PCA)
         *kind = uses_tc(ch) ? PCAD_KERNEL_TENSOR
-                            : (uses_win(ch) ? PCAD_KERNEL_WINDOW : PCAD_KERNEL_CUDA_CORE);
+                : uses_winw(ch) ? PCAD_KERNEL_WINDOW_WAVE
+                : uses_win(ch) ? PCAD_KERNEL_WINDOW : PCAD_KERNEL_CUDA_CORE;
     else if (ch->tb_k > 0)
         *kind = -ch->tb_k;
     else if (uses_tc(ch))
@@ -1012,10 +1024,9 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
         kind != PCAD_KERNEL_WINDOW_WAVE)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
                                  "_WAVE, _SMALL, _RESIDENT, _WINDOW or _WINDOW_WAVE");
-    if (kind == PCAD_KERNEL_WINDOW_WAVE &&
-        (ch->model.sampler != PCAD_SAMPLER_PCA || !pca_win_eligible(ch->dm)))
-        return fail(PCAD_EINVAL, "the windowed wavefront sweep needs the PCA sampler, "
-                                 "64 <= L <= 256, T <= 33, nbhd T <= 255 and the L0 price");
+    if (kind == PCAD_KERNEL_WINDOW_WAVE && !pca_win_eligible(ch->dm))
+        return fail(PCAD_EINVAL, "the windowed wavefront sweep needs 64 <= L <= 256, T <= 33, "
+                                 "nbhd T <= 255 and the L0 price");
     if (kind == PCAD_KERNEL_WINDOW && !pca_win_eligible(ch->dm))
         return fail(PCAD_EINVAL, "the windowed sweep needs 64 <= L <= 256, T <= 33, "
                                  "nbhd T <= 255 and the L0 inertia price");

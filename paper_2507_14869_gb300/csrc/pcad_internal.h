@@ -295,12 +295,21 @@ cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s
                            uint8_t *x0 = nullptr, uint8_t *x1 = nullptr,
                            const uint32_t *budget = nullptr);
 // The windowed sweep as one persistent wavefront launch of nsweeps sweeps
-// (planes x0 for even, x1 for odd sweeps of the launch): tiles of 4 x 32
-// sites, counters done[] (ceil(H / 4) * ceil(W / 32) zeroed entries), grab
-// zeroed, *err set when a bounded dependency wait gave up.
+// (planes x0 for even, x1 for odd sweeps of the launch, or by the parity of
+// the sweep index with par_from_t): tiles of 4 x 32 sites, counters done[]
+// (ceil(H / 4) * ceil(W / 32) zeroed entries), grab zeroed, *err set when a
+// bounded dependency wait gave up; budget (optional): sweeps at or past
+// *budget are skipped.
 cudaError_t launch_pca_winw(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1,
                             int nsweeps, unsigned int *done, unsigned int *grab, int *err,
-                            cudaStream_t s);
+                            cudaStream_t s, const uint32_t *budget = nullptr,
+                            bool par_from_t = false);
+// nsweeps checkerboard Gibbs sweeps in place on x with the windowed draw as
+// one wavefront launch of colour phases: tiles of 64 columns x 4 (8 for 8
+// neighbours) rows, counters done[] (one zeroed entry per tile), grab
+// zeroed, *err as launch_pca_winw's.
+cudaError_t launch_gibbs_winw(const SweepArgs &a, const float *ftab, uint8_t *x, int nsweeps,
+                              unsigned int *done, unsigned int *grab, int *err, cudaStream_t s);
 // Checkerboard Gibbs colour phase q (0..nbhd/2 - 1) in place on a.xin with
 // the windowed draw; a.last_phase: accumulate the cells after it.
 cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t s);

@@ -334,12 +334,15 @@ __global__ void __launch_bounds__(kWThreads, 8) pca_win_kernel(const SweepArgs a
 // that runs out sets *err and no block takes a further item).  Every item an
 // item depends on has a smaller index and was taken by a resident block (the
 // grid is the resident capacity), so the waits end.  Labels and sums written
-// by other blocks in the launch are read through L2.  Plane of sweep k: x0
-// for even k, x1 for odd.
+// by other blocks in the launch are read through L2.  Plane of sweep k of
+// the launch: x0 for even k, x1 for odd, or (par_from_t) by the parity of
+// the sweep index t; budget (optional): items of sweeps t >= *budget are
+// skipped (nothing waited for, read, written or published).
 template <int NB, bool LMASK>
 __global__ void __launch_bounds__(kWThreads, 8)
     pca_winw_kernel(const SweepArgs a, const float *ftab, uint8_t *x0, uint8_t *x1, int nsweeps,
-                    int tiles_x, int tiles_y, unsigned int *done, unsigned int *grab, int *err)
+                    int tiles_x, int tiles_y, unsigned int *done, unsigned int *grab, int *err,
+                    int par_from_t, const uint32_t *budget)
 {
     __shared__ WinShared<NB> sh;
     __shared__ __align__(16) uint32_t U_s[kWY * kWX];
@@ -362,6 +365,7 @@ __global__ void __launch_bounds__(kWThreads, 8)
         const int ty = j / tiles_x;
         const int tx = j - ty * tiles_x;
         const uint32_t t = t0 + (uint32_t)k;
+        const bool run = budget == nullptr || t < *budget;   // the same for the whole block
         __syncthreads();   // s_next read; the previous item's draw is complete
         if (tid <= kWMaxChunks)
             sh.bins[tid] = 0;
@@ -371,7 +375,7 @@ __global__ void __launch_bounds__(kWThreads, 8)
             if (lane == 31)
                 s_next = ld_flag(err) ? total : atomicAdd(grab, 1u);
             bool ok = true;
-            if (k > 0 && lane < 9) {
+            if (run && k > 0 && lane < 9) {
                 const int yy = ty + lane / 3 - 1;
                 const int xx = tx + lane % 3 - 1;
                 if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
@@ -382,29 +386,35 @@ __global__ void __launch_bounds__(kWThreads, 8)
             if (!ok)
                 atomicExch(err, 1);
             __syncwarp();
-        } else if (wp == 1) {
+        } else if (wp == 1 && run) {
             block_uniforms(a, ty * kWY, tx * kWX, t, U_s);
         }
         __syncthreads();
-        const uint8_t *xin = (k & 1) ? x1 : x0;
-        uint8_t *xout = (k & 1) ? x0 : x1;
-        const int r = ty * kWY + lr, c = tx * kWX + lc;
-        const bool valid = r < a.H && c < a.W;
-        SiteIn<NB> in{};
-        if (valid) {
-            load_site<NB, true, false>(a, xin, r, c, kTagPCA, t, in);
-            in.ub = U_s[lr * kWX + lc];
-        }
-        const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
-        if (valid) {
-            xout[(size_t)r * a.pitch + c] = (uint8_t)s;
-            if (accumulate_after(a, t)) {
-                float *p = a.acc + (size_t)r * a.W + c;
-                *p = __ldcg(p) + (float)s;
+        if (run) {
+            const uint32_t ph = par_from_t ? (t & 1u) : (uint32_t)(k & 1);
+            const uint8_t *xin = ph ? x1 : x0;
+            uint8_t *xout = ph ? x0 : x1;
+            const int r = ty * kWY + lr, c = tx * kWX + lc;
+            const bool valid = r < a.H && c < a.W;
+            SiteIn<NB> in{};
+            if (valid) {
+                load_site<NB, true, false>(a, xin, r, c, kTagPCA, t, in);
+                in.ub = U_s[lr * kWX + lc];
+            }
+            const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
+            if (valid) {
+                xout[(size_t)r * a.pitch + c] = (uint8_t)s;
+                if (accumulate_after(a, t)) {
+                    float *p = a.acc + (size_t)r * a.W + c;
+                    *p = __ldcg(p) + (float)s;
+                }
             }
         }
         __syncthreads();
-        if (tid == 0 && j != a.stall_tile - 1) {
+        // a skipped item publishes nothing: only later, also skipped, items of
+        // the chain could depend on it, and an early count would let a
+        // neighbour's item of an earlier sweep pass its wait too soon
+        if (run && tid == 0 && j != a.stall_tile - 1) {
             __threadfence();   // the tile's labels and sums before its counter
             atomicExch(done + j, (unsigned int)(k + 1));
         }
@@ -477,6 +487,115 @@ __global__ void __launch_bounds__(kWThreads, 8) gibbs_win_kernel(const SweepArgs
     }
 }
 
+// Wavefront form of the windowed Gibbs sweep: items (phase k, tile j) over
+// the tiles of gibbs_win_kernel's blocks (64 columns x 4 or 8 rows), phase k
+// being colour k mod (nbhd / 2) of sweep k / (nbhd / 2), in place.  Item
+// (k, j) waits until the 3 x 3 tiles around j have finished phase k - 1:
+// then the labels it reads are final and no neighbour still reads the ones
+// it overwrites.  Waits bounded as pca_winw_kernel's; labels read through L2.
+template <int NB, bool LMASK>
+__global__ void __launch_bounds__(kWThreads, 8)
+    gibbs_winw_kernel(const SweepArgs a, const float *ftab, uint8_t *x, int nphases, int tiles_x,
+                      int tiles_y, unsigned int *done, unsigned int *grab, int *err)
+{
+    constexpr int kCol = NB == 4 ? 2 : 4;
+    __shared__ WinShared<NB> sh;
+    __shared__ __align__(16) uint32_t U_s[kWY * 2 * kWX];   // 4 site rows x 64 columns
+    __shared__ unsigned int s_next;
+    const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
+    const int tid = wp * kWX + lane;
+    const unsigned int ntiles = (unsigned int)(tiles_x * tiles_y);
+    const unsigned int total = ntiles * (unsigned int)nphases;
+    const uint32_t t0 = sweep_index(a);
+    const long long limit = wait_limit(a.wait_ns);
+    win_setup(sh, a.m.T, ftab, tid);
+    if (tid == 0)
+        s_next = atomicAdd(grab, 1u);
+    __syncthreads();
+    unsigned int item = s_next;
+    while (item < total) {
+        const int k = (int)(item / ntiles);
+        const int j = (int)(item - (unsigned int)k * ntiles);
+        const int ty = j / tiles_x;
+        const int tx = j - ty * tiles_x;
+        const int q = k % kCol;
+        const uint32_t t = t0 + (uint32_t)(k / kCol);
+        __syncthreads();   // s_next read; the previous item's draw is complete
+        if (tid <= kWMaxChunks)
+            sh.bins[tid] = 0;
+        if (wp == 0) {
+            if (lane == 31)
+                s_next = ld_flag(err) ? total : atomicAdd(grab, 1u);
+            bool ok = true;
+            if (k > 0 && lane < 9) {
+                const int yy = ty + lane / 3 - 1;
+                const int xx = tx + lane % 3 - 1;
+                if (yy >= 0 && yy < tiles_y && xx >= 0 && xx < tiles_x) {
+                    const unsigned int *d = done + (size_t)yy * tiles_x + xx;
+                    ok = wait_ge(d, (unsigned int)k, ld_acquire_u32(d), err, limit);
+                }
+            }
+            if (!ok)
+                atomicExch(err, 1);
+            __syncwarp();
+        } else if (wp == 1 || wp == 2) {   // 64 Philox calls: site rows of the phase
+            const int i = (wp - 1) * 32 + lane;
+            const int ri = i >> 4;
+            const int row = NB == 4 ? ty * kWY + ri : 2 * (ty * kWY + ri) + (q >> 1);
+            uint32_t o0, o1, o2, o3;
+            philox4x32_10((uint32_t)(16 * tx + (i & 15)), (uint32_t)(row + a.row_off), t,
+                          (kTagGibbs << 24) | (a.chain & 0xFFFFFFu),
+                          (uint32_t)(a.seed & 0xFFFFFFFFull), (uint32_t)(a.seed >> 32), o0, o1,
+                          o2, o3);
+            reinterpret_cast<uint4 *>(U_s)[i] = make_uint4(o0 >> 8, o1 >> 8, o2 >> 8, o3 >> 8);
+        }
+        __syncthreads();
+        const int cx = tx * kWX + lane, cy = ty * kWY + wp;
+        int r0, c0, r, c;
+        if (NB == 4) {
+            r0 = cy;
+            c0 = 2 * cx;
+            r = r0;
+            c = c0 + ((r + q) & 1);
+        } else {
+            r0 = 2 * cy;
+            c0 = 2 * cx;
+            r = r0 + (q >> 1);
+            c = c0 + (q & 1);
+        }
+        const bool cell = r0 < a.H && c0 < a.W;
+        const bool valid = cell && r < a.H && c < a.W;
+        SiteIn<NB> in{};
+        if (valid) {
+            load_site<NB, true, false>(a, x, r, c, kTagGibbs, t, in);
+            in.ub = U_s[wp * 2 * kWX + (c - 2 * kWX * tx)];
+        }
+        const int s = win_draw<NB, LMASK>(sh, a.m, in, valid, tid, a.fp64_draws);
+        if (valid)
+            x[(size_t)r * a.pitch + c] = (uint8_t)s;
+        if (cell && q == kCol - 1 && accumulate_after(a, t)) {
+            const int nr = NB == 4 ? 1 : 2;
+#pragma unroll
+            for (int dr = 0; dr < nr; ++dr)
+#pragma unroll
+                for (int dc = 0; dc < 2; ++dc) {
+                    const int rr = r0 + dr, cc = c0 + dc;
+                    if (rr < a.H && cc < a.W) {
+                        float *p = a.acc + (size_t)rr * a.W + cc;
+                        const int v = (rr == r && cc == c) ? s : (int)__ldcg(x + (size_t)rr * a.pitch + cc);
+                        *p = __ldcg(p) + (float)v;
+                    }
+                }
+        }
+        __syncthreads();
+        if (tid == 0 && j != a.stall_tile - 1) {
+            __threadfence();   // the tile's labels and sums before its counter
+            atomicExch(done + j, (unsigned int)(k + 1));
+        }
+        item = s_next;
+    }
+}
+
 template <int NB, bool LMASK>
 cudaError_t launch_gibbs_win_t(const SweepArgs &a, int q, const float *ftab, cudaStream_t st)
 {
@@ -503,7 +622,8 @@ cudaError_t launch_win_t(const SweepArgs &a, const float *ftab, uint8_t *x0, uin
 
 template <int NB, bool LMASK>
 cudaError_t launch_winw_t(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1, int n,
-                          unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+                          unsigned int *done, unsigned int *grab, int *err, int par_from_t,
+                          const uint32_t *budget, cudaStream_t st)
 {
     static int per_sm[64] = {};
     int dev = 0;
@@ -534,16 +654,54 @@ cudaError_t launch_winw_t(const SweepArgs &a, const float *ftab, uint8_t *x0, ui
     // at most the resident capacity: every block that takes an item runs
     const long long cap = (long long)per_sm[dev] * sms;
     const int grid = (int)(items < cap ? items : cap);
-    pca_winw_kernel<NB, LMASK><<<grid, dim3(kWX, kWY), 0, st>>>(a, ftab, x0, x1, n, tiles_x,
-                                                                tiles_y, done, grab, err);
+    pca_winw_kernel<NB, LMASK><<<grid, dim3(kWX, kWY), 0, st>>>(
+        a, ftab, x0, x1, n, tiles_x, tiles_y, done, grab, err, par_from_t, budget);
+    return cudaGetLastError();
+}
+
+template <int NB, bool LMASK>
+cudaError_t launch_gibbs_winw_t(const SweepArgs &a, const float *ftab, uint8_t *x, int nsweeps,
+                                unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
+{
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, gibbs_winw_kernel<NB, LMASK>,
+                                                          kWThreads, 0);
+        if (e != cudaSuccess)
+            return e;
+        per_sm[dev] = nb > 0 ? nb : 1;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int rows = NB == 4 ? kWY : 2 * kWY;
+    const int tiles_x = (a.W + 2 * kWX - 1) / (2 * kWX);
+    const int tiles_y = (a.H + rows - 1) / rows;
+    const int nphases = nsweeps * (NB == 4 ? 2 : 4);
+    const long long items = (long long)tiles_x * tiles_y * nphases;
+    if (items <= 0)
+        return cudaSuccess;
+    if (items >= (1ll << 32))
+        return cudaErrorInvalidValue;
+    const long long cap = (long long)per_sm[dev] * sms;
+    const int grid = (int)(items < cap ? items : cap);
+    gibbs_winw_kernel<NB, LMASK><<<grid, dim3(kWX, kWY), 0, st>>>(a, ftab, x, nphases, tiles_x,
+                                                                  tiles_y, done, grab, err);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_pca_winw(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1,
-                            int nsweeps, unsigned int *done, unsigned int *grab, int *err,
-                            cudaStream_t st)
+cudaError_t launch_gibbs_winw(const SweepArgs &a, const float *ftab, uint8_t *x, int nsweeps,
+                              unsigned int *done, unsigned int *grab, int *err, cudaStream_t st)
 {
     if (!pca_win_eligible(a.m) || ftab == nullptr || nsweeps < 0)
         return cudaErrorInvalidValue;
@@ -551,10 +709,31 @@ cudaError_t launch_pca_winw(const SweepArgs &a, const float *ftab, uint8_t *x0, 
         return cudaSuccess;
     const bool lmask = (a.m.L % kChunk) != 0;
     if (a.m.nbhd == 8)
-        return lmask ? launch_winw_t<8, true>(a, ftab, x0, x1, nsweeps, done, grab, err, st)
-                     : launch_winw_t<8, false>(a, ftab, x0, x1, nsweeps, done, grab, err, st);
-    return lmask ? launch_winw_t<4, true>(a, ftab, x0, x1, nsweeps, done, grab, err, st)
-                 : launch_winw_t<4, false>(a, ftab, x0, x1, nsweeps, done, grab, err, st);
+        return lmask ? launch_gibbs_winw_t<8, true>(a, ftab, x, nsweeps, done, grab, err, st)
+                     : launch_gibbs_winw_t<8, false>(a, ftab, x, nsweeps, done, grab, err, st);
+    return lmask ? launch_gibbs_winw_t<4, true>(a, ftab, x, nsweeps, done, grab, err, st)
+                 : launch_gibbs_winw_t<4, false>(a, ftab, x, nsweeps, done, grab, err, st);
+}
+
+cudaError_t launch_pca_winw(const SweepArgs &a, const float *ftab, uint8_t *x0, uint8_t *x1,
+                            int nsweeps, unsigned int *done, unsigned int *grab, int *err,
+                            cudaStream_t st, const uint32_t *budget, bool par_from_t)
+{
+    if (!pca_win_eligible(a.m) || ftab == nullptr || nsweeps < 0)
+        return cudaErrorInvalidValue;
+    if (a.H <= 0 || a.W <= 0 || nsweeps == 0)
+        return cudaSuccess;
+    const bool lmask = (a.m.L % kChunk) != 0;
+    const int par = par_from_t ? 1 : 0;
+    if (a.m.nbhd == 8)
+        return lmask ? launch_winw_t<8, true>(a, ftab, x0, x1, nsweeps, done, grab, err, par,
+                                              budget, st)
+                     : launch_winw_t<8, false>(a, ftab, x0, x1, nsweeps, done, grab, err, par,
+                                               budget, st);
+    return lmask ? launch_winw_t<4, true>(a, ftab, x0, x1, nsweeps, done, grab, err, par, budget,
+                                          st)
+                 : launch_winw_t<4, false>(a, ftab, x0, x1, nsweeps, done, grab, err, par,
+                                           budget, st);
 }
 
 cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaStream_t st)

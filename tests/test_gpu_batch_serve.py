@@ -406,9 +406,10 @@ def test_batch_slice_lengths_are_bit_identical(pc, slice_sweeps, rows, order):
 
 
 def test_large_windowed_slots_in_batch_and_server(pc):
-    """Tensor-core eligible images of at least 16 blocks of 4 x 32 sites per
-    SM run the windowed sweep as their own per-sweep launches inside the
-    batch's and the server's slices (planes chosen by the device sweep
+    """Tensor-core eligible images of at least 8 blocks of 4 x 32 sites per
+    SM run the windowed sweep as their own launches inside the batch's and
+    the server's slices -- the wavefront form one launch per slice, from 100
+    blocks per SM one launch per sweep -- (planes chosen by the device sweep
     counter, budgets ending inside slices), one of them changing its
     coefficients between runs: results equal the chains run alone."""
     import torch
@@ -420,9 +421,12 @@ def test_large_windowed_slots_in_batch_and_server(pc):
             42, 4, 5)
     small = (_grey(42, 40, 33, 256, 15.0),
              Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=15.0, inertia=2.0), 43, 5, 5)
-    jobs = [big4, big8, small]
-    for g, *_ in jobs[:2]:
-        assert ((g.shape[1] + 31) // 32) * ((g.shape[0] + 3) // 4) >= 16 * sms
+    huge = (_grey(43, 1600, 1300, 256, 25.0),
+            Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=25.0, inertia=2.0), 44, 6, 9)
+    jobs = [big4, big8, small, huge]
+    tiles = [((g.shape[1] + 31) // 32) * ((g.shape[0] + 3) // 4) for g, *_ in jobs]
+    assert all(8 * sms <= n < 100 * sms for n in tiles[:2])   # the wavefront form
+    assert tiles[3] >= 100 * sms                                 # one launch per sweep
     m_new = Model(L=256, pair=TL, pair_coef=0.08, pair_T=30, sigma=20.0, inertia=1.0)
     b = pc.pcad_batch_create(jobs, autotune=False)
     try:
@@ -441,7 +445,7 @@ def test_large_windowed_slots_in_batch_and_server(pc):
             assert np.array_equal(pc.pcad_batch_read_mean(b, i, *g.shape), ms), i
     finally:
         pc.pcad_batch_destroy(b)
-    budgets = [37, 20, 45]
+    budgets = [37, 20, 45, 23]
     sv = pc.pcad_server_create(8, 1 << 31)
     try:
         ids, shapes = [], {}

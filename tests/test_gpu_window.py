@@ -103,28 +103,37 @@ def test_window_kernel_is_validated(pc):
             assert e.value.status == 1
 
 
-def test_auto_takes_the_windowed_gibbs_sweep_on_large_images(pc):
+def test_auto_rule_for_windowed_gibbs(pc):
     import torch
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    side = 1024
-    assert (side // 32) * (side // 4) >= 16 * sms
-    g = np.zeros((side, side), np.uint8)
-    for nbhd in (4, 8):
-        m = Model(L=256, nbhd=nbhd, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, sampler=1)
-        with pc.Chain(g, m, seed=1, sampler=1) as ch:
-            assert ch.kernel_in_use() == WINDOW
+    for side in (256, 1024, 2048):
+        blocks = (side // 32) * (side // 4)
+        g = np.zeros((side, side), np.uint8)
+        for nbhd in (4, 8):
+            m = Model(L=256, nbhd=nbhd, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0,
+                      sampler=1)
+            if nbhd == 8:
+                expect = pc.PCAD_KERNEL_WINDOW_WAVE if blocks >= 3 * sms else CUDA_CORE
+            elif blocks >= 100 * sms:
+                expect = WINDOW
+            else:
+                expect = pc.PCAD_KERNEL_WINDOW_WAVE if blocks >= 8 * sms else TENSOR
+            with pc.Chain(g, m, seed=1, sampler=1) as ch:
+                assert ch.kernel_in_use() == expect, (side, nbhd)
 
 
 @pytest.mark.parametrize("name,make,m", CASES[:6], ids=[c[0] for c in CASES[:6]])
-def test_window_wavefront_matches_per_sweep_and_oracle(pc, name, make, m):
+@pytest.mark.parametrize("sampler", [0, 1], ids=["pca", "gibbs"])
+def test_window_wavefront_matches_per_sweep_and_oracle(pc, name, make, m, sampler):
     """PCAD_KERNEL_WINDOW_WAVE: the windowed draw as one persistent wavefront
-    launch per block of sweeps (a captured 32-sweep block, then odd and
-    single sweeps): the per-sweep windowed kernel's labels, means and FP64
-    re-draw counts, and the oracle's labels."""
+    launch per block of sweeps (of colour phases for Gibbs; a captured
+    32-sweep block, then odd and single sweeps): the per-sweep windowed
+    kernel's labels, means and FP64 re-draw counts, and the oracle's
+    labels."""
     g = make()
     outs = {}
     for kind in (pc.PCAD_KERNEL_WINDOW_WAVE, WINDOW):
-        with pc.Chain(g, m, seed=11, chain_id=2, burn_in=4) as ch:
+        with pc.Chain(g, m, seed=11, chain_id=2, burn_in=4, sampler=sampler) as ch:
             ch.set_kernel(kind)
             assert ch.kernel_in_use() == kind
             for n in (32, 3, 1):
@@ -133,5 +142,6 @@ def test_window_wavefront_matches_per_sweep_and_oracle(pc, name, make, m):
             ch.sync()
     a, b = outs[pc.PCAD_KERNEL_WINDOW_WAVE], outs[WINDOW]
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and a[2] == b[2]
-    xo, _, _, _ = oracle.run_chain(m, g, 36, 4, seed=11, chain=2)
+    kw = {} if sampler == 0 else {"order": oracle.ORDER_COLOUR}
+    xo, _, _, _ = oracle.run_chain(m, g, 36, 4, seed=11, chain=2, sampler=sampler, **kw)
     assert np.array_equal(a[0], xo)
