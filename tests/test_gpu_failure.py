@@ -38,6 +38,9 @@ CASES = {
     # tensor-core wavefront, lazy PCA and checkerboard Gibbs
     "tensor_L256": (256, 20.0, dict(pair_coef=0.05, pair_T=30, inertia=2.0), 2),
     "tensor_gibbs_L256": (256, 20.0, dict(pair_coef=0.05, pair_T=30, sampler=1), 2),
+    # windowed CUDA-core wavefronts: 4 x 32 tiles (PCA), 4 x 64 cell tiles (Gibbs)
+    "window_wave_L256": (256, 20.0, dict(pair_coef=0.05, pair_T=30, inertia=2.0), 7),
+    "window_wave_gibbs_L256": (256, 20.0, dict(pair_coef=0.05, pair_T=30, sampler=1), 7),
 }
 
 
