@@ -188,9 +188,10 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * per 8-byte shared-memory entry, the other chunks' sums from a table of the
  * observation, the sites of a block sorted by the number of such chunks so
  * that a warp's lanes do similar work; same labels.  PCAD_KERNEL_WINDOW_WAVE
- * (PCA sampler, the same models) runs the windowed draw as one persistent
- * wavefront launch per block of sweeps, as PCAD_KERNEL_WAVE does the
- * CUDA-core draw (energy tracking: one sweep per launch); same labels. */
+ * (the same models, either sampler) runs the windowed draw as one
+ * persistent wavefront launch per block of sweeps (of Gibbs colour phases),
+ * as PCAD_KERNEL_WAVE does the CUDA-core draw (energy tracking: one launch
+ * per sweep); same labels. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
@@ -212,8 +213,8 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * windowed kernels for chains of models the tensor-core kernel takes with
  * nbhd T <= 255 (64 <= L <= 256, any neighbourhood for Gibbs) without
  * energy tracking, by image size in blocks of 4 x 32 sites per
- * multiprocessor: lazy PCA PCAD_KERNEL_WINDOW from 100, PCAD_KERNEL_WINDOW_WAVE
- * from 8, Gibbs PCAD_KERNEL_WINDOW from 16; the tensor-core kernel for the
+ * multiprocessor: PCAD_KERNEL_WINDOW from 100, PCAD_KERNEL_WINDOW_WAVE from 8
+ * (8-neighbourhood Gibbs: from 3); the tensor-core kernel for the
  * other eligible models with L >= 192 and no energy tracking;
  * PCAD_KERNEL_SMALL for the models it accepts; otherwise
  * the wavefront kernel for L >= 16 when the
