@@ -180,8 +180,9 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * FP64 re-draw of the other kernels; same labels and the same FP64 re-draw
  * count (with two labels every inertia price is the L0 one).  AUTO takes it
  * for the images it accepts (no energy tracking, no temporal blocking).
- * PCAD_KERNEL_WINDOW (the models PCAD_KERNEL_TENSOR accepts with
- * nbhd T <= 255, either sampler and neighbourhood; PCAD_EINVAL otherwise)
+ * PCAD_KERNEL_WINDOW (9 <= L <= 256, truncation 1 <= T <= 33 with
+ * nbhd T <= 255, the L0 price, either sampler and neighbourhood;
+ * PCAD_EINVAL otherwise)
  * runs one launch per sweep (per Gibbs colour phase) on the CUDA cores with
  * the tensor-core sweep's weights: each site evaluates only the label chunks
  * its neighbours' tents reach, their tent sums read from a table of 8 tents
@@ -210,9 +211,9 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
  * temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO the
  * resident kernel
  * is taken for the two-label images it accepts without energy tracking; the
- * windowed kernels for chains of models the tensor-core kernel takes with
- * nbhd T <= 255 (64 <= L <= 256, any neighbourhood for Gibbs) without
- * energy tracking, by image size in blocks of 4 x 32 sites per
+ * windowed kernels for chains of models they accept with L >= 32 (any
+ * neighbourhood for Gibbs) without energy tracking, by image size in blocks
+ * of 4 x 32 sites per
  * multiprocessor: PCAD_KERNEL_WINDOW from 100, PCAD_KERNEL_WINDOW_WAVE from 8
  * (8-neighbourhood Gibbs: from 3); the tensor-core kernel for the
  * other eligible models with L >= 192 and no energy tracking;

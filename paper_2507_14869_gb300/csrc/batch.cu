@@ -331,7 +331,7 @@ pcad_status tc_set_build(TcSet &ts, const std::vector<SlotDesc> &d,
         }
         const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 3) / 4);
         if (sms > 0 && tiles >= kWinWaveBlocks * sms && (d[i].H + 3) / 4 <= 65535 &&
-            pca_win_eligible(d[i].m)) {
+            pca_win_eligible(d[i].m) && d[i].m.L >= kWinAutoMinLabels) {
             if (tiles >= kWinBigBlocks * sms) {
                 ts.win.push_back(i);
             } else {

@@ -288,10 +288,9 @@ SweepArgs make_args(const pcad_chain *ch)
 }
 
 // The windowed sweeps AUTO takes (0: none, 1: one launch per sweep or
-// Gibbs colour phase, 2: the lazy-PCA wavefront), for the models the
-// tensor-core sweep accepts with nbhd T <= 255 (64 <= L <= 256), either
-// neighbourhood, without energy tracking, by image size in blocks of 4 x 32
-// sites per multiprocessor: per-sweep (per-phase) launches from 100 blocks
+// Gibbs colour phase, 2: the wavefront), for the models the windowed sweeps
+// accept with L >= 32, either neighbourhood, without energy tracking, by
+// image size in blocks of 4 x 32 sites per multiprocessor: per-sweep (per-phase) launches from 100 blocks
 // per SM, the wavefront from 8; 8-neighbourhood Gibbs the wavefront from 3.
 // Measured on GB300 at L = 256, lazy PCA (site-updates/s; per-sweep /
 // wavefront / tensor-core):
@@ -300,7 +299,11 @@ SweepArgs make_args(const pcad_chain *ch)
 // 1.11e10 / 1.45e10 / 1.08e10; 256^2 0.54e10 / 0.59e10 / 0.63e10.  At 2048^2
 // and L = 64, 96 (T = 8), 128, 160 the per-sweep windowed sweep ran 2.67e10,
 // 3.08e10, 2.24e10, 1.96e10 against 2.25e10, 1.49e10, 1.43e10, 0.80e10 for
-// the per-sweep CUDA-core kernel.  Gibbs, 4 neighbours (per-phase /
+// the per-sweep CUDA-core kernel; at 2048^2 (512^2: the wavefronts) L = 33
+// Potts 3.09e10 (2.57e10) against 2.19e10 (1.85e10) with 8 neighbours, L = 48
+// 3.22e10 (2.78e10) against 2.19e10 (1.87e10), L = 63 2.35e10 (2.10e10)
+// against 2.16e10 (1.83e10), but L = 24 3.65e10 against 3.96e10: AUTO takes
+// the windowed sweeps from L = 32.  Gibbs, 4 neighbours (per-phase /
 // wavefront / tensor-core phases): 2048^2 1.68e10 / 1.61e10 / 1.11e10,
 // 1024^2 1.39e10 / 1.55e10 / 1.09e10, 512^2 0.89e10 / 1.04e10 / 1.01e10,
 // 256^2 0.32e10 / 0.33e10 / 0.34e10; 8 neighbours (per-phase / wavefront /
@@ -310,7 +313,7 @@ int win_auto_mode(const pcad_chain *ch)
 {
     if (ch->tb_k > 0 || ch->track.trace || ch->kernel != PCAD_KERNEL_AUTO || ch->sms <= 0)
         return 0;
-    if (!pca_win_eligible(ch->dm))
+    if (!pca_win_eligible(ch->dm) || ch->model.L < kWinAutoMinLabels)
         return 0;
     // launch grids: (W / 32) x (H / 4) blocks (Gibbs: H / 8 for 8
     // neighbours); the second dimension is at most 65535
@@ -658,7 +661,7 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
         e = cudaMemsetAsync(ch->tdev, 0, misc, ch->stream);
     if (e == cudaSuccess && m->L <= kSmallMaxLabels)
         e = launch_ptab(tabs.dm.T, ch->ptab, ch->stream);
-    if (e == cudaSuccess && pca_tc_eligible(tabs.dm))
+    if (e == cudaSuccess && (pca_tc_eligible(tabs.dm) || pca_win_eligible(tabs.dm)))
         e = launch_tc_table(tabs.dm, ch->ftab, ch->stream);
     if (e == cudaSuccess && m->L == 2) {
         DevModel dm = tabs.dm;
@@ -860,7 +863,7 @@ pcad_status pcad_chain_set_model(pcad_chain *ch, const pcad_model *m)
     ch->dm.btab = m->L == 2 ? ch->btab : nullptr;
     if (m->L == 2)   // stream-ordered after the new FP64 tables
         CUDA_TRY(launch_btab(ch->dm, ch->btab, ch->stream));
-    if (pca_tc_eligible(ch->dm))
+    if (pca_tc_eligible(ch->dm) || pca_win_eligible(ch->dm))
         CUDA_TRY(launch_tc_table(ch->dm, ch->ftab, ch->stream));
     ch->ecoef = energy_coef(*m, (long)ch->H * ch->W);
     return PCAD_OK;

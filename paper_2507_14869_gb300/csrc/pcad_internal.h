@@ -288,8 +288,13 @@ cudaError_t launch_tc_table(const DevModel &m, float *out, cudaStream_t s);
 // from a byte table over each site's hull of labels, outside chunks from
 // ftab = launch_tc_table's table): one sweep a.xin -> a.xout, or (x0 set)
 // from the plane of the sweep index's parity (x0 even, x1 odd) to the
-// other, skipped at or past *budget (budget optional).  Models the
-// tensor-core sweep accepts with nbhd T <= 255.
+// other, skipped at or past *budget (budget optional).  Models with
+// kWinMinLabels <= L <= 256, 1 <= T <= kTcMaxT, nbhd T <= 255, the L0 price.
+constexpr int kWinMinLabels = 9;
+// The automatic kernel choice (chains, batches, the server) takes the
+// windowed sweeps from this many labels on (below, the small-label or
+// per-sweep CUDA-core kernels measured as fast or faster on GB300).
+constexpr int kWinAutoMinLabels = 32;
 bool pca_win_eligible(const DevModel &m);
 cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t s,
                            uint8_t *x0 = nullptr, uint8_t *x1 = nullptr,

@@ -752,7 +752,8 @@ cudaError_t launch_gibbs_win(const SweepArgs &a, int q, const float *ftab, cudaS
 
 bool pca_win_eligible(const DevModel &m)
 {
-    return pca_tc_eligible(m) && m.nbhd * m.T <= 255;
+    return m.L >= kWinMinLabels && m.L <= 256 && m.T >= 1 && m.T <= kTcMaxT && m.norm == 0 &&
+           (m.nbhd == 4 || m.nbhd == 8) && m.nbhd * m.T <= 255;
 }
 
 cudaError_t launch_pca_win(const SweepArgs &a, const float *ftab, cudaStream_t st, uint8_t *x0,

@@ -124,7 +124,7 @@ def test_set_kernel_rejects(pc):
         with pytest.raises(pc.PcadError):
             ch.set_kernel(pc.PCAD_KERNEL_TENSOR)      # L < 64
         with pytest.raises(pc.PcadError):
-            ch.set_kernel(7)
+            ch.set_kernel(99)                         # no such kind
         ch.set_kernel(pc.PCAD_KERNEL_CUDA_CORE)
     for T in (100, 34):   # T > 33: the tents of a 64-bin histogram leave the 128-label window
         wide = Model(L=256, pair=TL, pair_coef=0.01, pair_T=T, sigma=20.0, inertia=1.0)

@@ -48,6 +48,13 @@ CASES = [
      Model(L=128, nbhd=8, pair=TL, pair_coef=0.1, pair_T=20, sigma=10.0, inertia=1.0)),
     ("one_pixel", lambda: np.array([[200]], dtype=np.uint8),
      Model(L=256, pair=TL, pair_coef=0.05, pair_T=30, sigma=20.0, inertia=2.0)),
+    # fewer labels: the windowed kernels take 9 <= L <= 256
+    ("L33_potts8", lambda: _grey(100, 40, 70, 33, 3.0),
+     Model(L=33, nbhd=8, pair=POTTS, pair_coef=0.833, sigma=3.0, inertia=0.39)),
+    ("L17_T2", lambda: _grey(101, 37, 45, 17, 1.5),
+     Model(L=17, pair=TL, pair_coef=0.7, pair_T=2, sigma=1.5, inertia=1.0)),
+    ("L9_8nb_T31", lambda: _grey(102, 30, 33, 9, 1.0),
+     Model(L=9, nbhd=8, pair=TL, pair_coef=0.15, pair_T=31, sigma=1.0, inertia=0.5)),
 ]
 
 
@@ -57,7 +64,7 @@ def test_window_kernel_matches_oracle_and_other_kernels(pc, name, make, m, sampl
     g = make()
     sweeps, burn = 14, 5
     kinds = [WINDOW, CUDA_CORE]
-    if sampler == 0 or m.nbhd == 4:
+    if m.L >= 64 and (sampler == 0 or m.nbhd == 4):
         kinds.append(TENSOR)
     outs = {}
     for kind in kinds:
@@ -93,7 +100,7 @@ def test_window_kernel_long_chain_and_model_change(pc):
 
 def test_window_kernel_is_validated(pc):
     g = _grey(99, 20, 30, 16, 1.0)
-    for m, sampler in ((Model(L=16, pair=TL, pair_coef=0.1, pair_T=3, sigma=1.0), 0),
+    for m, sampler in ((Model(L=8, pair=TL, pair_coef=0.1, pair_T=3, sigma=1.0), 0),
                        (Model(L=256, pair=TL, pair_coef=0.05, pair_T=40, sigma=20.0), 1),
                        (Model(L=256, nbhd=8, pair=TL, pair_coef=0.05, pair_T=33, sigma=20.0), 0)):
         with pc.Chain(np.minimum(g * 16, m.L - 1).astype(np.uint8), m, seed=1,
