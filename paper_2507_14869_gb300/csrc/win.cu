@@ -1,6 +1,7 @@
-// Lazy-PCA sweep for many labels on the CUDA cores with a per-site label
-// window (Section 5.2, Eq. posterior_pca_transition_matrix), truncated-linear
-// or Potts priors with 64 <= L <= 256.
+// Lazy-PCA sweep (Section 5.2, Eq. posterior_pca_transition_matrix) and
+// checkerboard Gibbs colour phases (Section 5.1) on the CUDA cores with a
+// per-site label window, truncated-linear or Potts priors with
+// 9 <= L <= 256.
 //
 // The weights are those of the tensor-core sweep, w(s) = 2^fl(alpha (g-s)^2 +
 // fl(mu Pb(s) + cb)) with the tent sum Pb(s) = sum_j max(T - |x_j - s|, 0)
@@ -25,8 +26,11 @@
 //     the certified inverse-CDF selection with the chosen chunk's weights
 //     recomputed exactly, FP64 re-draws of uncertain draws by the warp.
 //
-// One thread per site, blocks of 4 x 32 sites, one launch per sweep; a warp
-// of each block computes the block's uniforms (one Philox call per 4 sites).
+// One thread per site in blocks of 128 threads: 4 x 32 sites for lazy PCA
+// (one Philox call per 4 sites, computed by one warp), the phase sites of
+// 64 x 4 (8) cells for Gibbs.  Each form runs as one launch per sweep (per
+// colour phase) or as a persistent wavefront of (sweep, tile) items with
+// bounded dependency waits.
 #include "tc_math.cuh"
 
 namespace pcad {
