@@ -21,12 +21,13 @@
 //     factors per label measured slower: the per-lane table reads conflict
 //     in shared memory, while the exponential unit has room.)
 //   * Inverse CDF over chunks of 4 labels: in-chunk prefix sums (3
-//     roundings), chunk prefix (3 more), one join per probed label and one
-//     for the inertia correction delta = w(x_i)(e^lambda - 1): every C_k
-//     within 8u and Z within 7u of exact, inside the 22u summation budget of
-//     the per-site certified margin (valid because gam <= 0 and alpha <= 0
-//     keep both exponent terms non-positive).  The chunk, then the label in
-//     it, are found by comparisons; draws within the margin of a CDF
+//     roundings), chunk prefix (3 more), the inertia correction delta =
+//     w(x_i)(e^lambda - 1) (w(x_i) read back from the weights in shared
+//     memory) joined once to the chunk prefix, one join per probed label:
+//     every C_k within 8u and Z within 7u of exact, inside the 22u summation
+//     budget of the per-site certified margin (valid because gam <= 0 and
+//     alpha <= 0 keep both exponent terms non-positive).  The chunk, then the
+//     label in it, are found by comparisons; draws within the margin of a CDF
 //     boundary are re-drawn by the warp in FP64.
 //
 // Persistent blocks of 128 threads take tiles of 16 x 32 sites in a
@@ -70,13 +71,6 @@ __global__ void ptab_kernel(int T, uint32_t *out)
         word |= (uint32_t)(da + db) << (8 * k);
     }
     out[i] = word;
-}
-
-// Exact float of byte k (0..3) of word p.
-__device__ __forceinline__ float byte_f(uint32_t p, int k)
-{
-    return __fsub_rn(__uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)k)),
-                     8388608.0f);
 }
 
 // The draw of one site from its neighbour codes nc[] and observation g.
@@ -147,54 +141,51 @@ __device__ __forceinline__ int draw_small(const DevModel &m, const uint32_t *pt,
             w[s + 1] = s + 1 < m.L ? w[s + 1] : 0.0f;
         }
     }
-    // in-chunk inclusive prefix sums (to shared memory) and the chunk prefix G
+    // the weights (to shared memory) and the chunk prefix G over the in-chunk
+    // sums ((w0 + w1) + w2) + w3
     float G[NW];
 #pragma unroll
     for (int c = 0; c < NW; ++c) {
-        const float p1 = __fadd_rn(w[4 * c], w[4 * c + 1]);
-        const float p2 = __fadd_rn(p1, w[4 * c + 2]);
-        const float p3 = __fadd_rn(p2, w[4 * c + 3]);
-        reinterpret_cast<float4 *>(pre)[c] = make_float4(w[4 * c], p1, p2, p3);
+        const float p3 = __fadd_rn(__fadd_rn(__fadd_rn(w[4 * c], w[4 * c + 1]), w[4 * c + 2]),
+                                   w[4 * c + 3]);
+        reinterpret_cast<float4 *>(pre)[c] =
+            make_float4(w[4 * c], w[4 * c + 1], w[4 * c + 2], w[4 * c + 3]);
         G[c] = c == 0 ? p3 : __fadd_rn(G[c - 1], p3);
     }
-    float delta = 0.0f;
-    if (m.em1 != 0.0f) {
-        // w(x_i), bit-identical to the packed evaluation above
-        uint32_t pw;
-        if constexpr (NW == 4) {
-            const uint32_t lo = (xi & 4) ? P[1] : P[0], hi = (xi & 4) ? P[3] : P[2];
-            pw = (xi & 8) ? hi : lo;
-        } else {
-            pw = (xi & 4) ? P[1] : P[0];
-        }
-        const float dg = __fsub_rn(gf, (float)xi);
-        const float v = __fmaf_rn(m.alpha, __fmul_rn(dg, dg), __fmul_rn(m.gam, byte_f(pw, xi & 3)));
-        delta = __fmul_rn(ex2_ftz(v), m.em1);
-    }
+    // inertia correction from w(x_i) as evaluated above
+    const float delta = m.em1 != 0.0f ? __fmul_rn(pre[xi], m.em1) : 0.0f;
     const float G0 = G[NW - 1];
     const float Z = __fadd_rn(G0, delta);
     const float t = __fmul_rn((float)ub * (1.0f / 16777216.0f), Z);
     const float margin = __fmul_rn(site_margin(m, G0, delta), Z);
-    // chunk: the number of chunk ends (with delta at and above x_i) <= t;
-    // Gp: the chunk prefix before it
+    // chunk: the number of chunk ends <= t, compared with t - delta where
+    // delta is added (at and above x_i); Gp: the chunk prefix before it.  Any
+    // rounding here only selects which label's interval is certified below:
+    // a chunk chosen off by one leaves t within a few u Z of that interval's
+    // end, inside the margin, and goes to FP64.
+    const float tmd = __fsub_rn(t, delta);
     int cs = 0;
     float Gp = 0.0f;
 #pragma unroll
     for (int c = 0; c + 1 < NW; ++c) {
-        const bool below = __fadd_rn(G[c], (4 * c + 3 >= xi) ? delta : 0.0f) <= t;
+        const bool below = G[c] <= ((4 * c + 3 >= xi) ? tmd : t);
         cs += below ? 1 : 0;
         Gp = below ? G[c] : Gp;
     }
-    const float4 pc = reinterpret_cast<const float4 *>(pre)[cs];
+    // the chosen chunk's in-chunk prefix sums, as summed for G; C_k joins
+    // them to Gp or to Gp + delta (two roundings either way)
+    const float4 wc = reinterpret_cast<const float4 *>(pre)[cs];
+    const float p1 = __fadd_rn(wc.x, wc.y), p2 = __fadd_rn(p1, wc.z), p3 = __fadd_rn(p2, wc.w);
     const int base = 4 * cs;
-    const float C0 = __fadd_rn(__fadd_rn(Gp, pc.x), (base >= xi) ? delta : 0.0f);
-    const float C1 = __fadd_rn(__fadd_rn(Gp, pc.y), (base + 1 >= xi) ? delta : 0.0f);
-    const float C2 = __fadd_rn(__fadd_rn(Gp, pc.z), (base + 2 >= xi) ? delta : 0.0f);
-    const float C3 = __fadd_rn(__fadd_rn(Gp, pc.w), (base + 3 >= xi) ? delta : 0.0f);
+    const float Gpd = __fadd_rn(Gp, delta);
+    const float C0 = __fadd_rn((base >= xi) ? Gpd : Gp, wc.x);
+    const float C1 = __fadd_rn((base + 1 >= xi) ? Gpd : Gp, p1);
+    const float C2 = __fadd_rn((base + 2 >= xi) ? Gpd : Gp, p2);
+    const float C3 = __fadd_rn((base + 3 >= xi) ? Gpd : Gp, p3);
     const bool b0 = C0 <= t, b1 = C1 <= t, b2 = C2 <= t;
     const int k = (int)b0 + (int)b1 + (int)b2;
     const float hiC = b2 ? C3 : (b1 ? C2 : (b0 ? C1 : C0));
-    const float Cm = __fadd_rn(Gp, (base - 1 >= xi) ? delta : 0.0f);   // before the chunk
+    const float Cm = (base - 1 >= xi) ? Gpd : Gp;   // before the chunk
     const float loC = b2 ? C2 : (b1 ? C1 : (b0 ? C0 : Cm));
     const int s = base + k;
     certain = (t < hiC) & (s < m.L) & ((s == m.L - 1) | (__fsub_rn(hiC, t) > margin)) &

@@ -41,6 +41,14 @@ CASES = [
      Model(L=3, pair=0, pair_coef=1.0, noise=2, sigma=1.0, inertia=1.0)),
     ("one_col", lambda: _grey(87, 77, 1, 16, 1.0),
      Model(L=16, nbhd=8, pair=1, pair_coef=0.8, pair_T=2, sigma=1.0, inertia=1.0)),
+    ("one_row", lambda: _grey(90, 1, 300, 16, 1.0),
+     Model(L=16, pair=1, pair_coef=0.05, pair_T=30, sigma=1.0, inertia=2.0)),
+    ("two_rows_8nb", lambda: _grey(91, 2, 33, 12, 1.0),
+     Model(L=12, nbhd=8, pair=1, pair_coef=0.4, pair_T=5, sigma=1.0, inertia=1.0)),
+    ("w32_h97_8nb", lambda: _grey(92, 97, 32, 16, 2.0),
+     Model(L=16, nbhd=8, pair=1, pair_coef=0.3, pair_T=6, sigma=2.0, inertia=1.5)),
+    ("w64_h65", lambda: _grey(93, 65, 64, 16, 1.0),
+     Model(L=16, pair=1, pair_coef=0.05, pair_T=30, sigma=1.0, inertia=2.0)),
 ]
 
 

@@ -117,8 +117,15 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
     delta = (w[np.arange(n), xi].astype(f64) * f64(em1)).astype(f32) if lam > 0 else np.zeros(n, f32)
     Z = (G + delta).astype(f32)
     Gprev = np.concatenate([np.zeros((n, 1), f32), Gc[:, :-1]], axis=1)
-    C = (np.repeat(Gprev, 4 if form == "small" else 8, axis=1)[:, :L] + pref[:, :L]).astype(f32)
-    C = (C + np.where(s[None, :] >= xi[:, None], delta[:, None], f32(0.0))).astype(f32)
+    if form == "small":
+        # the small-label kernel joins the in-chunk prefix to Gprev or to
+        # fl(Gprev + delta) (at and above x_i)
+        Gp = np.repeat(Gprev, 4, axis=1)[:, :L]
+        Gpd = (Gp + delta[:, None]).astype(f32)
+        C = (np.where(s[None, :] >= xi[:, None], Gpd, Gp) + pref[:, :L]).astype(f32)
+    else:
+        C = (np.repeat(Gprev, 8, axis=1)[:, :L] + pref[:, :L]).astype(f32)
+        C = (C + np.where(s[None, :] >= xi[:, None], delta[:, None], f32(0.0))).astype(f32)
     # exact conditional
     mu_e = c_e * LOG2E
     alpha_e = -LOG2E / (2.0 * sig_e ** 2) if model["noise"] == 0 else 0.0
