@@ -383,18 +383,41 @@ bool uses_winw(const pcad_chain *ch)
            pca_win_eligible(ch->dm);
 }
 
+// TMA descriptors of the two label planes and the observation (once).
+bool ensure_maps(pcad_chain *ch)
+{
+    if (!ch->maps_ready)
+        ch->maps_ready = encode_plane_map(&ch->xmap[0], ch->x[0], ch->H, ch->W, ch->pitch) &&
+                         encode_plane_map(&ch->xmap[1], ch->x[1], ch->H, ch->W, ch->pitch) &&
+                         encode_plane_map(&ch->gmap, ch->g, ch->H, ch->W, ch->pitch);
+    return ch->maps_ready;
+}
+
 // Unblocked PCA sweeps on the small-label kernel: on request, or with AUTO
 // for the models it accepts (3 <= L <= 16, c >= 0, L0 price) unless the
 // wavefront kernel is chosen (L = 16 at 1/2 to 3 waves of 4 x 32 tiles,
 // where the small-label kernel's 16 x 32 tiles leave SMs idle).  Measured on
-// GB300 at L = 16: 9.1e10 site-updates/s at 8192^2 and 6.6e10 at 1024^2
-// against 4.9e10 and 4.1e10 for the general per-sweep kernel; 3.2e10 at
-// 512^2 against 3.7e10 for the wavefront kernel.
+// GB300 at L = 16: 9.5e10 site-updates/s at 8192^2 (persistent tiles) and
+// 6.7e10 at 1024^2 against 4.9e10 and 4.1e10 for the general per-sweep
+// kernel; 3.2e10 at 512^2 against 3.7e10 for the wavefront kernel.
 bool uses_small(const pcad_chain *ch)
 {
     if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !pca_small_eligible(ch->dm))
         return false;
     return ch->kernel == PCAD_KERNEL_SMALL || (ch->kernel == PCAD_KERNEL_AUTO && !uses_wave(ch));
+}
+
+// The small-label kernel's launch form for large 4-neighbourhood images: one
+// sweep per launch on TMA-loaded 96 x 48 tiles (the temporally blocked kernel
+// at k = 1 with the small-label draw), from kSmallTmaMinSites sites.
+// Measured on GB300 at L = 16 (site-updates/s, tile form / persistent
+// 16 x 32 tiles): 8192^2 9.90e10 / 9.54e10, 6144^2 9.79e10 / 9.49e10,
+// 4096^2 9.39e10 / 9.40e10, 2048^2 8.28e10 / 9.02e10; with 8 neighbours at
+// 4096^2 the persistent form stays ahead (L = 5: 9.8e10 / 10.3e10).
+bool small_tma(const pcad_chain *ch)
+{
+    return ch->maps_ready && ch->model.nbhd == 4 && (long long)ch->H * ch->W >= kSmallTmaMinSites &&
+           uses_small(ch);
 }
 
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
@@ -496,7 +519,9 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
         if (ch->model.sampler == PCAD_SAMPLER_PCA) {
             a.xin = ch->x[cur];
             a.xout = ch->x[cur ^ 1];
-            if (uses_small(ch))
+            if (small_tma(ch))
+                CUDA_TRY(launch_pca_tb(ch->xmap[cur], ch->gmap, a, 1, ch->err, st));
+            else if (uses_small(ch))
                 CUDA_TRY(launch_pca_small(a, st));
             else if (uses_win(ch))
                 CUDA_TRY(launch_pca_win(a, ch->ftab, st));
@@ -689,6 +714,10 @@ pcad_status create_common(const uint8_t *g_src, bool g_on_device, int H, int W, 
     ch->dm.in64 = ch->in64;
     ch->dm.ptab = m->L <= kSmallMaxLabels ? ch->ptab : nullptr;
     ch->dm.btab = m->L == 2 ? ch->btab : nullptr;
+    // TMA descriptors of the planes for the small-label kernel's tile form
+    // (large images; temporal blocking encodes them on demand otherwise)
+    if (m->L <= kSmallMaxLabels && (long long)H * W >= kSmallTmaMinSites)
+        ensure_maps(ch);
     *out = ch;
     return PCAD_OK;
 }
@@ -804,7 +833,7 @@ pcad_status pcad_chain_sync(pcad_chain *ch)
     if (!ch)
         return fail(PCAD_EINVAL, "chain is NULL");
     CUDA_TRY(cudaStreamSynchronize(ch->stream));
-    if (ch->tb_k > 0 || uses_tc(ch) || uses_wave(ch) || uses_winw(ch)) {
+    if (ch->tb_k > 0 || uses_tc(ch) || uses_wave(ch) || uses_winw(ch) || small_tma(ch)) {
         int e = 0;
         CUDA_TRY(cudaMemcpy(&e, ch->err, sizeof(int), cudaMemcpyDeviceToHost));
         if (e == 2)
@@ -1139,13 +1168,8 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k)
         return fail(PCAD_EINVAL, "temporal blocking runs the L0 inertia price only");
     if (k > 0 && ch->track.trace)
         return fail(PCAD_ESTATE, "energy tracking needs every sweep's state: no temporal blocking");
-    if (k > 0 && !ch->maps_ready) {
-        if (!encode_plane_map(&ch->xmap[0], ch->x[0], ch->H, ch->W, ch->pitch) ||
-            !encode_plane_map(&ch->xmap[1], ch->x[1], ch->H, ch->W, ch->pitch) ||
-            !encode_plane_map(&ch->gmap, ch->g, ch->H, ch->W, ch->pitch))
-            return fail(PCAD_ECUDA, "TMA descriptor encoding failed");
-        ch->maps_ready = true;
-    }
+    if (k > 0 && !ensure_maps(ch))
+        return fail(PCAD_ECUDA, "TMA descriptor encoding failed");
     if (k != ch->tb_k && ch->graph) {
         cudaStreamSynchronize(ch->stream);
         cudaGraphExecDestroy(ch->graph);

@@ -341,6 +341,9 @@ bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);
 // the truncation T; the model's ptab points at it).
 constexpr int kSmallMinLabels = 3;
 constexpr int kSmallMaxLabels = 16;
+// From this many sites a 4-neighbourhood small-label chain sweeps on
+// TMA-loaded tiles (launch_pca_tb at k = 1) instead of the persistent kernel.
+constexpr long long kSmallTmaMinSites = 1ll << 25;
 int ptab_words();
 cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t s);
 bool pca_small_eligible(const DevModel &m);

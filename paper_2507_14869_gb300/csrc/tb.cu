@@ -12,11 +12,14 @@
 // identical labels.  Each thread accumulates its own output sites in
 // registers after every post-burn-in sweep; labels and the accumulator go
 // back to global memory once per k sweeps.  Every mbarrier wait is bounded:
-// on timeout the kernel records an error flag and returns.
+// on timeout the kernel records an error flag and returns.  Models the
+// small-label kernel accepts (3 <= L <= 16) draw with its pair table and
+// chunked CDF (small_draw.cuh); at k = 1 this is also that kernel's launch
+// form for large 4-neighbourhood images.
 #include <cuda.h>
 
 #include "async_ptx.cuh"
-#include "pcad_internal.h"
+#include "small_draw.cuh"
 
 namespace pcad {
 
@@ -47,6 +50,22 @@ __device__ __forceinline__ void site_from_box(const uint8_t *xp, const uint8_t *
     in.g = gp[lr * kBoxW + lc];
 }
 
+// Pair-table codes of site (lr, lc)'s neighbours for the small-label draw:
+// the label, or 16 outside the image.
+template <int NB>
+__device__ __forceinline__ void codes_from_box(const uint8_t *xp, int lr, int lc, int gr, int gc,
+                                               int H, int W, int (&nc)[NB])
+{
+    constexpr int dr[8] = {-1, 1, 0, 0, -1, -1, 1, 1};
+    constexpr int dc[8] = {0, 0, -1, 1, -1, 1, -1, 1};
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+        const int rr = gr + dr[j], cc = gc + dc[j];
+        const bool inside = rr >= 0 && rr < H && cc >= 0 && cc < W;
+        nc[j] = inside ? (int)xp[(lr + dr[j]) * kBoxW + lc + dc[j]] : 16;
+    }
+}
+
 template <int NC, int NB>
 __device__ __forceinline__ int tb_draw(const DevModel &m, bool valid, const SiteIn<NB> &in,
                                        float *Gcol, unsigned long long *fp64)
@@ -63,16 +82,26 @@ __device__ __forceinline__ int tb_draw(const DevModel &m, bool valid, const Site
 
 constexpr int kOwnMax = (kOutW * (kBoxH - 2) + kTbThreads - 1) / kTbThreads;   // 12
 
-template <int NC, int NB>
+// SL = 0: the general CUDA-core draw over NC chunks of 8 labels; SL = 8 or
+// 16: the small-label draw (labels < SL, MASK when L < SL) with the pair
+// table and a weight row per thread in shared memory.
+template <int NC, int NB, int SL, bool MASK>
 __global__ void __launch_bounds__(kTbThreads)
     pca_tb_kernel(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap gmap,
                   const SweepArgs a, int k, int *err)
 {
     __shared__ __align__(128) uint8_t xs[2][kPlane];
     __shared__ __align__(128) uint8_t gs[kPlane];
-    __shared__ float G_s[NC * kTbThreads];
+    __shared__ float G_s[SL > 0 ? 1 : NC * kTbThreads];
+    __shared__ __align__(16) uint32_t pt[SL > 0 ? sld::kPtabWords : 4];
+    __shared__ __align__(16) float pre_s[SL > 0 ? kTbThreads * sld::kPrefixStride : 4];
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
+    if constexpr (SL > 0) {   // ordered before use by the barrier after the loads
+        for (int i = tid; i < sld::kPtabWords / 4; i += kTbThreads)
+            reinterpret_cast<uint4 *>(pt)[i] =
+                __ldg(reinterpret_cast<const uint4 *>(a.m.ptab) + i);
+    }
     const int TH = kBoxH - 2 * k;
     const int x0 = blockIdx.x * kOutW, y0 = blockIdx.y * TH;
     const int bx = x0 - kColOff, by = y0 - k;       // global origin of the box
@@ -132,13 +161,37 @@ __global__ void __launch_bounds__(kTbThreads)
                 const int lc = lcg + q, gc = gc0 + q;
                 const bool valid = pvalid && lc >= c_lo && lc < c_hi && gr >= 0 && gr < a.H &&
                                    gc >= 0 && gc < a.W;
-                SiteIn<NB> in{};
-                if (valid) {
-                    site_from_box<NB>(xp, gs, lr, lc, gr, gc, a.H, a.W, in);
-                    const uint32_t w = q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
-                    in.ub = w >> 8;
+                const uint32_t w = q == 0 ? w0 : (q == 1 ? w1 : (q == 2 ? w2 : w3));
+                int s = 0;
+                if constexpr (SL > 0) {
+                    int nc[NB];
+                    int xi = 0, gv = 0;
+                    bool certain = true;
+                    if (valid) {
+                        codes_from_box<NB>(xp, lr, lc, gr, gc, a.H, a.W, nc);
+                        xi = xp[lr * kBoxW + lc];
+                        gv = gs[lr * kBoxW + lc];
+                        s = sld::draw_small<SL, NB, MASK>(a.m, pt, nc, gv, xi, w >> 8,
+                                                         pre_s + tid * sld::kPrefixStride,
+                                                         certain);
+                    }
+                    const bool need = valid && !certain;
+                    if (__any_sync(0xFFFFFFFFu, need)) {
+                        SiteIn<NB> in{};
+                        if (valid) {
+                            site_from_box<NB>(xp, gs, lr, lc, gr, gc, a.H, a.W, in);
+                            in.ub = w >> 8;
+                        }
+                        s = warp_redraw_fp64<NB>(a.m, need, in, s, a.fp64_draws);
+                    }
+                } else {
+                    SiteIn<NB> in{};
+                    if (valid) {
+                        site_from_box<NB>(xp, gs, lr, lc, gr, gc, a.H, a.W, in);
+                        in.ub = w >> 8;
+                    }
+                    s = tb_draw<NC, NB>(a.m, valid, in, G_s + tid, a.fp64_draws);
                 }
-                const int s = tb_draw<NC, NB>(a.m, valid, in, G_s + tid, a.fp64_draws);
                 if (valid)
                     xo[lr * kBoxW + lc] = (uint8_t)s;
             }
@@ -172,15 +225,28 @@ cudaError_t dispatch_tb(const CUtensorMap &xm, const CUtensorMap &gm, const Swee
                         int *err, cudaStream_t s)
 {
     const dim3 grid((a.W + kOutW - 1) / kOutW, (a.H + (kBoxH - 2 * k) - 1) / (kBoxH - 2 * k));
+    if (pca_small_eligible(a.m)) {   // the small-label draw, as the unblocked default
+        if (a.m.L <= 8) {
+            if (a.m.L == 8)
+                pca_tb_kernel<1, NB, 8, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err);
+            else
+                pca_tb_kernel<1, NB, 8, true><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err);
+        } else if (a.m.L == 16) {
+            pca_tb_kernel<1, NB, 16, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err);
+        } else {
+            pca_tb_kernel<1, NB, 16, true><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err);
+        }
+        return cudaGetLastError();
+    }
     switch (chunk_class(a.m.L)) {
-    case 1: pca_tb_kernel<1, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    case 2: pca_tb_kernel<2, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    case 3: pca_tb_kernel<3, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    case 4: pca_tb_kernel<4, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    case 5: pca_tb_kernel<5, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    case 8: pca_tb_kernel<8, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    case 16: pca_tb_kernel<16, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
-    default: pca_tb_kernel<32, NB><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 1: pca_tb_kernel<1, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 2: pca_tb_kernel<2, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 3: pca_tb_kernel<3, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 4: pca_tb_kernel<4, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 5: pca_tb_kernel<5, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 8: pca_tb_kernel<8, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    case 16: pca_tb_kernel<16, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
+    default: pca_tb_kernel<32, NB, 0, false><<<grid, kTbThreads, 0, s>>>(xm, gm, a, k, err); break;
     }
     return cudaGetLastError();
 }

@@ -108,3 +108,25 @@ def test_small_kernel_with_energy_tracking_and_blocking(pc):
             res.append((ch.sample(), ch.mean()))
     for x, mu in res[1:]:
         assert np.array_equal(x, res[0][0]) and np.array_equal(mu, res[0][1])
+
+
+def test_tile_form_for_large_images_equals_general_kernel(pc):
+    """From 2^25 sites a 4-neighbourhood small-label chain sweeps on
+    TMA-loaded tiles (the blocked kernel at k = 1 with the small-label draw);
+    it stays the small-label kernel for AUTO and SMALL, and its labels and
+    means equal the general kernel's (100 M draws, ragged tiles)."""
+    from pcad_inputs import large_image
+    _, g8, m = large_image(L=16)
+    g = np.ascontiguousarray(g8[:5801, :5790])
+    assert g.size >= 1 << 25
+    outs = {}
+    for kind in (0, SMALL, CUDA_CORE):
+        with pc.Chain(g, m, seed=5, chain_id=3, burn_in=1) as ch:
+            ch.set_kernel(kind)
+            assert ch.kernel_in_use() == (CUDA_CORE if kind == CUDA_CORE else SMALL)
+            ch.run(3)
+            ch.sync()
+            outs[kind] = (ch.sample(), ch.mean())
+    for kind in (0, SMALL):
+        assert np.array_equal(outs[kind][0], outs[CUDA_CORE][0])
+        assert np.array_equal(outs[kind][1], outs[CUDA_CORE][1])
