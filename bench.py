@@ -56,8 +56,8 @@ HBM_PEAK_FALLBACK = 6800.0   # GB/s, used only if MEASURED_PEAKS.json is absent
 # (profiles/); None until the current kernel is captured.  The tensor-core
 # figure is one 32-sweep launch at 4096^2 (planes, observation and
 # accumulator exceed L2); the small-label figure one accumulating per-sweep
-# launch at 8192^2 L = 16; the per-sweep CUDA-core kernel has no current
-# capture at 8192^2.
+# launch of its TMA-tile form at 8192^2 L = 16; the per-sweep CUDA-core
+# kernel has no current capture at 8192^2.
 NCU_TC_BYTES_PER_SITE = (3.213934e9 + 2.634401e9) / (32 * 4096 * 4096)
 NCU_TC_NOTE = ("ncu dram__bytes_read+write of one accumulating 32-sweep pca_tcw_kernel launch "
                "at 4096^2 L=256 (profiles/pca_tc_l256_4096sq.md), scaled by sites to 8192^2")
@@ -66,9 +66,10 @@ NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at
 NCU_WIN_BYTES_PER_SITE = (402903040 + 286483712) / (8192 * 8192)
 NCU_WIN_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_win_kernel launch at "
                 "8192^2 L=256 (profiles/pca_win_l256_8192sq.md)")
-NCU_SMALL_BYTES_PER_SITE = (407.3e6 + 282.3e6) / (8192 * 8192)
-NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_small_kernel launch at "
-                  "8192^2 L=16 (profiles/pca_small_l16_4096sq.md)")
+NCU_SMALL_BYTES_PER_SITE = (402707456 + 281261056) / (8192 * 8192)
+NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_tb_kernel<1,4,16,0> launch "
+                  "(the small-label draw on TMA tiles) at 8192^2 L=16 "
+                  "(profiles/pca_tb_small_l16_6144sq.md)")
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5,
                 "window": 6, "window_wave": 7}
@@ -77,7 +78,8 @@ KERNEL_NAMES = {
     2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
        "one launch per 32 sweeps)",
     3: "pca_wave_kernel (CUDA cores, wavefront, one launch per 32 sweeps)",
-    4: "pca_small_kernel (CUDA cores, prior sums from a pair table, one launch per sweep)",
+    4: "small-label draw (CUDA cores, prior sums from a pair table, one launch per sweep; "
+       "pca_tb_kernel on TMA-loaded 96x48 tiles from 2^25 sites, else pca_small_kernel)",
     5: "resident_kernel (two labels, whole run in one single-CTA launch, state in shared "
        "memory, exact per-configuration thresholds)",
     6: "pca_win_kernel (CUDA cores, hull chunks from a tent-byte table, one launch per sweep)",
