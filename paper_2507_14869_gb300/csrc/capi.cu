@@ -416,8 +416,9 @@ bool uses_small(const pcad_chain *ch)
 // 4096^2 the persistent form stays ahead (L = 5: 9.8e10 / 10.3e10).
 bool small_tma(const pcad_chain *ch)
 {
+    // tiles of 46 rows: the launch grid's second dimension is at most 65535
     return ch->maps_ready && ch->model.nbhd == 4 && (long long)ch->H * ch->W >= kSmallTmaMinSites &&
-           uses_small(ch);
+           (ch->H + 45) / 46 <= 65535 && uses_small(ch);
 }
 
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
