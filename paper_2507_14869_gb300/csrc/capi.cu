@@ -523,7 +523,8 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
             if (small_tma(ch))
                 CUDA_TRY(launch_pca_tb(ch->xmap[cur], ch->gmap, a, 1, ch->err, st));
             else if (uses_small(ch))
-                CUDA_TRY(launch_pca_small(a, st));
+                // chains check g < L at creation: the data term from a table
+                CUDA_TRY(launch_pca_small(a, st, nullptr, nullptr, nullptr, true));
             else if (uses_win(ch))
                 CUDA_TRY(launch_pca_win(a, ch->ftab, st));
             else

@@ -348,9 +348,12 @@ int ptab_words();
 cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t s);
 bool pca_small_eligible(const DevModel &m);
 // x0 / x1 (optional): the planes of even / odd sweep indices, used in place of
-// a.xin / a.xout; budget (optional): sweeps with index >= *budget are skipped.
+// a.xin / a.xout; budget (optional): sweeps with index >= *budget are skipped;
+// aq: the data term from a table of the observations g < 16 (callers whose
+// observations were checked against L).
 cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s, uint8_t *x0 = nullptr,
-                             uint8_t *x1 = nullptr, const uint32_t *budget = nullptr);
+                             uint8_t *x1 = nullptr, const uint32_t *budget = nullptr,
+                             bool aq = false);
 
 // Whole chains of small two-label images in one CTA (state in shared
 // memory): L = 2, 4 or 8 neighbours, the thresholds table m.btab built, at

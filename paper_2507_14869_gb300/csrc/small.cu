@@ -17,7 +17,10 @@
 //     2^fl(alpha q + fl(gam P)), q = (g - s)^2 and P exact integers, two
 //     labels per packed FP32x2 instruction (every lane rounds as the scalar
 //     operation).  A byte of P becomes an exact float by placing it in the
-//     mantissa of 2^23 and subtracting 2^23.  (Products of two table
+//     mantissa of 2^23 and subtracting 2^23.  Chains (whose observations are
+//     checked against L at creation) take fl(alpha q) from a 16 x 16 table in
+//     shared memory instead: one FFMA per label, fl(gam P + fl(alpha q)),
+//     within the same 3u |v| exponent bound; batches keep the arithmetic form.  (Products of two table
 //     factors per label measured slower: the per-lane table reads conflict
 //     in shared memory, while the exponential unit has room.)
 //   * Inverse CDF over chunks of 4 labels: in-chunk prefix sums (3
@@ -77,7 +80,7 @@ __global__ void ptab_kernel(int T, uint32_t *out)
 // planes: a.xin -> a.xout, or (par_from_t) x0 / x1 holding the states of
 // even / odd sweep indices; budget (optional): sweeps with index >= *budget
 // are skipped (a chain of a batch or of the server).
-template <int LMAX, int NB, bool MASK>
+template <int LMAX, int NB, bool MASK, bool AQ>
 __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, int tiles_x,
                                                              int ntiles, uint8_t *x0, uint8_t *x1,
                                                              int par_from_t,
@@ -87,10 +90,13 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
     __shared__ __align__(16) uint32_t U_s[kWarps * kSPT * kBX];
     __shared__ __align__(16) uint32_t codes[kCodeWords];
     __shared__ __align__(16) float pre_s[kThreads * kPrefixStride];
+    __shared__ __align__(16) float aq_s[AQ ? 16 * kAqStride : 4];
     const int lane = (int)threadIdx.x, wp = (int)threadIdx.y;
     const int tid = wp * kBX + lane;
     for (int i = tid; i < kPtabWords / 4; i += kThreads)
         reinterpret_cast<uint4 *>(pt)[i] = __ldg(reinterpret_cast<const uint4 *>(a.m.ptab) + i);
+    if (AQ)   // ordered before use by the tile loop's first barrier
+        fill_aq(a.m, aq_s, tid, kThreads);
     const uint32_t t = sweep_index(a);
     if (budget && t >= *budget)
         return;   // the whole launch: before any barrier
@@ -168,7 +174,7 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
             int s = 0;
             bool certain = true;
             if (valid)
-                s = draw_small<LMAX, NB, MASK>(a.m, pt, nc, g[i], xi, ub, pre, certain);
+                s = draw_small<LMAX, NB, MASK, AQ>(a.m, pt, nc, g[i], xi, ub, pre, certain, aq_s);
             const bool need = valid && !certain;
             if (__any_sync(0xFFFFFFFFu, need)) {
                 SiteIn<NB> in{};
@@ -195,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) pca_small_kernel(const SweepArgs a, 
     }
 }
 
-template <int LMAX, int NB, bool MASK>
+template <int LMAX, int NB, bool MASK, bool AQ>
 cudaError_t launch_small_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int par_from_t,
                            const uint32_t *budget, cudaStream_t st)
 {
@@ -208,7 +214,7 @@ cudaError_t launch_small_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int par
         return cudaErrorInvalidDevice;
     if (per_sm[dev] == 0) {
         int n = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pca_small_kernel<LMAX, NB, MASK>,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pca_small_kernel<LMAX, NB, MASK, AQ>,
                                                           kThreads, 0);
         if (e != cudaSuccess)
             return e;
@@ -226,20 +232,20 @@ cudaError_t launch_small_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int par
         return cudaErrorInvalidValue;
     const long long cap = (long long)per_sm[dev] * sms;
     const int grid = (int)(ntiles < cap ? ntiles : cap);
-    pca_small_kernel<LMAX, NB, MASK><<<grid, dim3(kBX, kWarps), 0, st>>>(
+    pca_small_kernel<LMAX, NB, MASK, AQ><<<grid, dim3(kBX, kWarps), 0, st>>>(
         a, tiles_x, (int)ntiles, x0, x1, par_from_t, budget);
     return cudaGetLastError();
 }
 
-template <int NB>
+template <int NB, bool AQ>
 cudaError_t dispatch_small(const SweepArgs &a, uint8_t *x0, uint8_t *x1, int par_from_t,
                            const uint32_t *budget, cudaStream_t st)
 {
     if (a.m.L <= 8)
-        return a.m.L == 8 ? launch_small_t<8, NB, false>(a, x0, x1, par_from_t, budget, st)
-                          : launch_small_t<8, NB, true>(a, x0, x1, par_from_t, budget, st);
-    return a.m.L == 16 ? launch_small_t<16, NB, false>(a, x0, x1, par_from_t, budget, st)
-                       : launch_small_t<16, NB, true>(a, x0, x1, par_from_t, budget, st);
+        return a.m.L == 8 ? launch_small_t<8, NB, false, AQ>(a, x0, x1, par_from_t, budget, st)
+                          : launch_small_t<8, NB, true, AQ>(a, x0, x1, par_from_t, budget, st);
+    return a.m.L == 16 ? launch_small_t<16, NB, false, AQ>(a, x0, x1, par_from_t, budget, st)
+                       : launch_small_t<16, NB, true, AQ>(a, x0, x1, par_from_t, budget, st);
 }
 
 }  // namespace
@@ -263,7 +269,7 @@ bool pca_small_eligible(const DevModel &m)
 }
 
 cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t st, uint8_t *x0, uint8_t *x1,
-                             const uint32_t *budget)
+                             const uint32_t *budget, bool aq)
 {
     if (!pca_small_eligible(a.m))
         return cudaErrorInvalidValue;
@@ -273,8 +279,11 @@ cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t st, uint8_t *x0, u
                                 : reinterpret_cast<uintptr_t>(a.xin);
     if ((a.pitch & 3) != 0 || (align & 3u) != 0)
         return cudaErrorMisalignedAddress;
-    return a.m.nbhd == 8 ? dispatch_small<8>(a, x0, x1, par, budget, st)
-                         : dispatch_small<4>(a, x0, x1, par, budget, st);
+    if (aq)
+        return a.m.nbhd == 8 ? dispatch_small<8, true>(a, x0, x1, par, budget, st)
+                             : dispatch_small<4, true>(a, x0, x1, par, budget, st);
+    return a.m.nbhd == 8 ? dispatch_small<8, false>(a, x0, x1, par, budget, st)
+                         : dispatch_small<4, false>(a, x0, x1, par, budget, st);
 }
 
 }  // namespace pcad

@@ -13,15 +13,31 @@ namespace sld {
 constexpr int kCodes = 17;                       // labels 0..15 and "missing"
 constexpr int kPtabWords = kCodes * kCodes * 4;  // 16 bytes per pair
 constexpr int kPrefixStride = 20;                // floats per thread row (conflict-free)
+constexpr int kAqStride = 20;                    // floats per row of the data-term table
+
+// Row g of the data-term table: fl(alpha (g - s)^2) for s = 0..15 (observations
+// g < 16; every chain checks g < L at creation).
+__device__ __forceinline__ void fill_aq(const DevModel &m, float *aq, int tid, int nthreads)
+{
+    for (int i = tid; i < 16 * 16; i += nthreads) {
+        const int g = i >> 4, sl = i & 15;
+        aq[g * kAqStride + sl] = __fmul_rn(m.alpha, (float)((g - sl) * (g - sl)));
+    }
+}
 
 // The draw of one site from its neighbour codes nc[] and observation g.
 // Returns the label; `certain` is false when the uniform lies within the
 // certified margin of the chosen label's CDF interval (the caller re-draws
 // it in FP64).  pt: the pair table in shared memory; pre: this thread's row
-// of shared memory (kPrefixStride floats), which receives the weights.
-template <int LMAX, int NB, bool MASK>
+// of shared memory (kPrefixStride floats), which receives the weights.  AQ:
+// the data term from the table aq (fill_aq; g < 16), the exponent
+// fl(gam P + fl(alpha q)) in one FFMA per label; otherwise
+// fl(alpha q + fl(gam P)).  Both terms are non-positive, so either form is
+// within 3u |v| of the exact exponent, the per-site margin's bound.
+template <int LMAX, int NB, bool MASK, bool AQ = false>
 __device__ __forceinline__ int draw_small(const DevModel &m, const uint32_t *pt, const int (&nc)[NB],
-                                          int g, int xi, uint32_t ub, float *pre, bool &certain)
+                                          int g, int xi, uint32_t ub, float *pre, bool &certain,
+                                          const float *aq = nullptr)
 {
     constexpr int NW = LMAX / 4;      // table words used per pair = chunks of 4 labels
     uint32_t P[NW];
@@ -67,6 +83,7 @@ __device__ __forceinline__ int draw_small(const DevModel &m, const uint32_t *pt,
     const float2 off2 = make_float2(-8388608.0f, -8388608.0f);
     const float2 gg = make_float2(gf, gf);
     float w[LMAX];
+    float4 aq4 = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll
     for (int s = 0; s < LMAX; s += 2) {
         const uint32_t p = P[s >> 2];
@@ -74,8 +91,16 @@ __device__ __forceinline__ int draw_small(const DevModel &m, const uint32_t *pt,
             __uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)(s & 3))),
             __uint_as_float(__byte_perm(p, 0x4B000000u, 0x7440u | (uint32_t)((s + 1) & 3))));
         const float2 Pf = __fadd2_rn(pm, off2);
-        const float2 dg = __fadd2_rn(gg, make_float2(-(float)s, -(float)(s + 1)));
-        const float2 v = __ffma2_rn(a2, __fmul2_rn(dg, dg), __fmul2_rn(g2, Pf));
+        float2 v;
+        if constexpr (AQ) {
+            if ((s & 3) == 0)
+                aq4 = *reinterpret_cast<const float4 *>(aq + g * kAqStride + s);
+            v = __ffma2_rn(g2, Pf, (s & 3) == 0 ? make_float2(aq4.x, aq4.y)
+                                                : make_float2(aq4.z, aq4.w));
+        } else {
+            const float2 dg = __fadd2_rn(gg, make_float2(-(float)s, -(float)(s + 1)));
+            v = __ffma2_rn(a2, __fmul2_rn(dg, dg), __fmul2_rn(g2, Pf));
+        }
         w[s] = ex2_ftz(v.x);
         w[s + 1] = ex2_ftz(v.y);
         if (MASK) {

@@ -95,12 +95,14 @@ __global__ void __launch_bounds__(kTbThreads)
     __shared__ float G_s[SL > 0 ? 1 : NC * kTbThreads];
     __shared__ __align__(16) uint32_t pt[SL > 0 ? sld::kPtabWords : 4];
     __shared__ __align__(16) float pre_s[SL > 0 ? kTbThreads * sld::kPrefixStride : 4];
+    __shared__ __align__(16) float aq_s[SL > 0 ? 16 * sld::kAqStride : 4];
     __shared__ __align__(8) uint64_t bar;
     const int tid = threadIdx.x;
     if constexpr (SL > 0) {   // ordered before use by the barrier after the loads
         for (int i = tid; i < sld::kPtabWords / 4; i += kTbThreads)
             reinterpret_cast<uint4 *>(pt)[i] =
                 __ldg(reinterpret_cast<const uint4 *>(a.m.ptab) + i);
+        sld::fill_aq(a.m, aq_s, tid, kTbThreads);   // chains hold observations g < L <= 16
     }
     const int TH = kBoxH - 2 * k;
     const int x0 = blockIdx.x * kOutW, y0 = blockIdx.y * TH;
@@ -171,9 +173,9 @@ __global__ void __launch_bounds__(kTbThreads)
                         codes_from_box<NB>(xp, lr, lc, gr, gc, a.H, a.W, nc);
                         xi = xp[lr * kBoxW + lc];
                         gv = gs[lr * kBoxW + lc];
-                        s = sld::draw_small<SL, NB, MASK>(a.m, pt, nc, gv, xi, w >> 8,
-                                                         pre_s + tid * sld::kPrefixStride,
-                                                         certain);
+                        s = sld::draw_small<SL, NB, MASK, true>(
+                            a.m, pt, nc, gv, xi, w >> 8, pre_s + tid * sld::kPrefixStride,
+                            certain, aq_s);
                     }
                     const bool need = valid && !certain;
                     if (__any_sync(0xFFFFFFFFu, need)) {

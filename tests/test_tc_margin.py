@@ -66,7 +66,10 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
         # kernel's pair table): it contributes nothing
         P = (np.where(present[:, :, None], np.minimum(np.abs(s[None, None, :] - x[:, :, None]), T),
                       T if form == "cc" else 0)).sum(1)
-        v = _fma32(alpha, q, (f64(gam) * P).astype(f32))
+        if form == "small_aq":   # the data term from a table: fl(gam P + fl(alpha q))
+            v = _fma32(gam, P, (f64(alpha) * q).astype(f32))
+        else:
+            v = _fma32(alpha, q, (f64(gam) * P).astype(f32))
     # ex2 within 2 ulp: correctly rounded, moved by 2u up for labels <= the
     # split and down above it, rounded again
     w = np.exp2(v.astype(f64)).astype(f32)
@@ -97,7 +100,7 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
         comp = (tt - G) - y
         G = tt
         Gc[:, c] = G
-    if form == "small":
+    if form.startswith("small"):
         # chunks of 4 labels: in-chunk sequential prefix, sequential chunk
         # prefix, no compensation
         nc = (L + 3) // 4
@@ -117,7 +120,7 @@ def _worst_error(mg, model, x, present, g, xi, sign_split, form="tc"):
     delta = (w[np.arange(n), xi].astype(f64) * f64(em1)).astype(f32) if lam > 0 else np.zeros(n, f32)
     Z = (G + delta).astype(f32)
     Gprev = np.concatenate([np.zeros((n, 1), f32), Gc[:, :-1]], axis=1)
-    if form == "small":
+    if form.startswith("small"):
         # the small-label kernel joins the in-chunk prefix to Gprev or to
         # fl(Gprev + delta) (at and above x_i)
         Gp = np.repeat(Gprev, 4, axis=1)[:, :L]
@@ -197,10 +200,12 @@ SMALL_MODELS = [
 ]
 
 
+@pytest.mark.parametrize("form", ["small", "small_aq"])
 @pytest.mark.parametrize("i", range(len(SMALL_MODELS)))
-def test_margin_covers_the_small_label_kernel(pc, i):
+def test_margin_covers_the_small_label_kernel(pc, i, form):
     """The small-label kernel: the same weight formula with a missing
-    neighbour contributing nothing, chunks of 4 labels summed without
+    neighbour contributing nothing (or, on TMA tiles, the data term from a
+    table: fl(gam P + fl(alpha q))), chunks of 4 labels summed without
     compensation -- inside the same per-site margin."""
     model = dict(SMALL_MODELS[i])
     model["T"] = 1 if model["pair"] == 0 else model["pair_T"]
@@ -215,9 +220,9 @@ def test_margin_covers_the_small_label_kernel(pc, i):
         elif split_kind == 1:
             split = np.full(len(g), model["L"])
         else:
-            _, _, Fk = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1), "small")
+            _, _, Fk = _worst_error(mg, model, x, present, g, xi, np.full(len(g), -1), form)
             split = (Fk < 0.5).sum(1)
-        err, eta, _ = _worst_error(mg, model, x, present, g, xi, split, "small")
+        err, eta, _ = _worst_error(mg, model, x, present, g, xi, split, form)
         bound = eta / 1.5 - U
         assert np.all(err <= bound), (float(err.max()), float(bound[np.argmax(err / bound)]))
         worst = max(worst, float((err / bound).max()))
