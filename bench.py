@@ -66,10 +66,9 @@ NCU_DIRECT_NOTE = "ncu dram__bytes_read+write of one pca_direct_kernel launch at
 NCU_WIN_BYTES_PER_SITE = (402903040 + 286483712) / (8192 * 8192)
 NCU_WIN_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_win_kernel launch at "
                 "8192^2 L=256 (profiles/pca_win_l256_8192sq.md)")
-NCU_SMALL_BYTES_PER_SITE = (402707456 + 281261056) / (8192 * 8192)
-NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_tb_kernel<1,4,16,0> launch "
-                  "(the small-label draw on TMA tiles) at 8192^2 L=16 "
-                  "(profiles/pca_tb_small_l16_6144sq.md)")
+NCU_SMALL_BYTES_PER_SITE = (408240384 + 280811264) / (8192 * 8192)
+NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_small_tma_kernel launch "
+                  "at 8192^2 L=16 (profiles/pca_small_tma_l16_6144sq.md)")
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5,
                 "window": 6, "window_wave": 7}
@@ -79,7 +78,7 @@ KERNEL_NAMES = {
        "one launch per 32 sweeps)",
     3: "pca_wave_kernel (CUDA cores, wavefront, one launch per 32 sweeps)",
     4: "small-label draw (CUDA cores, prior sums from a pair table, one launch per sweep; "
-       "pca_tb_kernel on TMA-loaded 96x48 tiles from 2^25 sites, else pca_small_kernel)",
+       "pca_small_tma_kernel on TMA-loaded tiles from 2^23 sites, else pca_small_kernel)",
     5: "resident_kernel (two labels, whole run in one single-CTA launch, state in shared "
        "memory, exact per-configuration thresholds)",
     6: "pca_win_kernel (CUDA cores, hull chunks from a tent-byte table, one launch per sweep)",

@@ -169,10 +169,11 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * PCAD_EINVAL otherwise) runs one launch per sweep that takes the prior sums
  * of all labels of a site from a table of neighbour pairs (16 bytes per pair
  * of labels, in shared memory) and draws from chunk prefix sums in
- * registers; same labels as the other kernels.  Images of at least 2^25
- * sites with the 4-neighbourhood sweep on TMA-loaded 96 x 48 tiles (the
- * temporally blocked kernel at one sweep per launch), smaller ones on
- * persistent 16 x 32 tiles.  AUTO takes it for every model it accepts.  PCAD_KERNEL_RESIDENT (L = 2, 4- or 8-neighbourhood,
+ * registers; same labels as the other kernels.  Images of at least 2^23
+ * sites sweep on TMA-loaded 64 x 46 tiles in persistent blocks (the next
+ * tile's copy in flight during the draw), smaller ones on persistent
+ * 16 x 32 tiles staged by the threads.  AUTO takes it for every model it
+ * accepts.  PCAD_KERNEL_RESIDENT (L = 2, 4- or 8-neighbourhood,
  * either sampler, H * ceil(W / 4) <= 4096, e.g. up to 128 x 128, and at most
  * 200 KB of shared memory; PCAD_EINVAL otherwise) runs all the sweeps of a
  * run in one launch of one 1024-thread CTA that keeps the state in shared

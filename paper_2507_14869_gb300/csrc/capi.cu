@@ -407,18 +407,17 @@ bool uses_small(const pcad_chain *ch)
     return ch->kernel == PCAD_KERNEL_SMALL || (ch->kernel == PCAD_KERNEL_AUTO && !uses_wave(ch));
 }
 
-// The small-label kernel's launch form for large 4-neighbourhood images: one
-// sweep per launch on TMA-loaded 96 x 48 tiles (the temporally blocked kernel
-// at k = 1 with the small-label draw), from kSmallTmaMinSites sites.
-// Measured on GB300 at L = 16 (site-updates/s, tile form / persistent
-// 16 x 32 tiles): 8192^2 9.90e10 / 9.54e10, 6144^2 9.79e10 / 9.49e10,
-// 4096^2 9.39e10 / 9.40e10, 2048^2 8.28e10 / 9.02e10; with 8 neighbours at
-// 4096^2 the persistent form stays ahead (L = 5: 9.8e10 / 10.3e10).
+// The small-label kernel's launch form for large images: persistent blocks
+// over TMA-loaded 64 x 46 tiles, the next tile's box in flight during the
+// draw (launch_pca_small_tma), from kSmallTmaMinSites sites.  Measured on
+// GB300 at L = 16 (site-updates/s, TMA tiles / persistent 16 x 32 tiles):
+// 8192^2 1.049e11 / 0.954e11, 4096^2 1.015e11 / 0.953e11, 3072^2
+// 0.997e11 / 0.959e11, 2048^2 0.931e11 / 0.926e11, 1024^2 0.588e11 /
+// 0.691e11; 8 neighbours at 4096^2: L = 5 10.9e10 / 10.4e10, L = 16
+// 9.5e10 / 9.1e10.
 bool small_tma(const pcad_chain *ch)
 {
-    // tiles of 46 rows: the launch grid's second dimension is at most 65535
-    return ch->maps_ready && ch->model.nbhd == 4 && (long long)ch->H * ch->W >= kSmallTmaMinSites &&
-           (ch->H + 45) / 46 <= 65535 && uses_small(ch);
+    return ch->maps_ready && (long long)ch->H * ch->W >= kSmallTmaMinSites && uses_small(ch);
 }
 
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
@@ -521,7 +520,7 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
             a.xin = ch->x[cur];
             a.xout = ch->x[cur ^ 1];
             if (small_tma(ch))
-                CUDA_TRY(launch_pca_tb(ch->xmap[cur], ch->gmap, a, 1, ch->err, st));
+                CUDA_TRY(launch_pca_small_tma(ch->xmap[cur], ch->gmap, a, ch->err, st));
             else if (uses_small(ch))
                 // chains check g < L at creation: the data term from a table
                 CUDA_TRY(launch_pca_small(a, st, nullptr, nullptr, nullptr, true));

@@ -341,12 +341,18 @@ bool encode_plane_map(CUtensorMap *map, void *base, int H, int W, int pitch);
 // the truncation T; the model's ptab points at it).
 constexpr int kSmallMinLabels = 3;
 constexpr int kSmallMaxLabels = 16;
-// From this many sites a 4-neighbourhood small-label chain sweeps on
-// TMA-loaded tiles (launch_pca_tb at k = 1) instead of the persistent kernel.
-constexpr long long kSmallTmaMinSites = 1ll << 25;
+// From this many sites a small-label chain sweeps on TMA-loaded tiles
+// (launch_pca_small_tma) instead of 16 x 32 staged tiles.
+constexpr long long kSmallTmaMinSites = 1ll << 23;
 int ptab_words();
 cudaError_t launch_ptab(int T, uint32_t *out, cudaStream_t s);
 bool pca_small_eligible(const DevModel &m);
+// One small-label sweep a.xin -> a.xout on TMA-loaded tiles (persistent,
+// double-buffered): xmap, gmap the maps of a.xin and of the observation
+// (encode_plane_map); the data term from a table, so observations g < L; a
+// bounded wait that runs out sets *err.
+cudaError_t launch_pca_small_tma(const CUtensorMap &xmap, const CUtensorMap &gmap,
+                                 const SweepArgs &a, int *err, cudaStream_t s);
 // x0 / x1 (optional): the planes of even / odd sweep indices, used in place of
 // a.xin / a.xout; budget (optional): sweeps with index >= *budget are skipped;
 // aq: the data term from a table of the observations g < 16 (callers whose

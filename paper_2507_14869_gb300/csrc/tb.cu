@@ -14,8 +14,7 @@
 // back to global memory once per k sweeps.  Every mbarrier wait is bounded:
 // on timeout the kernel records an error flag and returns.  Models the
 // small-label kernel accepts (3 <= L <= 16) draw with its pair table and
-// chunked CDF (small_draw.cuh); at k = 1 this is also that kernel's launch
-// form for large 4-neighbourhood images.
+// chunked CDF (small_draw.cuh).
 #include <cuda.h>
 
 #include "async_ptx.cuh"

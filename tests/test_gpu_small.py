@@ -110,15 +110,28 @@ def test_small_kernel_with_energy_tracking_and_blocking(pc):
         assert np.array_equal(x, res[0][0]) and np.array_equal(mu, res[0][1])
 
 
-def test_tile_form_for_large_images_equals_general_kernel(pc):
-    """From 2^25 sites a 4-neighbourhood small-label chain sweeps on
-    TMA-loaded tiles (the blocked kernel at k = 1 with the small-label draw);
-    it stays the small-label kernel for AUTO and SMALL, and its labels and
-    means equal the general kernel's (100 M draws, ragged tiles)."""
+TILE_CASES = [
+    # 4 neighbours, W % 4 != 0 (scalar accumulator updates), ragged tiles
+    ("L16_5801x5790", lambda: np.ascontiguousarray(_big16()[:5801, :5790]),
+     Model(L=16, pair=1, pair_coef=0.05, pair_T=30, sigma=1.0, inertia=2.0)),
+    # 8 neighbours, masked labels, W % 4 == 0 (float4 accumulator updates)
+    ("L12_8nb_2901x2900", lambda: _grey(94, 2901, 2900, 12, 1.5),
+     Model(L=12, nbhd=8, pair=1, pair_coef=0.3, pair_T=4, sigma=1.5, inertia=1.0)),
+]
+
+
+def _big16():
     from pcad_inputs import large_image
-    _, g8, m = large_image(L=16)
-    g = np.ascontiguousarray(g8[:5801, :5790])
-    assert g.size >= 1 << 25
+    return large_image(L=16)[1]
+
+
+@pytest.mark.parametrize("name,make,m", TILE_CASES, ids=[c[0] for c in TILE_CASES])
+def test_tile_form_for_large_images_equals_general_kernel(pc, name, make, m):
+    """From 2^23 sites a small-label chain sweeps on TMA-loaded tiles
+    (persistent, double-buffered); it stays the small-label kernel for AUTO
+    and SMALL, and its labels and means equal the general kernel's."""
+    g = make()
+    assert g.size >= 1 << 23
     outs = {}
     for kind in (0, SMALL, CUDA_CORE):
         with pc.Chain(g, m, seed=5, chain_id=3, burn_in=1) as ch:
