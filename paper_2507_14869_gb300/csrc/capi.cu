@@ -397,9 +397,9 @@ bool ensure_maps(pcad_chain *ch)
 // for the models it accepts (3 <= L <= 16, c >= 0, L0 price) unless the
 // wavefront kernel is chosen (L = 16 at 1/2 to 3 waves of 4 x 32 tiles,
 // where the small-label kernel's 16 x 32 tiles leave SMs idle).  Measured on
-// GB300 at L = 16: 9.5e10 site-updates/s at 8192^2 (persistent tiles) and
-// 6.7e10 at 1024^2 against 4.9e10 and 4.1e10 for the general per-sweep
-// kernel; 3.2e10 at 512^2 against 3.7e10 for the wavefront kernel.
+// GB300 at L = 16: 1.05e11 site-updates/s at 8192^2 (TMA tiles) and 6.9e10
+// at 1024^2 against 4.9e10 and 4.1e10 for the general per-sweep kernel;
+// 3.2e10 at 512^2 against 3.7e10 for the wavefront kernel.
 bool uses_small(const pcad_chain *ch)
 {
     if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !pca_small_eligible(ch->dm))
