@@ -71,7 +71,7 @@ NCU_SMALL_NOTE = ("ncu dram__bytes_read+write of one accumulating pca_small_tma_
                   "at 8192^2 L=16 (profiles/pca_small_tma_l16_6144sq.md)")
 
 KERNEL_KINDS = {"auto": 0, "cuda_core": 1, "tensor": 2, "wave": 3, "small": 4, "resident": 5,
-                "window": 6, "window_wave": 7}
+                "window": 6, "window_wave": 7, "binary": 8}
 KERNEL_NAMES = {
     1: "pca_direct_kernel (CUDA cores, one launch per sweep)",
     2: "pca_tcw_kernel<4,0,0,0> (tcgen05 windowed tent sums, CUDA-core CDF, wavefront, "
@@ -83,6 +83,7 @@ KERNEL_NAMES = {
        "memory, exact per-configuration thresholds)",
     6: "pca_win_kernel (CUDA cores, hull chunks from a tent-byte table, one launch per sweep)",
     7: "pca_winw_kernel (the windowed draw as a wavefront, one launch per 32 sweeps)",
+    8: "pca_binary_kernel (two labels, threshold table, one launch per sweep)",
 }
 
 
@@ -112,13 +113,13 @@ def _args():
                         "images and the q grid; cpu: the FP64 oracle on the host cores "
                         "(single-threaded Gibbs and PCA, OpenMP PCA) beside the GPU chain")
     p.add_argument("--kernel", default="auto",
-                   choices=["auto", "cuda_core", "tensor", "wave", "small", "resident", "window",
-                            "window_wave"],
+                   choices=list(KERNEL_KINDS),
                    help="kernel of the unblocked PCA sweep (headline chain and profile case): "
-                        "auto = for eligible models with L >= 192 the windowed CUDA-core sweep "
-                        "on large images and the tensor-core sweep on small ones, else the "
-                        "small-label, resident, per-sweep or wavefront CUDA-core kernel; "
-                        "tensor = prior sums by tcgen05.mma; window = the windowed sweep")
+                        "auto = for eligible models with L >= 32 the windowed CUDA-core sweep "
+                        "on large images and the tensor-core sweep on small ones (L >= 192), "
+                        "else the small-label, resident, two-label, per-sweep or wavefront "
+                        "CUDA-core kernel; tensor = prior sums by tcgen05.mma; window = the "
+                        "windowed sweep; binary = the two-label sweep")
     p.add_argument("--images", type=int, default=128, help="batch: number of images")
     p.add_argument("--requests", type=int, default=200, help="serve: requests per rate")
     p.add_argument("--rates", default="10,25,50,200",

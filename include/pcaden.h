@@ -195,7 +195,12 @@ pcad_status pcad_chain_set_blocking(pcad_chain *ch, int k);
  * (the same models, either sampler) runs the windowed draw as one
  * persistent wavefront launch per block of sweeps (of Gibbs colour phases),
  * as PCAD_KERNEL_WAVE does the CUDA-core draw (energy tracking: one launch
- * per sweep); same labels. */
+ * per sweep); same labels.  PCAD_KERNEL_BINARY (L = 2, 4- or 8-neighbourhood,
+ * PCA sampler; PCAD_EINVAL otherwise) runs one launch per sweep that draws
+ * each site by one read of the resident kernel's threshold table and a
+ * compare (persistent blocks over tiles of 16 x 128 sites staged in shared
+ * memory); same labels and the same FP64 re-draw count.  AUTO takes it for
+ * two-label images of at least 2^18 sites. */
 typedef enum {
     PCAD_KERNEL_AUTO = 0,
     PCAD_KERNEL_CUDA_CORE = 1,
@@ -204,16 +209,18 @@ typedef enum {
     PCAD_KERNEL_SMALL = 4,
     PCAD_KERNEL_RESIDENT = 5,
     PCAD_KERNEL_WINDOW = 6,
-    PCAD_KERNEL_WINDOW_WAVE = 7
+    PCAD_KERNEL_WINDOW_WAVE = 7,
+    PCAD_KERNEL_BINARY = 8
 } pcad_kernel;
 pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind);
 
 /* The kernel the chain's next sweeps run: PCAD_KERNEL_CUDA_CORE (one launch
  * per sweep or Gibbs colour phase), PCAD_KERNEL_WAVE, PCAD_KERNEL_TENSOR,
- * PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT, PCAD_KERNEL_WINDOW, or -k for
- * temporal blocking with k sweeps per launch.  With PCAD_KERNEL_AUTO the
- * resident kernel
- * is taken for the two-label images it accepts without energy tracking; the
+ * PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT, PCAD_KERNEL_WINDOW,
+ * PCAD_KERNEL_BINARY, or -k for temporal blocking with k sweeps per launch.
+ * With PCAD_KERNEL_AUTO the resident kernel
+ * is taken for the two-label images it accepts without energy tracking, the
+ * two-label sweep for two-label images of at least 2^18 sites; the
  * windowed kernels for chains of models they accept with L >= 32 (any
  * neighbourhood for Gibbs) without energy tracking, by image size in blocks
  * of 4 x 32 sites per

@@ -16,6 +16,7 @@ from ._capi import (  # noqa: F401
     pcad_bands_create, pcad_bands_run, pcad_bands_sync, pcad_bands_read_sample,
     pcad_bands_read_mean, pcad_bands_info, pcad_bands_destroy, PCAD_KERNEL_CUDA_CORE, PCAD_KERNEL_TENSOR, PCAD_KERNEL_WAVE,
     PCAD_KERNEL_SMALL, PCAD_KERNEL_RESIDENT, PCAD_KERNEL_WINDOW, PCAD_KERNEL_WINDOW_WAVE,
+    PCAD_KERNEL_BINARY,
     pcad_chain_energy, pcad_chain_track_energy, pcad_chain_read_energies,
     pcad_chain_read_min_state, pcad_chain_kernel_in_use, pcad_chain_set_model, pcad_chain_run_schedule,
     pcad_batch_set_model,

@@ -703,6 +703,7 @@ PCAD_KERNEL_SMALL = 4
 PCAD_KERNEL_RESIDENT = 5
 PCAD_KERNEL_WINDOW = 6
 PCAD_KERNEL_WINDOW_WAVE = 7
+PCAD_KERNEL_BINARY = 8
 
 
 def pcad_chain_set_kernel(h, kind: int):

@@ -466,13 +466,25 @@ pcad_status tc_set_issue(const TcSet &ts, const std::vector<SlotDesc> &desc,
 // launch skips sweeps at or past the chain's budget, so a captured slice
 // stays valid for any start.  One pair table per distinct truncation T.
 constexpr long kSmallBigTiles = 1216;
+// Two-label chains of at least kBinBigSites sites (one wave of the
+// two-label sweep's 16 x 128-site tiles at 8 blocks per SM) run the
+// two-label sweep the same way, each with its own threshold table.
+constexpr long kBinBigSites = 1216L * 16 * 128;
 
 struct SmallSet {
     std::vector<int> big;          // slots launched one at a time
     std::vector<int> table_T;      // T of each pair table
     uint32_t *tables = nullptr;    // the pair tables, ptab_words() words each
     size_t cap = 0;                // tables allocated
+    std::vector<int> bin;          // two-label slots launched one at a time
+    uint4 *btabs = nullptr;        // their threshold tables, same order
+    size_t bcap = 0;               // tables allocated
 };
+
+size_t bin_tab_entries()
+{
+    return (size_t)btab_bytes() / sizeof(uint4);
+}
 
 // Split `in` into the small-label slots launched one at a time and the rest.
 pcad_status small_set_build(SmallSet &ss, const std::vector<SlotDesc> &d,
@@ -480,19 +492,32 @@ pcad_status small_set_build(SmallSet &ss, const std::vector<SlotDesc> &d,
 {
     ss.big.clear();
     ss.table_T.clear();
+    ss.bin.clear();
     rest.clear();
     for (int i : in) {
         DevModel m = d[i].m;
         m.ptab = reinterpret_cast<const uint32_t *>(&ss);   // eligibility of the model only
+        m.btab = reinterpret_cast<const uint4 *>(&ss);
         const long tiles = (long)((d[i].W + 31) / 32) * ((d[i].H + 15) / 16);
         if (tiles >= kSmallBigTiles && pca_small_eligible(m)) {
             ss.big.push_back(i);
             if (std::find(ss.table_T.begin(), ss.table_T.end(), m.T) == ss.table_T.end())
                 ss.table_T.push_back(m.T);
+        } else if ((long)d[i].H * d[i].W >= kBinBigSites && binary_eligible(m)) {
+            ss.bin.push_back(i);
         } else {
             rest.push_back(i);
         }
     }
+    if (ss.bin.size() > ss.bcap) {
+        if (ss.btabs)
+            B_TRY(cudaFreeAsync(ss.btabs, st));
+        ss.btabs = nullptr;
+        ss.bcap = std::max(ss.bin.size(), 2 * ss.bcap);
+        B_TRY(cudaMallocAsync((void **)&ss.btabs, ss.bcap * bin_tab_entries() * sizeof(uint4), st));
+    }
+    for (size_t p = 0; p < ss.bin.size(); ++p)
+        B_TRY(launch_btab(d[ss.bin[p]].m, ss.btabs + p * bin_tab_entries(), st));
     if (ss.table_T.size() > ss.cap) {
         if (ss.tables)
             B_TRY(cudaFreeAsync(ss.tables, st));
@@ -530,6 +555,36 @@ pcad_status small_set_issue(const SmallSet &ss, const std::vector<SlotDesc> &des
             B_TRY(launch_pca_small(a, st, d.x[0], d.x[1], d.budget));
         }
     }
+    for (size_t p = 0; p < ss.bin.size(); ++p) {
+        const SlotDesc &d = desc[ss.bin[p]];
+        SweepArgs a{};
+        a.g = d.g;
+        a.acc = d.acc;
+        a.fp64_draws = d.fp64_draws;
+        a.sweep_base = d.tdev;
+        a.seed = d.seed;
+        a.H = d.H;
+        a.W = d.W;
+        a.pitch = d.pitch;
+        a.chain = d.chain;
+        a.burn_in = d.burn_in;
+        a.m = d.m;
+        a.m.btab = ss.btabs + p * bin_tab_entries();
+        for (int s = 0; s < n; ++s) {
+            a.sweep_off = (uint32_t)s;
+            B_TRY(launch_pca_binary(a, st, d.x[0], d.x[1], d.budget));
+        }
+    }
+    return PCAD_OK;
+}
+
+// The threshold table of two-label slot i again (its coefficients changed);
+// no-op for other slots.
+pcad_status small_set_retable(const SmallSet &ss, const SlotDesc &d, int i, cudaStream_t st)
+{
+    for (size_t p = 0; p < ss.bin.size(); ++p)
+        if (ss.bin[p] == i)
+            B_TRY(launch_btab(d.m, ss.btabs + p * bin_tab_entries(), st));
     return PCAD_OK;
 }
 
@@ -635,9 +690,14 @@ void small_set_free(SmallSet &ss, cudaStream_t st)
 {
     if (ss.tables)
         cudaFreeAsync(ss.tables, st);
+    if (ss.btabs)
+        cudaFreeAsync(ss.btabs, st);
     ss.tables = nullptr;
+    ss.btabs = nullptr;
     ss.cap = 0;
+    ss.bcap = 0;
     ss.big.clear();
+    ss.bin.clear();
     ss.table_T.clear();
 }
 
@@ -1048,13 +1108,16 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
     dm.ta64 = (const double *)(base + sm.ta);
     dm.pr64 = (const double *)(base + sm.pr);
     b->desc[i].m = dm;
-    if (b->desc[i].tctab) {   // the tensor-core sweep's outside sums follow the model
+    if (b->desc[i].tctab)   // the tensor-core sweep's outside sums follow the model
         B_TRY(launch_tc_table(dm, const_cast<float *>(b->desc[i].tctab), b->stream));
-        // a large slot's launch carries the model: capture the slice again
-        const bool own_launch =
-            std::find(b->tc.big.begin(), b->tc.big.end(), i) != b->tc.big.end() ||
-            std::find(b->tc.win.begin(), b->tc.win.end(), i) != b->tc.win.end() ||
-            std::find(b->tc.winw.begin(), b->tc.winw.end(), i) != b->tc.winw.end();
+    {
+        // a slot with launches of its own carries the model in their
+        // arguments: capture the slice again
+        auto in = [i](const std::vector<int> &v) {
+            return std::find(v.begin(), v.end(), i) != v.end();
+        };
+        const bool own_launch = in(b->tc.big) || in(b->tc.win) || in(b->tc.winw) ||
+                                in(b->small.big) || in(b->small.bin);
         if (b->graph && own_launch) {
             B_TRY(cudaStreamSynchronize(b->stream));
             cudaGraphExecDestroy(b->graph);
@@ -1065,6 +1128,8 @@ pcad_status pcad_batch_set_model(pcad_batch *b, int i, const pcad_model *m)
                           b->stream));
     {
         pcad_status st2 = res_set_retable(b->res, b->desc[i], i, b->stream);
+        if (st2 == PCAD_OK)
+            st2 = small_set_retable(b->small, b->desc[i], i, b->stream);
         if (st2 != PCAD_OK)
             return st2;
     }

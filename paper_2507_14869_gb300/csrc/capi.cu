@@ -420,6 +420,21 @@ bool small_tma(const pcad_chain *ch)
     return ch->maps_ready && (long long)ch->H * ch->W >= kSmallTmaMinSites && uses_small(ch);
 }
 
+// Unblocked two-label PCA sweeps, one launch per sweep with the threshold
+// table of the resident kernel (a table read and a compare per site): on
+// request, or with AUTO for images of kBinaryAutoMinSites sites and more
+// (smaller images run whole runs on the resident kernel, or the per-sweep
+// CUDA-core kernel).
+bool uses_binary(const pcad_chain *ch)
+{
+    if (ch->model.sampler != PCAD_SAMPLER_PCA || ch->tb_k > 0 || !binary_eligible(ch->dm))
+        return false;
+    if (ch->kernel == PCAD_KERNEL_BINARY)
+        return true;
+    return ch->kernel == PCAD_KERNEL_AUTO && !uses_resident(ch) &&
+           (long long)ch->H * ch->W >= kBinaryAutoMinSites;
+}
+
 // Unblocked PCA sweeps as wavefront launches (L0 price, no per-sweep energy).
 // AUTO takes them where the measured GB300 sweep favoured them: L >= 16 and
 // between 1/2 and 3 waves of the per-sweep kernel (10 resident 4 x 32 tiles
@@ -524,6 +539,8 @@ pcad_status issue_sweeps(pcad_chain *ch, int off0, int n, int &cur, cudaStream_t
             else if (uses_small(ch))
                 // chains check g < L at creation: the data term from a table
                 CUDA_TRY(launch_pca_small(a, st, nullptr, nullptr, nullptr, true));
+            else if (uses_binary(ch))
+                CUDA_TRY(launch_pca_binary(a, st));
             else if (uses_win(ch))
                 CUDA_TRY(launch_pca_win(a, ch->ftab, st));
             else
@@ -937,6 +954,8 @@ pcad_status pcad_chain_kernel_in_use(const pcad_chain *ch, int *kind)
         *kind = PCAD_KERNEL_WAVE;
     else if (uses_small(ch))
         *kind = PCAD_KERNEL_SMALL;
+    else if (uses_binary(ch))
+        *kind = PCAD_KERNEL_BINARY;
     else if (uses_win(ch))
         *kind = PCAD_KERNEL_WINDOW;
     else
@@ -1054,15 +1073,19 @@ pcad_status pcad_chain_set_kernel(pcad_chain *ch, int kind)
     if (kind != PCAD_KERNEL_AUTO && kind != PCAD_KERNEL_CUDA_CORE &&
         kind != PCAD_KERNEL_TENSOR && kind != PCAD_KERNEL_WAVE && kind != PCAD_KERNEL_SMALL &&
         kind != PCAD_KERNEL_RESIDENT && kind != PCAD_KERNEL_WINDOW &&
-        kind != PCAD_KERNEL_WINDOW_WAVE)
+        kind != PCAD_KERNEL_WINDOW_WAVE && kind != PCAD_KERNEL_BINARY)
         return fail(PCAD_EINVAL, "kernel kind must be PCAD_KERNEL_AUTO, _CUDA_CORE, _TENSOR, "
-                                 "_WAVE, _SMALL, _RESIDENT, _WINDOW or _WINDOW_WAVE");
+                                 "_WAVE, _SMALL, _RESIDENT, _WINDOW, _WINDOW_WAVE or _BINARY");
     if (kind == PCAD_KERNEL_WINDOW_WAVE && !pca_win_eligible(ch->dm))
-        return fail(PCAD_EINVAL, "the windowed wavefront sweep needs 64 <= L <= 256, T <= 33, "
+        return fail(PCAD_EINVAL, "the windowed wavefront sweep needs 9 <= L <= 256, T <= 33, "
                                  "nbhd T <= 255 and the L0 price");
     if (kind == PCAD_KERNEL_WINDOW && !pca_win_eligible(ch->dm))
-        return fail(PCAD_EINVAL, "the windowed sweep needs 64 <= L <= 256, T <= 33, "
+        return fail(PCAD_EINVAL, "the windowed sweep needs 9 <= L <= 256, T <= 33, "
                                  "nbhd T <= 255 and the L0 inertia price");
+    if (kind == PCAD_KERNEL_BINARY &&
+        (ch->model.sampler != PCAD_SAMPLER_PCA || !binary_eligible(ch->dm)))
+        return fail(PCAD_EINVAL, "the two-label sweep needs the PCA sampler, L = 2 and 4 or 8 "
+                                 "neighbours");
     if (kind == PCAD_KERNEL_RESIDENT && !resident_eligible(ch->dm, ch->H, ch->W))
         return fail(PCAD_EINVAL, "the resident kernel needs L = 2, 4 or 8 neighbours and at most "
                                  "4096 quads of 4 sites (H * ceil(W / 4))");

@@ -368,6 +368,16 @@ cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s, uint8_t *x0 = n
 // final state goes to x_out (x_in itself for Gibbs, the other plane when
 // nsweeps is odd for PCA).
 bool resident_eligible(const DevModel &m, int H, int W);
+// Two-label PCA sweep a.xin -> a.xout with the threshold table m.btab, one
+// launch per sweep (any image size; the planes read and written as words).
+// x0 / x1 (optional): the planes of even / odd sweep indices, used in place
+// of a.xin / a.xout; budget (optional): sweeps with index >= *budget are
+// skipped.
+bool binary_eligible(const DevModel &m);
+cudaError_t launch_pca_binary(const SweepArgs &a, cudaStream_t s, uint8_t *x0 = nullptr,
+                              uint8_t *x1 = nullptr, const uint32_t *budget = nullptr);
+// AUTO takes it for two-label images of this many sites and more.
+constexpr long long kBinaryAutoMinSites = 1ll << 18;
 cudaError_t launch_resident(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_out, int nsweeps,
                             bool gibbs, cudaStream_t s);
 // The two-label draw thresholds of every site configuration (L = 2), from

@@ -394,6 +394,162 @@ cudaError_t launch_res_q(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_out
     return launch_res_t<NB, GIBBS, kResMaxQuadsPerThread>(a, x_in, x_out, n, st);
 }
 
+// ------------------------------------------------------- large images
+// Two labels on images too large for one CTA: one launch per sweep, the
+// same threshold table (a table read and a compare per site), persistent
+// blocks of 256 threads over tiles of 16 rows x 128 columns.  A block stages
+// its tile's label words with a one-word halo in shared memory (words
+// outside the image and bytes beyond W read as zero: a missing neighbour
+// counts as no label-1 neighbour, and its absence enters through nm), and
+// each thread takes two quads: neighbour counts by byte-wise adds, the base
+// (g (NB + 1) + nm) (NB + 1) from the observation word (g < 2, checked at
+// chain creation), one Philox call, four table reads, one 32-bit label
+// store and one float4 accumulator update.
+constexpr int kBinThreads = 256;
+constexpr int kBinRows = 16;
+constexpr int kBinQW = 32;                 // quads (4-site words) per tile row
+constexpr int kBinPW = kBinQW + 2;         // staged words per row
+constexpr int kBinWords = (kBinRows + 2) * kBinPW;
+
+// Planes: a.xin -> a.xout, or (x0 != nullptr) x0 / x1 holding the states of
+// even / odd sweep indices; budget (optional): a sweep with index >= *budget
+// is skipped (a chain of a batch or of the server).
+template <int NB>
+__global__ void __launch_bounds__(kBinThreads)
+    pca_binary_kernel(const SweepArgs a, int tiles_x, int ntiles, int acc_vec, uint8_t *x0,
+                      uint8_t *x1, const uint32_t *budget)
+{
+    constexpr int NE = btab_entries<NB>();
+    __shared__ uint4 tab[NE];
+    __shared__ uint32_t X[kBinWords];
+    const int tid = (int)threadIdx.x;
+    const uint32_t t = sweep_index(a);
+    if (budget && t >= *budget)
+        return;   // the whole launch, before any barrier
+    const uint8_t *xin = x0 ? ((t & 1u) ? x1 : x0) : a.xin;
+    uint8_t *xout = x0 ? ((t & 1u) ? x0 : x1) : a.xout;
+    for (int i = tid; i < NE; i += kBinThreads)
+        tab[i] = a.m.btab[i];
+    const bool acc_on = accumulate_after(a, t);
+    const int H = a.H, W = a.W, pitch = a.pitch;
+    const int Wq = (W + 3) >> 2;
+    uint32_t nre = 0u;
+    for (int tile = (int)blockIdx.x; tile < ntiles; tile += (int)gridDim.x) {
+        const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        const int r0 = ty * kBinRows, q0 = tx * kBinQW;
+        __syncthreads();   // the table is in place; the last tile's words are read
+        for (int i = tid; i < kBinWords; i += kBinThreads) {
+            const int lr = i / kBinPW, lw = i - lr * kBinPW;
+            const int gr = r0 - 1 + lr, gq = q0 - 1 + lw;
+            uint32_t w = 0u;
+            if (gr >= 0 && gr < H && gq >= 0 && gq < Wq) {
+                w = *reinterpret_cast<const uint32_t *>(xin + (size_t)gr * pitch + 4 * gq);
+                const int nv = W - 4 * gq;
+                if (nv < 4)
+                    w &= (1u << (8 * nv)) - 1u;
+            }
+            X[i] = w;
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int k = tid; k < kBinRows * kBinQW; k += kBinThreads) {
+            const int lr = k / kBinQW, lq = k - lr * kBinQW;
+            const int gr = r0 + lr, gq = q0 + lq;
+            if (gr >= H || gq >= Wq)
+                continue;
+            const int nv = min(4, W - 4 * gq);
+            const uint32_t act = nv >= 4 ? 0xFFFFFFFFu : (1u << (8 * nv)) - 1u;
+            uint32_t M;
+            uint32_t S = quad_counts<NB>(X, (lr + 1) * kBinPW + 1 + lq, kBinPW, M);
+            const uint32_t G =
+                *reinterpret_cast<const uint32_t *>(a.g + (size_t)gr * pitch + 4 * gq);
+            S += (G & act & 0x01010101u) * (uint32_t)((NB + 1) * (NB + 1));
+            if (gr == 0 || gr == H - 1 || gq == 0 || 4 * gq + 4 >= W) {
+                // neighbours outside the image: nm (NB + 1) per byte
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = 4 * gq + j;
+                    int nm = (gr == 0) + (gr == H - 1) + (c == 0) + (c == W - 1);
+                    if (NB == 8)
+                        nm += (gr == 0 || c == 0) + (gr == 0 || c == W - 1) +
+                              (gr == H - 1 || c == 0) + (gr == H - 1 || c == W - 1);
+                    S += (uint32_t)(nm * (NB + 1)) << (8 * j);
+                }
+            }
+            uint32_t u[4];
+            quad_uniforms(a, kTagPCA, t, gr, gq, u);
+            const uint32_t nw = quad_draw(tab, S, M, u, act, nre);
+            uint8_t *out = xout + (size_t)gr * pitch + 4 * gq;
+            float *acc = a.acc + (size_t)gr * W + 4 * gq;
+            if (nv >= 4) {
+                *reinterpret_cast<uint32_t *>(out) = nw;
+                if (acc_on) {
+                    const float l0 = (float)(nw & 0xFFu), l1 = (float)((nw >> 8) & 0xFFu),
+                                l2 = (float)((nw >> 16) & 0xFFu), l3 = (float)(nw >> 24);
+                    if (acc_vec) {
+                        const float4 v = *reinterpret_cast<const float4 *>(acc);
+                        *reinterpret_cast<float4 *>(acc) =
+                            make_float4(v.x + l0, v.y + l1, v.z + l2, v.w + l3);
+                    } else {
+                        acc[0] += l0;
+                        acc[1] += l1;
+                        acc[2] += l2;
+                        acc[3] += l3;
+                    }
+                }
+            } else {
+                for (int j = 0; j < nv; ++j) {
+                    const uint32_t sl = (nw >> (8 * j)) & 0xFFu;
+                    out[j] = (uint8_t)sl;
+                    if (acc_on)
+                        acc[j] += (float)sl;
+                }
+            }
+        }
+    }
+    const uint32_t warp_re = __reduce_add_sync(0xFFFFFFFFu, nre);
+    if ((tid & 31) == 0 && warp_re != 0u)
+        atomicAdd(a.fp64_draws, (unsigned long long)warp_re);
+}
+
+template <int NB>
+cudaError_t launch_binary_t(const SweepArgs &a, uint8_t *x0, uint8_t *x1, const uint32_t *budget,
+                            cudaStream_t st)
+{
+    static int per_sm[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (dev >= 64)
+        return cudaErrorInvalidDevice;
+    if (per_sm[dev] == 0) {
+        int n = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, pca_binary_kernel<NB>, kBinThreads,
+                                                          0);
+        if (e != cudaSuccess)
+            return e;
+        per_sm[dev] = n > 0 ? n : 1;
+    }
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess)
+        return e;
+    const int Wq = (a.W + 3) >> 2;
+    const int tiles_x = (Wq + kBinQW - 1) / kBinQW;
+    const long long ntiles = (long long)tiles_x * ((a.H + kBinRows - 1) / kBinRows);
+    if (ntiles <= 0)
+        return cudaSuccess;
+    if (ntiles >= (1ll << 31))
+        return cudaErrorInvalidValue;
+    const long long cap = (long long)per_sm[dev] * sms;
+    const int grid = (int)(ntiles < cap ? ntiles : cap);
+    const int acc_vec = (a.W % 4 == 0 && (reinterpret_cast<uintptr_t>(a.acc) & 15u) == 0) ? 1 : 0;
+    pca_binary_kernel<NB><<<grid, kBinThreads, 0, st>>>(a, tiles_x, (int)ntiles, acc_vec, x0, x1,
+                                                        budget);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 int btab_bytes()
@@ -482,6 +638,26 @@ cudaError_t launch_resident(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_
                      : launch_res_q<8, false>(a, x_in, x_out, nsweeps, st);
     return gibbs ? launch_res_q<4, true>(a, x_in, x_out, nsweeps, st)
                  : launch_res_q<4, false>(a, x_in, x_out, nsweeps, st);
+}
+
+bool binary_eligible(const DevModel &m)
+{
+    return m.L == 2 && m.norm == 0 && (m.nbhd == 4 || m.nbhd == 8) && m.btab != nullptr;
+}
+
+cudaError_t launch_pca_binary(const SweepArgs &a, cudaStream_t st, uint8_t *x0, uint8_t *x1,
+                              const uint32_t *budget)
+{
+    if (!binary_eligible(a.m))
+        return cudaErrorInvalidValue;
+    // word loads and stores of the planes
+    const uintptr_t planes = x0 ? (reinterpret_cast<uintptr_t>(x0) | reinterpret_cast<uintptr_t>(x1))
+                                : (reinterpret_cast<uintptr_t>(a.xin) |
+                                   reinterpret_cast<uintptr_t>(a.xout));
+    if ((a.pitch & 3) != 0 || ((planes | reinterpret_cast<uintptr_t>(a.g)) & 3u) != 0)
+        return cudaErrorMisalignedAddress;
+    return a.m.nbhd == 8 ? launch_binary_t<8>(a, x0, x1, budget, st)
+                         : launch_binary_t<4>(a, x0, x1, budget, st);
 }
 
 }  // namespace pcad
