@@ -383,7 +383,8 @@ void pcad_chain_destroy(pcad_chain *ch);
  * sweep, row, col), so each chain's results are bit-identical to running it
  * alone with pcad_chain_create + pcad_chain_run. */
 typedef struct {
-    const uint8_t *g_host;   /* observation (H rows of g_pitch bytes); copied at creation */
+    const uint8_t *g_host;   /* observation (H rows of g_pitch bytes, labels < L:
+                                PCAD_EINVAL otherwise); copied at creation */
     int H, W, g_pitch;
     pcad_model model;        /* sampler must be PCAD_SAMPLER_PCA */
     uint64_t seed;

@@ -73,6 +73,18 @@ pcad_status check_job(const pcad_job &j)
         return set_error(PCAD_EINVAL, "batches and the server run the PCA sampler");
     if (j.model.inertia_norm != 0 && j.model.L > 2 && j.model.inertia > 0.0f)
         return set_error(PCAD_EINVAL, "batches and the server run the L0 inertia price only");
+    // observations are labels, as for chains: the two-label and small-label
+    // kernels index their tables by g
+    if (j.model.L < 256) {
+        for (int r = 0; r < j.H; ++r) {
+            const uint8_t *row = j.g_host + (size_t)r * j.g_pitch;
+            uint8_t mx = 0;
+            for (int c = 0; c < j.W; ++c)
+                mx = row[c] > mx ? row[c] : mx;
+            if (mx >= j.model.L)
+                return set_error(PCAD_EINVAL, "observed labels are >= L");
+        }
+    }
     return PCAD_OK;
 }
 

@@ -77,3 +77,20 @@ def test_host_validation_without_gpu(so):
         pc.pcad_chain_create(g, base, seed=1, burn_in=-1)
     assert pc.pcad_status_str(0) == "ok"
     assert "sm_103a" in pc.pcad_version()
+
+
+def test_batch_rejects_observations_outside_the_labels_without_gpu(so):
+    """Batch and server jobs are checked as chains are: an observed value
+    >= L is refused (PCAD_EINVAL) before any CUDA call."""
+    import paper_2507_14869_gb300 as pc
+    m2 = dict(L=2, nbhd=4, pair=0, pair_coef=1.2, pair_T=1, noise=1, sigma=1.0, flip_p=0.1,
+              inertia=1.0, sampler=0)
+    m16 = dict(L=16, nbhd=4, pair=1, pair_coef=0.05, pair_T=30, noise=0, sigma=1.0,
+               flip_p=0.1, inertia=2.0, sampler=0)
+    for m, bad_value in ((m2, 2), (m16, 16), (m16, 255)):
+        g = np.zeros((5, 7), dtype=np.uint8)
+        g[4, 6] = bad_value   # the last site, to reach the end of the scan
+        with pytest.raises(pc.PcadError) as e:
+            pc.pcad_batch_create([(g, m, 1, 0, 0)], autotune=False)
+        assert e.value.status == 1
+        assert "observed labels" in str(e.value)
