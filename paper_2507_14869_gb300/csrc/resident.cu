@@ -404,7 +404,9 @@ cudaError_t launch_res_q(const SweepArgs &a, const uint8_t *x_in, uint8_t *x_out
 // each thread takes two quads: neighbour counts by byte-wise adds, the base
 // (g (NB + 1) + nm) (NB + 1) from the observation word (g < 2, checked at
 // chain creation), one Philox call, four table reads, one 32-bit label
-// store and one float4 accumulator update.
+// store and one float4 accumulator update.  The next tile's label words are
+// loaded into registers during the draws, and a tile's observation words
+// and accumulator sums before them.
 constexpr int kBinThreads = 256;
 constexpr int kBinRows = 16;
 constexpr int kBinQW = 32;                 // quads (4-site words) per tile row
@@ -434,25 +436,64 @@ __global__ void __launch_bounds__(kBinThreads)
     const int H = a.H, W = a.W, pitch = a.pitch;
     const int Wq = (W + 3) >> 2;
     uint32_t nre = 0u;
-    for (int tile = (int)blockIdx.x; tile < ntiles; tile += (int)gridDim.x) {
+    constexpr int kSlots = (kBinWords + kBinThreads - 1) / kBinThreads;
+    // the label words of a tile into registers (issued early, stored later)
+    auto stage_load = [&](int tile, uint32_t (&pw)[kSlots]) {
+        const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+        const int r0 = ty * kBinRows, q0 = tx * kBinQW;
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int i = tid + sl * kBinThreads;
+            pw[sl] = 0u;
+            if (i < kBinWords) {
+                const int lr = i / kBinPW, lw = i - lr * kBinPW;
+                const int gr = r0 - 1 + lr, gq = q0 - 1 + lw;
+                if (gr >= 0 && gr < H && gq >= 0 && gq < Wq) {
+                    uint32_t w = *reinterpret_cast<const uint32_t *>(xin + (size_t)gr * pitch + 4 * gq);
+                    const int nv = W - 4 * gq;
+                    if (nv < 4)
+                        w &= (1u << (8 * nv)) - 1u;
+                    pw[sl] = w;
+                }
+            }
+        }
+    };
+    uint32_t pw[kSlots];
+    int tile = (int)blockIdx.x;
+    if (tile < ntiles)
+        stage_load(tile, pw);
+    for (; tile < ntiles; tile += (int)gridDim.x) {
         const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
         const int r0 = ty * kBinRows, q0 = tx * kBinQW;
         __syncthreads();   // the table is in place; the last tile's words are read
-        for (int i = tid; i < kBinWords; i += kBinThreads) {
-            const int lr = i / kBinPW, lw = i - lr * kBinPW;
-            const int gr = r0 - 1 + lr, gq = q0 - 1 + lw;
-            uint32_t w = 0u;
-            if (gr >= 0 && gr < H && gq >= 0 && gq < Wq) {
-                w = *reinterpret_cast<const uint32_t *>(xin + (size_t)gr * pitch + 4 * gq);
-                const int nv = W - 4 * gq;
-                if (nv < 4)
-                    w &= (1u << (8 * nv)) - 1u;
-            }
-            X[i] = w;
+#pragma unroll
+        for (int sl = 0; sl < kSlots; ++sl) {
+            const int i = tid + sl * kBinThreads;
+            if (i < kBinWords)
+                X[i] = pw[sl];
         }
         __syncthreads();
-#pragma unroll 1
-        for (int k = tid; k < kBinRows * kBinQW; k += kBinThreads) {
+        if (tile + (int)gridDim.x < ntiles)
+            stage_load(tile + (int)gridDim.x, pw);   // in flight during the draws
+        constexpr int kQ = kBinRows * kBinQW / kBinThreads;
+        uint32_t Gw[kQ];
+        float4 A4[kQ];
+#pragma unroll
+        for (int qi = 0; qi < kQ; ++qi) {   // the quads' observations and sums, issued first
+            const int k = tid + qi * kBinThreads;
+            const int lr = k / kBinQW, lq = k - lr * kBinQW;
+            const int gr = r0 + lr, gq = q0 + lq;
+            Gw[qi] = 0u;
+            A4[qi] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (gr < H && gq < Wq) {
+                Gw[qi] = *reinterpret_cast<const uint32_t *>(a.g + (size_t)gr * pitch + 4 * gq);
+                if (acc_on && acc_vec && 4 * gq + 4 <= W)
+                    A4[qi] = *reinterpret_cast<const float4 *>(a.acc + (size_t)gr * W + 4 * gq);
+            }
+        }
+#pragma unroll
+        for (int qi = 0; qi < kQ; ++qi) {
+            const int k = tid + qi * kBinThreads;
             const int lr = k / kBinQW, lq = k - lr * kBinQW;
             const int gr = r0 + lr, gq = q0 + lq;
             if (gr >= H || gq >= Wq)
@@ -461,11 +502,8 @@ __global__ void __launch_bounds__(kBinThreads)
             const uint32_t act = nv >= 4 ? 0xFFFFFFFFu : (1u << (8 * nv)) - 1u;
             uint32_t M;
             uint32_t S = quad_counts<NB>(X, (lr + 1) * kBinPW + 1 + lq, kBinPW, M);
-            const uint32_t G =
-                *reinterpret_cast<const uint32_t *>(a.g + (size_t)gr * pitch + 4 * gq);
-            S += (G & act & 0x01010101u) * (uint32_t)((NB + 1) * (NB + 1));
+            S += (Gw[qi] & act & 0x01010101u) * (uint32_t)((NB + 1) * (NB + 1));
             if (gr == 0 || gr == H - 1 || gq == 0 || 4 * gq + 4 >= W) {
-                // neighbours outside the image: nm (NB + 1) per byte
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int c = 4 * gq + j;
@@ -487,7 +525,7 @@ __global__ void __launch_bounds__(kBinThreads)
                     const float l0 = (float)(nw & 0xFFu), l1 = (float)((nw >> 8) & 0xFFu),
                                 l2 = (float)((nw >> 16) & 0xFFu), l3 = (float)(nw >> 24);
                     if (acc_vec) {
-                        const float4 v = *reinterpret_cast<const float4 *>(acc);
+                        const float4 v = A4[qi];
                         *reinterpret_cast<float4 *>(acc) =
                             make_float4(v.x + l0, v.y + l1, v.z + l2, v.w + l3);
                     } else {
