@@ -355,8 +355,8 @@ cudaError_t launch_pca_small_tma(const CUtensorMap &xmap, const CUtensorMap &gma
                                  const SweepArgs &a, int *err, cudaStream_t s);
 // x0 / x1 (optional): the planes of even / odd sweep indices, used in place of
 // a.xin / a.xout; budget (optional): sweeps with index >= *budget are skipped;
-// aq: the data term from a table of the observations g < 16 (callers whose
-// observations were checked against L).
+// aq: the data term from a table of the observations g < 16 (observations
+// checked against L: chains use it).
 cudaError_t launch_pca_small(const SweepArgs &a, cudaStream_t s, uint8_t *x0 = nullptr,
                              uint8_t *x1 = nullptr, const uint32_t *budget = nullptr,
                              bool aq = false);

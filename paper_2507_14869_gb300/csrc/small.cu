@@ -20,7 +20,8 @@
 //     mantissa of 2^23 and subtracting 2^23.  Chains (whose observations are
 //     checked against L at creation) take fl(alpha q) from a 16 x 16 table in
 //     shared memory instead: one FFMA per label, fl(gam P + fl(alpha q)),
-//     within the same 3u |v| exponent bound; batches keep the arithmetic form.  (Products of two table
+//     within the same 3u |v| exponent bound; batches and the server keep the
+//     arithmetic form.  (Products of two table
 //     factors per label measured slower: the per-lane table reads conflict
 //     in shared memory, while the exponential unit has room.)
 //   * Inverse CDF over chunks of 4 labels: in-chunk prefix sums (3
