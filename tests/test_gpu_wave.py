@@ -144,6 +144,7 @@ def test_kernel_in_use_auto_rule(pc):
         assert ch.kernel_in_use() == pc.PCAD_KERNEL_WAVE
         ch.set_kernel(pc.PCAD_KERNEL_TENSOR)
         assert ch.kernel_in_use() == pc.PCAD_KERNEL_TENSOR
+    # two labels at 512^2 (2^18 sites): the two-label sweep
     binary = Model(L=2, pair=POTTS, pair_coef=1.2, noise=FLIP, flip_p=0.1, inertia=1.0)
     with pc.Chain(g, binary, seed=1) as ch:
-        assert ch.kernel_in_use() == pc.PCAD_KERNEL_CUDA_CORE
+        assert ch.kernel_in_use() == pc.PCAD_KERNEL_BINARY
